@@ -1,0 +1,219 @@
+/*
+ * fdtd_llg.h -- C ABI of the B300 (sm_103a) Yee-Maxwell + LLG solver.
+ *
+ * Method: arxiv 2510.22221, section "Numerical Model":
+ *   Ampere's law      eps0 eps_r dE/dt + sigma E = curl H - J_src   (Eq. Ampere)
+ *   Faraday's law     dB/dt = -curl E,  B = mu0 (H + M)              (Eq. Faraday)
+ *   LLG               dM/dt = -mu0|gamma| M x H_eff + (alpha/Ms) M x dM/dt  (Eq. LLG)
+ *                     H_eff = H + H_bias, |M| = Ms
+ * discretised on a staggered Yee grid with a leap-frog step: an H/M half-push
+ * with curl E^n (Eq. iterate_H with the trapezoidal LLG solve of
+ * Eqs. llg_tra4-6, iterated until max |M^r - M^{r-1}|/Ms < tol), the E push of
+ * the Ampere update with curl H^{n+1/2} and J at t = (n+1/2) dt, and a second
+ * H/M half-push with curl E^{n+1}.  Every field update runs in hand-written
+ * CUDA kernels; fields are FP32, probe series, energies and gradients FP64.
+ *
+ * Grid and layout.  nx*ny*nz cells of size dx*dy*dz, PEC walls on all six
+ * faces.  Cell (i,j,k) spans [i,i+1]x[j,j+1]x[k,k+1] in units of the cell.
+ *   Ex(i,j,k) sits at (i+1/2, j, k)      Hx(i,j,k) at (i, j+1/2, k+1/2)
+ *   Ey(i,j,k) at (i, j+1/2, k)           Hy(i,j,k) at (i+1/2, j, k+1/2)
+ *   Ez(i,j,k) at (i, j, k+1/2)           Hz(i,j,k) at (i+1/2, j+1/2, k)
+ *   M(i,j,k) at the cell centre (magnetic cells only).
+ * Host arrays passed to or from the library are "compact": nx*ny*nz values,
+ * i fastest, then j, then k.  Edge values in a wall are zero and are not
+ * stored beyond index n-1; the normal H on the three far walls (i = nx,
+ * j = ny, k = nz) is stored in separate wall arrays (FDTD_F_HX_WALL ...).
+ *
+ * Edge material: eps_r and sigma of an edge are the mean over its four
+ * cells; an edge touching a PEC cell, or lying in a wall, holds E = 0.  A
+ * face adjacent to a magnetic cell subtracts half of that cell's change of
+ * M; H_eff at a cell centre is the mean of the two faces of each component
+ * plus H_bias.  Magnetisation is held as its deviation m = M - Ms h from the
+ * bias direction h = H_bias/|H_bias| (z when the bias is zero), expressed in
+ * a frame whose third axis is h, so that FP32 resolves small precession
+ * angles to full relative precision.
+ *
+ * Threading: a handle is not thread-safe; calls on one handle must be
+ * serialised by the caller.  Errors: every int-returning call returns
+ * FDTD_OK (0) or a negative FDTD_E_* code; fdtd_llg_last_error() returns a
+ * message for the last failing call on that handle.  Kernel-side conditions
+ * (LLG not converged, non-finite energy) are latched on the device and
+ * reported by the next call that synchronises (fdtd_llg_sync, probe, energy,
+ * get_field, save_state).
+ *
+ * Memory: the handle owns its device memory.  By default it is obtained with
+ * cudaMalloc; a caller may supply an allocator (fdtd_llg_config.alloc/free),
+ * e.g. a framework's caching allocator.  Host pointers passed in are only read
+ * during the call; output buffers are caller-owned.
+ */
+#ifndef FDTD_LLG_H
+#define FDTD_LLG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FDTD_LLG_ABI_VERSION 1
+
+enum {
+    FDTD_OK = 0,
+    FDTD_E_INVAL = -1,        /* bad argument, size or geometry                */
+    FDTD_E_CUDA = -2,         /* a CUDA call failed                            */
+    FDTD_E_OOM = -3,          /* device or host allocation failed              */
+    FDTD_E_UNSTABLE = -4,     /* dt above the Courant limit, or energy not finite */
+    FDTD_E_LLG_NOCONV = -5,   /* an LLG solve did not reach llg_tol            */
+    FDTD_E_STATE = -6,        /* call not valid in the handle's present state  */
+    FDTD_E_RANGE = -7,        /* index out of range                            */
+    FDTD_E_NOSYS = -8         /* not supported for this handle                 */
+};
+
+typedef struct fdtd_llg_s *fdtd_llg_t;
+
+typedef void *(*fdtd_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*fdtd_free_fn)(void *ptr, void *user);
+
+typedef struct {
+    int32_t nx, ny, nz;        /* cells                                        */
+    double dx, dy, dz;         /* cell size (m)                                */
+    double dt;                 /* time step (s); 0: courant_factor x 3-D limit  */
+    double courant_factor;     /* used when dt == 0 (e.g. 0.5; paper: 0.9)     */
+    double llg_tol;            /* LLG residual tolerance; 0: 1e-6              */
+    int32_t llg_max_iter;      /* 0: 20                                        */
+    int32_t llg_fixed_iter;    /* > 0: exactly this many iterations, no test   */
+    int32_t probe_capacity;    /* steps kept in the probe/energy rings; 0: 4096 */
+    int32_t energy_every;      /* 1: energy each step; 0: never                */
+    int32_t device;            /* CUDA device ordinal                          */
+    void *stream;              /* cudaStream_t; NULL: a stream the handle owns  */
+    fdtd_alloc_fn alloc;       /* NULL: cudaMalloc                             */
+    fdtd_free_fn free;         /* NULL: cudaFree                               */
+    void *alloc_user;
+} fdtd_llg_config;
+
+typedef struct {
+    double eps_r;              /* relative permittivity                        */
+    double sigma;              /* conductivity (S/m)                           */
+    double Ms;                 /* saturation magnetisation (A/m); 0: non-magnetic */
+    double alpha;              /* Gilbert damping                              */
+    double gamma;              /* |gamma| (rad/(s T)), e.g. 1.76e11            */
+    int32_t is_pec;            /* 1: perfect electric conductor                */
+    int32_t pad_;
+} fdtd_material;
+
+/* field selectors for get_field / set_field */
+enum {
+    FDTD_F_EX = 0, FDTD_F_EY, FDTD_F_EZ, FDTD_F_HX, FDTD_F_HY, FDTD_F_HZ,
+    FDTD_F_MX, FDTD_F_MY, FDTD_F_MZ,                  /* M (A/m), global axes      */
+    FDTD_F_HX_WALL, FDTD_F_HY_WALL, FDTD_F_HZ_WALL,   /* ny*nz, nx*nz, nx*ny       */
+    FDTD_F_DMX, FDTD_F_DMY, FDTD_F_DMZ                /* M - Ms h, global axes     */
+};
+
+/* Create a solver for one grid (a batch of one).  dt > Courant limit ->
+ * FDTD_E_UNSTABLE.  Fields start at zero; materials must be set before the
+ * first step. */
+int fdtd_llg_create(const fdtd_llg_config *cfg, fdtd_llg_t *out);
+
+/* Create n independent instances advanced together by fdtd_llg_step on the
+ * returned handle (the bias-sweep pattern).  Each cfgs[i] gives an instance's
+ * grid; all share dt (dt = 0 takes the smallest Courant step of the set),
+ * and the device, stream, allocator and LLG settings of cfgs[0].  Instance
+ * handles come from fdtd_llg_batch_member. */
+int fdtd_llg_create_batch(const fdtd_llg_config *cfgs, int32_t n, fdtd_llg_t *out);
+
+/* Handle of instance i of a batch (owned by the batch; do not destroy).
+ * A single-instance handle is its own member 0. */
+int fdtd_llg_batch_member(fdtd_llg_t batch, int32_t i, fdtd_llg_t *member);
+
+/* Materials (section "Numerical Model": eps_r, sigma per cell; Ms, alpha in
+ * magnets).  mat_id: nx*ny*nz bytes, compact layout, host or device pointer.
+ * table: ntable <= 255 entries, host.  hbias: H_bias (A/m), host.
+ * eps_r_design (nullable): per-cell eps_r over the box design_box =
+ * {i0, j0, k0, ni, nj, nk} (compact in that box, host), overriding the table's
+ * eps_r there.  Resets E, H to 0 and M to Ms h in magnetic cells, and the
+ * batch's step count to 0.  Each face-connected magnetic region must fit in a
+ * bounding box of at most 4096 cells; at most 16 magnetic materials.
+ * Errors: FDTD_E_INVAL (bad id, table, box or magnet region). */
+int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const fdtd_material *table,
+                           int32_t ntable, const double hbias[3], const double *eps_r_design,
+                           const int32_t design_box[6]);
+
+/* Point current density on one edge (section "Modeling Setup": modulated
+ * Gaussian J = J0 exp(-(t - t_peak)^2 / (2 Tp^2)) cos(2 pi f0 t)); comp 0/1/2
+ * selects an Ex/Ey/Ez edge with the indices of the layout above.  Tp = 0 ->
+ * 1/f0 (one period); t_peak = 0 -> 3 Tp.  At most 4 sources per instance.
+ * Adds to the sources already set. */
+int fdtd_llg_set_source(fdtd_llg_t h, int32_t comp, int32_t i, int32_t j, int32_t k,
+                        double J0, double f0, double Tp, double t_peak);
+
+/* Probe at cell (i,j,k): records, after every step n, the nine values
+ * Ex, Ey, Ez, Hx, Hy, Hz (the native components with index (i,j,k)) and
+ * Mx, My, Mz of the cell at time n dt, in FP64 (section "Datasets Curation":
+ * point samples of the fields).  At most 32 probes per instance; add probes
+ * before the first step. */
+int fdtd_llg_add_probe(fdtd_llg_t h, int32_t i, int32_t j, int32_t k, int32_t *id);
+
+/* Advance nsteps full steps on the handle's stream (asynchronous; a batch
+ * advances all its instances).  Kernel-side errors surface at the next
+ * synchronising call. */
+int fdtd_llg_step(fdtd_llg_t h, int64_t nsteps);
+
+/* Wait for the handle's stream and report latched device errors. */
+int fdtd_llg_sync(fdtd_llg_t h);
+
+/* Copy the last min(cap_rows, steps recorded, probe_capacity) rows of probe
+ * `id` to out (rows x 9 doubles, oldest first); *rows = rows written. */
+int fdtd_llg_probe(fdtd_llg_t h, int32_t id, double *out, int64_t cap_rows, int64_t *rows);
+
+/* Copy the last min(cap, steps, probe_capacity) energies
+ * W = sum_edges eps E^2/2 dV + sum_faces mu0 H^2/2 dV + sum_cells mu0 (|H0| Ms - H0.M) dV
+ * (oldest first, one per step) to out. */
+int fdtd_llg_energy(fdtd_llg_t h, double *out, int64_t cap, int64_t *written);
+
+/* Steps completed, and whether H and M are stored half a step ahead of E
+ * (1 after the first step; get_field then returns H, M at (n + 1/2) dt). */
+int fdtd_llg_time_state(fdtd_llg_t h, int64_t *step, int32_t *h_half_ahead);
+
+/* Read / write one field in the compact host layout (float32).  set_field
+ * declares the state to be at integer time (H, M not half a step ahead).
+ * FDTD_F_M* / FDTD_F_DM* entries outside magnets are zero and ignored on
+ * write. */
+int fdtd_llg_get_field(fdtd_llg_t h, int32_t which, float *out, size_t count);
+int fdtd_llg_set_field(fdtd_llg_t h, int32_t which, const float *in, size_t count);
+
+/* Checkpoint / resume of E, H, M, wall faces, step and time state.
+ * buf = NULL: *size receives the byte count needed. */
+int fdtd_llg_save_state(fdtd_llg_t h, void *buf, size_t *size);
+int fdtd_llg_load_state(fdtd_llg_t h, const void *buf, size_t size);
+
+/* Per-pass device time, measured with CUDA events that the library records
+ * on its stream around every launch while profiling is on (the kernels
+ * themselves are unchanged).  Pass kinds: E push, magnetic-region push (LLG),
+ * H push. */
+typedef struct {
+    int64_t launches[3];       /* E, magnet, H                                  */
+    double ms[3];              /* summed device time of those launches (ms)     */
+    int64_t cells;             /* cells advanced per launch of the E and H passes */
+} fdtd_llg_profile;
+
+int fdtd_llg_set_profiling(fdtd_llg_t h, int32_t on);
+
+/* Synchronise, add up the recorded events into *out; reset != 0 clears the
+ * record afterwards. */
+int fdtd_llg_read_profile(fdtd_llg_t h, fdtd_llg_profile *out, int32_t reset);
+
+/* Release everything.  NULL is accepted.  Members of a batch are released
+ * with the batch. */
+void fdtd_llg_destroy(fdtd_llg_t h);
+
+/* Message of the last failing call on h (thread-local when h is NULL). */
+const char *fdtd_llg_last_error(fdtd_llg_t h);
+
+/* Version of this ABI (FDTD_LLG_ABI_VERSION). */
+int fdtd_llg_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDTD_LLG_H */

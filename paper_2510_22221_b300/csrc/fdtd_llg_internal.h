@@ -1,0 +1,101 @@
+// Internal structures shared by the host runtime and the sm_103a kernels of
+// the Yee-Maxwell + LLG solver.  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fl {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kMu0 = 4.0e-7 * kPi;       // vacuum permeability (H/m)
+constexpr double kC0 = 299792458.0;         // speed of light (m/s)
+constexpr double kEps0 = 1.0 / (kMu0 * kC0 * kC0);
+
+constexpr int kMaxSrc = 4;
+constexpr int kMaxProbe = 32;
+constexpr int kMaxMagMat = 16;
+
+// Tile of the two-pass E and H kernels: 32 (x, one warp) x 8 (y) columns,
+// each thread marching kKC planes in z.
+constexpr int kTX = 32, kTY = 8, kKC = 16;
+
+// Magnet kernel: one CTA per face-connected magnetic region, whose bounding
+// box holds at most kMagMaxV cells, kMagCPT cells per thread.
+constexpr int kMagThreads = 512;
+constexpr int kMagMaxV = 4096;
+constexpr int kMagCPT = kMagMaxV / kMagThreads;
+
+// Class-table entry flags (bit field stored in the .w of the first float4).
+enum : uint32_t { CF_MAG_HX = 1u, CF_MAG_HY = 2u, CF_MAG_HZ = 4u };
+
+struct MagMat {
+    float Ms, inv_Ms, alpha, kappa;   // kappa = mu0 |gamma| (dt/2) / 2
+};
+
+// Everything a kernel needs about one grid instance.
+struct Inst {
+    float *Ex, *Ey, *Ez, *Hx, *Hy, *Hz;   // [nz][ny][px], x fastest
+    float *wHx, *wHy, *wHz;               // far-wall normal H: [nz][ny], [nz][nx], [ny][nx]
+    const void *cls;                      // class id per cell: uint8 or uint16
+    const float4 *ctab;                   // 3 float4 per class: (ca, flags) (cb) (eps/2)
+    double *probe_buf;                    // [cap][nprobe][9]
+    double *energy_buf;                   // [cap]
+    int nx, ny, nz, px;
+    long long plane;                      // ny * px
+    float idx, idy, idz;                  // 1/dx, 1/dy, 1/dz
+    float ch;                             // dt / (2 mu0), one half-push
+    float R[9];                           // rows: bias frame axes e1, e2, e3 = h (global coords)
+    float h0n;                            // |H_bias|
+    double u[3];                          // h = H_bias / |H_bias| (z when zero), FP64
+    double dt, dV;
+    int cap;                              // probe / energy ring length (steps)
+    int nsrc, nprobe;
+    int src[kMaxSrc][4];                  // comp, i, j, k
+    double srcp[kMaxSrc][4];              // J0, f0, Tp, tpk
+    int probe[kMaxProbe][3];
+    int tile_off, ntx, nty, ntz;          // tiles of this instance in the tile list
+    int mag_off, nmag;                    // magnet regions of this instance
+    MagMat mm[kMaxMagMat];
+};
+
+struct MagComp {
+    int inst;
+    int x0, y0, z0, bx, by, bz, V;
+    float *m;               // deviation M - Ms h in the bias frame: 3 blocks of V
+    const uint8_t *mat;     // V: magnet material index, 0xFF outside this region
+};
+
+// Device-resident control block of a batch.
+struct StepCtl {
+    long long step;         // completed steps
+    unsigned int counter;   // CTAs of the H pass that have finished this step
+    int status;             // latched error bits (ST_*)
+};
+enum : int { ST_NOCONV = 1, ST_UNSTABLE = 2 };
+
+struct LaunchSet {
+    const Inst *insts;
+    int ninst;
+    const int *tile_inst;
+    int ntiles;
+    const MagComp *comps;
+    int ncomp;
+    int vmax;
+    StepCtl *ctl;
+    double *part_e, *part_h, *part_m;   // energy partials per tile / per region
+    int grid_e, grid_h;
+    bool cls16;
+    float llg_tol;
+    int llg_max_iter, llg_fixed_iter;
+    int energy;
+};
+
+// Launchers (kernels_fwd.cu).  mode 0: a single H/M half-push (start-up);
+// mode 1: full step.
+cudaError_t launch_e_pass(const LaunchSet &L, cudaStream_t s);
+cudaError_t launch_h_pass(const LaunchSet &L, int mode, cudaStream_t s);
+cudaError_t launch_mag_pass(const LaunchSet &L, int mode, cudaStream_t s);
+int e_pass_blocks_per_sm(bool cls16);
+int h_pass_blocks_per_sm(bool cls16);
+
+}  // namespace fl
