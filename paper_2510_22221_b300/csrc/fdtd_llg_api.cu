@@ -1,0 +1,1063 @@
+// Host runtime of the C ABI declared in include/fdtd_llg.h: handles, device
+// memory, material preprocessing, magnetic-region discovery, launches.
+#include "../../include/fdtd_llg.h"
+#include "fdtd_llg_internal.h"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+using namespace fl;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct Instance {
+    int nx = 0, ny = 0, nz = 0, px = 0;
+    double dx = 0, dy = 0, dz = 0;
+    bool materials_set = false;
+    // device buffers (owned through Sim's allocator)
+    float *fields = nullptr;          // 6 arrays of nz*ny*px
+    float *walls = nullptr;           // wHx, wHy, wHz
+    void *cls = nullptr;
+    int cls_bytes = 1;
+    float4 *ctab = nullptr;
+    int nclass = 0;
+    double *probe_buf = nullptr;
+    int probe_alloc = -1;             // probes the probe ring was sized for
+    double *energy_buf = nullptr;
+    float *mbuf = nullptr;            // all regions' deviation m (bias frame)
+    uint8_t *magmat = nullptr;        // all regions' material maps
+    // host descriptions
+    std::vector<std::array<int, 4>> src;
+    std::vector<std::array<double, 4>> srcp;
+    std::vector<std::array<int, 3>> probes;
+    std::vector<MagComp> comps;       // device pointers inside
+    std::vector<MagMat> mm;
+    std::vector<double> mm_Ms;        // Ms of each magnet material (FP64)
+    double hbias[3] = {0, 0, 0};
+    double u[3] = {0, 0, 1};          // bias direction
+    float R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};   // bias frame rows (e1, e2, e3 = u)
+    size_t n_field() const { return (size_t)nz * ny * px; }
+    size_t n_wall() const { return (size_t)ny * nz + (size_t)nx * nz + (size_t)nx * ny; }
+};
+
+struct Sim {
+    std::vector<Instance> inst;
+    std::vector<struct fdtd_llg_s *> members;
+    double dt = 0;
+    fdtd_llg_config cfg{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    // device control and descriptors
+    Inst *d_insts = nullptr;
+    int *d_tile_inst = nullptr;
+    MagComp *d_comps = nullptr;
+    StepCtl *d_ctl = nullptr;
+    double *d_part = nullptr;         // part_e | part_h | part_m
+    int ntiles = 0, ncomp = 0, vmax = 0;
+    bool cls16 = false;
+    bool dirty = true;
+    int nsm = 148;
+    long long host_step = 0;
+    bool half_ahead = false;
+    std::vector<void *> allocs;
+    std::string err;
+    // profiling: event pairs recorded around launches
+    bool profiling = false;
+    struct Rec { int kind; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> ev_pool;
+    fdtd_llg_profile prof{};
+
+    cudaEvent_t take_event()
+    {
+        if (!ev_pool.empty()) { cudaEvent_t e = ev_pool.back(); ev_pool.pop_back(); return e; }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void *dalloc(size_t bytes)
+    {
+        if (bytes == 0) bytes = 16;
+        void *p = nullptr;
+        if (cfg.alloc) p = cfg.alloc(bytes, stream, cfg.alloc_user);
+        else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+        if (p) allocs.push_back(p);
+        return p;
+    }
+    void dfree(void *p)
+    {
+        if (!p) return;
+        auto it = std::find(allocs.begin(), allocs.end(), p);
+        if (it != allocs.end()) allocs.erase(it);
+        if (cfg.free) cfg.free(p, cfg.alloc_user);
+        else cudaFree(p);
+    }
+    ~Sim()
+    {
+        if (stream) cudaStreamSynchronize(stream);
+        for (auto &r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+        for (auto e : ev_pool) cudaEventDestroy(e);
+        for (void *p : allocs) {
+            if (cfg.free) cfg.free(p, cfg.alloc_user);
+            else cudaFree(p);
+        }
+        allocs.clear();
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+};
+
+}  // namespace
+
+struct fdtd_llg_s {
+    Sim *sim;
+    int index;          // -1: batch root
+    bool owns;          // destroy frees the Sim
+};
+
+namespace {
+
+int fail(fdtd_llg_t h, int code, const std::string &msg)
+{
+    g_last_error = msg;
+    if (h && h->sim) h->sim->err = msg;
+    return code;
+}
+
+#define CKR(h, call)                                                                                  \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return fail(h, FDTD_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));          \
+    } while (0)
+
+double courant_limit(double dx, double dy, double dz)
+{
+    return 1.0 / (kC0 * std::sqrt(1.0 / (dx * dx) + 1.0 / (dy * dy) + 1.0 / (dz * dz)));
+}
+
+bool valid_cfg(const fdtd_llg_config &c, std::string &why)
+{
+    if (c.nx < 1 || c.ny < 1 || c.nz < 1) { why = "nx, ny, nz must be >= 1"; return false; }
+    if ((long long)c.nx * c.ny * c.nz > (1LL << 34)) { why = "grid too large"; return false; }
+    if (!(c.dx > 0 && c.dy > 0 && c.dz > 0)) { why = "dx, dy, dz must be > 0"; return false; }
+    if (c.dt < 0 || (c.dt == 0 && !(c.courant_factor > 0 && c.courant_factor <= 1))) {
+        why = "dt must be > 0, or dt = 0 with 0 < courant_factor <= 1";
+        return false;
+    }
+    if (c.llg_tol < 0 || c.llg_max_iter < 0 || c.llg_fixed_iter < 0 || c.probe_capacity < 0) {
+        why = "negative LLG or probe settings";
+        return false;
+    }
+    return true;
+}
+
+Instance *inst_of(fdtd_llg_t h)
+{
+    if (!h || !h->sim) return nullptr;
+    int i = h->index < 0 ? 0 : h->index;
+    if (i >= (int)h->sim->inst.size()) return nullptr;
+    return &h->sim->inst[i];
+}
+
+bool is_member(fdtd_llg_t h) { return h && h->sim && h->index >= 0; }
+
+// ------------------------------------------------------- edge coefficients
+struct ClassKey {
+    uint32_t w[10];
+    bool operator==(const ClassKey &o) const { return std::memcmp(w, o.w, sizeof w) == 0; }
+};
+struct ClassKeyHash {
+    size_t operator()(const ClassKey &k) const
+    {
+        uint64_t h = 1469598103934665603ull;
+        for (uint32_t v : k.w) { h ^= v; h *= 1099511628211ull; }
+        return (size_t)h;
+    }
+};
+
+uint32_t fbits(float f) { uint32_t u; std::memcpy(&u, &f, 4); return u; }
+
+// Orthonormal frame with third axis u (rows e1, e2, e3).
+void bias_frame(const double u[3], double E[9])
+{
+    const double a[3] = {std::fabs(u[0]) < 0.9 ? 1.0 : 0.0, std::fabs(u[0]) < 0.9 ? 0.0 : 1.0, 0.0};
+    double e1[3] = {a[1] * u[2] - a[2] * u[1], a[2] * u[0] - a[0] * u[2], a[0] * u[1] - a[1] * u[0]};
+    const double n1 = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    for (double &v : e1) v /= n1;
+    const double e2[3] = {u[1] * e1[2] - u[2] * e1[1], u[2] * e1[0] - u[0] * e1[2], u[0] * e1[1] - u[1] * e1[0]};
+    for (int q = 0; q < 3; ++q) { E[q] = e1[q]; E[3 + q] = e2[q]; E[6 + q] = u[q]; }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ ABI
+extern "C" int fdtd_llg_abi_version(void) { return FDTD_LLG_ABI_VERSION; }
+
+extern "C" const char *fdtd_llg_last_error(fdtd_llg_t h)
+{
+    if (h && h->sim) return h->sim->err.c_str();
+    return g_last_error.c_str();
+}
+
+static int create_impl(const fdtd_llg_config *cfgs, int32_t n, fdtd_llg_t *out)
+{
+    if (!cfgs || !out || n < 1) return fail(nullptr, FDTD_E_INVAL, "null argument or n < 1");
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        std::string why;
+        if (!valid_cfg(cfgs[i], why)) return fail(nullptr, FDTD_E_INVAL, "instance " + std::to_string(i) + ": " + why);
+    }
+    // common time step: explicit, or the smallest Courant step of the set
+    double dt;
+    if (cfgs[0].dt > 0) dt = cfgs[0].dt;
+    else {
+        dt = 1e300;
+        for (int i = 0; i < n; ++i)
+            dt = std::min(dt, cfgs[0].courant_factor * courant_limit(cfgs[i].dx, cfgs[i].dy, cfgs[i].dz));
+    }
+    for (int i = 0; i < n; ++i) {
+        const double lim = courant_limit(cfgs[i].dx, cfgs[i].dy, cfgs[i].dz);
+        if (dt > lim * (1 + 1e-12))
+            return fail(nullptr, FDTD_E_UNSTABLE, "dt exceeds the 3-D Courant limit of instance " + std::to_string(i));
+    }
+    if (cudaSetDevice(cfgs[0].device) != cudaSuccess) return fail(nullptr, FDTD_E_CUDA, "cudaSetDevice failed");
+    Sim *S = new Sim();
+    S->cfg = cfgs[0];
+    if (S->cfg.llg_tol == 0) S->cfg.llg_tol = 1e-6;
+    if (S->cfg.llg_max_iter == 0) S->cfg.llg_max_iter = 20;
+    if (S->cfg.probe_capacity == 0) S->cfg.probe_capacity = 4096;
+    S->dt = dt;
+    cudaDeviceGetAttribute(&S->nsm, cudaDevAttrMultiProcessorCount, cfgs[0].device);
+    if (S->cfg.stream) S->stream = (cudaStream_t)S->cfg.stream;
+    else {
+        if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete S;
+            return fail(nullptr, FDTD_E_CUDA, "cudaStreamCreate failed");
+        }
+        S->own_stream = true;
+    }
+    S->inst.resize(n);
+    fdtd_llg_t root = new fdtd_llg_s{S, n == 1 ? 0 : -1, true};
+    for (int i = 0; i < n; ++i) {
+        Instance &I = S->inst[i];
+        I.nx = cfgs[i].nx; I.ny = cfgs[i].ny; I.nz = cfgs[i].nz;
+        I.px = (I.nx + 31) / 32 * 32;
+        I.dx = cfgs[i].dx; I.dy = cfgs[i].dy; I.dz = cfgs[i].dz;
+        I.fields = (float *)S->dalloc(6 * I.n_field() * sizeof(float));
+        I.walls = (float *)S->dalloc(I.n_wall() * sizeof(float));
+        I.energy_buf = (double *)S->dalloc((size_t)S->cfg.probe_capacity * sizeof(double));
+        if (!I.fields || !I.walls || !I.energy_buf) {
+            fdtd_llg_destroy(root);
+            return fail(nullptr, FDTD_E_OOM, "device allocation failed");
+        }
+        cudaMemsetAsync(I.fields, 0, 6 * I.n_field() * sizeof(float), S->stream);
+        cudaMemsetAsync(I.walls, 0, I.n_wall() * sizeof(float), S->stream);
+        cudaMemsetAsync(I.energy_buf, 0, (size_t)S->cfg.probe_capacity * sizeof(double), S->stream);
+        S->members.push_back(n == 1 ? root : new fdtd_llg_s{S, i, false});
+    }
+    S->d_ctl = (StepCtl *)S->dalloc(sizeof(StepCtl));
+    if (!S->d_ctl) { fdtd_llg_destroy(root); return fail(nullptr, FDTD_E_OOM, "device allocation failed"); }
+    cudaMemsetAsync(S->d_ctl, 0, sizeof(StepCtl), S->stream);
+    if (cudaStreamSynchronize(S->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        fdtd_llg_destroy(root);
+        return fail(nullptr, FDTD_E_CUDA, "initialisation failed");
+    }
+    *out = root;
+    return FDTD_OK;
+}
+
+extern "C" int fdtd_llg_create(const fdtd_llg_config *cfg, fdtd_llg_t *out) { return create_impl(cfg, 1, out); }
+
+extern "C" int fdtd_llg_create_batch(const fdtd_llg_config *cfgs, int32_t n, fdtd_llg_t *out)
+{
+    return create_impl(cfgs, n, out);
+}
+
+extern "C" int fdtd_llg_batch_member(fdtd_llg_t b, int32_t i, fdtd_llg_t *m)
+{
+    if (!b || !b->sim || !m) return fail(b, FDTD_E_INVAL, "null argument");
+    if (i < 0 || i >= (int)b->sim->members.size()) return fail(b, FDTD_E_RANGE, "member index out of range");
+    *m = b->sim->members[i];
+    return FDTD_OK;
+}
+
+extern "C" void fdtd_llg_destroy(fdtd_llg_t h)
+{
+    if (!h) return;
+    if (!h->owns) return;   // members go with their batch
+    Sim *S = h->sim;
+    if (S) {
+        for (auto *m : S->members)
+            if (m != h) delete m;
+        delete S;
+    }
+    delete h;
+}
+
+// --------------------------------------------------------- set_materials
+extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const fdtd_material *table, int32_t ntable,
+                                      const double hbias[3], const double *eps_r_design, const int32_t design_box[6])
+{
+    if (!is_member(h)) return fail(h, FDTD_E_INVAL, "set_materials needs an instance handle (use fdtd_llg_batch_member)");
+    if (!mat_id || !table || !hbias || ntable < 1 || ntable > 255)
+        return fail(h, FDTD_E_INVAL, "null argument or ntable outside 1..255");
+    Sim *S = h->sim;
+    Instance &I = *inst_of(h);
+    const int nx = I.nx, ny = I.ny, nz = I.nz;
+    const size_t nc = (size_t)nx * ny * nz;
+    // material ids to the host (the caller may pass a device pointer)
+    std::vector<uint8_t> mid(nc);
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, mat_id) == cudaSuccess && pa.type == cudaMemoryTypeDevice) {
+        CKR(h, cudaMemcpy(mid.data(), mat_id, nc, cudaMemcpyDeviceToHost));
+    } else {
+        cudaGetLastError();
+        std::memcpy(mid.data(), mat_id, nc);
+    }
+    for (size_t c = 0; c < nc; ++c)
+        if (mid[c] >= ntable) return fail(h, FDTD_E_INVAL, "mat_id references a material beyond ntable");
+    for (int m = 0; m < ntable; ++m) {
+        const fdtd_material &t = table[m];
+        if (!(t.eps_r > 0) || t.sigma < 0 || t.Ms < 0 || t.alpha < 0 || (t.Ms > 0 && !(t.gamma > 0)))
+            return fail(h, FDTD_E_INVAL, "material " + std::to_string(m) + " has an invalid parameter");
+    }
+    for (int q = 0; q < 3; ++q)
+        if (!std::isfinite(hbias[q])) return fail(h, FDTD_E_INVAL, "hbias is not finite");
+    const bool has_design = eps_r_design != nullptr;
+    int db[6] = {0, 0, 0, 0, 0, 0};
+    if (has_design) {
+        if (!design_box) return fail(h, FDTD_E_INVAL, "eps_r_design given without design_box");
+        std::memcpy(db, design_box, sizeof db);
+        if (db[0] < 0 || db[1] < 0 || db[2] < 0 || db[3] < 1 || db[4] < 1 || db[5] < 1 || db[0] + db[3] > nx ||
+            db[1] + db[4] > ny || db[2] + db[5] > nz)
+            return fail(h, FDTD_E_INVAL, "design_box outside the grid");
+        const size_t nd = (size_t)db[3] * db[4] * db[5];
+        for (size_t q = 0; q < nd; ++q)
+            if (!(eps_r_design[q] > 0)) return fail(h, FDTD_E_INVAL, "eps_r_design must be > 0");
+    }
+    auto cid = [&](int i, int j, int k) { return ((size_t)k * ny + j) * nx + i; };
+    auto in_box = [&](int i, int j, int k) {
+        return has_design && i >= db[0] && i < db[0] + db[3] && j >= db[1] && j < db[1] + db[4] && k >= db[2] &&
+               k < db[2] + db[5];
+    };
+    auto eps_of = [&](int i, int j, int k) -> double {
+        if (in_box(i, j, k)) return eps_r_design[((size_t)(k - db[2]) * db[4] + (j - db[1])) * db[3] + (i - db[0])];
+        return table[mid[cid(i, j, k)]].eps_r;
+    };
+    const double dt = S->dt;
+    // per-cell class: (ca, cb, eps/2) of the three edges with index (i,j,k) + magnetic-face flags
+    std::unordered_map<ClassKey, int, ClassKeyHash> classes;
+    std::vector<ClassKey> keys;
+    std::vector<uint16_t> cls(nc);
+    auto edge = [&](int comp, int i, int j, int k, float &ca, float &cb, float &he) {
+        bool wall;
+        if (comp == 0) wall = (j == 0 || k == 0);
+        else if (comp == 1) wall = (i == 0 || k == 0);
+        else wall = (i == 0 || j == 0);
+        ca = cb = he = 0.f;
+        if (wall) return;
+        double se = 0, ss = 0;
+        bool pec = false;
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+                int ci = i, cj = j, ck = k;
+                if (comp == 0) { cj -= a; ck -= b; }
+                else if (comp == 1) { ci -= a; ck -= b; }
+                else { ci -= a; cj -= b; }
+                const fdtd_material &t = table[mid[cid(ci, cj, ck)]];
+                se += eps_of(ci, cj, ck);
+                ss += t.sigma;
+                pec = pec || t.is_pec;
+            }
+        if (pec) return;
+        const double eps = kEps0 * se / 4, sig = ss / 4;
+        const double den = eps / dt + sig / 2;
+        ca = (float)((eps / dt - sig / 2) / den);
+        cb = (float)(1.0 / den);
+        he = (float)(eps / 2);
+    };
+    auto magc = [&](int i, int j, int k) { return table[mid[cid(i, j, k)]].Ms > 0; };
+    // Outside the design box a cell's class depends only on the materials of
+    // the seven cells its three edges and three faces touch and on which walls
+    // it lies against, so classes are memoised on that 59-bit neighbourhood.
+    std::unordered_map<uint64_t, int> by_nbhd;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const int nb[7][3] = {{i, j, k}, {i - 1, j, k}, {i, j - 1, k}, {i, j, k - 1},
+                                      {i, j - 1, k - 1}, {i - 1, j, k - 1}, {i - 1, j - 1, k}};
+                uint64_t nk = 0;
+                bool design_touch = false;
+                for (int q = 0; q < 7; ++q) {
+                    const int ci = nb[q][0], cj = nb[q][1], ck = nb[q][2];
+                    const bool in = ci >= 0 && cj >= 0 && ck >= 0;
+                    nk = (nk << 8) | (in ? mid[cid(ci, cj, ck)] : 0xFFu);
+                    design_touch = design_touch || (in && in_box(ci, cj, ck));
+                }
+                nk = (nk << 3) | (uint64_t)((i == 0) | ((j == 0) << 1) | ((k == 0) << 2));
+                if (!design_touch) {
+                    auto hit = by_nbhd.find(nk);
+                    if (hit != by_nbhd.end()) {
+                        cls[cid(i, j, k)] = (uint16_t)hit->second;
+                        continue;
+                    }
+                }
+                ClassKey key;
+                float v[9];
+                edge(0, i, j, k, v[0], v[3], v[6]);
+                edge(1, i, j, k, v[1], v[4], v[7]);
+                edge(2, i, j, k, v[2], v[5], v[8]);
+                for (int q = 0; q < 9; ++q) key.w[q] = fbits(v[q]);
+                uint32_t f = 0;
+                if (magc(i, j, k) || (i > 0 && magc(i - 1, j, k))) f |= CF_MAG_HX;
+                if (magc(i, j, k) || (j > 0 && magc(i, j - 1, k))) f |= CF_MAG_HY;
+                if (magc(i, j, k) || (k > 0 && magc(i, j, k - 1))) f |= CF_MAG_HZ;
+                key.w[9] = f;
+                auto it = classes.find(key);
+                int c;
+                if (it == classes.end()) {
+                    c = (int)keys.size();
+                    if (c >= 65536) return fail(h, FDTD_E_INVAL, "more than 65536 distinct edge classes");
+                    classes.emplace(key, c);
+                    keys.push_back(key);
+                } else c = it->second;
+                cls[cid(i, j, k)] = (uint16_t)c;
+                if (!design_touch) by_nbhd.emplace(nk, c);
+            }
+    const int nclass = (int)keys.size();
+    const bool c16 = nclass > 256;
+    // magnetic regions: face-connected components of cells with Ms > 0
+    std::vector<int> label(nc, -1);
+    struct Box { int x0, y0, z0, x1, y1, z1; };
+    std::vector<Box> boxes;
+    std::vector<size_t> stack;
+    for (size_t c0 = 0; c0 < nc; ++c0) {
+        if (label[c0] >= 0 || table[mid[c0]].Ms <= 0) continue;
+        const int L = (int)boxes.size();
+        Box b{nx, ny, nz, -1, -1, -1};
+        stack.clear();
+        stack.push_back(c0);
+        label[c0] = L;
+        while (!stack.empty()) {
+            const size_t c = stack.back();
+            stack.pop_back();
+            const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((size_t)nx * ny));
+            b.x0 = std::min(b.x0, i); b.y0 = std::min(b.y0, j); b.z0 = std::min(b.z0, k);
+            b.x1 = std::max(b.x1, i); b.y1 = std::max(b.y1, j); b.z1 = std::max(b.z1, k);
+            const int nb[6][3] = {{i - 1, j, k}, {i + 1, j, k}, {i, j - 1, k}, {i, j + 1, k}, {i, j, k - 1}, {i, j, k + 1}};
+            for (auto &q : nb) {
+                if (q[0] < 0 || q[1] < 0 || q[2] < 0 || q[0] >= nx || q[1] >= ny || q[2] >= nz) continue;
+                const size_t cc = cid(q[0], q[1], q[2]);
+                if (label[cc] < 0 && table[mid[cc]].Ms > 0) { label[cc] = L; stack.push_back(cc); }
+            }
+        }
+        const long long V = (long long)(b.x1 - b.x0 + 1) * (b.y1 - b.y0 + 1) * (b.z1 - b.z0 + 1);
+        if (V > kMagMaxV)
+            return fail(h, FDTD_E_INVAL, "a magnetic region's bounding box holds " + std::to_string(V) + " cells (maximum " +
+                                             std::to_string(kMagMaxV) + ")");
+        boxes.push_back(b);
+    }
+    // magnet material table (compact index per magnetic material)
+    std::vector<int> mm_index(ntable, 0xFF);
+    std::vector<MagMat> mm;
+    std::vector<double> mm_Ms;
+    const double hdt = 0.5 * dt;
+    for (int m = 0; m < ntable; ++m)
+        if (table[m].Ms > 0) {
+            if ((int)mm.size() >= kMaxMagMat) return fail(h, FDTD_E_INVAL, "more than 16 magnetic materials");
+            mm_index[m] = (int)mm.size();
+            MagMat q;
+            q.Ms = (float)table[m].Ms;
+            q.inv_Ms = (float)(1.0 / table[m].Ms);
+            q.alpha = (float)table[m].alpha;
+            q.kappa = (float)(kMu0 * table[m].gamma * hdt / 2);
+            mm.push_back(q);
+            mm_Ms.push_back(table[m].Ms);
+        }
+    size_t totV = 0;
+    for (auto &b : boxes) totV += (size_t)(b.x1 - b.x0 + 1) * (b.y1 - b.y0 + 1) * (b.z1 - b.z0 + 1);
+    std::vector<uint8_t> hmat(totV);
+    // release the previous materials of this instance
+    CKR(h, cudaStreamSynchronize(S->stream));
+    S->dfree(I.cls); S->dfree(I.ctab); S->dfree(I.mbuf); S->dfree(I.magmat);
+    I.cls = nullptr; I.ctab = nullptr; I.mbuf = nullptr; I.magmat = nullptr;
+    I.mbuf = (float *)S->dalloc(3 * totV * sizeof(float));
+    I.magmat = (uint8_t *)S->dalloc(totV);
+    I.cls = S->dalloc((size_t)I.nz * I.ny * I.px * (c16 ? 2 : 1));
+    I.ctab = (float4 *)S->dalloc((size_t)3 * nclass * sizeof(float4));
+    if (!I.mbuf || !I.magmat || !I.cls || !I.ctab) return fail(h, FDTD_E_OOM, "device allocation failed");
+    I.comps.clear();
+    size_t off = 0;
+    for (size_t L = 0; L < boxes.size(); ++L) {
+        const Box &b = boxes[L];
+        MagComp C{};
+        C.x0 = b.x0; C.y0 = b.y0; C.z0 = b.z0;
+        C.bx = b.x1 - b.x0 + 1; C.by = b.y1 - b.y0 + 1; C.bz = b.z1 - b.z0 + 1;
+        C.V = C.bx * C.by * C.bz;
+        for (int lk = 0; lk < C.bz; ++lk)
+            for (int lj = 0; lj < C.by; ++lj)
+                for (int li = 0; li < C.bx; ++li) {
+                    const int v = (lk * C.by + lj) * C.bx + li;
+                    const size_t c = cid(C.x0 + li, C.y0 + lj, C.z0 + lk);
+                    hmat[off + v] = label[c] == (int)L ? (uint8_t)mm_index[mid[c]] : 0xFF;
+                }
+        C.m = I.mbuf + 3 * off;
+        C.mat = I.magmat + off;
+        I.comps.push_back(C);
+        off += C.V;
+    }
+    // bias frame: M starts at Ms h, i.e. m = 0
+    const double h0n = std::sqrt(hbias[0] * hbias[0] + hbias[1] * hbias[1] + hbias[2] * hbias[2]);
+    double u[3] = {0, 0, 1};
+    if (h0n > 0) for (int q = 0; q < 3; ++q) u[q] = hbias[q] / h0n;
+    double E[9];
+    bias_frame(u, E);
+    // upload: class ids in the padded layout, table, regions; zero the fields
+    {
+        std::vector<uint8_t> pad((size_t)I.nz * I.ny * I.px * (c16 ? 2 : 1), 0);
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    const size_t o = ((size_t)k * ny + j) * I.px + i;
+                    const uint16_t c = cls[cid(i, j, k)];
+                    if (c16) std::memcpy(pad.data() + 2 * o, &c, 2);
+                    else pad[o] = (uint8_t)c;
+                }
+        CKR(h, cudaMemcpy(I.cls, pad.data(), pad.size(), cudaMemcpyHostToDevice));
+        std::vector<float4> tab(3 * (size_t)nclass);
+        for (int c = 0; c < nclass; ++c) {
+            const uint32_t *w = keys[c].w;
+            float v[9];
+            std::memcpy(v, w, sizeof v);
+            float flag;
+            std::memcpy(&flag, &w[9], 4);
+            tab[3 * c] = make_float4(v[0], v[1], v[2], flag);
+            tab[3 * c + 1] = make_float4(v[3], v[4], v[5], 0.f);
+            tab[3 * c + 2] = make_float4(v[6], v[7], v[8], 0.f);
+        }
+        CKR(h, cudaMemcpy(I.ctab, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice));
+        if (totV) {
+            CKR(h, cudaMemset(I.mbuf, 0, 3 * totV * sizeof(float)));
+            CKR(h, cudaMemcpy(I.magmat, hmat.data(), hmat.size(), cudaMemcpyHostToDevice));
+        }
+        CKR(h, cudaMemset(I.fields, 0, 6 * I.n_field() * sizeof(float)));
+        CKR(h, cudaMemset(I.walls, 0, I.n_wall() * sizeof(float)));
+    }
+    I.cls_bytes = c16 ? 2 : 1;
+    I.nclass = nclass;
+    I.mm = mm;
+    I.mm_Ms = mm_Ms;
+    std::memcpy(I.hbias, hbias, sizeof I.hbias);
+    std::memcpy(I.u, u, sizeof I.u);
+    for (int q = 0; q < 9; ++q) I.R[q] = (float)E[q];
+    I.materials_set = true;
+    // a batch's step count restarts with any instance's materials
+    S->host_step = 0;
+    S->half_ahead = false;
+    CKR(h, cudaMemset(S->d_ctl, 0, sizeof(StepCtl)));
+    S->dirty = true;
+    return FDTD_OK;
+}
+
+extern "C" int fdtd_llg_set_source(fdtd_llg_t h, int32_t comp, int32_t i, int32_t j, int32_t k, double J0, double f0,
+                                   double Tp, double t_peak)
+{
+    if (!is_member(h)) return fail(h, FDTD_E_INVAL, "set_source needs an instance handle");
+    Instance *I = inst_of(h);
+    if (comp < 0 || comp > 2) return fail(h, FDTD_E_INVAL, "comp must be 0, 1 or 2");
+    if (i < 0 || j < 0 || k < 0 || i >= I->nx || j >= I->ny || k >= I->nz) return fail(h, FDTD_E_RANGE, "source edge outside the grid");
+    if (!(f0 > 0) || Tp < 0 || !std::isfinite(J0)) return fail(h, FDTD_E_INVAL, "f0 must be > 0, Tp >= 0, J0 finite");
+    if ((int)I->src.size() >= kMaxSrc) return fail(h, FDTD_E_INVAL, "at most 4 sources per instance");
+    if (Tp == 0) Tp = 1.0 / f0;
+    if (t_peak == 0) t_peak = 3.0 * Tp;
+    I->src.push_back({comp, i, j, k});
+    I->srcp.push_back({J0, f0, Tp, t_peak});
+    h->sim->dirty = true;
+    return FDTD_OK;
+}
+
+extern "C" int fdtd_llg_add_probe(fdtd_llg_t h, int32_t i, int32_t j, int32_t k, int32_t *id)
+{
+    if (!is_member(h)) return fail(h, FDTD_E_INVAL, "add_probe needs an instance handle");
+    Instance *I = inst_of(h);
+    if (i < 0 || j < 0 || k < 0 || i >= I->nx || j >= I->ny || k >= I->nz) return fail(h, FDTD_E_RANGE, "probe cell outside the grid");
+    if ((int)I->probes.size() >= kMaxProbe) return fail(h, FDTD_E_INVAL, "at most 32 probes per instance");
+    if (h->sim->host_step > 0) return fail(h, FDTD_E_STATE, "add probes before the first step");
+    I->probes.push_back({i, j, k});
+    if (id) *id = (int32_t)I->probes.size() - 1;
+    h->sim->dirty = true;
+    return FDTD_OK;
+}
+
+// ----------------------------------------------------------- descriptors
+static int upload_descriptors(fdtd_llg_t h)
+{
+    Sim *S = h->sim;
+    if (!S->dirty) return FDTD_OK;
+    CKR(h, cudaStreamSynchronize(S->stream));
+    std::vector<Inst> hi(S->inst.size());
+    std::vector<int> tile_inst;
+    std::vector<MagComp> comps;
+    bool c16 = false;
+    int vmax = 0;
+    for (size_t ii = 0; ii < S->inst.size(); ++ii) {
+        Instance &I = S->inst[ii];
+        if (!I.materials_set) return fail(h, FDTD_E_STATE, "instance " + std::to_string(ii) + " has no materials");
+        if ((int)I.probes.size() != I.probe_alloc) {
+            S->dfree(I.probe_buf);
+            const size_t pb = (size_t)S->cfg.probe_capacity * std::max<size_t>(1, I.probes.size()) * 9 * sizeof(double);
+            I.probe_buf = (double *)S->dalloc(pb);
+            if (!I.probe_buf) return fail(h, FDTD_E_OOM, "device allocation failed");
+            CKR(h, cudaMemset(I.probe_buf, 0, pb));
+            I.probe_alloc = (int)I.probes.size();
+        }
+        Inst &d = hi[ii];
+        std::memset(&d, 0, sizeof d);
+        const size_t nf = I.n_field();
+        d.Ex = I.fields; d.Ey = I.fields + nf; d.Ez = I.fields + 2 * nf;
+        d.Hx = I.fields + 3 * nf; d.Hy = I.fields + 4 * nf; d.Hz = I.fields + 5 * nf;
+        d.wHx = I.walls; d.wHy = I.walls + (size_t)I.ny * I.nz; d.wHz = d.wHy + (size_t)I.nx * I.nz;
+        d.cls = I.cls; d.ctab = I.ctab;
+        d.probe_buf = I.probe_buf; d.energy_buf = I.energy_buf;
+        d.nx = I.nx; d.ny = I.ny; d.nz = I.nz; d.px = I.px;
+        d.plane = (long long)I.ny * I.px;
+        d.idx = (float)(1.0 / I.dx); d.idy = (float)(1.0 / I.dy); d.idz = (float)(1.0 / I.dz);
+        d.ch = (float)(S->dt / (2.0 * kMu0));
+        for (int q = 0; q < 9; ++q) d.R[q] = I.R[q];
+        d.h0n = (float)std::sqrt(I.hbias[0] * I.hbias[0] + I.hbias[1] * I.hbias[1] + I.hbias[2] * I.hbias[2]);
+        for (int q = 0; q < 3; ++q) d.u[q] = I.u[q];
+        d.dt = S->dt;
+        d.dV = I.dx * I.dy * I.dz;
+        d.cap = S->cfg.probe_capacity;
+        d.nsrc = (int)I.src.size();
+        for (int s = 0; s < d.nsrc; ++s)
+            for (int q = 0; q < 4; ++q) { d.src[s][q] = I.src[s][q]; d.srcp[s][q] = I.srcp[s][q]; }
+        d.nprobe = (int)I.probes.size();
+        for (int p = 0; p < d.nprobe; ++p)
+            for (int q = 0; q < 3; ++q) d.probe[p][q] = I.probes[p][q];
+        d.ntx = (I.nx + kTX - 1) / kTX; d.nty = (I.ny + kTY - 1) / kTY; d.ntz = (I.nz + kKC - 1) / kKC;
+        d.tile_off = (int)tile_inst.size();
+        const int nt = d.ntx * d.nty * d.ntz;
+        for (int t = 0; t < nt; ++t) tile_inst.push_back((int)ii);
+        d.mag_off = (int)comps.size();
+        d.nmag = (int)I.comps.size();
+        for (auto C : I.comps) {
+            C.inst = (int)ii;
+            comps.push_back(C);
+            vmax = std::max(vmax, C.V);
+        }
+        for (size_t m = 0; m < I.mm.size(); ++m) d.mm[m] = I.mm[m];
+        c16 = c16 || I.cls_bytes == 2;
+    }
+    if (c16)
+        for (size_t ii = 0; ii < S->inst.size(); ++ii) {
+            Instance &I = S->inst[ii];
+            if (I.cls_bytes == 2) continue;
+            // widen this instance's class ids so that a batch shares one width
+            std::vector<uint8_t> narrow(I.n_field());
+            CKR(h, cudaMemcpy(narrow.data(), I.cls, narrow.size(), cudaMemcpyDeviceToHost));
+            std::vector<uint16_t> wide(narrow.begin(), narrow.end());
+            void *w = S->dalloc(wide.size() * 2);
+            if (!w) return fail(h, FDTD_E_OOM, "device allocation failed");
+            CKR(h, cudaMemcpy(w, wide.data(), wide.size() * 2, cudaMemcpyHostToDevice));
+            S->dfree(I.cls);
+            I.cls = w;
+            I.cls_bytes = 2;
+            hi[ii].cls = w;
+        }
+    S->dfree(S->d_insts); S->dfree(S->d_tile_inst); S->dfree(S->d_comps); S->dfree(S->d_part);
+    S->d_insts = (Inst *)S->dalloc(hi.size() * sizeof(Inst));
+    S->d_tile_inst = (int *)S->dalloc(tile_inst.size() * sizeof(int));
+    S->d_comps = (MagComp *)S->dalloc(std::max<size_t>(1, comps.size()) * sizeof(MagComp));
+    S->d_part = (double *)S->dalloc((2 * tile_inst.size() + comps.size() + 1) * sizeof(double));
+    if (!S->d_insts || !S->d_tile_inst || !S->d_comps || !S->d_part) return fail(h, FDTD_E_OOM, "device allocation failed");
+    CKR(h, cudaMemcpy(S->d_insts, hi.data(), hi.size() * sizeof(Inst), cudaMemcpyHostToDevice));
+    CKR(h, cudaMemcpy(S->d_tile_inst, tile_inst.data(), tile_inst.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if (!comps.empty()) CKR(h, cudaMemcpy(S->d_comps, comps.data(), comps.size() * sizeof(MagComp), cudaMemcpyHostToDevice));
+    CKR(h, cudaMemset(S->d_part, 0, (2 * tile_inst.size() + comps.size() + 1) * sizeof(double)));
+    S->ntiles = (int)tile_inst.size();
+    S->ncomp = (int)comps.size();
+    S->vmax = vmax;
+    S->cls16 = c16;
+    S->dirty = false;
+    return FDTD_OK;
+}
+
+static LaunchSet launch_set(Sim *S)
+{
+    LaunchSet L{};
+    L.insts = S->d_insts;
+    L.ninst = (int)S->inst.size();
+    L.tile_inst = S->d_tile_inst;
+    L.ntiles = S->ntiles;
+    L.comps = S->d_comps;
+    L.ncomp = S->ncomp;
+    L.vmax = S->vmax;
+    L.ctl = S->d_ctl;
+    L.part_e = S->d_part;
+    L.part_h = S->d_part + S->ntiles;
+    L.part_m = S->d_part + 2 * S->ntiles;
+    L.cls16 = S->cls16;
+    L.grid_e = std::min(S->ntiles, S->nsm * e_pass_blocks_per_sm(S->cls16));
+    L.grid_h = std::min(S->ntiles, S->nsm * h_pass_blocks_per_sm(S->cls16));
+    L.llg_tol = (float)S->cfg.llg_tol;
+    L.llg_max_iter = S->cfg.llg_max_iter;
+    L.llg_fixed_iter = S->cfg.llg_fixed_iter;
+    L.energy = S->cfg.energy_every != 0;
+    return L;
+}
+
+extern "C" int fdtd_llg_step(fdtd_llg_t h, int64_t nsteps)
+{
+    if (!h || !h->sim) return fail(h, FDTD_E_INVAL, "null handle");
+    if (!h->owns) return fail(h, FDTD_E_INVAL, "step the batch handle, not a member");
+    if (nsteps < 0) return fail(h, FDTD_E_INVAL, "nsteps < 0");
+    Sim *S = h->sim;
+    int rc = upload_descriptors(h);
+    if (rc) return rc;
+    const LaunchSet L = launch_set(S);
+    auto timed = [&](int kind, auto &&fn) -> cudaError_t {
+        if (!S->profiling || (kind == 1 && L.ncomp == 0)) return fn();
+        Sim::Rec r{kind, S->take_event(), S->take_event()};
+        cudaEventRecord(r.a, S->stream);
+        cudaError_t e = fn();
+        cudaEventRecord(r.b, S->stream);
+        S->recs.push_back(r);
+        return e;
+    };
+    if (!S->half_ahead && nsteps > 0) {
+        CKR(h, launch_mag_pass(L, 0, S->stream));
+        CKR(h, launch_h_pass(L, 0, S->stream));
+        S->half_ahead = true;
+    }
+    for (int64_t s = 0; s < nsteps; ++s) {
+        CKR(h, timed(0, [&] { return launch_e_pass(L, S->stream); }));
+        CKR(h, timed(1, [&] { return launch_mag_pass(L, 1, S->stream); }));
+        CKR(h, timed(2, [&] { return launch_h_pass(L, 1, S->stream); }));
+    }
+    S->host_step += nsteps;
+    return FDTD_OK;
+}
+
+static int sync_status(fdtd_llg_t h)
+{
+    Sim *S = h->sim;
+    CKR(h, cudaStreamSynchronize(S->stream));
+    StepCtl c{};
+    CKR(h, cudaMemcpy(&c, S->d_ctl, sizeof c, cudaMemcpyDeviceToHost));
+    if (c.status & ST_UNSTABLE) return fail(h, FDTD_E_UNSTABLE, "energy is not finite (unstable run)");
+    if (c.status & ST_NOCONV) return fail(h, FDTD_E_LLG_NOCONV, "an LLG solve did not reach llg_tol within llg_max_iter");
+    return FDTD_OK;
+}
+
+extern "C" int fdtd_llg_sync(fdtd_llg_t h)
+{
+    if (!h || !h->sim) return fail(h, FDTD_E_INVAL, "null handle");
+    return sync_status(h);
+}
+
+extern "C" int fdtd_llg_time_state(fdtd_llg_t h, int64_t *step, int32_t *half)
+{
+    if (!h || !h->sim) return fail(h, FDTD_E_INVAL, "null handle");
+    if (step) *step = h->sim->host_step;
+    if (half) *half = h->sim->half_ahead ? 1 : 0;
+    return FDTD_OK;
+}
+
+// rows of a ring holding host_step records of `stride` doubles (oldest first)
+static int read_ring(fdtd_llg_t h, const double *dbuf, int stride, int col_off, int ncols, double *out, int64_t cap_rows,
+                     int64_t *rows)
+{
+    Sim *S = h->sim;
+    const long long cap = S->cfg.probe_capacity;
+    const long long have = std::min<long long>(S->host_step, cap);
+    const long long want = std::max<long long>(0, std::min<long long>(have, cap_rows));
+    for (long long r = 0; r < want;) {
+        const long long stepi = S->host_step - want + r;   // record of state stepi+1
+        const long long slot = stepi % cap;
+        const long long run = std::min<long long>(want - r, cap - slot);   // contiguous slots
+        if (ncols == stride) {
+            CKR(h, cudaMemcpyAsync(out + r * ncols, dbuf + slot * stride, run * ncols * sizeof(double),
+                                   cudaMemcpyDeviceToHost, S->stream));
+        } else {
+            CKR(h, cudaMemcpy2DAsync(out + r * ncols, ncols * sizeof(double), dbuf + slot * stride + col_off,
+                                     stride * sizeof(double), ncols * sizeof(double), run, cudaMemcpyDeviceToHost, S->stream));
+        }
+        r += run;
+    }
+    CKR(h, cudaStreamSynchronize(S->stream));
+    if (rows) *rows = want;
+    return FDTD_OK;
+}
+
+extern "C" int fdtd_llg_probe(fdtd_llg_t h, int32_t id, double *out, int64_t cap_rows, int64_t *rows)
+{
+    if (!is_member(h)) return fail(h, FDTD_E_INVAL, "probe needs an instance handle");
+    Instance *I = inst_of(h);
+    if (id < 0 || id >= (int)I->probes.size()) return fail(h, FDTD_E_RANGE, "no such probe");
+    if (!out && cap_rows > 0) return fail(h, FDTD_E_INVAL, "null output");
+    int rc = sync_status(h);
+    if (rc) return rc;
+    if (!I->probe_buf || I->probe_alloc != (int)I->probes.size()) {
+        if (rows) *rows = 0;
+        return FDTD_OK;
+    }
+    return read_ring(h, I->probe_buf, (int)I->probes.size() * 9, id * 9, 9, out, cap_rows, rows);
+}
+
+extern "C" int fdtd_llg_energy(fdtd_llg_t h, double *out, int64_t cap, int64_t *written)
+{
+    if (!is_member(h)) return fail(h, FDTD_E_INVAL, "energy needs an instance handle");
+    Instance *I = inst_of(h);
+    if (!out && cap > 0) return fail(h, FDTD_E_INVAL, "null output");
+    int rc = sync_status(h);
+    if (rc) return rc;
+    return read_ring(h, I->energy_buf, 1, 0, 1, out, cap, written);
+}
+
+// ------------------------------------------------------------- fields
+static int field_count(const Instance &I, int which, size_t &count)
+{
+    if ((which >= FDTD_F_EX && which <= FDTD_F_MZ) || (which >= FDTD_F_DMX && which <= FDTD_F_DMZ)) {
+        count = (size_t)I.nx * I.ny * I.nz;
+        return 0;
+    }
+    if (which == FDTD_F_HX_WALL) { count = (size_t)I.ny * I.nz; return 0; }
+    if (which == FDTD_F_HY_WALL) { count = (size_t)I.nx * I.nz; return 0; }
+    if (which == FDTD_F_HZ_WALL) { count = (size_t)I.nx * I.ny; return 0; }
+    return -1;
+}
+
+// M of every region in global axes (FP64), as deviation (dev = true) or full value.
+static int magnet_read(fdtd_llg_t h, Instance &I, std::vector<std::vector<double>> &out, std::vector<std::vector<uint8_t>> &mats,
+                       bool dev)
+{
+    out.clear();
+    mats.clear();
+    for (auto &C : I.comps) {
+        std::vector<float> m(3 * (size_t)C.V);
+        std::vector<uint8_t> mt(C.V);
+        CKR(h, cudaMemcpy(m.data(), C.m, m.size() * sizeof(float), cudaMemcpyDeviceToHost));
+        CKR(h, cudaMemcpy(mt.data(), C.mat, C.V, cudaMemcpyDeviceToHost));
+        std::vector<double> g(3 * (size_t)C.V, 0.0);
+        for (int v = 0; v < C.V; ++v) {
+            if (mt[v] == 0xFF) continue;
+            const double l[3] = {m[v], m[C.V + v], m[2 * (size_t)C.V + v]};
+            for (int d = 0; d < 3; ++d) {
+                double val = (double)I.R[d] * l[0] + (double)I.R[3 + d] * l[1] + (double)I.R[6 + d] * l[2];
+                if (!dev) val += I.mm_Ms[mt[v]] * I.u[d];
+                g[(size_t)d * C.V + v] = val;
+            }
+        }
+        out.push_back(std::move(g));
+        mats.push_back(std::move(mt));
+    }
+    return FDTD_OK;
+}
+
+extern "C" int fdtd_llg_get_field(fdtd_llg_t h, int32_t which, float *out, size_t count)
+{
+    if (!is_member(h)) return fail(h, FDTD_E_INVAL, "get_field needs an instance handle");
+    Instance *I = inst_of(h);
+    size_t need;
+    if (field_count(*I, which, need)) return fail(h, FDTD_E_INVAL, "unknown field selector");
+    if (!out || count < need) return fail(h, FDTD_E_INVAL, "output too small");
+    int rc = sync_status(h);
+    if (rc) return rc;
+    const size_t nf = I->n_field();
+    if (which <= FDTD_F_HZ) {
+        CKR(h, cudaMemcpy2D(out, I->nx * sizeof(float), I->fields + which * nf, I->px * sizeof(float), I->nx * sizeof(float),
+                            (size_t)I->ny * I->nz, cudaMemcpyDeviceToHost));
+    } else if (which <= FDTD_F_MZ || which >= FDTD_F_DMX) {
+        const bool dev = which >= FDTD_F_DMX;
+        const int d = dev ? which - FDTD_F_DMX : which - FDTD_F_MX;
+        std::vector<std::vector<double>> g;
+        std::vector<std::vector<uint8_t>> mt;
+        rc = magnet_read(h, *I, g, mt, dev);
+        if (rc) return rc;
+        std::fill(out, out + need, 0.f);
+        for (size_t c = 0; c < I->comps.size(); ++c) {
+            const MagComp &C = I->comps[c];
+            for (int v = 0; v < C.V; ++v) {
+                if (mt[c][v] == 0xFF) continue;
+                const int li = v % C.bx, lj = (v / C.bx) % C.by, lk = v / (C.bx * C.by);
+                out[((size_t)(C.z0 + lk) * I->ny + (C.y0 + lj)) * I->nx + (C.x0 + li)] = (float)g[c][(size_t)d * C.V + v];
+            }
+        }
+    } else {
+        size_t off = 0;
+        if (which >= FDTD_F_HY_WALL) off += (size_t)I->ny * I->nz;
+        if (which >= FDTD_F_HZ_WALL) off += (size_t)I->nx * I->nz;
+        CKR(h, cudaMemcpy(out, I->walls + off, need * sizeof(float), cudaMemcpyDeviceToHost));
+    }
+    return FDTD_OK;
+}
+
+extern "C" int fdtd_llg_set_field(fdtd_llg_t h, int32_t which, const float *in, size_t count)
+{
+    if (!is_member(h)) return fail(h, FDTD_E_INVAL, "set_field needs an instance handle");
+    Instance *I = inst_of(h);
+    if (!I->materials_set) return fail(h, FDTD_E_STATE, "set materials first");
+    size_t need;
+    if (field_count(*I, which, need)) return fail(h, FDTD_E_INVAL, "unknown field selector");
+    if (!in || count < need) return fail(h, FDTD_E_INVAL, "input too small");
+    CKR(h, cudaStreamSynchronize(h->sim->stream));
+    const size_t nf = I->n_field();
+    if (which <= FDTD_F_HZ) {
+        CKR(h, cudaMemcpy2D(I->fields + which * nf, I->px * sizeof(float), in, I->nx * sizeof(float), I->nx * sizeof(float),
+                            (size_t)I->ny * I->nz, cudaMemcpyHostToDevice));
+    } else if (which <= FDTD_F_MZ || which >= FDTD_F_DMX) {
+        const bool dev = which >= FDTD_F_DMX;
+        const int d = dev ? which - FDTD_F_DMX : which - FDTD_F_MX;
+        std::vector<std::vector<double>> g;
+        std::vector<std::vector<uint8_t>> mt;
+        int rc = magnet_read(h, *I, g, mt, true);
+        if (rc) return rc;
+        for (size_t c = 0; c < I->comps.size(); ++c) {
+            const MagComp &C = I->comps[c];
+            std::vector<float> m(3 * (size_t)C.V, 0.f);
+            for (int v = 0; v < C.V; ++v) {
+                if (mt[c][v] == 0xFF) continue;
+                const int li = v % C.bx, lj = (v / C.bx) % C.by, lk = v / (C.bx * C.by);
+                const double x = in[((size_t)(C.z0 + lk) * I->ny + (C.y0 + lj)) * I->nx + (C.x0 + li)];
+                g[c][(size_t)d * C.V + v] = dev ? x : x - I->mm_Ms[mt[c][v]] * I->u[d];
+                const double dg[3] = {g[c][v], g[c][C.V + v], g[c][2 * (size_t)C.V + v]};
+                for (int q = 0; q < 3; ++q)
+                    m[(size_t)q * C.V + v] = (float)((double)I->R[3 * q] * dg[0] + (double)I->R[3 * q + 1] * dg[1] +
+                                                     (double)I->R[3 * q + 2] * dg[2]);
+            }
+            CKR(h, cudaMemcpy(C.m, m.data(), m.size() * sizeof(float), cudaMemcpyHostToDevice));
+        }
+    } else {
+        size_t off = 0;
+        if (which >= FDTD_F_HY_WALL) off += (size_t)I->ny * I->nz;
+        if (which >= FDTD_F_HZ_WALL) off += (size_t)I->nx * I->nz;
+        CKR(h, cudaMemcpy(I->walls + off, in, need * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    h->sim->half_ahead = false;
+    return FDTD_OK;
+}
+
+// ---------------------------------------------------------- checkpoints
+namespace {
+struct StateHeader {
+    uint32_t magic, version;
+    int32_t nx, ny, nz, ncomp;
+    int64_t step;
+    int32_t half_ahead, pad;
+    uint64_t bytes;
+};
+constexpr uint32_t kMagic = 0x4c4c4446u;   // "FDLL"
+}  // namespace
+
+static size_t state_bytes(const Instance &I)
+{
+    size_t b = sizeof(StateHeader) + 6 * (size_t)I.nx * I.ny * I.nz * sizeof(float);
+    b += I.n_wall() * sizeof(float);
+    for (auto &C : I.comps) b += 3 * (size_t)C.V * sizeof(float);
+    return b;
+}
+
+extern "C" int fdtd_llg_save_state(fdtd_llg_t h, void *buf, size_t *size)
+{
+    if (!is_member(h)) return fail(h, FDTD_E_INVAL, "save_state needs an instance handle");
+    Instance *I = inst_of(h);
+    if (!size) return fail(h, FDTD_E_INVAL, "null size");
+    const size_t need = state_bytes(*I);
+    if (!buf) { *size = need; return FDTD_OK; }
+    if (*size < need) { *size = need; return fail(h, FDTD_E_INVAL, "buffer too small"); }
+    int rc = sync_status(h);
+    if (rc) return rc;
+    StateHeader hd{kMagic, 1, I->nx, I->ny, I->nz, (int32_t)I->comps.size(), h->sim->host_step, h->sim->half_ahead ? 1 : 0, 0, need};
+    char *p = (char *)buf;
+    std::memcpy(p, &hd, sizeof hd);
+    p += sizeof hd;
+    const size_t nf = I->n_field();
+    const size_t ncell = (size_t)I->nx * I->ny * I->nz;
+    for (int f = 0; f < 6; ++f) {
+        CKR(h, cudaMemcpy2D(p, I->nx * sizeof(float), I->fields + f * nf, I->px * sizeof(float), I->nx * sizeof(float),
+                            (size_t)I->ny * I->nz, cudaMemcpyDeviceToHost));
+        p += ncell * sizeof(float);
+    }
+    CKR(h, cudaMemcpy(p, I->walls, I->n_wall() * sizeof(float), cudaMemcpyDeviceToHost));
+    p += I->n_wall() * sizeof(float);
+    for (auto &C : I->comps) {
+        CKR(h, cudaMemcpy(p, C.m, 3 * (size_t)C.V * sizeof(float), cudaMemcpyDeviceToHost));
+        p += 3 * (size_t)C.V * sizeof(float);
+    }
+    *size = need;
+    return FDTD_OK;
+}
+
+extern "C" int fdtd_llg_load_state(fdtd_llg_t h, const void *buf, size_t size)
+{
+    if (!is_member(h)) return fail(h, FDTD_E_INVAL, "load_state needs an instance handle");
+    Instance *I = inst_of(h);
+    if (h->sim->inst.size() > 1) return fail(h, FDTD_E_NOSYS, "load_state applies to single-instance handles");
+    if (!buf || size < sizeof(StateHeader)) return fail(h, FDTD_E_INVAL, "buffer too small");
+    StateHeader hd;
+    std::memcpy(&hd, buf, sizeof hd);
+    if (hd.magic != kMagic || hd.version != 1 || hd.nx != I->nx || hd.ny != I->ny || hd.nz != I->nz ||
+        hd.ncomp != (int)I->comps.size() || hd.bytes != state_bytes(*I) || size < hd.bytes)
+        return fail(h, FDTD_E_INVAL, "state does not match this handle");
+    CKR(h, cudaStreamSynchronize(h->sim->stream));
+    const char *p = (const char *)buf + sizeof hd;
+    const size_t nf = I->n_field();
+    const size_t ncell = (size_t)I->nx * I->ny * I->nz;
+    for (int f = 0; f < 6; ++f) {
+        CKR(h, cudaMemcpy2D(I->fields + f * nf, I->px * sizeof(float), p, I->nx * sizeof(float), I->nx * sizeof(float),
+                            (size_t)I->ny * I->nz, cudaMemcpyHostToDevice));
+        p += ncell * sizeof(float);
+    }
+    CKR(h, cudaMemcpy(I->walls, p, I->n_wall() * sizeof(float), cudaMemcpyHostToDevice));
+    p += I->n_wall() * sizeof(float);
+    for (auto &C : I->comps) {
+        CKR(h, cudaMemcpy(C.m, p, 3 * (size_t)C.V * sizeof(float), cudaMemcpyHostToDevice));
+        p += 3 * (size_t)C.V * sizeof(float);
+    }
+    Sim *S = h->sim;
+    S->host_step = hd.step;
+    S->half_ahead = hd.half_ahead != 0;
+    StepCtl c{};
+    c.step = hd.step;
+    CKR(h, cudaMemcpy(S->d_ctl, &c, sizeof c, cudaMemcpyHostToDevice));
+    return FDTD_OK;
+}
+
+// ------------------------------------------------------------- profiling
+extern "C" int fdtd_llg_set_profiling(fdtd_llg_t h, int32_t on)
+{
+    if (!h || !h->sim) return fail(h, FDTD_E_INVAL, "null handle");
+    h->sim->profiling = on != 0;
+    return FDTD_OK;
+}
+
+extern "C" int fdtd_llg_read_profile(fdtd_llg_t h, fdtd_llg_profile *out, int32_t reset)
+{
+    if (!h || !h->sim || !out) return fail(h, FDTD_E_INVAL, "null argument");
+    Sim *S = h->sim;
+    CKR(h, cudaStreamSynchronize(S->stream));
+    for (auto &r : S->recs) {
+        float ms = 0.f;
+        CKR(h, cudaEventElapsedTime(&ms, r.a, r.b));
+        S->prof.launches[r.kind] += 1;
+        S->prof.ms[r.kind] += ms;
+        S->ev_pool.push_back(r.a);
+        S->ev_pool.push_back(r.b);
+    }
+    S->recs.clear();
+    long long cells = 0;
+    for (auto &I : S->inst) cells += (long long)I.nx * I.ny * I.nz;
+    S->prof.cells = cells;
+    *out = S->prof;
+    if (reset) S->prof = fdtd_llg_profile{};
+    return FDTD_OK;
+}
