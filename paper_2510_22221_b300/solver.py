@@ -1,0 +1,248 @@
+"""Thin Python binding of the C ABI (include/fdtd_llg.h): argument
+marshalling only; every step of the method runs in libfdtd_llg.so.
+
+PyTorch supplies the CUDA stream and, by default, device memory through its
+caching allocator (passed to the library as alloc/free callbacks).
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+from typing import Sequence
+
+import numpy as np
+
+from . import _abi
+from ._abi import FIELDS, check
+
+
+@dataclass
+class Material:
+    eps_r: float = 1.0
+    sigma: float = 0.0
+    Ms: float = 0.0            # A/m; 0 = non-magnetic
+    alpha: float = 0.0
+    gamma: float = 1.76e11     # |gamma| in rad/(s T)
+    pec: bool = False
+
+
+class _TorchAllocator:
+    """alloc/free callbacks backed by torch's CUDA caching allocator."""
+
+    def __init__(self):
+        import torch
+
+        def _alloc(nbytes, stream, user):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), stream=stream or 0))
+            except Exception:
+                return None
+
+        def _free(ptr, user):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.alloc = _abi.ALLOC_FN(_alloc)
+        self.free = _abi.FREE_FN(_free)
+
+
+def _config(nx, ny, nz, dx, dy, dz, dt, courant_factor, llg_tol, llg_max_iter, llg_fixed_iter,
+            probe_capacity, energy, device, stream, allocator):
+    cfg = _abi.Config()
+    cfg.nx, cfg.ny, cfg.nz = int(nx), int(ny), int(nz)
+    cfg.dx, cfg.dy, cfg.dz = float(dx), float(dy), float(dz)
+    cfg.dt, cfg.courant_factor = float(dt), float(courant_factor)
+    cfg.llg_tol, cfg.llg_max_iter, cfg.llg_fixed_iter = float(llg_tol), int(llg_max_iter), int(llg_fixed_iter)
+    cfg.probe_capacity, cfg.energy_every, cfg.device = int(probe_capacity), 1 if energy else 0, int(device)
+    cfg.stream = stream
+    if allocator is not None:
+        cfg.alloc, cfg.free = allocator.alloc, allocator.free
+    return cfg
+
+
+def _torch_stream(device):
+    import torch
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device: the solver runs only on the GPU")
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+class FdtdLlg:
+    """One grid (``create``) or a batch of grids (``create_batch``)."""
+
+    def __init__(self, handle, root, allocator=None, dims=None):
+        self._h = handle
+        self._root = root          # the owning handle object (self for roots)
+        self._alloc = allocator
+        self._dims = dims          # (nx, ny, nz)
+        self._members = {}
+        self._batch_dims = None
+
+    # ------------------------------------------------------------- creation
+    @classmethod
+    def create(cls, nx, ny, nz, dx, dy, dz, dt=0.0, courant_factor=0.5, llg_tol=1e-6, llg_max_iter=20,
+               llg_fixed_iter=0, probe_capacity=4096, energy=True, device=0, torch_memory=True):
+        lib = _abi.load()
+        stream = _torch_stream(device)
+        alloc = _TorchAllocator() if torch_memory else None
+        cfg = _config(nx, ny, nz, dx, dy, dz, dt, courant_factor, llg_tol, llg_max_iter, llg_fixed_iter,
+                      probe_capacity, energy, device, stream, alloc)
+        h = C.c_void_p()
+        check(lib.fdtd_llg_create(C.byref(cfg), C.byref(h)))
+        obj = cls(h, None, alloc, (int(nx), int(ny), int(nz)))
+        obj._root = obj
+        return obj
+
+    @classmethod
+    def create_batch(cls, dims: Sequence[tuple], spacings: Sequence[tuple], dt=0.0, courant_factor=0.5,
+                     llg_tol=1e-6, llg_max_iter=20, llg_fixed_iter=0, probe_capacity=4096, energy=True,
+                     device=0, torch_memory=True):
+        lib = _abi.load()
+        stream = _torch_stream(device)
+        alloc = _TorchAllocator() if torch_memory else None
+        n = len(dims)
+        arr = (_abi.Config * n)()
+        for q, ((nx, ny, nz), (dx, dy, dz)) in enumerate(zip(dims, spacings)):
+            arr[q] = _config(nx, ny, nz, dx, dy, dz, dt, courant_factor, llg_tol, llg_max_iter, llg_fixed_iter,
+                             probe_capacity, energy, device, stream, alloc)
+        h = C.c_void_p()
+        check(lib.fdtd_llg_create_batch(arr, n, C.byref(h)))
+        obj = cls(h, None, alloc, None)
+        obj._root = obj
+        obj._batch_dims = [tuple(int(v) for v in d) for d in dims]
+        if n == 1:
+            obj._dims = obj._batch_dims[0]
+        return obj
+
+    def batch_member(self, i: int) -> "FdtdLlg":
+        if self._batch_dims is None:
+            if i != 0:
+                raise IndexError("a single-instance handle has only member 0")
+            return self
+        if i not in self._members:
+            m = C.c_void_p()
+            check(_abi.load().fdtd_llg_batch_member(self._h, int(i), C.byref(m)), self._h)
+            self._members[i] = FdtdLlg(m, self, None, self._batch_dims[i])
+        return self._members[i]
+
+    # ------------------------------------------------------------ set-up
+    def set_materials(self, mat_id, table: Sequence[Material], hbias, eps_r_design=None, design_box=None):
+        lib = _abi.load()
+        nx, ny, nz = self._dims
+        if hasattr(mat_id, "data_ptr"):                      # torch tensor (host or device)
+            if mat_id.numel() != nx * ny * nz:
+                raise ValueError("mat_id must hold nx*ny*nz entries")
+            keep = mat_id.contiguous()
+            ptr = C.c_void_p(keep.data_ptr())
+        else:
+            keep = np.ascontiguousarray(mat_id, dtype=np.uint8).reshape(-1)
+            if keep.size != nx * ny * nz:
+                raise ValueError("mat_id must hold nx*ny*nz entries")
+            ptr = C.c_void_p(keep.ctypes.data)
+        tab = (_abi.MaterialC * len(table))()
+        for q, m in enumerate(table):
+            tab[q] = _abi.MaterialC(m.eps_r, m.sigma, m.Ms, m.alpha, m.gamma, 1 if m.pec else 0, 0)
+        hb = (C.c_double * 3)(*[float(v) for v in hbias])
+        des = None
+        box = None
+        des_np = None
+        if eps_r_design is not None:
+            des_np = np.ascontiguousarray(eps_r_design, dtype=np.float64).reshape(-1)
+            des = des_np.ctypes.data_as(C.POINTER(C.c_double))
+            box = (C.c_int32 * 6)(*[int(v) for v in design_box])
+        rc = lib.fdtd_llg_set_materials(self._h, ptr, tab, len(table), hb, des, box)
+        del keep, des_np
+        check(rc, self._h)
+
+    def set_source(self, comp, i, j, k, J0, f0, Tp=0.0, t_peak=0.0):
+        check(_abi.load().fdtd_llg_set_source(self._h, int(comp), int(i), int(j), int(k), float(J0), float(f0),
+                                              float(Tp), float(t_peak)), self._h)
+
+    def add_probe(self, i, j, k) -> int:
+        pid = C.c_int32()
+        check(_abi.load().fdtd_llg_add_probe(self._h, int(i), int(j), int(k), C.byref(pid)), self._h)
+        return pid.value
+
+    # -------------------------------------------------------------- run
+    def step(self, nsteps: int):
+        check(_abi.load().fdtd_llg_step(self._h, int(nsteps)), self._h)
+
+    def sync(self):
+        check(_abi.load().fdtd_llg_sync(self._h), self._h)
+
+    def time_state(self):
+        s = C.c_int64()
+        half = C.c_int32()
+        check(_abi.load().fdtd_llg_time_state(self._h, C.byref(s), C.byref(half)), self._h)
+        return s.value, bool(half.value)
+
+    # ------------------------------------------------------------ outputs
+    def probe(self, pid: int, cap_rows: int = 1 << 40) -> np.ndarray:
+        lib = _abi.load()
+        step, _ = self.time_state()
+        rows_max = int(min(cap_rows, step))
+        out = np.zeros((max(rows_max, 1), 9))
+        rows = C.c_int64()
+        check(lib.fdtd_llg_probe(self._h, int(pid), out.ctypes.data_as(C.POINTER(C.c_double)), rows_max,
+                                 C.byref(rows)), self._h)
+        return out[: rows.value]
+
+    def energy(self, cap: int = 1 << 40) -> np.ndarray:
+        lib = _abi.load()
+        step, _ = self.time_state()
+        n = int(min(cap, step))
+        out = np.zeros(max(n, 1))
+        w = C.c_int64()
+        check(lib.fdtd_llg_energy(self._h, out.ctypes.data_as(C.POINTER(C.c_double)), n, C.byref(w)), self._h)
+        return out[: w.value]
+
+    def _shape(self, name):
+        nx, ny, nz = self._dims
+        return {"Hx_wall": (nz, ny), "Hy_wall": (nz, nx), "Hz_wall": (ny, nx)}.get(name, (nz, ny, nx))
+
+    def get_field(self, name: str) -> np.ndarray:
+        shp = self._shape(name)
+        out = np.zeros(shp, dtype=np.float32)
+        check(_abi.load().fdtd_llg_get_field(self._h, FIELDS[name], out.ctypes.data_as(C.POINTER(C.c_float)),
+                                             out.size), self._h)
+        return out
+
+    def set_field(self, name: str, values):
+        shp = self._shape(name)
+        arr = np.ascontiguousarray(np.broadcast_to(values, shp), dtype=np.float32)
+        check(_abi.load().fdtd_llg_set_field(self._h, FIELDS[name], arr.ctypes.data_as(C.POINTER(C.c_float)),
+                                             arr.size), self._h)
+
+    def save_state(self) -> bytes:
+        lib = _abi.load()
+        n = C.c_size_t()
+        check(lib.fdtd_llg_save_state(self._h, None, C.byref(n)), self._h)
+        buf = C.create_string_buffer(n.value)
+        check(lib.fdtd_llg_save_state(self._h, buf, C.byref(n)), self._h)
+        return buf.raw[: n.value]
+
+    def load_state(self, data: bytes):
+        buf = C.create_string_buffer(data, len(data))
+        check(_abi.load().fdtd_llg_load_state(self._h, buf, len(data)), self._h)
+
+    # ------------------------------------------------------------ profiling
+    def set_profiling(self, on: bool):
+        check(_abi.load().fdtd_llg_set_profiling(self._h, 1 if on else 0), self._h)
+
+    def read_profile(self, reset: bool = True) -> dict:
+        pr = _abi.Profile()
+        check(_abi.load().fdtd_llg_read_profile(self._h, C.byref(pr), 1 if reset else 0), self._h)
+        kinds = ("e_pass", "mag_pass", "h_pass")
+        return {"cells": pr.cells, **{k: {"launches": pr.launches[q], "ms": pr.ms[q]} for q, k in enumerate(kinds)}}
+
+    # ----------------------------------------------------------- cleanup
+    def destroy(self):
+        if self._root is self and self._h:
+            _abi.load().fdtd_llg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
