@@ -1,0 +1,235 @@
+"""CUDA path vs the FP64 oracle, element by element, on the same seeded
+inputs, through the C ABI (arxiv 2510.22221, section "Numerical Model").
+
+Tolerance.  Fields are FP32 (unit roundoff u = 6e-8).  Each update rounds a
+handful of times and the leap-frog neither damps nor amplifies roundoff, so
+after N steps the deviation from FP64 is ~u sqrt(N) typical, bounded by ~c u N
+with c of order ten; the tests use max|gpu - fp64| <= TOL(N) * scale with
+TOL(N) = 20 u N, floored at 2e-5 (the FP32 rounding of the coefficients
+themselves, ~u relative per update, enters every step).  FP32 errors are
+absolute at the size of the largest nearby values, so the scale is the
+largest FP64 value of the same family (E: Ex, Ey, Ez; H: the three H
+components and the wall faces; M: the change of M from its start) at the
+probe or over the grid, not the component's own largest value: a component a
+thousand times weaker than its neighbours carries the same absolute error."""
+import numpy as np
+import pytest
+
+import paper_2510_22221_b300 as pkg
+from paper_2510_22221_b300 import workloads as W
+from tests.helpers import compact, dropped_values, oracle_from_workload
+
+pytestmark = pytest.mark.gpu
+
+U32 = 6e-8
+
+
+def tol(n):
+    return max(2e-5, 20 * U32 * n)
+
+
+def rel_err(a, b, scale=None):
+    if scale is None:
+        scale = float(np.abs(b).max())
+    if scale == 0.0:
+        return float(np.abs(a).max())
+    return float(np.abs(np.asarray(a, np.float64) - b).max()) / scale
+
+
+FAMILIES = {"E": ("Ex", "Ey", "Ez"), "H": ("Hx", "Hy", "Hz", "Hx_wall", "Hy_wall", "Hz_wall"), "M": ("Mx", "My", "Mz")}
+
+
+def probe_errors(g, ref, M0cell):
+    """Per-component errors of a probe series (rows x 9) with family scales."""
+    g = np.asarray(g, np.float64).copy()
+    ref = np.asarray(ref, np.float64).copy()
+    for d in range(3):
+        g[:, 6 + d] -= M0cell[d]
+        ref[:, 6 + d] -= M0cell[d]
+    errs = []
+    for c in range(9):
+        fam = slice(3 * (c // 3), 3 * (c // 3) + 3)
+        errs.append(rel_err(g[:, c], ref[:, c], float(np.abs(ref[:, fam]).max())))
+    return errs
+
+
+def run_pair(w, steps, **kw):
+    sim = pkg.from_workload(w, probe_capacity=max(steps, 1), **kw)
+    orc = oracle_from_workload(w, llg_fixed_iter=kw.get("llg_fixed_iter", 0))
+    M0 = orc.M.copy()
+    sim.step(steps)
+    out = orc.run(steps)
+    return sim, orc, out, M0
+
+
+def compare_fields(sim, orc, M0, t):
+    """GPU state after N steps holds E^N and H, M at N + 1/2; move the oracle
+    there with one half-push and compare every stored value."""
+    assert dropped_values(orc) == 0.0
+    orc.half_push()
+    ref = compact(orc)
+    got = {n: sim.get_field(n).astype(np.float64) for n in FAMILIES["E"] + FAMILIES["H"]}
+    for d, n in enumerate(FAMILIES["M"]):
+        ref[n] = ref[n] - M0[d]
+        got[n] = sim.get_field("d" + n).astype(np.float64)
+    errs = {}
+    for fam in FAMILIES.values():
+        scale = max(float(np.abs(ref[n]).max()) for n in fam)
+        for n in fam:
+            errs[n] = rel_err(got[n], ref[n], scale)
+    bad = {k: v for k, v in errs.items() if v > t}
+    assert not bad, (bad, errs)
+    return errs
+
+
+def test_cavity_block_probe_energy_and_fields():
+    w = W.cavity_block(steps=2000)
+    sim, orc, out, M0 = run_pair(w, w.steps)
+    g = sim.probe(0)
+    assert g.shape == (w.steps, 9)
+    t = tol(w.steps)
+    errs = probe_errors(g, out["probes"][:, 0], np.zeros(3))
+    assert max(errs) < t, errs
+    assert np.all(g[:, 6:] == 0)          # the probe cell is outside the block
+    assert rel_err(sim.energy(), out["energy"]) < t
+    compare_fields(sim, orc, M0, t)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_random_small_every_feature(seed):
+    w = W.random_small(seed, steps=60, sigma=3e3 * seed, design=seed > 0)
+    sim, orc, out, M0 = run_pair(w, w.steps)
+    t = tol(w.steps)
+    for p, (i, j, k) in enumerate(w.probes):
+        errs = probe_errors(sim.probe(p), out["probes"][:, p], M0[:, k, j, i])
+        assert max(errs) < t, (p, errs)
+    assert rel_err(sim.energy(), out["energy"]) < t
+    compare_fields(sim, orc, M0, t)
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (1, 1, 2), (33, 9, 17), (40, 1, 3), (3, 70, 2)])
+def test_ragged_and_degenerate_grids(dims):
+    nx, ny, nz = dims
+    rng = np.random.default_rng(nx * 100 + ny * 10 + nz)
+    mats = [W.material(), W.material(eps_r=3.0), W.material(eps_r=1.0, Ms=1.4e5, alpha=0.02, gamma=1.76e11)]
+    mid = rng.integers(0, 2, size=(nz, ny, nx)).astype(np.uint8)
+    mid[nz // 2, ny // 2, nx // 2] = 2
+    w = W.Workload("ragged", nx, ny, nz, 1e-6, 0.7e-6, 1.2e-6, 0.5, 30, mats, mid,
+                   np.array([1e5, -3e4, 2e4]),
+                   [dict(comp=1, i=nx // 2, j=0, k=nz // 2, J0=2e6, f0=3e12, Tp=1e-13, tpk=2e-13)],
+                   [(nx // 2, ny // 2, nz // 2), (nx - 1, ny - 1, nz - 1)])
+    sim, orc, out, M0 = run_pair(w, w.steps)
+    compare_fields(sim, orc, M0, tol(w.steps))
+
+
+def test_tilted_magnetisation_precesses_like_the_oracle():
+    """Set a tilted M through the ABI (deviation from the bias), run, compare."""
+    w = W.random_small(7, steps=80)
+    sim = pkg.from_workload(w, probe_capacity=80)
+    orc = oracle_from_workload(w)
+    rng = np.random.default_rng(3)
+    Ms = np.array([m["Ms"] for m in w.materials])[w.mat_id]
+    M0 = orc.M.copy()
+    M = M0 + rng.normal(size=M0.shape) * 2e4 * (Ms > 0)
+    M *= np.where(Ms > 0, Ms / np.maximum(np.linalg.norm(M, axis=0), 1e-300), 0.0)
+    dM = M - M0
+    for d, n in enumerate(("dMx", "dMy", "dMz")):
+        sim.set_field(n, dM[d].astype(np.float32))
+    # start the oracle from the float32 value the solver holds
+    for d, n in enumerate(("dMx", "dMy", "dMz")):
+        dM[d] = sim.get_field(n)
+    orc.set_fields(M=M0 + dM)
+    sim.step(80)
+    orc.run(80)
+    compare_fields(sim, orc, M0, tol(80))
+
+
+def test_zero_steps_and_initial_state():
+    w = W.cavity_block(steps=0)
+    sim = pkg.from_workload(w, probe_capacity=4)
+    sim.step(0)
+    assert sim.time_state() == (0, False)
+    assert sim.probe(0).shape == (0, 9)
+    mz = sim.get_field("Mz")
+    assert np.allclose(mz[w.mat_id == 1], 1.4e5) and np.all(mz[w.mat_id == 0] == 0)
+    assert np.all(sim.get_field("dMx") == 0)
+
+
+def test_checkpoint_resume_is_bitwise():
+    w = W.random_small(5, steps=40, design=True)
+    a = pkg.from_workload(w, probe_capacity=64)
+    a.step(17)
+    blob = a.save_state()
+    a.step(23)
+    fa = {n: a.get_field(n) for n in ("Ex", "Hy", "dMz", "Hx_wall")}
+    b = pkg.from_workload(w, probe_capacity=64)
+    b.load_state(blob)
+    assert b.time_state() == (17, True)
+    b.step(23)
+    for n, v in fa.items():
+        np.testing.assert_array_equal(b.get_field(n), v)
+
+
+def test_batch_equals_separate_runs_bitwise():
+    ws = [W.random_small(s, nx=9 + 7 * s, ny=10, nz=8 + s, steps=25) for s in range(3)]
+    dims = [(x.nx, x.ny, x.nz) for x in ws]
+    sp = [(x.dx, x.dy, x.dz) for x in ws]
+    dt_common = 0.6 * min(1 / (299792458.0 * np.sqrt(1 / x.dx ** 2 + 1 / x.dy ** 2 + 1 / x.dz ** 2)) for x in ws)
+    batch = pkg.FdtdLlg.create_batch(dims, sp, dt=dt_common, probe_capacity=32)
+    for q, x in enumerate(ws):
+        pkg.configure(batch.batch_member(q), x)
+    batch.step(25)
+    for q, x in enumerate(ws):
+        single = pkg.FdtdLlg.create(x.nx, x.ny, x.nz, x.dx, x.dy, x.dz, dt=dt_common, probe_capacity=32)
+        pkg.configure(single, x)
+        single.step(25)
+        m = batch.batch_member(q)
+        for n in ("Ex", "Ez", "Hy", "dMx", "Hx_wall"):
+            np.testing.assert_array_equal(m.get_field(n), single.get_field(n))
+        np.testing.assert_array_equal(m.probe(1), single.probe(1))
+        np.testing.assert_array_equal(m.energy(), single.energy())
+
+
+def test_llg_nonconvergence_is_reported():
+    w = W.random_small(3, steps=5)
+    sim = pkg.FdtdLlg.create(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, courant_factor=w.courant, llg_tol=1e-30,
+                             llg_max_iter=2)
+    pkg.configure(sim, w)
+    sim.step(3)
+    with pytest.raises(pkg.LLGError) as ei:
+        sim.sync()
+    assert ei.value.code == -5
+
+
+def test_unstable_run_is_reported():
+    w = W.cavity_block(steps=5)
+    sim = pkg.from_workload(w, probe_capacity=8)
+    sim.set_field("Ex", np.full((w.nz, w.ny, w.nx), np.inf, dtype=np.float32))
+    sim.step(2)
+    with pytest.raises(pkg.LLGError) as ei:
+        sim.sync()
+    assert ei.value.code == -4
+
+
+def test_invalid_geometry_rejected():
+    n = 40
+    mats = [W.material(), W.material(Ms=1.4e5, alpha=0.01)]
+    mid = np.zeros((n, n, n), dtype=np.uint8)
+    mid[:20, :20, :20] = 1                    # 8000-cell region > 4096
+    sim = pkg.FdtdLlg.create(n, n, n, 1e-6, 1e-6, 1e-6)
+    with pytest.raises(pkg.LLGError) as ei:
+        sim.set_materials(mid, [pkg.Material(**m) for m in mats], [0, 0, 1e5])
+    assert ei.value.code == -1
+    with pytest.raises(pkg.LLGError):
+        sim.add_probe(n, 0, 0)
+
+
+def test_torch_allocator_backs_device_memory():
+    import torch
+
+    before = torch.cuda.memory_allocated()
+    w = W.cavity_block(steps=1)
+    sim = pkg.from_workload(w, probe_capacity=4)
+    assert torch.cuda.memory_allocated() - before >= 6 * w.cells * 4
+    sim.destroy()
+    assert torch.cuda.memory_allocated() - before < 1 << 20
