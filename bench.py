@@ -1,0 +1,276 @@
+#!/usr/bin/env python
+"""Throughput of the Yee-Maxwell + LLG step on one B300 (or N replicas).
+
+A step is one full time step of the hot path over the whole grid: E push with
+the point source, the LLG-coupled H/M half-push pair of the magnetic regions,
+the H push, FP64 probe samples and the FP64 energy sum.  Workload: the
+256 x 256 x 128 strip resonator with a YIG film (8.39 M cells, FP32 fields,
+201 MB of field state > the 126 MB L2, so every step streams from HBM).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Yee+LLG Mcell-updates/s, % of HBM roofline; adjoint/forward time ratio"
+UNIT = "Mcell-updates/s"
+ALG_BYTES_PER_CELL_STEP = 49          # FP32 E and H read + written once, 1 B material class
+PASS_BYTES_PER_CELL = {"e_pass": 37, "h_pass": 37}   # read E,H (24) + write one field (12) + class (1)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_2510_22221_b300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".h", ".cuh")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the
+    present kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{kernel}_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_sources_sha1") != kernel_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 6 and parts[0].isdigit():
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [int(r[0]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4) if r[2 + q].lower() == "active"})
+        loaded = [v for v in sm if v > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": int(rows[0][1]), "reasons": reasons,
+                "samples": len(sm)}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def cpu_baseline(w, steps, seconds_cap=25.0):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of
+    the workload: up to `steps` full time steps of the whole grid."""
+    from tests.helpers import oracle_from_workload
+
+    orc = oracle_from_workload(w)
+    t0 = time.perf_counter()
+    done = 0
+    while done < steps:
+        orc.run(1)
+        done += 1
+        if time.perf_counter() - t0 > seconds_cap:
+            break
+    t = time.perf_counter() - t0
+    return {"value": round(w.cells * done / t / 1e6, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} full steps of the {w.nx}x{w.ny}x{w.nz} grid ({w.cells / 1e6:.2f} M cells), "
+                      f"FP64 C oracle, one thread, {t:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2510_22221_b300 import workloads as W
+
+    w = W.strip_resonator(steps=args.steps)
+    base = cpu_baseline(w, min(args.steps, 12), seconds_cap=120.0)
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "cells": w.cells, "parallelism": "host oracle, rank 0"},
+            "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2510_22221_b300 as pkg
+    from paper_2510_22221_b300 import workloads as W
+
+    K, Wm = args.steps, max(args.warmup, 3)
+    w = W.strip_resonator(steps=K)
+    sim = pkg.from_workload(w, probe_capacity=K + Wm + 16)
+    stream = torch.cuda.current_stream()
+
+    sim.step(Wm)
+    sim.sync()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(K)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    sim.sync()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * w.cells * K / (ms * 1e-3) / 1e6
+
+    # per-pass device time from events the library records on its stream
+    kp = min(K, 2000)
+    sim.set_profiling(True)
+    sim.step(kp)
+    prof = sim.read_profile(reset=True)
+    sim.set_profiling(False)
+    hbm, peak_kind = peaks()
+    passes = {k: prof[k] for k in ("e_pass", "mag_pass", "h_pass")}
+    dom = max(("e_pass", "h_pass"), key=lambda k: passes[k]["ms"])
+    avg_ms = passes[dom]["ms"] / max(passes[dom]["launches"], 1)
+    alg = PASS_BYTES_PER_CELL[dom] * w.cells
+    achieved = alg / (avg_ms * 1e-3) / 1e9
+    traffic = recorded_traffic(dom, w.name)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": traffic,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                "alg_bytes_per_launch": alg, "avg_launch_ms": round(avg_ms, 5),
+                "pass_ms_per_step": {k: round(v["ms"] / max(v["launches"], 1), 5) for k, v in passes.items()}}
+
+    line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
+            "ms_per_step": round(ms / K, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "cells": w.cells, "dx_m": w.dx, "magnet_cells": int((w.mat_id == 3).sum()),
+                       "probes": len(w.probes), "energy": "every step, FP64",
+                       "l2": "field state 201 MB > 126 MB L2: inputs larger than L2, no flush",
+                       "parallelism": "one independent grid per GPU" if world > 1 else "single GPU"},
+            "hbm_roofline_pct": round(100 * value * 1e6 * ALG_BYTES_PER_CELL_STEP / (world * hbm * 1e9), 2),
+            "roofline": roofline, "gpu_launches": 3 * K, "clocks": clk,
+            "adjoint_forward_ratio": None}
+
+    # end to end through the public API: materials from pinned host memory,
+    # then every step a step call and a device-to-host read of its probe rows
+    # and energy
+    ke = min(K, 2000)
+    mat_pinned = torch.from_numpy(np.ascontiguousarray(w.mat_id).reshape(-1)).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    sim2 = pkg.FdtdLlg.create(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, courant_factor=w.courant, probe_capacity=ke + 8)
+    sim2.set_materials(mat_pinned, [pkg.Material(**m) for m in w.materials], w.hbias)
+    for s in w.sources:
+        sim2.set_source(s["comp"], s["i"], s["j"], s["k"], s["J0"], s["f0"], s["Tp"], s["tpk"])
+    for p in w.probes:
+        sim2.add_probe(*p)
+    for _ in range(ke):
+        sim2.step(1)
+        for p in range(len(w.probes)):
+            sim2.probe(p, cap_rows=1)
+        sim2.energy(cap=1)
+    barrier()
+    te = time.perf_counter() - t0
+    sim2.destroy()
+    line["e2e"] = {"value": round(world * w.cells * ke / te / 1e6, 1), "unit": UNIT,
+                   "h2d_bytes_per_step": round((w.cells + 64 * len(w.materials)) / ke, 1),
+                   "d2h_bytes_per_step": 8 * (9 * len(w.probes) + 1), "steps": ke,
+                   "includes": "create + set_materials (host preprocessing, H2D) + per-step D2H of probes and energy"}
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(w, 12)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
