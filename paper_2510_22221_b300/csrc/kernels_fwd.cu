@@ -323,8 +323,11 @@ __device__ __forceinline__ float curl_z(const Inst *I, int i, int j, int k)
 // The LLG solve runs in the bias frame (rows of I->R: e1, e2, e3 = h) on the
 // deviation m = M - Ms e3, so the transverse components that carry the
 // precession are resolved to full FP32 relative precision even when Ms h has
-// three large global components.  The face coupling and the neighbour terms
-// of H_eff stay in global components (they act per axis).
+// three large global components, and the change of M that feeds the faces is
+// computed from small terms only (never as the difference of two large
+// values).  The normalisation keeps |M| at its stored value, equal to Ms up to
+// FP32 storage rounding.  The face coupling and the neighbour terms of H_eff
+// stay in global components (they act per axis).
 __device__ __forceinline__ void to_frame(const float *R, float gx, float gy, float gz, float &lx, float &ly, float &lz)
 {
     lx = R[0] * gx + R[1] * gy + R[2] * gz;
@@ -345,7 +348,7 @@ __global__ void __launch_bounds__(kMagThreads) mag_pass_kernel(LaunchSet L, int 
     __shared__ double sredd[kMagThreads / 32];
     const int Vm = L.vmax;
     float *sM = smem;            // m at the start of the half-push (bias frame)
-    float *sB = sM + 3 * Vm;     // b of Eq. llg_tra6 (bias frame; z stored as b_z - Ms)
+    float *sB = sM + 3 * Vm;     // b - M^n of Eq. llg_tra6 (bias frame)
     float *sA = sB + 3 * Vm;     // cell mean of H^* (H after the curl push), global
     float *sD = sA + 3 * Vm;     // M^{r} - M^{n}, current iterate, global
     uint8_t *smat = reinterpret_cast<uint8_t *>(sD + 3 * Vm);
@@ -397,9 +400,10 @@ __global__ void __launch_bounds__(kMagThreads) mag_pass_kernel(LaunchSet L, int 
             const float mx = sM[v], my = sM[Vm + v], mz = sM[2 * Vm + v];
             const float Mz = I->mm[m].Ms + mz;
             const float kap = I->mm[m].kappa;
-            sB[v] = mx - kap * (my * hez - Mz * hey);
-            sB[Vm + v] = my - kap * (Mz * hex - mx * hez);
-            sB[2 * Vm + v] = mz - kap * (mx * hey - my * hex);
+            // b - M^n of Eq. llg_tra6: -kappa M^n x H_eff^n
+            sB[v] = -kap * (my * hez - Mz * hey);
+            sB[Vm + v] = -kap * (Mz * hex - mx * hez);
+            sB[2 * Vm + v] = -kap * (mx * hey - my * hex);
         }
         __syncthreads();
 
@@ -430,25 +434,32 @@ __global__ void __launch_bounds__(kMagThreads) mag_pass_kernel(LaunchSet L, int 
                 hez += h0n;
                 const MagMat mm = I->mm[m];
                 const float mx = sM[v], my = sM[Vm + v], mz = sM[2 * Vm + v];
+                const float Mz = mm.Ms + mz;
                 const float dam = mm.alpha * mm.inv_Ms;
                 const float ax = -(mm.kappa * hex + dam * mx);
                 const float ay = -(mm.kappa * hey + dam * my);
                 const float az = -(mm.kappa * hez + mm.alpha + dam * mz);
-                const float bxv = sB[v], byv = sB[Vm + v], bzd = sB[2 * Vm + v];
-                const float bzv = mm.Ms + bzd;
-                // T = b + (a.b) a - a x b = (1 + |a|^2) M~ ; N(M~) = Ms T / |T|
-                const float ab = ax * bxv + ay * byv + az * bzv;
-                const float Tx = bxv + ab * ax - (ay * bzv - az * byv);
-                const float Ty = byv + ab * ay - (az * bxv - ax * bzv);
-                const float tz = bzd + (ax * bxv + ay * byv + az * bzd) * az - (ax * byv - ay * bxv);
-                const float Tz = mm.Ms * (1.f + az * az) + tz;
-                const float t2 = Tx * Tx + Ty * Ty;
-                const float nT = sqrtf(t2 + Tz * Tz);
-                const float nmx = mm.Ms * Tx / nT, nmy = mm.Ms * Ty / nT;
-                const float nmz = Tz > 0.f ? -mm.Ms * t2 / (nT * (Tz + nT)) : mm.Ms * Tz / nT - mm.Ms;
-                dl[q][0] = nmx - mx;
-                dl[q][1] = nmy - my;
-                dl[q][2] = nmz - mz;
+                // Eq. llg_tra4 written for the increment d = M~ - M^n, which solves
+                // d + a x d = r with r = b - M^n - a x M^n = -kappa M^n x (H_eff^n + H_eff^{r-1})
+                // (the damping part of a is parallel to M^n); every term is small,
+                // so d keeps full FP32 relative precision however large M^n is.
+                const float rx = sB[v] - mm.kappa * (my * hez - Mz * hey);
+                const float ry = sB[Vm + v] - mm.kappa * (Mz * hex - mx * hez);
+                const float rz = sB[2 * Vm + v] - mm.kappa * (mx * hey - my * hex);
+                const float ar = ax * rx + ay * ry + az * rz;
+                const float inv1 = 1.f / (1.f + ax * ax + ay * ay + az * az);
+                const float ddx = (rx + ar * ax - (ay * rz - az * ry)) * inv1;
+                const float ddy = (ry + ar * ay - (az * rx - ax * rz)) * inv1;
+                const float ddz = (rz + ar * az - (ax * ry - ay * rx)) * inv1;
+                // N(M~) = |M^n| M~ / |M~|; the change is d + s1 M~ with
+                // s1 = |M^n|/|M~| - 1 = -(2 M^n.d + |d|^2) / (|M~| (|M^n| + |M~|))
+                const float nM2 = mx * mx + my * my + Mz * Mz;
+                const float md2 = 2.f * (mx * ddx + my * ddy + Mz * ddz) + (ddx * ddx + ddy * ddy + ddz * ddz);
+                const float nM = sqrtf(nM2), nMt = sqrtf(nM2 + md2);
+                const float s1 = -md2 / (nMt * (nM + nMt));
+                dl[q][0] = ddx + s1 * (mx + ddx);
+                dl[q][1] = ddy + s1 * (my + ddy);
+                dl[q][2] = ddz + s1 * (Mz + ddz);
                 from_frame(R, dl[q][0], dl[q][1], dl[q][2], dn[q][0], dn[q][1], dn[q][2]);
                 const float e0 = dn[q][0] - d0, e1 = dn[q][1] - d1, e2 = dn[q][2] - d2;
                 res = fmaxf(res, sqrtf(e0 * e0 + e1 * e1 + e2 * e2) * mm.inv_Ms);
