@@ -33,7 +33,8 @@
  *       M^{r}-M^{r-1} divided by Ms, maximum over every magnetic cell.
  *   R6  Source J(t) = J0 exp(-(t-tpk)^2/(2 Tp^2)) cos(2 pi f0 t) on one edge.
  *   R7  Energy W = sum_edges eps E^2/2 dV + sum_faces mu0 H^2/2 dV
- *                + sum_cells mu0 (|H0| Ms - H0.M) dV.
+ *                + sum_cells mu0 (|H0| Ms - H0.M) dV, the last term evaluated
+ *       as mu0 |H0|/(2 Ms) |M - Ms h|^2 (equal on |M| = Ms).
  *
  * Array layout: C order with i fastest.  Full staggered sizes:
  *   Ex nx*(ny+1)*(nz+1)  Ey (nx+1)*ny*(nz+1)  Ez (nx+1)*(ny+1)*nz
@@ -474,14 +475,22 @@ static double energy_ws(const orc_problem *p, const orc_state *s, const orc_ws *
     for (int64_t f = 0; f < nHx(p); ++f) Wh += 0.5 * ORC_MU0 * s->Hx[f] * s->Hx[f];
     for (int64_t f = 0; f < nHy(p); ++f) Wh += 0.5 * ORC_MU0 * s->Hy[f] * s->Hy[f];
     for (int64_t f = 0; f < nHz(p); ++f) Wh += 0.5 * ORC_MU0 * s->Hz[f] * s->Hz[f];
+    /* mu0 (|H0| Ms - H0.M) equals mu0 |H0| / (2 Ms) |M - Ms h|^2 when |M| = Ms
+     * (h = H0/|H0|); the second form is evaluated because the first cancels
+     * to rounding noise (and can turn negative) for small precession angles. */
     const int64_t nc = nC(p);
     const double h0 = sqrt(dot3(p->hbias, p->hbias));
-    for (int64_t q = 0; q < w->nm; ++q) {
-        int64_t cc = w->mcell[q];
-        double Ms = cell_Ms(p, cc);
-        double HM = p->hbias[0] * s->M[cc] + p->hbias[1] * s->M[nc + cc] + p->hbias[2] * s->M[2 * nc + cc];
-        Wz += ORC_MU0 * (h0 * Ms - HM);
-    }
+    if (h0 > 0.0)
+        for (int64_t q = 0; q < w->nm; ++q) {
+            int64_t cc = w->mcell[q];
+            double Ms = cell_Ms(p, cc);
+            double d2 = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                double dv = s->M[d * nc + cc] - Ms * p->hbias[d] / h0;
+                d2 += dv * dv;
+            }
+            Wz += ORC_MU0 * h0 / (2.0 * Ms) * d2;
+        }
     return (We + Wh + Wz) * p->dx * p->dy * p->dz;
 }
 
