@@ -203,6 +203,30 @@ int fdtd_llg_set_profiling(fdtd_llg_t h, int32_t on);
  * record afterwards. */
 int fdtd_llg_read_profile(fdtd_llg_t h, fdtd_llg_profile *out, int32_t reset);
 
+/* E push that allocates nothing.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory (code running
+ * inside another framework's memory pool, a real-time loop that forbids
+ * allocation, a host that hands the library a fixed set of buffers).  It does
+ * one Ampere update E = ca E + cb curl H of a uniform medium (eps_r, sigma)
+ * with PEC walls on caller-owned device arrays in the compact layout
+ * (nx*ny*nz floats each, pitch nx; wall edges stay zero) and, when w_e is not
+ * NULL, writes the FP64 electric energy (eps0 eps_r / 2) sum E^2 dx dy dz of
+ * the result to the device double *w_e.  Work is queued on `stream`
+ * (cudaStream_t, NULL = default stream) of the current device.
+ * Its per-block partial sums live in a fixed device array of 65536 doubles
+ * (512 KB) that every GPU which loads the library holds until the process
+ * exits; grids needing more than 65536 blocks of 32x8x16 cells are rejected
+ * with FDTD_E_INVAL.  The first call on a device looks up that array's device
+ * address (with that device current); make that first call before any stream
+ * capture.  Every call shares the array and overwrites the slots it reads, so
+ * calls that overlap on the GPU (other streams, other threads) race.  No
+ * cudaMalloc, cudaFree or allocating library routine is called.  Errors:
+ * FDTD_E_INVAL, FDTD_E_UNSTABLE (dt above the Courant limit), FDTD_E_CUDA;
+ * message in fdtd_llg_last_error(NULL). */
+int fdtd_llg_e_push_noalloc(float *Ex, float *Ey, float *Ez, const float *Hx, const float *Hy, const float *Hz,
+                            int32_t nx, int32_t ny, int32_t nz, double dx, double dy, double dz, double dt,
+                            double eps_r, double sigma, double *w_e, void *stream);
+
 /* Release everything.  NULL is accepted.  Members of a batch are released
  * with the batch. */
 void fdtd_llg_destroy(fdtd_llg_t h);

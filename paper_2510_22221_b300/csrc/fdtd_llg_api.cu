@@ -198,6 +198,12 @@ void bias_frame(const double u[3], double E[9])
 
 }  // namespace
 
+namespace fl {
+// Records a message for fdtd_llg_last_error(NULL) (used by entry points that
+// have no handle).
+void set_last_error(const char *msg) { g_last_error = msg; }
+}  // namespace fl
+
 // ------------------------------------------------------------------ ABI
 extern "C" int fdtd_llg_abi_version(void) { return FDTD_LLG_ABI_VERSION; }
 

@@ -98,4 +98,7 @@ cudaError_t launch_mag_pass(const LaunchSet &L, int mode, cudaStream_t s);
 int e_pass_blocks_per_sm(bool cls16);
 int h_pass_blocks_per_sm(bool cls16);
 
+// fdtd_llg_last_error(NULL) message for entry points without a handle.
+void set_last_error(const char *msg);
+
 }  // namespace fl
