@@ -29,7 +29,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Yee+LLG Mcell-updates/s, % of HBM roofline; adjoint/forward time ratio"
 UNIT = "Mcell-updates/s"
 ALG_BYTES_PER_CELL_STEP = 49          # FP32 E and H read + written once, 1 B material class
-PASS_BYTES_PER_CELL = {"e_pass": 37, "h_pass": 37}   # read E,H (24) + write one field (12) + class (1)
+PASS_BYTES_PER_CELL = {"step": 49}    # the fused field sweep moves the whole step's bytes
 
 
 def peaks():
@@ -215,8 +215,8 @@ def main():
     prof = sim.read_profile(reset=True)
     sim.set_profiling(False)
     hbm, peak_kind = peaks()
-    passes = {k: prof[k] for k in ("e_pass", "mag_pass", "h_pass")}
-    dom = max(("e_pass", "h_pass"), key=lambda k: passes[k]["ms"])
+    passes = {k: prof[k] for k in ("step", "mag")}
+    dom = "step"
     avg_ms = passes[dom]["ms"] / max(passes[dom]["launches"], 1)
     alg = PASS_BYTES_PER_CELL[dom] * w.cells
     achieved = alg / (avg_ms * 1e-3) / 1e9
@@ -235,7 +235,7 @@ def main():
                        "l2": "field state 201 MB > 126 MB L2: inputs larger than L2, no flush",
                        "parallelism": "one independent grid per GPU" if world > 1 else "single GPU"},
             "hbm_roofline_pct": round(100 * value * 1e6 * ALG_BYTES_PER_CELL_STEP / (world * hbm * 1e9), 2),
-            "roofline": roofline, "gpu_launches": 3 * K, "clocks": clk,
+            "roofline": roofline, "gpu_launches": (2 if passes["mag"]["launches"] else 1) * K, "clocks": clk,
             "adjoint_forward_ratio": None}
 
     # end to end through the public API: materials from pinned host memory,

@@ -187,14 +187,15 @@ int fdtd_llg_set_field(fdtd_llg_t h, int32_t which, const float *in, size_t coun
 int fdtd_llg_save_state(fdtd_llg_t h, void *buf, size_t *size);
 int fdtd_llg_load_state(fdtd_llg_t h, const void *buf, size_t size);
 
-/* Per-pass device time, measured with CUDA events that the library records
- * on its stream around every launch while profiling is on (the kernels
- * themselves are unchanged).  Pass kinds: E push, magnetic-region push (LLG),
- * H push. */
+/* Per-kernel device time, measured with CUDA events that the library records
+ * around every launch while profiling is on (the kernels themselves are
+ * unchanged).  Kinds: [0] the field sweep of a step (E push and H
+ * half-push pair of every non-magnetic face), [1] the magnetic-region kernel
+ * (runs concurrently with [0] on a second stream), [2] unused. */
 typedef struct {
-    int64_t launches[3];       /* E, magnet, H                                  */
+    int64_t launches[3];
     double ms[3];              /* summed device time of those launches (ms)     */
-    int64_t cells;             /* cells advanced per launch of the E and H passes */
+    int64_t cells;             /* cells advanced per launch of the field sweep  */
 } fdtd_llg_profile;
 
 int fdtd_llg_set_profiling(fdtd_llg_t h, int32_t on);

@@ -23,7 +23,7 @@ struct Instance {
     double dx = 0, dy = 0, dz = 0;
     bool materials_set = false;
     // device buffers (owned through Sim's allocator)
-    float *fields = nullptr;          // 6 arrays of nz*ny*px
+    float *fields[2] = {nullptr, nullptr};   // two buffers of 6 arrays of nz*ny*px
     float *walls = nullptr;           // wHx, wHy, wHz
     void *cls = nullptr;
     int cls_bytes = 1;
@@ -33,6 +33,7 @@ struct Instance {
     int probe_alloc = -1;             // probes the probe ring was sized for
     double *energy_buf = nullptr;
     float *mbuf = nullptr;            // all regions' deviation m (bias frame)
+    float *fcurl = nullptr;           // all regions' face-curl scratch
     uint8_t *magmat = nullptr;        // all regions' material maps
     // host descriptions
     std::vector<std::array<int, 4>> src;
@@ -55,13 +56,17 @@ struct Sim {
     fdtd_llg_config cfg{};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t s_mag = nullptr;     // magnetic regions run here, concurrently with the field sweep
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    int cur = 0;                      // field buffer holding the present state
     // device control and descriptors
     Inst *d_insts = nullptr;
     int *d_tile_inst = nullptr;
+    int *d_ftile_inst = nullptr;
     MagComp *d_comps = nullptr;
     StepCtl *d_ctl = nullptr;
     double *d_part = nullptr;         // part_e | part_h | part_m
-    int ntiles = 0, ncomp = 0, vmax = 0;
+    int ntiles = 0, nftiles = 0, ncomp = 0, vmax = 0;
     bool cls16 = false;
     bool dirty = true;
     int nsm = 148;
@@ -110,6 +115,9 @@ struct Sim {
             else cudaFree(p);
         }
         allocs.clear();
+        if (s_mag) cudaStreamDestroy(s_mag);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -250,6 +258,12 @@ static int create_impl(const fdtd_llg_config *cfgs, int32_t n, fdtd_llg_t *out)
         }
         S->own_stream = true;
     }
+    if (cudaStreamCreateWithFlags(&S->s_mag, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&S->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&S->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        delete S;
+        return fail(nullptr, FDTD_E_CUDA, "stream or event creation failed");
+    }
     S->inst.resize(n);
     fdtd_llg_t root = new fdtd_llg_s{S, n == 1 ? 0 : -1, true};
     for (int i = 0; i < n; ++i) {
@@ -257,14 +271,16 @@ static int create_impl(const fdtd_llg_config *cfgs, int32_t n, fdtd_llg_t *out)
         I.nx = cfgs[i].nx; I.ny = cfgs[i].ny; I.nz = cfgs[i].nz;
         I.px = (I.nx + 31) / 32 * 32;
         I.dx = cfgs[i].dx; I.dy = cfgs[i].dy; I.dz = cfgs[i].dz;
-        I.fields = (float *)S->dalloc(6 * I.n_field() * sizeof(float));
+        I.fields[0] = (float *)S->dalloc(6 * I.n_field() * sizeof(float));
+        I.fields[1] = (float *)S->dalloc(6 * I.n_field() * sizeof(float));
         I.walls = (float *)S->dalloc(I.n_wall() * sizeof(float));
         I.energy_buf = (double *)S->dalloc((size_t)S->cfg.probe_capacity * sizeof(double));
-        if (!I.fields || !I.walls || !I.energy_buf) {
+        if (!I.fields[0] || !I.fields[1] || !I.walls || !I.energy_buf) {
             fdtd_llg_destroy(root);
             return fail(nullptr, FDTD_E_OOM, "device allocation failed");
         }
-        cudaMemsetAsync(I.fields, 0, 6 * I.n_field() * sizeof(float), S->stream);
+        cudaMemsetAsync(I.fields[0], 0, 6 * I.n_field() * sizeof(float), S->stream);
+        cudaMemsetAsync(I.fields[1], 0, 6 * I.n_field() * sizeof(float), S->stream);
         cudaMemsetAsync(I.walls, 0, I.n_wall() * sizeof(float), S->stream);
         cudaMemsetAsync(I.energy_buf, 0, (size_t)S->cfg.probe_capacity * sizeof(double), S->stream);
         S->members.push_back(n == 1 ? root : new fdtd_llg_s{S, i, false});
@@ -493,15 +509,21 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
     std::vector<uint8_t> hmat(totV);
     // release the previous materials of this instance
     CKR(h, cudaStreamSynchronize(S->stream));
-    S->dfree(I.cls); S->dfree(I.ctab); S->dfree(I.mbuf); S->dfree(I.magmat);
-    I.cls = nullptr; I.ctab = nullptr; I.mbuf = nullptr; I.magmat = nullptr;
+    S->dfree(I.cls); S->dfree(I.ctab); S->dfree(I.mbuf); S->dfree(I.magmat); S->dfree(I.fcurl);
+    I.cls = nullptr; I.ctab = nullptr; I.mbuf = nullptr; I.magmat = nullptr; I.fcurl = nullptr;
+    size_t totF = 0;
+    for (auto &b : boxes) {
+        const size_t bx = b.x1 - b.x0 + 1, by = b.y1 - b.y0 + 1, bz = b.z1 - b.z0 + 1;
+        totF += (bx + 1) * by * bz + bx * (by + 1) * bz + bx * by * (bz + 1);
+    }
+    I.fcurl = (float *)S->dalloc(totF * sizeof(float));
     I.mbuf = (float *)S->dalloc(3 * totV * sizeof(float));
     I.magmat = (uint8_t *)S->dalloc(totV);
     I.cls = S->dalloc((size_t)I.nz * I.ny * I.px * (c16 ? 2 : 1));
     I.ctab = (float4 *)S->dalloc((size_t)3 * nclass * sizeof(float4));
-    if (!I.mbuf || !I.magmat || !I.cls || !I.ctab) return fail(h, FDTD_E_OOM, "device allocation failed");
+    if (!I.mbuf || !I.magmat || !I.cls || !I.ctab || !I.fcurl) return fail(h, FDTD_E_OOM, "device allocation failed");
     I.comps.clear();
-    size_t off = 0;
+    size_t off = 0, foff = 0;
     for (size_t L = 0; L < boxes.size(); ++L) {
         const Box &b = boxes[L];
         MagComp C{};
@@ -517,8 +539,10 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
                 }
         C.m = I.mbuf + 3 * off;
         C.mat = I.magmat + off;
+        C.fcurl = I.fcurl + foff;
         I.comps.push_back(C);
         off += C.V;
+        foff += (size_t)(C.bx + 1) * C.by * C.bz + (size_t)C.bx * (C.by + 1) * C.bz + (size_t)C.bx * C.by * (C.bz + 1);
     }
     // bias frame: M starts at Ms h, i.e. m = 0
     const double h0n = std::sqrt(hbias[0] * hbias[0] + hbias[1] * hbias[1] + hbias[2] * hbias[2]);
@@ -554,7 +578,8 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
             CKR(h, cudaMemset(I.mbuf, 0, 3 * totV * sizeof(float)));
             CKR(h, cudaMemcpy(I.magmat, hmat.data(), hmat.size(), cudaMemcpyHostToDevice));
         }
-        CKR(h, cudaMemset(I.fields, 0, 6 * I.n_field() * sizeof(float)));
+        CKR(h, cudaMemset(I.fields[0], 0, 6 * I.n_field() * sizeof(float)));
+        CKR(h, cudaMemset(I.fields[1], 0, 6 * I.n_field() * sizeof(float)));
         CKR(h, cudaMemset(I.walls, 0, I.n_wall() * sizeof(float)));
     }
     I.cls_bytes = c16 ? 2 : 1;
@@ -568,6 +593,7 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
     // a batch's step count restarts with any instance's materials
     S->host_step = 0;
     S->half_ahead = false;
+    S->cur = 0;
     CKR(h, cudaMemset(S->d_ctl, 0, sizeof(StepCtl)));
     S->dirty = true;
     return FDTD_OK;
@@ -610,7 +636,7 @@ static int upload_descriptors(fdtd_llg_t h)
     if (!S->dirty) return FDTD_OK;
     CKR(h, cudaStreamSynchronize(S->stream));
     std::vector<Inst> hi(S->inst.size());
-    std::vector<int> tile_inst;
+    std::vector<int> tile_inst, ftile_inst;
     std::vector<MagComp> comps;
     bool c16 = false;
     int vmax = 0;
@@ -628,8 +654,8 @@ static int upload_descriptors(fdtd_llg_t h)
         Inst &d = hi[ii];
         std::memset(&d, 0, sizeof d);
         const size_t nf = I.n_field();
-        d.Ex = I.fields; d.Ey = I.fields + nf; d.Ez = I.fields + 2 * nf;
-        d.Hx = I.fields + 3 * nf; d.Hy = I.fields + 4 * nf; d.Hz = I.fields + 5 * nf;
+        for (int b = 0; b < 2; ++b)
+            for (int c = 0; c < 6; ++c) d.F[b][c] = I.fields[b] + c * nf;
         d.wHx = I.walls; d.wHy = I.walls + (size_t)I.ny * I.nz; d.wHz = d.wHy + (size_t)I.nx * I.nz;
         d.cls = I.cls; d.ctab = I.ctab;
         d.probe_buf = I.probe_buf; d.energy_buf = I.energy_buf;
@@ -653,6 +679,11 @@ static int upload_descriptors(fdtd_llg_t h)
         d.tile_off = (int)tile_inst.size();
         const int nt = d.ntx * d.nty * d.ntz;
         for (int t = 0; t < nt; ++t) tile_inst.push_back((int)ii);
+        d.fkc = std::min(I.nz, kFusedPlanes);
+        d.fntx = (I.nx + kFX - 1) / kFX; d.fnty = (I.ny + kFY - 1) / kFY; d.fntz = (I.nz + d.fkc - 1) / d.fkc;
+        d.ftile_off = (int)ftile_inst.size();
+        const int nft = d.fntx * d.fnty * d.fntz;
+        for (int t = 0; t < nft; ++t) ftile_inst.push_back((int)ii);
         d.mag_off = (int)comps.size();
         d.nmag = (int)I.comps.size();
         for (auto C : I.comps) {
@@ -679,17 +710,21 @@ static int upload_descriptors(fdtd_llg_t h)
             I.cls_bytes = 2;
             hi[ii].cls = w;
         }
-    S->dfree(S->d_insts); S->dfree(S->d_tile_inst); S->dfree(S->d_comps); S->dfree(S->d_part);
+    S->dfree(S->d_insts); S->dfree(S->d_tile_inst); S->dfree(S->d_ftile_inst); S->dfree(S->d_comps); S->dfree(S->d_part);
     S->d_insts = (Inst *)S->dalloc(hi.size() * sizeof(Inst));
     S->d_tile_inst = (int *)S->dalloc(tile_inst.size() * sizeof(int));
+    S->d_ftile_inst = (int *)S->dalloc(ftile_inst.size() * sizeof(int));
     S->d_comps = (MagComp *)S->dalloc(std::max<size_t>(1, comps.size()) * sizeof(MagComp));
-    S->d_part = (double *)S->dalloc((2 * tile_inst.size() + comps.size() + 1) * sizeof(double));
-    if (!S->d_insts || !S->d_tile_inst || !S->d_comps || !S->d_part) return fail(h, FDTD_E_OOM, "device allocation failed");
+    S->d_part = (double *)S->dalloc((ftile_inst.size() + comps.size() + 1) * sizeof(double));
+    if (!S->d_insts || !S->d_tile_inst || !S->d_ftile_inst || !S->d_comps || !S->d_part)
+        return fail(h, FDTD_E_OOM, "device allocation failed");
     CKR(h, cudaMemcpy(S->d_insts, hi.data(), hi.size() * sizeof(Inst), cudaMemcpyHostToDevice));
     CKR(h, cudaMemcpy(S->d_tile_inst, tile_inst.data(), tile_inst.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CKR(h, cudaMemcpy(S->d_ftile_inst, ftile_inst.data(), ftile_inst.size() * sizeof(int), cudaMemcpyHostToDevice));
     if (!comps.empty()) CKR(h, cudaMemcpy(S->d_comps, comps.data(), comps.size() * sizeof(MagComp), cudaMemcpyHostToDevice));
-    CKR(h, cudaMemset(S->d_part, 0, (2 * tile_inst.size() + comps.size() + 1) * sizeof(double)));
+    CKR(h, cudaMemset(S->d_part, 0, (ftile_inst.size() + comps.size() + 1) * sizeof(double)));
     S->ntiles = (int)tile_inst.size();
+    S->nftiles = (int)ftile_inst.size();
     S->ncomp = (int)comps.size();
     S->vmax = vmax;
     S->cls16 = c16;
@@ -708,12 +743,14 @@ static LaunchSet launch_set(Sim *S)
     L.ncomp = S->ncomp;
     L.vmax = S->vmax;
     L.ctl = S->d_ctl;
-    L.part_e = S->d_part;
-    L.part_h = S->d_part + S->ntiles;
-    L.part_m = S->d_part + 2 * S->ntiles;
+    L.part_f = S->d_part;
+    L.part_m = S->d_part + S->nftiles;
+    L.ftile_inst = S->d_ftile_inst;
+    L.nftiles = S->nftiles;
+    L.src = S->cur;
+    L.dst = 1 - S->cur;
     L.cls16 = S->cls16;
-    L.grid_e = std::min(S->ntiles, S->nsm * e_pass_blocks_per_sm(S->cls16));
-    L.grid_h = std::min(S->ntiles, S->nsm * h_pass_blocks_per_sm(S->cls16));
+    L.grid_h = std::min(S->ntiles, S->nsm * h_half_blocks_per_sm(S->cls16));
     L.llg_tol = (float)S->cfg.llg_tol;
     L.llg_max_iter = S->cfg.llg_max_iter;
     L.llg_fixed_iter = S->cfg.llg_fixed_iter;
@@ -729,25 +766,28 @@ extern "C" int fdtd_llg_step(fdtd_llg_t h, int64_t nsteps)
     Sim *S = h->sim;
     int rc = upload_descriptors(h);
     if (rc) return rc;
-    const LaunchSet L = launch_set(S);
-    auto timed = [&](int kind, auto &&fn) -> cudaError_t {
-        if (!S->profiling || (kind == 1 && L.ncomp == 0)) return fn();
-        Sim::Rec r{kind, S->take_event(), S->take_event()};
-        cudaEventRecord(r.a, S->stream);
-        cudaError_t e = fn();
-        cudaEventRecord(r.b, S->stream);
-        S->recs.push_back(r);
-        return e;
-    };
+    LaunchSet L = launch_set(S);
     if (!S->half_ahead && nsteps > 0) {
-        CKR(h, launch_mag_pass(L, 0, S->stream));
-        CKR(h, launch_h_pass(L, 0, S->stream));
+        L.src = L.dst = S->cur;
+        CKR(h, launch_half(L, S->stream));
         S->half_ahead = true;
     }
     for (int64_t s = 0; s < nsteps; ++s) {
-        CKR(h, timed(0, [&] { return launch_e_pass(L, S->stream); }));
-        CKR(h, timed(1, [&] { return launch_mag_pass(L, 1, S->stream); }));
-        CKR(h, timed(2, [&] { return launch_h_pass(L, 1, S->stream); }));
+        L.src = S->cur;
+        L.dst = 1 - S->cur;
+        cudaEvent_t ev[4];
+        cudaEvent_t *prof = nullptr;
+        if (S->profiling) {
+            for (auto &e : ev) e = S->take_event();
+            prof = ev;
+        }
+        CKR(h, launch_step(L, S->stream, S->s_mag, S->ev_fork, S->ev_join, prof));
+        if (prof) {
+            S->recs.push_back({0, ev[0], ev[1]});
+            if (L.ncomp) S->recs.push_back({1, ev[2], ev[3]});
+            else { S->ev_pool.push_back(ev[2]); S->ev_pool.push_back(ev[3]); }
+        }
+        S->cur ^= 1;
     }
     S->host_step += nsteps;
     return FDTD_OK;
@@ -880,7 +920,7 @@ extern "C" int fdtd_llg_get_field(fdtd_llg_t h, int32_t which, float *out, size_
     if (rc) return rc;
     const size_t nf = I->n_field();
     if (which <= FDTD_F_HZ) {
-        CKR(h, cudaMemcpy2D(out, I->nx * sizeof(float), I->fields + which * nf, I->px * sizeof(float), I->nx * sizeof(float),
+        CKR(h, cudaMemcpy2D(out, I->nx * sizeof(float), I->fields[h->sim->cur] + which * nf, I->px * sizeof(float), I->nx * sizeof(float),
                             (size_t)I->ny * I->nz, cudaMemcpyDeviceToHost));
     } else if (which <= FDTD_F_MZ || which >= FDTD_F_DMX) {
         const bool dev = which >= FDTD_F_DMX;
@@ -918,7 +958,7 @@ extern "C" int fdtd_llg_set_field(fdtd_llg_t h, int32_t which, const float *in, 
     CKR(h, cudaStreamSynchronize(h->sim->stream));
     const size_t nf = I->n_field();
     if (which <= FDTD_F_HZ) {
-        CKR(h, cudaMemcpy2D(I->fields + which * nf, I->px * sizeof(float), in, I->nx * sizeof(float), I->nx * sizeof(float),
+        CKR(h, cudaMemcpy2D(I->fields[h->sim->cur] + which * nf, I->px * sizeof(float), in, I->nx * sizeof(float), I->nx * sizeof(float),
                             (size_t)I->ny * I->nz, cudaMemcpyHostToDevice));
     } else if (which <= FDTD_F_MZ || which >= FDTD_F_DMX) {
         const bool dev = which >= FDTD_F_DMX;
@@ -989,7 +1029,7 @@ extern "C" int fdtd_llg_save_state(fdtd_llg_t h, void *buf, size_t *size)
     const size_t nf = I->n_field();
     const size_t ncell = (size_t)I->nx * I->ny * I->nz;
     for (int f = 0; f < 6; ++f) {
-        CKR(h, cudaMemcpy2D(p, I->nx * sizeof(float), I->fields + f * nf, I->px * sizeof(float), I->nx * sizeof(float),
+        CKR(h, cudaMemcpy2D(p, I->nx * sizeof(float), I->fields[h->sim->cur] + f * nf, I->px * sizeof(float), I->nx * sizeof(float),
                             (size_t)I->ny * I->nz, cudaMemcpyDeviceToHost));
         p += ncell * sizeof(float);
     }
@@ -1019,7 +1059,7 @@ extern "C" int fdtd_llg_load_state(fdtd_llg_t h, const void *buf, size_t size)
     const size_t nf = I->n_field();
     const size_t ncell = (size_t)I->nx * I->ny * I->nz;
     for (int f = 0; f < 6; ++f) {
-        CKR(h, cudaMemcpy2D(I->fields + f * nf, I->px * sizeof(float), p, I->nx * sizeof(float), I->nx * sizeof(float),
+        CKR(h, cudaMemcpy2D(I->fields[h->sim->cur] + f * nf, I->px * sizeof(float), p, I->nx * sizeof(float), I->nx * sizeof(float),
                             (size_t)I->ny * I->nz, cudaMemcpyHostToDevice));
         p += ncell * sizeof(float);
     }

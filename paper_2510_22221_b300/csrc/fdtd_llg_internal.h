@@ -15,9 +15,21 @@ constexpr int kMaxSrc = 4;
 constexpr int kMaxProbe = 32;
 constexpr int kMaxMagMat = 16;
 
-// Tile of the two-pass E and H kernels: 32 (x, one warp) x 8 (y) columns,
+// Tile of the start-up H half-push kernel: 32 (x, one warp) x 8 (y) columns,
 // each thread marching kKC planes in z.
 constexpr int kTX = 32, kTY = 8, kKC = 16;
+
+// Tile of the fused step kernel: kFX x kFY columns marching kFC(runtime)
+// planes in z, kFT threads; shared-memory planes of H with a one-cell halo on
+// the low x and y sides plus the high extension, and of E^{n+1} on the tile
+// extended by one cell on the high x and y sides.
+constexpr int kFX = 64, kFY = 16, kFT = 256;
+constexpr int kHX = kFX + 2, kHY = kFY + 2, kHN = kHX * kHY;
+constexpr int kEX = kFX + 1, kEY = kFY + 1, kEN = kEX * kEY;
+constexpr int kHQ = (kHN + kFT - 1) / kFT;
+constexpr int kEQ = (kEN + kFT - 1) / kFT;
+constexpr int kIQ = kFX * kFY / kFT;
+constexpr int kFusedPlanes = 16;   // z planes per fused-step tile
 
 // Magnet kernel: one CTA per face-connected magnetic region, whose bounding
 // box holds at most kMagMaxV cells, kMagCPT cells per thread.
@@ -34,7 +46,7 @@ struct MagMat {
 
 // Everything a kernel needs about one grid instance.
 struct Inst {
-    float *Ex, *Ey, *Ez, *Hx, *Hy, *Hz;   // [nz][ny][px], x fastest
+    float *F[2][6];                       // two buffers of Ex, Ey, Ez, Hx, Hy, Hz: [nz][ny][px]
     float *wHx, *wHy, *wHz;               // far-wall normal H: [nz][ny], [nz][nx], [ny][nx]
     const void *cls;                      // class id per cell: uint8 or uint16
     const float4 *ctab;                   // 3 float4 per class: (ca, flags) (cb) (eps/2)
@@ -53,7 +65,8 @@ struct Inst {
     int src[kMaxSrc][4];                  // comp, i, j, k
     double srcp[kMaxSrc][4];              // J0, f0, Tp, tpk
     int probe[kMaxProbe][3];
-    int tile_off, ntx, nty, ntz;          // tiles of this instance in the tile list
+    int tile_off, ntx, nty, ntz;          // half-push tiles of this instance in the tile list
+    int ftile_off, fntx, fnty, fntz, fkc; // fused-step tiles (kFX x kFY x fkc)
     int mag_off, nmag;                    // magnet regions of this instance
     MagMat mm[kMaxMagMat];
 };
@@ -63,6 +76,7 @@ struct MagComp {
     int x0, y0, z0, bx, by, bz, V;
     float *m;               // deviation M - Ms h in the bias frame: 3 blocks of V
     const uint8_t *mat;     // V: magnet material index, 0xFF outside this region
+    float *fcurl;           // scratch: curl E at the region's faces (x, y, z face blocks)
 };
 
 // Device-resident control block of a batch.
@@ -82,21 +96,26 @@ struct LaunchSet {
     int ncomp;
     int vmax;
     StepCtl *ctl;
-    double *part_e, *part_h, *part_m;   // energy partials per tile / per region
-    int grid_e, grid_h;
+    double *part_f, *part_m;            // energy partials per fused tile / per region
+    const int *ftile_inst;
+    int nftiles;
+    int src, dst;                       // field buffers read / written by a step
+    int grid_h;
     bool cls16;
     float llg_tol;
     int llg_max_iter, llg_fixed_iter;
     int energy;
 };
 
-// Launchers (kernels_fwd.cu).  mode 0: a single H/M half-push (start-up);
-// mode 1: full step.
-cudaError_t launch_e_pass(const LaunchSet &L, cudaStream_t s);
-cudaError_t launch_h_pass(const LaunchSet &L, int mode, cudaStream_t s);
-cudaError_t launch_mag_pass(const LaunchSet &L, int mode, cudaStream_t s);
-int e_pass_blocks_per_sm(bool cls16);
-int h_pass_blocks_per_sm(bool cls16);
+// Launchers (kernels_fwd.cu).  launch_half: the start-up H/M half-push that
+// moves H, M from integer time to half a step ahead, in place on buffer src.
+// launch_step: one full step reading buffer src and writing buffer dst, the
+// field kernel on s and the magnetic regions concurrently on s_mag (events
+// ev_fork / ev_join order them with the surrounding work on s).
+cudaError_t launch_half(const LaunchSet &L, cudaStream_t s);
+cudaError_t launch_step(const LaunchSet &L, cudaStream_t s, cudaStream_t s_mag, cudaEvent_t ev_fork,
+                        cudaEvent_t ev_join, cudaEvent_t *prof);
+int h_half_blocks_per_sm(bool cls16);
 
 // fdtd_llg_last_error(NULL) message for entry points without a handle.
 void set_last_error(const char *msg);

@@ -232,7 +232,7 @@ class FdtdLlg:
     def read_profile(self, reset: bool = True) -> dict:
         pr = _abi.Profile()
         check(_abi.load().fdtd_llg_read_profile(self._h, C.byref(pr), 1 if reset else 0), self._h)
-        kinds = ("e_pass", "mag_pass", "h_pass")
+        kinds = ("step", "mag", "half")
         return {"cells": pr.cells, **{k: {"launches": pr.launches[q], "ms": pr.ms[q]} for q, k in enumerate(kinds)}}
 
     # ----------------------------------------------------------- cleanup
