@@ -656,6 +656,7 @@ static int upload_descriptors(fdtd_llg_t h)
         const size_t nf = I.n_field();
         for (int b = 0; b < 2; ++b)
             for (int c = 0; c < 6; ++c) d.F[b][c] = I.fields[b] + c * nf;
+        d.fstride = (long long)nf;
         d.wHx = I.walls; d.wHy = I.walls + (size_t)I.ny * I.nz; d.wHz = d.wHy + (size_t)I.nx * I.nz;
         d.cls = I.cls; d.ctab = I.ctab;
         d.probe_buf = I.probe_buf; d.energy_buf = I.energy_buf;

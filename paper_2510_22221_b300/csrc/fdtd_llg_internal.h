@@ -47,6 +47,7 @@ struct MagMat {
 // Everything a kernel needs about one grid instance.
 struct Inst {
     float *F[2][6];                       // two buffers of Ex, Ey, Ez, Hx, Hy, Hz: [nz][ny][px]
+    long long fstride;                    // F[b][c] = F[b][0] + c * fstride
     float *wHx, *wHy, *wHz;               // far-wall normal H: [nz][ny], [nz][nx], [ny][nx]
     const void *cls;                      // class id per cell: uint8 or uint16
     const float4 *ctab;                   // 3 float4 per class: (ca, flags) (cb) (eps/2)

@@ -478,9 +478,20 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
 }
 
 // ---------------------------------------------------------- fused step
+// 4-byte asynchronous global -> shared copy; src_bytes 0 writes a zero and
+// reads nothing (the source pointer given is still a valid address).
+__device__ __forceinline__ void cp_async4(void *sdst, const void *gsrc, int src_bytes)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gsrc), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 struct FusedSmem {
     float h[3][3][kHN];     // H^{n+1/2} planes k-1, k, k+1 (ring of three), halo tile
     float e[2][3][kEN];     // E^{n+1} planes k-1, k (ring of two), extended tile
+    float en[2][3][kEN];    // E^n planes k, k+1, extended tile
     uint16_t c[3][kEN];     // class ids, planes k-1, k, k+1
 };
 
@@ -502,8 +513,9 @@ __global__ void __launch_bounds__(kFT, 2) step_kernel(LaunchSet L)
     const int i0 = tx * kFX, j0 = ty * kFY, k0 = tz * I->fkc;
     const int k1 = min(k0 + I->fkc, nz);
     const int kend = k1 < nz ? k1 : nz;
-    float *const *Fs = I->F[L.src];
-    float *const *Fd = I->F[L.dst];
+    const float *__restrict__ Fs = I->F[L.src][0];   // component c at Fs + c * fs
+    float *__restrict__ Fd = I->F[L.dst][0];
+    const long long fs = I->fstride;
     const ClsT *__restrict__ cls = static_cast<const ClsT *>(I->cls);
     const float4 *__restrict__ ctab = I->ctab;
     const bool has_mag = I->nmag > 0;
@@ -521,60 +533,58 @@ __global__ void __launch_bounds__(kFT, 2) step_kernel(LaunchSet L)
     }
     const double tn = ((double)n + 0.5) * I->dt;
 
-    float rh[kHQ][3];         // H of the next plane on its way to shared memory
-    int rc[kEQ];              // class ids of the next plane
-    float re[kEQ][3];         // E^n of the plane being advanced
-    float rn[kEQ][3];         // E^n of the next plane
+    int rc[kEQ];              // class ids of the next plane, on their way to shared memory
 
-#define FL_LOAD_H(kk)                                                                                           \
+    // H of plane kk (zero outside the grid) into S.h[b], asynchronously
+#define FL_LOAD_H(kk, b)                                                                                        \
     _Pragma("unroll") for (int q = 0; q < kHQ; ++q) {                                                           \
         const int p = tid + q * kFT;                                                                            \
-        const int hi = i0 - 1 + p % kHX, hj = j0 - 1 + p / kHX;                                                \
-        const bool ok = p < kHN && hi >= 0 && hi < nx && hj >= 0 && hj < ny && (kk) >= 0 && (kk) < nz;       \
-        const long long o = (long long)(kk) * plane + (long long)hj * px + hi;                                 \
-        rh[q][0] = ok ? __ldg(Fs[3] + o) : 0.f;                                                                 \
-        rh[q][1] = ok ? __ldg(Fs[4] + o) : 0.f;                                                                 \
-        rh[q][2] = ok ? __ldg(Fs[5] + o) : 0.f;                                                                 \
+        if (p < kHN) {                                                                                          \
+            const int hi = i0 - 1 + p % kHX, hj = j0 - 1 + p / kHX;                                            \
+            const bool ok = hi >= 0 && hi < nx && hj >= 0 && hj < ny && (kk) >= 0 && (kk) < nz;               \
+            const long long o = ok ? (long long)(kk) * plane + (long long)hj * px + hi : 0;                    \
+            cp_async4(&S.h[b][0][p], Fs + 3 * fs + o, ok ? 4 : 0);                                              \
+            cp_async4(&S.h[b][1][p], Fs + 4 * fs + o, ok ? 4 : 0);                                              \
+            cp_async4(&S.h[b][2][p], Fs + 5 * fs + o, ok ? 4 : 0);                                              \
+        }                                                                                                       \
     }
-#define FL_LOAD_E(kk, dst)                                                                                      \
+    // E^n of plane kk into S.en[kk & 1] asynchronously, class ids into rc
+#define FL_LOAD_E(kk)                                                                                           \
     _Pragma("unroll") for (int q = 0; q < kEQ; ++q) {                                                           \
         const int p = tid + q * kFT;                                                                            \
-        const int ei = i0 + p % kEX, ej = j0 + p / kEX;                                                         \
-        const bool ok = p < kEN && ei < nx && ej < ny;                                                          \
-        const long long o = (long long)(kk) * plane + (long long)ej * px + ei;                                 \
-        dst[q][0] = ok ? __ldg(Fs[0] + o) : 0.f;                                                                \
-        dst[q][1] = ok ? __ldg(Fs[1] + o) : 0.f;                                                                \
-        dst[q][2] = ok ? __ldg(Fs[2] + o) : 0.f;                                                                \
-        rc[q] = ok ? (int)cls[o] : 0;                                                                           \
+        rc[q] = 0;                                                                                              \
+        if (p < kEN) {                                                                                          \
+            const int ei = i0 + p % kEX, ej = j0 + p / kEX;                                                     \
+            const bool ok = ei < nx && ej < ny;                                                                 \
+            const long long o = ok ? (long long)(kk) * plane + (long long)ej * px + ei : 0;                    \
+            cp_async4(&S.en[(kk) & 1][0][p], Fs + o, ok ? 4 : 0);                                               \
+            cp_async4(&S.en[(kk) & 1][1][p], Fs + fs + o, ok ? 4 : 0);                                          \
+            cp_async4(&S.en[(kk) & 1][2][p], Fs + 2 * fs + o, ok ? 4 : 0);                                      \
+            if (ok) rc[q] = (int)cls[o];                                                                        \
+        }                                                                                                       \
     }
-#define FL_STORE(b)                                                                                             \
-    _Pragma("unroll") for (int q = 0; q < kHQ; ++q) {                                                           \
-        const int p = tid + q * kFT;                                                                            \
-        if (p < kHN) { S.h[b][0][p] = rh[q][0]; S.h[b][1][p] = rh[q][1]; S.h[b][2][p] = rh[q][2]; }            \
-    }                                                                                                           \
+#define FL_STORE_C(b)                                                                                           \
     _Pragma("unroll") for (int q = 0; q < kEQ; ++q) {                                                           \
         const int p = tid + q * kFT;                                                                            \
         if (p < kEN) S.c[b][p] = (uint16_t)rc[q];                                                               \
     }
 
     // prologue: H of plane k0-1 (zero below the grid) and H, E^n, classes of plane k0
-    FL_LOAD_H(k0 - 1);
-#pragma unroll
-    for (int q = 0; q < kHQ; ++q) {
-        const int p = tid + q * kFT;
-        if (p < kHN) { S.h[(k0 + 2) % 3][0][p] = rh[q][0]; S.h[(k0 + 2) % 3][1][p] = rh[q][1]; S.h[(k0 + 2) % 3][2][p] = rh[q][2]; }
-    }
-    FL_LOAD_H(k0);
-    FL_LOAD_E(k0, re);
-    FL_STORE(k0 % 3);
+    FL_LOAD_H(k0 - 1, (k0 + 2) % 3);
+    FL_LOAD_H(k0, k0 % 3);
+    FL_LOAD_E(k0);
+    cp_async_commit();
+    cp_async_wait_all();
+    FL_STORE_C(k0 % 3);
     __syncthreads();
 
     float acc = 0.f;
     for (int k = k0; k <= kend; ++k) {
         const bool pre = k + 1 <= kend && k + 1 < nz;
         if (pre) {
-            FL_LOAD_H(k + 1);
-            FL_LOAD_E(k + 1, rn);
+            FL_LOAD_H(k + 1, (k + 1) % 3);
+            FL_LOAD_E(k + 1);
+            cp_async_commit();
         }
         const int b = k % 3, bm = (k + 2) % 3, eb = k & 1;
         // ---- E^{n+1} of plane k on the extended tile
@@ -606,14 +616,14 @@ __global__ void __launch_bounds__(kFT, 2) step_kernel(LaunchSet L)
                 const int c = S.c[b][p];
                 const float4 A = __ldg(ctab + 3 * c);
                 const float4 B = __ldg(ctab + 3 * c + 1);
-                ex = A.x * re[q][0] + B.x * cx;
-                ey = A.y * re[q][1] + B.y * cy;
-                ez = A.z * re[q][2] + B.z * cz;
+                ex = A.x * S.en[eb][0][p] + B.x * cx;
+                ey = A.y * S.en[eb][1][p] + B.y * cy;
+                ez = A.z * S.en[eb][2][p] + B.z * cz;
                 if (px_ < kFX && py_ < kFY && k < k1) {
                     const long long o = (long long)k * plane + (long long)j * px + i;
-                    Fd[0][o] = ex;
-                    Fd[1][o] = ey;
-                    Fd[2][o] = ez;
+                    Fd[o] = ex;
+                    Fd[fs + o] = ey;
+                    Fd[2 * fs + o] = ez;
                     if (L.energy) {
                         const float4 Q = __ldg(ctab + 3 * c + 2);
                         acc += Q.x * ex * ex + Q.y * ey * ey + Q.z * ez * ez;
@@ -656,9 +666,9 @@ __global__ void __launch_bounds__(kFT, 2) step_kernel(LaunchSet L)
                 const int hp = (pj + 1) * kHX + pi + 1;
                 const long long o = (long long)kh * plane + (long long)j * px + i;
                 float hmx = 0.f, hmy = 0.f, hmz = 0.f;
-                if (!(fl & CF_MAG_HX)) { hmx = S.h[hb][0][hp] - ch * cx; Fd[3][o] = hmx - ch * cx; }
-                if (!(fl & CF_MAG_HY)) { hmy = S.h[hb][1][hp] - ch * cy; Fd[4][o] = hmy - ch * cy; }
-                if (!(fl & CF_MAG_HZ)) { hmz = S.h[hb][2][hp] - ch * cz; Fd[5][o] = hmz - ch * cz; }
+                if (!(fl & CF_MAG_HX)) { hmx = S.h[hb][0][hp] - ch * cx; Fd[3 * fs + o] = hmx - ch * cx; }
+                if (!(fl & CF_MAG_HY)) { hmy = S.h[hb][1][hp] - ch * cy; Fd[4 * fs + o] = hmy - ch * cy; }
+                if (!(fl & CF_MAG_HZ)) { hmz = S.h[hb][2][hp] - ch * cz; Fd[5 * fs + o] = hmz - ch * cz; }
                 if (L.energy) acc += (float)(0.5 * kMu0) * (hmx * hmx + hmy * hmy + hmz * hmz);
                 if (pmask) {
                     for (int pp = 0; pp < I->nprobe; ++pp)
@@ -672,19 +682,14 @@ __global__ void __launch_bounds__(kFT, 2) step_kernel(LaunchSet L)
             }
         }
         if (pre) {
-            FL_STORE((k + 1) % 3);
-#pragma unroll
-            for (int q = 0; q < kEQ; ++q) {
-                re[q][0] = rn[q][0];
-                re[q][1] = rn[q][1];
-                re[q][2] = rn[q][2];
-            }
+            cp_async_wait_all();
+            FL_STORE_C((k + 1) % 3);
         }
         __syncthreads();
     }
 #undef FL_LOAD_H
 #undef FL_LOAD_E
-#undef FL_STORE
+#undef FL_STORE_C
     if (L.energy) {
         const double s = block_sum((double)acc, sred);
         if (tid == 0) L.part_f[t] = s;
