@@ -3,6 +3,8 @@
 #include "../../include/fdtd_llg.h"
 #include "fdtd_llg_internal.h"
 
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -33,7 +35,7 @@ struct Instance {
     int probe_alloc = -1;             // probes the probe ring was sized for
     double *energy_buf = nullptr;
     float *mbuf = nullptr;            // all regions' deviation m (bias frame)
-    float *fcurl = nullptr;           // all regions' face-curl scratch
+    float *eedge = nullptr;           // all regions' box-edge E scratch
     uint8_t *magmat = nullptr;        // all regions' material maps
     // host descriptions
     std::vector<std::array<int, 4>> src;
@@ -66,7 +68,8 @@ struct Sim {
     MagComp *d_comps = nullptr;
     StepCtl *d_ctl = nullptr;
     double *d_part = nullptr;         // part_e | part_h | part_m
-    int ntiles = 0, nftiles = 0, ncomp = 0, vmax = 0;
+    int ntiles = 0, nftiles = 0, ncomp = 0, vmax = 0, emax = 0, mag_smem = 0;
+    bool stab = false;                // every class table small enough for shared memory
     bool cls16 = false;
     bool dirty = true;
     int nsm = 148;
@@ -154,7 +157,10 @@ double courant_limit(double dx, double dy, double dz)
 bool valid_cfg(const fdtd_llg_config &c, std::string &why)
 {
     if (c.nx < 1 || c.ny < 1 || c.nz < 1) { why = "nx, ny, nz must be >= 1"; return false; }
-    if ((long long)c.nx * c.ny * c.nz > (1LL << 34)) { why = "grid too large"; return false; }
+    if ((long long)c.nz * c.ny * ((c.nx + 31) / 32 * 32) >= (1LL << 32)) {
+        why = "grid too large: nz * ny * (nx rounded up to 32) must be below 2^32";
+        return false;
+    }
     if (!(c.dx > 0 && c.dy > 0 && c.dz > 0)) { why = "dx, dy, dz must be > 0"; return false; }
     if (c.dt < 0 || (c.dt == 0 && !(c.courant_factor > 0 && c.courant_factor <= 1))) {
         why = "dt must be > 0, or dt = 0 with 0 < courant_factor <= 1";
@@ -258,7 +264,11 @@ static int create_impl(const fdtd_llg_config *cfgs, int32_t n, fdtd_llg_t *out)
         }
         S->own_stream = true;
     }
-    if (cudaStreamCreateWithFlags(&S->s_mag, cudaStreamNonBlocking) != cudaSuccess ||
+    // the magnet kernels run beside the field sweep; at the highest priority
+    // their CTAs take the first SM slots that the sweep's CTAs free
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if (cudaStreamCreateWithPriority(&S->s_mag, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&S->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&S->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         delete S;
@@ -378,6 +388,14 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
     // per-cell class: (ca, cb, eps/2) of the three edges with index (i,j,k) + magnetic-face flags
     std::unordered_map<ClassKey, int, ClassKeyHash> classes;
     std::vector<ClassKey> keys;
+    {
+        // class 0: every coefficient zero and no flags; the field kernel reads
+        // it for the cells beyond the far walls, whose E^{n+1} is then zero
+        ClassKey zero;
+        std::memset(&zero, 0, sizeof zero);
+        classes.emplace(zero, 0);
+        keys.push_back(zero);
+    }
     std::vector<uint16_t> cls(nc);
     auto edge = [&](int comp, int i, int j, int k, float &ca, float &cb, float &he) {
         bool wall;
@@ -485,6 +503,8 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
         if (V > kMagMaxV)
             return fail(h, FDTD_E_INVAL, "a magnetic region's bounding box holds " + std::to_string(V) + " cells (maximum " +
                                              std::to_string(kMagMaxV) + ")");
+        if (mag_smem_bytes(b.x1 - b.x0 + 1, b.y1 - b.y0 + 1, b.z1 - b.z0 + 1) > kMagSmemMax)
+            return fail(h, FDTD_E_INVAL, "a magnetic region's bounding box has too many faces for one CTA's shared memory");
         boxes.push_back(b);
     }
     // magnet material table (compact index per magnetic material)
@@ -509,19 +529,19 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
     std::vector<uint8_t> hmat(totV);
     // release the previous materials of this instance
     CKR(h, cudaStreamSynchronize(S->stream));
-    S->dfree(I.cls); S->dfree(I.ctab); S->dfree(I.mbuf); S->dfree(I.magmat); S->dfree(I.fcurl);
-    I.cls = nullptr; I.ctab = nullptr; I.mbuf = nullptr; I.magmat = nullptr; I.fcurl = nullptr;
-    size_t totF = 0;
+    S->dfree(I.cls); S->dfree(I.ctab); S->dfree(I.mbuf); S->dfree(I.magmat); S->dfree(I.eedge);
+    I.cls = nullptr; I.ctab = nullptr; I.mbuf = nullptr; I.magmat = nullptr; I.eedge = nullptr;
+    size_t totE = 0;
     for (auto &b : boxes) {
         const size_t bx = b.x1 - b.x0 + 1, by = b.y1 - b.y0 + 1, bz = b.z1 - b.z0 + 1;
-        totF += (bx + 1) * by * bz + bx * (by + 1) * bz + bx * by * (bz + 1);
+        totE += 3 * (bx + 1) * (by + 1) * (bz + 1);
     }
-    I.fcurl = (float *)S->dalloc(totF * sizeof(float));
+    I.eedge = (float *)S->dalloc(std::max<size_t>(totE, 1) * sizeof(float));
     I.mbuf = (float *)S->dalloc(3 * totV * sizeof(float));
     I.magmat = (uint8_t *)S->dalloc(totV);
     I.cls = S->dalloc((size_t)I.nz * I.ny * I.px * (c16 ? 2 : 1));
     I.ctab = (float4 *)S->dalloc((size_t)3 * nclass * sizeof(float4));
-    if (!I.mbuf || !I.magmat || !I.cls || !I.ctab || !I.fcurl) return fail(h, FDTD_E_OOM, "device allocation failed");
+    if (!I.mbuf || !I.magmat || !I.cls || !I.ctab || !I.eedge) return fail(h, FDTD_E_OOM, "device allocation failed");
     I.comps.clear();
     size_t off = 0, foff = 0;
     for (size_t L = 0; L < boxes.size(); ++L) {
@@ -539,10 +559,10 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
                 }
         C.m = I.mbuf + 3 * off;
         C.mat = I.magmat + off;
-        C.fcurl = I.fcurl + foff;
+        C.eedge = I.eedge + foff;
         I.comps.push_back(C);
         off += C.V;
-        foff += (size_t)(C.bx + 1) * C.by * C.bz + (size_t)C.bx * (C.by + 1) * C.bz + (size_t)C.bx * C.by * (C.bz + 1);
+        foff += (size_t)3 * (C.bx + 1) * (C.by + 1) * (C.bz + 1);
     }
     // bias frame: M starts at Ms h, i.e. m = 0
     const double h0n = std::sqrt(hbias[0] * hbias[0] + hbias[1] * hbias[1] + hbias[2] * hbias[2]);
@@ -630,6 +650,53 @@ extern "C" int fdtd_llg_add_probe(fdtd_llg_t h, int32_t i, int32_t j, int32_t k,
 }
 
 // ----------------------------------------------------------- descriptors
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// The field kernel's TMA boxes: per buffer, H (components 3-5) on kHBX x kHBY
+// and E (components 0-2) on kEBX x kEBY of one z-plane, over a 4-D view
+// (x, y, z, component) of the six arrays; the class ids on kCBX x kEBY.  Reads
+// outside (nx, ny, nz) return zeros.
+static int encode_tensor_maps(fdtd_llg_t h, const Instance &I, Inst &d)
+{
+    auto enc = tensor_map_encoder();
+    if (!enc) return fail(h, FDTD_E_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    const cuuint64_t nf = I.n_field();
+    for (int b = 0; b < 2; ++b) {
+        const cuuint64_t dims[4] = {(cuuint64_t)I.nx, (cuuint64_t)I.ny, (cuuint64_t)I.nz, 6};
+        const cuuint64_t strides[3] = {(cuuint64_t)I.px * 4, (cuuint64_t)I.px * I.ny * 4, nf * 4};
+        const cuuint32_t boxH[4] = {kHBX, kHBY, 1, 3}, boxE[4] = {kEBX, kEBY, 1, 3};
+        CUresult r = enc(&d.tm[TM_H0 + b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, I.fields[b], dims, strides, boxH, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r == CUDA_SUCCESS)
+            r = enc(&d.tm[TM_E0 + b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, I.fields[b], dims, strides, boxE, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(h, FDTD_E_CUDA, "cuTensorMapEncodeTiled failed for a field buffer");
+    }
+    const bool c16 = I.cls_bytes == 2;
+    const cuuint64_t cdims[3] = {(cuuint64_t)I.nx, (cuuint64_t)I.ny, (cuuint64_t)I.nz};
+    const cuuint64_t cstr[2] = {(cuuint64_t)I.px * I.cls_bytes, (cuuint64_t)I.px * I.ny * I.cls_bytes};
+    const cuuint32_t cbox[3] = {(cuuint32_t)(c16 ? kCBX16 : kCBX8), kEBY, 1};
+    const CUresult r = enc(&d.tm[TM_CLS], c16 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, I.cls,
+                           cdims, cstr, cbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, FDTD_E_CUDA, "cuTensorMapEncodeTiled failed for the class ids");
+    return FDTD_OK;
+}
+
 static int upload_descriptors(fdtd_llg_t h)
 {
     Sim *S = h->sim;
@@ -639,7 +706,8 @@ static int upload_descriptors(fdtd_llg_t h)
     std::vector<int> tile_inst, ftile_inst;
     std::vector<MagComp> comps;
     bool c16 = false;
-    int vmax = 0;
+    int vmax = 0, emax = 0, msmem = 0;
+    bool stab = true;
     for (size_t ii = 0; ii < S->inst.size(); ++ii) {
         Instance &I = S->inst[ii];
         if (!I.materials_set) return fail(h, FDTD_E_STATE, "instance " + std::to_string(ii) + " has no materials");
@@ -658,7 +726,8 @@ static int upload_descriptors(fdtd_llg_t h)
             for (int c = 0; c < 6; ++c) d.F[b][c] = I.fields[b] + c * nf;
         d.fstride = (long long)nf;
         d.wHx = I.walls; d.wHy = I.walls + (size_t)I.ny * I.nz; d.wHz = d.wHy + (size_t)I.nx * I.nz;
-        d.cls = I.cls; d.ctab = I.ctab;
+        d.cls = I.cls; d.ctab = I.ctab; d.nclass = I.nclass;
+        stab = stab && I.nclass <= kTabMax;
         d.probe_buf = I.probe_buf; d.energy_buf = I.energy_buf;
         d.nx = I.nx; d.ny = I.ny; d.nz = I.nz; d.px = I.px;
         d.plane = (long long)I.ny * I.px;
@@ -680,8 +749,8 @@ static int upload_descriptors(fdtd_llg_t h)
         d.tile_off = (int)tile_inst.size();
         const int nt = d.ntx * d.nty * d.ntz;
         for (int t = 0; t < nt; ++t) tile_inst.push_back((int)ii);
-        d.fkc = std::min(I.nz, kFusedPlanes);
-        d.fntx = (I.nx + kFX - 1) / kFX; d.fnty = (I.ny + kFY - 1) / kFY; d.fntz = (I.nz + d.fkc - 1) / d.fkc;
+        d.fkc = std::min(I.nz, kSZ);
+        d.fntx = (I.nx + kSX - 1) / kSX; d.fnty = (I.ny + kSY - 1) / kSY; d.fntz = (I.nz + d.fkc - 1) / d.fkc;
         d.ftile_off = (int)ftile_inst.size();
         const int nft = d.fntx * d.fnty * d.fntz;
         for (int t = 0; t < nft; ++t) ftile_inst.push_back((int)ii);
@@ -691,6 +760,8 @@ static int upload_descriptors(fdtd_llg_t h)
             C.inst = (int)ii;
             comps.push_back(C);
             vmax = std::max(vmax, C.V);
+            emax = std::max(emax, 3 * (C.bx + 1) * (C.by + 1) * (C.bz + 1));
+            msmem = std::max(msmem, (int)mag_smem_bytes(C.bx, C.by, C.bz));
         }
         for (size_t m = 0; m < I.mm.size(); ++m) d.mm[m] = I.mm[m];
         c16 = c16 || I.cls_bytes == 2;
@@ -711,6 +782,11 @@ static int upload_descriptors(fdtd_llg_t h)
             I.cls_bytes = 2;
             hi[ii].cls = w;
         }
+    // TMA descriptors of every instance, after the class width is settled
+    for (size_t ii = 0; ii < S->inst.size(); ++ii) {
+        const int rc = encode_tensor_maps(h, S->inst[ii], hi[ii]);
+        if (rc) return rc;
+    }
     S->dfree(S->d_insts); S->dfree(S->d_tile_inst); S->dfree(S->d_ftile_inst); S->dfree(S->d_comps); S->dfree(S->d_part);
     S->d_insts = (Inst *)S->dalloc(hi.size() * sizeof(Inst));
     S->d_tile_inst = (int *)S->dalloc(tile_inst.size() * sizeof(int));
@@ -728,6 +804,9 @@ static int upload_descriptors(fdtd_llg_t h)
     S->nftiles = (int)ftile_inst.size();
     S->ncomp = (int)comps.size();
     S->vmax = vmax;
+    S->emax = emax;
+    S->stab = stab;
+    S->mag_smem = msmem;
     S->cls16 = c16;
     S->dirty = false;
     return FDTD_OK;
@@ -743,6 +822,9 @@ static LaunchSet launch_set(Sim *S)
     L.comps = S->d_comps;
     L.ncomp = S->ncomp;
     L.vmax = S->vmax;
+    L.emax = S->emax;
+    L.mag_smem = S->mag_smem;
+    L.stab = S->stab;
     L.ctl = S->d_ctl;
     L.part_f = S->d_part;
     L.part_m = S->d_part + S->nftiles;
@@ -802,6 +884,7 @@ static int sync_status(fdtd_llg_t h)
     CKR(h, cudaMemcpy(&c, S->d_ctl, sizeof c, cudaMemcpyDeviceToHost));
     if (c.status & ST_UNSTABLE) return fail(h, FDTD_E_UNSTABLE, "energy is not finite (unstable run)");
     if (c.status & ST_NOCONV) return fail(h, FDTD_E_LLG_NOCONV, "an LLG solve did not reach llg_tol within llg_max_iter");
+    if (c.status & ST_TIMEOUT) return fail(h, FDTD_E_CUDA, "a field-kernel wait for its tile copies timed out");
     return FDTD_OK;
 }
 

@@ -2,6 +2,7 @@
 // the Yee-Maxwell + LLG solver.  Not part of the public ABI.
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace fl {
@@ -19,23 +20,45 @@ constexpr int kMaxMagMat = 16;
 // each thread marching kKC planes in z.
 constexpr int kTX = 32, kTY = 8, kKC = 16;
 
-// Tile of the fused step kernel: kFX x kFY columns marching kFC(runtime)
-// planes in z, kFT threads; shared-memory planes of H with a one-cell halo on
-// the low x and y sides plus the high extension, and of E^{n+1} on the tile
-// extended by one cell on the high x and y sides.
-constexpr int kFX = 64, kFY = 16, kFT = 256;
-constexpr int kHX = kFX + 2, kHY = kFY + 2, kHN = kHX * kHY;
-constexpr int kEX = kFX + 1, kEY = kFY + 1, kEN = kEX * kEY;
-constexpr int kHQ = (kHN + kFT - 1) / kFT;
-constexpr int kEQ = (kEN + kFT - 1) / kFT;
-constexpr int kIQ = kFX * kFY / kFT;
-constexpr int kFusedPlanes = 16;   // z planes per fused-step tile
+// Fused step kernel: one CTA of kST threads per column task of kSX x kSY
+// cells x fkc (at most kSZ) planes, marching the task in z.  Each
+// z-plane arrives by TMA in one stage of a kNS-deep shared-memory ring: H on
+// the tile extended by one cell on the low x/y sides (box kHBX x kHBY, x
+// starting 4 cells low so that the copy stays 16-byte aligned), E^n and the
+// class ids on the tile extended by one cell on the high x/y sides.  E^{n+1}
+// overwrites E^n in place.  A stage stays live for two planes (as plane k and
+// then as plane k-1), so kNS - 2 planes are in flight while one is computed.
+constexpr int kSX = 64, kSY = 8, kSZ = 16, kST = 256, kNS = 4;
+constexpr int kHBX = kSX + 8, kHBY = kSY + 2, kHC = kHBX * kHBY;   // H box, one component
+constexpr int kEBX = kSX + 4, kEBY = kSY + 1, kEC = kEBX * kEBY;   // E box, one component
+constexpr int kCBX8 = kSX + 16, kCBX16 = kSX + 8;                  // class box width (u8 / u16)
+constexpr int kStageH = 3 * kHC * 4;                               // 8640 B
+constexpr int kStageE = 3 * kEC * 4;                               // 7344 B
+constexpr int kStageHOff = 0;
+constexpr int kStageEOff = (kStageH + 127) / 128 * 128;
+constexpr int kStageCOff = kStageEOff + (kStageE + 127) / 128 * 128;
+constexpr int kStageBytes = kStageCOff + (kCBX16 * kEBY * 2 + 127) / 128 * 128;
+// Class tables of at most kTabMax entries are staged in shared memory.
+constexpr int kTabMax = 64;
 
 // Magnet kernel: one CTA per face-connected magnetic region, whose bounding
-// box holds at most kMagMaxV cells, kMagCPT cells per thread.
+// box holds at most kMagMaxV cells, kMagCPT cells per thread, and whose cells
+// and faces fit in one CTA's shared memory (mag_smem_bytes).
 constexpr int kMagThreads = 512;
 constexpr int kMagMaxV = 4096;
 constexpr int kMagCPT = kMagMaxV / kMagThreads;
+constexpr int kMagSmemMax = 226 * 1024;   // 227 KB per CTA less the static shared memory
+inline long long mag_faces(int bx, int by, int bz)
+{
+    return (long long)(bx + 1) * by * bz + (long long)bx * (by + 1) * bz + (long long)bx * by * (bz + 1);
+}
+// m and its change (3 V floats each), face H and (dt/2mu0) curl E (one float
+// per face each), the material byte of each cell
+inline long long mag_smem_bytes(int bx, int by, int bz)
+{
+    const long long V = (long long)bx * by * bz;
+    return 4 * (6 * V + 2 * mag_faces(bx, by, bz)) + V;
+}
 
 // Class-table entry flags (bit field stored in the .w of the first float4).
 enum : uint32_t { CF_MAG_HX = 1u, CF_MAG_HY = 2u, CF_MAG_HZ = 4u };
@@ -44,13 +67,18 @@ struct MagMat {
     float Ms, inv_Ms, alpha, kappa;   // kappa = mu0 |gamma| (dt/2) / 2
 };
 
+// Tensor maps of one instance (TMA descriptors, 128-byte aligned in device memory).
+enum { TM_H0 = 0, TM_H1 = 1, TM_E0 = 2, TM_E1 = 3, TM_CLS = 4, TM_COUNT = 5 };
+
 // Everything a kernel needs about one grid instance.
-struct Inst {
+struct alignas(128) Inst {
+    CUtensorMap tm[TM_COUNT];             // H box and E box of buffers 0/1, class box
     float *F[2][6];                       // two buffers of Ex, Ey, Ez, Hx, Hy, Hz: [nz][ny][px]
     long long fstride;                    // F[b][c] = F[b][0] + c * fstride
     float *wHx, *wHy, *wHz;               // far-wall normal H: [nz][ny], [nz][nx], [ny][nx]
     const void *cls;                      // class id per cell: uint8 or uint16
     const float4 *ctab;                   // 3 float4 per class: (ca, flags) (cb) (eps/2)
+    int nclass;                           // entries of ctab
     double *probe_buf;                    // [cap][nprobe][9]
     double *energy_buf;                   // [cap]
     int nx, ny, nz, px;
@@ -67,7 +95,7 @@ struct Inst {
     double srcp[kMaxSrc][4];              // J0, f0, Tp, tpk
     int probe[kMaxProbe][3];
     int tile_off, ntx, nty, ntz;          // half-push tiles of this instance in the tile list
-    int ftile_off, fntx, fnty, fntz, fkc; // fused-step tiles (kFX x kFY x fkc)
+    int ftile_off, fntx, fnty, fntz, fkc; // fused-step tasks (kSX x kSY x fkc)
     int mag_off, nmag;                    // magnet regions of this instance
     MagMat mm[kMaxMagMat];
 };
@@ -77,16 +105,16 @@ struct MagComp {
     int x0, y0, z0, bx, by, bz, V;
     float *m;               // deviation M - Ms h in the bias frame: 3 blocks of V
     const uint8_t *mat;     // V: magnet material index, 0xFF outside this region
-    float *fcurl;           // scratch: curl E at the region's faces (x, y, z face blocks)
+    float *eedge;           // scratch: E at the edges of the box, 3 blocks of (bx+1)(by+1)(bz+1)
 };
 
 // Device-resident control block of a batch.
 struct StepCtl {
     long long step;         // completed steps
-    unsigned int counter;   // CTAs of the H pass that have finished this step
+    unsigned int counter;   // CTAs (field and magnet kernels) that have finished this step
     int status;             // latched error bits (ST_*)
 };
-enum : int { ST_NOCONV = 1, ST_UNSTABLE = 2 };
+enum : int { ST_NOCONV = 1, ST_UNSTABLE = 2, ST_TIMEOUT = 4 };
 
 struct LaunchSet {
     const Inst *insts;
@@ -99,13 +127,16 @@ struct LaunchSet {
     StepCtl *ctl;
     double *part_f, *part_m;            // energy partials per fused tile / per region
     const int *ftile_inst;
-    int nftiles;
+    int nftiles;                        // fused-step tasks (one CTA each)
+    int emax;                           // most edges of a magnet region's box (3 components)
+    int mag_smem;                       // dynamic shared memory of the magnet kernel (bytes)
     int src, dst;                       // field buffers read / written by a step
     int grid_h;
     bool cls16;
     float llg_tol;
     int llg_max_iter, llg_fixed_iter;
     int energy;
+    bool stab;                          // every instance's class table fits kTabMax
 };
 
 // Launchers (kernels_fwd.cu).  launch_half: the start-up H/M half-push that
@@ -117,6 +148,7 @@ cudaError_t launch_half(const LaunchSet &L, cudaStream_t s);
 cudaError_t launch_step(const LaunchSet &L, cudaStream_t s, cudaStream_t s_mag, cudaEvent_t ev_fork,
                         cudaEvent_t ev_join, cudaEvent_t *prof);
 int h_half_blocks_per_sm(bool cls16);
+int step_blocks_per_sm(bool cls16);
 
 // fdtd_llg_last_error(NULL) message for entry points without a handle.
 void set_last_error(const char *msg);

@@ -4,20 +4,32 @@
 // The state alternates between two field buffers: a step reads E^n and
 // H^{n+1/2} from buffer src and writes E^{n+1} and H^{n+3/2} to buffer dst.
 //
-//   step_kernel : one sweep over the grid computing, plane by plane in z,
-//                 E^{n+1} = ca E^n + cb (curl H^{n+1/2} - J(t_{n+1/2})) (Eq. Ampere
-//                 with time-centred H and J) on a shared-memory tile extended by
-//                 one cell, then the two half-pushes H^{n+1/2} -> H^{n+1} ->
-//                 H^{n+3/2} of every non-magnetic face (M = 0 there, the plain
-//                 Faraday update); FP64 energy partials and probe samples.
-//   mag_kernel  : the two H/M half-pushes of every magnetic face and cell (Eq.
-//                 iterate_H with the trapezoidal LLG solve of Eqs. llg_tra4-6,
-//                 Jacobi-iterated until max |M^r - M^{r-1}|/Ms < tol), one CTA per
-//                 face-connected magnetic region; it recomputes E^{n+1} at its
-//                 own faces from buffer src, so it runs concurrently with
-//                 step_kernel (the two write disjoint faces of buffer dst).
-//   h_half_kernel + mag_kernel<false> : the start-up half-push that moves H and
-//                 M from integer time to half a step ahead, in place.
+//   step_kernel     : one sweep over the grid.  Each CTA marches a column of
+//                     64 x 8 cells through up to 16 z-planes; every plane of H,
+//                     E^n and class ids arrives by TMA in a 4-stage
+//                     shared-memory ring (two planes in flight while one is
+//                     computed).  Per plane it computes E^{n+1} = ca E^n +
+//                     cb (curl H^{n+1/2} - J(t_{n+1/2})) (Eq. Ampere with
+//                     time-centred H and J) on the tile extended by one cell,
+//                     in place, then the two half-pushes H^{n+1/2} -> H^{n+1}
+//                     -> H^{n+3/2} of the plane below for every non-magnetic
+//                     face (M = 0 there: the plain Faraday update), with FP64
+//                     energy partials and probe samples.
+//   mag_edge_kernel : E^{n+1} (or the stored E, at start-up) at every edge of
+//                     each magnetic region's box, with the same arithmetic as
+//                     step_kernel, into a scratch array; many CTAs, one edge
+//                     per thread.
+//   mag_kernel      : the H/M half-pushes of every magnetic face and cell (Eq.
+//                     iterate_H with the trapezoidal LLG solve of Eqs.
+//                     llg_tra4-6, Jacobi-iterated until max |M^r - M^{r-1}|/Ms
+//                     < tol), one CTA per face-connected magnetic region, its
+//                     cells, faces and face curls resident in shared memory.
+//   The two magnet kernels run on a second, high-priority stream concurrently
+//   with step_kernel: they read only buffer src and write only magnetic faces
+//   of buffer dst, which step_kernel never writes.
+//   h_half_kernel + the magnet kernels with one half-push : the start-up
+//                     half-push that moves H and M from integer time to half a
+//                     step ahead, in place.
 // The last CTA to finish a step, over both kernels, sums the energy partials
 // in a fixed order and advances the device step counter (no extra launch).
 #include "fdtd_llg_internal.h"
@@ -68,10 +80,6 @@ __device__ double source_value(const double *p, double t)
     return p[0] * exp(-u * u / (2.0 * p[2] * p[2])) * cos(2.0 * kPi * p[1] * t);
 }
 
-__device__ __forceinline__ int class_at(const LaunchSet &L, const Inst *I, long long off)
-{
-    return L.cls16 ? (int)static_cast<const uint16_t *>(I->cls)[off] : (int)static_cast<const uint8_t *>(I->cls)[off];
-}
 
 // Called by every CTA of a step (field and magnet kernels) after its partials
 // are written: the last one sums them per instance and advances the step.
@@ -146,60 +154,78 @@ __global__ void __launch_bounds__(kTX *kTY) h_half_kernel(LaunchSet L)
     }
 }
 
+// ------------------------------------------------- shared E^{n+1} arithmetic
+// Written with explicit round-to-nearest operations so that step_kernel and
+// mag_edge_kernel produce bitwise the same E^{n+1}.
+// (a1 - b1) i1 - (a2 - b2) i2: one component of a Yee curl.
+__device__ __forceinline__ float curl2(float a1, float b1, float i1, float a2, float b2, float i2)
+{
+    return __fsub_rn(__fmul_rn(__fsub_rn(a1, b1), i1), __fmul_rn(__fsub_rn(a2, b2), i2));
+}
+// ca E^n + cb (curl H - J)
+__device__ __forceinline__ float e_next(float ca, float e, float cb, float c)
+{
+    return __fadd_rn(__fmul_rn(ca, e), __fmul_rn(cb, c));
+}
+
 // ------------------------------------------------------------ magnet pass
-__device__ __forceinline__ float *hx_ptr(const Inst *I, float *const *F, int i, int j, int k)
+__device__ __forceinline__ float *hx_ptr(const Inst *I, float *F0, int i, int j, int k)
 {
-    return (i == I->nx) ? I->wHx + (long long)k * I->ny + j : F[3] + (long long)k * I->plane + (long long)j * I->px + i;
+    return (i == I->nx) ? I->wHx + (long long)k * I->ny + j : F0 + 3 * I->fstride + (long long)k * I->plane + (long long)j * I->px + i;
 }
-__device__ __forceinline__ float *hy_ptr(const Inst *I, float *const *F, int i, int j, int k)
+__device__ __forceinline__ float *hy_ptr(const Inst *I, float *F0, int i, int j, int k)
 {
-    return (j == I->ny) ? I->wHy + (long long)k * I->nx + i : F[4] + (long long)k * I->plane + (long long)j * I->px + i;
+    return (j == I->ny) ? I->wHy + (long long)k * I->nx + i : F0 + 4 * I->fstride + (long long)k * I->plane + (long long)j * I->px + i;
 }
-__device__ __forceinline__ float *hz_ptr(const Inst *I, float *const *F, int i, int j, int k)
+__device__ __forceinline__ float *hz_ptr(const Inst *I, float *F0, int i, int j, int k)
 {
-    return (k == I->nz) ? I->wHz + (long long)j * I->nx + i : F[5] + (long long)k * I->plane + (long long)j * I->px + i;
-}
-
-// E of component comp at edge (i,j,k): as stored in F (ADVANCE false), or
-// advanced to E^{n+1} from F's E^n and H^{n+1/2} with the same arithmetic as
-// step_kernel (ADVANCE true).  Edges beyond the far walls are zero.
-template <bool ADVANCE>
-__device__ float e_edge(const LaunchSet &L, const Inst *I, float *const *F, int comp, int i, int j, int k, long long n)
-{
-    if (i >= I->nx || j >= I->ny || k >= I->nz) return 0.f;
-    const long long plane = I->plane;
-    const long long off = (long long)k * plane + (long long)j * I->px + i;
-    if (!ADVANCE) return __ldg(F[comp] + off);
-    const float *Hx = F[3], *Hy = F[4], *Hz = F[5];
-    float cu;
-    if (comp == 0)
-        cu = (Hz[off] - (j > 0 ? Hz[off - I->px] : 0.f)) * I->idy - (Hy[off] - (k > 0 ? Hy[off - plane] : 0.f)) * I->idz;
-    else if (comp == 1)
-        cu = (Hx[off] - (k > 0 ? Hx[off - plane] : 0.f)) * I->idz - (Hz[off] - (i > 0 ? Hz[off - 1] : 0.f)) * I->idx;
-    else
-        cu = (Hy[off] - (i > 0 ? Hy[off - 1] : 0.f)) * I->idx - (Hx[off] - (j > 0 ? Hx[off - I->px] : 0.f)) * I->idy;
-    for (int s = 0; s < I->nsrc; ++s)
-        if (I->src[s][0] == comp && I->src[s][1] == i && I->src[s][2] == j && I->src[s][3] == k)
-            cu -= (float)source_value(I->srcp[s], ((double)n + 0.5) * I->dt);
-    const int c = class_at(L, I, off);
-    const float4 A = __ldg(I->ctab + 3 * c), B = __ldg(I->ctab + 3 * c + 1);
-    const float ca = comp == 0 ? A.x : (comp == 1 ? A.y : A.z);
-    const float cb = comp == 0 ? B.x : (comp == 1 ? B.y : B.z);
-    return ca * F[comp][off] + cb * cu;
+    return (k == I->nz) ? I->wHz + (long long)j * I->nx + i : F0 + 5 * I->fstride + (long long)k * I->plane + (long long)j * I->px + i;
 }
 
-// curl of E at the x-face (i, j+1/2, k+1/2), y-face (i+1/2, j, k+1/2), z-face (i+1/2, j+1/2, k)
-template <bool ADVANCE>
-__device__ float face_curl(const LaunchSet &L, const Inst *I, float *const *F, int a, int i, int j, int k, long long n)
+// E at every edge (comp, i, j, k) of each magnetic region's box,
+// i in [x0, x0+bx], j in [y0, y0+by], k in [z0, z0+bz]: advanced to E^{n+1}
+// from buffer src (ADVANCE) or as stored.  Edges beyond the far walls are zero.
+// Grid: (edges / 256 rounded up, regions).
+template <bool ADVANCE, typename ClsT>
+__global__ void __launch_bounds__(256) mag_edge_kernel(LaunchSet L)
 {
-    if (a == 0)
-        return (e_edge<ADVANCE>(L, I, F, 2, i, j + 1, k, n) - e_edge<ADVANCE>(L, I, F, 2, i, j, k, n)) * I->idy -
-               (e_edge<ADVANCE>(L, I, F, 1, i, j, k + 1, n) - e_edge<ADVANCE>(L, I, F, 1, i, j, k, n)) * I->idz;
-    if (a == 1)
-        return (e_edge<ADVANCE>(L, I, F, 0, i, j, k + 1, n) - e_edge<ADVANCE>(L, I, F, 0, i, j, k, n)) * I->idz -
-               (e_edge<ADVANCE>(L, I, F, 2, i + 1, j, k, n) - e_edge<ADVANCE>(L, I, F, 2, i, j, k, n)) * I->idx;
-    return (e_edge<ADVANCE>(L, I, F, 1, i + 1, j, k, n) - e_edge<ADVANCE>(L, I, F, 1, i, j, k, n)) * I->idx -
-           (e_edge<ADVANCE>(L, I, F, 0, i, j + 1, k, n) - e_edge<ADVANCE>(L, I, F, 0, i, j, k, n)) * I->idy;
+    const MagComp C = L.comps[blockIdx.y];
+    const int ex = C.bx + 1, ey = C.by + 1, ne = ex * ey * (C.bz + 1);
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 3 * ne) return;
+    const Inst *I = L.insts + C.inst;
+    const int comp = e / ne, r = e - comp * ne;
+    const int li = r % ex, lj = (r / ex) % ey, lk = r / (ex * ey);
+    const int i = C.x0 + li, j = C.y0 + lj, k = C.z0 + lk;
+    float v = 0.f;
+    if (i < I->nx && j < I->ny && k < I->nz) {
+        const float *__restrict__ Fs = I->F[L.src][0];
+        const long long fs = I->fstride, plane = I->plane;
+        const int px = I->px;
+        const long long o = (long long)k * plane + (long long)j * px + i;
+        if (!ADVANCE) {
+            v = Fs[comp * fs + o];
+        } else {
+            const float *Hx = Fs + 3 * fs, *Hy = Fs + 4 * fs, *Hz = Fs + 5 * fs;
+            float cu;
+            if (comp == 0)
+                cu = curl2(Hz[o], j > 0 ? Hz[o - px] : 0.f, I->idy, Hy[o], k > 0 ? Hy[o - plane] : 0.f, I->idz);
+            else if (comp == 1)
+                cu = curl2(Hx[o], k > 0 ? Hx[o - plane] : 0.f, I->idz, Hz[o], i > 0 ? Hz[o - 1] : 0.f, I->idx);
+            else
+                cu = curl2(Hy[o], i > 0 ? Hy[o - 1] : 0.f, I->idx, Hx[o], j > 0 ? Hx[o - px] : 0.f, I->idy);
+            const long long n = *(volatile long long *)&L.ctl->step;
+            for (int s = 0; s < I->nsrc; ++s)
+                if (I->src[s][0] == comp && I->src[s][1] == i && I->src[s][2] == j && I->src[s][3] == k)
+                    cu = __fsub_rn(cu, (float)source_value(I->srcp[s], ((double)n + 0.5) * I->dt));
+            const int c = (int)static_cast<const ClsT *>(I->cls)[o];
+            const float4 A = __ldg(I->ctab + 3 * c), B = __ldg(I->ctab + 3 * c + 1);
+            const float ca = comp == 0 ? A.x : (comp == 1 ? A.y : A.z);
+            const float cb = comp == 0 ? B.x : (comp == 1 ? B.y : B.z);
+            v = e_next(ca, Fs[comp * fs + o], cb, cu);
+        }
+    }
+    C.eedge[e] = v;
 }
 
 // The LLG solve runs in the bias frame (rows of I->R: e1, e2, e3 = h) on the
@@ -223,8 +249,34 @@ __device__ __forceinline__ void from_frame(const float *R, float lx, float ly, f
     gz = R[2] * lx + R[5] * ly + R[8] * lz;
 }
 
-// FUSED: a full step, H^s from buffer src, results to buffer dst, curl of
-// E^{n+1}.  Otherwise: the start-up half-push, in place, curl of the stored E.
+// Face f of a region's box: axis a and box-local indices; the cells on its low
+// (vl) and high (vr) side, -1 outside the box.  Faces are numbered x faces
+// ((bx+1) by bz), then y faces (bx (by+1) bz), then z faces (bx by (bz+1)).
+__device__ __forceinline__ void face_decode(int f, int bx, int by, int bz, int &a, int &fi, int &fj, int &fk, int &vl,
+                                            int &vr)
+{
+    const int nfx = (bx + 1) * by * bz, nfy = bx * (by + 1) * bz;
+    vl = vr = -1;
+    if (f < nfx) {
+        a = 0; fi = f % (bx + 1); fj = (f / (bx + 1)) % by; fk = f / ((bx + 1) * by);
+        if (fi > 0) vl = (fk * by + fj) * bx + fi - 1;
+        if (fi < bx) vr = (fk * by + fj) * bx + fi;
+    } else if (f < nfx + nfy) {
+        const int g = f - nfx;
+        a = 1; fi = g % bx; fj = (g / bx) % (by + 1); fk = g / (bx * (by + 1));
+        if (fj > 0) vl = (fk * by + fj - 1) * bx + fi;
+        if (fj < by) vr = (fk * by + fj) * bx + fi;
+    } else {
+        const int g = f - nfx - nfy;
+        a = 2; fi = g % bx; fj = (g / bx) % by; fk = g / (bx * by);
+        if (fk > 0) vl = ((fk - 1) * by + fj) * bx + fi;
+        if (fk < bz) vr = (fk * by + fj) * bx + fi;
+    }
+}
+
+// FUSED: a full step (two half-pushes), H^{n+1/2} from buffer src, results to
+// buffer dst, curl of E^{n+1}.  Otherwise: the start-up half-push, in place on
+// buffer src, curl of the stored E.  mag_edge_kernel has filled C.eedge.
 template <bool FUSED>
 __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
 {
@@ -232,85 +284,68 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
     __shared__ float sredf[kMagThreads / 32];
     __shared__ double sredd[kMagThreads / 32];
     __shared__ int s_last;
-    const int Vm = L.vmax;
-    float *sM = smem;            // m at the start of the half-push (bias frame)
-    float *sB = sM + 3 * Vm;     // b - M^n of Eq. llg_tra6 (bias frame)
-    float *sA = sB + 3 * Vm;     // cell mean of H^* (H after the curl push), global
-    float *sD = sA + 3 * Vm;     // M^{r} - M^{n}, current iterate, global
-    uint8_t *smat = reinterpret_cast<uint8_t *>(sD + 3 * Vm);
-
     const MagComp C = L.comps[blockIdx.x];
     const Inst *I = L.insts + C.inst;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int V = C.V, bx = C.bx, by = C.by, bz = C.bz, bxy = bx * by;
+    const int nfx = (bx + 1) * by * bz, nfy = bx * (by + 1) * bz, nfz = bx * by * (bz + 1);
+    const int nf = nfx + nfy + nfz;
+    float *sM = smem;            // m (bias frame), 3 blocks of V
+    float *sD = sM + 3 * V;      // M^{r} - M^{n} of the current iterate (global axes), 3 blocks of V
+    float *sH = sD + 3 * V;      // face H: H^s of the half-push, then its result
+    float *sC = sH + nf;         // (dt/2mu0) curl E at the face
+    uint8_t *smat = reinterpret_cast<uint8_t *>(sC + nf);
     const long long n = *(volatile long long *)&L.ctl->step;
     const float ch = I->ch, h0n = I->h0n;
-    float *const *Fs = I->F[L.src];
-    float *const *Fd = I->F[FUSED ? L.dst : L.src];
+    float *Fs = I->F[L.src][0];
+    float *Fd = I->F[FUSED ? L.dst : L.src][0];
     float R[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) R[q] = I->R[q];
-    const int nfx = (bx + 1) * by * bz, nfy = bx * (by + 1) * bz, nfz = bx * by * (bz + 1);
 
     for (int v = tid; v < V; v += nth) {
         smat[v] = C.mat[v];
         sM[v] = C.m[v];
-        sM[Vm + v] = C.m[V + v];
-        sM[2 * Vm + v] = C.m[2 * V + v];
+        sM[V + v] = C.m[V + v];
+        sM[2 * V + v] = C.m[2 * V + v];
     }
     __syncthreads();
-    // curl E at every face of the region, once for both half-pushes
-    for (int f = tid; f < nfx + nfy + nfz; f += nth) {
-        int a, fi, fj, fk;
-        if (f < nfx) { a = 0; fi = f % (bx + 1); fj = (f / (bx + 1)) % by; fk = f / ((bx + 1) * by); }
-        else if (f < nfx + nfy) { const int g = f - nfx; a = 1; fi = g % bx; fj = (g / bx) % (by + 1); fk = g / (bx * (by + 1)); }
-        else { const int g = f - nfx - nfy; a = 2; fi = g % bx; fj = (g / bx) % by; fk = g / bxy; }
-        int vl = -1, vr = -1;
-        if (a == 0) { if (fi > 0) vl = (fk * by + fj) * bx + fi - 1; if (fi < bx) vr = (fk * by + fj) * bx + fi; }
-        else if (a == 1) { if (fj > 0) vl = (fk * by + fj - 1) * bx + fi; if (fj < by) vr = (fk * by + fj) * bx + fi; }
-        else { if (fk > 0) vl = ((fk - 1) * by + fj) * bx + fi; if (fk < bz) vr = (fk * by + fj) * bx + fi; }
-        const bool own = (vl >= 0 && smat[vl] != 0xFF) || (vr >= 0 && smat[vr] != 0xFF);
-        C.fcurl[f] = own ? face_curl<FUSED>(L, I, Fs, a, C.x0 + fi, C.y0 + fj, C.z0 + fk, n) : 0.f;
+    // H^s and (dt/2mu0) curl E at every face of the region, once for both half-pushes
+    {
+        const int ex = bx + 1, exy = (bx + 1) * (by + 1), ne = exy * (bz + 1);
+        const float *Ex = C.eedge, *Ey = Ex + ne, *Ez = Ey + ne;
+        for (int f = tid; f < nf; f += nth) {
+            int a, fi, fj, fk, vl, vr;
+            face_decode(f, bx, by, bz, a, fi, fj, fk, vl, vr);
+            const bool own = (vl >= 0 && smat[vl] != 0xFF) || (vr >= 0 && smat[vr] != 0xFF);
+            float h = 0.f, c = 0.f;
+            if (own) {
+                const int i = C.x0 + fi, j = C.y0 + fj, k = C.z0 + fk;
+                const int e0 = fk * exy + fj * ex + fi;
+                float cu;
+                if (a == 0) {
+                    h = *hx_ptr(I, Fs, i, j, k);
+                    cu = curl2(Ez[e0 + ex], Ez[e0], I->idy, Ey[e0 + exy], Ey[e0], I->idz);
+                } else if (a == 1) {
+                    h = *hy_ptr(I, Fs, i, j, k);
+                    cu = curl2(Ex[e0 + exy], Ex[e0], I->idz, Ez[e0 + 1], Ez[e0], I->idx);
+                } else {
+                    h = *hz_ptr(I, Fs, i, j, k);
+                    cu = curl2(Ey[e0 + 1], Ey[e0], I->idx, Ex[e0 + ex], Ex[e0], I->idy);
+                }
+                c = ch * cu;
+            }
+            sH[f] = h;
+            sC[f] = c;
+        }
     }
     __syncthreads();
 
     double eacc = 0.0;
     const int nhalf = FUSED ? 2 : 1;
     for (int hp = 0; hp < nhalf; ++hp) {
-        float *const *Fin = hp == 0 ? Fs : Fd;   // H^s of this half-push
-        // cell means of H^s and H^*, and b - M^n
-        for (int v = tid; v < V; v += nth) {
-            const int m = smat[v];
-            sD[v] = sD[Vm + v] = sD[2 * Vm + v] = 0.f;
-            if (m == 0xFF) {
-                sB[v] = sB[Vm + v] = sB[2 * Vm + v] = 0.f;
-                sA[v] = sA[Vm + v] = sA[2 * Vm + v] = 0.f;
-                continue;
-            }
-            const int li = v % bx, lj = (v / bx) % by, lk = v / bxy;
-            const int i = C.x0 + li, j = C.y0 + lj, k = C.z0 + lk;
-            const float hx0 = *hx_ptr(I, Fin, i, j, k), hx1 = *hx_ptr(I, Fin, i + 1, j, k);
-            const float hy0 = *hy_ptr(I, Fin, i, j, k), hy1 = *hy_ptr(I, Fin, i, j + 1, k);
-            const float hz0 = *hz_ptr(I, Fin, i, j, k), hz1 = *hz_ptr(I, Fin, i, j, k + 1);
-            const float cx0 = C.fcurl[(lk * by + lj) * (bx + 1) + li], cx1 = C.fcurl[(lk * by + lj) * (bx + 1) + li + 1];
-            const float cy0 = C.fcurl[nfx + (lk * (by + 1) + lj) * bx + li], cy1 = C.fcurl[nfx + (lk * (by + 1) + lj + 1) * bx + li];
-            const float cz0 = C.fcurl[nfx + nfy + (lk * by + lj) * bx + li], cz1 = C.fcurl[nfx + nfy + ((lk + 1) * by + lj) * bx + li];
-            sA[v] = 0.5f * ((hx0 - ch * cx0) + (hx1 - ch * cx1));
-            sA[Vm + v] = 0.5f * ((hy0 - ch * cy0) + (hy1 - ch * cy1));
-            sA[2 * Vm + v] = 0.5f * ((hz0 - ch * cz0) + (hz1 - ch * cz1));
-            float hex, hey, hez;   // H_eff^s in the bias frame
-            to_frame(R, 0.5f * (hx0 + hx1), 0.5f * (hy0 + hy1), 0.5f * (hz0 + hz1), hex, hey, hez);
-            hez += h0n;
-            const float mx = sM[v], my = sM[Vm + v], mz = sM[2 * Vm + v];
-            const float Mz = I->mm[m].Ms + mz;
-            const float kap = I->mm[m].kappa;
-            // b - M^n of Eq. llg_tra6: -kappa M^n x H_eff^n
-            sB[v] = -kap * (my * hez - Mz * hey);
-            sB[Vm + v] = -kap * (Mz * hex - mx * hez);
-            sB[2 * Vm + v] = -kap * (mx * hey - my * hex);
-        }
+        for (int v = tid; v < V; v += nth) sD[v] = sD[V + v] = sD[2 * V + v] = 0.f;
         __syncthreads();
-
         // Jacobi iteration of Eq. llg_tra4 with H_eff^{r-1} from the previous iterate
         float dl[kMagCPT][3];   // last iterate's change of m, bias frame
 #pragma unroll
@@ -328,28 +363,43 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
                 const int m = smat[v];
                 if (m == 0xFF) continue;
                 const int li = v % bx, lj = (v / bx) % by, lk = v / bxy;
-                const float d0 = sD[v], d1 = sD[Vm + v], d2 = sD[2 * Vm + v];
+                const int fx0 = (lk * by + lj) * (bx + 1) + li, fy0 = nfx + (lk * (by + 1) + lj) * bx + li,
+                          fz0 = nfx + nfy + (lk * by + lj) * bx + li;
+                const float hx0 = sH[fx0], hx1 = sH[fx0 + 1], hy0 = sH[fy0], hy1 = sH[fy0 + bx];
+                const float hz0 = sH[fz0], hz1 = sH[fz0 + bxy];
+                // cell means of H^* = H^s - (dt/2mu0) curl E
+                const float ax_ = 0.5f * ((hx0 - sC[fx0]) + (hx1 - sC[fx0 + 1]));
+                const float ay_ = 0.5f * ((hy0 - sC[fy0]) + (hy1 - sC[fy0 + bx]));
+                const float az_ = 0.5f * ((hz0 - sC[fz0]) + (hz1 - sC[fz0 + bxy]));
+                const float d0 = sD[v], d1 = sD[V + v], d2 = sD[2 * V + v];
                 const float dxm = li > 0 ? sD[v - 1] : 0.f, dxp = li < bx - 1 ? sD[v + 1] : 0.f;
-                const float dym = lj > 0 ? sD[Vm + v - bx] : 0.f, dyp = lj < by - 1 ? sD[Vm + v + bx] : 0.f;
-                const float dzm = lk > 0 ? sD[2 * Vm + v - bxy] : 0.f, dzp = lk < bz - 1 ? sD[2 * Vm + v + bxy] : 0.f;
-                float hex, hey, hez;
-                to_frame(R, sA[v] - 0.25f * (dxm + 2.f * d0 + dxp), sA[Vm + v] - 0.25f * (dym + 2.f * d1 + dyp),
-                         sA[2 * Vm + v] - 0.25f * (dzm + 2.f * d2 + dzp), hex, hey, hez);
+                const float dym = lj > 0 ? sD[V + v - bx] : 0.f, dyp = lj < by - 1 ? sD[V + v + bx] : 0.f;
+                const float dzm = lk > 0 ? sD[2 * V + v - bxy] : 0.f, dzp = lk < bz - 1 ? sD[2 * V + v + bxy] : 0.f;
+                float hex, hey, hez;   // H_eff^{r-1} in the bias frame
+                to_frame(R, ax_ - 0.25f * (dxm + 2.f * d0 + dxp), ay_ - 0.25f * (dym + 2.f * d1 + dyp),
+                         az_ - 0.25f * (dzm + 2.f * d2 + dzp), hex, hey, hez);
                 hez += h0n;
+                float sx, sy, sz;      // H_eff^s (start of the half-push) in the bias frame
+                to_frame(R, 0.5f * (hx0 + hx1), 0.5f * (hy0 + hy1), 0.5f * (hz0 + hz1), sx, sy, sz);
+                sz += h0n;
                 const MagMat mm = I->mm[m];
-                const float mx = sM[v], my = sM[Vm + v], mz = sM[2 * Vm + v];
+                const float mx = sM[v], my = sM[V + v], mz = sM[2 * V + v];
                 const float Mz = mm.Ms + mz;
                 const float dam = mm.alpha * mm.inv_Ms;
                 const float ax = -(mm.kappa * hex + dam * mx);
                 const float ay = -(mm.kappa * hey + dam * my);
                 const float az = -(mm.kappa * hez + mm.alpha + dam * mz);
                 // Eq. llg_tra4 written for the increment d = M~ - M^n, which solves
-                // d + a x d = r with r = b - M^n - a x M^n = -kappa M^n x (H_eff^n + H_eff^{r-1})
-                // (the damping part of a is parallel to M^n); every term is small,
-                // so d keeps full FP32 relative precision however large M^n is.
-                const float rx = sB[v] - mm.kappa * (my * hez - Mz * hey);
-                const float ry = sB[Vm + v] - mm.kappa * (Mz * hex - mx * hez);
-                const float rz = sB[2 * Vm + v] - mm.kappa * (mx * hey - my * hex);
+                // d + a x d = r with r = b - M^n - a x M^n = -kappa M^n x (H_eff^s + H_eff^{r-1})
+                // (Eq. llg_tra6 gives b - M^n = -kappa M^n x H_eff^s; the damping part
+                // of a is parallel to M^n); every term is small, so d keeps full FP32
+                // relative precision however large M^n is.
+                const float bx_ = -mm.kappa * (my * sz - Mz * sy);
+                const float by_ = -mm.kappa * (Mz * sx - mx * sz);
+                const float bz_ = -mm.kappa * (mx * sy - my * sx);
+                const float rx = bx_ - mm.kappa * (my * hez - Mz * hey);
+                const float ry = by_ - mm.kappa * (Mz * hex - mx * hez);
+                const float rz = bz_ - mm.kappa * (mx * hey - my * hex);
                 const float ar = ax * rx + ay * ry + az * rz;
                 const float inv1 = 1.f / (1.f + ax * ax + ay * ay + az * az);
                 const float ddx = (rx + ar * ax - (ay * rz - az * ry)) * inv1;
@@ -374,8 +424,8 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
                 const int v = tid + q * nth;
                 if (v < V && smat[v] != 0xFF) {
                     sD[v] = dn[q][0];
-                    sD[Vm + v] = dn[q][1];
-                    sD[2 * Vm + v] = dn[q][2];
+                    sD[V + v] = dn[q][1];
+                    sD[2 * V + v] = dn[q][2];
                 }
             }
             res = block_max(res, sredf);
@@ -390,25 +440,16 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
             }
         }
 
-        // faces: H = H^s - (dt/2mu0) curl E - (dM_left + dM_right)/2
+        // faces: H = H^s - (dt/2mu0) curl E - (dM_low + dM_high)/2
         const bool rec = FUSED && hp == 0;
-        for (int f = tid; f < nfx + nfy + nfz; f += nth) {
-            int a, fi, fj, fk;
-            if (f < nfx) { a = 0; fi = f % (bx + 1); fj = (f / (bx + 1)) % by; fk = f / ((bx + 1) * by); }
-            else if (f < nfx + nfy) { const int g = f - nfx; a = 1; fi = g % bx; fj = (g / bx) % (by + 1); fk = g / (bx * (by + 1)); }
-            else { const int g = f - nfx - nfy; a = 2; fi = g % bx; fj = (g / bx) % by; fk = g / bxy; }
-            int vl = -1, vr = -1;
-            if (a == 0) { if (fi > 0) vl = (fk * by + fj) * bx + fi - 1; if (fi < bx) vr = (fk * by + fj) * bx + fi; }
-            else if (a == 1) { if (fj > 0) vl = (fk * by + fj - 1) * bx + fi; if (fj < by) vr = (fk * by + fj) * bx + fi; }
-            else { if (fk > 0) vl = ((fk - 1) * by + fj) * bx + fi; if (fk < bz) vr = (fk * by + fj) * bx + fi; }
+        for (int f = tid; f < nf; f += nth) {
+            int a, fi, fj, fk, vl, vr;
+            face_decode(f, bx, by, bz, a, fi, fj, fk, vl, vr);
             const bool inl = vl >= 0 && smat[vl] != 0xFF, inr = vr >= 0 && smat[vr] != 0xFF;
             if (!inl && !inr) continue;
-            const int i = C.x0 + fi, j = C.y0 + fj, k = C.z0 + fk;
-            const float dlv = inl ? sD[a * Vm + vl] : 0.f, drv = inr ? sD[a * Vm + vr] : 0.f;
-            const float hin = a == 0 ? *hx_ptr(I, Fin, i, j, k) : (a == 1 ? *hy_ptr(I, Fin, i, j, k) : *hz_ptr(I, Fin, i, j, k));
-            float *hout = a == 0 ? hx_ptr(I, Fd, i, j, k) : (a == 1 ? hy_ptr(I, Fd, i, j, k) : hz_ptr(I, Fd, i, j, k));
-            const float h = (hin - ch * C.fcurl[f]) - 0.5f * (dlv + drv);
-            *hout = h;
+            const float dlv = inl ? sD[a * V + vl] : 0.f, drv = inr ? sD[a * V + vr] : 0.f;
+            const float h = (sH[f] - sC[f]) - 0.5f * (dlv + drv);
+            sH[f] = h;
             if (rec) eacc += (double)(h * h);
         }
 #pragma unroll
@@ -416,8 +457,8 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
             const int v = tid + q * nth;
             if (v < V && smat[v] != 0xFF) {
                 sM[v] += dl[q][0];
-                sM[Vm + v] += dl[q][1];
-                sM[2 * Vm + v] += dl[q][2];
+                sM[V + v] += dl[q][1];
+                sM[2 * V + v] += dl[q][2];
             }
         }
         __syncthreads();
@@ -428,7 +469,7 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
             for (int v = tid; v < V; v += nth) {
                 const int m = smat[v];
                 if (m == 0xFF) continue;
-                const float qx = sM[v], qy = sM[Vm + v], qz = sM[2 * Vm + v];
+                const float qx = sM[v], qy = sM[V + v], qz = sM[2 * V + v];
                 z += (qx * qx + qy * qy + qz * qz) * I->mm[m].inv_Ms;
             }
             eacc += (double)z * (0.5 * kMu0 * (double)h0n);
@@ -437,25 +478,24 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
                 const int pi = I->probe[p][0] - C.x0, pj = I->probe[p][1] - C.y0, pk = I->probe[p][2] - C.z0;
                 if (pi < 0 || pj < 0 || pk < 0 || pi > bx || pj > by || pk > bz) continue;
                 double *row = I->probe_buf + ((long long)(n % I->cap) * I->nprobe + p) * 9;
-                const int gi = I->probe[p][0], gj = I->probe[p][1], gk = I->probe[p][2];
                 if (pj < by && pk < bz) {
                     const bool l = pi > 0 && smat[(pk * by + pj) * bx + pi - 1] != 0xFF;
-                    if (l || (pi < bx && smat[(pk * by + pj) * bx + pi] != 0xFF)) row[3] = *hx_ptr(I, Fd, gi, gj, gk);
+                    if (l || (pi < bx && smat[(pk * by + pj) * bx + pi] != 0xFF)) row[3] = sH[(pk * by + pj) * (bx + 1) + pi];
                 }
                 if (pi < bx && pk < bz) {
                     const bool l = pj > 0 && smat[(pk * by + pj - 1) * bx + pi] != 0xFF;
-                    if (l || (pj < by && smat[(pk * by + pj) * bx + pi] != 0xFF)) row[4] = *hy_ptr(I, Fd, gi, gj, gk);
+                    if (l || (pj < by && smat[(pk * by + pj) * bx + pi] != 0xFF)) row[4] = sH[nfx + (pk * (by + 1) + pj) * bx + pi];
                 }
                 if (pi < bx && pj < by) {
                     const bool l = pk > 0 && smat[((pk - 1) * by + pj) * bx + pi] != 0xFF;
-                    if (l || (pk < bz && smat[(pk * by + pj) * bx + pi] != 0xFF)) row[5] = *hz_ptr(I, Fd, gi, gj, gk);
+                    if (l || (pk < bz && smat[(pk * by + pj) * bx + pi] != 0xFF)) row[5] = sH[nfx + nfy + (pk * by + pj) * bx + pi];
                 }
                 if (pi < bx && pj < by && pk < bz) {
                     const int vc = (pk * by + pj) * bx + pi;
                     const int m = smat[vc];
                     if (m != 0xFF) {
                         // M = Ms h + R^T m, in FP64
-                        const double mx = sM[vc], my = sM[Vm + vc], mz = sM[2 * Vm + vc];
+                        const double mx = sM[vc], my = sM[V + vc], mz = sM[2 * V + vc];
                         const double Ms = I->mm[m].Ms;
                         for (int d = 0; d < 3; ++d)
                             row[6 + d] = Ms * I->u[d] + (double)R[d] * mx + (double)R[3 + d] * my + (double)R[6 + d] * mz;
@@ -465,10 +505,20 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
         }
         __syncthreads();
     }
+    // results: the magnetic faces of the output buffer (and far-wall arrays), m
+    for (int f = tid; f < nf; f += nth) {
+        int a, fi, fj, fk, vl, vr;
+        face_decode(f, bx, by, bz, a, fi, fj, fk, vl, vr);
+        const bool own = (vl >= 0 && smat[vl] != 0xFF) || (vr >= 0 && smat[vr] != 0xFF);
+        if (!own) continue;
+        const int i = C.x0 + fi, j = C.y0 + fj, k = C.z0 + fk;
+        float *out = a == 0 ? hx_ptr(I, Fd, i, j, k) : (a == 1 ? hy_ptr(I, Fd, i, j, k) : hz_ptr(I, Fd, i, j, k));
+        *out = sH[f];
+    }
     for (int v = tid; v < V; v += nth) {
         C.m[v] = sM[v];
-        C.m[V + v] = sM[Vm + v];
-        C.m[2 * V + v] = sM[2 * Vm + v];
+        C.m[V + v] = sM[V + v];
+        C.m[2 * V + v] = sM[2 * V + v];
     }
     if (FUSED) {
         const double s = block_sum(eacc, sredd);
@@ -478,218 +528,309 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
 }
 
 // ---------------------------------------------------------- fused step
-// 4-byte asynchronous global -> shared copy; src_bytes 0 writes a zero and
-// reads nothing (the source pointer given is still a valid address).
-__device__ __forceinline__ void cp_async4(void *sdst, const void *gsrc, int src_bytes)
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *b, unsigned count)
 {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gsrc), "r"(src_bytes) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)), "r"(count) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-struct FusedSmem {
-    float h[3][3][kHN];     // H^{n+1/2} planes k-1, k, k+1 (ring of three), halo tile
-    float e[2][3][kEN];     // E^{n+1} planes k-1, k (ring of two), extended tile
-    float en[2][3][kEN];    // E^n planes k, k+1, extended tile
-    uint16_t c[3][kEN];     // class ids, planes k-1, k, k+1
-};
-
-template <typename ClsT>
-__global__ void __launch_bounds__(kFT, 2) step_kernel(LaunchSet L)
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, unsigned bytes)
 {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    FusedSmem &S = *reinterpret_cast<FusedSmem *>(smraw);
-    __shared__ double sred[kFT / 32];
-    __shared__ int s_last;
-    const int tid = threadIdx.x;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase with the given parity: false after 2^22 polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, unsigned parity)
+{
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try_wait(b, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void tmap_acquire(const CUtensorMap *tm)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(tm) : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *tm, int c0, int c1, int c2, int c3, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(tm), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *tm, int c0, int c1, int c2, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(tm), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// One CTA per task: column (tx, ty) of kSX x kSY cells, planes [k0, k1).  The
+// CTA walks the items k = k0-1 (H only, for the curl of plane k0), k0, ..., k1
+// (the plane above, for E^{n+1} there; zeros beyond the grid).  Item q lives
+// in stage q % kNS.  Per item: E^{n+1} of plane k at the tile's own cells, one
+// barrier, then H of plane k-1 and E^{n+1} of plane k at the halo edges that
+// the next item's H update reads (Ex and Ez of the row above the tile, Ey and
+// Ez of the column beyond it).  After the barrier of item q the stage of item
+// q-2 has no readers left and receives item q + kNS - 2.  The tensor maps
+// zero-fill everything outside the grid and class 0 has zero coefficients,
+// so cells beyond the far walls get E^{n+1} = 0 without a branch.
+template <typename ClsT, bool STAB>
+__global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
+{
+    extern __shared__ __align__(128) unsigned char stg[];
+    __shared__ uint64_t bar[kNS];
+    __shared__ float4 stab[STAB ? 3 * kTabMax : 1];
+    __shared__ double sred[kST / 32];
+    __shared__ int s_last, s_abort;
+    constexpr int CBX = sizeof(ClsT) == 1 ? kCBX8 : kCBX16;
+    constexpr unsigned kClsBytes = CBX * kEBY * sizeof(ClsT);
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const long long n = *(volatile long long *)&L.ctl->step;
     const int t = blockIdx.x;
     const Inst *I = L.insts + L.ftile_inst[t];
     const int lt = t - I->ftile_off;
     const int tx = lt % I->fntx, ty = (lt / I->fntx) % I->fnty, tz = lt / (I->fntx * I->fnty);
     const int nx = I->nx, ny = I->ny, nz = I->nz, px = I->px;
-    const long long plane = I->plane;
-    const int i0 = tx * kFX, j0 = ty * kFY, k0 = tz * I->fkc;
-    const int k1 = min(k0 + I->fkc, nz);
-    const int kend = k1 < nz ? k1 : nz;
-    const float *__restrict__ Fs = I->F[L.src][0];   // component c at Fs + c * fs
-    float *__restrict__ Fd = I->F[L.dst][0];
+    const unsigned plane = (unsigned)I->plane;
     const long long fs = I->fstride;
-    const ClsT *__restrict__ cls = static_cast<const ClsT *>(I->cls);
+    const int i0 = tx * kSX, j0 = ty * kSY, k0 = tz * I->fkc;
+    const int k1 = min(k0 + I->fkc, nz);
+    const int nitems = k1 - k0 + 2;
     const float4 *__restrict__ ctab = I->ctab;
     const bool has_mag = I->nmag > 0;
     const float idx = I->idx, idy = I->idy, idz = I->idz, ch = I->ch;
+    const CUtensorMap *tmH = &I->tm[TM_H0 + L.src], *tmE = &I->tm[TM_E0 + L.src], *tmC = &I->tm[TM_CLS];
+    auto tab = [&](int i) -> float4 {
+        if constexpr (STAB) return stab[i];
+        else return __ldg(ctab + i);
+    };
+
+    int issued = 0;   // items whose loads were issued (thread 0)
+    auto issue = [&](int q) {
+        const int k = k0 - 1 + q;
+        unsigned char *base = stg + (q % kNS) * kStageBytes;
+        uint64_t *b = &bar[q % kNS];
+        if (q == 0) {
+            mbar_expect_tx(b, kStageH);
+            tma_load_4d(base + kStageHOff, tmH, i0 - 4, j0 - 1, k, 3, b);
+        } else {
+            mbar_expect_tx(b, kStageH + kStageE + kClsBytes);
+            tma_load_4d(base + kStageHOff, tmH, i0 - 4, j0 - 1, k, 3, b);
+            tma_load_4d(base + kStageEOff, tmE, i0, j0, k, 0, b);
+            tma_load_3d(base + kStageCOff, tmC, i0, j0, k, b);
+        }
+        issued = q + 1;
+    };
+    if (tid == 0) {
+        for (int s = 0; s < kNS; ++s) mbar_init(&bar[s], 1);
+        fence_barrier_init();
+        fence_proxy_async();
+        s_abort = 0;
+        tmap_acquire(tmH);
+        tmap_acquire(tmE);
+        tmap_acquire(tmC);
+        for (int q = 0; q < min(kNS - 1, nitems); ++q) issue(q);
+    }
+    if constexpr (STAB)
+        for (int c = tid; c < 3 * I->nclass; c += kST) stab[c] = __ldg(ctab + c);
 
     // sources and probes whose column lies in this tile's extended / interior area
     unsigned smask = 0, pmask = 0;
     for (int s = 0; s < I->nsrc; ++s) {
         const int si = I->src[s][1] - i0, sj = I->src[s][2] - j0;
-        if (si >= 0 && si <= kFX && sj >= 0 && sj <= kFY) smask |= 1u << s;
+        if (si >= 0 && si <= kSX && sj >= 0 && sj <= kSY) smask |= 1u << s;
     }
     for (int p = 0; p < I->nprobe; ++p) {
         const int pi = I->probe[p][0] - i0, pj = I->probe[p][1] - j0;
-        if (pi >= 0 && pi < kFX && pj >= 0 && pj < kFY && I->probe[p][2] >= k0 && I->probe[p][2] < k1) pmask |= 1u << p;
+        if (pi >= 0 && pi < kSX && pj >= 0 && pj < kSY && I->probe[p][2] >= k0 && I->probe[p][2] < k1) pmask |= 1u << p;
     }
     const double tn = ((double)n + 0.5) * I->dt;
+    // source current (FP64 time evaluation) subtracted from one curl component
+    auto add_src = [&](int i, int j, int k, float &cx, float &cy, float &cz) {
+        for (int so = 0; so < I->nsrc; ++so)
+            if (((smask >> so) & 1u) && I->src[so][1] == i && I->src[so][2] == j && I->src[so][3] == k) {
+                const float J = (float)source_value(I->srcp[so], tn);
+                if (I->src[so][0] == 0) cx = __fsub_rn(cx, J);
+                else if (I->src[so][0] == 1) cy = __fsub_rn(cy, J);
+                else cz = __fsub_rn(cz, J);
+            }
+    };
 
-    int rc[kEQ];              // class ids of the next plane, on their way to shared memory
-
-    // H of plane kk (zero outside the grid) into S.h[b], asynchronously
-#define FL_LOAD_H(kk, b)                                                                                        \
-    _Pragma("unroll") for (int q = 0; q < kHQ; ++q) {                                                           \
-        const int p = tid + q * kFT;                                                                            \
-        if (p < kHN) {                                                                                          \
-            const int hi = i0 - 1 + p % kHX, hj = j0 - 1 + p / kHX;                                            \
-            const bool ok = hi >= 0 && hi < nx && hj >= 0 && hj < ny && (kk) >= 0 && (kk) < nz;               \
-            const long long o = ok ? (long long)(kk) * plane + (long long)hj * px + hi : 0;                    \
-            cp_async4(&S.h[b][0][p], Fs + 3 * fs + o, ok ? 4 : 0);                                              \
-            cp_async4(&S.h[b][1][p], Fs + 4 * fs + o, ok ? 4 : 0);                                              \
-            cp_async4(&S.h[b][2][p], Fs + 5 * fs + o, ok ? 4 : 0);                                              \
-        }                                                                                                       \
-    }
-    // E^n of plane kk into S.en[kk & 1] asynchronously, class ids into rc
-#define FL_LOAD_E(kk)                                                                                           \
-    _Pragma("unroll") for (int q = 0; q < kEQ; ++q) {                                                           \
-        const int p = tid + q * kFT;                                                                            \
-        rc[q] = 0;                                                                                              \
-        if (p < kEN) {                                                                                          \
-            const int ei = i0 + p % kEX, ej = j0 + p / kEX;                                                     \
-            const bool ok = ei < nx && ej < ny;                                                                 \
-            const long long o = ok ? (long long)(kk) * plane + (long long)ej * px + ei : 0;                    \
-            cp_async4(&S.en[(kk) & 1][0][p], Fs + o, ok ? 4 : 0);                                               \
-            cp_async4(&S.en[(kk) & 1][1][p], Fs + fs + o, ok ? 4 : 0);                                          \
-            cp_async4(&S.en[(kk) & 1][2][p], Fs + 2 * fs + o, ok ? 4 : 0);                                      \
-            if (ok) rc[q] = (int)cls[o];                                                                        \
-        }                                                                                                       \
-    }
-#define FL_STORE_C(b)                                                                                           \
-    _Pragma("unroll") for (int q = 0; q < kEQ; ++q) {                                                           \
-        const int p = tid + q * kFT;                                                                            \
-        if (p < kEN) S.c[b][p] = (uint16_t)rc[q];                                                               \
-    }
-
-    // prologue: H of plane k0-1 (zero below the grid) and H, E^n, classes of plane k0
-    FL_LOAD_H(k0 - 1, (k0 + 2) % 3);
-    FL_LOAD_H(k0, k0 % 3);
-    FL_LOAD_E(k0);
-    cp_async_commit();
-    cp_async_wait_all();
-    FL_STORE_C(k0 % 3);
+    // this thread's cells: (xi, yi) and (xi, yi + 4); output pointers per component
+    const int xi = (w & 1) * 32 + lane, yi = w >> 1;
+    const int gi = i0 + xi, gj = j0 + yi;
+    const bool in0 = gi < nx && gj < ny, in1 = gi < nx && gj + 4 < ny;
+    const unsigned ob = (unsigned)gj * (unsigned)px + (unsigned)gi, ob1 = ob + 4u * (unsigned)px;
+    float *const F0 = I->F[L.dst][0];
+    float *const Fx = F0, *const Fy = F0 + fs, *const Fz = F0 + 2 * fs;
+    float *const Gx = F0 + 3 * fs, *const Gy = F0 + 4 * fs, *const Gz = F0 + 5 * fs;
+    // halo role: warps 0-1 Ex and warps 2-3 Ez of row kSY (x = 0..63); warp 4
+    // lanes 0-7 Ey and lanes 8-15 Ez of column kSX (y = 0..7)
+    const int xr = (w < 4) ? (tid & 63) : kSX;
+    const int yr = (w < 4) ? kSY : (lane & 7);
+    const int cr = (w < 2) ? 0 : (w < 4 ? 2 : (lane < 8 ? 1 : 2));
+    const bool halo = w < 4 || (w == 4 && lane < 16);
     __syncthreads();
 
     float acc = 0.f;
-    for (int k = k0; k <= kend; ++k) {
-        const bool pre = k + 1 <= kend && k + 1 < nz;
-        if (pre) {
-            FL_LOAD_H(k + 1, (k + 1) % 3);
-            FL_LOAD_E(k + 1);
-            cp_async_commit();
+    int consumed = 0;
+    for (int q = 0; q < nitems; ++q) {
+        const int s = q % kNS, sp = (q + kNS - 1) % kNS;
+        if (!mbar_wait(&bar[s], (unsigned)(q / kNS) & 1u)) {
+            atomicOr(&L.ctl->status, ST_TIMEOUT);
+            s_abort = 1;
         }
-        const int b = k % 3, bm = (k + 2) % 3, eb = k & 1;
-        // ---- E^{n+1} of plane k on the extended tile
+        consumed = q + 1;
+        const int k = k0 - 1 + q;
+        unsigned char *cur = stg + s * kStageBytes, *prv = stg + sp * kStageBytes;
+        const float *Hc = reinterpret_cast<const float *>(cur + kStageHOff);
+        const float *Hp = reinterpret_cast<const float *>(prv + kStageHOff);
+        float *Ec = reinterpret_cast<float *>(cur + kStageEOff);
+        const ClsT *Cc = reinterpret_cast<const ClsT *>(cur + kStageCOff);
+        if (q > 0) {
+            // ---- E^{n+1} of plane k at the tile's cells, in place over E^n
+            float ve[2][3];
+            float4 Qe[2];
 #pragma unroll
-        for (int q = 0; q < kEQ; ++q) {
-            const int p = tid + q * kFT;
-            if (p >= kEN) continue;
-            const int px_ = p % kEX, py_ = p / kEX;
-            const int i = i0 + px_, j = j0 + py_;
-            float ex = 0.f, ey = 0.f, ez = 0.f;
-            if (k < nz && i < nx && j < ny) {
-                const int hp = (py_ + 1) * kHX + px_ + 1;
-                const float hx = S.h[b][0][hp], hy = S.h[b][1][hp], hz = S.h[b][2][hp];
-                const float hz_jm = S.h[b][2][hp - kHX], hx_jm = S.h[b][0][hp - kHX];
-                const float hz_im = S.h[b][2][hp - 1], hy_im = S.h[b][1][hp - 1];
-                const float hx_km = S.h[bm][0][hp], hy_km = S.h[bm][1][hp];
-                float cx = (hz - hz_jm) * idy - (hy - hy_km) * idz;
-                float cy = (hx - hx_km) * idz - (hz - hz_im) * idx;
-                float cz = (hy - hy_im) * idx - (hx - hx_jm) * idy;
-                if (smask) {
-                    for (int s = 0; s < I->nsrc; ++s)
-                        if (((smask >> s) & 1u) && I->src[s][1] == i && I->src[s][2] == j && I->src[s][3] == k) {
-                            const float J = (float)source_value(I->srcp[s], tn);
-                            if (I->src[s][0] == 0) cx -= J;
-                            else if (I->src[s][0] == 1) cy -= J;
-                            else cz -= J;
-                        }
-                }
-                const int c = S.c[b][p];
-                const float4 A = __ldg(ctab + 3 * c);
-                const float4 B = __ldg(ctab + 3 * c + 1);
-                ex = A.x * S.en[eb][0][p] + B.x * cx;
-                ey = A.y * S.en[eb][1][p] + B.y * cy;
-                ez = A.z * S.en[eb][2][p] + B.z * cz;
-                if (px_ < kFX && py_ < kFY && k < k1) {
-                    const long long o = (long long)k * plane + (long long)j * px + i;
-                    Fd[o] = ex;
-                    Fd[fs + o] = ey;
-                    Fd[2 * fs + o] = ez;
-                    if (L.energy) {
-                        const float4 Q = __ldg(ctab + 3 * c + 2);
-                        acc += Q.x * ex * ex + Q.y * ey * ey + Q.z * ez * ez;
-                    }
-                    if (pmask) {
-                        for (int pp = 0; pp < I->nprobe; ++pp)
-                            if (((pmask >> pp) & 1u) && I->probe[pp][0] == i && I->probe[pp][1] == j && I->probe[pp][2] == k) {
-                                double *row = I->probe_buf + ((long long)(n % I->cap) * I->nprobe + pp) * 9;
-                                row[0] = ex;
-                                row[1] = ey;
-                                row[2] = ez;
-                            }
-                    }
+            for (int r = 0; r < 2; ++r) {
+                const int y = yi + 4 * r;
+                const int hp = (y + 1) * kHBX + xi + 4;
+                const float hx = Hc[hp], hy = Hc[kHC + hp], hz = Hc[2 * kHC + hp];
+                const float hz_jm = Hc[2 * kHC + hp - kHBX], hx_jm = Hc[hp - kHBX];
+                const float hz_im = Hc[2 * kHC + hp - 1], hy_im = Hc[kHC + hp - 1];
+                const float hx_km = Hp[hp], hy_km = Hp[kHC + hp];
+                float cx = curl2(hz, hz_jm, idy, hy, hy_km, idz);
+                float cy = curl2(hx, hx_km, idz, hz, hz_im, idx);
+                float cz = curl2(hy, hy_im, idx, hx, hx_jm, idy);
+                if (smask) add_src(gi, j0 + y, k, cx, cy, cz);
+                const int ep = y * kEBX + xi;
+                const int c = (int)Cc[y * CBX + xi];
+                const float4 A = tab(3 * c), B = tab(3 * c + 1);
+                Qe[r] = tab(3 * c + 2);
+                ve[r][0] = e_next(A.x, Ec[ep], B.x, cx);
+                ve[r][1] = e_next(A.y, Ec[kEC + ep], B.y, cy);
+                ve[r][2] = e_next(A.z, Ec[2 * kEC + ep], B.z, cz);
+            }
+            const bool kin = k < k1;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int ep = (yi + 4 * r) * kEBX + xi;
+                Ec[ep] = ve[r][0];
+                Ec[kEC + ep] = ve[r][1];
+                Ec[2 * kEC + ep] = ve[r][2];
+                if (kin && (r ? in1 : in0)) {
+                    const unsigned o = (unsigned)k * plane + (r ? ob1 : ob);
+                    Fx[o] = ve[r][0];
+                    Fy[o] = ve[r][1];
+                    Fz[o] = ve[r][2];
+                    acc += Qe[r].x * ve[r][0] * ve[r][0] + Qe[r].y * ve[r][1] * ve[r][1] + Qe[r].z * ve[r][2] * ve[r][2];
                 }
             }
-            S.e[eb][0][p] = ex;
-            S.e[eb][1][p] = ey;
-            S.e[eb][2][p] = ez;
-        }
-        __syncthreads();
-        // ---- H^{n+1} and H^{n+3/2} of plane k-1 on the interior
-        if (k > k0) {
-            const int kh = k - 1, hb = kh % 3, e0 = kh & 1;
+            if (pmask && kin) {
+                for (int pp = 0; pp < I->nprobe; ++pp)
 #pragma unroll
-            for (int q = 0; q < kIQ; ++q) {
-                const int p = tid + q * kFT;
-                const int pi = p % kFX, pj = p / kFX;
-                const int i = i0 + pi, j = j0 + pj;
-                if (i >= nx || j >= ny) continue;
-                const int ep = pj * kEX + pi;
-                const float ex = S.e[e0][0][ep], ey = S.e[e0][1][ep], ez = S.e[e0][2][ep];
-                const float ex_jp = S.e[e0][0][ep + kEX], ez_jp = S.e[e0][2][ep + kEX];
-                const float ey_ip = S.e[e0][1][ep + 1], ez_ip = S.e[e0][2][ep + 1];
-                const float ex_kp = S.e[eb][0][ep], ey_kp = S.e[eb][1][ep];
-                const float cx = (ez_jp - ez) * idy - (ey_kp - ey) * idz;
-                const float cy = (ex_kp - ex) * idz - (ez_ip - ez) * idx;
-                const float cz = (ey_ip - ey) * idx - (ex_jp - ex) * idy;
-                uint32_t fl = 0;
-                if (has_mag) fl = __float_as_uint(__ldg(ctab + 3 * (int)S.c[hb][ep]).w);
-                const int hp = (pj + 1) * kHX + pi + 1;
-                const long long o = (long long)kh * plane + (long long)j * px + i;
-                float hmx = 0.f, hmy = 0.f, hmz = 0.f;
-                if (!(fl & CF_MAG_HX)) { hmx = S.h[hb][0][hp] - ch * cx; Fd[3 * fs + o] = hmx - ch * cx; }
-                if (!(fl & CF_MAG_HY)) { hmy = S.h[hb][1][hp] - ch * cy; Fd[4 * fs + o] = hmy - ch * cy; }
-                if (!(fl & CF_MAG_HZ)) { hmz = S.h[hb][2][hp] - ch * cz; Fd[5 * fs + o] = hmz - ch * cz; }
-                if (L.energy) acc += (float)(0.5 * kMu0) * (hmx * hmx + hmy * hmy + hmz * hmz);
-                if (pmask) {
-                    for (int pp = 0; pp < I->nprobe; ++pp)
-                        if (((pmask >> pp) & 1u) && I->probe[pp][0] == i && I->probe[pp][1] == j && I->probe[pp][2] == kh) {
+                    for (int r = 0; r < 2; ++r)
+                        if (((pmask >> pp) & 1u) && I->probe[pp][0] == gi && I->probe[pp][1] == gj + 4 * r && I->probe[pp][2] == k) {
                             double *row = I->probe_buf + ((long long)(n % I->cap) * I->nprobe + pp) * 9;
-                            if (!(fl & CF_MAG_HX)) row[3] = hmx;
-                            if (!(fl & CF_MAG_HY)) row[4] = hmy;
-                            if (!(fl & CF_MAG_HZ)) row[5] = hmz;
+                            row[0] = ve[r][0];
+                            row[1] = ve[r][1];
+                            row[2] = ve[r][2];
                         }
-                }
             }
         }
-        if (pre) {
-            cp_async_wait_all();
-            FL_STORE_C((k + 1) % 3);
-        }
+        // every generic write to the stage of item q-2 is ordered before the
+        // TMA that overwrites it
+        fence_proxy_async();
         __syncthreads();
+        if (s_abort) break;
+        if (tid == 0 && q >= 1 && q + kNS - 2 < nitems) issue(q + kNS - 2);
+        // ---- H^{n+1} and H^{n+3/2} of plane k-1 at the tile's cells
+        if (q > 1) {
+            const unsigned kh = (unsigned)(k - 1);
+            const float *Ep = reinterpret_cast<const float *>(prv + kStageEOff);
+            const ClsT *Cp = reinterpret_cast<const ClsT *>(prv + kStageCOff);
+            float hv[2][3];
+            uint32_t fl[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int y = yi + 4 * r;
+                const int ep = y * kEBX + xi;
+                const float ex = Ep[ep], ey = Ep[kEC + ep], ez = Ep[2 * kEC + ep];
+                const float ex_jp = Ep[ep + kEBX], ez_jp = Ep[2 * kEC + ep + kEBX];
+                const float ey_ip = Ep[kEC + ep + 1], ez_ip = Ep[2 * kEC + ep + 1];
+                const float ex_kp = Ec[ep], ey_kp = Ec[kEC + ep];
+                const float cx = curl2(ez_jp, ez, idy, ey_kp, ey, idz);
+                const float cy = curl2(ex_kp, ex, idz, ez_ip, ez, idx);
+                const float cz = curl2(ey_ip, ey, idx, ex_jp, ex, idy);
+                fl[r] = has_mag ? __float_as_uint(tab(3 * (int)Cp[y * CBX + xi]).w) : 0u;
+                const int hp = (y + 1) * kHBX + xi + 4;
+                hv[r][0] = __fsub_rn(Hp[hp], __fmul_rn(ch, cx));
+                hv[r][1] = __fsub_rn(Hp[kHC + hp], __fmul_rn(ch, cy));
+                hv[r][2] = __fsub_rn(Hp[2 * kHC + hp], __fmul_rn(ch, cz));
+                // second half-push with the same curl
+                const float ddx = __fmul_rn(ch, cx), ddy = __fmul_rn(ch, cy), ddz = __fmul_rn(ch, cz);
+                if (fl[r] & CF_MAG_HX) hv[r][0] = 0.f;
+                if (fl[r] & CF_MAG_HY) hv[r][1] = 0.f;
+                if (fl[r] & CF_MAG_HZ) hv[r][2] = 0.f;
+                const bool inr = r ? in1 : in0;
+                if (inr) {
+                    const unsigned o = kh * plane + (r ? ob1 : ob);
+                    if (!(fl[r] & CF_MAG_HX)) Gx[o] = __fsub_rn(hv[r][0], ddx);
+                    if (!(fl[r] & CF_MAG_HY)) Gy[o] = __fsub_rn(hv[r][1], ddy);
+                    if (!(fl[r] & CF_MAG_HZ)) Gz[o] = __fsub_rn(hv[r][2], ddz);
+                    acc += (float)(0.5 * kMu0) * (hv[r][0] * hv[r][0] + hv[r][1] * hv[r][1] + hv[r][2] * hv[r][2]);
+                }
+            }
+            if (pmask) {
+                for (int pp = 0; pp < I->nprobe; ++pp)
+#pragma unroll
+                    for (int r = 0; r < 2; ++r)
+                        if (((pmask >> pp) & 1u) && I->probe[pp][0] == gi && I->probe[pp][1] == gj + 4 * r &&
+                            I->probe[pp][2] == (int)kh) {
+                            double *row = I->probe_buf + ((long long)(n % I->cap) * I->nprobe + pp) * 9;
+                            if (!(fl[r] & CF_MAG_HX)) row[3] = hv[r][0];
+                            if (!(fl[r] & CF_MAG_HY)) row[4] = hv[r][1];
+                            if (!(fl[r] & CF_MAG_HZ)) row[5] = hv[r][2];
+                        }
+            }
+        }
+        // ---- E^{n+1} of plane k at the halo edges read by the next item
+        if (q > 0 && q + 1 < nitems && halo) {
+            const int hp = (yr + 1) * kHBX + xr + 4;
+            float cu;
+            if (cr == 0) cu = curl2(Hc[2 * kHC + hp], Hc[2 * kHC + hp - kHBX], idy, Hc[kHC + hp], Hp[kHC + hp], idz);
+            else if (cr == 1) cu = curl2(Hc[hp], Hp[hp], idz, Hc[2 * kHC + hp], Hc[2 * kHC + hp - 1], idx);
+            else cu = curl2(Hc[kHC + hp], Hc[kHC + hp - 1], idx, Hc[hp], Hc[hp - kHBX], idy);
+            if (smask) {
+                float c3[3] = {0.f, 0.f, 0.f};
+                c3[cr] = cu;
+                add_src(i0 + xr, j0 + yr, k, c3[0], c3[1], c3[2]);
+                cu = c3[cr];
+            }
+            const int c = (int)Cc[yr * CBX + xr];
+            const float4 A = tab(3 * c), B = tab(3 * c + 1);
+            const float ca = cr == 0 ? A.x : (cr == 1 ? A.y : A.z);
+            const float cb = cr == 0 ? B.x : (cr == 1 ? B.y : B.z);
+            const int ep = cr * kEC + yr * kEBX + xr;
+            Ec[ep] = e_next(ca, Ec[ep], cb, cu);
+        }
     }
-#undef FL_LOAD_H
-#undef FL_LOAD_E
-#undef FL_STORE_C
+    // after a timed-out wait: wait (bounded) for the copies still in flight
+    if (tid == 0)
+        for (int q = consumed; q < issued; ++q) mbar_wait(&bar[q % kNS], (unsigned)(q / kNS) & 1u);
     if (L.energy) {
         const double s = block_sum((double)acc, sred);
         if (tid == 0) L.part_f[t] = s;
@@ -707,15 +848,49 @@ int h_half_blocks_per_sm(bool cls16)
     return nb > 0 ? nb : 1;
 }
 
-static size_t mag_smem(const LaunchSet &L) { return (size_t)12 * L.vmax * sizeof(float) + (size_t)L.vmax; }
+static constexpr int kStepSmem = kNS * kStageBytes;
+
+static cudaError_t step_attrs()
+{
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<uint8_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStepSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<uint8_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStepSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<uint16_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStepSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<uint16_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStepSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(mag_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMagSmemMax);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(mag_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMagSmemMax);
+    done = e == cudaSuccess;
+    return e;
+}
+
+int step_blocks_per_sm(bool cls16)
+{
+    if (step_attrs() != cudaSuccess) return 0;
+    int nb = 0;
+    if (cls16) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<uint16_t, true>, kST, kStepSmem);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<uint8_t, true>, kST, kStepSmem);
+    return nb;
+}
+
+static void launch_edges(const LaunchSet &L, bool advance, cudaStream_t s)
+{
+    const dim3 grid((L.emax + 255) / 256, L.ncomp);
+    if (advance) {
+        if (L.cls16) mag_edge_kernel<true, uint16_t><<<grid, 256, 0, s>>>(L);
+        else mag_edge_kernel<true, uint8_t><<<grid, 256, 0, s>>>(L);
+    } else {
+        mag_edge_kernel<false, uint8_t><<<grid, 256, 0, s>>>(L);
+    }
+}
 
 cudaError_t launch_half(const LaunchSet &L, cudaStream_t s)
 {
+    cudaError_t e = step_attrs();
+    if (e != cudaSuccess) return e;
     if (L.ncomp) {
-        const size_t sm = mag_smem(L);
-        cudaError_t e = cudaFuncSetAttribute(mag_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        mag_kernel<false><<<L.ncomp, kMagThreads, sm, s>>>(L);
+        launch_edges(L, false, s);
+        mag_kernel<false><<<L.ncomp, kMagThreads, L.mag_smem, s>>>(L);
     }
     const dim3 blk(kTX, kTY);
     if (L.cls16) h_half_kernel<uint16_t><<<L.grid_h, blk, 0, s>>>(L);
@@ -726,26 +901,25 @@ cudaError_t launch_half(const LaunchSet &L, cudaStream_t s)
 cudaError_t launch_step(const LaunchSet &L, cudaStream_t s, cudaStream_t s_mag, cudaEvent_t ev_fork, cudaEvent_t ev_join,
                         cudaEvent_t *prof)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(step_kernel<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FusedSmem));
-        cudaFuncSetAttribute(step_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FusedSmem));
-        attr_set = true;
-    }
+    cudaError_t e = step_attrs();
+    if (e != cudaSuccess) return e;
     if (L.ncomp) {
-        const size_t sm = mag_smem(L);
-        cudaError_t e = cudaFuncSetAttribute(mag_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
         cudaEventRecord(ev_fork, s);
         cudaStreamWaitEvent(s_mag, ev_fork, 0);
         if (prof) cudaEventRecord(prof[2], s_mag);
-        mag_kernel<true><<<L.ncomp, kMagThreads, sm, s_mag>>>(L);
+        launch_edges(L, true, s_mag);
+        mag_kernel<true><<<L.ncomp, kMagThreads, L.mag_smem, s_mag>>>(L);
         if (prof) cudaEventRecord(prof[3], s_mag);
         cudaEventRecord(ev_join, s_mag);
     }
     if (prof) cudaEventRecord(prof[0], s);
-    if (L.cls16) step_kernel<uint16_t><<<L.nftiles, kFT, sizeof(FusedSmem), s>>>(L);
-    else step_kernel<uint8_t><<<L.nftiles, kFT, sizeof(FusedSmem), s>>>(L);
+    if (L.cls16) {
+        if (L.stab) step_kernel<uint16_t, true><<<L.nftiles, kST, kStepSmem, s>>>(L);
+        else step_kernel<uint16_t, false><<<L.nftiles, kST, kStepSmem, s>>>(L);
+    } else {
+        if (L.stab) step_kernel<uint8_t, true><<<L.nftiles, kST, kStepSmem, s>>>(L);
+        else step_kernel<uint8_t, false><<<L.nftiles, kST, kStepSmem, s>>>(L);
+    }
     if (prof) cudaEventRecord(prof[1], s);
     if (L.ncomp) cudaStreamWaitEvent(s, ev_join, 0);
     return cudaGetLastError();
