@@ -180,8 +180,11 @@ def main():
 
     K, Wm = args.steps, max(args.warmup, 3)
     w = W.strip_resonator(steps=K)
+    # a stream of our own, current for the library handles created below, so
+    # that the timing events sit on the stream every step is launched on
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     sim = pkg.from_workload(w, probe_capacity=K + Wm + 16)
-    stream = torch.cuda.current_stream()
 
     sim.step(Wm)
     sim.sync()

@@ -190,8 +190,11 @@ int fdtd_llg_load_state(fdtd_llg_t h, const void *buf, size_t size);
 /* Per-kernel device time, measured with CUDA events that the library records
  * around every launch while profiling is on (the kernels themselves are
  * unchanged).  Kinds: [0] the field sweep of a step (E push and H
- * half-push pair of every non-magnetic face), [1] the magnetic-region kernel
- * (runs concurrently with [0] on a second stream), [2] unused. */
+ * half-push pair of every non-magnetic face), [1] the magnetic-region kernel,
+ * [2] unused.  Outside profiling the two kernels of a step run side by side
+ * (the sweep is a programmatic dependent launch of the magnet kernel); the
+ * events between them make them run one after the other, so each is timed
+ * alone. */
 typedef struct {
     int64_t launches[3];
     double ms[3];              /* summed device time of those launches (ms)     */
@@ -203,6 +206,30 @@ int fdtd_llg_set_profiling(fdtd_llg_t h, int32_t on);
 /* Synchronise, add up the recorded events into *out; reset != 0 clears the
  * record afterwards. */
 int fdtd_llg_read_profile(fdtd_llg_t h, fdtd_llg_profile *out, int32_t reset);
+
+/* Tiling of the field sweep.  Each CTA of the sweep marches a column of
+ * 64 x 8 cells through `planes` z-planes (clamped to each instance's nz), so
+ * the sweep launches sum over instances of ceil(nx/64) ceil(ny/8)
+ * ceil(nz/planes) CTAs.  planes = 0 (the default) lets the library choose
+ * from a model of the CTA waves the GPU runs.  The tiling changes only the
+ * order in which the energy partial sums are added: fields and probe samples
+ * are the same to the bit.  Takes effect at the next step.  Errors:
+ * FDTD_E_INVAL (planes < 0, or a member handle). */
+int fdtd_llg_set_tiling(fdtd_llg_t h, int32_t planes);
+
+/* The z-planes per sweep task in effect (resolving planes = 0); *planes is
+ * 0 before the first step or sync after materials were set. */
+int fdtd_llg_get_tiling(fdtd_llg_t h, int32_t *planes);
+
+/* Autotuner of the tiling.  Runs trial_steps real steps (they advance the
+ * simulation, fill the probe and energy rings and count in the step number)
+ * with each of a fixed list of candidate plane counts plus the model's
+ * choice, timed with CUDA events on the handle's stream, and keeps the
+ * fastest, which it returns in *planes (may be NULL).  The handle then holds
+ * that tiling as if set with fdtd_llg_set_tiling.  Synchronises the stream.
+ * Errors: FDTD_E_INVAL (trial_steps < 1, a member handle), those of
+ * fdtd_llg_step. */
+int fdtd_llg_autotune(fdtd_llg_t h, int32_t trial_steps, int32_t *planes);
 
 /* E push that allocates nothing.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory (code running

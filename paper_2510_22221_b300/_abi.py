@@ -69,6 +69,9 @@ SIGNATURES = {
     "fdtd_llg_load_state": (C.c_int, [_vp, _vp, C.c_size_t]),
     "fdtd_llg_set_profiling": (C.c_int, [_vp, C.c_int32]),
     "fdtd_llg_read_profile": (C.c_int, [_vp, C.POINTER(Profile), C.c_int32]),
+    "fdtd_llg_set_tiling": (C.c_int, [_vp, C.c_int32]),
+    "fdtd_llg_get_tiling": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
+    "fdtd_llg_autotune": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_int32)]),
     "fdtd_llg_e_push_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.c_int32,
                                          C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
                                          _vp, _vp]),

@@ -58,8 +58,6 @@ struct Sim {
     fdtd_llg_config cfg{};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    cudaStream_t s_mag = nullptr;     // magnetic regions run here, concurrently with the field sweep
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int cur = 0;                      // field buffer holding the present state
     // device control and descriptors
     Inst *d_insts = nullptr;
@@ -68,8 +66,10 @@ struct Sim {
     MagComp *d_comps = nullptr;
     StepCtl *d_ctl = nullptr;
     double *d_part = nullptr;         // part_e | part_h | part_m
-    int ntiles = 0, nftiles = 0, ncomp = 0, vmax = 0, emax = 0, mag_smem = 0;
+    int ntiles = 0, nftiles = 0, ncomp = 0, vmax = 0, mag_smem = 0;
     bool stab = false;                // every class table small enough for shared memory
+    int tiling = 0;                   // requested z-planes per sweep task (0: model)
+    int planes = 0;                   // z-planes per sweep task in effect
     bool cls16 = false;
     bool dirty = true;
     int nsm = 148;
@@ -118,9 +118,6 @@ struct Sim {
             else cudaFree(p);
         }
         allocs.clear();
-        if (s_mag) cudaStreamDestroy(s_mag);
-        if (ev_fork) cudaEventDestroy(ev_fork);
-        if (ev_join) cudaEventDestroy(ev_join);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -263,16 +260,6 @@ static int create_impl(const fdtd_llg_config *cfgs, int32_t n, fdtd_llg_t *out)
             return fail(nullptr, FDTD_E_CUDA, "cudaStreamCreate failed");
         }
         S->own_stream = true;
-    }
-    // the magnet kernels run beside the field sweep; at the highest priority
-    // their CTAs take the first SM slots that the sweep's CTAs free
-    int prio_lo = 0, prio_hi = 0;
-    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
-    if (cudaStreamCreateWithPriority(&S->s_mag, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
-        cudaEventCreateWithFlags(&S->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&S->ev_join, cudaEventDisableTiming) != cudaSuccess) {
-        delete S;
-        return fail(nullptr, FDTD_E_CUDA, "stream or event creation failed");
     }
     S->inst.resize(n);
     fdtd_llg_t root = new fdtd_llg_s{S, n == 1 ? 0 : -1, true};
@@ -697,16 +684,42 @@ static int encode_tensor_maps(fdtd_llg_t h, const Instance &I, Inst &d)
     return FDTD_OK;
 }
 
+// Plane count of the sweep tasks from a wave model: with `slots` CTAs resident
+// at once and tasks of about equal length, the sweep takes ceil(tasks/slots)
+// waves of (planes + 2) plane-times (two extra planes per task: the one below
+// for the curl and the one above for E^{n+1}); pick the count that keeps the
+// most slots busy per unit of work, preferring fewer extra planes on ties.
+static int model_planes(const Sim *S, int slots)
+{
+    int best = kSZ, maxnz = 1;
+    double best_eff = -1.0;
+    for (const Instance &I : S->inst) maxnz = std::max(maxnz, I.nz);
+    for (int P = 4; P <= std::max(4, std::min(maxnz, 128)); ++P) {
+        double tasks = 0, work = 0;
+        for (const Instance &I : S->inst) {
+            const int pk = std::min(P, I.nz), nch = (I.nz + pk - 1) / pk;
+            const double cols = (double)((I.nx + kSX - 1) / kSX) * ((I.ny + kSY - 1) / kSY);
+            tasks += cols * nch;
+            work += cols * (I.nz + 2.0 * nch);
+        }
+        const double waves = std::ceil(tasks / std::max(1, slots));
+        const double eff = work / (std::max(1, slots) * waves * (std::min(P, maxnz) + 2.0));
+        if (eff > best_eff * (1.0 + 1e-3)) { best_eff = eff; best = P; }
+    }
+    return best;
+}
+
 static int upload_descriptors(fdtd_llg_t h)
 {
     Sim *S = h->sim;
     if (!S->dirty) return FDTD_OK;
     CKR(h, cudaStreamSynchronize(S->stream));
+    S->planes = S->tiling > 0 ? S->tiling : model_planes(S, S->nsm * std::max(1, step_blocks_per_sm(false)));
     std::vector<Inst> hi(S->inst.size());
     std::vector<int> tile_inst, ftile_inst;
     std::vector<MagComp> comps;
     bool c16 = false;
-    int vmax = 0, emax = 0, msmem = 0;
+    int vmax = 0, msmem = 0;
     bool stab = true;
     for (size_t ii = 0; ii < S->inst.size(); ++ii) {
         Instance &I = S->inst[ii];
@@ -749,7 +762,7 @@ static int upload_descriptors(fdtd_llg_t h)
         d.tile_off = (int)tile_inst.size();
         const int nt = d.ntx * d.nty * d.ntz;
         for (int t = 0; t < nt; ++t) tile_inst.push_back((int)ii);
-        d.fkc = std::min(I.nz, kSZ);
+        d.fkc = std::min(I.nz, S->planes);
         d.fntx = (I.nx + kSX - 1) / kSX; d.fnty = (I.ny + kSY - 1) / kSY; d.fntz = (I.nz + d.fkc - 1) / d.fkc;
         d.ftile_off = (int)ftile_inst.size();
         const int nft = d.fntx * d.fnty * d.fntz;
@@ -760,7 +773,6 @@ static int upload_descriptors(fdtd_llg_t h)
             C.inst = (int)ii;
             comps.push_back(C);
             vmax = std::max(vmax, C.V);
-            emax = std::max(emax, 3 * (C.bx + 1) * (C.by + 1) * (C.bz + 1));
             msmem = std::max(msmem, (int)mag_smem_bytes(C.bx, C.by, C.bz));
         }
         for (size_t m = 0; m < I.mm.size(); ++m) d.mm[m] = I.mm[m];
@@ -804,7 +816,6 @@ static int upload_descriptors(fdtd_llg_t h)
     S->nftiles = (int)ftile_inst.size();
     S->ncomp = (int)comps.size();
     S->vmax = vmax;
-    S->emax = emax;
     S->stab = stab;
     S->mag_smem = msmem;
     S->cls16 = c16;
@@ -822,7 +833,6 @@ static LaunchSet launch_set(Sim *S)
     L.comps = S->d_comps;
     L.ncomp = S->ncomp;
     L.vmax = S->vmax;
-    L.emax = S->emax;
     L.mag_smem = S->mag_smem;
     L.stab = S->stab;
     L.ctl = S->d_ctl;
@@ -864,7 +874,7 @@ extern "C" int fdtd_llg_step(fdtd_llg_t h, int64_t nsteps)
             for (auto &e : ev) e = S->take_event();
             prof = ev;
         }
-        CKR(h, launch_step(L, S->stream, S->s_mag, S->ev_fork, S->ev_join, prof));
+        CKR(h, launch_step(L, S->stream, prof));
         if (prof) {
             S->recs.push_back({0, ev[0], ev[1]});
             if (L.ncomp) S->recs.push_back({1, ev[2], ev[3]});
@@ -1163,6 +1173,70 @@ extern "C" int fdtd_llg_load_state(fdtd_llg_t h, const void *buf, size_t size)
 }
 
 // ------------------------------------------------------------- profiling
+extern "C" int fdtd_llg_set_tiling(fdtd_llg_t h, int32_t planes)
+{
+    if (!h || !h->sim) return fail(h, FDTD_E_INVAL, "null handle");
+    if (!h->owns) return fail(h, FDTD_E_INVAL, "set the tiling on the batch handle, not a member");
+    if (planes < 0) return fail(h, FDTD_E_INVAL, "planes must be >= 0");
+    if (planes != h->sim->tiling) {
+        h->sim->tiling = planes;
+        h->sim->dirty = true;
+    }
+    return FDTD_OK;
+}
+
+extern "C" int fdtd_llg_get_tiling(fdtd_llg_t h, int32_t *planes)
+{
+    if (!h || !h->sim || !planes) return fail(h, FDTD_E_INVAL, "null handle or output");
+    *planes = h->sim->dirty ? 0 : h->sim->planes;
+    return FDTD_OK;
+}
+
+extern "C" int fdtd_llg_autotune(fdtd_llg_t h, int32_t trial_steps, int32_t *planes)
+{
+    if (!h || !h->sim) return fail(h, FDTD_E_INVAL, "null handle");
+    if (!h->owns) return fail(h, FDTD_E_INVAL, "autotune the batch handle, not a member");
+    if (trial_steps < 1) return fail(h, FDTD_E_INVAL, "trial_steps must be >= 1");
+    Sim *S = h->sim;
+    const int keep = S->tiling;
+    int rc = fdtd_llg_set_tiling(h, 0);
+    if (!rc) rc = fdtd_llg_step(h, 1);   // start-up half-push and descriptors
+    if (rc) return rc;
+    std::vector<int> cand = {S->planes, 8, 12, 16, 24, 32, 48, 64};
+    int maxnz = 1;
+    for (const Instance &I : S->inst) maxnz = std::max(maxnz, I.nz);
+    for (int &c : cand) c = std::min(c, maxnz);
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    cudaEvent_t e0, e1;
+    CKR(h, cudaEventCreate(&e0));
+    CKR(h, cudaEventCreate(&e1));
+    int best = cand[0];
+    float best_ms = -1.f;
+    for (int c : cand) {
+        rc = fdtd_llg_set_tiling(h, c);
+        if (!rc) rc = fdtd_llg_step(h, 1);   // upload the new descriptors outside the timing
+        if (rc) break;
+        cudaEventRecord(e0, S->stream);
+        rc = fdtd_llg_step(h, trial_steps);
+        if (rc) break;
+        cudaEventRecord(e1, S->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(h, FDTD_E_CUDA, "autotune timing failed"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best_ms < 0.f || ms < best_ms) { best_ms = ms; best = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) {
+        fdtd_llg_set_tiling(h, keep);
+        return rc;
+    }
+    rc = fdtd_llg_set_tiling(h, best);
+    if (planes) *planes = best;
+    return rc;
+}
+
 extern "C" int fdtd_llg_set_profiling(fdtd_llg_t h, int32_t on)
 {
     if (!h || !h->sim) return fail(h, FDTD_E_INVAL, "null handle");

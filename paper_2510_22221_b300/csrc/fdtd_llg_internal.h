@@ -21,8 +21,9 @@ constexpr int kMaxMagMat = 16;
 constexpr int kTX = 32, kTY = 8, kKC = 16;
 
 // Fused step kernel: one CTA of kST threads per column task of kSX x kSY
-// cells x fkc (at most kSZ) planes, marching the task in z.  Each
-// z-plane arrives by TMA in one stage of a kNS-deep shared-memory ring: H on
+// cells x fkc planes (the host picks fkc; kSZ is the fallback), marching the
+// task in z.  Each z-plane arrives by TMA in one stage of a kNS-deep
+// shared-memory ring: H on
 // the tile extended by one cell on the low x/y sides (box kHBX x kHBY, x
 // starting 4 cells low so that the copy stays 16-byte aligned), E^n and the
 // class ids on the tile extended by one cell on the high x/y sides.  E^{n+1}
@@ -128,7 +129,6 @@ struct LaunchSet {
     double *part_f, *part_m;            // energy partials per fused tile / per region
     const int *ftile_inst;
     int nftiles;                        // fused-step tasks (one CTA each)
-    int emax;                           // most edges of a magnet region's box (3 components)
     int mag_smem;                       // dynamic shared memory of the magnet kernel (bytes)
     int src, dst;                       // field buffers read / written by a step
     int grid_h;
@@ -141,12 +141,12 @@ struct LaunchSet {
 
 // Launchers (kernels_fwd.cu).  launch_half: the start-up H/M half-push that
 // moves H, M from integer time to half a step ahead, in place on buffer src.
-// launch_step: one full step reading buffer src and writing buffer dst, the
-// field kernel on s and the magnetic regions concurrently on s_mag (events
-// ev_fork / ev_join order them with the surrounding work on s).
+// launch_step: one full step reading buffer src and writing buffer dst on
+// stream s, the magnetic regions and the field sweep side by side (the sweep
+// is a programmatic dependent launch of the magnet kernel); prof, when not
+// NULL, holds four events recorded around the two kernels.
 cudaError_t launch_half(const LaunchSet &L, cudaStream_t s);
-cudaError_t launch_step(const LaunchSet &L, cudaStream_t s, cudaStream_t s_mag, cudaEvent_t ev_fork,
-                        cudaEvent_t ev_join, cudaEvent_t *prof);
+cudaError_t launch_step(const LaunchSet &L, cudaStream_t s, cudaEvent_t *prof);
 int h_half_blocks_per_sm(bool cls16);
 int step_blocks_per_sm(bool cls16);
 

@@ -15,19 +15,18 @@
 //                     -> H^{n+3/2} of the plane below for every non-magnetic
 //                     face (M = 0 there: the plain Faraday update), with FP64
 //                     energy partials and probe samples.
-//   mag_edge_kernel : E^{n+1} (or the stored E, at start-up) at every edge of
-//                     each magnetic region's box, with the same arithmetic as
-//                     step_kernel, into a scratch array; many CTAs, one edge
-//                     per thread.
 //   mag_kernel      : the H/M half-pushes of every magnetic face and cell (Eq.
 //                     iterate_H with the trapezoidal LLG solve of Eqs.
 //                     llg_tra4-6, Jacobi-iterated until max |M^r - M^{r-1}|/Ms
 //                     < tol), one CTA per face-connected magnetic region, its
-//                     cells, faces and face curls resident in shared memory.
-//   The two magnet kernels run on a second, high-priority stream concurrently
-//   with step_kernel: they read only buffer src and write only magnetic faces
-//   of buffer dst, which step_kernel never writes.
-//   h_half_kernel + the magnet kernels with one half-push : the start-up
+//                     cells, faces and face curls resident in shared memory;
+//                     it first evaluates E^{n+1} (with the arithmetic of
+//                     step_kernel) at the edges of its box.  It runs on a
+//                     second, high-priority stream, launched ahead of and
+//                     concurrently with step_kernel: it reads only buffer src
+//                     and writes only magnetic faces of buffer dst, which
+//                     step_kernel never writes.
+//   h_half_kernel + mag_kernel with one half-push : the start-up
 //                     half-push that moves H and M from integer time to half a
 //                     step ahead, in place.
 // The last CTA to finish a step, over both kernels, sums the energy partials
@@ -156,7 +155,7 @@ __global__ void __launch_bounds__(kTX *kTY) h_half_kernel(LaunchSet L)
 
 // ------------------------------------------------- shared E^{n+1} arithmetic
 // Written with explicit round-to-nearest operations so that step_kernel and
-// mag_edge_kernel produce bitwise the same E^{n+1}.
+// mag_kernel produce bitwise the same E^{n+1}.
 // (a1 - b1) i1 - (a2 - b2) i2: one component of a Yee curl.
 __device__ __forceinline__ float curl2(float a1, float b1, float i1, float a2, float b2, float i2)
 {
@@ -182,18 +181,14 @@ __device__ __forceinline__ float *hz_ptr(const Inst *I, float *F0, int i, int j,
     return (k == I->nz) ? I->wHz + (long long)j * I->nx + i : F0 + 5 * I->fstride + (long long)k * I->plane + (long long)j * I->px + i;
 }
 
-// E at every edge (comp, i, j, k) of each magnetic region's box,
-// i in [x0, x0+bx], j in [y0, y0+by], k in [z0, z0+bz]: advanced to E^{n+1}
-// from buffer src (ADVANCE) or as stored.  Edges beyond the far walls are zero.
-// Grid: (edges / 256 rounded up, regions).
+// E at edge e of a magnetic region's box: e = comp * ne + ((lk (by+1) + lj)
+// (bx+1) + li), global edge (comp, x0+li, y0+lj, z0+lk) with li in [0, bx],
+// lj in [0, by], lk in [0, bz]; advanced to E^{n+1} from buffer src (ADVANCE)
+// or as stored.  Edges beyond the far walls are zero.
 template <bool ADVANCE, typename ClsT>
-__global__ void __launch_bounds__(256) mag_edge_kernel(LaunchSet L)
+__device__ __forceinline__ float box_edge(const LaunchSet &L, const MagComp &C, const Inst *I, int e, long long n)
 {
-    const MagComp C = L.comps[blockIdx.y];
     const int ex = C.bx + 1, ey = C.by + 1, ne = ex * ey * (C.bz + 1);
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 3 * ne) return;
-    const Inst *I = L.insts + C.inst;
     const int comp = e / ne, r = e - comp * ne;
     const int li = r % ex, lj = (r / ex) % ey, lk = r / (ex * ey);
     const int i = C.x0 + li, j = C.y0 + lj, k = C.z0 + lk;
@@ -214,7 +209,6 @@ __global__ void __launch_bounds__(256) mag_edge_kernel(LaunchSet L)
                 cu = curl2(Hx[o], k > 0 ? Hx[o - plane] : 0.f, I->idz, Hz[o], i > 0 ? Hz[o - 1] : 0.f, I->idx);
             else
                 cu = curl2(Hy[o], i > 0 ? Hy[o - 1] : 0.f, I->idx, Hx[o], j > 0 ? Hx[o - px] : 0.f, I->idy);
-            const long long n = *(volatile long long *)&L.ctl->step;
             for (int s = 0; s < I->nsrc; ++s)
                 if (I->src[s][0] == comp && I->src[s][1] == i && I->src[s][2] == j && I->src[s][3] == k)
                     cu = __fsub_rn(cu, (float)source_value(I->srcp[s], ((double)n + 0.5) * I->dt));
@@ -225,7 +219,7 @@ __global__ void __launch_bounds__(256) mag_edge_kernel(LaunchSet L)
             v = e_next(ca, Fs[comp * fs + o], cb, cu);
         }
     }
-    C.eedge[e] = v;
+    return v;
 }
 
 // The LLG solve runs in the bias frame (rows of I->R: e1, e2, e3 = h) on the
@@ -276,14 +270,20 @@ __device__ __forceinline__ void face_decode(int f, int bx, int by, int bz, int &
 
 // FUSED: a full step (two half-pushes), H^{n+1/2} from buffer src, results to
 // buffer dst, curl of E^{n+1}.  Otherwise: the start-up half-push, in place on
-// buffer src, curl of the stored E.  mag_edge_kernel has filled C.eedge.
-template <bool FUSED>
+// buffer src, curl of the stored E.  The CTA first evaluates E at every edge of
+// its box (with the arithmetic of step_kernel) into the region's scratch.
+template <bool FUSED, typename ClsT>
 __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
 {
     extern __shared__ float smem[];
     __shared__ float sredf[kMagThreads / 32];
     __shared__ double sredd[kMagThreads / 32];
+    __shared__ MagMat smm[kMaxMagMat];
     __shared__ int s_last;
+    // in a full step the field sweep, launched right behind this kernel on the
+    // same stream, may start now: it writes only non-magnetic faces and E of
+    // buffer dst and reads nothing this kernel writes
+    if (FUSED) asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     const MagComp C = L.comps[blockIdx.x];
     const Inst *I = L.insts + C.inst;
     const int tid = threadIdx.x, nth = blockDim.x;
@@ -309,11 +309,30 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
         sM[V + v] = C.m[V + v];
         sM[2 * V + v] = C.m[2 * V + v];
     }
+    if (tid < kMaxMagMat) smm[tid] = I->mm[tid];
+    // E (E^{n+1} in a full step) at every edge of the box, four edges per
+    // thread in flight at a time
+    {
+        const int ne3 = 3 * (bx + 1) * (by + 1) * (bz + 1);
+        for (int e0 = tid; e0 < ne3; e0 += 4 * nth) {
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + u * nth;
+                v[u] = e < ne3 ? box_edge<FUSED, ClsT>(L, C, I, e, n) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + u * nth;
+                if (e < ne3) C.eedge[e] = v[u];
+            }
+        }
+    }
     __syncthreads();
     // H^s and (dt/2mu0) curl E at every face of the region, once for both half-pushes
     {
         const int ex = bx + 1, exy = (bx + 1) * (by + 1), ne = exy * (bz + 1);
-        const float *Ex = C.eedge, *Ey = Ex + ne, *Ez = Ey + ne;
+        const float *Ex = C.eedge, *Ey = Ex + ne, *Ez = Ey + ne;   // written above by this CTA: read through L2
         for (int f = tid; f < nf; f += nth) {
             int a, fi, fj, fk, vl, vr;
             face_decode(f, bx, by, bz, a, fi, fj, fk, vl, vr);
@@ -325,13 +344,13 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
                 float cu;
                 if (a == 0) {
                     h = *hx_ptr(I, Fs, i, j, k);
-                    cu = curl2(Ez[e0 + ex], Ez[e0], I->idy, Ey[e0 + exy], Ey[e0], I->idz);
+                    cu = curl2(__ldcg(Ez + e0 + ex), __ldcg(Ez + e0), I->idy, __ldcg(Ey + e0 + exy), __ldcg(Ey + e0), I->idz);
                 } else if (a == 1) {
                     h = *hy_ptr(I, Fs, i, j, k);
-                    cu = curl2(Ex[e0 + exy], Ex[e0], I->idz, Ez[e0 + 1], Ez[e0], I->idx);
+                    cu = curl2(__ldcg(Ex + e0 + exy), __ldcg(Ex + e0), I->idz, __ldcg(Ez + e0 + 1), __ldcg(Ez + e0), I->idx);
                 } else {
                     h = *hz_ptr(I, Fs, i, j, k);
-                    cu = curl2(Ey[e0 + 1], Ey[e0], I->idx, Ex[e0 + ex], Ex[e0], I->idy);
+                    cu = curl2(__ldcg(Ey + e0 + 1), __ldcg(Ey + e0), I->idx, __ldcg(Ex + e0 + ex), __ldcg(Ex + e0), I->idy);
                 }
                 c = ch * cu;
             }
@@ -382,7 +401,7 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
                 float sx, sy, sz;      // H_eff^s (start of the half-push) in the bias frame
                 to_frame(R, 0.5f * (hx0 + hx1), 0.5f * (hy0 + hy1), 0.5f * (hz0 + hz1), sx, sy, sz);
                 sz += h0n;
-                const MagMat mm = I->mm[m];
+                const MagMat mm = smm[m];
                 const float mx = sM[v], my = sM[V + v], mz = sM[2 * V + v];
                 const float Mz = mm.Ms + mz;
                 const float dam = mm.alpha * mm.inv_Ms;
@@ -470,7 +489,7 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
                 const int m = smat[v];
                 if (m == 0xFF) continue;
                 const float qx = sM[v], qy = sM[V + v], qz = sM[2 * V + v];
-                z += (qx * qx + qy * qy + qz * qz) * I->mm[m].inv_Ms;
+                z += (qx * qx + qy * qy + qz * qz) * smm[m].inv_Ms;
             }
             eacc += (double)z * (0.5 * kMu0 * (double)h0n);
             // probe samples of magnetic faces and of M at step n+1
@@ -496,7 +515,7 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
                     if (m != 0xFF) {
                         // M = Ms h + R^T m, in FP64
                         const double mx = sM[vc], my = sM[V + vc], mz = sM[2 * V + vc];
-                        const double Ms = I->mm[m].Ms;
+                        const double Ms = smm[m].Ms;
                         for (int d = 0; d < 3; ++d)
                             row[6 + d] = Ms * I->u[d] + (double)R[d] * mx + (double)R[3 + d] * my + (double)R[6 + d] * mz;
                     }
@@ -577,16 +596,48 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *tm, in
         : "memory");
 }
 
+__device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+// Cascaded compensated accumulation of FP32 terms (Ogita, Rump and Oishi's
+// Sum2): TwoSum gives the exact rounding error of every addition, which is
+// summed separately, so s + c carries the running sum as if in twice the
+// precision and the FP64 total does not depend on how terms are grouped into
+// tasks.
+__device__ __forceinline__ void sum2_add(float &s, float &c, float x)
+{
+    const float t = __fadd_rn(s, x);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+    c = __fadd_rn(c, err);
+    s = t;
+}
+__device__ __forceinline__ void st2(float *p, float a, float b) { *reinterpret_cast<float2 *>(p) = make_float2(a, b); }
+// class ids of the cell pair (x, x+1), x even
+__device__ __forceinline__ void cls2(const uint8_t *p, int &c0, int &c1)
+{
+    const unsigned v = *reinterpret_cast<const uint16_t *>(p);
+    c0 = (int)(v & 0xFFu);
+    c1 = (int)(v >> 8);
+}
+__device__ __forceinline__ void cls2(const uint16_t *p, int &c0, int &c1)
+{
+    const unsigned v = *reinterpret_cast<const uint32_t *>(p);
+    c0 = (int)(v & 0xFFFFu);
+    c1 = (int)(v >> 16);
+}
+
 // One CTA per task: column (tx, ty) of kSX x kSY cells, planes [k0, k1).  The
 // CTA walks the items k = k0-1 (H only, for the curl of plane k0), k0, ..., k1
 // (the plane above, for E^{n+1} there; zeros beyond the grid).  Item q lives
-// in stage q % kNS.  Per item: E^{n+1} of plane k at the tile's own cells, one
-// barrier, then H of plane k-1 and E^{n+1} of plane k at the halo edges that
-// the next item's H update reads (Ex and Ez of the row above the tile, Ey and
-// Ez of the column beyond it).  After the barrier of item q the stage of item
-// q-2 has no readers left and receives item q + kNS - 2.  The tensor maps
-// zero-fill everything outside the grid and class 0 has zero coefficients,
-// so cells beyond the far walls get E^{n+1} = 0 without a branch.
+// in stage q % kNS.  Warp w owns row y = w of the tile and each lane the cell
+// pair (x, x+1), x = 2 lane, so shared-memory and global accesses move float2
+// pairs and x neighbours come from the pair itself.  Per item: E^{n+1} of
+// plane k at the tile's own cells, one barrier, then H of plane k-1 and
+// E^{n+1} of plane k at the halo edges that the next item's H update reads (Ex
+// and Ez of the row above the tile, Ey and Ez of the column beyond it).  After
+// the barrier of item q the stage of item q-2 has no readers left and receives
+// item q + kNS - 2.  The tensor maps zero-fill everything outside the grid and
+// class 0 has zero coefficients, so cells beyond the far walls get E^{n+1} = 0
+// and H = 0 without a branch.
 template <typename ClsT, bool STAB>
 __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
 {
@@ -597,6 +648,7 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
     __shared__ int s_last, s_abort;
     constexpr int CBX = sizeof(ClsT) == 1 ? kCBX8 : kCBX16;
     constexpr unsigned kClsBytes = CBX * kEBY * sizeof(ClsT);
+    static_assert(kST == 32 * kSY && kSX == 64, "one warp per tile row, one cell pair per lane");
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const long long n = *(volatile long long *)&L.ctl->step;
     const int t = blockIdx.x;
@@ -668,24 +720,21 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
                 else cz = __fsub_rn(cz, J);
             }
     };
+    auto probe_row = [&](int pp) { return I->probe_buf + ((long long)(n % I->cap) * I->nprobe + pp) * 9; };
 
-    // this thread's cells: (xi, yi) and (xi, yi + 4); output pointers per component
-    const int xi = (w & 1) * 32 + lane, yi = w >> 1;
-    const int gi = i0 + xi, gj = j0 + yi;
-    const bool in0 = gi < nx && gj < ny, in1 = gi < nx && gj + 4 < ny;
-    const unsigned ob = (unsigned)gj * (unsigned)px + (unsigned)gi, ob1 = ob + 4u * (unsigned)px;
+    // this thread's cells: (x, y), (x+1, y); output pointers per component
+    const int x = 2 * lane, y = w;
+    const int gi = i0 + x, gj = j0 + y;
+    const bool in = gi < nx && gj < ny;   // gi + 1 < px always: the pair stays in the padded row
+    const unsigned ob = (unsigned)gj * (unsigned)px + (unsigned)gi;
     float *const F0 = I->F[L.dst][0];
     float *const Fx = F0, *const Fy = F0 + fs, *const Fz = F0 + 2 * fs;
     float *const Gx = F0 + 3 * fs, *const Gy = F0 + 4 * fs, *const Gz = F0 + 5 * fs;
-    // halo role: warps 0-1 Ex and warps 2-3 Ez of row kSY (x = 0..63); warp 4
-    // lanes 0-7 Ey and lanes 8-15 Ez of column kSX (y = 0..7)
-    const int xr = (w < 4) ? (tid & 63) : kSX;
-    const int yr = (w < 4) ? kSY : (lane & 7);
-    const int cr = (w < 2) ? 0 : (w < 4 ? 2 : (lane < 8 ? 1 : 2));
-    const bool halo = w < 4 || (w == 4 && lane < 16);
+    const int hp = (y + 1) * kHBX + x + 4;   // (x, y) in the H box
+    const int ep = y * kEBX + x;             // (x, y) in the E box
     __syncthreads();
 
-    float acc = 0.f;
+    float acc = 0.f, acc_c = 0.f;   // energy of this thread's cells, compensated
     int consumed = 0;
     for (int q = 0; q < nitems; ++q) {
         const int s = q % kNS, sp = (q + kNS - 1) % kNS;
@@ -702,53 +751,48 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
         const ClsT *Cc = reinterpret_cast<const ClsT *>(cur + kStageCOff);
         if (q > 0) {
             // ---- E^{n+1} of plane k at the tile's cells, in place over E^n
-            float ve[2][3];
-            float4 Qe[2];
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const int y = yi + 4 * r;
-                const int hp = (y + 1) * kHBX + xi + 4;
-                const float hx = Hc[hp], hy = Hc[kHC + hp], hz = Hc[2 * kHC + hp];
-                const float hz_jm = Hc[2 * kHC + hp - kHBX], hx_jm = Hc[hp - kHBX];
-                const float hz_im = Hc[2 * kHC + hp - 1], hy_im = Hc[kHC + hp - 1];
-                const float hx_km = Hp[hp], hy_km = Hp[kHC + hp];
-                float cx = curl2(hz, hz_jm, idy, hy, hy_km, idz);
-                float cy = curl2(hx, hx_km, idz, hz, hz_im, idx);
-                float cz = curl2(hy, hy_im, idx, hx, hx_jm, idy);
-                if (smask) add_src(gi, j0 + y, k, cx, cy, cz);
-                const int ep = y * kEBX + xi;
-                const int c = (int)Cc[y * CBX + xi];
-                const float4 A = tab(3 * c), B = tab(3 * c + 1);
-                Qe[r] = tab(3 * c + 2);
-                ve[r][0] = e_next(A.x, Ec[ep], B.x, cx);
-                ve[r][1] = e_next(A.y, Ec[kEC + ep], B.y, cy);
-                ve[r][2] = e_next(A.z, Ec[2 * kEC + ep], B.z, cz);
+            const float2 HX = ld2(Hc + hp), HY = ld2(Hc + kHC + hp), HZ = ld2(Hc + 2 * kHC + hp);
+            const float2 HXj = ld2(Hc + hp - kHBX), HZj = ld2(Hc + 2 * kHC + hp - kHBX);
+            const float hyi = Hc[kHC + hp - 1], hzi = Hc[2 * kHC + hp - 1];
+            const float2 HXk = ld2(Hp + hp), HYk = ld2(Hp + kHC + hp);
+            const float2 EX = ld2(Ec + ep), EY = ld2(Ec + kEC + ep), EZ = ld2(Ec + 2 * kEC + ep);
+            int c0, c1;
+            cls2(Cc + y * CBX + x, c0, c1);
+            float cx0 = curl2(HZ.x, HZj.x, idy, HY.x, HYk.x, idz);
+            float cy0 = curl2(HX.x, HXk.x, idz, HZ.x, hzi, idx);
+            float cz0 = curl2(HY.x, hyi, idx, HX.x, HXj.x, idy);
+            float cx1 = curl2(HZ.y, HZj.y, idy, HY.y, HYk.y, idz);
+            float cy1 = curl2(HX.y, HXk.y, idz, HZ.y, HZ.x, idx);
+            float cz1 = curl2(HY.y, HY.x, idx, HX.y, HXj.y, idy);
+            if (smask) {
+                add_src(gi, gj, k, cx0, cy0, cz0);
+                add_src(gi + 1, gj, k, cx1, cy1, cz1);
             }
-            const bool kin = k < k1;
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const int ep = (yi + 4 * r) * kEBX + xi;
-                Ec[ep] = ve[r][0];
-                Ec[kEC + ep] = ve[r][1];
-                Ec[2 * kEC + ep] = ve[r][2];
-                if (kin && (r ? in1 : in0)) {
-                    const unsigned o = (unsigned)k * plane + (r ? ob1 : ob);
-                    Fx[o] = ve[r][0];
-                    Fy[o] = ve[r][1];
-                    Fz[o] = ve[r][2];
-                    acc += Qe[r].x * ve[r][0] * ve[r][0] + Qe[r].y * ve[r][1] * ve[r][1] + Qe[r].z * ve[r][2] * ve[r][2];
-                }
-            }
-            if (pmask && kin) {
-                for (int pp = 0; pp < I->nprobe; ++pp)
-#pragma unroll
-                    for (int r = 0; r < 2; ++r)
-                        if (((pmask >> pp) & 1u) && I->probe[pp][0] == gi && I->probe[pp][1] == gj + 4 * r && I->probe[pp][2] == k) {
-                            double *row = I->probe_buf + ((long long)(n % I->cap) * I->nprobe + pp) * 9;
-                            row[0] = ve[r][0];
-                            row[1] = ve[r][1];
-                            row[2] = ve[r][2];
+            const float4 A0 = tab(3 * c0), B0 = tab(3 * c0 + 1), A1 = tab(3 * c1), B1 = tab(3 * c1 + 1);
+            const float ex0 = e_next(A0.x, EX.x, B0.x, cx0), ey0 = e_next(A0.y, EY.x, B0.y, cy0), ez0 = e_next(A0.z, EZ.x, B0.z, cz0);
+            const float ex1 = e_next(A1.x, EX.y, B1.x, cx1), ey1 = e_next(A1.y, EY.y, B1.y, cy1), ez1 = e_next(A1.z, EZ.y, B1.z, cz1);
+            st2(Ec + ep, ex0, ex1);
+            st2(Ec + kEC + ep, ey0, ey1);
+            st2(Ec + 2 * kEC + ep, ez0, ez1);
+            if (k < k1 && in) {
+                const unsigned o = (unsigned)k * plane + ob;
+                st2(Fx + o, ex0, ex1);
+                st2(Fy + o, ey0, ey1);
+                st2(Fz + o, ez0, ez1);
+                const float4 Q0 = tab(3 * c0 + 2), Q1 = tab(3 * c1 + 2);
+                sum2_add(acc, acc_c, Q0.x * ex0 * ex0 + Q0.y * ey0 * ey0 + Q0.z * ez0 * ez0 + Q1.x * ex1 * ex1 +
+                                          Q1.y * ey1 * ey1 + Q1.z * ez1 * ez1);
+                if (pmask) {
+                    for (int pp = 0; pp < I->nprobe; ++pp)
+                        if (((pmask >> pp) & 1u) && I->probe[pp][1] == gj && I->probe[pp][2] == k &&
+                            (I->probe[pp][0] == gi || I->probe[pp][0] == gi + 1)) {
+                            const bool second = I->probe[pp][0] != gi;
+                            double *row = probe_row(pp);
+                            row[0] = second ? ex1 : ex0;
+                            row[1] = second ? ey1 : ey0;
+                            row[2] = second ? ez1 : ez0;
                         }
+                }
             }
         }
         // every generic write to the stage of item q-2 is ordered before the
@@ -759,80 +803,124 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
         if (tid == 0 && q >= 1 && q + kNS - 2 < nitems) issue(q + kNS - 2);
         // ---- H^{n+1} and H^{n+3/2} of plane k-1 at the tile's cells
         if (q > 1) {
-            const unsigned kh = (unsigned)(k - 1);
             const float *Ep = reinterpret_cast<const float *>(prv + kStageEOff);
             const ClsT *Cp = reinterpret_cast<const ClsT *>(prv + kStageCOff);
-            float hv[2][3];
-            uint32_t fl[2];
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const int y = yi + 4 * r;
-                const int ep = y * kEBX + xi;
-                const float ex = Ep[ep], ey = Ep[kEC + ep], ez = Ep[2 * kEC + ep];
-                const float ex_jp = Ep[ep + kEBX], ez_jp = Ep[2 * kEC + ep + kEBX];
-                const float ey_ip = Ep[kEC + ep + 1], ez_ip = Ep[2 * kEC + ep + 1];
-                const float ex_kp = Ec[ep], ey_kp = Ec[kEC + ep];
-                const float cx = curl2(ez_jp, ez, idy, ey_kp, ey, idz);
-                const float cy = curl2(ex_kp, ex, idz, ez_ip, ez, idx);
-                const float cz = curl2(ey_ip, ey, idx, ex_jp, ex, idy);
-                fl[r] = has_mag ? __float_as_uint(tab(3 * (int)Cp[y * CBX + xi]).w) : 0u;
-                const int hp = (y + 1) * kHBX + xi + 4;
-                hv[r][0] = __fsub_rn(Hp[hp], __fmul_rn(ch, cx));
-                hv[r][1] = __fsub_rn(Hp[kHC + hp], __fmul_rn(ch, cy));
-                hv[r][2] = __fsub_rn(Hp[2 * kHC + hp], __fmul_rn(ch, cz));
-                // second half-push with the same curl
-                const float ddx = __fmul_rn(ch, cx), ddy = __fmul_rn(ch, cy), ddz = __fmul_rn(ch, cz);
-                if (fl[r] & CF_MAG_HX) hv[r][0] = 0.f;
-                if (fl[r] & CF_MAG_HY) hv[r][1] = 0.f;
-                if (fl[r] & CF_MAG_HZ) hv[r][2] = 0.f;
-                const bool inr = r ? in1 : in0;
-                if (inr) {
-                    const unsigned o = kh * plane + (r ? ob1 : ob);
-                    if (!(fl[r] & CF_MAG_HX)) Gx[o] = __fsub_rn(hv[r][0], ddx);
-                    if (!(fl[r] & CF_MAG_HY)) Gy[o] = __fsub_rn(hv[r][1], ddy);
-                    if (!(fl[r] & CF_MAG_HZ)) Gz[o] = __fsub_rn(hv[r][2], ddz);
-                    acc += (float)(0.5 * kMu0) * (hv[r][0] * hv[r][0] + hv[r][1] * hv[r][1] + hv[r][2] * hv[r][2]);
+            const float2 EX = ld2(Ep + ep), EY = ld2(Ep + kEC + ep), EZ = ld2(Ep + 2 * kEC + ep);
+            const float2 EXj = ld2(Ep + ep + kEBX), EZj = ld2(Ep + 2 * kEC + ep + kEBX);
+            const float eyi = Ep[kEC + ep + 2], ezi = Ep[2 * kEC + ep + 2];
+            const float2 EXk = ld2(Ec + ep), EYk = ld2(Ec + kEC + ep);
+            const float2 HX = ld2(Hp + hp), HY = ld2(Hp + kHC + hp), HZ = ld2(Hp + 2 * kHC + hp);
+            const float cx0 = curl2(EZj.x, EZ.x, idy, EYk.x, EY.x, idz);
+            const float cy0 = curl2(EXk.x, EX.x, idz, EZ.y, EZ.x, idx);
+            const float cz0 = curl2(EY.y, EY.x, idx, EXj.x, EX.x, idy);
+            const float cx1 = curl2(EZj.y, EZ.y, idy, EYk.y, EY.y, idz);
+            const float cy1 = curl2(EXk.y, EX.y, idz, ezi, EZ.y, idx);
+            const float cz1 = curl2(eyi, EY.y, idx, EXj.y, EX.y, idy);
+            uint32_t f0 = 0, f1 = 0;
+            if (has_mag) {
+                int c0, c1;
+                cls2(Cp + y * CBX + x, c0, c1);
+                f0 = __float_as_uint(tab(3 * c0).w);
+                f1 = __float_as_uint(tab(3 * c1).w);
+            }
+            const float dx0 = __fmul_rn(ch, cx0), dy0 = __fmul_rn(ch, cy0), dz0 = __fmul_rn(ch, cz0);
+            const float dx1 = __fmul_rn(ch, cx1), dy1 = __fmul_rn(ch, cy1), dz1 = __fmul_rn(ch, cz1);
+            // H^{n+1} (zero where the face is magnetic: the magnet kernel owns it)
+            const float hx0 = (f0 & CF_MAG_HX) ? 0.f : __fsub_rn(HX.x, dx0);
+            const float hy0 = (f0 & CF_MAG_HY) ? 0.f : __fsub_rn(HY.x, dy0);
+            const float hz0 = (f0 & CF_MAG_HZ) ? 0.f : __fsub_rn(HZ.x, dz0);
+            const float hx1 = (f1 & CF_MAG_HX) ? 0.f : __fsub_rn(HX.y, dx1);
+            const float hy1 = (f1 & CF_MAG_HY) ? 0.f : __fsub_rn(HY.y, dy1);
+            const float hz1 = (f1 & CF_MAG_HZ) ? 0.f : __fsub_rn(HZ.y, dz1);
+            if (in) {
+                const unsigned o = (unsigned)(k - 1) * plane + ob;
+                if (!((f0 | f1) & (CF_MAG_HX | CF_MAG_HY | CF_MAG_HZ))) {
+                    st2(Gx + o, __fsub_rn(hx0, dx0), __fsub_rn(hx1, dx1));
+                    st2(Gy + o, __fsub_rn(hy0, dy0), __fsub_rn(hy1, dy1));
+                    st2(Gz + o, __fsub_rn(hz0, dz0), __fsub_rn(hz1, dz1));
+                } else {
+                    if (!(f0 & CF_MAG_HX)) Gx[o] = __fsub_rn(hx0, dx0);
+                    if (!(f0 & CF_MAG_HY)) Gy[o] = __fsub_rn(hy0, dy0);
+                    if (!(f0 & CF_MAG_HZ)) Gz[o] = __fsub_rn(hz0, dz0);
+                    if (!(f1 & CF_MAG_HX)) Gx[o + 1] = __fsub_rn(hx1, dx1);
+                    if (!(f1 & CF_MAG_HY)) Gy[o + 1] = __fsub_rn(hy1, dy1);
+                    if (!(f1 & CF_MAG_HZ)) Gz[o + 1] = __fsub_rn(hz1, dz1);
+                }
+                sum2_add(acc, acc_c, (float)(0.5 * kMu0) * (hx0 * hx0 + hy0 * hy0 + hz0 * hz0 + hx1 * hx1 + hy1 * hy1 + hz1 * hz1));
+                if (pmask) {
+                    for (int pp = 0; pp < I->nprobe; ++pp)
+                        if (((pmask >> pp) & 1u) && I->probe[pp][1] == gj && I->probe[pp][2] == k - 1 &&
+                            (I->probe[pp][0] == gi || I->probe[pp][0] == gi + 1)) {
+                            const bool second = I->probe[pp][0] != gi;
+                            const uint32_t f = second ? f1 : f0;
+                            double *row = probe_row(pp);
+                            if (!(f & CF_MAG_HX)) row[3] = second ? hx1 : hx0;
+                            if (!(f & CF_MAG_HY)) row[4] = second ? hy1 : hy0;
+                            if (!(f & CF_MAG_HZ)) row[5] = second ? hz1 : hz0;
+                        }
                 }
             }
-            if (pmask) {
-                for (int pp = 0; pp < I->nprobe; ++pp)
-#pragma unroll
-                    for (int r = 0; r < 2; ++r)
-                        if (((pmask >> pp) & 1u) && I->probe[pp][0] == gi && I->probe[pp][1] == gj + 4 * r &&
-                            I->probe[pp][2] == (int)kh) {
-                            double *row = I->probe_buf + ((long long)(n % I->cap) * I->nprobe + pp) * 9;
-                            if (!(fl[r] & CF_MAG_HX)) row[3] = hv[r][0];
-                            if (!(fl[r] & CF_MAG_HY)) row[4] = hv[r][1];
-                            if (!(fl[r] & CF_MAG_HZ)) row[5] = hv[r][2];
-                        }
-            }
         }
-        // ---- E^{n+1} of plane k at the halo edges read by the next item
-        if (q > 0 && q + 1 < nitems && halo) {
-            const int hp = (yr + 1) * kHBX + xr + 4;
-            float cu;
-            if (cr == 0) cu = curl2(Hc[2 * kHC + hp], Hc[2 * kHC + hp - kHBX], idy, Hc[kHC + hp], Hp[kHC + hp], idz);
-            else if (cr == 1) cu = curl2(Hc[hp], Hp[hp], idz, Hc[2 * kHC + hp], Hc[2 * kHC + hp - 1], idx);
-            else cu = curl2(Hc[kHC + hp], Hc[kHC + hp - 1], idx, Hc[hp], Hc[hp - kHBX], idy);
-            if (smask) {
-                float c3[3] = {0.f, 0.f, 0.f};
-                c3[cr] = cu;
-                add_src(i0 + xr, j0 + yr, k, c3[0], c3[1], c3[2]);
-                cu = c3[cr];
+        // ---- E^{n+1} of plane k at the halo edges read by the next item:
+        // warp 0 Ex and warp 1 Ez of row kSY (pairs), warp 2 Ey (lanes 0-7)
+        // and Ez (lanes 8-15) of column kSX
+        if (q > 0 && q + 1 < nitems && (w < 2 || (w == 2 && lane < 16))) {
+            if (w < 2) {
+                const int hr = (kSY + 1) * kHBX + x + 4, er = kSY * kEBX + x;
+                int c0, c1;
+                cls2(Cc + kSY * CBX + x, c0, c1);
+                const float4 A0 = tab(3 * c0), B0 = tab(3 * c0 + 1), A1 = tab(3 * c1), B1 = tab(3 * c1 + 1);
+                if (w == 0) {
+                    const float2 HZ = ld2(Hc + 2 * kHC + hr), HZj = ld2(Hc + 2 * kHC + hr - kHBX);
+                    const float2 HY = ld2(Hc + kHC + hr), HYk = ld2(Hp + kHC + hr);
+                    float cx0 = curl2(HZ.x, HZj.x, idy, HY.x, HYk.x, idz), cx1 = curl2(HZ.y, HZj.y, idy, HY.y, HYk.y, idz);
+                    if (smask) {
+                        float d0 = 0.f, d1 = 0.f;
+                        add_src(gi, j0 + kSY, k, cx0, d0, d1);
+                        add_src(gi + 1, j0 + kSY, k, cx1, d0, d1);
+                    }
+                    const float2 EN = ld2(Ec + er);
+                    st2(Ec + er, e_next(A0.x, EN.x, B0.x, cx0), e_next(A1.x, EN.y, B1.x, cx1));
+                } else {
+                    const float2 HY = ld2(Hc + kHC + hr), HX = ld2(Hc + hr), HXj = ld2(Hc + hr - kHBX);
+                    const float hyi = Hc[kHC + hr - 1];
+                    float cz0 = curl2(HY.x, hyi, idx, HX.x, HXj.x, idy), cz1 = curl2(HY.y, HY.x, idx, HX.y, HXj.y, idy);
+                    if (smask) {
+                        float d0 = 0.f, d1 = 0.f;
+                        add_src(gi, j0 + kSY, k, d0, d1, cz0);
+                        add_src(gi + 1, j0 + kSY, k, d0, d1, cz1);
+                    }
+                    const float2 EN = ld2(Ec + 2 * kEC + er);
+                    st2(Ec + 2 * kEC + er, e_next(A0.z, EN.x, B0.z, cz0), e_next(A1.z, EN.y, B1.z, cz1));
+                }
+            } else {
+                const int yc = lane & 7;
+                const int hc = (yc + 1) * kHBX + kSX + 4, ec = yc * kEBX + kSX;
+                const int c = (int)Cc[yc * CBX + kSX];
+                const float4 A = tab(3 * c), B = tab(3 * c + 1);
+                if (lane < 8) {
+                    float cy = curl2(Hc[hc], Hp[hc], idz, Hc[2 * kHC + hc], Hc[2 * kHC + hc - 1], idx);
+                    if (smask) {
+                        float d0 = 0.f, d1 = 0.f;
+                        add_src(i0 + kSX, j0 + yc, k, d0, cy, d1);
+                    }
+                    Ec[kEC + ec] = e_next(A.y, Ec[kEC + ec], B.y, cy);
+                } else {
+                    float cz = curl2(Hc[kHC + hc], Hc[kHC + hc - 1], idx, Hc[hc], Hc[hc - kHBX], idy);
+                    if (smask) {
+                        float d0 = 0.f, d1 = 0.f;
+                        add_src(i0 + kSX, j0 + yc, k, d0, d1, cz);
+                    }
+                    Ec[2 * kEC + ec] = e_next(A.z, Ec[2 * kEC + ec], B.z, cz);
+                }
             }
-            const int c = (int)Cc[yr * CBX + xr];
-            const float4 A = tab(3 * c), B = tab(3 * c + 1);
-            const float ca = cr == 0 ? A.x : (cr == 1 ? A.y : A.z);
-            const float cb = cr == 0 ? B.x : (cr == 1 ? B.y : B.z);
-            const int ep = cr * kEC + yr * kEBX + xr;
-            Ec[ep] = e_next(ca, Ec[ep], cb, cu);
         }
     }
     // after a timed-out wait: wait (bounded) for the copies still in flight
     if (tid == 0)
         for (int q = consumed; q < issued; ++q) mbar_wait(&bar[q % kNS], (unsigned)(q / kNS) & 1u);
     if (L.energy) {
-        const double s = block_sum((double)acc, sred);
+        const double s = block_sum((double)acc + (double)acc_c, sred);
         if (tid == 0) L.part_f[t] = s;
     }
     finish_step(L, n, sred, &s_last);
@@ -858,8 +946,9 @@ static cudaError_t step_attrs()
     if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<uint8_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStepSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<uint16_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStepSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<uint16_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStepSmem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(mag_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMagSmemMax);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(mag_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMagSmemMax);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(mag_kernel<true, uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMagSmemMax);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(mag_kernel<true, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMagSmemMax);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(mag_kernel<false, uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMagSmemMax);
     done = e == cudaSuccess;
     return e;
 }
@@ -873,24 +962,12 @@ int step_blocks_per_sm(bool cls16)
     return nb;
 }
 
-static void launch_edges(const LaunchSet &L, bool advance, cudaStream_t s)
-{
-    const dim3 grid((L.emax + 255) / 256, L.ncomp);
-    if (advance) {
-        if (L.cls16) mag_edge_kernel<true, uint16_t><<<grid, 256, 0, s>>>(L);
-        else mag_edge_kernel<true, uint8_t><<<grid, 256, 0, s>>>(L);
-    } else {
-        mag_edge_kernel<false, uint8_t><<<grid, 256, 0, s>>>(L);
-    }
-}
-
 cudaError_t launch_half(const LaunchSet &L, cudaStream_t s)
 {
     cudaError_t e = step_attrs();
     if (e != cudaSuccess) return e;
     if (L.ncomp) {
-        launch_edges(L, false, s);
-        mag_kernel<false><<<L.ncomp, kMagThreads, L.mag_smem, s>>>(L);
+        mag_kernel<false, uint8_t><<<L.ncomp, kMagThreads, L.mag_smem, s>>>(L);
     }
     const dim3 blk(kTX, kTY);
     if (L.cls16) h_half_kernel<uint16_t><<<L.grid_h, blk, 0, s>>>(L);
@@ -898,30 +975,41 @@ cudaError_t launch_half(const LaunchSet &L, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_step(const LaunchSet &L, cudaStream_t s, cudaStream_t s_mag, cudaEvent_t ev_fork, cudaEvent_t ev_join,
-                        cudaEvent_t *prof)
+// One full step on stream s: the magnet kernel first, then the field sweep as
+// its programmatic dependent (PDL), so the sweep's CTAs are dispatched as soon
+// as the magnet CTAs are resident and the two run side by side; the next
+// step's magnet kernel, a plain launch, waits for both.  With prof (four
+// events) the events split the two and they run one after the other.
+cudaError_t launch_step(const LaunchSet &L, cudaStream_t s, cudaEvent_t *prof)
 {
     cudaError_t e = step_attrs();
     if (e != cudaSuccess) return e;
     if (L.ncomp) {
-        cudaEventRecord(ev_fork, s);
-        cudaStreamWaitEvent(s_mag, ev_fork, 0);
-        if (prof) cudaEventRecord(prof[2], s_mag);
-        launch_edges(L, true, s_mag);
-        mag_kernel<true><<<L.ncomp, kMagThreads, L.mag_smem, s_mag>>>(L);
-        if (prof) cudaEventRecord(prof[3], s_mag);
-        cudaEventRecord(ev_join, s_mag);
+        if (prof) cudaEventRecord(prof[2], s);
+        if (L.cls16) mag_kernel<true, uint16_t><<<L.ncomp, kMagThreads, L.mag_smem, s>>>(L);
+        else mag_kernel<true, uint8_t><<<L.ncomp, kMagThreads, L.mag_smem, s>>>(L);
+        if (prof) cudaEventRecord(prof[3], s);
     }
     if (prof) cudaEventRecord(prof[0], s);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(L.nftiles);
+    cfg.blockDim = dim3(kST);
+    cfg.dynamicSmemBytes = kStepSmem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = (L.ncomp && !prof) ? 1 : 0;
     if (L.cls16) {
-        if (L.stab) step_kernel<uint16_t, true><<<L.nftiles, kST, kStepSmem, s>>>(L);
-        else step_kernel<uint16_t, false><<<L.nftiles, kST, kStepSmem, s>>>(L);
+        if (L.stab) e = cudaLaunchKernelEx(&cfg, step_kernel<uint16_t, true>, L);
+        else e = cudaLaunchKernelEx(&cfg, step_kernel<uint16_t, false>, L);
     } else {
-        if (L.stab) step_kernel<uint8_t, true><<<L.nftiles, kST, kStepSmem, s>>>(L);
-        else step_kernel<uint8_t, false><<<L.nftiles, kST, kStepSmem, s>>>(L);
+        if (L.stab) e = cudaLaunchKernelEx(&cfg, step_kernel<uint8_t, true>, L);
+        else e = cudaLaunchKernelEx(&cfg, step_kernel<uint8_t, false>, L);
     }
+    if (e != cudaSuccess) return e;
     if (prof) cudaEventRecord(prof[1], s);
-    if (L.ncomp) cudaStreamWaitEvent(s, ev_join, 0);
     return cudaGetLastError();
 }
 

@@ -34,7 +34,9 @@ class _TorchAllocator:
 
         def _alloc(nbytes, stream, user):
             try:
-                return int(torch.cuda.caching_allocator_alloc(int(nbytes), stream=stream or 0))
+                # the legacy default stream (handle 1) is torch's default stream (handle 0)
+                s = stream if stream not in (None, _LEGACY_STREAM) else 0
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), stream=s))
             except Exception:
                 return None
 
@@ -59,12 +61,20 @@ def _config(nx, ny, nz, dx, dy, dz, dt, courant_factor, llg_tol, llg_max_iter, l
     return cfg
 
 
+_LEGACY_STREAM = 1   # cudaStreamLegacy
+
+
 def _torch_stream(device):
+    """torch's current stream as a cudaStream_t.  torch reports its default
+    stream as 0, which the C ABI reads as "create a stream of your own"; the
+    explicit legacy-stream handle keeps the work on torch's default stream, so
+    events and synchronisation on torch's side see it."""
     import torch
 
     if not torch.cuda.is_available():
         raise RuntimeError("no CUDA device: the solver runs only on the GPU")
-    return torch.cuda.current_stream(device).cuda_stream
+    h = torch.cuda.current_stream(device).cuda_stream
+    return h if h else _LEGACY_STREAM
 
 
 class FdtdLlg:
@@ -224,6 +234,22 @@ class FdtdLlg:
     def load_state(self, data: bytes):
         buf = C.create_string_buffer(data, len(data))
         check(_abi.load().fdtd_llg_load_state(self._h, buf, len(data)), self._h)
+
+    # --------------------------------------------------------------- tiling
+    def set_tiling(self, planes: int):
+        """z-planes per field-sweep task; 0 lets the library choose."""
+        check(_abi.load().fdtd_llg_set_tiling(self._h, int(planes)), self._h)
+
+    def get_tiling(self) -> int:
+        p = C.c_int32(0)
+        check(_abi.load().fdtd_llg_get_tiling(self._h, C.byref(p)), self._h)
+        return p.value
+
+    def autotune(self, trial_steps: int = 20) -> int:
+        """Time the candidate tilings with real steps (they advance the run) and keep the fastest."""
+        p = C.c_int32(0)
+        check(_abi.load().fdtd_llg_autotune(self._h, int(trial_steps), C.byref(p)), self._h)
+        return p.value
 
     # ------------------------------------------------------------ profiling
     def set_profiling(self, on: bool):

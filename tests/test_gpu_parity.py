@@ -191,16 +191,59 @@ def test_batch_equals_separate_runs_bitwise():
     batch = pkg.FdtdLlg.create_batch(dims, sp, dt=dt_common, probe_capacity=32)
     for q, x in enumerate(ws):
         pkg.configure(batch.batch_member(q), x)
+    # the same tiling on both sides: it fixes the order of the energy sum
+    batch.set_tiling(4)
     batch.step(25)
     for q, x in enumerate(ws):
         single = pkg.FdtdLlg.create(x.nx, x.ny, x.nz, x.dx, x.dy, x.dz, dt=dt_common, probe_capacity=32)
         pkg.configure(single, x)
+        single.set_tiling(4)
         single.step(25)
         m = batch.batch_member(q)
         for n in ("Ex", "Ez", "Hy", "dMx", "Hx_wall"):
             np.testing.assert_array_equal(m.get_field(n), single.get_field(n))
         np.testing.assert_array_equal(m.probe(1), single.probe(1))
         np.testing.assert_array_equal(m.energy(), single.energy())
+
+
+@pytest.mark.parametrize("seed", [4, 5])
+def test_tiling_changes_no_field_or_probe_bit(seed):
+    """The z-planes per sweep task only regroup the work: fields, magnet state
+    and probe samples agree to the bit across tilings (the oracle comparisons
+    above run at the default tiling); the energy differs only by the order of
+    its partial sums."""
+    w = W.random_small(seed, nx=70, ny=19, nz=23, steps=30)
+    runs = []
+    for planes in (0, 1, 5, 23, 64):
+        sim = pkg.from_workload(w, probe_capacity=64)
+        sim.set_tiling(planes)
+        sim.step(30)
+        sim.sync()
+        runs.append(sim)
+    assert runs[2].get_tiling() == 5 and runs[1].get_tiling() == 1
+    ref = runs[0]
+    for sim in runs[1:]:
+        for name in ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz", "dMx", "dMz", "Hx_wall", "Hz_wall"):
+            np.testing.assert_array_equal(sim.get_field(name), ref.get_field(name))
+        for p in range(len(w.probes)):
+            np.testing.assert_array_equal(sim.probe(p), ref.probe(p))
+        np.testing.assert_allclose(sim.energy(), ref.energy(), rtol=1e-12, atol=0)
+    for sim in runs:
+        sim.destroy()
+
+
+def test_autotune_keeps_a_candidate_and_advances_the_run():
+    w = W.random_small(6, nx=70, ny=19, nz=23, steps=200)
+    sim = pkg.from_workload(w, probe_capacity=256)
+    planes = sim.autotune(trial_steps=3)
+    assert 1 <= planes <= w.nz
+    assert sim.get_tiling() in (0, planes)
+    sim.step(1)
+    sim.sync()
+    assert sim.get_tiling() == planes
+    step, _ = sim.time_state()
+    assert step >= 4
+    sim.destroy()
 
 
 def test_llg_nonconvergence_is_reported():
@@ -238,8 +281,12 @@ def test_invalid_geometry_rejected():
 
 
 def test_torch_allocator_backs_device_memory():
+    import gc
+
     import torch
 
+    gc.collect()   # handles of earlier tests release their memory now, not during the measurement
+    torch.cuda.synchronize()
     before = torch.cuda.memory_allocated()
     w = W.cavity_block(steps=1)
     sim = pkg.from_workload(w, probe_capacity=4)
