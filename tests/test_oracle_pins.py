@@ -404,3 +404,24 @@ def test_magnet_coupling_matches_assembled_mean_operator():
     for c in np.flatnonzero(mid.ravel() > 0):
         m_new = oracle.llg_trapezoid(Mold.reshape(3, -1)[:, c], h0, He1[:, c], kappa, 0.02, 1.4e5)
         np.testing.assert_allclose(sim.M.reshape(3, -1)[:, c], m_new, rtol=0, atol=1e-9)
+
+
+def test_coupled_cavity_and_magnet_do_not_gain_energy_at_small_angles():
+    """A pulse rings a PEC cavity holding a YIG block (alpha > 0) at tiny
+    precession angles, where the change of M per half-push is far below
+    tol * Ms.  After the pulse the energy must not grow (Eq. LLG with damping
+    and lossless Maxwell: it decays).  Stopping the LLG iteration at the first
+    iterate, whose residual against M^n is just the size of the change, keeps
+    only the explicit part of the M-H coupling and makes this energy grow
+    ~10^4-fold in 3000 steps; the solve must take at least two iterates."""
+    from paper_2510_22221_b300 import workloads as W
+    from tests.helpers import oracle_from_workload
+
+    w = W.anticrossing_sweep(n_inst=1, n=10, mag=(4, 4, 2), b_lo=0.1, b_hi=0.1, steps=3000)[0]
+    sim = oracle_from_workload(w)
+    out = sim.run(3000)
+    E = out["energy"]
+    assert out["iters"].min() >= 2
+    tail = E[600:].reshape(-1, 200).mean(axis=1)    # the pulse is over by step ~400
+    assert np.all(np.diff(tail) <= 1e-12 * tail[0])
+    assert E[-1] < E[600]
