@@ -451,7 +451,9 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
             if (L.llg_fixed_iter > 0) {
                 if (r >= L.llg_fixed_iter) break;
             } else {
-                if (res < L.llg_tol) break;
+                // the test compares two iterates: from r = 2 on (the first
+                // iterate against M^n measures only the change of M)
+                if (r >= 2 && res < L.llg_tol) break;
                 if (r >= L.llg_max_iter) {
                     if (tid == 0) atomicOr(&L.ctl->status, ST_NOCONV);
                     break;
