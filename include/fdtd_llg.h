@@ -207,6 +207,9 @@ int fdtd_llg_set_profiling(fdtd_llg_t h, int32_t on);
  * record afterwards. */
 int fdtd_llg_read_profile(fdtd_llg_t h, fdtd_llg_profile *out, int32_t reset);
 
+/* The time step (s) shared by every instance of the handle's batch. */
+int fdtd_llg_get_dt(fdtd_llg_t h, double *dt);
+
 /* Tiling of the field sweep.  Each CTA of the sweep marches a column of
  * 64 x 8 cells through `planes` z-planes (clamped to each instance's nz), so
  * the sweep launches sum over instances of ceil(nx/64) ceil(ny/8)
@@ -230,6 +233,41 @@ int fdtd_llg_get_tiling(fdtd_llg_t h, int32_t *planes);
  * Errors: FDTD_E_INVAL (trial_steps < 1, a member handle), those of
  * fdtd_llg_step. */
 int fdtd_llg_autotune(fdtd_llg_t h, int32_t trial_steps, int32_t *planes);
+
+/* Spectra and mode fits of probe time series (the E_x spectra behind the
+ * anti-crossing maps of section "Results", the ESPRIT extraction of the
+ * polariton frequencies and Q factors, and Eq. omega_pm). */
+
+/* |sum_t w_t x_t exp(-2 pi i f t dt)| of probe `probe`, component comp (the
+ * column of fdtd_llg_probe: 0-2 E, 3-5 H, 6-8 M), over the samples the ring
+ * holds (the last min(steps, probe_capacity) steps, t = 0 the oldest), at
+ * f = f0 + i (f1 - f0)/(nf - 1), i < nf; w = 1 (window 0) or the symmetric
+ * Hann window 0.5 - 0.5 cos(2 pi t/(N-1)) (window 1).  Computed on the GPU in
+ * FP64 from the device ring; out: host array of nf doubles.  Synchronises the
+ * handle's stream.  Errors: FDTD_E_INVAL, FDTD_E_RANGE (probe id),
+ * FDTD_E_STATE (no samples yet), FDTD_E_OOM, FDTD_E_CUDA. */
+int fdtd_llg_probe_spectrum(fdtd_llg_t h, int32_t probe, int32_t comp, double f0, double f1, int32_t nf,
+                            int32_t window, double *out);
+
+/* ESPRIT on a real series x[0..n) sampled every dt: the `order` complex
+ * exponentials z_k^t of the Hankel data matrix's signal subspace (pencil
+ * length L = pencil, or min(n/3, 200) when pencil <= 0; needs
+ * order <= L <= n - order, L <= 4096), their amplitudes by least squares, and
+ * of those with positive frequency in [fmin, fmax] the max_modes of largest
+ * amplitude, sorted by frequency: freq (Hz), decay (1/s, amplitude
+ * ~ exp(-decay t)), amp (of the real cosine), q = pi freq / decay.  Output
+ * arrays hold max_modes doubles; *nfound receives the count.  Runs on the
+ * host in FP64; needs no GPU.  Errors: FDTD_E_INVAL (message in
+ * fdtd_llg_last_error(NULL)). */
+int fdtd_llg_fit_modes(const double *x, int64_t n, double dt, int32_t order, int32_t pencil, double fmin, double fmax,
+                       int32_t max_modes, double *freq, double *decay, double *amp, double *q, int32_t *nfound);
+
+/* Cavity frequency f_p and coupling g of Eq. omega_pm from n >= 2 hybrid
+ * pairs (f_plus[i] > f_minus[i], Hz) measured at different detunings: with
+ * S = f+ + f- and D = f+ - f-, Eq. omega_pm gives D^2 - S^2 = 4 (f_p^2 + g^2)
+ * - 4 f_p S, fitted by least squares.  The splitting at resonance is 2 g.
+ * Host, FP64.  Errors: FDTD_E_INVAL. */
+int fdtd_llg_fit_coupling(const double *f_plus, const double *f_minus, int32_t n, double *f_p, double *g);
 
 /* E push that allocates nothing.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory (code running

@@ -4,8 +4,10 @@ thin Python binding.  There is no CPU fallback: without the CUDA library or a
 GPU every entry point raises."""
 from ._abi import LLGError, load as load_library
 from .solver import FdtdLlg, Material
+from .spectra import fit_coupling, fit_modes
 
-__all__ = ["FdtdLlg", "Material", "LLGError", "load_library", "from_workload", "configure"]
+__all__ = ["FdtdLlg", "Material", "LLGError", "load_library", "from_workload", "configure", "fit_modes",
+           "fit_coupling"]
 
 
 def from_workload(w, probe_capacity=None, energy=True, llg_fixed_iter=0, llg_tol=1e-6, llg_max_iter=20,

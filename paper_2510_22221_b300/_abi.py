@@ -69,9 +69,15 @@ SIGNATURES = {
     "fdtd_llg_load_state": (C.c_int, [_vp, _vp, C.c_size_t]),
     "fdtd_llg_set_profiling": (C.c_int, [_vp, C.c_int32]),
     "fdtd_llg_read_profile": (C.c_int, [_vp, C.POINTER(Profile), C.c_int32]),
+    "fdtd_llg_get_dt": (C.c_int, [_vp, _dp]),
     "fdtd_llg_set_tiling": (C.c_int, [_vp, C.c_int32]),
     "fdtd_llg_get_tiling": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
     "fdtd_llg_autotune": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_int32)]),
+    "fdtd_llg_probe_spectrum": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_int32, C.c_int32,
+                                         _dp]),
+    "fdtd_llg_fit_modes": (C.c_int, [_dp, C.c_int64, C.c_double, C.c_int32, C.c_int32, C.c_double, C.c_double,
+                                    C.c_int32, _dp, _dp, _dp, _dp, C.POINTER(C.c_int32)]),
+    "fdtd_llg_fit_coupling": (C.c_int, [_dp, _dp, C.c_int32, _dp, _dp]),
     "fdtd_llg_e_push_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.c_int32,
                                          C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
                                          _vp, _vp]),
@@ -91,9 +97,10 @@ def load(build_if_missing: bool = True):
     global _lib
     if _lib is None:
         path = lib_path()
-        if not os.path.exists(path):
+        if not os.path.exists(path) or _build.stale():
             if not build_if_missing:
-                raise RuntimeError(f"CUDA library {path} is missing; run paper_2510_22221_b300._build.build()")
+                raise RuntimeError(f"CUDA library {path} is missing or was built from other sources; "
+                                   "run paper_2510_22221_b300._build.build()")
             _build.build()
         lib = C.CDLL(path)
         for name, (res, args) in SIGNATURES.items():

@@ -2,6 +2,7 @@
 from __future__ import annotations
 
 import glob
+import hashlib
 import os
 import subprocess
 
@@ -16,13 +17,33 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
-        return True
-    t = os.path.getmtime(LIB)
+def _deps():
     deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
-    deps += glob.glob(os.path.join(ROOT, "include", "*.h"))
-    return any(os.path.getmtime(d) > t for d in deps)
+    return sorted(deps + glob.glob(os.path.join(ROOT, "include", "*.h")))
+
+
+def sources_hash() -> str:
+    """sha1 over the library's sources and headers (names and contents)."""
+    h = hashlib.sha1()
+    for d in _deps():
+        h.update(os.path.relpath(d, ROOT).encode())
+        with open(d, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def stale() -> bool:
+    """True when the library is missing or was built from other sources than
+    the present ones (recorded beside it at build time; file times are not
+    trusted, they do not survive copies of the tree)."""
+    try:
+        with open(LIB + ".sha1") as f:
+            return f.read().strip() != sources_hash() or not os.path.exists(LIB)
+    except OSError:
+        return True
+
+
+_stale = stale
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -35,6 +56,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.check_call(cmd)
     os.replace(LIB + ".tmp", LIB)
+    with open(LIB + ".sha1", "w") as f:
+        f.write(sources_hash() + "\n")
     return LIB
 
 

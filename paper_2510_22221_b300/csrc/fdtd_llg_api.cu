@@ -1173,6 +1173,13 @@ extern "C" int fdtd_llg_load_state(fdtd_llg_t h, const void *buf, size_t size)
 }
 
 // ------------------------------------------------------------- profiling
+extern "C" int fdtd_llg_get_dt(fdtd_llg_t h, double *dt)
+{
+    if (!h || !h->sim || !dt) return fail(h, FDTD_E_INVAL, "null handle or output");
+    *dt = h->sim->dt;
+    return FDTD_OK;
+}
+
 extern "C" int fdtd_llg_set_tiling(fdtd_llg_t h, int32_t planes)
 {
     if (!h || !h->sim) return fail(h, FDTD_E_INVAL, "null handle");
@@ -1265,3 +1272,29 @@ extern "C" int fdtd_llg_read_profile(fdtd_llg_t h, fdtd_llg_profile *out, int32_
     if (reset) S->prof = fdtd_llg_profile{};
     return FDTD_OK;
 }
+
+// ---------------------------------------------- hooks for spectra.cu
+namespace fl {
+int fail_handle(fdtd_llg_t h, int code, const std::string &msg) { return fail(h, code, msg); }
+
+// The device probe ring of an instance and the window of samples it holds:
+// rows first .. first+count-1 (mod cap) are the states after those steps.
+int probe_ring_view(fdtd_llg_t h, int32_t probe, const double **ring, int *cap, int *nprobe, long long *first,
+                    int *count, double *dt, cudaStream_t *stream)
+{
+    if (!is_member(h)) return fail(h, FDTD_E_INVAL, "probe_spectrum needs an instance handle");
+    Instance *I = inst_of(h);
+    Sim *S = h->sim;
+    if (probe < 0 || probe >= (int)I->probes.size()) return fail(h, FDTD_E_RANGE, "probe id out of range");
+    const long long c = S->cfg.probe_capacity;
+    const long long have = (I->probe_buf && I->probe_alloc == (int)I->probes.size()) ? std::min<long long>(S->host_step, c) : 0;
+    *ring = I->probe_buf;
+    *cap = (int)c;
+    *nprobe = I->probe_alloc;
+    *first = S->host_step - have;
+    *count = (int)have;
+    *dt = S->dt;
+    *stream = S->stream;
+    return FDTD_OK;
+}
+}  // namespace fl

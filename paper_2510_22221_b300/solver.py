@@ -180,6 +180,13 @@ class FdtdLlg:
     def sync(self):
         check(_abi.load().fdtd_llg_sync(self._h), self._h)
 
+    @property
+    def dt(self) -> float:
+        """Time step (s) of the handle's batch."""
+        v = C.c_double()
+        check(_abi.load().fdtd_llg_get_dt(self._h, C.byref(v)), self._h)
+        return v.value
+
     def time_state(self):
         s = C.c_int64()
         half = C.c_int32()
@@ -234,6 +241,15 @@ class FdtdLlg:
     def load_state(self, data: bytes):
         buf = C.create_string_buffer(data, len(data))
         check(_abi.load().fdtd_llg_load_state(self._h, buf, len(data)), self._h)
+
+    def probe_spectrum(self, pid: int, comp: int, f0: float, f1: float, nf: int, window: str = "hann") -> np.ndarray:
+        """|DFT| of probe `pid`, column `comp` (0-2 E, 3-5 H, 6-8 M), at nf
+        frequencies from f0 to f1, computed on the GPU from the device ring."""
+        out = np.zeros(int(nf))
+        win = {"rect": 0, "hann": 1}[window]
+        check(_abi.load().fdtd_llg_probe_spectrum(self._h, int(pid), int(comp), float(f0), float(f1), int(nf), win,
+                                                   out.ctypes.data_as(C.POINTER(C.c_double))), self._h)
+        return out
 
     # --------------------------------------------------------------- tiling
     def set_tiling(self, planes: int):

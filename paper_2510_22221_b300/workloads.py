@@ -138,6 +138,33 @@ def bias_sweep(n_inst=64, steps=10000, seed=0, L=7.57e-2) -> list:
     return out
 
 
+def anticrossing_sweep(n_inst=5, b_lo=0.0375, b_hi=0.06, steps=16000, nx=24, ny=16, nz=5, d=3.15e-3,
+                       mag=(4, 4, 2)) -> list:
+    """A bias sweep through one magnon-photon anti-crossing at a size the FP64
+    oracle runs in seconds: a flat PEC box (nx, ny, nz cells of side d: 7.6 x
+    5.0 x 1.6 cm) whose only mode near 3.6 GHz is TM110 (E along z, H in the
+    x-y plane, largest at the y = 0 wall); a YIG block mx x my x mz against
+    that wall, centred in x and z; bias along z from b_lo to b_hi (T), over
+    which the block's uniform precession mode crosses TM110 (the splitting is
+    smallest near 0.05 T for the default block); z-current at the box centre,
+    3.7 GHz pulse; probe at the centre (E_z).  Higher magnetostatic modes of
+    the block cross the cavity mode above ~0.06 T."""
+    out = []
+    mx, my, mz = mag
+    for q in range(n_inst):
+        mats = [material(), material(eps_r=1.0, **YIG)]
+        mid = np.zeros((nz, ny, nx), dtype=np.uint8)
+        x0, z0 = nx // 2 - mx // 2, nz // 2 - mz // 2
+        mid[z0:z0 + mz, 0:my, x0:x0 + mx] = 1
+        b = b_lo + (b_hi - b_lo) * q / max(n_inst - 1, 1)
+        src = [dict(comp=2, i=nx // 2, j=ny // 2, k=nz // 2, J0=1.0, f0=3.7e9, Tp=0.0, tpk=0.0)]
+        probes = [(nx // 2, ny // 2, nz // 2)]
+        out.append(Workload(f"anticross_{q}", nx, ny, nz, d, d, d, 0.5, steps, mats, mid,
+                            np.array([0.0, 0.0, b / MU0]), src, probes,
+                            note=f"flat box {nx}x{ny}x{nz}, magnet {mx}x{my}x{mz} on the y=0 wall, bias {b:.4f} T"))
+    return out
+
+
 def adjoint_design(nx=128, ny=128, nz=64, steps=4000, seed=2, design=(32, 32, 4), block=(16, 16, 4)) -> Workload:
     """dx = 0.5 um PEC box, vacuum; design region design = (x, y, z) cells with
     eps_r ~ U[1, 12] (seed) between the source and the probe; a YIG block of

@@ -417,7 +417,7 @@ def test_coupled_cavity_and_magnet_do_not_gain_energy_at_small_angles():
     from paper_2510_22221_b300 import workloads as W
     from tests.helpers import oracle_from_workload
 
-    w = W.anticrossing_sweep(n_inst=1, n=10, mag=(4, 4, 2), b_lo=0.1, b_hi=0.1, steps=3000)[0]
+    w = W.anticrossing_sweep(n_inst=1, b_lo=0.1, b_hi=0.1, steps=3000)[0]
     sim = oracle_from_workload(w)
     out = sim.run(3000)
     E = out["energy"]
