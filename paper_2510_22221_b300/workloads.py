@@ -139,7 +139,7 @@ def bias_sweep(n_inst=64, steps=10000, seed=0, L=7.57e-2) -> list:
 
 
 def anticrossing_sweep(n_inst=5, b_lo=0.0375, b_hi=0.06, steps=16000, nx=24, ny=16, nz=5, d=3.15e-3,
-                       mag=(4, 4, 2)) -> list:
+                       mag=(4, 4, 2), design=None, seed=3) -> list:
     """A bias sweep through one magnon-photon anti-crossing at a size the FP64
     oracle runs in seconds: a flat PEC box (nx, ny, nz cells of side d: 7.6 x
     5.0 x 1.6 cm) whose only mode near 3.6 GHz is TM110 (E along z, H in the
@@ -159,8 +159,13 @@ def anticrossing_sweep(n_inst=5, b_lo=0.0375, b_hi=0.06, steps=16000, nx=24, ny=
         b = b_lo + (b_hi - b_lo) * q / max(n_inst - 1, 1)
         src = [dict(comp=2, i=nx // 2, j=ny // 2, k=nz // 2, J0=1.0, f0=3.7e9, Tp=0.0, tpk=0.0)]
         probes = [(nx // 2, ny // 2, nz // 2)]
+        eps, box = None, None
+        if design is not None:   # a dielectric design box between the source and the magnet
+            ddx, ddy, ddz = design
+            box = (nx // 2 - ddx // 2, my + 1, nz // 2 - ddz // 2, ddx, ddy, ddz)
+            eps = np.random.default_rng(seed).uniform(1.0, 4.0, size=(ddz, ddy, ddx))
         out.append(Workload(f"anticross_{q}", nx, ny, nz, d, d, d, 0.5, steps, mats, mid,
-                            np.array([0.0, 0.0, b / MU0]), src, probes,
+                            np.array([0.0, 0.0, b / MU0]), src, probes, eps_design=eps, design_box=box,
                             note=f"flat box {nx}x{ny}x{nz}, magnet {mx}x{my}x{mz} on the y=0 wall, bias {b:.4f} T"))
     return out
 
@@ -184,6 +189,30 @@ def adjoint_design(nx=128, ny=128, nz=64, steps=4000, seed=2, design=(32, 32, 4)
     return Workload(f"adjoint_design_{nx}x{ny}x{nz}", nx, ny, nz, 0.5e-6, 0.5e-6, 0.5e-6, 0.5, steps, mats, mid,
                     np.array([0.0, 0.0, 0.1 / MU0]), src, probes, eps_design=eps, design_box=box,
                     note=f"design {dx_}x{dy_}x{dz_} eps_r~U[1,12], YIG {bx}x{by}x{bz}")
+
+
+def adjoint_small(n=24, steps=400, seed=2, design=(8, 8, 2), block=(4, 4, 2), f0=20e12) -> Workload:
+    """The adjoint case at a size the FP64 oracle differentiates in seconds:
+    an n^3 PEC box of 0.5 um cells, vacuum; a design region of design cells
+    with eps_r ~ U[1, 12] (seed) between an x-current source and an E probe on
+    the x axis through the centre, a YIG block past the design region (0.1 T
+    on z).  f0 = 20 THz puts several wavelengths between source and probe."""
+    rng = np.random.default_rng(seed)
+    mats = [material(), material(eps_r=1.0, **YIG)]
+    mid = np.zeros((n, n, n), dtype=np.uint8)
+    c = n // 2
+    dx_, dy_, dz_ = design
+    bx, by, bz = block
+    x_d = n // 6
+    box = (x_d, c - dy_ // 2, c - dz_ // 2, dx_, dy_, dz_)
+    x_m = x_d + dx_ + 2
+    mid[c - bz // 2:c - bz // 2 + bz, c - by // 2:c - by // 2 + by, x_m:x_m + bx] = 1
+    eps = rng.uniform(1.0, 12.0, size=(dz_, dy_, dx_))
+    src = [dict(comp=0, i=max(x_d - 2, 1), j=c, k=c, J0=1.0, f0=f0, Tp=0.0, tpk=0.0)]
+    probes = [(min(x_m + bx + 2, n - 2), c, c)]
+    return Workload(f"adjoint_small_{n}", n, n, n, 0.5e-6, 0.5e-6, 0.5e-6, 0.5, steps, mats, mid,
+                    np.array([0.0, 0.0, 0.1 / MU0]), src, probes, eps_design=eps, design_box=box,
+                    note=f"{n}^3, design {dx_}x{dy_}x{dz_} eps_r~U[1,12], YIG {bx}x{by}x{bz}")
 
 
 def random_small(seed, nx=13, ny=11, nz=9, steps=40, magnets=True, sigma=0.0, design=False) -> Workload:
