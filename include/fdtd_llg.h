@@ -234,6 +234,34 @@ int fdtd_llg_get_tiling(fdtd_llg_t h, int32_t *planes);
  * fdtd_llg_step. */
 int fdtd_llg_autotune(fdtd_llg_t h, int32_t trial_steps, int32_t *planes);
 
+/* Adjoint (reverse-time) gradients of a probe objective.  Single-instance
+ * handles only.
+ *
+ * fdtd_llg_run_checkpointed: from step 0 (right after fdtd_llg_set_materials
+ * and the sources and probes), run nsteps steps like fdtd_llg_step while
+ * keeping a copy of the state (E, H, walls, M: 6 field arrays + walls + 3
+ * floats per magnet cell) every `interval` steps (0: ceil(sqrt(nsteps))), on
+ * the device through the handle's allocator.  With magnets the LLG solve must
+ * be a fixed map: llg_fixed_iter >= 2 at creation.  Errors: FDTD_E_INVAL,
+ * FDTD_E_STATE (not at step 0), FDTD_E_NOSYS (batch), FDTD_E_OOM.
+ *
+ * fdtd_llg_adjoint: the exact gradient of the discrete forward map of that
+ * run for an objective J whose derivative with respect to the recorded probe
+ * E samples is dJ_dE[n][p][c] (host, FP64, nsteps x nprobes x 3: step n's
+ * row, probe p, Ex/Ey/Ez of its cell).  Reverse sweep segment by segment
+ * from the last checkpoint: each segment's forward steps are recomputed
+ * (recording what the reverse step needs), then reversed step by step on the
+ * GPU (FP32 adjoint fields, FP64 gradient accumulation).  Outputs, host,
+ * FP64, either may be NULL: grad_eps[k][j][i], dJ/d eps_r of every cell of the
+ * design box given to fdtd_llg_set_materials; *grad_h0, dJ/d |H_bias| (per
+ * A/m) along the bias direction (M starts along it whatever its size).  The
+ * call may be repeated with other dJ_dE; afterwards the handle's state is
+ * that after the first checkpoint interval (read probes and energy before
+ * calling).  Errors: FDTD_E_STATE (no checkpointed run; grad_eps without a
+ * design box), FDTD_E_INVAL, FDTD_E_OOM, FDTD_E_UNSTABLE, FDTD_E_CUDA. */
+int fdtd_llg_run_checkpointed(fdtd_llg_t h, int64_t nsteps, int32_t interval);
+int fdtd_llg_adjoint(fdtd_llg_t h, const double *dJ_dE, double *grad_eps, double *grad_h0);
+
 /* Spectra and mode fits of probe time series (the E_x spectra behind the
  * anti-crossing maps of section "Results", the ESPRIT extraction of the
  * polariton frequencies and Q factors, and Eq. omega_pm). */

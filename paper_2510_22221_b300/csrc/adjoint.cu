@@ -1,0 +1,593 @@
+// Reverse-time (adjoint) kernels of the Yee-Maxwell + LLG step (arxiv
+// 2510.22221, section "Numerical Model"): the exact transpose of the discrete
+// forward map of kernels_fwd.cu, one reverse step at a time.
+//
+// Forward step n:  E' = ca E + cb (C_H H - J);  then two half-pushes
+//   H* = H - ch C_E E',  M' = LLG(M, H*),  H' = H* - P (M' - M)
+// (P: half the change of each adjacent cell's M on a face).  Its transpose,
+// with lambda the adjoint of the step's outputs:
+//   magnetic regions (adj_mag_kernel): both half-pushes reversed through the
+//     fixed number of Jacobi iterates of the trapezoidal LLG solve (the 3 x 9
+//     Jacobian of one cell's increment by forward-mode dual numbers), giving
+//     the adjoint of the faces' H and of M at the step's start, of the curl
+//     terms, and d J / d |H_bias|;
+//   adj_curl_h_kernel:  lambda_E' = lambda_E - (dt/mu0) C_H lambda_H (for a
+//     non-magnetic face both half-pushes pass lambda_H through; magnetic faces
+//     carry the magnet kernel's curl adjoint here);
+//   adj_design_kernel:  d J / d eps_edge += (cb/dt) lambda_E' (E^n - E^{n+1});
+//   adj_curl_e_kernel:  lambda_H += C_E (cb lambda_E'),  lambda_E = ca lambda_E';
+//   adj_fix_kernel:     the magnetic faces take their own adjoint.
+// C_E^T = C_H on the Yee grid, so the transposed curls are the forward curls.
+#include "fdtd_llg_internal.h"
+
+namespace fl {
+
+namespace {
+
+// ------------------------------------------------------------ dual numbers
+struct D1 {
+    float v, d;
+};
+__device__ __forceinline__ D1 mk(float v, float d = 0.f) { return {v, d}; }
+__device__ __forceinline__ D1 operator+(D1 a, D1 b) { return {a.v + b.v, a.d + b.d}; }
+__device__ __forceinline__ D1 operator-(D1 a, D1 b) { return {a.v - b.v, a.d - b.d}; }
+__device__ __forceinline__ D1 operator-(D1 a) { return {-a.v, -a.d}; }
+__device__ __forceinline__ D1 operator*(D1 a, D1 b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+__device__ __forceinline__ D1 operator*(float s, D1 a) { return {s * a.v, s * a.d}; }
+__device__ __forceinline__ D1 operator+(D1 a, float s) { return {a.v + s, a.d}; }
+__device__ __forceinline__ D1 operator+(float s, D1 a) { return {a.v + s, a.d}; }
+__device__ __forceinline__ D1 operator/(D1 a, D1 b) { return {a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)}; }
+__device__ __forceinline__ D1 dsqrt(D1 a)
+{
+    const float r = sqrtf(a.v);
+    return {r, r > 0.f ? 0.5f * a.d / r : 0.f};
+}
+__device__ __forceinline__ float dsqrt(float a) { return sqrtf(a); }
+
+// One cell's LLG increment in the bias frame (the arithmetic of mag_kernel):
+// m deviation from Ms e3, hs = H_eff at the start of the half-push, h = H_eff
+// of the previous iterate (both with the bias on e3); returns dl = M^{r} - M^n.
+template <typename T>
+__device__ __forceinline__ void llg_inc(const T m[3], const T hs[3], const T h[3], const MagMat &mm, T dl[3])
+{
+    const T Mz = m[2] + mm.Ms;
+    const float dam = mm.alpha * mm.inv_Ms, k = mm.kappa;
+    const T ax = -(k * h[0] + dam * m[0]);
+    const T ay = -(k * h[1] + dam * m[1]);
+    const T az = -(k * h[2] + dam * m[2] + mm.alpha);
+    const T rx = (-k) * (m[1] * hs[2] - Mz * hs[1]) - k * (m[1] * h[2] - Mz * h[1]);
+    const T ry = (-k) * (Mz * hs[0] - m[0] * hs[2]) - k * (Mz * h[0] - m[0] * h[2]);
+    const T rz = (-k) * (m[0] * hs[1] - m[1] * hs[0]) - k * (m[0] * h[1] - m[1] * h[0]);
+    const T ar = ax * rx + ay * ry + az * rz;
+    const T inv1 = mk(1.f) / (1.f + (ax * ax + ay * ay + az * az));
+    const T dx = (rx + ar * ax - (ay * rz - az * ry)) * inv1;
+    const T dy = (ry + ar * ay - (az * rx - ax * rz)) * inv1;
+    const T dz = (rz + ar * az - (ax * ry - ay * rx)) * inv1;
+    const T nM2 = m[0] * m[0] + m[1] * m[1] + Mz * Mz;
+    const T md2 = 2.f * (m[0] * dx + m[1] * dy + Mz * dz) + (dx * dx + dy * dy + dz * dz);
+    const T nM = dsqrt(nM2), nMt = dsqrt(nM2 + md2);
+    const T s1 = -(md2 / (nMt * (nM + nMt)));
+    dl[0] = dx + s1 * (m[0] + dx);
+    dl[1] = dy + s1 * (m[1] + dy);
+    dl[2] = dz + s1 * (Mz + dz);
+}
+template <>
+__device__ __forceinline__ void llg_inc<float>(const float m[3], const float hs[3], const float h[3], const MagMat &mm,
+                                               float dl[3])
+{
+    const float Mz = m[2] + mm.Ms;
+    const float dam = mm.alpha * mm.inv_Ms, k = mm.kappa;
+    const float ax = -(k * h[0] + dam * m[0]);
+    const float ay = -(k * h[1] + dam * m[1]);
+    const float az = -(k * h[2] + dam * m[2] + mm.alpha);
+    const float rx = (-k) * (m[1] * hs[2] - Mz * hs[1]) - k * (m[1] * h[2] - Mz * h[1]);
+    const float ry = (-k) * (Mz * hs[0] - m[0] * hs[2]) - k * (Mz * h[0] - m[0] * h[2]);
+    const float rz = (-k) * (m[0] * hs[1] - m[1] * hs[0]) - k * (m[0] * h[1] - m[1] * h[0]);
+    const float ar = ax * rx + ay * ry + az * rz;
+    const float inv1 = 1.f / (1.f + (ax * ax + ay * ay + az * az));
+    const float dx = (rx + ar * ax - (ay * rz - az * ry)) * inv1;
+    const float dy = (ry + ar * ay - (az * rx - ax * rz)) * inv1;
+    const float dz = (rz + ar * az - (ax * ry - ay * rx)) * inv1;
+    const float nM2 = m[0] * m[0] + m[1] * m[1] + Mz * Mz;
+    const float md2 = 2.f * (m[0] * dx + m[1] * dy + Mz * dz) + (dx * dx + dy * dy + dz * dz);
+    const float nM = sqrtf(nM2), nMt = sqrtf(nM2 + md2);
+    const float s1 = -md2 / (nMt * (nM + nMt));
+    dl[0] = dx + s1 * (m[0] + dx);
+    dl[1] = dy + s1 * (m[1] + dy);
+    dl[2] = dz + s1 * (Mz + dz);
+}
+
+__device__ __forceinline__ void to_fr(const float *R, const float g[3], float l[3])
+{
+    l[0] = R[0] * g[0] + R[1] * g[1] + R[2] * g[2];
+    l[1] = R[3] * g[0] + R[4] * g[1] + R[5] * g[2];
+    l[2] = R[6] * g[0] + R[7] * g[1] + R[8] * g[2];
+}
+__device__ __forceinline__ void from_fr(const float *R, const float l[3], float g[3])
+{
+    g[0] = R[0] * l[0] + R[3] * l[1] + R[6] * l[2];
+    g[1] = R[1] * l[0] + R[4] * l[1] + R[7] * l[2];
+    g[2] = R[2] * l[0] + R[5] * l[1] + R[8] * l[2];
+}
+__device__ __forceinline__ float curl2a(float a1, float b1, float i1, float a2, float b2, float i2)
+{
+    return __fsub_rn(__fmul_rn(__fsub_rn(a1, b1), i1), __fmul_rn(__fsub_rn(a2, b2), i2));
+}
+
+// face f of a box: axis, indices, adjacent cells (-1 outside)
+__device__ __forceinline__ void fdecode(int f, int bx, int by, int bz, int &a, int &fi, int &fj, int &fk, int &vl, int &vr)
+{
+    const int nfx = (bx + 1) * by * bz, nfy = bx * (by + 1) * bz;
+    vl = vr = -1;
+    if (f < nfx) {
+        a = 0; fi = f % (bx + 1); fj = (f / (bx + 1)) % by; fk = f / ((bx + 1) * by);
+        if (fi > 0) vl = (fk * by + fj) * bx + fi - 1;
+        if (fi < bx) vr = (fk * by + fj) * bx + fi;
+    } else if (f < nfx + nfy) {
+        const int g = f - nfx;
+        a = 1; fi = g % bx; fj = (g / bx) % (by + 1); fk = g / (bx * (by + 1));
+        if (fj > 0) vl = (fk * by + fj - 1) * bx + fi;
+        if (fj < by) vr = (fk * by + fj) * bx + fi;
+    } else {
+        const int g = f - nfx - nfy;
+        a = 2; fi = g % bx; fj = (g / bx) % by; fk = g / (bx * by);
+        if (fk > 0) vl = ((fk - 1) * by + fj) * bx + fi;
+        if (fk < bz) vr = (fk * by + fj) * bx + fi;
+    }
+}
+
+__device__ __forceinline__ float *hx_at(const Inst *I, float *F0, int i, int j, int k, float *wall)
+{
+    return (i == I->nx) ? wall + (long long)k * I->ny + j : F0 + 3 * I->fstride + (long long)k * I->plane + (long long)j * I->px + i;
+}
+__device__ __forceinline__ float *hy_at(const Inst *I, float *F0, int i, int j, int k, float *wall)
+{
+    return (j == I->ny) ? wall + (long long)I->ny * I->nz + (long long)k * I->nx + i
+                        : F0 + 4 * I->fstride + (long long)k * I->plane + (long long)j * I->px + i;
+}
+__device__ __forceinline__ float *hz_at(const Inst *I, float *F0, int i, int j, int k, float *wall)
+{
+    return (k == I->nz) ? wall + (long long)I->ny * I->nz + (long long)I->nx * I->nz + (long long)j * I->nx + i
+                        : F0 + 5 * I->fstride + (long long)k * I->plane + (long long)j * I->px + i;
+}
+
+// Workspace of one region (floats), nf faces, V cells, R iterates:
+//   Hs1, Hs2, C, lamHout, lamHin, lamC, fix (7 nf);
+//   m1, m2, DL1, DL2, lamM, lamDl, lamA, lamHsm, lamHg (9 x 3V), D1[R], D2[R] (2R x 3V).
+struct RegionWS {
+    float *Hs1, *Hs2, *C, *lamHout, *lamHin, *lamC, *fix;
+    float *m1, *m2, *DL1, *DL2, *lamM, *lamDl, *lamA, *lamHsm, *lamHg, *D1, *D2;
+};
+__device__ __forceinline__ RegionWS carve(float *w, int nf, int V, int R)
+{
+    RegionWS r;
+    r.Hs1 = w; r.Hs2 = r.Hs1 + nf; r.C = r.Hs2 + nf; r.lamHout = r.C + nf; r.lamHin = r.lamHout + nf;
+    r.lamC = r.lamHin + nf; r.fix = r.lamC + nf;
+    float *p = r.fix + nf;
+    r.m1 = p; r.m2 = p + 3 * V; r.DL1 = p + 6 * V; r.DL2 = p + 9 * V; r.lamM = p + 12 * V; r.lamDl = p + 15 * V;
+    r.lamA = p + 18 * V; r.lamHsm = p + 21 * V; r.lamHg = p + 24 * V;
+    r.D1 = p + 27 * V;
+    r.D2 = r.D1 + 3 * V * R;
+    return r;
+}
+
+// Cell v's inputs to iteration r of a half-push: hs (bias frame, with bias),
+// h (bias frame, from D^{r-1}; Dprev NULL for r = 1), m.
+__device__ void cell_inputs(const MagComp &C, const Inst *I, const float *R9, const uint8_t *smat, int V, const float *Hs,
+                            const float *Cc, const float *Dprev, const float *m, int v, float hs[3], float h[3],
+                            float mm[3], int nfx, int nfy)
+{
+    const int bx = C.bx, by = C.by, bxy = C.bx * C.by;
+    const int li = v % bx, lj = (v / bx) % by, lk = v / bxy;
+    const int fx0 = (lk * by + lj) * (bx + 1) + li, fy0 = nfx + (lk * (by + 1) + lj) * bx + li,
+              fz0 = nfx + nfy + (lk * by + lj) * bx + li;
+    const int f0[3] = {fx0, fy0, fz0}, f1[3] = {fx0 + 1, fy0 + bx, fz0 + bxy};
+    float Hm[3], A[3];
+    for (int a = 0; a < 3; ++a) {
+        Hm[a] = 0.5f * (Hs[f0[a]] + Hs[f1[a]]);
+        A[a] = 0.5f * ((Hs[f0[a]] - Cc[f0[a]]) + (Hs[f1[a]] - Cc[f1[a]]));
+    }
+    if (Dprev) {
+        const int st[3] = {1, bx, bxy};
+        const bool lo[3] = {li > 0, lj > 0, lk > 0}, hi[3] = {li < bx - 1, lj < by - 1, lk < C.bz - 1};
+        for (int a = 0; a < 3; ++a) {
+            const float dm = lo[a] && smat[v - st[a]] != 0xFF ? Dprev[a * V + v - st[a]] : 0.f;
+            const float dp = hi[a] && smat[v + st[a]] != 0xFF ? Dprev[a * V + v + st[a]] : 0.f;
+            A[a] -= 0.25f * (dm + 2.f * Dprev[a * V + v] + dp);
+        }
+    }
+    to_fr(R9, Hm, hs);
+    to_fr(R9, A, h);
+    hs[2] += I->h0n;
+    h[2] += I->h0n;
+    mm[0] = m[v];
+    mm[1] = m[V + v];
+    mm[2] = m[2 * V + v];
+}
+
+// Forward half-push of a region (R Jacobi iterates) from faces Hs and m: the
+// iterates D^r (global axes, r = 1..R) into D, the last increment (bias
+// frame) into DL, the result faces into Hout (owned faces) and m + DL into mout.
+__device__ void fwd_half(const MagComp &C, const Inst *I, const float *R9, const uint8_t *smat, int V, int nf, int R,
+                         const float *Hs, const float *Cc, const float *m, float *D, float *DL, float *Hout, float *mout,
+                         int nfx, int nfy)
+{
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int r = 1; r <= R; ++r) {
+        const float *Dp = r >= 2 ? D + 3 * V * (r - 2) : nullptr;
+        float *Dr = D + 3 * V * (r - 1);
+        for (int v = tid; v < V; v += nth) {
+            const int mt = smat[v];
+            if (mt == 0xFF) {
+                Dr[v] = Dr[V + v] = Dr[2 * V + v] = 0.f;
+                continue;
+            }
+            float hs[3], h[3], mm[3], dl[3], dg[3];
+            cell_inputs(C, I, R9, smat, V, Hs, Cc, Dp, m, v, hs, h, mm, nfx, nfy);
+            llg_inc<float>(mm, hs, h, I->mm[mt], dl);
+            from_fr(R9, dl, dg);
+            for (int a = 0; a < 3; ++a) Dr[a * V + v] = dg[a];
+            if (r == R)
+                for (int a = 0; a < 3; ++a) DL[a * V + v] = dl[a];
+        }
+        __syncthreads();
+    }
+    const float *DR = D + 3 * V * (R - 1);
+    for (int f = tid; f < nf; f += nth) {
+        int a, fi, fj, fk, vl, vr;
+        fdecode(f, C.bx, C.by, C.bz, a, fi, fj, fk, vl, vr);
+        const bool inl = vl >= 0 && smat[vl] != 0xFF, inr = vr >= 0 && smat[vr] != 0xFF;
+        Hout[f] = (inl || inr) ? (Hs[f] - Cc[f]) - 0.5f * ((inl ? DR[a * V + vl] : 0.f) + (inr ? DR[a * V + vr] : 0.f)) : 0.f;
+    }
+    for (int v = tid; v < 3 * V; v += nth) mout[v] = m[v] + (smat[v % V] != 0xFF ? DL[v] : 0.f);
+    __syncthreads();
+}
+
+// Reverse of one half-push.  In: lamHout (faces), lamM (adjoint of the output
+// m, bias frame; overwritten with the adjoint of the input m).  Out: lamHin,
+// lamC (faces); *gh0 accumulates d J / d |H_bias| of this thread's cells.
+__device__ void rev_half(const MagComp &C, const Inst *I, const float *R9, const uint8_t *smat, int V, int nf, int R,
+                         const float *Hs, const float *Cc, const float *m, const float *D, RegionWS &W, const float *lamHout,
+                         float *lamHin, float *lamC, double *gh0, int nfx, int nfy)
+{
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int bx = C.bx, by = C.by, bxy = bx * by;
+    // direct terms of H_out = H* - P D^R, H* = Hs - C; adjoint of D^R and of dl^R
+    for (int f = tid; f < nf; f += nth) {
+        lamHin[f] = lamHout[f];
+        lamC[f] = -lamHout[f];
+    }
+    for (int v = tid; v < V; v += nth) {
+        for (int a = 0; a < 3; ++a) W.lamA[a * V + v] = W.lamHsm[a * V + v] = 0.f;
+        if (smat[v] == 0xFF) {
+            for (int a = 0; a < 3; ++a) W.lamDl[a * V + v] = 0.f;
+            continue;
+        }
+        const int li = v % bx, lj = (v / bx) % by, lk = v / bxy;
+        const int fx0 = (lk * by + lj) * (bx + 1) + li, fy0 = nfx + (lk * (by + 1) + lj) * bx + li,
+                  fz0 = nfx + nfy + (lk * by + lj) * bx + li;
+        const float lD[3] = {-0.5f * (lamHout[fx0] + lamHout[fx0 + 1]), -0.5f * (lamHout[fy0] + lamHout[fy0 + bx]),
+                             -0.5f * (lamHout[fz0] + lamHout[fz0 + bxy])};
+        float l[3];
+        to_fr(R9, lD, l);   // D = R^T dl, so the adjoint of dl is R times that of D
+        for (int a = 0; a < 3; ++a) W.lamDl[a * V + v] = W.lamM[a * V + v] + l[a];
+    }
+    __syncthreads();
+    double g = 0.0;
+    for (int r = R; r >= 1; --r) {
+        const float *Dp = r >= 2 ? D + 3 * V * (r - 2) : nullptr;
+        for (int v = tid; v < V; v += nth) {
+            const int mt = smat[v];
+            if (mt == 0xFF) {
+                W.lamHg[v] = W.lamHg[V + v] = W.lamHg[2 * V + v] = 0.f;
+                continue;
+            }
+            float hs[3], h[3], mm[3];
+            cell_inputs(C, I, R9, smat, V, Hs, Cc, Dp, m, v, hs, h, mm, nfx, nfy);
+            const float ld[3] = {W.lamDl[v], W.lamDl[V + v], W.lamDl[2 * V + v]};
+            // J^T lambda, one input direction at a time (forward-mode duals)
+            float gin[9];
+            for (int q = 0; q < 9; ++q) {
+                D1 dm[3], dhs[3], dh[3], out[3];
+                for (int a = 0; a < 3; ++a) {
+                    dm[a] = mk(mm[a], q == a ? 1.f : 0.f);
+                    dhs[a] = mk(hs[a], q == 3 + a ? 1.f : 0.f);
+                    dh[a] = mk(h[a], q == 6 + a ? 1.f : 0.f);
+                }
+                llg_inc<D1>(dm, dhs, dh, I->mm[mt], out);
+                gin[q] = out[0].d * ld[0] + out[1].d * ld[1] + out[2].d * ld[2];
+            }
+            for (int a = 0; a < 3; ++a) {
+                W.lamM[a * V + v] += gin[a];
+                W.lamHsm[a * V + v] += gin[3 + a];   // bias frame, converted below
+            }
+            g += (double)gin[5] + (double)gin[8];     // |H_bias| enters hs and h on e3
+            float lh[3] = {gin[6], gin[7], gin[8]}, lg[3];
+            from_fr(R9, lh, lg);
+            for (int a = 0; a < 3; ++a) {
+                W.lamHg[a * V + v] = lg[a];
+                W.lamA[a * V + v] += lg[a];
+            }
+        }
+        __syncthreads();
+        if (r >= 2) {
+            // h depends on D^{r-1} through -1/4 (D_{v-1} + 2 D_v + D_{v+1}) per component
+            for (int v = tid; v < V; v += nth) {
+                if (smat[v] == 0xFF) {
+                    W.lamDl[v] = W.lamDl[V + v] = W.lamDl[2 * V + v] = 0.f;
+                    continue;
+                }
+                const int li = v % bx, lj = (v / bx) % by, lk = v / bxy;
+                const int st[3] = {1, bx, bxy};
+                const bool lo[3] = {li > 0, lj > 0, lk > 0}, hi[3] = {li < bx - 1, lj < by - 1, lk < C.bz - 1};
+                float lD[3];
+                for (int a = 0; a < 3; ++a) {
+                    const float gm = lo[a] ? W.lamHg[a * V + v - st[a]] : 0.f;
+                    const float gp = hi[a] ? W.lamHg[a * V + v + st[a]] : 0.f;
+                    lD[a] = -0.25f * (gm + 2.f * W.lamHg[a * V + v] + gp);
+                }
+                float l[3];
+                to_fr(R9, lD, l);
+                for (int a = 0; a < 3; ++a) W.lamDl[a * V + v] = l[a];
+            }
+            __syncthreads();
+        }
+    }
+    *gh0 += g;
+    // faces: A = mean(Hs - C), hs = R mean(Hs) + bias
+    for (int v = tid; v < V; v += nth) {
+        if (smat[v] == 0xFF) continue;
+        const float l[3] = {W.lamHsm[v], W.lamHsm[V + v], W.lamHsm[2 * V + v]};
+        float gq[3];
+        from_fr(R9, l, gq);
+        for (int a = 0; a < 3; ++a) W.lamHsm[a * V + v] = gq[a];
+    }
+    __syncthreads();
+    for (int f = tid; f < nf; f += nth) {
+        int a, fi, fj, fk, vl, vr;
+        fdecode(f, bx, by, C.bz, a, fi, fj, fk, vl, vr);
+        float sA = 0.f, sH = 0.f;
+        if (vl >= 0 && smat[vl] != 0xFF) { sA += 0.5f * W.lamA[a * V + vl]; sH += 0.5f * W.lamHsm[a * V + vl]; }
+        if (vr >= 0 && smat[vr] != 0xFF) { sA += 0.5f * W.lamA[a * V + vr]; sH += 0.5f * W.lamHsm[a * V + vr]; }
+        lamHin[f] += sA + sH;
+        lamC[f] -= sA;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSet A, int slot)
+{
+    __shared__ double sred[kMagThreads / 32];
+    const MagComp C = L.comps[blockIdx.x];
+    const Inst *I = L.insts + C.inst;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int V = C.V, bx = C.bx, by = C.by, bz = C.bz;
+    const int nfx = (bx + 1) * by * bz, nfy = bx * (by + 1) * bz, nf = nfx + nfy + bx * by * (bz + 1);
+    const int ex = bx + 1, exy = (bx + 1) * (by + 1), ne = exy * (bz + 1);
+    const int R = A.R;
+    float *wsb = A.ws + A.ws_off[blockIdx.x];
+    uint8_t *smat = reinterpret_cast<uint8_t *>(wsb);              // V bytes, rounded up to floats
+    RegionWS W = carve(wsb + (V + 3) / 4, nf, V, R);
+    float R9[9];
+    for (int q = 0; q < 9; ++q) R9[q] = I->R[q];
+    const float *T = C.tape + (long long)slot * C.tstride;          // m^{n+1/2}, H^{n+1/2} faces, E^{n+1} edges
+    const float *Ex = T + 3 * V + nf, *Ey = Ex + ne, *Ez = Ey + ne;
+    for (int v = tid; v < V; v += nth) smat[v] = C.mat[v];
+    for (int v = tid; v < 3 * V; v += nth) W.m1[v] = T[v];
+    const float ch = I->ch;
+    for (int f = tid; f < nf; f += nth) {
+        int a, fi, fj, fk, vl, vr;
+        fdecode(f, bx, by, bz, a, fi, fj, fk, vl, vr);
+        W.Hs1[f] = T[3 * V + f];
+        const int e0 = fk * exy + fj * ex + fi;
+        float cu = 0.f;
+        if (a == 0) cu = curl2a(Ez[e0 + ex], Ez[e0], I->idy, Ey[e0 + exy], Ey[e0], I->idz);
+        else if (a == 1) cu = curl2a(Ex[e0 + exy], Ex[e0], I->idz, Ez[e0 + 1], Ez[e0], I->idx);
+        else cu = curl2a(Ey[e0 + 1], Ey[e0], I->idx, Ex[e0 + ex], Ex[e0], I->idy);
+        W.C[f] = ch * cu;
+        // adjoint of the step's output faces (H^{n+3/2}): field arrays or walls
+        const int i = C.x0 + fi, j = C.y0 + fj, k = C.z0 + fk;
+        const bool own = (vl >= 0 && C.mat[vl] != 0xFF) || (vr >= 0 && C.mat[vr] != 0xFF);
+        W.lamHout[f] = own ? *(a == 0 ? hx_at(I, A.lamH, i, j, k, A.lamW)
+                                      : (a == 1 ? hy_at(I, A.lamH, i, j, k, A.lamW) : hz_at(I, A.lamH, i, j, k, A.lamW)))
+                           : 0.f;
+    }
+    __syncthreads();
+    // recompute both half-pushes of the step
+    fwd_half(C, I, R9, smat, V, nf, R, W.Hs1, W.C, W.m1, W.D1, W.DL1, W.Hs2, W.m2, nfx, nfy);
+    fwd_half(C, I, R9, smat, V, nf, R, W.Hs2, W.C, W.m2, W.D2, W.DL2, W.fix /*scratch*/, W.lamDl /*scratch*/, nfx, nfy);
+    // reverse: second half-push, then the first
+    double g = 0.0;
+    rev_half(C, I, R9, smat, V, nf, R, W.Hs2, W.C, W.m2, W.D2, W, W.lamHout, W.lamHin, W.lamC, &g, nfx, nfy);
+    for (int f = tid; f < nf; f += nth) {
+        W.lamHout[f] = W.lamHin[f];      // adjoint of H^{n+1}
+        W.fix[f] = W.lamC[f];            // curl adjoint of the second half-push
+    }
+    __syncthreads();
+    rev_half(C, I, R9, smat, V, nf, R, W.Hs1, W.C, W.m1, W.D1, W, W.lamHout, W.lamHin, W.lamC, &g, nfx, nfy);
+    // write back: for a magnetic face the curl sweep must see q/2 with
+    // q = -(lamC1 + lamC2) (a plain face contributes 2 lambda_H); afterwards
+    // the face takes lamHin, which adj_fix_kernel restores from fix
+    for (int f = tid; f < nf; f += nth) {
+        int a, fi, fj, fk, vl, vr;
+        fdecode(f, bx, by, bz, a, fi, fj, fk, vl, vr);
+        const bool own = (vl >= 0 && smat[vl] != 0xFF) || (vr >= 0 && smat[vr] != 0xFF);
+        if (!own) continue;
+        const int i = C.x0 + fi, j = C.y0 + fj, k = C.z0 + fk;
+        const float q = -(W.lamC[f] + W.fix[f]);
+        const bool wall = (a == 0 && i == I->nx) || (a == 1 && j == I->ny) || (a == 2 && k == I->nz);
+        float *p = a == 0 ? hx_at(I, A.lamH, i, j, k, A.lamW) : (a == 1 ? hy_at(I, A.lamH, i, j, k, A.lamW) : hz_at(I, A.lamH, i, j, k, A.lamW));
+        if (wall) {
+            *p = W.lamHin[f];            // the sweeps never touch the wall arrays
+            W.fix[f] = 0.f;
+        } else {
+            *p = 0.5f * q;
+            W.fix[f] = W.lamHin[f] - 0.5f * q;
+        }
+    }
+    // block sum of d J / d |H_bias|, fixed order
+    for (int o = 16; o > 0; o >>= 1) g += __shfl_down_sync(0xffffffffu, g, o);
+    if ((tid & 31) == 0) sred[tid >> 5] = g;
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int w = 0; w < nth / 32; ++w) s += sred[w];
+        A.gh0[blockIdx.x] += s;
+    }
+}
+
+// magnetic faces: lambda_H = (value after the curl sweep) - q/2 + lamHin
+__global__ void adj_fix_kernel(LaunchSet L, AdjSet A)
+{
+    const MagComp C = L.comps[blockIdx.x];
+    const Inst *I = L.insts + C.inst;
+    const int V = C.V, bx = C.bx, by = C.by, bz = C.bz;
+    const int nfx = (bx + 1) * by * bz, nfy = bx * (by + 1) * bz, nf = nfx + nfy + bx * by * (bz + 1);
+    float *wsb = A.ws + A.ws_off[blockIdx.x];
+    RegionWS W = carve(wsb + (V + 3) / 4, nf, V, A.R);
+    for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+        int a, fi, fj, fk, vl, vr;
+        fdecode(f, bx, by, bz, a, fi, fj, fk, vl, vr);
+        const bool own = (vl >= 0 && C.mat[vl] != 0xFF) || (vr >= 0 && C.mat[vr] != 0xFF);
+        if (!own) continue;
+        const int i = C.x0 + fi, j = C.y0 + fj, k = C.z0 + fk;
+        const bool wall = (a == 0 && i == I->nx) || (a == 1 && j == I->ny) || (a == 2 && k == I->nz);
+        if (wall) continue;
+        float *p = a == 0 ? hx_at(I, A.lamH, i, j, k, A.lamW) : (a == 1 ? hy_at(I, A.lamH, i, j, k, A.lamW) : hz_at(I, A.lamH, i, j, k, A.lamW));
+        *p += W.fix[f];
+    }
+}
+
+__global__ void adj_seed_kernel(LaunchSet L, AdjSet A, long long n)
+{
+    const Inst *I = L.insts;
+    const int t = threadIdx.x;
+    if (t >= 3 * A.nprobe) return;
+    const int p = t / 3, c = t % 3;
+    const long long o = (long long)I->probe[p][2] * I->plane + (long long)I->probe[p][1] * I->px + I->probe[p][0];
+    A.lamE[c * I->fstride + o] += (float)A.seed[(n * A.nprobe + p) * 3 + c];
+}
+
+// lambda_E' = lambda_E - (dt/mu0) C_H lambda_H at every edge (i, j, k)
+template <typename ClsT>
+__global__ void __launch_bounds__(256) adj_curl_h_kernel(LaunchSet L, AdjSet A)
+{
+    const Inst *I = L.insts;
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (i >= I->nx || j >= I->ny || k >= I->nz) return;
+    const long long fs = I->fstride, plane = I->plane;
+    const int px = I->px;
+    const long long o = (long long)k * plane + (long long)j * px + i;
+    const float *lx = A.lamH + 3 * fs, *ly = A.lamH + 4 * fs, *lz = A.lamH + 5 * fs;
+    const float c2 = 2.f * I->ch;   // dt / mu0: both half-pushes
+    const float cx = curl2a(lz[o], j > 0 ? lz[o - px] : 0.f, I->idy, ly[o], k > 0 ? ly[o - plane] : 0.f, I->idz);
+    const float cy = curl2a(lx[o], k > 0 ? lx[o - plane] : 0.f, I->idz, lz[o], i > 0 ? lz[o - 1] : 0.f, I->idx);
+    const float cz = curl2a(ly[o], i > 0 ? ly[o - 1] : 0.f, I->idx, lx[o], j > 0 ? lx[o - px] : 0.f, I->idy);
+    A.lamEn[o] = A.lamE[o] - c2 * cx;
+    A.lamEn[fs + o] = A.lamE[fs + o] - c2 * cy;
+    A.lamEn[2 * fs + o] = A.lamE[2 * fs + o] - c2 * cz;
+}
+
+// lambda_H += C_E (cb lambda_E'),  lambda_E = ca lambda_E'
+template <typename ClsT>
+__global__ void __launch_bounds__(256) adj_curl_e_kernel(LaunchSet L, AdjSet A)
+{
+    const Inst *I = L.insts;
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (i >= I->nx || j >= I->ny || k >= I->nz) return;
+    const long long fs = I->fstride, plane = I->plane;
+    const int px = I->px;
+    const long long o = (long long)k * plane + (long long)j * px + i;
+    const ClsT *cls = static_cast<const ClsT *>(I->cls);
+    const float4 *ctab = I->ctab;
+    auto w = [&](int comp, int ii, int jj, int kk) -> float {   // cb lambda_E' of edge (comp, ii, jj, kk)
+        if (ii >= I->nx || jj >= I->ny || kk >= I->nz) return 0.f;
+        const long long q = (long long)kk * plane + (long long)jj * px + ii;
+        const float4 B = __ldg(ctab + 3 * (int)cls[q] + 1);
+        const float cb = comp == 0 ? B.x : (comp == 1 ? B.y : B.z);
+        return cb * A.lamEn[comp * fs + q];
+    };
+    const float wx = w(0, i, j, k), wy = w(1, i, j, k), wz = w(2, i, j, k);
+    const float cx = curl2a(w(2, i, j + 1, k), wz, I->idy, w(1, i, j, k + 1), wy, I->idz);
+    const float cy = curl2a(w(0, i, j, k + 1), wx, I->idz, w(2, i + 1, j, k), wz, I->idx);
+    const float cz = curl2a(w(1, i + 1, j, k), wy, I->idx, w(0, i, j + 1, k), wx, I->idy);
+    A.lamH[3 * fs + o] += cx;
+    A.lamH[4 * fs + o] += cy;
+    A.lamH[5 * fs + o] += cz;
+    const float4 Ca = __ldg(ctab + 3 * (int)cls[o]);
+    A.lamE[o] = Ca.x * A.lamEn[o];
+    A.lamE[fs + o] = Ca.y * A.lamEn[fs + o];
+    A.lamE[2 * fs + o] = Ca.z * A.lamEn[2 * fs + o];
+}
+
+// E at the design-box edges after the current step, from buffer buf, into slot
+__global__ void adj_record_design_kernel(LaunchSet L, AdjSet A, int slot, int buf)
+{
+    const Inst *I = L.insts;
+    const int ex = A.dbx + 1, ey = A.dby + 1, ez = A.dbz + 1, ne = ex * ey * ez;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 3 * ne) return;
+    const int comp = e / ne, r = e - comp * ne;
+    const int i = A.di0 + r % ex, j = A.dj0 + (r / ex) % ey, k = A.dk0 + r / (ex * ey);
+    float v = 0.f;
+    if (i < I->nx && j < I->ny && k < I->nz)
+        v = I->F[buf][comp][(long long)k * I->plane + (long long)j * I->px + i];
+    A.dtape[(long long)slot * 3 * ne + e] = v;
+}
+
+// d J / d eps_edge += (cb/dt) lambda_E' (E^n - E^{n+1}) on the design-box edges
+template <typename ClsT>
+__global__ void adj_design_kernel(LaunchSet L, AdjSet A, int slot)
+{
+    const Inst *I = L.insts;
+    const int ex = A.dbx + 1, ey = A.dby + 1, ez = A.dbz + 1, ne = ex * ey * ez;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 3 * ne) return;
+    const int comp = e / ne, r = e - comp * ne;
+    const int i = A.di0 + r % ex, j = A.dj0 + (r / ex) % ey, k = A.dk0 + r / (ex * ey);
+    if (i >= I->nx || j >= I->ny || k >= I->nz) return;
+    const long long o = (long long)k * I->plane + (long long)j * I->px + i;
+    const float4 B = __ldg(I->ctab + 3 * (int)static_cast<const ClsT *>(I->cls)[o] + 1);
+    const float cb = comp == 0 ? B.x : (comp == 1 ? B.y : B.z);
+    if (cb == 0.f) return;
+    const float En = A.dtape[(long long)slot * 3 * ne + e], En1 = A.dtape[(long long)(slot + 1) * 3 * ne + e];
+    A.geps[e] += (double)cb / I->dt * (double)A.lamEn[comp * I->fstride + o] * ((double)En - (double)En1);
+}
+
+}  // namespace
+
+long long adj_ws_floats(int bx, int by, int bz, int R)
+{
+    const long long V = (long long)bx * by * bz;
+    return (V + 3) / 4 + 7 * mag_faces(bx, by, bz) + (27 + 6LL * R) * V;
+}
+
+cudaError_t adj_record_design(const LaunchSet &L, const AdjSet &A, int slot, int buf, cudaStream_t s)
+{
+    const int ne3 = 3 * (A.dbx + 1) * (A.dby + 1) * (A.dbz + 1);
+    adj_record_design_kernel<<<(ne3 + 255) / 256, 256, 0, s>>>(L, A, slot, buf);
+    return cudaGetLastError();
+}
+
+// Reverse of forward step n, whose records sit in tape slot `slot`
+// (magnets) and design slots slot, slot+1 (E^n, E^{n+1}).
+cudaError_t adj_reverse_step(const LaunchSet &L, const AdjSet &A, long long n, int slot, cudaStream_t s)
+{
+    if (A.nprobe > 0) adj_seed_kernel<<<1, 3 * A.nprobe, 0, s>>>(L, A, n);
+    if (L.ncomp) adj_mag_kernel<<<L.ncomp, kMagThreads, 0, s>>>(L, A, slot);
+    const dim3 blk(32, 8), grid((A.nx + 31) / 32, (A.ny + 7) / 8, A.nz);
+    const int ne3 = 3 * (A.dbx + 1) * (A.dby + 1) * (A.dbz + 1);
+    if (L.cls16) {
+        adj_curl_h_kernel<uint16_t><<<grid, blk, 0, s>>>(L, A);
+        if (A.geps) adj_design_kernel<uint16_t><<<(ne3 + 255) / 256, 256, 0, s>>>(L, A, slot);
+        adj_curl_e_kernel<uint16_t><<<grid, blk, 0, s>>>(L, A);
+    } else {
+        adj_curl_h_kernel<uint8_t><<<grid, blk, 0, s>>>(L, A);
+        if (A.geps) adj_design_kernel<uint8_t><<<(ne3 + 255) / 256, 256, 0, s>>>(L, A, slot);
+        adj_curl_e_kernel<uint8_t><<<grid, blk, 0, s>>>(L, A);
+    }
+    if (L.ncomp) adj_fix_kernel<<<L.ncomp, 256, 0, s>>>(L, A);
+    return cudaGetLastError();
+}
+
+}  // namespace fl

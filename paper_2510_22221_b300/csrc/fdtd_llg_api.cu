@@ -45,6 +45,8 @@ struct Instance {
     std::vector<MagMat> mm;
     std::vector<double> mm_Ms;        // Ms of each magnet material (FP64)
     double hbias[3] = {0, 0, 0};
+    bool has_design = false;
+    int dbox[6] = {0, 0, 0, 0, 0, 0}; // design box: i0, j0, k0, bx, by, bz
     double u[3] = {0, 0, 1};          // bias direction
     float R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};   // bias frame rows (e1, e2, e3 = u)
     size_t n_field() const { return (size_t)nz * ny * px; }
@@ -75,6 +77,11 @@ struct Sim {
     int nsm = 148;
     long long host_step = 0;
     bool half_ahead = false;
+    // checkpointed run for the adjoint
+    long long adj_N = 0;              // steps of the recorded run (0: none)
+    long long adj_K = 0;              // steps between checkpoints
+    float *ckpt = nullptr;            // ceil(N/K) states: fields of the present buffer, walls, m
+    size_t ckpt_floats = 0;
     std::vector<void *> allocs;
     std::string err;
     // profiling: event pairs recorded around launches
@@ -597,10 +604,13 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
     std::memcpy(I.u, u, sizeof I.u);
     for (int q = 0; q < 9; ++q) I.R[q] = (float)E[q];
     I.materials_set = true;
+    I.has_design = has_design;
+    std::memcpy(I.dbox, db, sizeof db);
     // a batch's step count restarts with any instance's materials
     S->host_step = 0;
     S->half_ahead = false;
     S->cur = 0;
+    S->adj_N = 0;   // a recorded run belongs to the previous materials
     CKR(h, cudaMemset(S->d_ctl, 0, sizeof(StepCtl)));
     S->dirty = true;
     return FDTD_OK;
@@ -1270,6 +1280,200 @@ extern "C" int fdtd_llg_read_profile(fdtd_llg_t h, fdtd_llg_profile *out, int32_
     S->prof.cells = cells;
     *out = S->prof;
     if (reset) S->prof = fdtd_llg_profile{};
+    return FDTD_OK;
+}
+
+// ------------------------------------------------ checkpointed run, adjoint
+static size_t state_floats(const Instance &I)
+{
+    size_t totV = 0;
+    for (const auto &C : I.comps) totV += C.V;
+    return 6 * I.n_field() + I.n_wall() + 3 * totV;
+}
+
+// copy the present state (fields of the current buffer, walls, m) to/from dst
+static cudaError_t copy_state(Sim *S, float *buf, bool save)
+{
+    Instance &I = S->inst[0];
+    const size_t f6 = 6 * I.n_field(), nw = I.n_wall();
+    size_t totV = 0;
+    for (const auto &C : I.comps) totV += C.V;
+    float *F = I.fields[S->cur];
+    cudaError_t e = save ? cudaMemcpyAsync(buf, F, f6 * 4, cudaMemcpyDeviceToDevice, S->stream)
+                         : cudaMemcpyAsync(F, buf, f6 * 4, cudaMemcpyDeviceToDevice, S->stream);
+    if (e == cudaSuccess)
+        e = save ? cudaMemcpyAsync(buf + f6, I.walls, nw * 4, cudaMemcpyDeviceToDevice, S->stream)
+                 : cudaMemcpyAsync(I.walls, buf + f6, nw * 4, cudaMemcpyDeviceToDevice, S->stream);
+    if (e == cudaSuccess && totV)
+        e = save ? cudaMemcpyAsync(buf + f6 + nw, I.mbuf, 3 * totV * 4, cudaMemcpyDeviceToDevice, S->stream)
+                 : cudaMemcpyAsync(I.mbuf, buf + f6 + nw, 3 * totV * 4, cudaMemcpyDeviceToDevice, S->stream);
+    return e;
+}
+
+extern "C" int fdtd_llg_run_checkpointed(fdtd_llg_t h, int64_t nsteps, int32_t interval)
+{
+    if (!h || !h->sim || !h->owns) return fail(h, FDTD_E_INVAL, "run_checkpointed needs the handle, not a member");
+    Sim *S = h->sim;
+    if (S->inst.size() != 1) return fail(h, FDTD_E_NOSYS, "the adjoint supports single-instance handles");
+    if (nsteps < 1 || interval < 0) return fail(h, FDTD_E_INVAL, "nsteps must be >= 1 and interval >= 0");
+    if (S->host_step != 0) return fail(h, FDTD_E_STATE, "run_checkpointed starts at step 0 (set the materials again)");
+    int rc = upload_descriptors(h);
+    if (rc) return rc;
+    if (S->ncomp && S->cfg.llg_fixed_iter < 2)
+        return fail(h, FDTD_E_INVAL, "with magnets the adjoint needs llg_fixed_iter >= 2 (a fixed LLG map)");
+    const long long K = interval > 0 ? interval : (long long)std::ceil(std::sqrt((double)nsteps));
+    const long long nck = (nsteps + K - 1) / K;
+    const size_t sf = state_floats(S->inst[0]);
+    S->dfree(S->ckpt);
+    S->ckpt = (float *)S->dalloc((size_t)nck * sf * sizeof(float));
+    if (!S->ckpt) return fail(h, FDTD_E_OOM, "checkpoint allocation failed");
+    S->ckpt_floats = sf;
+    S->adj_N = 0;
+    if (!S->half_ahead) {
+        LaunchSet L = launch_set(S);
+        L.src = L.dst = S->cur;
+        CKR(h, launch_half(L, S->stream));
+        S->half_ahead = true;
+    }
+    for (long long c = 0; c < nck; ++c) {
+        CKR(h, copy_state(S, S->ckpt + c * sf, true));
+        rc = fdtd_llg_step(h, std::min<long long>(K, nsteps - c * K));
+        if (rc) return rc;
+    }
+    S->adj_N = nsteps;
+    S->adj_K = K;
+    return FDTD_OK;
+}
+
+extern "C" int fdtd_llg_adjoint(fdtd_llg_t h, const double *dJ_dE, double *grad_eps, double *grad_h0)
+{
+    if (!h || !h->sim || !h->owns) return fail(h, FDTD_E_INVAL, "adjoint needs the handle, not a member");
+    Sim *S = h->sim;
+    if (S->adj_N <= 0 || !S->ckpt) return fail(h, FDTD_E_STATE, "no checkpointed run: call fdtd_llg_run_checkpointed first");
+    if (!dJ_dE) return fail(h, FDTD_E_INVAL, "dJ_dE is NULL");
+    Instance &I = S->inst[0];
+    const long long N = S->adj_N, K = S->adj_K, nck = (N + K - 1) / K;
+    const int np = (int)I.probes.size();
+    const size_t nf = I.n_field(), sf = S->ckpt_floats;
+    const int R = std::max(2, S->cfg.llg_fixed_iter);
+    std::vector<void *> owned;
+    auto alloc = [&](size_t bytes) -> void * {
+        void *p = S->dalloc(bytes);
+        if (p) owned.push_back(p);
+        return p;
+    };
+    auto cleanup = [&]() {
+        for (auto &C : I.comps) { C.tape = nullptr; C.tstride = 0; }
+        S->dirty = true;
+        cudaStreamSynchronize(S->stream);
+        for (void *p : owned) S->dfree(p);
+    };
+    AdjSet A{};
+    A.lamE = (float *)alloc(3 * nf * 4);
+    A.lamEn = (float *)alloc(3 * nf * 4);
+    A.lamH = (float *)alloc(6 * nf * 4);
+    A.lamW = (float *)alloc(I.n_wall() * 4);
+    const int nc = (int)I.comps.size();
+    std::vector<long long> ws_off(std::max(1, nc), 0);
+    long long ws_tot = 0, tape_tot = 0;
+    std::vector<long long> toff(std::max(1, nc), 0), tstr(std::max(1, nc), 0);
+    for (int c = 0; c < nc; ++c) {
+        const MagComp &C = I.comps[c];
+        ws_off[c] = ws_tot;
+        ws_tot += (adj_ws_floats(C.bx, C.by, C.bz, R) + 63) / 64 * 64;
+        tstr[c] = 3LL * C.V + mag_faces(C.bx, C.by, C.bz) + 3LL * (C.bx + 1) * (C.by + 1) * (C.bz + 1);
+        toff[c] = tape_tot;
+        tape_tot += K * tstr[c];
+    }
+    A.ws = (float *)alloc(std::max<long long>(ws_tot, 1) * 4);
+    long long *d_wsoff = (long long *)alloc(ws_off.size() * sizeof(long long));
+    A.ws_off = d_wsoff;
+    A.gh0 = (double *)alloc(std::max(1, nc) * sizeof(double));
+    float *tape = (float *)alloc(std::max<long long>(tape_tot, 1) * 4);
+    const long long nseed = N * std::max(1, np) * 3;
+    double *d_seed = (double *)alloc(nseed * sizeof(double));
+    A.seed = d_seed;
+    A.nprobe = np;
+    A.nx = I.nx; A.ny = I.ny; A.nz = I.nz;
+    A.R = R;
+    long long nbe = 0;
+    if (I.has_design) {
+        A.di0 = I.dbox[0]; A.dj0 = I.dbox[1]; A.dk0 = I.dbox[2];
+        A.dbx = I.dbox[3]; A.dby = I.dbox[4]; A.dbz = I.dbox[5];
+        nbe = (long long)(A.dbx + 1) * (A.dby + 1) * (A.dbz + 1);
+        A.dtape = (float *)alloc((size_t)(K + 1) * 3 * nbe * 4);
+        A.geps = (double *)alloc(3 * nbe * sizeof(double));
+    }
+    bool ok = A.lamE && A.lamEn && A.lamH && A.lamW && A.ws && d_wsoff && A.gh0 && tape && d_seed &&
+              (!I.has_design || (A.dtape && A.geps));
+    if (!ok) { cleanup(); return fail(h, FDTD_E_OOM, "adjoint buffers: device allocation failed"); }
+    cudaError_t e = cudaMemsetAsync(A.lamE, 0, 3 * nf * 4, S->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(A.lamH, 0, 6 * nf * 4, S->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(A.lamW, 0, I.n_wall() * 4, S->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(A.ws, 0, std::max<long long>(ws_tot, 1) * 4, S->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(A.gh0, 0, std::max(1, nc) * sizeof(double), S->stream);
+    if (e == cudaSuccess && A.geps) e = cudaMemsetAsync(A.geps, 0, 3 * nbe * sizeof(double), S->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_wsoff, ws_off.data(), ws_off.size() * sizeof(long long), cudaMemcpyHostToDevice, S->stream);
+    if (e == cudaSuccess && np) e = cudaMemcpyAsync(d_seed, dJ_dE, nseed * sizeof(double), cudaMemcpyHostToDevice, S->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    if (e != cudaSuccess) { cleanup(); return fail(h, FDTD_E_CUDA, std::string("adjoint setup: ") + cudaGetErrorString(e)); }
+    for (int c = 0; c < nc; ++c) {
+        I.comps[c].tape = tape + toff[c];
+        I.comps[c].tstride = tstr[c];
+    }
+    S->dirty = true;
+    int rc = upload_descriptors(h);
+    if (rc) { cleanup(); return rc; }
+    LaunchSet L = launch_set(S);
+    L.rec = 1;
+    for (long long seg = nck - 1; seg >= 0 && e == cudaSuccess; --seg) {
+        const long long na = seg * K, nb = std::min(N, na + K);
+        e = copy_state(S, S->ckpt + seg * sf, false);
+        StepCtl ctl{};
+        ctl.step = na;
+        if (e == cudaSuccess) e = cudaMemcpy(S->d_ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice);
+        L.rec_n0 = na;
+        if (e == cudaSuccess && I.has_design) e = adj_record_design(L, A, 0, S->cur, S->stream);
+        for (long long n = na; n < nb && e == cudaSuccess; ++n) {
+            L.src = S->cur;
+            L.dst = 1 - S->cur;
+            e = launch_step(L, S->stream, nullptr);
+            S->cur ^= 1;
+            if (e == cudaSuccess && I.has_design) e = adj_record_design(L, A, (int)(n - na + 1), S->cur, S->stream);
+        }
+        for (long long n = nb - 1; n >= na && e == cudaSuccess; --n) e = adj_reverse_step(L, A, n, (int)(n - na), S->stream);
+        S->host_step = nb;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    std::vector<double> gh(std::max(1, nc), 0.0), ge(3 * nbe, 0.0);
+    if (e == cudaSuccess) e = cudaMemcpy(gh.data(), A.gh0, gh.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && nbe) e = cudaMemcpy(ge.data(), A.geps, ge.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    StepCtl st{};
+    if (e == cudaSuccess) e = cudaMemcpy(&st, S->d_ctl, sizeof st, cudaMemcpyDeviceToHost);
+    cleanup();
+    if (e != cudaSuccess) return fail(h, FDTD_E_CUDA, std::string("adjoint: ") + cudaGetErrorString(e));
+    if (st.status & ST_UNSTABLE) return fail(h, FDTD_E_UNSTABLE, "adjoint recomputation: energy not finite");
+    if (grad_h0) {
+        double s = 0.0;
+        for (int c = 0; c < nc; ++c) s += gh[c];
+        *grad_h0 = s;
+    }
+    if (grad_eps && I.has_design) {
+        // eps of an edge = eps0 times the mean eps_r of its four cells
+        const int bx = A.dbx, by = A.dby, bz = A.dbz, ex = bx + 1, ey = by + 1;
+        auto g = [&](int comp, int li, int lj, int lk) { return ge[(size_t)comp * nbe + ((size_t)lk * ey + lj) * ex + li]; };
+        for (int k = 0; k < bz; ++k)
+            for (int j = 0; j < by; ++j)
+                for (int i = 0; i < bx; ++i) {
+                    double s = 0.0;
+                    for (int a = 0; a < 2; ++a)
+                        for (int b = 0; b < 2; ++b)
+                            s += g(0, i, j + a, k + b) + g(1, i + a, j, k + b) + g(2, i + a, j + b, k);
+                    grad_eps[((size_t)k * by + j) * bx + i] = 0.25 * kEps0 * s;
+                }
+    } else if (grad_eps) {
+        return fail(h, FDTD_E_STATE, "grad_eps requested but the materials have no design box");
+    }
     return FDTD_OK;
 }
 

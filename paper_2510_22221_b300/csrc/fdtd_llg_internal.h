@@ -107,6 +107,8 @@ struct MagComp {
     float *m;               // deviation M - Ms h in the bias frame: 3 blocks of V
     const uint8_t *mat;     // V: magnet material index, 0xFF outside this region
     float *eedge;           // scratch: E at the edges of the box, 3 blocks of (bx+1)(by+1)(bz+1)
+    float *tape;            // adjoint recording: per step m (3V), face H (faces), box-edge E; NULL when off
+    long long tstride;      // floats per step of the tape
 };
 
 // Device-resident control block of a batch.
@@ -137,6 +139,8 @@ struct LaunchSet {
     int llg_max_iter, llg_fixed_iter;
     int energy;
     bool stab;                          // every instance's class table fits kTabMax
+    int rec;                            // magnet kernel writes its tape (adjoint recomputation)
+    long long rec_n0;                   // step of tape slot 0
 };
 
 // Launchers (kernels_fwd.cu).  launch_half: the start-up H/M half-push that
@@ -149,6 +153,29 @@ cudaError_t launch_half(const LaunchSet &L, cudaStream_t s);
 cudaError_t launch_step(const LaunchSet &L, cudaStream_t s, cudaEvent_t *prof);
 int h_half_blocks_per_sm(bool cls16);
 int step_blocks_per_sm(bool cls16);
+
+// ------------------------------------------------------------- adjoint
+// Device pointers of one reverse sweep (adjoint.cu), single instance.
+struct AdjSet {
+    float *lamE;            // adjoint of E^{n+1} (3 field arrays, fstride apart), then of E^n
+    float *lamEn;           // lambda_E' = lambda_E - (dt/mu0) C_H lambda_H (3 arrays)
+    float *lamH;            // adjoint of H (3 field arrays)
+    float *lamW;            // adjoint of the far-wall normal H (walls layout)
+    float *ws;              // per-region workspace (ws_off[region] floats in)
+    const long long *ws_off;
+    double *gh0;            // per region: d J / d |H_bias|
+    const double *seed;     // [nsteps][nprobe][3]: dJ/dE at the probe edges
+    int nprobe;
+    int nx, ny, nz;         // the instance's grid
+    int R;                  // Jacobi iterates of every LLG solve (fixed)
+    // design box (superset of the edges whose eps depends on a design cell)
+    int di0, dj0, dk0, dbx, dby, dbz;   // cells; edges span (dbx+1)(dby+1)(dbz+1) per component
+    float *dtape;           // [slot][3][dbz+1][dby+1][dbx+1]: E at the design-box edges after step rec_n0+slot-1
+    double *geps;           // per design-box edge: d J / d eps_edge (FP64)
+};
+long long adj_ws_floats(int bx, int by, int bz, int R);
+cudaError_t adj_record_design(const LaunchSet &L, const AdjSet &A, int slot, int buf, cudaStream_t s);
+cudaError_t adj_reverse_step(const LaunchSet &L, const AdjSet &A, long long n, int slot, cudaStream_t s);
 
 // fdtd_llg_last_error(NULL) message for entry points without a handle.
 void set_last_error(const char *msg);

@@ -359,6 +359,14 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
         }
     }
     __syncthreads();
+    if (FUSED && L.rec && C.tape) {
+        // adjoint recording: m and face H at the start of the step, E^{n+1} at the box edges
+        float *T = C.tape + (n - L.rec_n0) * C.tstride;
+        const int ne3 = 3 * (bx + 1) * (by + 1) * (bz + 1);
+        for (int v = tid; v < 3 * V; v += nth) T[v] = sM[v];
+        for (int f = tid; f < nf; f += nth) T[3 * V + f] = sH[f];
+        for (int e = tid; e < ne3; e += nth) T[3 * V + nf + e] = __ldcg(C.eedge + e);
+    }
 
     double eacc = 0.0;
     const int nhalf = FUSED ? 2 : 1;

@@ -1,0 +1,127 @@
+"""Adjoint gradients through the C ABI (arxiv 2510.22221, section "Numerical
+Model"; the probe-objective design case): the GPU reverse sweep (FP32
+adjoint fields, FP64 gradient sums) against the FP64 reference gradients of
+oracle/adjoint.py, whose own pins tie them to central finite differences.
+
+Tolerance: the FP32 forward run itself differs from FP64 by ~1e-6 of the
+fields (TOL(N) of the parity tests), and the reverse sweep adds the same
+order, so gradients agree to ~1e-6 relative; the tests allow 1e-4 (bias
+gradient: 1e-3, it is a sum of many small cancelling terms)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2510_22221_b300 as pkg
+from oracle import adjoint as A
+from paper_2510_22221_b300 import workloads as W
+from paper_2510_22221_b300.autograd import probe_energy
+
+pytestmark = pytest.mark.gpu
+
+
+def _reference(w, N, n0):
+    dt = oracle.courant_dt(w.dx, w.dy, w.dz, w.courant)
+    src = [dict(comp=s["comp"], ijk=(s["i"], s["j"], s["k"]), J0=s["J0"], f0=s["f0"], Tp=s["Tp"], tpk=s["tpk"])
+           for s in w.sources]
+    m = A.TorchStep(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, dt, w.materials, w.mat_id, w.hbias, sources=src,
+                    probes=w.probes, design_box=w.design_box, fixed_iter=3)
+    return A.gradients(m, N, w.eps_design, float(np.linalg.norm(w.hbias)), n0=n0)
+
+
+def _gpu(w, N, n0, interval=0):
+    sim = pkg.from_workload(w, probe_capacity=N, llg_fixed_iter=3)
+    sim.run_checkpointed(N, interval)
+    rows = np.stack([sim.probe(p)[:, :3] for p in range(len(w.probes))], axis=1)
+    seed = np.zeros_like(rows)
+    seed[n0:] = 2 * rows[n0:]
+    ge, gh = sim.adjoint(seed, design_shape=w.eps_design.shape)
+    J = float((rows[n0:] ** 2).sum())
+    sim.destroy()
+    return J, ge, gh
+
+
+CASES = {
+    "design16": (lambda: W.adjoint_small(n=16, steps=260, design=(6, 6, 2), block=(4, 4, 2)), 260, 160, 1e-4),
+    "anticross": (lambda: W.anticrossing_sweep(n_inst=1, b_lo=0.05, b_hi=0.05, steps=900, design=(4, 3, 1))[0], 900,
+                  500, 1e-3),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_adjoint_matches_fp64_reference(case):
+    make, N, n0, tol_h = CASES[case]
+    w = make()
+    J, ge, gh = _gpu(w, N, n0)
+    Jo, geo, gho = _reference(w, N, n0)
+    assert J == pytest.approx(Jo, rel=1e-5)
+    assert np.linalg.norm(ge - geo) / np.linalg.norm(geo) < 1e-4
+    assert np.abs(ge - geo).max() < 1e-4 * np.abs(geo).max()
+    assert gh == pytest.approx(gho, rel=tol_h)
+
+
+def test_checkpoint_interval_does_not_change_the_gradient():
+    make, N, n0, _ = CASES["anticross"]
+    w = make()
+    _, g0, h0 = _gpu(w, N, n0, interval=0)      # sqrt(N) = 30
+    _, g1, h1 = _gpu(w, N, n0, interval=7)
+    _, g2, h2 = _gpu(w, N, n0, interval=N)      # one segment
+    np.testing.assert_array_equal(g0, g1)
+    np.testing.assert_array_equal(g0, g2)
+    assert h0 == h1 == h2
+
+
+def test_adjoint_directional_derivatives_equal_gpu_central_differences():
+    """Central differences of the FP32 forward run itself, along a random
+    direction and along the gradient, over all design cells at once (a single
+    cell moves J by less than the FP32 rounding of J)."""
+    make, N, n0, _ = CASES["design16"]
+    w = make()
+    J, ge, gh = _gpu(w, N, n0)
+
+    def J_at(eps):
+        w2 = make()
+        w2.eps_design = eps
+        sim = pkg.from_workload(w2, probe_capacity=N, llg_fixed_iter=3)
+        sim.step(N)
+        rows = np.stack([sim.probe(p)[:, :3] for p in range(len(w2.probes))], axis=1)
+        sim.destroy()
+        return float((rows[n0:] ** 2).sum())
+
+    for d in (np.random.default_rng(7).standard_normal(w.eps_design.shape), ge / np.abs(ge).max()):
+        h = 1e-2
+        fd = (J_at(w.eps_design + h * d) - J_at(w.eps_design - h * d)) / (2 * h)
+        assert float((ge * d).sum()) == pytest.approx(fd, rel=5e-3)
+
+
+def test_autograd_function_returns_the_library_gradients():
+    make, N, n0, _ = CASES["design16"]
+    w = make()
+    eps = torch.tensor(w.eps_design, dtype=torch.float64, requires_grad=True)
+    h0 = torch.tensor(float(np.linalg.norm(w.hbias)), dtype=torch.float64, requires_grad=True)
+    J = probe_energy(w, eps, h0, N, n0)
+    (3.0 * J).backward()
+    _, ge, gh = _gpu(w, N, n0)
+    # the wrapper rebuilds the bias as |H0| times its direction: the FP32 run
+    # may differ in the last bits, so the gradients agree to FP32 run level
+    np.testing.assert_allclose(eps.grad.numpy(), 3.0 * ge, rtol=1e-5, atol=1e-5 * np.abs(3.0 * ge).max())
+    assert float(h0.grad) == pytest.approx(3.0 * gh, rel=1e-4)
+
+
+def test_adjoint_argument_errors():
+    w = CASES["design16"][0]()
+    sim = pkg.from_workload(w, probe_capacity=10, llg_fixed_iter=3)
+    with pytest.raises(pkg.LLGError) as ei:
+        sim.adjoint(np.zeros((10, 1, 3)), design_shape=w.eps_design.shape)
+    assert ei.value.code == -6
+    sim.destroy()
+    sim = pkg.from_workload(w, probe_capacity=10)           # magnets without a fixed LLG map
+    with pytest.raises(pkg.LLGError) as ei:
+        sim.run_checkpointed(10)
+    assert ei.value.code == -1
+    sim.destroy()
+    batch = pkg.FdtdLlg.create_batch([(8, 8, 8), (8, 8, 8)], [(1e-6,) * 3] * 2, probe_capacity=4)
+    with pytest.raises(pkg.LLGError) as ei:
+        batch.run_checkpointed(4)
+    assert ei.value.code == -8
+    batch.destroy()
