@@ -137,6 +137,117 @@ def cpu_baseline(w, steps, seconds_cap=25.0):
                       f"FP64 C oracle, one thread, {t:.1f} s"}
 
 
+def adjoint_ratio(torch, pkg, W, steps=4000, n0=3000):
+    """Config-3 design case (128x128x64, 4000 steps, 32x32x4 design cells):
+    forward time, and the time of one gradient (checkpointed run + reverse
+    sweep, which recomputes every segment) through the C ABI."""
+    import numpy as np
+
+    w = W.adjoint_design(steps=steps)
+    stream = torch.cuda.current_stream()
+    sim = pkg.from_workload(w, probe_capacity=steps, llg_fixed_iter=3)
+    sim.step(1)
+    sim.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps - 1)
+    e1.record(stream)
+    sim.sync()
+    t_fwd = e0.elapsed_time(e1) / 1e3 * steps / (steps - 1)
+    sim.destroy()
+    sim = pkg.from_workload(w, probe_capacity=steps, llg_fixed_iter=3)
+    t0 = time.perf_counter()
+    sim.run_checkpointed(steps)
+    sim.sync()
+    t1 = time.perf_counter()
+    rows = np.stack([sim.probe(p)[:, :3] for p in range(len(w.probes))], axis=1)
+    seed = np.zeros_like(rows)
+    seed[n0:] = 2 * rows[n0:]
+    t2 = time.perf_counter()
+    ge, gh = sim.adjoint(seed, design_shape=w.eps_design.shape)
+    t3 = time.perf_counter()
+    sim.destroy()
+    # directional central difference of the FP32 forward run along the gradient
+    d = ge / np.abs(ge).max()
+
+    def J_at(eps):
+        w2 = W.adjoint_design(steps=steps)
+        w2.eps_design = eps
+        s2 = pkg.from_workload(w2, probe_capacity=steps, llg_fixed_iter=3)
+        s2.step(steps)
+        r = np.stack([s2.probe(p)[:, :3] for p in range(len(w2.probes))], axis=1)
+        s2.destroy()
+        return float((r[n0:] ** 2).sum())
+
+    h = 1e-2
+    fd = (J_at(w.eps_design + h * d) - J_at(w.eps_design - h * d)) / (2 * h)
+    ad = float((ge * d).sum())
+    return {"workload": w.name, "steps": steps, "design_cells": int(ge.size), "forward_s": round(t_fwd, 4),
+            "checkpointed_forward_s": round(t1 - t0, 4), "adjoint_s": round(t3 - t2, 4),
+            "adjoint_forward_ratio": round((t3 - t2) / t_fwd, 3),
+            "gradient_forward_ratio": round((t1 - t0 + t3 - t2) / t_fwd, 3),
+            "directional_fd_rel_err": float(f"{abs(ad - fd) / abs(fd):.3g}"),
+            "grad_h0_per_A_per_m": gh}
+
+
+def batch_sweep(torch, pkg, W, steps_timed=2000, steps_total=10000):
+    """Config 2: 64 uneven cubes 48^3..96^3 with magnets, bias swept over
+    0.05..0.15 T.  Batched (one launch per kernel per step for all instances)
+    against the same instances run one after another; then the full run's
+    probe spectra and ESPRIT polariton pairs with the (f_p, g) fit."""
+    import numpy as np
+
+    ws = W.bias_sweep(steps=steps_total)
+    cells = sum(w.cells for w in ws)
+    stream = torch.cuda.current_stream()
+
+    def timed(sim, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(n)
+        e1.record(stream)
+        sim.sync()
+        return e0.elapsed_time(e1) / 1e3
+
+    dims = [(w.nx, w.ny, w.nz) for w in ws]
+    sp = [(w.dx, w.dy, w.dz) for w in ws]
+    batch = pkg.FdtdLlg.create_batch(dims, sp, courant_factor=0.5, probe_capacity=steps_total)
+    for q, w in enumerate(ws):
+        pkg.configure(batch.batch_member(q), w)
+    dt = batch.dt
+    batch.step(20)
+    t_batch = timed(batch, steps_timed)
+    t_seq = 0.0
+    for w in ws:
+        single = pkg.FdtdLlg.create(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, dt=dt, probe_capacity=64)
+        pkg.configure(single, w)
+        single.step(20)
+        t_seq += timed(single, steps_timed)
+        single.destroy()
+    batch.step(steps_total - 20 - steps_timed)
+    batch.sync()
+    pairs, peaks = [], []
+    lo, hi = 1.5e9, 4.5e9
+    for q in range(len(ws)):
+        m = batch.batch_member(q)
+        spec = m.probe_spectrum(0, 0, lo, hi, 601)
+        peaks.append(float(np.linspace(lo, hi, 601)[int(np.argmax(spec))]))
+        tr = m.probe(0)[steps_total // 5:, 0]
+        f, a, amp, Q = pkg.fit_modes(tr, dt, 24, pencil=300, fmin=lo, fmax=hi, max_modes=2)
+        if len(f) == 2:
+            pairs.append(f)
+    batch.destroy()
+    fit = None
+    if len(pairs) >= 2:
+        fp, g = pkg.fit_coupling([p[1] for p in pairs], [p[0] for p in pairs])
+        fit = {"f_p_hz": fp, "two_g_hz": 2 * g, "pairs": len(pairs)}
+    return {"instances": len(ws), "cells": cells, "steps_timed": steps_timed,
+            "batched_mcells_per_s": round(cells * steps_timed / t_batch / 1e6, 1),
+            "sequential_mcells_per_s": round(cells * steps_timed / t_seq / 1e6, 1),
+            "speedup": round(t_seq / t_batch, 3), "steps_total": steps_total,
+            "spectrum_peak_hz_first_last": [peaks[0], peaks[-1]], "anticrossing_fit": fit}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -161,6 +272,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-extra", action="store_true", help="skip the adjoint and batched-sweep measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -267,6 +379,11 @@ def main():
                    "d2h_bytes_per_step": 8 * (9 * len(w.probes) + 1), "steps": ke,
                    "includes": "create + set_materials (host preprocessing, H2D) + per-step D2H of probes and energy"}
 
+    if not args.no_extra and rank == 0:
+        adj = adjoint_ratio(torch, pkg, W)
+        line["adjoint"] = adj
+        line["adjoint_forward_ratio"] = adj["adjoint_forward_ratio"]
+        line["batch_sweep"] = batch_sweep(torch, pkg, W)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w, 12)
     if rank == 0:

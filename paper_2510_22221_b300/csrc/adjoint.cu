@@ -42,7 +42,6 @@ __device__ __forceinline__ D1 dsqrt(D1 a)
     const float r = sqrtf(a.v);
     return {r, r > 0.f ? 0.5f * a.d / r : 0.f};
 }
-__device__ __forceinline__ float dsqrt(float a) { return sqrtf(a); }
 
 // One cell's LLG increment in the bias frame (the arithmetic of mag_kernel):
 // m deviation from Ms e3, hs = H_eff at the start of the half-push, h = H_eff

@@ -82,6 +82,11 @@ struct Sim {
     long long adj_K = 0;              // steps between checkpoints
     float *ckpt = nullptr;            // ceil(N/K) states: fields of the present buffer, walls, m
     size_t ckpt_floats = 0;
+    // CUDA graph of kGraphSteps steps (even: the buffer parity returns), replayed by long step calls
+    cudaGraphExec_t graph = nullptr;
+    int graph_parity = -1;            // buffer holding the state when the graph starts; -1: none
+    bool graph_off = false;           // capture failed once on this stream: launch step by step
+    int graph_mode = -1;              // 1 always, 0 never, -1 when a step is launch-bound
     std::vector<void *> allocs;
     std::string err;
     // profiling: event pairs recorded around launches
@@ -125,6 +130,7 @@ struct Sim {
             else cudaFree(p);
         }
         allocs.clear();
+        if (graph) cudaGraphExecDestroy(graph);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -830,6 +836,8 @@ static int upload_descriptors(fdtd_llg_t h)
     S->mag_smem = msmem;
     S->cls16 = c16;
     S->dirty = false;
+    if (S->graph) { cudaGraphExecDestroy(S->graph); S->graph = nullptr; }   // its launch set is stale
+    S->graph_parity = -1;
     return FDTD_OK;
 }
 
@@ -861,6 +869,37 @@ static LaunchSet launch_set(Sim *S)
     return L;
 }
 
+// Steps per CUDA graph: long step calls on a stream that can be captured
+// replay one graph of kGraphSteps steps instead of launching kernel by kernel.
+constexpr int64_t kGraphSteps = 32;
+// By default graphs serve launch-bound steps only: below this many cells a
+// step's kernels run for less than their launch overhead.
+constexpr long long kGraphCells = 2LL << 20;
+
+static bool capturable(cudaStream_t s) { return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread; }
+
+// (Re)build the graph of kGraphSteps steps starting from buffer S->cur.
+static cudaError_t build_graph(Sim *S, LaunchSet L)
+{
+    if (S->graph) { cudaGraphExecDestroy(S->graph); S->graph = nullptr; }
+    cudaError_t e = cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    int cur = S->cur;
+    for (int64_t q = 0; q < kGraphSteps && e == cudaSuccess; ++q) {
+        L.src = cur;
+        L.dst = 1 - cur;
+        e = launch_step(L, S->stream, nullptr);
+        cur ^= 1;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(S->stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&S->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    S->graph_parity = e == cudaSuccess ? S->cur : -1;
+    return e;
+}
+
 extern "C" int fdtd_llg_step(fdtd_llg_t h, int64_t nsteps)
 {
     if (!h || !h->sim) return fail(h, FDTD_E_INVAL, "null handle");
@@ -875,7 +914,19 @@ extern "C" int fdtd_llg_step(fdtd_llg_t h, int64_t nsteps)
         CKR(h, launch_half(L, S->stream));
         S->half_ahead = true;
     }
-    for (int64_t s = 0; s < nsteps; ++s) {
+    int64_t s = 0;
+    long long cells = 0;
+    for (const Instance &I : S->inst) cells += (long long)I.nx * I.ny * I.nz;
+    const bool want = S->graph_mode == 1 || (S->graph_mode < 0 && cells <= kGraphCells);
+    if (want && !S->profiling && !S->graph_off && nsteps >= 2 * kGraphSteps && capturable(S->stream)) {
+        if ((!S->graph || S->graph_parity != S->cur) && build_graph(S, L) != cudaSuccess) {
+            cudaGetLastError();   // not fatal: this stream is stepped launch by launch
+            S->graph_off = true;
+        }
+        if (S->graph)
+            for (; s + kGraphSteps <= nsteps; s += kGraphSteps) CKR(h, cudaGraphLaunch(S->graph, S->stream));
+    }
+    for (; s < nsteps; ++s) {
         L.src = S->cur;
         L.dst = 1 - S->cur;
         cudaEvent_t ev[4];
@@ -1183,6 +1234,14 @@ extern "C" int fdtd_llg_load_state(fdtd_llg_t h, const void *buf, size_t size)
 }
 
 // ------------------------------------------------------------- profiling
+extern "C" int fdtd_llg_set_graphs(fdtd_llg_t h, int32_t mode)
+{
+    if (!h || !h->sim || !h->owns) return fail(h, FDTD_E_INVAL, "set graphs on the handle, not a member");
+    if (mode < -1 || mode > 1) return fail(h, FDTD_E_INVAL, "mode must be -1, 0 or 1");
+    h->sim->graph_mode = mode;
+    return FDTD_OK;
+}
+
 extern "C" int fdtd_llg_get_dt(fdtd_llg_t h, double *dt)
 {
     if (!h || !h->sim || !dt) return fail(h, FDTD_E_INVAL, "null handle or output");
@@ -1429,10 +1488,10 @@ extern "C" int fdtd_llg_adjoint(fdtd_llg_t h, const double *dJ_dE, double *grad_
     for (long long seg = nck - 1; seg >= 0 && e == cudaSuccess; --seg) {
         const long long na = seg * K, nb = std::min(N, na + K);
         e = copy_state(S, S->ckpt + seg * sf, false);
-        StepCtl ctl{};
-        ctl.step = na;
-        if (e == cudaSuccess) e = cudaMemcpy(S->d_ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice);
+        // ordered on the handle's stream: earlier segments' kernels may still run
+        if (e == cudaSuccess) e = set_device_step(S->d_ctl, na, S->stream);
         L.rec_n0 = na;
+        L.rec_slots = (int)K;
         if (e == cudaSuccess && I.has_design) e = adj_record_design(L, A, 0, S->cur, S->stream);
         for (long long n = na; n < nb && e == cudaSuccess; ++n) {
             L.src = S->cur;
@@ -1453,6 +1512,7 @@ extern "C" int fdtd_llg_adjoint(fdtd_llg_t h, const double *dJ_dE, double *grad_
     cleanup();
     if (e != cudaSuccess) return fail(h, FDTD_E_CUDA, std::string("adjoint: ") + cudaGetErrorString(e));
     if (st.status & ST_UNSTABLE) return fail(h, FDTD_E_UNSTABLE, "adjoint recomputation: energy not finite");
+    if (st.status & ST_TAPE) return fail(h, FDTD_E_CUDA, "adjoint recomputation: a step fell outside its tape");
     if (grad_h0) {
         double s = 0.0;
         for (int c = 0; c < nc; ++c) s += gh[c];

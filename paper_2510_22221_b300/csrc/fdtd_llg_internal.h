@@ -117,7 +117,7 @@ struct StepCtl {
     unsigned int counter;   // CTAs (field and magnet kernels) that have finished this step
     int status;             // latched error bits (ST_*)
 };
-enum : int { ST_NOCONV = 1, ST_UNSTABLE = 2, ST_TIMEOUT = 4 };
+enum : int { ST_NOCONV = 1, ST_UNSTABLE = 2, ST_TIMEOUT = 4, ST_TAPE = 8 };
 
 struct LaunchSet {
     const Inst *insts;
@@ -141,6 +141,7 @@ struct LaunchSet {
     bool stab;                          // every instance's class table fits kTabMax
     int rec;                            // magnet kernel writes its tape (adjoint recomputation)
     long long rec_n0;                   // step of tape slot 0
+    int rec_slots;                      // slots of the tape
 };
 
 // Launchers (kernels_fwd.cu).  launch_half: the start-up H/M half-push that
@@ -174,6 +175,8 @@ struct AdjSet {
     double *geps;           // per design-box edge: d J / d eps_edge (FP64)
 };
 long long adj_ws_floats(int bx, int by, int bz, int R);
+// stream-ordered write of the device step counter (and clear of the CTA count)
+cudaError_t set_device_step(StepCtl *ctl, long long n, cudaStream_t s);
 cudaError_t adj_record_design(const LaunchSet &L, const AdjSet &A, int slot, int buf, cudaStream_t s);
 cudaError_t adj_reverse_step(const LaunchSet &L, const AdjSet &A, long long n, int slot, cudaStream_t s);
 

@@ -359,7 +359,9 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
         }
     }
     __syncthreads();
-    if (FUSED && L.rec && C.tape) {
+    if (FUSED && L.rec && C.tape && (n < L.rec_n0 || n - L.rec_n0 >= L.rec_slots)) {
+        if (tid == 0) atomicOr(&L.ctl->status, ST_TAPE);   // out of the tape: record nothing
+    } else if (FUSED && L.rec && C.tape) {
         // adjoint recording: m and face H at the start of the step, E^{n+1} at the box edges
         float *T = C.tape + (n - L.rec_n0) * C.tstride;
         const int ne3 = 3 * (bx + 1) * (by + 1) * (bz + 1);
@@ -936,7 +938,19 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
     finish_step(L, n, sred, &s_last);
 }
 
+__global__ void set_step_kernel(StepCtl *ctl, long long n)
+{
+    ctl->step = n;
+    ctl->counter = 0u;
+}
+
 }  // namespace
+
+cudaError_t set_device_step(StepCtl *ctl, long long n, cudaStream_t s)
+{
+    set_step_kernel<<<1, 1, 0, s>>>(ctl, n);
+    return cudaGetLastError();
+}
 
 int h_half_blocks_per_sm(bool cls16)
 {

@@ -273,6 +273,10 @@ class FdtdLlg:
         """z-planes per field-sweep task; 0 lets the library choose."""
         check(_abi.load().fdtd_llg_set_tiling(self._h, int(planes)), self._h)
 
+    def set_graphs(self, mode: int):
+        """CUDA graphs for long step calls: 1 on, 0 off, -1 automatic."""
+        check(_abi.load().fdtd_llg_set_graphs(self._h, int(mode)), self._h)
+
     def get_tiling(self) -> int:
         p = C.c_int32(0)
         check(_abi.load().fdtd_llg_get_tiling(self._h, C.byref(p)), self._h)

@@ -125,3 +125,18 @@ def test_adjoint_argument_errors():
         batch.run_checkpointed(4)
     assert ei.value.code == -8
     batch.destroy()
+
+
+def test_adjoint_on_a_stream_of_its_own_equals_the_default_stream():
+    """The reverse sweep orders every device write on the handle's stream: on
+    a non-blocking stream of the caller's, with many short segments, the
+    gradient is bitwise that of the default stream."""
+    make, N, n0, _ = CASES["anticross"]
+    w = make()
+    _, g_ref, h_ref = _gpu(w, N, n0, interval=9)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        _, g, h = _gpu(w, N, n0, interval=9)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(g, g_ref)
+    assert h == h_ref
