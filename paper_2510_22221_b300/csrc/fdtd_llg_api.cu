@@ -35,7 +35,6 @@ struct Instance {
     int probe_alloc = -1;             // probes the probe ring was sized for
     double *energy_buf = nullptr;
     float *mbuf = nullptr;            // all regions' deviation m (bias frame)
-    float *eedge = nullptr;           // all regions' box-edge E scratch
     uint8_t *magmat = nullptr;        // all regions' material maps
     // host descriptions
     std::vector<std::array<int, 4>> src;
@@ -529,21 +528,15 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
     std::vector<uint8_t> hmat(totV);
     // release the previous materials of this instance
     CKR(h, cudaStreamSynchronize(S->stream));
-    S->dfree(I.cls); S->dfree(I.ctab); S->dfree(I.mbuf); S->dfree(I.magmat); S->dfree(I.eedge);
-    I.cls = nullptr; I.ctab = nullptr; I.mbuf = nullptr; I.magmat = nullptr; I.eedge = nullptr;
-    size_t totE = 0;
-    for (auto &b : boxes) {
-        const size_t bx = b.x1 - b.x0 + 1, by = b.y1 - b.y0 + 1, bz = b.z1 - b.z0 + 1;
-        totE += 3 * (bx + 1) * (by + 1) * (bz + 1);
-    }
-    I.eedge = (float *)S->dalloc(std::max<size_t>(totE, 1) * sizeof(float));
+    S->dfree(I.cls); S->dfree(I.ctab); S->dfree(I.mbuf); S->dfree(I.magmat);
+    I.cls = nullptr; I.ctab = nullptr; I.mbuf = nullptr; I.magmat = nullptr;
     I.mbuf = (float *)S->dalloc(3 * totV * sizeof(float));
     I.magmat = (uint8_t *)S->dalloc(totV);
     I.cls = S->dalloc((size_t)I.nz * I.ny * I.px * (c16 ? 2 : 1));
     I.ctab = (float4 *)S->dalloc((size_t)3 * nclass * sizeof(float4));
-    if (!I.mbuf || !I.magmat || !I.cls || !I.ctab || !I.eedge) return fail(h, FDTD_E_OOM, "device allocation failed");
+    if (!I.mbuf || !I.magmat || !I.cls || !I.ctab) return fail(h, FDTD_E_OOM, "device allocation failed");
     I.comps.clear();
-    size_t off = 0, foff = 0;
+    size_t off = 0;
     for (size_t L = 0; L < boxes.size(); ++L) {
         const Box &b = boxes[L];
         MagComp C{};
@@ -559,10 +552,8 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
                 }
         C.m = I.mbuf + 3 * off;
         C.mat = I.magmat + off;
-        C.eedge = I.eedge + foff;
         I.comps.push_back(C);
         off += C.V;
-        foff += (size_t)3 * (C.bx + 1) * (C.by + 1) * (C.bz + 1);
     }
     // bias frame: M starts at Ms h, i.e. m = 0
     const double h0n = std::sqrt(hbias[0] * hbias[0] + hbias[1] * hbias[1] + hbias[2] * hbias[2]);

@@ -53,12 +53,15 @@ inline long long mag_faces(int bx, int by, int bz)
 {
     return (long long)(bx + 1) * by * bz + (long long)bx * (by + 1) * bz + (long long)bx * by * (bz + 1);
 }
-// m and its change (3 V floats each), face H and (dt/2mu0) curl E (one float
-// per face each), the material byte of each cell
+inline long long mag_edges(int bx, int by, int bz) { return 3LL * (bx + 1) * (by + 1) * (bz + 1); }
+// m (3 V floats), face H and (dt/2mu0) curl E (one float per face each), the
+// box-edge E (3 per edge; the change of M, 3 V floats, reuses it later), the
+// material byte of each cell
 inline long long mag_smem_bytes(int bx, int by, int bz)
 {
     const long long V = (long long)bx * by * bz;
-    return 4 * (6 * V + 2 * mag_faces(bx, by, bz)) + V;
+    const long long e = mag_edges(bx, by, bz);
+    return 4 * (3 * V + 2 * mag_faces(bx, by, bz) + (e > 3 * V ? e : 3 * V)) + V;
 }
 
 // Class-table entry flags (bit field stored in the .w of the first float4).
@@ -106,7 +109,6 @@ struct MagComp {
     int x0, y0, z0, bx, by, bz, V;
     float *m;               // deviation M - Ms h in the bias frame: 3 blocks of V
     const uint8_t *mat;     // V: magnet material index, 0xFF outside this region
-    float *eedge;           // scratch: E at the edges of the box, 3 blocks of (bx+1)(by+1)(bz+1)
     float *tape;            // adjoint recording: per step m (3V), face H (faces), box-edge E; NULL when off
     long long tstride;      // floats per step of the tape
 };

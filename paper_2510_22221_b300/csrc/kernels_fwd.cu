@@ -243,29 +243,67 @@ __device__ __forceinline__ void from_frame(const float *R, float lx, float ly, f
     gz = R[2] * lx + R[5] * ly + R[8] * lz;
 }
 
+// Division by a box dimension d by multiplication: with m = ceil(2^32 / d),
+// umulhi(n, m) = floor(n / d) exactly whenever n d < 2^32 (the error term
+// n (m d - 2^32) / 2^32 stays below 1).  Box indices here are below 2^16 and
+// dimensions at most 4097.
+struct UDiv {
+    unsigned d, m;
+    __device__ explicit UDiv(unsigned dd) : d(dd), m(dd > 1 ? (unsigned)(0xFFFFFFFFull / dd + 1ull) : 0u) {}
+    __device__ __forceinline__ unsigned div(unsigned n) const { return d > 1 ? __umulhi(n, m) : n; }
+};
+struct BoxDiv {
+    UDiv bx, by, bx1, by1;
+    __device__ BoxDiv(int x, int y) : bx(x), by(y), bx1(x + 1), by1(y + 1) {}
+};
+// (li, lj, lk) of cell v of a bx x by x bz box
+__device__ __forceinline__ void cell_decode(int v, const BoxDiv &D, int &li, int &lj, int &lk)
+{
+    const unsigned q1 = D.bx.div(v), q2 = D.by.div(q1);
+    li = v - (int)(q1 * D.bx.d);
+    lj = (int)(q1 - q2 * D.by.d);
+    lk = (int)q2;
+}
+
 // Face f of a region's box: axis a and box-local indices; the cells on its low
 // (vl) and high (vr) side, -1 outside the box.  Faces are numbered x faces
 // ((bx+1) by bz), then y faces (bx (by+1) bz), then z faces (bx by (bz+1)).
-__device__ __forceinline__ void face_decode(int f, int bx, int by, int bz, int &a, int &fi, int &fj, int &fk, int &vl,
-                                            int &vr)
+__device__ __forceinline__ void face_decode(int f, const BoxDiv &D, int bx, int by, int bz, int &a, int &fi, int &fj,
+                                            int &fk, int &vl, int &vr)
 {
     const int nfx = (bx + 1) * by * bz, nfy = bx * (by + 1) * bz;
     vl = vr = -1;
     if (f < nfx) {
-        a = 0; fi = f % (bx + 1); fj = (f / (bx + 1)) % by; fk = f / ((bx + 1) * by);
+        const unsigned q1 = D.bx1.div(f), q2 = D.by.div(q1);
+        a = 0; fi = f - (int)(q1 * (bx + 1)); fj = (int)(q1 - q2 * by); fk = (int)q2;
         if (fi > 0) vl = (fk * by + fj) * bx + fi - 1;
         if (fi < bx) vr = (fk * by + fj) * bx + fi;
     } else if (f < nfx + nfy) {
         const int g = f - nfx;
-        a = 1; fi = g % bx; fj = (g / bx) % (by + 1); fk = g / (bx * (by + 1));
+        const unsigned q1 = D.bx.div(g), q2 = D.by1.div(q1);
+        a = 1; fi = g - (int)(q1 * bx); fj = (int)(q1 - q2 * (by + 1)); fk = (int)q2;
         if (fj > 0) vl = (fk * by + fj - 1) * bx + fi;
         if (fj < by) vr = (fk * by + fj) * bx + fi;
     } else {
         const int g = f - nfx - nfy;
-        a = 2; fi = g % bx; fj = (g / bx) % by; fk = g / (bx * by);
+        const unsigned q1 = D.bx.div(g), q2 = D.by.div(q1);
+        a = 2; fi = g - (int)(q1 * bx); fj = (int)(q1 - q2 * by); fk = (int)q2;
         if (fk > 0) vl = ((fk - 1) * by + fj) * bx + fi;
         if (fk < bz) vr = (fk * by + fj) * bx + fi;
     }
+}
+
+// Cascaded compensated accumulation of FP32 terms (Ogita, Rump and Oishi's
+// Sum2): TwoSum gives the exact rounding error of every addition, which is
+// summed separately, so s + c carries the running sum as if in twice the
+// precision and the FP64 total does not depend on how terms are grouped.
+__device__ __forceinline__ void sum2_add(float &s, float &c, float x)
+{
+    const float t = __fadd_rn(s, x);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+    c = __fadd_rn(c, err);
+    s = t;
 }
 
 // FUSED: a full step (two half-pushes), H^{n+1/2} from buffer src, results to
@@ -290,11 +328,14 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
     const int V = C.V, bx = C.bx, by = C.by, bz = C.bz, bxy = bx * by;
     const int nfx = (bx + 1) * by * bz, nfy = bx * (by + 1) * bz, nfz = bx * by * (bz + 1);
     const int nf = nfx + nfy + nfz;
+    const int ex = bx + 1, exy = (bx + 1) * (by + 1), ne = exy * (bz + 1);
+    const BoxDiv BD(bx, by);
     float *sM = smem;            // m (bias frame), 3 blocks of V
-    float *sD = sM + 3 * V;      // M^{r} - M^{n} of the current iterate (global axes), 3 blocks of V
-    float *sH = sD + 3 * V;      // face H: H^s of the half-push, then its result
+    float *sH = sM + 3 * V;      // face H: H^s of the half-push, then its result
     float *sC = sH + nf;         // (dt/2mu0) curl E at the face
-    uint8_t *smat = reinterpret_cast<uint8_t *>(sC + nf);
+    float *sE = sC + nf;         // E at the box edges, 3 blocks of ne (until the faces are set up)
+    float *sD = sE;              // then M^{r} - M^{n} of the current iterate (global axes), 3 blocks of V
+    uint8_t *smat = reinterpret_cast<uint8_t *>(sE + (3 * ne > 3 * V ? 3 * ne : 3 * V));
     const long long n = *(volatile long long *)&L.ctl->step;
     const float ch = I->ch, h0n = I->h0n;
     float *Fs = I->F[L.src][0];
@@ -310,10 +351,10 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
         sM[2 * V + v] = C.m[2 * V + v];
     }
     if (tid < kMaxMagMat) smm[tid] = I->mm[tid];
-    // E (E^{n+1} in a full step) at every edge of the box, four edges per
-    // thread in flight at a time
+    // E (E^{n+1} in a full step) at every edge of the box into shared memory,
+    // four edges per thread in flight at a time
     {
-        const int ne3 = 3 * (bx + 1) * (by + 1) * (bz + 1);
+        const int ne3 = 3 * ne;
         for (int e0 = tid; e0 < ne3; e0 += 4 * nth) {
             float v[4];
 #pragma unroll
@@ -324,38 +365,51 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int e = e0 + u * nth;
-                if (e < ne3) C.eedge[e] = v[u];
+                if (e < ne3) sE[e] = v[u];
             }
         }
     }
     __syncthreads();
-    // H^s and (dt/2mu0) curl E at every face of the region, once for both half-pushes
+    // H^s and (dt/2mu0) curl E at every face of the region, once for both
+    // half-pushes; four faces per thread in flight at a time
     {
-        const int ex = bx + 1, exy = (bx + 1) * (by + 1), ne = exy * (bz + 1);
-        const float *Ex = C.eedge, *Ey = Ex + ne, *Ez = Ey + ne;   // written above by this CTA: read through L2
-        for (int f = tid; f < nf; f += nth) {
-            int a, fi, fj, fk, vl, vr;
-            face_decode(f, bx, by, bz, a, fi, fj, fk, vl, vr);
-            const bool own = (vl >= 0 && smat[vl] != 0xFF) || (vr >= 0 && smat[vr] != 0xFF);
-            float h = 0.f, c = 0.f;
-            if (own) {
+        const float *Ex = sE, *Ey = Ex + ne, *Ez = Ey + ne;
+        for (int f0 = tid; f0 < nf; f0 += 4 * nth) {
+            float hv[4];
+            int fa[4], fe[4];   // axis (-1: not a face of the region) and box-edge index of each face
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int f = f0 + u * nth;
+                hv[u] = 0.f;
+                fa[u] = -1;
+                fe[u] = 0;
+                if (f >= nf) continue;
+                int a, fi, fj, fk, vl, vr;
+                face_decode(f, BD, bx, by, bz, a, fi, fj, fk, vl, vr);
+                const bool own = (vl >= 0 && smat[vl] != 0xFF) || (vr >= 0 && smat[vr] != 0xFF);
+                if (!own) continue;
+                fa[u] = a;
+                fe[u] = fk * exy + fj * ex + fi;
                 const int i = C.x0 + fi, j = C.y0 + fj, k = C.z0 + fk;
-                const int e0 = fk * exy + fj * ex + fi;
-                float cu;
-                if (a == 0) {
-                    h = *hx_ptr(I, Fs, i, j, k);
-                    cu = curl2(__ldcg(Ez + e0 + ex), __ldcg(Ez + e0), I->idy, __ldcg(Ey + e0 + exy), __ldcg(Ey + e0), I->idz);
-                } else if (a == 1) {
-                    h = *hy_ptr(I, Fs, i, j, k);
-                    cu = curl2(__ldcg(Ex + e0 + exy), __ldcg(Ex + e0), I->idz, __ldcg(Ez + e0 + 1), __ldcg(Ez + e0), I->idx);
-                } else {
-                    h = *hz_ptr(I, Fs, i, j, k);
-                    cu = curl2(__ldcg(Ey + e0 + 1), __ldcg(Ey + e0), I->idx, __ldcg(Ex + e0 + ex), __ldcg(Ex + e0), I->idy);
-                }
-                c = ch * cu;
+                hv[u] = a == 0 ? *hx_ptr(I, Fs, i, j, k) : (a == 1 ? *hy_ptr(I, Fs, i, j, k) : *hz_ptr(I, Fs, i, j, k));
             }
-            sH[f] = h;
-            sC[f] = c;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int f = f0 + u * nth;
+                if (f >= nf) continue;
+                const int a = fa[u];
+                float c = 0.f;
+                if (a >= 0) {
+                    const int e0 = fe[u];
+                    float cu;
+                    if (a == 0) cu = curl2(Ez[e0 + ex], Ez[e0], I->idy, Ey[e0 + exy], Ey[e0], I->idz);
+                    else if (a == 1) cu = curl2(Ex[e0 + exy], Ex[e0], I->idz, Ez[e0 + 1], Ez[e0], I->idx);
+                    else cu = curl2(Ey[e0 + 1], Ey[e0], I->idx, Ex[e0 + ex], Ex[e0], I->idy);
+                    c = ch * cu;
+                }
+                sH[f] = hv[u];
+                sC[f] = c;
+            }
         }
     }
     __syncthreads();
@@ -364,11 +418,11 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
     } else if (FUSED && L.rec && C.tape) {
         // adjoint recording: m and face H at the start of the step, E^{n+1} at the box edges
         float *T = C.tape + (n - L.rec_n0) * C.tstride;
-        const int ne3 = 3 * (bx + 1) * (by + 1) * (bz + 1);
         for (int v = tid; v < 3 * V; v += nth) T[v] = sM[v];
         for (int f = tid; f < nf; f += nth) T[3 * V + f] = sH[f];
-        for (int e = tid; e < ne3; e += nth) T[3 * V + nf + e] = __ldcg(C.eedge + e);
+        for (int e = tid; e < 3 * ne; e += nth) T[3 * V + nf + e] = sE[e];
     }
+    __syncthreads();   // sE becomes sD
 
     double eacc = 0.0;
     const int nhalf = FUSED ? 2 : 1;
@@ -391,7 +445,8 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
                 if (v >= V) continue;
                 const int m = smat[v];
                 if (m == 0xFF) continue;
-                const int li = v % bx, lj = (v / bx) % by, lk = v / bxy;
+                int li, lj, lk;
+                cell_decode(v, BD, li, lj, lk);
                 const int fx0 = (lk * by + lj) * (bx + 1) + li, fy0 = nfx + (lk * (by + 1) + lj) * bx + li,
                           fz0 = nfx + nfy + (lk * by + lj) * bx + li;
                 const float hx0 = sH[fx0], hx1 = sH[fx0 + 1], hy0 = sH[fy0], hy1 = sH[fy0 + bx];
@@ -473,16 +528,18 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
 
         // faces: H = H^s - (dt/2mu0) curl E - (dM_low + dM_high)/2
         const bool rec = FUSED && hp == 0;
+        float es = 0.f, ec = 0.f;   // face energy of this thread, compensated
         for (int f = tid; f < nf; f += nth) {
             int a, fi, fj, fk, vl, vr;
-            face_decode(f, bx, by, bz, a, fi, fj, fk, vl, vr);
+            face_decode(f, BD, bx, by, bz, a, fi, fj, fk, vl, vr);
             const bool inl = vl >= 0 && smat[vl] != 0xFF, inr = vr >= 0 && smat[vr] != 0xFF;
             if (!inl && !inr) continue;
             const float dlv = inl ? sD[a * V + vl] : 0.f, drv = inr ? sD[a * V + vr] : 0.f;
             const float h = (sH[f] - sC[f]) - 0.5f * (dlv + drv);
             sH[f] = h;
-            if (rec) eacc += (double)(h * h);
+            if (rec) sum2_add(es, ec, h * h);
         }
+        if (rec) eacc += (double)es + (double)ec;
 #pragma unroll
         for (int q = 0; q < kMagCPT; ++q) {
             const int v = tid + q * nth;
@@ -539,7 +596,7 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
     // results: the magnetic faces of the output buffer (and far-wall arrays), m
     for (int f = tid; f < nf; f += nth) {
         int a, fi, fj, fk, vl, vr;
-        face_decode(f, bx, by, bz, a, fi, fj, fk, vl, vr);
+        face_decode(f, BD, bx, by, bz, a, fi, fj, fk, vl, vr);
         const bool own = (vl >= 0 && smat[vl] != 0xFF) || (vr >= 0 && smat[vr] != 0xFF);
         if (!own) continue;
         const int i = C.x0 + fi, j = C.y0 + fj, k = C.z0 + fk;
@@ -609,19 +666,6 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *tm, in
 }
 
 __device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
-// Cascaded compensated accumulation of FP32 terms (Ogita, Rump and Oishi's
-// Sum2): TwoSum gives the exact rounding error of every addition, which is
-// summed separately, so s + c carries the running sum as if in twice the
-// precision and the FP64 total does not depend on how terms are grouped into
-// tasks.
-__device__ __forceinline__ void sum2_add(float &s, float &c, float x)
-{
-    const float t = __fadd_rn(s, x);
-    const float bp = __fsub_rn(t, s);
-    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
-    c = __fadd_rn(c, err);
-    s = t;
-}
 __device__ __forceinline__ void st2(float *p, float a, float b) { *reinterpret_cast<float2 *>(p) = make_float2(a, b); }
 // class ids of the cell pair (x, x+1), x even
 __device__ __forceinline__ void cls2(const uint8_t *p, int &c0, int &c1)
