@@ -721,7 +721,7 @@ static int upload_descriptors(fdtd_llg_t h)
     Sim *S = h->sim;
     if (!S->dirty) return FDTD_OK;
     CKR(h, cudaStreamSynchronize(S->stream));
-    S->planes = S->tiling > 0 ? S->tiling : model_planes(S, S->nsm * std::max(1, step_blocks_per_sm(false)));
+    S->planes = S->tiling > 0 ? S->tiling : model_planes(S, S->nsm * std::max(1, step_blocks_per_sm(false, true)));
     std::vector<Inst> hi(S->inst.size());
     std::vector<int> tile_inst, ftile_inst;
     std::vector<MagComp> comps;
@@ -849,6 +849,9 @@ static LaunchSet launch_set(Sim *S)
     L.part_m = S->d_part + S->nftiles;
     L.ftile_inst = S->d_ftile_inst;
     L.nftiles = S->nftiles;
+    // persistent field-sweep CTAs: as many as fit at once (late ones, queued
+    // behind the magnet CTAs, take what is left of the task counter)
+    L.nfblocks = std::max(1, std::min(S->nftiles, S->nsm * std::max(1, step_blocks_per_sm(S->cls16, S->stab))));
     L.src = S->cur;
     L.dst = 1 - S->cur;
     L.cls16 = S->cls16;

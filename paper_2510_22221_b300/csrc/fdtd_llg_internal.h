@@ -118,6 +118,7 @@ struct StepCtl {
     long long step;         // completed steps
     unsigned int counter;   // CTAs (field and magnet kernels) that have finished this step
     int status;             // latched error bits (ST_*)
+    unsigned int work;      // next field-sweep task to hand out
 };
 enum : int { ST_NOCONV = 1, ST_UNSTABLE = 2, ST_TIMEOUT = 4, ST_TAPE = 8 };
 
@@ -132,7 +133,8 @@ struct LaunchSet {
     StepCtl *ctl;
     double *part_f, *part_m;            // energy partials per fused tile / per region
     const int *ftile_inst;
-    int nftiles;                        // fused-step tasks (one CTA each)
+    int nftiles;                        // field-sweep tasks
+    int nfblocks;                       // persistent CTAs of the field sweep
     int mag_smem;                       // dynamic shared memory of the magnet kernel (bytes)
     int src, dst;                       // field buffers read / written by a step
     int grid_h;
@@ -155,7 +157,7 @@ struct LaunchSet {
 cudaError_t launch_half(const LaunchSet &L, cudaStream_t s);
 cudaError_t launch_step(const LaunchSet &L, cudaStream_t s, cudaEvent_t *prof);
 int h_half_blocks_per_sm(bool cls16);
-int step_blocks_per_sm(bool cls16);
+int step_blocks_per_sm(bool cls16, bool stab);
 
 // ------------------------------------------------------------- adjoint
 // Device pointers of one reverse sweep (adjoint.cu), single instance.

@@ -90,7 +90,7 @@ __device__ void finish_step(const LaunchSet &L, long long n, double *sred, int *
     if (tid == 0) {
         __threadfence();
         const unsigned prev = atomicAdd(&L.ctl->counter, 1u);
-        *s_last = (prev == (unsigned)(L.nftiles + L.ncomp) - 1u);
+        *s_last = (prev == (unsigned)(L.nfblocks + L.ncomp) - 1u);
     }
     __syncthreads();
     if (!*s_last) return;
@@ -112,6 +112,7 @@ __device__ void finish_step(const LaunchSet &L, long long n, double *sred, int *
     }
     if (tid == 0) {
         L.ctl->counter = 0u;
+        L.ctl->work = 0u;
         L.ctl->step = n + 1;
         __threadfence();
     }
@@ -154,17 +155,17 @@ __global__ void __launch_bounds__(kTX *kTY) h_half_kernel(LaunchSet L)
 }
 
 // ------------------------------------------------- shared E^{n+1} arithmetic
-// Written with explicit round-to-nearest operations so that step_kernel and
-// mag_kernel produce bitwise the same E^{n+1}.
+// Written with explicit round-to-nearest and fused operations so that
+// step_kernel and mag_kernel produce bitwise the same E^{n+1}.
 // (a1 - b1) i1 - (a2 - b2) i2: one component of a Yee curl.
 __device__ __forceinline__ float curl2(float a1, float b1, float i1, float a2, float b2, float i2)
 {
-    return __fsub_rn(__fmul_rn(__fsub_rn(a1, b1), i1), __fmul_rn(__fsub_rn(a2, b2), i2));
+    return __fmaf_rn(__fsub_rn(a1, b1), i1, -__fmul_rn(__fsub_rn(a2, b2), i2));
 }
 // ca E^n + cb (curl H - J)
 __device__ __forceinline__ float e_next(float ca, float e, float cb, float c)
 {
-    return __fadd_rn(__fmul_rn(ca, e), __fmul_rn(cb, c));
+    return __fmaf_rn(ca, e, __fmul_rn(cb, c));
 }
 
 // ------------------------------------------------------------ magnet pass
@@ -701,13 +702,30 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
     __shared__ uint64_t bar[kNS];
     __shared__ float4 stab[STAB ? 3 * kTabMax : 1];
     __shared__ double sred[kST / 32];
-    __shared__ int s_last, s_abort;
+    __shared__ int s_last, s_abort, s_task;
     constexpr int CBX = sizeof(ClsT) == 1 ? kCBX8 : kCBX16;
     constexpr unsigned kClsBytes = CBX * kEBY * sizeof(ClsT);
     static_assert(kST == 32 * kSY && kSX == 64, "one warp per tile row, one cell pair per lane");
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const long long n = *(volatile long long *)&L.ctl->step;
-    const int t = blockIdx.x;
+    if (tid == 0) {
+        for (int s = 0; s < kNS; ++s) mbar_init(&bar[s], 1);
+        fence_barrier_init();
+        fence_proxy_async();
+        s_abort = 0;
+    }
+    __syncthreads();
+    // persistent CTA: tasks come from a device counter; item g (counted over
+    // all of this CTA's tasks) lives in stage g % kNS with phase parity (g / kNS) & 1
+    long long gbase = 0;                      // items of the earlier tasks
+    long long issued = 0, consumed = 0;       // items issued (thread 0) / waited for
+    const Inst *Iprev = nullptr;
+    for (;;) {
+    if (tid == 0) s_task = (int)atomicAdd(&L.ctl->work, 1u);
+    fence_proxy_async();
+    __syncthreads();
+    const int t = s_task;
+    if (t >= L.nftiles || s_abort) break;
     const Inst *I = L.insts + L.ftile_inst[t];
     const int lt = t - I->ftile_off;
     const int tx = lt % I->fntx, ty = (lt / I->fntx) % I->fnty, tz = lt / (I->fntx * I->fnty);
@@ -726,11 +744,11 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
         else return __ldg(ctab + i);
     };
 
-    int issued = 0;   // items whose loads were issued (thread 0)
     auto issue = [&](int q) {
         const int k = k0 - 1 + q;
-        unsigned char *base = stg + (q % kNS) * kStageBytes;
-        uint64_t *b = &bar[q % kNS];
+        const long long g = gbase + q;
+        unsigned char *base = stg + (int)(g % kNS) * kStageBytes;
+        uint64_t *b = &bar[g % kNS];
         if (q == 0) {
             mbar_expect_tx(b, kStageH);
             tma_load_4d(base + kStageHOff, tmH, i0 - 4, j0 - 1, k, 3, b);
@@ -740,20 +758,22 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
             tma_load_4d(base + kStageEOff, tmE, i0, j0, k, 0, b);
             tma_load_3d(base + kStageCOff, tmC, i0, j0, k, b);
         }
-        issued = q + 1;
+        issued = g + 1;
     };
     if (tid == 0) {
-        for (int s = 0; s < kNS; ++s) mbar_init(&bar[s], 1);
-        fence_barrier_init();
-        fence_proxy_async();
-        s_abort = 0;
-        tmap_acquire(tmH);
-        tmap_acquire(tmE);
-        tmap_acquire(tmC);
+        if (I != Iprev) {
+            tmap_acquire(tmH);
+            tmap_acquire(tmE);
+            tmap_acquire(tmC);
+        }
         for (int q = 0; q < min(kNS - 1, nitems); ++q) issue(q);
     }
-    if constexpr (STAB)
-        for (int c = tid; c < 3 * I->nclass; c += kST) stab[c] = __ldg(ctab + c);
+    if constexpr (STAB) {
+        if (I != Iprev) {   // the class table of this task's instance
+            for (int c = tid; c < 3 * I->nclass; c += kST) stab[c] = __ldg(ctab + c);
+        }
+    }
+    Iprev = I;
 
     // sources and probes whose column lies in this tile's extended / interior area
     unsigned smask = 0, pmask = 0;
@@ -791,14 +811,14 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
     __syncthreads();
 
     float acc = 0.f, acc_c = 0.f;   // energy of this thread's cells, compensated
-    int consumed = 0;
     for (int q = 0; q < nitems; ++q) {
-        const int s = q % kNS, sp = (q + kNS - 1) % kNS;
-        if (!mbar_wait(&bar[s], (unsigned)(q / kNS) & 1u)) {
+        const long long g = gbase + q;
+        const int s = (int)(g % kNS), sp = (int)((g + kNS - 1) % kNS);
+        if (!mbar_wait(&bar[s], (unsigned)(g / kNS) & 1u)) {
             atomicOr(&L.ctl->status, ST_TIMEOUT);
             s_abort = 1;
         }
-        consumed = q + 1;
+        consumed = g + 1;
         const int k = k0 - 1 + q;
         unsigned char *cur = stg + s * kStageBytes, *prv = stg + sp * kStageBytes;
         const float *Hc = reinterpret_cast<const float *>(cur + kStageHOff);
@@ -879,28 +899,28 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
                 f0 = __float_as_uint(tab(3 * c0).w);
                 f1 = __float_as_uint(tab(3 * c1).w);
             }
-            const float dx0 = __fmul_rn(ch, cx0), dy0 = __fmul_rn(ch, cy0), dz0 = __fmul_rn(ch, cz0);
-            const float dx1 = __fmul_rn(ch, cx1), dy1 = __fmul_rn(ch, cy1), dz1 = __fmul_rn(ch, cz1);
-            // H^{n+1} (zero where the face is magnetic: the magnet kernel owns it)
-            const float hx0 = (f0 & CF_MAG_HX) ? 0.f : __fsub_rn(HX.x, dx0);
-            const float hy0 = (f0 & CF_MAG_HY) ? 0.f : __fsub_rn(HY.x, dy0);
-            const float hz0 = (f0 & CF_MAG_HZ) ? 0.f : __fsub_rn(HZ.x, dz0);
-            const float hx1 = (f1 & CF_MAG_HX) ? 0.f : __fsub_rn(HX.y, dx1);
-            const float hy1 = (f1 & CF_MAG_HY) ? 0.f : __fsub_rn(HY.y, dy1);
-            const float hz1 = (f1 & CF_MAG_HZ) ? 0.f : __fsub_rn(HZ.y, dz1);
+            // the two half-pushes H - ch c - ch c, each one fused step; zero
+            // where the face is magnetic (the magnet kernel owns it)
+            const float mch = -ch;
+            const float hx0 = (f0 & CF_MAG_HX) ? 0.f : __fmaf_rn(mch, cx0, HX.x);
+            const float hy0 = (f0 & CF_MAG_HY) ? 0.f : __fmaf_rn(mch, cy0, HY.x);
+            const float hz0 = (f0 & CF_MAG_HZ) ? 0.f : __fmaf_rn(mch, cz0, HZ.x);
+            const float hx1 = (f1 & CF_MAG_HX) ? 0.f : __fmaf_rn(mch, cx1, HX.y);
+            const float hy1 = (f1 & CF_MAG_HY) ? 0.f : __fmaf_rn(mch, cy1, HY.y);
+            const float hz1 = (f1 & CF_MAG_HZ) ? 0.f : __fmaf_rn(mch, cz1, HZ.y);
             if (in) {
                 const unsigned o = (unsigned)(k - 1) * plane + ob;
                 if (!((f0 | f1) & (CF_MAG_HX | CF_MAG_HY | CF_MAG_HZ))) {
-                    st2(Gx + o, __fsub_rn(hx0, dx0), __fsub_rn(hx1, dx1));
-                    st2(Gy + o, __fsub_rn(hy0, dy0), __fsub_rn(hy1, dy1));
-                    st2(Gz + o, __fsub_rn(hz0, dz0), __fsub_rn(hz1, dz1));
+                    st2(Gx + o, __fmaf_rn(mch, cx0, hx0), __fmaf_rn(mch, cx1, hx1));
+                    st2(Gy + o, __fmaf_rn(mch, cy0, hy0), __fmaf_rn(mch, cy1, hy1));
+                    st2(Gz + o, __fmaf_rn(mch, cz0, hz0), __fmaf_rn(mch, cz1, hz1));
                 } else {
-                    if (!(f0 & CF_MAG_HX)) Gx[o] = __fsub_rn(hx0, dx0);
-                    if (!(f0 & CF_MAG_HY)) Gy[o] = __fsub_rn(hy0, dy0);
-                    if (!(f0 & CF_MAG_HZ)) Gz[o] = __fsub_rn(hz0, dz0);
-                    if (!(f1 & CF_MAG_HX)) Gx[o + 1] = __fsub_rn(hx1, dx1);
-                    if (!(f1 & CF_MAG_HY)) Gy[o + 1] = __fsub_rn(hy1, dy1);
-                    if (!(f1 & CF_MAG_HZ)) Gz[o + 1] = __fsub_rn(hz1, dz1);
+                    if (!(f0 & CF_MAG_HX)) Gx[o] = __fmaf_rn(mch, cx0, hx0);
+                    if (!(f0 & CF_MAG_HY)) Gy[o] = __fmaf_rn(mch, cy0, hy0);
+                    if (!(f0 & CF_MAG_HZ)) Gz[o] = __fmaf_rn(mch, cz0, hz0);
+                    if (!(f1 & CF_MAG_HX)) Gx[o + 1] = __fmaf_rn(mch, cx1, hx1);
+                    if (!(f1 & CF_MAG_HY)) Gy[o + 1] = __fmaf_rn(mch, cy1, hy1);
+                    if (!(f1 & CF_MAG_HZ)) Gz[o + 1] = __fmaf_rn(mch, cz1, hz1);
                 }
                 sum2_add(acc, acc_c, (float)(0.5 * kMu0) * (hx0 * hx0 + hy0 * hy0 + hz0 * hz0 + hx1 * hx1 + hy1 * hy1 + hz1 * hz1));
                 if (pmask) {
@@ -972,13 +992,15 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
             }
         }
     }
-    // after a timed-out wait: wait (bounded) for the copies still in flight
-    if (tid == 0)
-        for (int q = consumed; q < issued; ++q) mbar_wait(&bar[q % kNS], (unsigned)(q / kNS) & 1u);
     if (L.energy) {
         const double s = block_sum((double)acc + (double)acc_c, sred);
         if (tid == 0) L.part_f[t] = s;
     }
+    gbase += nitems;
+    }
+    // after a timed-out wait: wait (bounded) for the copies still in flight
+    if (tid == 0)
+        for (long long g = consumed; g < issued; ++g) mbar_wait(&bar[g % kNS], (unsigned)(g / kNS) & 1u);
     finish_step(L, n, sred, &s_last);
 }
 
@@ -986,6 +1008,7 @@ __global__ void set_step_kernel(StepCtl *ctl, long long n)
 {
     ctl->step = n;
     ctl->counter = 0u;
+    ctl->work = 0u;
 }
 
 }  // namespace
@@ -1021,12 +1044,17 @@ static cudaError_t step_attrs()
     return e;
 }
 
-int step_blocks_per_sm(bool cls16)
+int step_blocks_per_sm(bool cls16, bool stab)
 {
     if (step_attrs() != cudaSuccess) return 0;
     int nb = 0;
-    if (cls16) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<uint16_t, true>, kST, kStepSmem);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<uint8_t, true>, kST, kStepSmem);
+    if (cls16) {
+        if (stab) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<uint16_t, true>, kST, kStepSmem);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<uint16_t, false>, kST, kStepSmem);
+    } else {
+        if (stab) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<uint8_t, true>, kST, kStepSmem);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<uint8_t, false>, kST, kStepSmem);
+    }
     return nb;
 }
 
@@ -1060,7 +1088,7 @@ cudaError_t launch_step(const LaunchSet &L, cudaStream_t s, cudaEvent_t *prof)
     }
     if (prof) cudaEventRecord(prof[0], s);
     cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(L.nftiles);
+    cfg.gridDim = dim3(L.nfblocks);
     cfg.blockDim = dim3(kST);
     cfg.dynamicSmemBytes = kStepSmem;
     cfg.stream = s;
