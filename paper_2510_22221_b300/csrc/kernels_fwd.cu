@@ -811,6 +811,10 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
     __syncthreads();
 
     float acc = 0.f, acc_c = 0.f;   // energy of this thread's cells, compensated
+    // this thread's own two cells carried from plane to plane in registers: H
+    // of the previous plane, E^{n+1} of the previous plane; only neighbours'
+    // values come from shared memory
+    float2 cHX = make_float2(0.f, 0.f), cHY = cHX, cHZ = cHX, cEX = cHX, cEY = cHX, cEZ = cHX;
     for (int q = 0; q < nitems; ++q) {
         const long long g = gbase + q;
         const int s = (int)(g % kNS), sp = (int)((g + kNS - 1) % kNS);
@@ -825,12 +829,18 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
         const float *Hp = reinterpret_cast<const float *>(prv + kStageHOff);
         float *Ec = reinterpret_cast<float *>(cur + kStageEOff);
         const ClsT *Cc = reinterpret_cast<const ClsT *>(cur + kStageCOff);
-        if (q > 0) {
+        float2 nHX, nHY, nHZ, nEX, nEY, nEZ;   // this plane's values of the own cells
+        if (q == 0) {
+            nHX = ld2(Hc + hp);
+            nHY = ld2(Hc + kHC + hp);
+            nHZ = ld2(Hc + 2 * kHC + hp);
+            nEX = nEY = nEZ = make_float2(0.f, 0.f);
+        } else {
             // ---- E^{n+1} of plane k at the tile's cells, in place over E^n
             const float2 HX = ld2(Hc + hp), HY = ld2(Hc + kHC + hp), HZ = ld2(Hc + 2 * kHC + hp);
             const float2 HXj = ld2(Hc + hp - kHBX), HZj = ld2(Hc + 2 * kHC + hp - kHBX);
             const float hyi = Hc[kHC + hp - 1], hzi = Hc[2 * kHC + hp - 1];
-            const float2 HXk = ld2(Hp + hp), HYk = ld2(Hp + kHC + hp);
+            const float2 HXk = cHX, HYk = cHY;
             const float2 EX = ld2(Ec + ep), EY = ld2(Ec + kEC + ep), EZ = ld2(Ec + 2 * kEC + ep);
             int c0, c1;
             cls2(Cc + y * CBX + x, c0, c1);
@@ -850,6 +860,12 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
             st2(Ec + ep, ex0, ex1);
             st2(Ec + kEC + ep, ey0, ey1);
             st2(Ec + 2 * kEC + ep, ez0, ez1);
+            nHX = HX;
+            nHY = HY;
+            nHZ = HZ;
+            nEX = make_float2(ex0, ex1);
+            nEY = make_float2(ey0, ey1);
+            nEZ = make_float2(ez0, ez1);
             if (k < k1 && in) {
                 const unsigned o = (unsigned)k * plane + ob;
                 st2(Fx + o, ex0, ex1);
@@ -881,11 +897,11 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
         if (q > 1) {
             const float *Ep = reinterpret_cast<const float *>(prv + kStageEOff);
             const ClsT *Cp = reinterpret_cast<const ClsT *>(prv + kStageCOff);
-            const float2 EX = ld2(Ep + ep), EY = ld2(Ep + kEC + ep), EZ = ld2(Ep + 2 * kEC + ep);
+            const float2 EX = cEX, EY = cEY, EZ = cEZ;
             const float2 EXj = ld2(Ep + ep + kEBX), EZj = ld2(Ep + 2 * kEC + ep + kEBX);
             const float eyi = Ep[kEC + ep + 2], ezi = Ep[2 * kEC + ep + 2];
-            const float2 EXk = ld2(Ec + ep), EYk = ld2(Ec + kEC + ep);
-            const float2 HX = ld2(Hp + hp), HY = ld2(Hp + kHC + hp), HZ = ld2(Hp + 2 * kHC + hp);
+            const float2 EXk = nEX, EYk = nEY;
+            const float2 HX = cHX, HY = cHY, HZ = cHZ;
             const float cx0 = curl2(EZj.x, EZ.x, idy, EYk.x, EY.x, idz);
             const float cy0 = curl2(EXk.x, EX.x, idz, EZ.y, EZ.x, idx);
             const float cz0 = curl2(EY.y, EY.x, idx, EXj.x, EX.x, idy);
@@ -991,6 +1007,12 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
                 }
             }
         }
+        cHX = nHX;
+        cHY = nHY;
+        cHZ = nHZ;
+        cEX = nEX;
+        cEY = nEY;
+        cEZ = nEZ;
     }
     if (L.energy) {
         const double s = block_sum((double)acc + (double)acc_c, sred);
