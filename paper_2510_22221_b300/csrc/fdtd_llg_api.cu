@@ -297,6 +297,7 @@ static int create_impl(const fdtd_llg_config *cfgs, int32_t n, fdtd_llg_t *out)
     S->d_ctl = (StepCtl *)S->dalloc(sizeof(StepCtl));
     if (!S->d_ctl) { fdtd_llg_destroy(root); return fail(nullptr, FDTD_E_OOM, "device allocation failed"); }
     cudaMemsetAsync(S->d_ctl, 0, sizeof(StepCtl), S->stream);
+    set_device_step(S->d_ctl, 0, S->stream);   // also: no energy partials pending
     if (cudaStreamSynchronize(S->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
         fdtd_llg_destroy(root);
         return fail(nullptr, FDTD_E_CUDA, "initialisation failed");
@@ -502,7 +503,8 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
         if (V > kMagMaxV)
             return fail(h, FDTD_E_INVAL, "a magnetic region's bounding box holds " + std::to_string(V) + " cells (maximum " +
                                              std::to_string(kMagMaxV) + ")");
-        if (mag_smem_bytes(b.x1 - b.x0 + 1, b.y1 - b.y0 + 1, b.z1 - b.z0 + 1) > kMagSmemMax)
+        int qx, py, ps;
+        if (!mag_stage_block(b.x1 - b.x0 + 1, b.y1 - b.y0 + 1, b.z1 - b.z0 + 1, qx, py, ps))
             return fail(h, FDTD_E_INVAL, "a magnetic region's bounding box has too many faces for one CTA's shared memory");
         boxes.push_back(b);
     }
@@ -608,7 +610,10 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
     S->half_ahead = false;
     S->cur = 0;
     S->adj_N = 0;   // a recorded run belongs to the previous materials
-    CKR(h, cudaMemset(S->d_ctl, 0, sizeof(StepCtl)));
+    // ordered on the handle's stream (its kernels may still run)
+    CKR(h, cudaMemsetAsync(S->d_ctl, 0, sizeof(StepCtl), S->stream));
+    CKR(h, set_device_step(S->d_ctl, 0, S->stream));
+    CKR(h, cudaStreamSynchronize(S->stream));
     S->dirty = true;
     return FDTD_OK;
 }
@@ -778,9 +783,10 @@ static int upload_descriptors(fdtd_llg_t h)
         d.nmag = (int)I.comps.size();
         for (auto C : I.comps) {
             C.inst = (int)ii;
+            mag_stage_block(C.bx, C.by, C.bz, C.qx, C.py, C.ps);
             comps.push_back(C);
             vmax = std::max(vmax, C.V);
-            msmem = std::max(msmem, (int)mag_smem_bytes(C.bx, C.by, C.bz));
+            msmem = std::max(msmem, (int)mag_smem_bytes(C.bx, C.by, C.bz, C.qx, C.py, C.ps));
         }
         for (size_t m = 0; m < I.mm.size(); ++m) d.mm[m] = I.mm[m];
         c16 = c16 || I.cls_bytes == 2;
@@ -811,14 +817,19 @@ static int upload_descriptors(fdtd_llg_t h)
     S->d_tile_inst = (int *)S->dalloc(tile_inst.size() * sizeof(int));
     S->d_ftile_inst = (int *)S->dalloc(ftile_inst.size() * sizeof(int));
     S->d_comps = (MagComp *)S->dalloc(std::max<size_t>(1, comps.size()) * sizeof(MagComp));
-    S->d_part = (double *)S->dalloc((ftile_inst.size() + comps.size() + 1) * sizeof(double));
+    const size_t part_stride = ftile_inst.size() * kSW + comps.size();
+    S->d_part = (double *)S->dalloc((2 * part_stride + 1) * sizeof(double));
     if (!S->d_insts || !S->d_tile_inst || !S->d_ftile_inst || !S->d_comps || !S->d_part)
         return fail(h, FDTD_E_OOM, "device allocation failed");
     CKR(h, cudaMemcpy(S->d_insts, hi.data(), hi.size() * sizeof(Inst), cudaMemcpyHostToDevice));
     CKR(h, cudaMemcpy(S->d_tile_inst, tile_inst.data(), tile_inst.size() * sizeof(int), cudaMemcpyHostToDevice));
     CKR(h, cudaMemcpy(S->d_ftile_inst, ftile_inst.data(), ftile_inst.size() * sizeof(int), cudaMemcpyHostToDevice));
     if (!comps.empty()) CKR(h, cudaMemcpy(S->d_comps, comps.data(), comps.size() * sizeof(MagComp), cudaMemcpyHostToDevice));
-    CKR(h, cudaMemset(S->d_part, 0, (ftile_inst.size() + comps.size() + 1) * sizeof(double)));
+    CKR(h, cudaMemset(S->d_part, 0, (2 * part_stride + 1) * sizeof(double)));
+    // the pending step's partials are gone with the old buffer (its energy was
+    // already summed by the flush that ended its run): epend = -1
+    CKR(h, cudaMemsetAsync(&S->d_ctl->epend, 0xFF, sizeof(long long), S->stream));
+    CKR(h, cudaStreamSynchronize(S->stream));
     S->ntiles = (int)tile_inst.size();
     S->nftiles = (int)ftile_inst.size();
     S->ncomp = (int)comps.size();
@@ -845,8 +856,10 @@ static LaunchSet launch_set(Sim *S)
     L.mag_smem = S->mag_smem;
     L.stab = S->stab;
     L.ctl = S->d_ctl;
+    L.nslot_f = S->nftiles * kSW;
+    L.part_stride = L.nslot_f + S->ncomp;
     L.part_f = S->d_part;
-    L.part_m = S->d_part + S->nftiles;
+    L.part_m = S->d_part + L.nslot_f;
     L.ftile_inst = S->d_ftile_inst;
     L.nftiles = S->nftiles;
     // persistent field-sweep CTAs: as many as fit at once (late ones, queued
@@ -937,6 +950,7 @@ extern "C" int fdtd_llg_step(fdtd_llg_t h, int64_t nsteps)
         }
         S->cur ^= 1;
     }
+    if (nsteps > 0) CKR(h, launch_energy_flush(L, S->stream));
     S->host_step += nsteps;
     return FDTD_OK;
 }
@@ -1221,9 +1235,10 @@ extern "C" int fdtd_llg_load_state(fdtd_llg_t h, const void *buf, size_t size)
     Sim *S = h->sim;
     S->host_step = hd.step;
     S->half_ahead = hd.half_ahead != 0;
-    StepCtl c{};
-    c.step = hd.step;
-    CKR(h, cudaMemcpy(S->d_ctl, &c, sizeof c, cudaMemcpyHostToDevice));
+    CKR(h, cudaStreamSynchronize(S->stream));
+    CKR(h, cudaMemsetAsync(S->d_ctl, 0, sizeof(StepCtl), S->stream));
+    CKR(h, set_device_step(S->d_ctl, hd.step, S->stream));
+    CKR(h, cudaStreamSynchronize(S->stream));
     return FDTD_OK;
 }
 
@@ -1494,6 +1509,7 @@ extern "C" int fdtd_llg_adjoint(fdtd_llg_t h, const double *dJ_dE, double *grad_
             S->cur ^= 1;
             if (e == cudaSuccess && I.has_design) e = adj_record_design(L, A, (int)(n - na + 1), S->cur, S->stream);
         }
+        if (e == cudaSuccess) e = launch_energy_flush(L, S->stream);
         for (long long n = nb - 1; n >= na && e == cudaSuccess; --n) e = adj_reverse_step(L, A, n, (int)(n - na), S->stream);
         S->host_step = nb;
     }

@@ -30,6 +30,7 @@ constexpr int kTX = 32, kTY = 8, kKC = 16;
 // overwrites E^n in place.  A stage stays live for two planes (as plane k and
 // then as plane k-1), so kNS - 2 planes are in flight while one is computed.
 constexpr int kSX = 64, kSY = 8, kSZ = 16, kST = 256, kNS = 4;
+constexpr int kSW = kST / 32;   // warps of a sweep CTA (one energy partial each per task)
 constexpr int kHBX = kSX + 8, kHBY = kSY + 2, kHC = kHBX * kHBY;   // H box, one component
 constexpr int kEBX = kSX + 4, kEBY = kSY + 1, kEC = kEBX * kEBY;   // E box, one component
 constexpr int kCBX8 = kSX + 16, kCBX16 = kSX + 8;                  // class box width (u8 / u16)
@@ -54,14 +55,41 @@ inline long long mag_faces(int bx, int by, int bz)
     return (long long)(bx + 1) * by * bz + (long long)bx * (by + 1) * bz + (long long)bx * by * (bz + 1);
 }
 inline long long mag_edges(int bx, int by, int bz) { return 3LL * (bx + 1) * (by + 1) * (bz + 1); }
-// m (3 V floats), face H and (dt/2mu0) curl E (one float per face each), the
-// box-edge E (3 per edge; the change of M, 3 V floats, reuses it later), the
+// m (3 V floats), face H (one float per face), the box-edge E (3 per edge;
+// the change of M, 3 V floats, reuses it later), then one area that first
+// holds the stage of a block of qx x py x ps edge sites (H on the block grown
+// by one cell on its low x, y and z sides, 3 components, and the class id of
+// each site as u16) and then (dt/2mu0) curl E (one float per face), the
 // material byte of each cell
-inline long long mag_smem_bytes(int bx, int by, int bz)
+inline long long mag_stage_floats(int bx, int by, int bz, int qx, int py, int ps)
+{
+    const long long stage = 3LL * (qx + 1) * (py + 1) * (ps + 1) + ((long long)qx * py * ps + 1) / 2;
+    const long long nf = mag_faces(bx, by, bz);
+    return stage > nf ? stage : nf;
+}
+inline long long mag_smem_bytes(int bx, int by, int bz, int qx, int py, int ps)
 {
     const long long V = (long long)bx * by * bz;
     const long long e = mag_edges(bx, by, bz);
-    return 4 * (3 * V + 2 * mag_faces(bx, by, bz) + (e > 3 * V ? e : 3 * V)) + V;
+    return 4 * (3 * V + mag_faces(bx, by, bz) + (e > 3 * V ? e : 3 * V) + mag_stage_floats(bx, by, bz, qx, py, ps)) + V;
+}
+// Block of the staged box (the box has (bx+1)(by+1)(bz+1) edge sites): whole
+// x rows and y columns with as many z planes as fit, else one plane and as
+// many rows as fit, else one row and as many sites as fit; false when not
+// even one site fits (the region is too large for one CTA).
+inline bool mag_stage_block(int bx, int by, int bz, int &qx, int &py, int &ps)
+{
+    qx = bx + 1;
+    py = by + 1;
+    for (ps = bz + 1; ps >= 1; --ps)
+        if (mag_smem_bytes(bx, by, bz, qx, py, ps) <= kMagSmemMax) return true;
+    ps = 1;
+    for (py = by; py >= 1; --py)
+        if (mag_smem_bytes(bx, by, bz, qx, py, ps) <= kMagSmemMax) return true;
+    py = 1;
+    for (qx = bx; qx >= 1; --qx)
+        if (mag_smem_bytes(bx, by, bz, qx, py, ps) <= kMagSmemMax) return true;
+    return false;
 }
 
 // Class-table entry flags (bit field stored in the .w of the first float4).
@@ -107,6 +135,7 @@ struct alignas(128) Inst {
 struct MagComp {
     int inst;
     int x0, y0, z0, bx, by, bz, V;
+    int qx, py, ps;         // edge sites per staged block in x, y, z (mag_stage_block)
     float *m;               // deviation M - Ms h in the bias frame: 3 blocks of V
     const uint8_t *mat;     // V: magnet material index, 0xFF outside this region
     float *tape;            // adjoint recording: per step m (3V), face H (faces), box-edge E; NULL when off
@@ -119,6 +148,7 @@ struct StepCtl {
     unsigned int counter;   // CTAs (field and magnet kernels) that have finished this step
     int status;             // latched error bits (ST_*)
     unsigned int work;      // next field-sweep task to hand out
+    long long epend;        // step whose energy partials await their sums (-1: none)
 };
 enum : int { ST_NOCONV = 1, ST_UNSTABLE = 2, ST_TIMEOUT = 4, ST_TAPE = 8 };
 
@@ -131,7 +161,11 @@ struct LaunchSet {
     int ncomp;
     int vmax;
     StepCtl *ctl;
-    double *part_f, *part_m;            // energy partials per fused tile / per region
+    // energy partials of one step, two sets used by step parity: part_f[t *
+    // kSW + w] per sweep task t and warp w, then part_m[c] per magnet region
+    // (part_m = part_f + nslot_f); set p starts at part_f + p * part_stride
+    double *part_f, *part_m;
+    int nslot_f, part_stride;
     const int *ftile_inst;
     int nftiles;                        // field-sweep tasks
     int nfblocks;                       // persistent CTAs of the field sweep
@@ -156,6 +190,11 @@ struct LaunchSet {
 // NULL, holds four events recorded around the two kernels.
 cudaError_t launch_half(const LaunchSet &L, cudaStream_t s);
 cudaError_t launch_step(const LaunchSet &L, cudaStream_t s, cudaEvent_t *prof);
+// The energy of step n is summed during step n + 1 (by the sweep CTAs that
+// draw its reduction tasks); launch_energy_flush sums the last step's after a
+// run of steps, with the same arithmetic, so the values do not depend on where
+// a run of steps ends.
+cudaError_t launch_energy_flush(const LaunchSet &L, cudaStream_t s);
 int h_half_blocks_per_sm(bool cls16);
 int step_blocks_per_sm(bool cls16, bool stab);
 

@@ -80,12 +80,44 @@ __device__ double source_value(const double *p, double t)
 }
 
 
+// The energy of step m of instance ii from that step's partials (written by
+// the step's sweep warps and magnet CTAs), into its ring slot.  Every thread
+// of the CTA calls it with the same arguments; thread q sums the slots
+// q, q + blockDim, ... in order and block_sum adds the threads in a fixed
+// tree, so the value is the same whichever CTA or kernel forms it.  Nothing
+// is done unless step m's partials are the pending ones.
+__device__ void reduce_energy(const LaunchSet &L, int ii, long long m, double *sred)
+{
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const bool pend = m >= 0 && *(volatile long long *)&L.ctl->epend == m;
+    if (!pend) return;
+    const Inst *I = L.insts + ii;
+    const double *pf = L.part_f + (m & 1) * L.part_stride, *pm = L.part_m + (m & 1) * L.part_stride;
+    const int s0 = I->ftile_off * kSW, s1 = (I->ftile_off + I->fntx * I->fnty * I->fntz) * kSW;
+    double s = 0.0;
+    int q = s0 + tid;
+    for (; q + 3 * nth < s1; q += 4 * nth) {
+        const double a = ld_cg(pf + q), b = ld_cg(pf + q + nth), c = ld_cg(pf + q + 2 * nth), d = ld_cg(pf + q + 3 * nth);
+        s += a;
+        s += b;
+        s += c;
+        s += d;
+    }
+    for (; q < s1; q += nth) s += ld_cg(pf + q);
+    for (int c = I->mag_off + tid; c < I->mag_off + I->nmag; c += nth) s += ld_cg(pm + c);
+    s = block_sum(s, sred);
+    if (tid == 0) {
+        const double W = s * I->dV;
+        I->energy_buf[m % I->cap] = W;
+        if (!isfinite(W)) atomicOr(&L.ctl->status, ST_UNSTABLE);
+    }
+}
+
 // Called by every CTA of a step (field and magnet kernels) after its partials
-// are written: the last one sums them per instance and advances the step.
-__device__ void finish_step(const LaunchSet &L, long long n, double *sred, int *s_last)
+// are written: the last one advances the step and marks its partials pending.
+__device__ void finish_step(const LaunchSet &L, long long n, int *s_last)
 {
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-    const int nth = blockDim.x * blockDim.y;
     __syncthreads();
     if (tid == 0) {
         __threadfence();
@@ -94,25 +126,11 @@ __device__ void finish_step(const LaunchSet &L, long long n, double *sred, int *
     }
     __syncthreads();
     if (!*s_last) return;
-    __threadfence();
-    if (L.energy) {
-        for (int ii = 0; ii < L.ninst; ++ii) {
-            const Inst *I = L.insts + ii;
-            const int t0 = I->ftile_off, t1 = t0 + I->fntx * I->fnty * I->fntz;
-            double s = 0.0;
-            for (int t = t0 + tid; t < t1; t += nth) s += ld_cg(L.part_f + t);
-            for (int c = I->mag_off + tid; c < I->mag_off + I->nmag; c += nth) s += ld_cg(L.part_m + c);
-            s = block_sum(s, sred);
-            if (tid == 0) {
-                const double W = s * I->dV;
-                I->energy_buf[n % I->cap] = W;
-                if (!isfinite(W)) atomicOr(&L.ctl->status, ST_UNSTABLE);
-            }
-        }
-    }
     if (tid == 0) {
+        __threadfence();
         L.ctl->counter = 0u;
         L.ctl->work = 0u;
+        L.ctl->epend = L.energy ? n : -1;
         L.ctl->step = n + 1;
         __threadfence();
     }
@@ -169,6 +187,13 @@ __device__ __forceinline__ float e_next(float ca, float e, float cb, float c)
 }
 
 // ------------------------------------------------------------ magnet pass
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+// 4-byte asynchronous copy global -> shared (completion: cp_async_wait_all)
+__device__ __forceinline__ void cp_async4(float *dst, const float *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 __device__ __forceinline__ float *hx_ptr(const Inst *I, float *F0, int i, int j, int k)
 {
     return (i == I->nx) ? I->wHx + (long long)k * I->ny + j : F0 + 3 * I->fstride + (long long)k * I->plane + (long long)j * I->px + i;
@@ -181,46 +206,16 @@ __device__ __forceinline__ float *hz_ptr(const Inst *I, float *F0, int i, int j,
 {
     return (k == I->nz) ? I->wHz + (long long)j * I->nx + i : F0 + 5 * I->fstride + (long long)k * I->plane + (long long)j * I->px + i;
 }
-
-// E at edge e of a magnetic region's box: e = comp * ne + ((lk (by+1) + lj)
-// (bx+1) + li), global edge (comp, x0+li, y0+lj, z0+lk) with li in [0, bx],
-// lj in [0, by], lk in [0, bz]; advanced to E^{n+1} from buffer src (ADVANCE)
-// or as stored.  Edges beyond the far walls are zero.
-template <bool ADVANCE, typename ClsT>
-__device__ __forceinline__ float box_edge(const LaunchSet &L, const MagComp &C, const Inst *I, int e, long long n)
+// H component c (0: x, 1: y, 2: z) of buffer F0 at cell (i, j, k) where it is
+// stored (the far-wall arrays hold Hx at i = nx, Hy at j = ny, Hz at k = nz);
+// NULL where nothing is stored, which the kernels read as zero
+__device__ __forceinline__ const float *h_src(const Inst *I, float *F0, int c, int i, int j, int k)
 {
-    const int ex = C.bx + 1, ey = C.by + 1, ne = ex * ey * (C.bz + 1);
-    const int comp = e / ne, r = e - comp * ne;
-    const int li = r % ex, lj = (r / ex) % ey, lk = r / (ex * ey);
-    const int i = C.x0 + li, j = C.y0 + lj, k = C.z0 + lk;
-    float v = 0.f;
-    if (i < I->nx && j < I->ny && k < I->nz) {
-        const float *__restrict__ Fs = I->F[L.src][0];
-        const long long fs = I->fstride, plane = I->plane;
-        const int px = I->px;
-        const long long o = (long long)k * plane + (long long)j * px + i;
-        if (!ADVANCE) {
-            v = Fs[comp * fs + o];
-        } else {
-            const float *Hx = Fs + 3 * fs, *Hy = Fs + 4 * fs, *Hz = Fs + 5 * fs;
-            float cu;
-            if (comp == 0)
-                cu = curl2(Hz[o], j > 0 ? Hz[o - px] : 0.f, I->idy, Hy[o], k > 0 ? Hy[o - plane] : 0.f, I->idz);
-            else if (comp == 1)
-                cu = curl2(Hx[o], k > 0 ? Hx[o - plane] : 0.f, I->idz, Hz[o], i > 0 ? Hz[o - 1] : 0.f, I->idx);
-            else
-                cu = curl2(Hy[o], i > 0 ? Hy[o - 1] : 0.f, I->idx, Hx[o], j > 0 ? Hx[o - px] : 0.f, I->idy);
-            for (int s = 0; s < I->nsrc; ++s)
-                if (I->src[s][0] == comp && I->src[s][1] == i && I->src[s][2] == j && I->src[s][3] == k)
-                    cu = __fsub_rn(cu, (float)source_value(I->srcp[s], ((double)n + 0.5) * I->dt));
-            const int c = (int)static_cast<const ClsT *>(I->cls)[o];
-            const float4 A = __ldg(I->ctab + 3 * c), B = __ldg(I->ctab + 3 * c + 1);
-            const float ca = comp == 0 ? A.x : (comp == 1 ? A.y : A.z);
-            const float cb = comp == 0 ? B.x : (comp == 1 ? B.y : B.z);
-            v = e_next(ca, Fs[comp * fs + o], cb, cu);
-        }
-    }
-    return v;
+    if (i < 0 || j < 0 || k < 0) return nullptr;
+    const int nx = I->nx, ny = I->ny, nz = I->nz;
+    if (c == 0) return (i <= nx && j < ny && k < nz) ? hx_ptr(I, F0, i, j, k) : nullptr;
+    if (c == 1) return (i < nx && j <= ny && k < nz) ? hy_ptr(I, F0, i, j, k) : nullptr;
+    return (i < nx && j < ny && k <= nz) ? hz_ptr(I, F0, i, j, k) : nullptr;
 }
 
 // The LLG solve runs in the bias frame (rows of I->R: e1, e2, e3 = h) on the
@@ -309,8 +304,11 @@ __device__ __forceinline__ void sum2_add(float &s, float &c, float x)
 
 // FUSED: a full step (two half-pushes), H^{n+1/2} from buffer src, results to
 // buffer dst, curl of E^{n+1}.  Otherwise: the start-up half-push, in place on
-// buffer src, curl of the stored E.  The CTA first evaluates E at every edge of
-// its box (with the arithmetic of step_kernel) into the region's scratch.
+// buffer src, curl of the stored E.  The CTA first copies what it reads of
+// buffer src into shared memory with asynchronous copies (m, E at the box
+// edges, then per block of edge sites H and the class ids), so that the set-up
+// costs one memory round trip per block instead of one per dependent load,
+// and evaluates E^{n+1} at every box edge with the arithmetic of step_kernel.
 template <bool FUSED, typename ClsT>
 __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
 {
@@ -333,84 +331,132 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
     const BoxDiv BD(bx, by);
     float *sM = smem;            // m (bias frame), 3 blocks of V
     float *sH = sM + 3 * V;      // face H: H^s of the half-push, then its result
-    float *sC = sH + nf;         // (dt/2mu0) curl E at the face
-    float *sE = sC + nf;         // E at the box edges, 3 blocks of ne (until the faces are set up)
+    float *sE = sH + nf;         // E at the box edges, 3 blocks of ne (until the faces are set up)
     float *sD = sE;              // then M^{r} - M^{n} of the current iterate (global axes), 3 blocks of V
-    uint8_t *smat = reinterpret_cast<uint8_t *>(sE + (3 * ne > 3 * V ? 3 * ne : 3 * V));
+    // stage of one block of at most qx x py x ps edge sites: H of buffer src
+    // on the block grown by one cell on its low sides, then the class id of
+    // each site; once the edges and faces are set up the area holds sC
+    const int sst = (C.qx + 1) * (C.py + 1) * (C.ps + 1);
+    float *sS = sE + (3 * ne > 3 * V ? 3 * ne : 3 * V);
+    float *sC = sS;              // (dt/2mu0) curl E at the face
+    uint16_t *scl = reinterpret_cast<uint16_t *>(sS + 3 * sst);
+    const int narea = max(nf, 3 * sst + (C.qx * C.py * C.ps + 1) / 2);
+    uint8_t *smat = reinterpret_cast<uint8_t *>(sS + narea);
     const long long n = *(volatile long long *)&L.ctl->step;
     const float ch = I->ch, h0n = I->h0n;
     float *Fs = I->F[L.src][0];
     float *Fd = I->F[FUSED ? L.dst : L.src][0];
+    const int nx = I->nx, ny = I->ny, nz = I->nz, px = I->px;
+    const long long fs = I->fstride, plane = I->plane;
     float R[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) R[q] = I->R[q];
 
+    // m, the material ids and E^n at every box edge: one batch of
+    // asynchronous copies (edges beyond the far walls are zero)
     for (int v = tid; v < V; v += nth) {
         smat[v] = C.mat[v];
-        sM[v] = C.m[v];
-        sM[V + v] = C.m[V + v];
-        sM[2 * V + v] = C.m[2 * V + v];
+        cp_async4(sM + v, C.m + v);
+        cp_async4(sM + V + v, C.m + V + v);
+        cp_async4(sM + 2 * V + v, C.m + 2 * V + v);
     }
     if (tid < kMaxMagMat) smm[tid] = I->mm[tid];
-    // E (E^{n+1} in a full step) at every edge of the box into shared memory,
-    // four edges per thread in flight at a time
     {
-        const int ne3 = 3 * ne;
-        for (int e0 = tid; e0 < ne3; e0 += 4 * nth) {
-            float v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int e = e0 + u * nth;
-                v[u] = e < ne3 ? box_edge<FUSED, ClsT>(L, C, I, e, n) : 0.f;
+        const UDiv dex(ex), dey(by + 1);
+        for (int e = tid; e < 3 * ne; e += nth) {
+            const int comp = e >= 2 * ne ? 2 : (e >= ne ? 1 : 0), r = e - comp * ne;
+            const unsigned q1 = dex.div(r), q2 = dey.div(q1);
+            const int i = C.x0 + r - (int)(q1 * ex), j = C.y0 + (int)(q1 - q2 * (by + 1)), k = C.z0 + (int)q2;
+            if (i < nx && j < ny && k < nz) cp_async4(sE + e, Fs + comp * fs + k * plane + (long long)j * px + i);
+            else sE[e] = 0.f;
+        }
+    }
+    // per block of edge sites [xa, xb) x [ya, yb) x [za, zb): stage H (and the
+    // class ids), then E^{n+1} at the block's edges (with the arithmetic of
+    // step_kernel) and H^s at the faces whose indices lie in the block
+    bool first = true;
+    for (int za = 0; za <= bz; za += C.ps)
+    for (int ya = 0; ya <= by; ya += C.py)
+    for (int xa = 0; xa <= bx; xa += C.qx) {
+        const int xb = min(xa + C.qx, bx + 1), yb = min(ya + C.py, by + 1), zb = min(za + C.ps, bz + 1);
+        const int nbx = xb - xa, nby = yb - ya, nbz = zb - za;
+        const int SX = nbx + 1, SXY = SX * (nby + 1), nsc = SXY * (nbz + 1), nsite = nbx * nby * nbz;
+        const UDiv dsx(SX), dsxy(SXY), dbx(nbx), dby(nby);
+        if (!first) __syncthreads();   // the previous block is done with the stage
+        first = false;
+        for (int q = tid; q < 3 * nsc; q += nth) {
+            const int c = q >= 2 * nsc ? 2 : (q >= nsc ? 1 : 0), r = q - c * nsc;
+            const unsigned kk = dsxy.div(r), r2 = r - kk * SXY, jj = dsx.div(r2), ii = r2 - jj * SX;
+            const float *src = h_src(I, Fs, c, C.x0 + xa - 1 + (int)ii, C.y0 + ya - 1 + (int)jj, C.z0 + za - 1 + (int)kk);
+            float *dst = sS + c * sst + r;
+            if (src) cp_async4(dst, src);
+            else *dst = 0.f;
+        }
+        if (FUSED) {
+            for (int q = tid; q < nsite; q += nth) {
+                const unsigned q1 = dbx.div(q), q2 = dby.div(q1);
+                const int i = C.x0 + xa + q - (int)(q1 * nbx), j = C.y0 + ya + (int)(q1 - q2 * nby), k = C.z0 + za + (int)q2;
+                scl[q] = (i < nx && j < ny && k < nz) ? (uint16_t) static_cast<const ClsT *>(I->cls)[k * plane + (long long)j * px + i] : 0;
             }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int e = e0 + u * nth;
-                if (e < ne3) sE[e] = v[u];
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        // stage value of H component c at box-local cell (li, lj, lk), each
+        // index at most one below the block
+        auto hs = [&](int c, int li, int lj, int lk) {
+            return sS[c * sst + (lk - za + 1) * SXY + (lj - ya + 1) * SX + li - xa + 1];
+        };
+        if (FUSED) {
+            for (int q = tid; q < 3 * nsite; q += nth) {
+                const int comp = q >= 2 * nsite ? 2 : (q >= nsite ? 1 : 0), r = q - comp * nsite;
+                const unsigned q1 = dbx.div(r), q2 = dby.div(q1);
+                const int li = xa + r - (int)(q1 * nbx), lj = ya + (int)(q1 - q2 * nby), lk = za + (int)q2;
+                const int i = C.x0 + li, j = C.y0 + lj, k = C.z0 + lk;
+                if (i >= nx || j >= ny || k >= nz) continue;
+                float cu;
+                if (comp == 0)
+                    cu = curl2(hs(2, li, lj, lk), hs(2, li, lj - 1, lk), I->idy, hs(1, li, lj, lk), hs(1, li, lj, lk - 1), I->idz);
+                else if (comp == 1)
+                    cu = curl2(hs(0, li, lj, lk), hs(0, li, lj, lk - 1), I->idz, hs(2, li, lj, lk), hs(2, li - 1, lj, lk), I->idx);
+                else
+                    cu = curl2(hs(1, li, lj, lk), hs(1, li - 1, lj, lk), I->idx, hs(0, li, lj, lk), hs(0, li, lj - 1, lk), I->idy);
+                for (int so = 0; so < I->nsrc; ++so)
+                    if (I->src[so][0] == comp && I->src[so][1] == i && I->src[so][2] == j && I->src[so][3] == k)
+                        cu = __fsub_rn(cu, (float)source_value(I->srcp[so], ((double)n + 0.5) * I->dt));
+                const int c = scl[r];
+                const float4 A = __ldg(I->ctab + 3 * c), B = __ldg(I->ctab + 3 * c + 1);
+                const float ca = comp == 0 ? A.x : (comp == 1 ? A.y : A.z);
+                const float cb = comp == 0 ? B.x : (comp == 1 ? B.y : B.z);
+                const int e = comp * ne + (lk * (by + 1) + lj) * ex + li;
+                sE[e] = e_next(ca, sE[e], cb, cu);
             }
+        }
+        for (int f = tid; f < nf; f += nth) {
+            int a, fi, fj, fk, vl, vr;
+            face_decode(f, BD, bx, by, bz, a, fi, fj, fk, vl, vr);
+            if (fi < xa || fi >= xb || fj < ya || fj >= yb || fk < za || fk >= zb) continue;
+            const bool own = (vl >= 0 && smat[vl] != 0xFF) || (vr >= 0 && smat[vr] != 0xFF);
+            sH[f] = own ? hs(a, fi, fj, fk) : 0.f;
         }
     }
     __syncthreads();
-    // H^s and (dt/2mu0) curl E at every face of the region, once for both
-    // half-pushes; four faces per thread in flight at a time
+    // (dt/2mu0) curl E at every face of the region
     {
         const float *Ex = sE, *Ey = Ex + ne, *Ez = Ey + ne;
-        for (int f0 = tid; f0 < nf; f0 += 4 * nth) {
-            float hv[4];
-            int fa[4], fe[4];   // axis (-1: not a face of the region) and box-edge index of each face
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int f = f0 + u * nth;
-                hv[u] = 0.f;
-                fa[u] = -1;
-                fe[u] = 0;
-                if (f >= nf) continue;
-                int a, fi, fj, fk, vl, vr;
-                face_decode(f, BD, bx, by, bz, a, fi, fj, fk, vl, vr);
-                const bool own = (vl >= 0 && smat[vl] != 0xFF) || (vr >= 0 && smat[vr] != 0xFF);
-                if (!own) continue;
-                fa[u] = a;
-                fe[u] = fk * exy + fj * ex + fi;
-                const int i = C.x0 + fi, j = C.y0 + fj, k = C.z0 + fk;
-                hv[u] = a == 0 ? *hx_ptr(I, Fs, i, j, k) : (a == 1 ? *hy_ptr(I, Fs, i, j, k) : *hz_ptr(I, Fs, i, j, k));
+        for (int f = tid; f < nf; f += nth) {
+            int a, fi, fj, fk, vl, vr;
+            face_decode(f, BD, bx, by, bz, a, fi, fj, fk, vl, vr);
+            const bool own = (vl >= 0 && smat[vl] != 0xFF) || (vr >= 0 && smat[vr] != 0xFF);
+            float c = 0.f;
+            if (own) {
+                const int e0 = fk * exy + fj * ex + fi;
+                float cu;
+                if (a == 0) cu = curl2(Ez[e0 + ex], Ez[e0], I->idy, Ey[e0 + exy], Ey[e0], I->idz);
+                else if (a == 1) cu = curl2(Ex[e0 + exy], Ex[e0], I->idz, Ez[e0 + 1], Ez[e0], I->idx);
+                else cu = curl2(Ey[e0 + 1], Ey[e0], I->idx, Ex[e0 + ex], Ex[e0], I->idy);
+                c = ch * cu;
             }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int f = f0 + u * nth;
-                if (f >= nf) continue;
-                const int a = fa[u];
-                float c = 0.f;
-                if (a >= 0) {
-                    const int e0 = fe[u];
-                    float cu;
-                    if (a == 0) cu = curl2(Ez[e0 + ex], Ez[e0], I->idy, Ey[e0 + exy], Ey[e0], I->idz);
-                    else if (a == 1) cu = curl2(Ex[e0 + exy], Ex[e0], I->idz, Ez[e0 + 1], Ez[e0], I->idx);
-                    else cu = curl2(Ey[e0 + 1], Ey[e0], I->idx, Ex[e0 + ex], Ex[e0], I->idy);
-                    c = ch * cu;
-                }
-                sH[f] = hv[u];
-                sC[f] = c;
-            }
+            sC[f] = c;
         }
     }
     __syncthreads();
@@ -611,13 +657,12 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
     }
     if (FUSED) {
         const double s = block_sum(eacc, sredd);
-        if (tid == 0) L.part_m[blockIdx.x] = s;
-        finish_step(L, n, sredd, &s_last);
+        if (tid == 0) L.part_m[(n & 1) * L.part_stride + blockIdx.x] = s;
+        finish_step(L, n, &s_last);
     }
 }
 
 // ---------------------------------------------------------- fused step
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint64_t *b, unsigned count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)), "r"(count) : "memory");
@@ -720,12 +765,22 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
     long long gbase = 0;                      // items of the earlier tasks
     long long issued = 0, consumed = 0;       // items issued (thread 0) / waited for
     const Inst *Iprev = nullptr;
+    // the first nred values of the task counter are the previous step's
+    // per-instance energy sums, the rest the sweep tasks
+    const int nred = L.energy ? L.ninst : 0;
+    double *const pf = L.part_f + (n & 1) * L.part_stride;
     for (;;) {
     if (tid == 0) s_task = (int)atomicAdd(&L.ctl->work, 1u);
     fence_proxy_async();
     __syncthreads();
-    const int t = s_task;
-    if (t >= L.nftiles || s_abort) break;
+    const int v = s_task;
+    if (v >= nred + L.nftiles || s_abort) break;
+    if (v < nred) {
+        reduce_energy(L, v, n - 1, sred);
+        __syncthreads();   // every thread has read s_task before thread 0 draws again
+        continue;
+    }
+    const int t = v - nred;
     const Inst *I = L.insts + L.ftile_inst[t];
     const int lt = t - I->ftile_off;
     const int tx = lt % I->fntx, ty = (lt / I->fntx) % I->fnty, tz = lt / (I->fntx * I->fnty);
@@ -1014,16 +1069,26 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
         cEY = nEY;
         cEZ = nEZ;
     }
-    if (L.energy) {
-        const double s = block_sum((double)acc + (double)acc_c, sred);
-        if (tid == 0) L.part_f[t] = s;
+    if (L.energy) {   // one partial per warp: no block barrier per task
+        double e = (double)acc + (double)acc_c;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        if (lane == 0) pf[(long long)t * kSW + w] = e;
     }
     gbase += nitems;
     }
     // after a timed-out wait: wait (bounded) for the copies still in flight
     if (tid == 0)
         for (long long g = consumed; g < issued; ++g) mbar_wait(&bar[g % kNS], (unsigned)(g / kNS) & 1u);
-    finish_step(L, n, sred, &s_last);
+    finish_step(L, n, &s_last);
+}
+
+// The pending step's energy of instance blockIdx.x (after the last step of a
+// run; kST threads, as in the sweep, so that the sums are the same bits).
+__global__ void __launch_bounds__(kST) energy_flush_kernel(LaunchSet L)
+{
+    __shared__ double sred[kST / 32];
+    reduce_energy(L, blockIdx.x, *(volatile long long *)&L.ctl->epend, sred);
 }
 
 __global__ void set_step_kernel(StepCtl *ctl, long long n)
@@ -1031,6 +1096,7 @@ __global__ void set_step_kernel(StepCtl *ctl, long long n)
     ctl->step = n;
     ctl->counter = 0u;
     ctl->work = 0u;
+    ctl->epend = -1;
 }
 
 }  // namespace
@@ -1090,6 +1156,13 @@ cudaError_t launch_half(const LaunchSet &L, cudaStream_t s)
     const dim3 blk(kTX, kTY);
     if (L.cls16) h_half_kernel<uint16_t><<<L.grid_h, blk, 0, s>>>(L);
     else h_half_kernel<uint8_t><<<L.grid_h, blk, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy_flush(const LaunchSet &L, cudaStream_t s)
+{
+    if (!L.energy || L.ninst < 1) return cudaSuccess;
+    energy_flush_kernel<<<L.ninst, kST, 0, s>>>(L);
     return cudaGetLastError();
 }
 

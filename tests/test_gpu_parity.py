@@ -120,6 +120,51 @@ def test_random_small_every_feature(seed):
     compare_fields(sim, orc, M0, t)
 
 
+def _large_region(kind, steps):
+    """One magnetic region near the size limit of the magnet kernel, touching
+    a far wall, in a grid the oracle runs in seconds.  The kernel stages the
+    box in blocks of edge sites that fit shared memory: the 16^3 cube in two
+    blocks of z planes, the 60x32x2 film in blocks of y rows, the 2000-cell
+    line in blocks of x sites.  The probes sit where the source's pulse
+    arrives within the run (elsewhere both sides hold only rounding residue of
+    the static magnetisation, FP64 in the oracle, exact zeros here)."""
+    mats = [W.material(), W.material(eps_r=2.0, Ms=1.4e5, alpha=0.01, gamma=1.76e11)]
+    if kind == "cube":
+        nx, ny, nz = 20, 19, 18
+        mid = np.zeros((nz, ny, nx), dtype=np.uint8)
+        mid[1:17, 2:18, nx - 16:nx] = 1
+        src = [dict(comp=2, i=2, j=9, k=9, J0=3e6, f0=4e12, Tp=2e-13, tpk=4e-13)]
+        probes = [(nx - 8, 9, 8), (2, 2, 2)]
+    elif kind == "film":
+        nx, ny, nz = 64, 34, 6
+        mid = np.zeros((nz, ny, nx), dtype=np.uint8)
+        mid[2:4, ny - 32:ny, 2:62] = 1
+        src = [dict(comp=0, i=30, j=1, k=4, J0=3e6, f0=4e12, Tp=2e-13, tpk=4e-13)]
+        probes = [(30, 3, 3), (31, 4, 2)]
+    else:
+        nx, ny, nz = 2000, 3, 3
+        mid = np.zeros((nz, ny, nx), dtype=np.uint8)
+        mid[1, 1, :] = 1
+        src = [dict(comp=2, i=1000, j=2, k=1, J0=3e6, f0=4e12, Tp=2e-13, tpk=4e-13)]
+        probes = [(1000, 1, 1), (1003, 1, 1)]
+    h0 = np.array([0.6, -0.3, 0.75])
+    h0 = h0 / np.linalg.norm(h0) * (2.0 / W.MU0)
+    return W.Workload(f"large_region_{kind}", nx, ny, nz, 1e-6, 1.1e-6, 0.9e-6, 0.6, steps, mats, mid, h0, src, probes)
+
+
+@pytest.mark.parametrize("kind", ["cube", "film", "line"])
+def test_large_region_staged_in_blocks(kind):
+    w = _large_region(kind, 40)
+    sim, orc, out, M0 = run_pair(w, w.steps)
+    t = tol(w.steps)
+    for p, (i, j, k) in enumerate(w.probes):
+        errs = probe_errors(sim.probe(p), out["probes"][:, p], M0[:, k, j, i], t, w.steps)
+        assert max(errs) < t, (p, errs)
+    assert rel_err(sim.energy(), out["energy"]) < t
+    compare_fields(sim, orc, M0, t)
+    sim.destroy()
+
+
 @pytest.mark.parametrize("dims", [(1, 1, 1), (1, 1, 2), (33, 9, 17), (40, 1, 3), (3, 70, 2)])
 def test_ragged_and_degenerate_grids(dims):
     nx, ny, nz = dims
@@ -181,6 +226,42 @@ def test_checkpoint_resume_is_bitwise():
     b.step(23)
     for n, v in fa.items():
         np.testing.assert_array_equal(b.get_field(n), v)
+
+
+def test_energy_does_not_depend_on_how_the_run_is_split():
+    """Each step's energy is summed from per-warp partials in a fixed order,
+    during the next step or by the flush that ends a call: one call with
+    CUDA graphs, many short calls without, a save/load and a tiling change in
+    the middle all give the same record (to the bit where the tiling, which
+    fixes the order of the partial sums, is the same)."""
+    import torch
+
+    w = W.random_small(7, nx=40, ny=21, nz=19, steps=70)
+    with torch.cuda.stream(torch.cuda.Stream()):   # graphs need a stream that can be captured
+        a = pkg.from_workload(w, probe_capacity=128)
+        a.set_graphs(1)
+        a.step(70)
+        ref = a.energy()
+    assert ref.shape == (70,) and np.all(np.isfinite(ref)) and np.all(ref[5:] > 0)
+    b = pkg.from_workload(w, probe_capacity=128)
+    b.set_graphs(0)
+    for n in (1, 1, 1, 1, 1, 30, 35):
+        b.step(n)
+    np.testing.assert_array_equal(b.energy(), ref)
+    c = pkg.from_workload(w, probe_capacity=128)
+    c.step(33)
+    blob = c.save_state()
+    d = pkg.from_workload(w, probe_capacity=128)
+    d.load_state(blob)
+    d.step(37)
+    np.testing.assert_array_equal(d.energy()[33:], ref[33:])
+    c.set_tiling(5)
+    c.step(37)
+    e = c.energy()
+    np.testing.assert_array_equal(e[:33], ref[:33])
+    np.testing.assert_allclose(e[33:], ref[33:], rtol=1e-12, atol=0)
+    for sim in (a, b, c, d):
+        sim.destroy()
 
 
 def test_batch_equals_separate_runs_bitwise():
