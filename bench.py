@@ -248,6 +248,29 @@ def batch_sweep(torch, pkg, W, steps_timed=2000, steps_total=10000):
             "spectrum_peak_hz_first_last": [peaks[0], peaks[-1]], "anticrossing_fit": fit}
 
 
+def large_run(torch, pkg, W, steps=1000, warmup=10):
+    """Config 4: the 512 x 512 x 256 eight-strip array (67 M cells, eight
+    3072-cell YIG films, alpha 1e-4, strong drive); FP32 fields, FP64 energy
+    and probe rows every step; throughput and fraction of the HBM roofline."""
+    w = W.multi_strip(steps=steps)
+    stream = torch.cuda.current_stream()
+    sim = pkg.from_workload(w, probe_capacity=steps + warmup + 8)
+    sim.step(warmup)
+    sim.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    sim.sync()
+    sec = e0.elapsed_time(e1) * 1e-3
+    sim.destroy()
+    value = w.cells * steps / sec / 1e6
+    hbm, _ = peaks()
+    return {"workload": w.name, "cells": w.cells, "magnet_cells": int((w.mat_id == 3).sum()), "steps": steps,
+            "mcells_per_s": round(value, 1), "ms_per_step": round(sec * 1e3 / steps, 5),
+            "hbm_roofline_pct": round(100 * value * 1e6 * ALG_BYTES_PER_CELL_STEP / (hbm * 1e9), 2)}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -272,7 +295,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
-    ap.add_argument("--no-extra", action="store_true", help="skip the adjoint and batched-sweep measurements")
+    ap.add_argument("--no-extra", action="store_true", help="skip the adjoint, batched-sweep and 512x512x256 measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -350,7 +373,8 @@ def main():
                        "l2": "field state 201 MB > 126 MB L2: inputs larger than L2, no flush",
                        "parallelism": "one independent grid per GPU" if world > 1 else "single GPU"},
             "hbm_roofline_pct": round(100 * value * 1e6 * ALG_BYTES_PER_CELL_STEP / (world * hbm * 1e9), 2),
-            "roofline": roofline, "gpu_launches": (2 if passes["mag"]["launches"] else 1) * K, "clocks": clk,
+            # two kernels per step (magnet, sweep), one energy flush per step call
+            "roofline": roofline, "gpu_launches": (2 if passes["mag"]["launches"] else 1) * K + 1, "clocks": clk,
             "adjoint_forward_ratio": None}
 
     # end to end through the public API: materials from pinned host memory,
@@ -384,6 +408,7 @@ def main():
         line["adjoint"] = adj
         line["adjoint_forward_ratio"] = adj["adjoint_forward_ratio"]
         line["batch_sweep"] = batch_sweep(torch, pkg, W)
+        line["large_run"] = large_run(torch, pkg, W)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w, 12)
     if rank == 0:

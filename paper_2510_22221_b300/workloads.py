@@ -105,8 +105,12 @@ def strip_resonator(nx=256, ny=256, nz=128, steps=20000, strips=1, film=(40, 8, 
 
 def multi_strip(steps=50000) -> Workload:
     """512 x 512 x 256, eight strips each loaded by a 64 x 12 x 4 YIG film,
-    alpha = 1e-4, drive amplitude 1e6 times the linear configurations'."""
-    return strip_resonator(512, 512, 256, steps, strips=8, film=(64, 12, 4), alpha=1e-4, J0=1e6,
+    alpha = 1e-4, drive amplitude 1e6 times the linear configurations'.  Each
+    film lies along its strip: 64 cells in y, 12 across in x, 4 thick; the
+    strips are 64 cells apart in x, so the films stay separate magnetic
+    regions (64 cells across would make the eight one connected 512-cell
+    band, beyond one region's size)."""
+    return strip_resonator(512, 512, 256, steps, strips=8, film=(12, 64, 4), alpha=1e-4, J0=1e6,
                            name="multi_strip_512x512x256")
 
 
