@@ -7,8 +7,9 @@
 // (P: half the change of each adjacent cell's M on a face).  Its transpose,
 // with lambda the adjoint of the step's outputs:
 //   magnetic regions (adj_mag_kernel): both half-pushes reversed through the
-//     fixed number of Jacobi iterates of the trapezoidal LLG solve (the 3 x 9
-//     Jacobian of one cell's increment by forward-mode dual numbers), giving
+//     fixed number of Jacobi iterates of the trapezoidal LLG solve (the
+//     transposed 3 x 9 Jacobian of one cell's increment applied in one
+//     reverse-mode pass, llg_inc_vjp), giving
 //     the adjoint of the faces' H and of M at the step's start, of the curl
 //     terms, and d J / d |H_bias|;
 //   adj_curl_h_kernel:  lambda_E' = lambda_E - (dt/mu0) C_H lambda_H (for a
@@ -24,55 +25,11 @@ namespace fl {
 
 namespace {
 
-// ------------------------------------------------------------ dual numbers
-struct D1 {
-    float v, d;
-};
-__device__ __forceinline__ D1 mk(float v, float d = 0.f) { return {v, d}; }
-__device__ __forceinline__ D1 operator+(D1 a, D1 b) { return {a.v + b.v, a.d + b.d}; }
-__device__ __forceinline__ D1 operator-(D1 a, D1 b) { return {a.v - b.v, a.d - b.d}; }
-__device__ __forceinline__ D1 operator-(D1 a) { return {-a.v, -a.d}; }
-__device__ __forceinline__ D1 operator*(D1 a, D1 b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
-__device__ __forceinline__ D1 operator*(float s, D1 a) { return {s * a.v, s * a.d}; }
-__device__ __forceinline__ D1 operator+(D1 a, float s) { return {a.v + s, a.d}; }
-__device__ __forceinline__ D1 operator+(float s, D1 a) { return {a.v + s, a.d}; }
-__device__ __forceinline__ D1 operator/(D1 a, D1 b) { return {a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)}; }
-__device__ __forceinline__ D1 dsqrt(D1 a)
-{
-    const float r = sqrtf(a.v);
-    return {r, r > 0.f ? 0.5f * a.d / r : 0.f};
-}
-
 // One cell's LLG increment in the bias frame (the arithmetic of mag_kernel):
 // m deviation from Ms e3, hs = H_eff at the start of the half-push, h = H_eff
 // of the previous iterate (both with the bias on e3); returns dl = M^{r} - M^n.
-template <typename T>
-__device__ __forceinline__ void llg_inc(const T m[3], const T hs[3], const T h[3], const MagMat &mm, T dl[3])
-{
-    const T Mz = m[2] + mm.Ms;
-    const float dam = mm.alpha * mm.inv_Ms, k = mm.kappa;
-    const T ax = -(k * h[0] + dam * m[0]);
-    const T ay = -(k * h[1] + dam * m[1]);
-    const T az = -(k * h[2] + dam * m[2] + mm.alpha);
-    const T rx = (-k) * (m[1] * hs[2] - Mz * hs[1]) - k * (m[1] * h[2] - Mz * h[1]);
-    const T ry = (-k) * (Mz * hs[0] - m[0] * hs[2]) - k * (Mz * h[0] - m[0] * h[2]);
-    const T rz = (-k) * (m[0] * hs[1] - m[1] * hs[0]) - k * (m[0] * h[1] - m[1] * h[0]);
-    const T ar = ax * rx + ay * ry + az * rz;
-    const T inv1 = mk(1.f) / (1.f + (ax * ax + ay * ay + az * az));
-    const T dx = (rx + ar * ax - (ay * rz - az * ry)) * inv1;
-    const T dy = (ry + ar * ay - (az * rx - ax * rz)) * inv1;
-    const T dz = (rz + ar * az - (ax * ry - ay * rx)) * inv1;
-    const T nM2 = m[0] * m[0] + m[1] * m[1] + Mz * Mz;
-    const T md2 = 2.f * (m[0] * dx + m[1] * dy + Mz * dz) + (dx * dx + dy * dy + dz * dz);
-    const T nM = dsqrt(nM2), nMt = dsqrt(nM2 + md2);
-    const T s1 = -(md2 / (nMt * (nM + nMt)));
-    dl[0] = dx + s1 * (m[0] + dx);
-    dl[1] = dy + s1 * (m[1] + dy);
-    dl[2] = dz + s1 * (Mz + dz);
-}
-template <>
-__device__ __forceinline__ void llg_inc<float>(const float m[3], const float hs[3], const float h[3], const MagMat &mm,
-                                               float dl[3])
+__device__ __forceinline__ void llg_inc(const float m[3], const float hs[3], const float h[3], const MagMat &mm,
+                                        float dl[3])
 {
     const float Mz = m[2] + mm.Ms;
     const float dam = mm.alpha * mm.inv_Ms, k = mm.kappa;
@@ -94,6 +51,91 @@ __device__ __forceinline__ void llg_inc<float>(const float m[3], const float hs[
     dl[0] = dx + s1 * (m[0] + dx);
     dl[1] = dy + s1 * (m[1] + dy);
     dl[2] = dz + s1 * (Mz + dz);
+}
+
+// Reverse mode of llg_inc: given ld, the adjoint of dl, returns the
+// adjoints gm, ghs, gh of m, hs and h (J^T ld for the 3 x 9 Jacobian).  With
+// M = m + Ms e3 and S = hs + h the increment is
+//   a = -(kappa h + (alpha/Ms) M),  r = -kappa M x S,
+//   d = (r + (a.r) a - a x r) / (1 + a.a),
+//   dl = d + s1 (M + d),  s1 = -md2 / (|M~| (|M| + |M~|)),
+//   md2 = 2 M.d + d.d,  |M~| = sqrt(|M|^2 + md2),
+// and the adjoints below run those lines backwards.
+__device__ __forceinline__ void cross3(const float a[3], const float b[3], float c[3])
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+__device__ __forceinline__ float dot3(const float a[3], const float b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+__device__ void llg_inc_vjp(const float m[3], const float hs[3], const float h[3], const MagMat &mm, const float ld[3],
+                            float gm[3], float ghs[3], float gh[3])
+{
+    const float k = mm.kappa, dam = mm.alpha * mm.inv_Ms;
+    const float M[3] = {m[0], m[1], m[2] + mm.Ms};
+    const float S[3] = {hs[0] + h[0], hs[1] + h[1], hs[2] + h[2]};
+    float a[3], r[3], MxS[3], axr[3], u[3], d[3], Md[3];
+    for (int c = 0; c < 3; ++c) a[c] = -(k * h[c] + dam * M[c]);
+    cross3(M, S, MxS);
+    for (int c = 0; c < 3; ++c) r[c] = -k * MxS[c];
+    const float ar = dot3(a, r);
+    const float inv1 = 1.f / (1.f + dot3(a, a));
+    cross3(a, r, axr);
+    for (int c = 0; c < 3; ++c) {
+        u[c] = r[c] + ar * a[c] - axr[c];
+        d[c] = u[c] * inv1;
+        Md[c] = M[c] + d[c];
+    }
+    const float nM2 = dot3(M, M);
+    const float md2 = 2.f * dot3(M, d) + dot3(d, d);
+    const float nM = sqrtf(nM2), nMt = sqrtf(nM2 + md2);
+    const float P = nMt * (nM + nMt);
+    const float s1 = -md2 / P;
+    // dl = d + s1 (M + d)
+    float gd[3], gM[3];
+    for (int c = 0; c < 3; ++c) {
+        gd[c] = ld[c] * (1.f + s1);
+        gM[c] = ld[c] * s1;
+    }
+    const float gs1 = dot3(ld, Md);
+    // s1 = -md2 / P, P = nMt nM + nMt^2
+    float gmd2 = -gs1 / P;
+    const float gP = gs1 * md2 / (P * P);
+    const float gnMt = gP * (nM + 2.f * nMt), gnM = gP * nMt;
+    const float gt = gnMt / (2.f * nMt);       // nMt = sqrt(nM2 + md2)
+    gmd2 += gt;
+    const float gnM2 = gt + gnM / (2.f * nM);
+    // md2 = 2 M.d + d.d,  nM2 = M.M
+    for (int c = 0; c < 3; ++c) {
+        gM[c] += 2.f * gmd2 * d[c] + 2.f * gnM2 * M[c];
+        gd[c] += 2.f * gmd2 * (M[c] + d[c]);
+    }
+    // d = u inv1,  inv1 = 1 / (1 + a.a)
+    float gu[3], ga[3], gr[3];
+    const float ginv1 = dot3(gd, u);
+    for (int c = 0; c < 3; ++c) {
+        gu[c] = gd[c] * inv1;
+        ga[c] = -2.f * ginv1 * inv1 * inv1 * a[c];
+    }
+    // u = r + (a.r) a - a x r
+    const float gar = dot3(gu, a);
+    float uxr[3], axu[3];
+    cross3(gu, r, uxr);   // adjoint of a in -(a x r): gu x r
+    cross3(a, gu, axu);   // adjoint of r in -(a x r): a x gu
+    for (int c = 0; c < 3; ++c) {
+        gr[c] = gu[c] + axu[c] + gar * a[c];
+        ga[c] += ar * gu[c] + uxr[c] + gar * r[c];
+    }
+    // a = -(kappa h + dam M),  r = -kappa M x S
+    float Sxg[3], gxM[3];
+    cross3(S, gr, Sxg);
+    cross3(gr, M, gxM);
+    for (int c = 0; c < 3; ++c) {
+        gm[c] = gM[c] - dam * ga[c] - k * Sxg[c];
+        const float gS = -k * gxM[c];
+        ghs[c] = gS;
+        gh[c] = gS - k * ga[c];
+    }
 }
 
 __device__ __forceinline__ void to_fr(const float *R, const float g[3], float l[3])
@@ -223,7 +265,7 @@ __device__ void fwd_half(const MagComp &C, const Inst *I, const float *R9, const
             }
             float hs[3], h[3], mm[3], dl[3], dg[3];
             cell_inputs(C, I, R9, smat, V, Hs, Cc, Dp, m, v, hs, h, mm, nfx, nfy);
-            llg_inc<float>(mm, hs, h, I->mm[mt], dl);
+            llg_inc(mm, hs, h, I->mm[mt], dl);
             from_fr(R9, dl, dg);
             for (int a = 0; a < 3; ++a) Dr[a * V + v] = dg[a];
             if (r == R)
@@ -284,18 +326,9 @@ __device__ void rev_half(const MagComp &C, const Inst *I, const float *R9, const
             float hs[3], h[3], mm[3];
             cell_inputs(C, I, R9, smat, V, Hs, Cc, Dp, m, v, hs, h, mm, nfx, nfy);
             const float ld[3] = {W.lamDl[v], W.lamDl[V + v], W.lamDl[2 * V + v]};
-            // J^T lambda, one input direction at a time (forward-mode duals)
+            // J^T lambda in one reverse pass: gin = (m, hs, h) adjoints
             float gin[9];
-            for (int q = 0; q < 9; ++q) {
-                D1 dm[3], dhs[3], dh[3], out[3];
-                for (int a = 0; a < 3; ++a) {
-                    dm[a] = mk(mm[a], q == a ? 1.f : 0.f);
-                    dhs[a] = mk(hs[a], q == 3 + a ? 1.f : 0.f);
-                    dh[a] = mk(h[a], q == 6 + a ? 1.f : 0.f);
-                }
-                llg_inc<D1>(dm, dhs, dh, I->mm[mt], out);
-                gin[q] = out[0].d * ld[0] + out[1].d * ld[1] + out[2].d * ld[2];
-            }
+            llg_inc_vjp(mm, hs, h, I->mm[mt], ld, gin, gin + 3, gin + 6);
             for (int a = 0; a < 3; ++a) {
                 W.lamM[a * V + v] += gin[a];
                 W.lamHsm[a * V + v] += gin[3 + a];   // bias frame, converted below

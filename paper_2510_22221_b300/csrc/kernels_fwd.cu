@@ -96,12 +96,12 @@ __device__ void reduce_energy(const LaunchSet &L, int ii, long long m, double *s
     const int s0 = I->ftile_off * kSW, s1 = (I->ftile_off + I->fntx * I->fnty * I->fntz) * kSW;
     double s = 0.0;
     int q = s0 + tid;
-    for (; q + 3 * nth < s1; q += 4 * nth) {
-        const double a = ld_cg(pf + q), b = ld_cg(pf + q + nth), c = ld_cg(pf + q + 2 * nth), d = ld_cg(pf + q + 3 * nth);
-        s += a;
-        s += b;
-        s += c;
-        s += d;
+    for (; q + 7 * nth < s1; q += 8 * nth) {   // eight loads in flight, added in slot order
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = ld_cg(pf + q + u * nth);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += v[u];
     }
     for (; q < s1; q += nth) s += ld_cg(pf + q);
     for (int c = I->mag_off + tid; c < I->mag_off + I->nmag; c += nth) s += ld_cg(pm + c);
