@@ -14,10 +14,13 @@
 //     terms, and d J / d |H_bias|;
 //   adj_curl_h_kernel:  lambda_E' = lambda_E - (dt/mu0) C_H lambda_H (for a
 //     non-magnetic face both half-pushes pass lambda_H through; magnetic faces
-//     carry the magnet kernel's curl adjoint here);
-//   adj_design_kernel:  d J / d eps_edge += (cb/dt) lambda_E' (E^n - E^{n+1});
-//   adj_curl_e_kernel:  lambda_H += C_E (cb lambda_E'),  lambda_E = ca lambda_E';
-//   adj_fix_kernel:     the magnetic faces take their own adjoint.
+//     carry the magnet kernel's curl adjoint here); it stores w = cb lambda_E'
+//     and lambda_E = ca lambda_E' (the class lookup once per edge);
+//   adj_design_kernel:  d J / d eps_edge += (w/dt) (E^n - E^{n+1});
+//   adj_curl_e_kernel:  lambda_H += C_E w;
+//   the magnetic faces then take their own adjoint: the next reverse step's
+//     magnet kernel adds the pending correction as it reads them
+//     (adj_fix_kernel applies the last one after the sweep).
 // C_E^T = C_H on the Yee grid, so the transposed curls are the forward curls.
 #include "fdtd_llg_internal.h"
 
@@ -417,11 +420,13 @@ __global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSe
         else if (a == 1) cu = curl2a(Ex[e0 + exy], Ex[e0], I->idz, Ez[e0 + 1], Ez[e0], I->idx);
         else cu = curl2a(Ey[e0 + 1], Ey[e0], I->idx, Ex[e0 + ex], Ex[e0], I->idy);
         W.C[f] = ch * cu;
-        // adjoint of the step's output faces (H^{n+3/2}): field arrays or walls
+        // adjoint of the step's output faces (H^{n+3/2}): field arrays or
+        // walls, plus the correction the later step left pending in fix
         const int i = C.x0 + fi, j = C.y0 + fj, k = C.z0 + fk;
         const bool own = (vl >= 0 && C.mat[vl] != 0xFF) || (vr >= 0 && C.mat[vr] != 0xFF);
         W.lamHout[f] = own ? *(a == 0 ? hx_at(I, A.lamH, i, j, k, A.lamW)
-                                      : (a == 1 ? hy_at(I, A.lamH, i, j, k, A.lamW) : hz_at(I, A.lamH, i, j, k, A.lamW)))
+                                      : (a == 1 ? hy_at(I, A.lamH, i, j, k, A.lamW) : hz_at(I, A.lamH, i, j, k, A.lamW))) +
+                                 W.fix[f]
                            : 0.f;
     }
     __syncthreads();
@@ -439,7 +444,8 @@ __global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSe
     rev_half(C, I, R9, smat, V, nf, R, W.Hs1, W.C, W.m1, W.D1, W, W.lamHout, W.lamHin, W.lamC, &g, nfx, nfy);
     // write back: for a magnetic face the curl sweep must see q/2 with
     // q = -(lamC1 + lamC2) (a plain face contributes 2 lambda_H); afterwards
-    // the face takes lamHin, which adj_fix_kernel restores from fix
+    // the face takes lamHin, restored from fix by the next reverse step's
+    // magnet kernel (or adj_fix_kernel after the last)
     for (int f = tid; f < nf; f += nth) {
         int a, fi, fj, fk, vl, vr;
         fdecode(f, bx, by, bz, a, fi, fj, fk, vl, vr);
@@ -515,13 +521,18 @@ __global__ void __launch_bounds__(256) adj_curl_h_kernel(LaunchSet L, AdjSet A)
     const float cx = curl2a(lz[o], j > 0 ? lz[o - px] : 0.f, I->idy, ly[o], k > 0 ? ly[o - plane] : 0.f, I->idz);
     const float cy = curl2a(lx[o], k > 0 ? lx[o - plane] : 0.f, I->idz, lz[o], i > 0 ? lz[o - 1] : 0.f, I->idx);
     const float cz = curl2a(ly[o], i > 0 ? ly[o - 1] : 0.f, I->idx, lx[o], j > 0 ? lx[o - px] : 0.f, I->idy);
-    A.lamEn[o] = A.lamE[o] - c2 * cx;
-    A.lamEn[fs + o] = A.lamE[fs + o] - c2 * cy;
-    A.lamEn[2 * fs + o] = A.lamE[2 * fs + o] - c2 * cz;
+    const float ex = A.lamE[o] - c2 * cx, ey = A.lamE[fs + o] - c2 * cy, ez = A.lamE[2 * fs + o] - c2 * cz;
+    const int c = (int)static_cast<const ClsT *>(I->cls)[o];
+    const float4 Ca = __ldg(I->ctab + 3 * c), Cb = __ldg(I->ctab + 3 * c + 1);
+    A.lamEn[o] = Cb.x * ex;           // w = cb lambda_E'
+    A.lamEn[fs + o] = Cb.y * ey;
+    A.lamEn[2 * fs + o] = Cb.z * ez;
+    A.lamE[o] = Ca.x * ex;            // lambda_E = ca lambda_E'
+    A.lamE[fs + o] = Ca.y * ey;
+    A.lamE[2 * fs + o] = Ca.z * ez;
 }
 
-// lambda_H += C_E (cb lambda_E'),  lambda_E = ca lambda_E'
-template <typename ClsT>
+// lambda_H += C_E w  (w = cb lambda_E', zero beyond the far walls)
 __global__ void __launch_bounds__(256) adj_curl_e_kernel(LaunchSet L, AdjSet A)
 {
     const Inst *I = L.insts;
@@ -530,26 +541,15 @@ __global__ void __launch_bounds__(256) adj_curl_e_kernel(LaunchSet L, AdjSet A)
     const long long fs = I->fstride, plane = I->plane;
     const int px = I->px;
     const long long o = (long long)k * plane + (long long)j * px + i;
-    const ClsT *cls = static_cast<const ClsT *>(I->cls);
-    const float4 *ctab = I->ctab;
-    auto w = [&](int comp, int ii, int jj, int kk) -> float {   // cb lambda_E' of edge (comp, ii, jj, kk)
-        if (ii >= I->nx || jj >= I->ny || kk >= I->nz) return 0.f;
-        const long long q = (long long)kk * plane + (long long)jj * px + ii;
-        const float4 B = __ldg(ctab + 3 * (int)cls[q] + 1);
-        const float cb = comp == 0 ? B.x : (comp == 1 ? B.y : B.z);
-        return cb * A.lamEn[comp * fs + q];
-    };
-    const float wx = w(0, i, j, k), wy = w(1, i, j, k), wz = w(2, i, j, k);
-    const float cx = curl2a(w(2, i, j + 1, k), wz, I->idy, w(1, i, j, k + 1), wy, I->idz);
-    const float cy = curl2a(w(0, i, j, k + 1), wx, I->idz, w(2, i + 1, j, k), wz, I->idx);
-    const float cz = curl2a(w(1, i + 1, j, k), wy, I->idx, w(0, i, j + 1, k), wx, I->idy);
+    const float *wx_ = A.lamEn, *wy_ = A.lamEn + fs, *wz_ = A.lamEn + 2 * fs;
+    const bool xi = i + 1 < I->nx, yj = j + 1 < I->ny, zk = k + 1 < I->nz;
+    const float wx = wx_[o], wy = wy_[o], wz = wz_[o];
+    const float cx = curl2a(yj ? wz_[o + px] : 0.f, wz, I->idy, zk ? wy_[o + plane] : 0.f, wy, I->idz);
+    const float cy = curl2a(zk ? wx_[o + plane] : 0.f, wx, I->idz, xi ? wz_[o + 1] : 0.f, wz, I->idx);
+    const float cz = curl2a(xi ? wy_[o + 1] : 0.f, wy, I->idx, yj ? wx_[o + px] : 0.f, wx, I->idy);
     A.lamH[3 * fs + o] += cx;
     A.lamH[4 * fs + o] += cy;
     A.lamH[5 * fs + o] += cz;
-    const float4 Ca = __ldg(ctab + 3 * (int)cls[o]);
-    A.lamE[o] = Ca.x * A.lamEn[o];
-    A.lamE[fs + o] = Ca.y * A.lamEn[fs + o];
-    A.lamE[2 * fs + o] = Ca.z * A.lamEn[2 * fs + o];
 }
 
 // E at the design-box edges after the current step, from buffer buf, into slot
@@ -567,8 +567,7 @@ __global__ void adj_record_design_kernel(LaunchSet L, AdjSet A, int slot, int bu
     A.dtape[(long long)slot * 3 * ne + e] = v;
 }
 
-// d J / d eps_edge += (cb/dt) lambda_E' (E^n - E^{n+1}) on the design-box edges
-template <typename ClsT>
+// d J / d eps_edge += (w/dt) (E^n - E^{n+1}) on the design-box edges
 __global__ void adj_design_kernel(LaunchSet L, AdjSet A, int slot)
 {
     const Inst *I = L.insts;
@@ -579,11 +578,10 @@ __global__ void adj_design_kernel(LaunchSet L, AdjSet A, int slot)
     const int i = A.di0 + r % ex, j = A.dj0 + (r / ex) % ey, k = A.dk0 + r / (ex * ey);
     if (i >= I->nx || j >= I->ny || k >= I->nz) return;
     const long long o = (long long)k * I->plane + (long long)j * I->px + i;
-    const float4 B = __ldg(I->ctab + 3 * (int)static_cast<const ClsT *>(I->cls)[o] + 1);
-    const float cb = comp == 0 ? B.x : (comp == 1 ? B.y : B.z);
-    if (cb == 0.f) return;
+    const float w = A.lamEn[comp * I->fstride + o];   // cb lambda_E'
+    if (w == 0.f) return;
     const float En = A.dtape[(long long)slot * 3 * ne + e], En1 = A.dtape[(long long)(slot + 1) * 3 * ne + e];
-    A.geps[e] += (double)cb / I->dt * (double)A.lamEn[comp * I->fstride + o] * ((double)En - (double)En1);
+    A.geps[e] += (double)w / I->dt * ((double)En - (double)En1);
 }
 
 }  // namespace
@@ -609,15 +607,16 @@ cudaError_t adj_reverse_step(const LaunchSet &L, const AdjSet &A, long long n, i
     if (L.ncomp) adj_mag_kernel<<<L.ncomp, kMagThreads, 0, s>>>(L, A, slot);
     const dim3 blk(32, 8), grid((A.nx + 31) / 32, (A.ny + 7) / 8, A.nz);
     const int ne3 = 3 * (A.dbx + 1) * (A.dby + 1) * (A.dbz + 1);
-    if (L.cls16) {
-        adj_curl_h_kernel<uint16_t><<<grid, blk, 0, s>>>(L, A);
-        if (A.geps) adj_design_kernel<uint16_t><<<(ne3 + 255) / 256, 256, 0, s>>>(L, A, slot);
-        adj_curl_e_kernel<uint16_t><<<grid, blk, 0, s>>>(L, A);
-    } else {
-        adj_curl_h_kernel<uint8_t><<<grid, blk, 0, s>>>(L, A);
-        if (A.geps) adj_design_kernel<uint8_t><<<(ne3 + 255) / 256, 256, 0, s>>>(L, A, slot);
-        adj_curl_e_kernel<uint8_t><<<grid, blk, 0, s>>>(L, A);
-    }
+    if (L.cls16) adj_curl_h_kernel<uint16_t><<<grid, blk, 0, s>>>(L, A);
+    else adj_curl_h_kernel<uint8_t><<<grid, blk, 0, s>>>(L, A);
+    if (A.geps) adj_design_kernel<<<(ne3 + 255) / 256, 256, 0, s>>>(L, A, slot);
+    adj_curl_e_kernel<<<grid, blk, 0, s>>>(L, A);
+    return cudaGetLastError();
+}
+
+// The magnetic faces' pending correction of the last reverse step.
+cudaError_t adj_finish(const LaunchSet &L, const AdjSet &A, cudaStream_t s)
+{
     if (L.ncomp) adj_fix_kernel<<<L.ncomp, 256, 0, s>>>(L, A);
     return cudaGetLastError();
 }

@@ -1513,6 +1513,7 @@ extern "C" int fdtd_llg_adjoint(fdtd_llg_t h, const double *dJ_dE, double *grad_
         for (long long n = nb - 1; n >= na && e == cudaSuccess; --n) e = adj_reverse_step(L, A, n, (int)(n - na), S->stream);
         S->host_step = nb;
     }
+    if (e == cudaSuccess) e = adj_finish(L, A, S->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
     std::vector<double> gh(std::max(1, nc), 0.0), ge(3 * nbe, 0.0);
     if (e == cudaSuccess) e = cudaMemcpy(gh.data(), A.gh0, gh.size() * sizeof(double), cudaMemcpyDeviceToHost);

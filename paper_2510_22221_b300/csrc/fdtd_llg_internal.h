@@ -222,6 +222,7 @@ long long adj_ws_floats(int bx, int by, int bz, int R);
 cudaError_t set_device_step(StepCtl *ctl, long long n, cudaStream_t s);
 cudaError_t adj_record_design(const LaunchSet &L, const AdjSet &A, int slot, int buf, cudaStream_t s);
 cudaError_t adj_reverse_step(const LaunchSet &L, const AdjSet &A, long long n, int slot, cudaStream_t s);
+cudaError_t adj_finish(const LaunchSet &L, const AdjSet &A, cudaStream_t s);
 
 // fdtd_llg_last_error(NULL) message for entry points without a handle.
 void set_last_error(const char *msg);
