@@ -158,27 +158,12 @@ __device__ __forceinline__ float curl2a(float a1, float b1, float i1, float a2, 
     return __fsub_rn(__fmul_rn(__fsub_rn(a1, b1), i1), __fmul_rn(__fsub_rn(a2, b2), i2));
 }
 
-// face f of a box: axis, indices, adjacent cells (-1 outside)
-__device__ __forceinline__ void fdecode(int f, int bx, int by, int bz, int &a, int &fi, int &fj, int &fk, int &vl, int &vr)
-{
-    const int nfx = (bx + 1) * by * bz, nfy = bx * (by + 1) * bz;
-    vl = vr = -1;
-    if (f < nfx) {
-        a = 0; fi = f % (bx + 1); fj = (f / (bx + 1)) % by; fk = f / ((bx + 1) * by);
-        if (fi > 0) vl = (fk * by + fj) * bx + fi - 1;
-        if (fi < bx) vr = (fk * by + fj) * bx + fi;
-    } else if (f < nfx + nfy) {
-        const int g = f - nfx;
-        a = 1; fi = g % bx; fj = (g / bx) % (by + 1); fk = g / (bx * (by + 1));
-        if (fj > 0) vl = (fk * by + fj - 1) * bx + fi;
-        if (fj < by) vr = (fk * by + fj) * bx + fi;
-    } else {
-        const int g = f - nfx - nfy;
-        a = 2; fi = g % bx; fj = (g / bx) % by; fk = g / (bx * by);
-        if (fk > 0) vl = ((fk - 1) * by + fj) * bx + fi;
-        if (fk < bz) vr = (fk * by + fj) * bx + fi;
-    }
-}
+// Magnetic neighbours of face f (cells on its low and high side, -1 where
+// outside the box or not magnetic), built once per kernel in shared memory.
+struct FaceNb {
+    int vl, vr;
+};
+__device__ __forceinline__ int face_axis(int f, int nfx, int nfy) { return f < nfx ? 0 : (f < nfx + nfy ? 1 : 2); }
 
 __device__ __forceinline__ float *hx_at(const Inst *I, float *F0, int i, int j, int k, float *wall)
 {
@@ -217,12 +202,13 @@ __device__ __forceinline__ RegionWS carve(float *w, int nf, int V, int R)
 
 // Cell v's inputs to iteration r of a half-push: hs (bias frame, with bias),
 // h (bias frame, from D^{r-1}; Dprev NULL for r = 1), m.
-__device__ void cell_inputs(const MagComp &C, const Inst *I, const float *R9, const uint8_t *smat, int V, const float *Hs,
-                            const float *Cc, const float *Dprev, const float *m, int v, float hs[3], float h[3],
-                            float mm[3], int nfx, int nfy)
+__device__ void cell_inputs(const MagComp &C, const BoxDiv &BD, const Inst *I, const float *R9, const uint8_t *smat, int V,
+                            const float *Hs, const float *Cc, const float *Dprev, const float *m, int v, float hs[3],
+                            float h[3], float mm[3], int nfx, int nfy)
 {
     const int bx = C.bx, by = C.by, bxy = C.bx * C.by;
-    const int li = v % bx, lj = (v / bx) % by, lk = v / bxy;
+    int li, lj, lk;
+    cell_decode(v, BD, li, lj, lk);
     const int fx0 = (lk * by + lj) * (bx + 1) + li, fy0 = nfx + (lk * (by + 1) + lj) * bx + li,
               fz0 = nfx + nfy + (lk * by + lj) * bx + li;
     const int f0[3] = {fx0, fy0, fz0}, f1[3] = {fx0 + 1, fy0 + bx, fz0 + bxy};
@@ -252,9 +238,9 @@ __device__ void cell_inputs(const MagComp &C, const Inst *I, const float *R9, co
 // Forward half-push of a region (R Jacobi iterates) from faces Hs and m: the
 // iterates D^r (global axes, r = 1..R) into D, the last increment (bias
 // frame) into DL, the result faces into Hout (owned faces) and m + DL into mout.
-__device__ void fwd_half(const MagComp &C, const Inst *I, const float *R9, const uint8_t *smat, int V, int nf, int R,
-                         const float *Hs, const float *Cc, const float *m, float *D, float *DL, float *Hout, float *mout,
-                         int nfx, int nfy)
+__device__ void fwd_half(const MagComp &C, const BoxDiv &BD, const FaceNb *fnb, const Inst *I, const float *R9,
+                         const uint8_t *smat, int V, int nf, int R, const float *Hs, const float *Cc, const float *m, float *D,
+                         float *DL, float *Hout, float *mout, int nfx, int nfy)
 {
     const int tid = threadIdx.x, nth = blockDim.x;
     for (int r = 1; r <= R; ++r) {
@@ -267,7 +253,7 @@ __device__ void fwd_half(const MagComp &C, const Inst *I, const float *R9, const
                 continue;
             }
             float hs[3], h[3], mm[3], dl[3], dg[3];
-            cell_inputs(C, I, R9, smat, V, Hs, Cc, Dp, m, v, hs, h, mm, nfx, nfy);
+            cell_inputs(C, BD, I, R9, smat, V, Hs, Cc, Dp, m, v, hs, h, mm, nfx, nfy);
             llg_inc(mm, hs, h, I->mm[mt], dl);
             from_fr(R9, dl, dg);
             for (int a = 0; a < 3; ++a) Dr[a * V + v] = dg[a];
@@ -278,10 +264,11 @@ __device__ void fwd_half(const MagComp &C, const Inst *I, const float *R9, const
     }
     const float *DR = D + 3 * V * (R - 1);
     for (int f = tid; f < nf; f += nth) {
-        int a, fi, fj, fk, vl, vr;
-        fdecode(f, C.bx, C.by, C.bz, a, fi, fj, fk, vl, vr);
-        const bool inl = vl >= 0 && smat[vl] != 0xFF, inr = vr >= 0 && smat[vr] != 0xFF;
-        Hout[f] = (inl || inr) ? (Hs[f] - Cc[f]) - 0.5f * ((inl ? DR[a * V + vl] : 0.f) + (inr ? DR[a * V + vr] : 0.f)) : 0.f;
+        const FaceNb q = fnb[f];
+        const int a = face_axis(f, nfx, nfy);
+        const bool inl = q.vl >= 0, inr = q.vr >= 0;
+        Hout[f] = (inl || inr) ? (Hs[f] - Cc[f]) - 0.5f * ((inl ? DR[a * V + q.vl] : 0.f) + (inr ? DR[a * V + q.vr] : 0.f))
+                               : 0.f;
     }
     for (int v = tid; v < 3 * V; v += nth) mout[v] = m[v] + (smat[v % V] != 0xFF ? DL[v] : 0.f);
     __syncthreads();
@@ -290,9 +277,10 @@ __device__ void fwd_half(const MagComp &C, const Inst *I, const float *R9, const
 // Reverse of one half-push.  In: lamHout (faces), lamM (adjoint of the output
 // m, bias frame; overwritten with the adjoint of the input m).  Out: lamHin,
 // lamC (faces); *gh0 accumulates d J / d |H_bias| of this thread's cells.
-__device__ void rev_half(const MagComp &C, const Inst *I, const float *R9, const uint8_t *smat, int V, int nf, int R,
-                         const float *Hs, const float *Cc, const float *m, const float *D, RegionWS &W, const float *lamHout,
-                         float *lamHin, float *lamC, double *gh0, int nfx, int nfy)
+__device__ void rev_half(const MagComp &C, const BoxDiv &BD, const FaceNb *fnb, const Inst *I, const float *R9,
+                         const uint8_t *smat, int V, int nf, int R, const float *Hs, const float *Cc, const float *m,
+                         const float *D, RegionWS &W, const float *lamHout, float *lamHin, float *lamC, double *gh0, int nfx,
+                         int nfy)
 {
     const int tid = threadIdx.x, nth = blockDim.x;
     const int bx = C.bx, by = C.by, bxy = bx * by;
@@ -307,7 +295,8 @@ __device__ void rev_half(const MagComp &C, const Inst *I, const float *R9, const
             for (int a = 0; a < 3; ++a) W.lamDl[a * V + v] = 0.f;
             continue;
         }
-        const int li = v % bx, lj = (v / bx) % by, lk = v / bxy;
+        int li, lj, lk;
+        cell_decode(v, BD, li, lj, lk);
         const int fx0 = (lk * by + lj) * (bx + 1) + li, fy0 = nfx + (lk * (by + 1) + lj) * bx + li,
                   fz0 = nfx + nfy + (lk * by + lj) * bx + li;
         const float lD[3] = {-0.5f * (lamHout[fx0] + lamHout[fx0 + 1]), -0.5f * (lamHout[fy0] + lamHout[fy0 + bx]),
@@ -327,7 +316,7 @@ __device__ void rev_half(const MagComp &C, const Inst *I, const float *R9, const
                 continue;
             }
             float hs[3], h[3], mm[3];
-            cell_inputs(C, I, R9, smat, V, Hs, Cc, Dp, m, v, hs, h, mm, nfx, nfy);
+            cell_inputs(C, BD, I, R9, smat, V, Hs, Cc, Dp, m, v, hs, h, mm, nfx, nfy);
             const float ld[3] = {W.lamDl[v], W.lamDl[V + v], W.lamDl[2 * V + v]};
             // J^T lambda in one reverse pass: gin = (m, hs, h) adjoints
             float gin[9];
@@ -352,7 +341,8 @@ __device__ void rev_half(const MagComp &C, const Inst *I, const float *R9, const
                     W.lamDl[v] = W.lamDl[V + v] = W.lamDl[2 * V + v] = 0.f;
                     continue;
                 }
-                const int li = v % bx, lj = (v / bx) % by, lk = v / bxy;
+                int li, lj, lk;
+                cell_decode(v, BD, li, lj, lk);
                 const int st[3] = {1, bx, bxy};
                 const bool lo[3] = {li > 0, lj > 0, lk > 0}, hi[3] = {li < bx - 1, lj < by - 1, lk < C.bz - 1};
                 float lD[3];
@@ -379,11 +369,11 @@ __device__ void rev_half(const MagComp &C, const Inst *I, const float *R9, const
     }
     __syncthreads();
     for (int f = tid; f < nf; f += nth) {
-        int a, fi, fj, fk, vl, vr;
-        fdecode(f, bx, by, C.bz, a, fi, fj, fk, vl, vr);
+        const FaceNb q = fnb[f];
+        const int a = face_axis(f, nfx, nfy);
         float sA = 0.f, sH = 0.f;
-        if (vl >= 0 && smat[vl] != 0xFF) { sA += 0.5f * W.lamA[a * V + vl]; sH += 0.5f * W.lamHsm[a * V + vl]; }
-        if (vr >= 0 && smat[vr] != 0xFF) { sA += 0.5f * W.lamA[a * V + vr]; sH += 0.5f * W.lamHsm[a * V + vr]; }
+        if (q.vl >= 0) { sA += 0.5f * W.lamA[a * V + q.vl]; sH += 0.5f * W.lamHsm[a * V + q.vl]; }
+        if (q.vr >= 0) { sA += 0.5f * W.lamA[a * V + q.vr]; sH += 0.5f * W.lamHsm[a * V + q.vr]; }
         lamHin[f] += sA + sH;
         lamC[f] -= sA;
     }
@@ -392,6 +382,7 @@ __device__ void rev_half(const MagComp &C, const Inst *I, const float *R9, const
 
 __global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSet A, int slot)
 {
+    extern __shared__ FaceNb fnb[];   // nf entries
     __shared__ double sred[kMagThreads / 32];
     const MagComp C = L.comps[blockIdx.x];
     const Inst *I = L.insts + C.inst;
@@ -407,12 +398,14 @@ __global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSe
     for (int q = 0; q < 9; ++q) R9[q] = I->R[q];
     const float *T = C.tape + (long long)slot * C.tstride;          // m^{n+1/2}, H^{n+1/2} faces, E^{n+1} edges
     const float *Ex = T + 3 * V + nf, *Ey = Ex + ne, *Ez = Ey + ne;
+    const BoxDiv BD(bx, by);
     for (int v = tid; v < V; v += nth) smat[v] = C.mat[v];
     for (int v = tid; v < 3 * V; v += nth) W.m1[v] = T[v];
     const float ch = I->ch;
     for (int f = tid; f < nf; f += nth) {
         int a, fi, fj, fk, vl, vr;
-        fdecode(f, bx, by, bz, a, fi, fj, fk, vl, vr);
+        face_decode(f, BD, bx, by, bz, a, fi, fj, fk, vl, vr);
+        fnb[f] = {vl >= 0 && C.mat[vl] != 0xFF ? vl : -1, vr >= 0 && C.mat[vr] != 0xFF ? vr : -1};
         W.Hs1[f] = T[3 * V + f];
         const int e0 = fk * exy + fj * ex + fi;
         float cu = 0.f;
@@ -431,26 +424,26 @@ __global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSe
     }
     __syncthreads();
     // recompute both half-pushes of the step
-    fwd_half(C, I, R9, smat, V, nf, R, W.Hs1, W.C, W.m1, W.D1, W.DL1, W.Hs2, W.m2, nfx, nfy);
-    fwd_half(C, I, R9, smat, V, nf, R, W.Hs2, W.C, W.m2, W.D2, W.DL2, W.fix /*scratch*/, W.lamDl /*scratch*/, nfx, nfy);
+    fwd_half(C, BD, fnb, I, R9, smat, V, nf, R, W.Hs1, W.C, W.m1, W.D1, W.DL1, W.Hs2, W.m2, nfx, nfy);
+    fwd_half(C, BD, fnb, I, R9, smat, V, nf, R, W.Hs2, W.C, W.m2, W.D2, W.DL2, W.fix /*scratch*/, W.lamDl /*scratch*/, nfx,
+             nfy);
     // reverse: second half-push, then the first
     double g = 0.0;
-    rev_half(C, I, R9, smat, V, nf, R, W.Hs2, W.C, W.m2, W.D2, W, W.lamHout, W.lamHin, W.lamC, &g, nfx, nfy);
+    rev_half(C, BD, fnb, I, R9, smat, V, nf, R, W.Hs2, W.C, W.m2, W.D2, W, W.lamHout, W.lamHin, W.lamC, &g, nfx, nfy);
     for (int f = tid; f < nf; f += nth) {
         W.lamHout[f] = W.lamHin[f];      // adjoint of H^{n+1}
         W.fix[f] = W.lamC[f];            // curl adjoint of the second half-push
     }
     __syncthreads();
-    rev_half(C, I, R9, smat, V, nf, R, W.Hs1, W.C, W.m1, W.D1, W, W.lamHout, W.lamHin, W.lamC, &g, nfx, nfy);
+    rev_half(C, BD, fnb, I, R9, smat, V, nf, R, W.Hs1, W.C, W.m1, W.D1, W, W.lamHout, W.lamHin, W.lamC, &g, nfx, nfy);
     // write back: for a magnetic face the curl sweep must see q/2 with
     // q = -(lamC1 + lamC2) (a plain face contributes 2 lambda_H); afterwards
     // the face takes lamHin, restored from fix by the next reverse step's
     // magnet kernel (or adj_fix_kernel after the last)
     for (int f = tid; f < nf; f += nth) {
+        if (fnb[f].vl < 0 && fnb[f].vr < 0) continue;
         int a, fi, fj, fk, vl, vr;
-        fdecode(f, bx, by, bz, a, fi, fj, fk, vl, vr);
-        const bool own = (vl >= 0 && smat[vl] != 0xFF) || (vr >= 0 && smat[vr] != 0xFF);
-        if (!own) continue;
+        face_decode(f, BD, bx, by, bz, a, fi, fj, fk, vl, vr);
         const int i = C.x0 + fi, j = C.y0 + fj, k = C.z0 + fk;
         const float q = -(W.lamC[f] + W.fix[f]);
         const bool wall = (a == 0 && i == I->nx) || (a == 1 && j == I->ny) || (a == 2 && k == I->nz);
@@ -483,9 +476,10 @@ __global__ void adj_fix_kernel(LaunchSet L, AdjSet A)
     const int nfx = (bx + 1) * by * bz, nfy = bx * (by + 1) * bz, nf = nfx + nfy + bx * by * (bz + 1);
     float *wsb = A.ws + A.ws_off[blockIdx.x];
     RegionWS W = carve(wsb + (V + 3) / 4, nf, V, A.R);
+    const BoxDiv BD(bx, by);
     for (int f = threadIdx.x; f < nf; f += blockDim.x) {
         int a, fi, fj, fk, vl, vr;
-        fdecode(f, bx, by, bz, a, fi, fj, fk, vl, vr);
+        face_decode(f, BD, bx, by, bz, a, fi, fj, fk, vl, vr);
         const bool own = (vl >= 0 && C.mat[vl] != 0xFF) || (vr >= 0 && C.mat[vr] != 0xFF);
         if (!own) continue;
         const int i = C.x0 + fi, j = C.y0 + fj, k = C.z0 + fk;
@@ -604,7 +598,11 @@ cudaError_t adj_record_design(const LaunchSet &L, const AdjSet &A, int slot, int
 cudaError_t adj_reverse_step(const LaunchSet &L, const AdjSet &A, long long n, int slot, cudaStream_t s)
 {
     if (A.nprobe > 0) adj_seed_kernel<<<1, 3 * A.nprobe, 0, s>>>(L, A, n);
-    if (L.ncomp) adj_mag_kernel<<<L.ncomp, kMagThreads, 0, s>>>(L, A, slot);
+    if (L.ncomp) {
+        const cudaError_t e = cudaFuncSetAttribute(adj_mag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, A.fnb_bytes);
+        if (e != cudaSuccess) return e;
+        adj_mag_kernel<<<L.ncomp, kMagThreads, A.fnb_bytes, s>>>(L, A, slot);
+    }
     const dim3 blk(32, 8), grid((A.nx + 31) / 32, (A.ny + 7) / 8, A.nz);
     const int ne3 = 3 * (A.dbx + 1) * (A.dby + 1) * (A.dbz + 1);
     if (L.cls16) adj_curl_h_kernel<uint16_t><<<grid, blk, 0, s>>>(L, A);

@@ -1464,6 +1464,8 @@ extern "C" int fdtd_llg_adjoint(fdtd_llg_t h, const double *dJ_dE, double *grad_
     A.nprobe = np;
     A.nx = I.nx; A.ny = I.ny; A.nz = I.nz;
     A.R = R;
+    for (int c = 0; c < nc; ++c)
+        A.fnb_bytes = std::max(A.fnb_bytes, (int)(8 * mag_faces(I.comps[c].bx, I.comps[c].by, I.comps[c].bz)));
     long long nbe = 0;
     if (I.has_design) {
         A.di0 = I.dbox[0]; A.dj0 = I.dbox[1]; A.dk0 = I.dbox[2];

@@ -239,56 +239,6 @@ __device__ __forceinline__ void from_frame(const float *R, float lx, float ly, f
     gz = R[2] * lx + R[5] * ly + R[8] * lz;
 }
 
-// Division by a box dimension d by multiplication: with m = ceil(2^32 / d),
-// umulhi(n, m) = floor(n / d) exactly whenever n d < 2^32 (the error term
-// n (m d - 2^32) / 2^32 stays below 1).  Box indices here are below 2^16 and
-// dimensions at most 4097.
-struct UDiv {
-    unsigned d, m;
-    __device__ explicit UDiv(unsigned dd) : d(dd), m(dd > 1 ? (unsigned)(0xFFFFFFFFull / dd + 1ull) : 0u) {}
-    __device__ __forceinline__ unsigned div(unsigned n) const { return d > 1 ? __umulhi(n, m) : n; }
-};
-struct BoxDiv {
-    UDiv bx, by, bx1, by1;
-    __device__ BoxDiv(int x, int y) : bx(x), by(y), bx1(x + 1), by1(y + 1) {}
-};
-// (li, lj, lk) of cell v of a bx x by x bz box
-__device__ __forceinline__ void cell_decode(int v, const BoxDiv &D, int &li, int &lj, int &lk)
-{
-    const unsigned q1 = D.bx.div(v), q2 = D.by.div(q1);
-    li = v - (int)(q1 * D.bx.d);
-    lj = (int)(q1 - q2 * D.by.d);
-    lk = (int)q2;
-}
-
-// Face f of a region's box: axis a and box-local indices; the cells on its low
-// (vl) and high (vr) side, -1 outside the box.  Faces are numbered x faces
-// ((bx+1) by bz), then y faces (bx (by+1) bz), then z faces (bx by (bz+1)).
-__device__ __forceinline__ void face_decode(int f, const BoxDiv &D, int bx, int by, int bz, int &a, int &fi, int &fj,
-                                            int &fk, int &vl, int &vr)
-{
-    const int nfx = (bx + 1) * by * bz, nfy = bx * (by + 1) * bz;
-    vl = vr = -1;
-    if (f < nfx) {
-        const unsigned q1 = D.bx1.div(f), q2 = D.by.div(q1);
-        a = 0; fi = f - (int)(q1 * (bx + 1)); fj = (int)(q1 - q2 * by); fk = (int)q2;
-        if (fi > 0) vl = (fk * by + fj) * bx + fi - 1;
-        if (fi < bx) vr = (fk * by + fj) * bx + fi;
-    } else if (f < nfx + nfy) {
-        const int g = f - nfx;
-        const unsigned q1 = D.bx.div(g), q2 = D.by1.div(q1);
-        a = 1; fi = g - (int)(q1 * bx); fj = (int)(q1 - q2 * (by + 1)); fk = (int)q2;
-        if (fj > 0) vl = (fk * by + fj - 1) * bx + fi;
-        if (fj < by) vr = (fk * by + fj) * bx + fi;
-    } else {
-        const int g = f - nfx - nfy;
-        const unsigned q1 = D.bx.div(g), q2 = D.by.div(q1);
-        a = 2; fi = g - (int)(q1 * bx); fj = (int)(q1 - q2 * by); fk = (int)q2;
-        if (fk > 0) vl = ((fk - 1) * by + fj) * bx + fi;
-        if (fk < bz) vr = (fk * by + fj) * bx + fi;
-    }
-}
-
 // Cascaded compensated accumulation of FP32 terms (Ogita, Rump and Oishi's
 // Sum2): TwoSum gives the exact rounding error of every addition, which is
 // summed separately, so s + c carries the running sum as if in twice the
