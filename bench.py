@@ -165,7 +165,7 @@ def adjoint_ratio(torch, pkg, W, steps=4000, n0=3000):
     seed = np.zeros_like(rows)
     seed[n0:] = 2 * rows[n0:]
     t2 = time.perf_counter()
-    ge, gh = sim.adjoint(seed, design_shape=w.eps_design.shape)
+    ge, gh = sim.adjoint_step(seed, design_shape=w.eps_design.shape)
     t3 = time.perf_counter()
     sim.destroy()
     # directional central difference of the FP32 forward run along the gradient

@@ -253,8 +253,9 @@ int fdtd_llg_autotune(fdtd_llg_t h, int32_t trial_steps, int32_t *planes);
  * be a fixed map: llg_fixed_iter >= 2 at creation.  Errors: FDTD_E_INVAL,
  * FDTD_E_STATE (not at step 0), FDTD_E_NOSYS (batch), FDTD_E_OOM.
  *
- * fdtd_llg_adjoint: the exact gradient of the discrete forward map of that
- * run for an objective J whose derivative with respect to the recorded probe
+ * fdtd_llg_adjoint_step: the reverse-time counterpart of fdtd_llg_step over
+ * the whole recorded run, i.e. the exact gradient of the discrete forward map
+ * of that run for an objective J whose derivative with respect to the recorded probe
  * E samples is dJ_dE[n][p][c] (host, FP64, nsteps x nprobes x 3: step n's
  * row, probe p, Ex/Ey/Ez of its cell).  Reverse sweep segment by segment
  * from the last checkpoint: each segment's forward steps are recomputed
@@ -268,7 +269,7 @@ int fdtd_llg_autotune(fdtd_llg_t h, int32_t trial_steps, int32_t *planes);
  * calling).  Errors: FDTD_E_STATE (no checkpointed run; grad_eps without a
  * design box), FDTD_E_INVAL, FDTD_E_OOM, FDTD_E_UNSTABLE, FDTD_E_CUDA. */
 int fdtd_llg_run_checkpointed(fdtd_llg_t h, int64_t nsteps, int32_t interval);
-int fdtd_llg_adjoint(fdtd_llg_t h, const double *dJ_dE, double *grad_eps, double *grad_h0);
+int fdtd_llg_adjoint_step(fdtd_llg_t h, const double *dJ_dE, double *grad_eps, double *grad_h0);
 
 /* Spectra and mode fits of probe time series (the E_x spectra behind the
  * anti-crossing maps of section "Results", the ESPRIT extraction of the

@@ -44,7 +44,7 @@ class ProbeEnergy(torch.autograd.Function):
     def backward(ctx, gJ):
         seed = np.zeros_like(ctx.rows)
         seed[ctx.n0:] = 2.0 * ctx.rows[ctx.n0:] * float(gJ)
-        ge, gh = ctx.sim.adjoint(seed, design_shape=ctx.shape)
+        ge, gh = ctx.sim.adjoint_step(seed, design_shape=ctx.shape)
         ctx.sim.destroy()
         ctx.sim = None
         return torch.from_numpy(ge), torch.tensor(gh, dtype=torch.float64), None, None, None, None, None

@@ -1413,7 +1413,7 @@ extern "C" int fdtd_llg_run_checkpointed(fdtd_llg_t h, int64_t nsteps, int32_t i
     return FDTD_OK;
 }
 
-extern "C" int fdtd_llg_adjoint(fdtd_llg_t h, const double *dJ_dE, double *grad_eps, double *grad_h0)
+extern "C" int fdtd_llg_adjoint_step(fdtd_llg_t h, const double *dJ_dE, double *grad_eps, double *grad_h0)
 {
     if (!h || !h->sim || !h->owns) return fail(h, FDTD_E_INVAL, "adjoint needs the handle, not a member");
     Sim *S = h->sim;

@@ -257,13 +257,13 @@ class FdtdLlg:
         check(_abi.load().fdtd_llg_run_checkpointed(self._h, int(nsteps), int(interval)), self._h)
         self._adj_steps = int(nsteps)
 
-    def adjoint(self, dJ_dE, design_shape=None):
+    def adjoint_step(self, dJ_dE, design_shape=None):
         """Gradients of J given dJ/dE at the probes (nsteps x nprobes x 3):
         (dJ/d eps_r of the design cells or None, dJ/d |H_bias| per A/m)."""
         seed = np.ascontiguousarray(dJ_dE, dtype=np.float64)
         ge = np.zeros(design_shape) if design_shape is not None else None
         gh = C.c_double(0.0)
-        check(_abi.load().fdtd_llg_adjoint(self._h, seed.ctypes.data_as(C.POINTER(C.c_double)),
+        check(_abi.load().fdtd_llg_adjoint_step(self._h, seed.ctypes.data_as(C.POINTER(C.c_double)),
                                            ge.ctypes.data_as(C.POINTER(C.c_double)) if ge is not None else None,
                                            C.byref(gh)), self._h)
         return ge, gh.value

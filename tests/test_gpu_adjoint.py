@@ -35,7 +35,7 @@ def _gpu(w, N, n0, interval=0):
     rows = np.stack([sim.probe(p)[:, :3] for p in range(len(w.probes))], axis=1)
     seed = np.zeros_like(rows)
     seed[n0:] = 2 * rows[n0:]
-    ge, gh = sim.adjoint(seed, design_shape=w.eps_design.shape)
+    ge, gh = sim.adjoint_step(seed, design_shape=w.eps_design.shape)
     J = float((rows[n0:] ** 2).sum())
     sim.destroy()
     return J, ge, gh
@@ -112,7 +112,7 @@ def test_adjoint_argument_errors():
     w = CASES["design16"][0]()
     sim = pkg.from_workload(w, probe_capacity=10, llg_fixed_iter=3)
     with pytest.raises(pkg.LLGError) as ei:
-        sim.adjoint(np.zeros((10, 1, 3)), design_shape=w.eps_design.shape)
+        sim.adjoint_step(np.zeros((10, 1, 3)), design_shape=w.eps_design.shape)
     assert ei.value.code == -6
     sim.destroy()
     sim = pkg.from_workload(w, probe_capacity=10)           # magnets without a fixed LLG map
