@@ -7,9 +7,10 @@
 // (P: half the change of each adjacent cell's M on a face).  Its transpose,
 // with lambda the adjoint of the step's outputs:
 //   magnetic regions (adj_mag_kernel): both half-pushes reversed through the
-//     fixed number of Jacobi iterates of the trapezoidal LLG solve (the
-//     transposed 3 x 9 Jacobian of one cell's increment applied in one
-//     reverse-mode pass, llg_inc_vjp), giving
+//     fixed number of Jacobi iterates of the trapezoidal LLG solve, which the
+//     forward magnet kernel recorded on the tape during the segment's
+//     recomputation (the transposed 3 x 9 Jacobian of one cell's increment
+//     applied in one reverse-mode pass, llg_inc_vjp), giving
 //     the adjoint of the faces' H and of M at the step's start, of the curl
 //     terms, and d J / d |H_bias|;
 //   adj_curl_h_kernel:  lambda_E' = lambda_E - (dt/mu0) C_H lambda_H (for a
@@ -28,35 +29,10 @@ namespace fl {
 
 namespace {
 
-// One cell's LLG increment in the bias frame (the arithmetic of mag_kernel):
-// m deviation from Ms e3, hs = H_eff at the start of the half-push, h = H_eff
-// of the previous iterate (both with the bias on e3); returns dl = M^{r} - M^n.
-__device__ __forceinline__ void llg_inc(const float m[3], const float hs[3], const float h[3], const MagMat &mm,
-                                        float dl[3])
-{
-    const float Mz = m[2] + mm.Ms;
-    const float dam = mm.alpha * mm.inv_Ms, k = mm.kappa;
-    const float ax = -(k * h[0] + dam * m[0]);
-    const float ay = -(k * h[1] + dam * m[1]);
-    const float az = -(k * h[2] + dam * m[2] + mm.alpha);
-    const float rx = (-k) * (m[1] * hs[2] - Mz * hs[1]) - k * (m[1] * h[2] - Mz * h[1]);
-    const float ry = (-k) * (Mz * hs[0] - m[0] * hs[2]) - k * (Mz * h[0] - m[0] * h[2]);
-    const float rz = (-k) * (m[0] * hs[1] - m[1] * hs[0]) - k * (m[0] * h[1] - m[1] * h[0]);
-    const float ar = ax * rx + ay * ry + az * rz;
-    const float inv1 = 1.f / (1.f + (ax * ax + ay * ay + az * az));
-    const float dx = (rx + ar * ax - (ay * rz - az * ry)) * inv1;
-    const float dy = (ry + ar * ay - (az * rx - ax * rz)) * inv1;
-    const float dz = (rz + ar * az - (ax * ry - ay * rx)) * inv1;
-    const float nM2 = m[0] * m[0] + m[1] * m[1] + Mz * Mz;
-    const float md2 = 2.f * (m[0] * dx + m[1] * dy + Mz * dz) + (dx * dx + dy * dy + dz * dz);
-    const float nM = sqrtf(nM2), nMt = sqrtf(nM2 + md2);
-    const float s1 = -md2 / (nMt * (nM + nMt));
-    dl[0] = dx + s1 * (m[0] + dx);
-    dl[1] = dy + s1 * (m[1] + dy);
-    dl[2] = dz + s1 * (Mz + dz);
-}
-
-// Reverse mode of llg_inc: given ld, the adjoint of dl, returns the
+// Reverse mode of one cell's LLG increment dl = M^{r} - M^n in the bias frame
+// (the arithmetic of mag_kernel; m deviation from Ms e3, hs = H_eff at the
+// start of the half-push, h = H_eff of the previous iterate, both with the
+// bias on e3): given ld, the adjoint of dl, returns the
 // adjoints gm, ghs, gh of m, hs and h (J^T ld for the 3 x 9 Jacobian).  With
 // M = m + Ms e3 and S = hs + h the increment is
 //   a = -(kappa h + (alpha/Ms) M),  r = -kappa M x S,
@@ -180,23 +156,20 @@ __device__ __forceinline__ float *hz_at(const Inst *I, float *F0, int i, int j, 
                         : F0 + 5 * I->fstride + (long long)k * I->plane + (long long)j * I->px + i;
 }
 
-// Workspace of one region (floats), nf faces, V cells, R iterates:
-//   Hs1, Hs2, C, lamHout, lamHin, lamC, fix (7 nf);
-//   m1, m2, DL1, DL2, lamM, lamDl, lamA, lamHsm, lamHg (9 x 3V), D1[R], D2[R] (2R x 3V).
+// Workspace of one region (floats), nf faces, V cells:
+//   C, lamHout, lamHin, lamC, fix (5 nf);  lamM, lamDl, lamA, lamHsm, lamHg (5 x 3V).
+// fix carries the magnetic faces' pending correction from one reverse step to
+// the next; everything the forward step computed comes from the tape.
 struct RegionWS {
-    float *Hs1, *Hs2, *C, *lamHout, *lamHin, *lamC, *fix;
-    float *m1, *m2, *DL1, *DL2, *lamM, *lamDl, *lamA, *lamHsm, *lamHg, *D1, *D2;
+    float *C, *lamHout, *lamHin, *lamC, *fix;
+    float *lamM, *lamDl, *lamA, *lamHsm, *lamHg;
 };
-__device__ __forceinline__ RegionWS carve(float *w, int nf, int V, int R)
+__device__ __forceinline__ RegionWS carve(float *w, int nf, int V)
 {
     RegionWS r;
-    r.Hs1 = w; r.Hs2 = r.Hs1 + nf; r.C = r.Hs2 + nf; r.lamHout = r.C + nf; r.lamHin = r.lamHout + nf;
-    r.lamC = r.lamHin + nf; r.fix = r.lamC + nf;
+    r.C = w; r.lamHout = r.C + nf; r.lamHin = r.lamHout + nf; r.lamC = r.lamHin + nf; r.fix = r.lamC + nf;
     float *p = r.fix + nf;
-    r.m1 = p; r.m2 = p + 3 * V; r.DL1 = p + 6 * V; r.DL2 = p + 9 * V; r.lamM = p + 12 * V; r.lamDl = p + 15 * V;
-    r.lamA = p + 18 * V; r.lamHsm = p + 21 * V; r.lamHg = p + 24 * V;
-    r.D1 = p + 27 * V;
-    r.D2 = r.D1 + 3 * V * R;
+    r.lamM = p; r.lamDl = p + 3 * V; r.lamA = p + 6 * V; r.lamHsm = p + 9 * V; r.lamHg = p + 12 * V;
     return r;
 }
 
@@ -233,45 +206,6 @@ __device__ void cell_inputs(const MagComp &C, const BoxDiv &BD, const Inst *I, c
     mm[0] = m[v];
     mm[1] = m[V + v];
     mm[2] = m[2 * V + v];
-}
-
-// Forward half-push of a region (R Jacobi iterates) from faces Hs and m: the
-// iterates D^r (global axes, r = 1..R) into D, the last increment (bias
-// frame) into DL, the result faces into Hout (owned faces) and m + DL into mout.
-__device__ void fwd_half(const MagComp &C, const BoxDiv &BD, const FaceNb *fnb, const Inst *I, const float *R9,
-                         const uint8_t *smat, int V, int nf, int R, const float *Hs, const float *Cc, const float *m, float *D,
-                         float *DL, float *Hout, float *mout, int nfx, int nfy)
-{
-    const int tid = threadIdx.x, nth = blockDim.x;
-    for (int r = 1; r <= R; ++r) {
-        const float *Dp = r >= 2 ? D + 3 * V * (r - 2) : nullptr;
-        float *Dr = D + 3 * V * (r - 1);
-        for (int v = tid; v < V; v += nth) {
-            const int mt = smat[v];
-            if (mt == 0xFF) {
-                Dr[v] = Dr[V + v] = Dr[2 * V + v] = 0.f;
-                continue;
-            }
-            float hs[3], h[3], mm[3], dl[3], dg[3];
-            cell_inputs(C, BD, I, R9, smat, V, Hs, Cc, Dp, m, v, hs, h, mm, nfx, nfy);
-            llg_inc(mm, hs, h, I->mm[mt], dl);
-            from_fr(R9, dl, dg);
-            for (int a = 0; a < 3; ++a) Dr[a * V + v] = dg[a];
-            if (r == R)
-                for (int a = 0; a < 3; ++a) DL[a * V + v] = dl[a];
-        }
-        __syncthreads();
-    }
-    const float *DR = D + 3 * V * (R - 1);
-    for (int f = tid; f < nf; f += nth) {
-        const FaceNb q = fnb[f];
-        const int a = face_axis(f, nfx, nfy);
-        const bool inl = q.vl >= 0, inr = q.vr >= 0;
-        Hout[f] = (inl || inr) ? (Hs[f] - Cc[f]) - 0.5f * ((inl ? DR[a * V + q.vl] : 0.f) + (inr ? DR[a * V + q.vr] : 0.f))
-                               : 0.f;
-    }
-    for (int v = tid; v < 3 * V; v += nth) mout[v] = m[v] + (smat[v % V] != 0xFF ? DL[v] : 0.f);
-    __syncthreads();
 }
 
 // Reverse of one half-push.  In: lamHout (faces), lamM (adjoint of the output
@@ -393,20 +327,24 @@ __global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSe
     const int R = A.R;
     float *wsb = A.ws + A.ws_off[blockIdx.x];
     uint8_t *smat = reinterpret_cast<uint8_t *>(wsb);              // V bytes, rounded up to floats
-    RegionWS W = carve(wsb + (V + 3) / 4, nf, V, R);
+    RegionWS W = carve(wsb + (V + 3) / 4, nf, V);
     float R9[9];
     for (int q = 0; q < 9; ++q) R9[q] = I->R[q];
-    const float *T = C.tape + (long long)slot * C.tstride;          // m^{n+1/2}, H^{n+1/2} faces, E^{n+1} edges
+    // the forward step's records (mag_tape_floats): m and faces at its start,
+    // E^{n+1} at the box edges, the Jacobi iterates of both half-pushes, faces
+    // and m after the first half-push
+    const float *T = C.tape + (long long)slot * C.tstride;
+    const float *m1 = T, *Hs1 = T + 3 * V;
     const float *Ex = T + 3 * V + nf, *Ey = Ex + ne, *Ez = Ey + ne;
+    const float *D1 = T + 3 * V + nf + 3 * ne, *D2 = D1 + 3LL * R * V;
+    const float *Hs2 = D2 + 3LL * R * V, *m2 = Hs2 + nf;
     const BoxDiv BD(bx, by);
     for (int v = tid; v < V; v += nth) smat[v] = C.mat[v];
-    for (int v = tid; v < 3 * V; v += nth) W.m1[v] = T[v];
     const float ch = I->ch;
     for (int f = tid; f < nf; f += nth) {
         int a, fi, fj, fk, vl, vr;
         face_decode(f, BD, bx, by, bz, a, fi, fj, fk, vl, vr);
         fnb[f] = {vl >= 0 && C.mat[vl] != 0xFF ? vl : -1, vr >= 0 && C.mat[vr] != 0xFF ? vr : -1};
-        W.Hs1[f] = T[3 * V + f];
         const int e0 = fk * exy + fj * ex + fi;
         float cu = 0.f;
         if (a == 0) cu = curl2a(Ez[e0 + ex], Ez[e0], I->idy, Ey[e0 + exy], Ey[e0], I->idz);
@@ -423,19 +361,15 @@ __global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSe
                            : 0.f;
     }
     __syncthreads();
-    // recompute both half-pushes of the step
-    fwd_half(C, BD, fnb, I, R9, smat, V, nf, R, W.Hs1, W.C, W.m1, W.D1, W.DL1, W.Hs2, W.m2, nfx, nfy);
-    fwd_half(C, BD, fnb, I, R9, smat, V, nf, R, W.Hs2, W.C, W.m2, W.D2, W.DL2, W.fix /*scratch*/, W.lamDl /*scratch*/, nfx,
-             nfy);
     // reverse: second half-push, then the first
     double g = 0.0;
-    rev_half(C, BD, fnb, I, R9, smat, V, nf, R, W.Hs2, W.C, W.m2, W.D2, W, W.lamHout, W.lamHin, W.lamC, &g, nfx, nfy);
+    rev_half(C, BD, fnb, I, R9, smat, V, nf, R, Hs2, W.C, m2, D2, W, W.lamHout, W.lamHin, W.lamC, &g, nfx, nfy);
     for (int f = tid; f < nf; f += nth) {
         W.lamHout[f] = W.lamHin[f];      // adjoint of H^{n+1}
         W.fix[f] = W.lamC[f];            // curl adjoint of the second half-push
     }
     __syncthreads();
-    rev_half(C, BD, fnb, I, R9, smat, V, nf, R, W.Hs1, W.C, W.m1, W.D1, W, W.lamHout, W.lamHin, W.lamC, &g, nfx, nfy);
+    rev_half(C, BD, fnb, I, R9, smat, V, nf, R, Hs1, W.C, m1, D1, W, W.lamHout, W.lamHin, W.lamC, &g, nfx, nfy);
     // write back: for a magnetic face the curl sweep must see q/2 with
     // q = -(lamC1 + lamC2) (a plain face contributes 2 lambda_H); afterwards
     // the face takes lamHin, restored from fix by the next reverse step's
@@ -475,7 +409,7 @@ __global__ void adj_fix_kernel(LaunchSet L, AdjSet A)
     const int V = C.V, bx = C.bx, by = C.by, bz = C.bz;
     const int nfx = (bx + 1) * by * bz, nfy = bx * (by + 1) * bz, nf = nfx + nfy + bx * by * (bz + 1);
     float *wsb = A.ws + A.ws_off[blockIdx.x];
-    RegionWS W = carve(wsb + (V + 3) / 4, nf, V, A.R);
+    RegionWS W = carve(wsb + (V + 3) / 4, nf, V);
     const BoxDiv BD(bx, by);
     for (int f = threadIdx.x; f < nf; f += blockDim.x) {
         int a, fi, fj, fk, vl, vr;
@@ -582,8 +516,9 @@ __global__ void adj_design_kernel(LaunchSet L, AdjSet A, int slot)
 
 long long adj_ws_floats(int bx, int by, int bz, int R)
 {
+    (void)R;
     const long long V = (long long)bx * by * bz;
-    return (V + 3) / 4 + 7 * mag_faces(bx, by, bz) + (27 + 6LL * R) * V;
+    return (V + 3) / 4 + 5 * mag_faces(bx, by, bz) + 15 * V;
 }
 
 cudaError_t adj_record_design(const LaunchSet &L, const AdjSet &A, int slot, int buf, cudaStream_t s)

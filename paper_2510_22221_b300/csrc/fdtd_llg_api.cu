@@ -1449,7 +1449,7 @@ extern "C" int fdtd_llg_adjoint_step(fdtd_llg_t h, const double *dJ_dE, double *
         const MagComp &C = I.comps[c];
         ws_off[c] = ws_tot;
         ws_tot += (adj_ws_floats(C.bx, C.by, C.bz, R) + 63) / 64 * 64;
-        tstr[c] = 3LL * C.V + mag_faces(C.bx, C.by, C.bz) + 3LL * (C.bx + 1) * (C.by + 1) * (C.bz + 1);
+        tstr[c] = mag_tape_floats(C.bx, C.by, C.bz, R);
         toff[c] = tape_tot;
         tape_tot += K * tstr[c];
     }

@@ -55,6 +55,15 @@ inline long long mag_faces(int bx, int by, int bz)
     return (long long)(bx + 1) * by * bz + (long long)bx * (by + 1) * bz + (long long)bx * by * (bz + 1);
 }
 inline long long mag_edges(int bx, int by, int bz) { return 3LL * (bx + 1) * (by + 1) * (bz + 1); }
+// One step of a region's adjoint tape (floats): m and face H at the step's
+// start (3V, faces), E^{n+1} at the box edges, the R Jacobi iterates of both
+// half-pushes (M^r - M^n, global axes, 2 R x 3V, half-push major), then face
+// H and m after the first half-push (faces, 3V).
+inline long long mag_tape_floats(int bx, int by, int bz, int R)
+{
+    const long long V = (long long)bx * by * bz;
+    return 3 * V + mag_faces(bx, by, bz) + mag_edges(bx, by, bz) + 6LL * R * V + mag_faces(bx, by, bz) + 3 * V;
+}
 // m (3 V floats), face H (one float per face), the box-edge E (3 per edge;
 // the change of M, 3 V floats, reuses it later), then one area that first
 // holds the stage of a block of qx x py x ps edge sites (H on the block grown
@@ -191,7 +200,7 @@ struct MagComp {
     int qx, py, ps;         // edge sites per staged block in x, y, z (mag_stage_block)
     float *m;               // deviation M - Ms h in the bias frame: 3 blocks of V
     const uint8_t *mat;     // V: magnet material index, 0xFF outside this region
-    float *tape;            // adjoint recording: per step m (3V), face H (faces), box-edge E; NULL when off
+    float *tape;            // adjoint recording, per step mag_tape_floats; NULL when off
     long long tstride;      // floats per step of the tape
 };
 

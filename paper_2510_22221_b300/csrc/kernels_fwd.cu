@@ -410,11 +410,17 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
         }
     }
     __syncthreads();
-    if (FUSED && L.rec && C.tape && (n < L.rec_n0 || n - L.rec_n0 >= L.rec_slots)) {
-        if (tid == 0) atomicOr(&L.ctl->status, ST_TAPE);   // out of the tape: record nothing
-    } else if (FUSED && L.rec && C.tape) {
-        // adjoint recording: m and face H at the start of the step, E^{n+1} at the box edges
-        float *T = C.tape + (n - L.rec_n0) * C.tstride;
+    // adjoint recording (mag_tape_floats): this step's tape slot, else NULL
+    float *T = nullptr;
+    if (FUSED && L.rec && C.tape) {
+        if (n < L.rec_n0 || n - L.rec_n0 >= L.rec_slots || L.llg_fixed_iter < 1) {
+            if (tid == 0) atomicOr(&L.ctl->status, ST_TAPE);   // out of the tape: record nothing
+        } else {
+            T = C.tape + (n - L.rec_n0) * C.tstride;
+        }
+    }
+    const int RI = L.llg_fixed_iter;
+    if (T) {   // m and face H at the start of the step, E^{n+1} at the box edges
         for (int v = tid; v < 3 * V; v += nth) T[v] = sM[v];
         for (int f = tid; f < nf; f += nth) T[3 * V + f] = sH[f];
         for (int e = tid; e < 3 * ne; e += nth) T[3 * V + nf + e] = sE[e];
@@ -508,6 +514,12 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
                     sD[V + v] = dn[q][1];
                     sD[2 * V + v] = dn[q][2];
                 }
+                if (T && v < V && r <= RI) {   // iterate r of half-push hp (zero outside the region)
+                    float *TD = T + 3 * V + nf + 3 * ne + (long long)((hp * RI + r - 1) * 3) * V;
+                    TD[v] = dn[q][0];
+                    TD[V + v] = dn[q][1];
+                    TD[2 * V + v] = dn[q][2];
+                }
             }
             res = block_max(res, sredf);
             if (L.llg_fixed_iter > 0) {
@@ -547,6 +559,11 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
             }
         }
         __syncthreads();
+        if (T && hp == 0) {   // face H and m after the first half-push
+            float *TH = T + 3 * V + nf + 3 * ne + 6LL * RI * V;
+            for (int f = tid; f < nf; f += nth) TH[f] = sH[f];
+            for (int v = tid; v < 3 * V; v += nth) TH[nf + v] = sM[v];
+        }
         if (rec) {
             eacc *= 0.5 * kMu0;
             // Zeeman energy mu0 (|H0| Ms - H0.M) = mu0 |H0|/(2 Ms) |M - Ms h|^2 on |M| = Ms
