@@ -13,11 +13,12 @@
 //     applied in one reverse-mode pass, llg_inc_vjp), giving
 //     the adjoint of the faces' H and of M at the step's start, of the curl
 //     terms, and d J / d |H_bias|;
-//   adj_curl_h_kernel:  lambda_E' = lambda_E - (dt/mu0) C_H lambda_H (for a
-//     non-magnetic face both half-pushes pass lambda_H through; magnetic faces
-//     carry the magnet kernel's curl adjoint here); it stores w = cb lambda_E'
-//     and lambda_E = ca lambda_E' (the class lookup once per edge);
-//   adj_design_kernel:  d J / d eps_edge += (w/dt) (E^n - E^{n+1});
+//   adj_curl_h_kernel:  the probe seed dJ/dE^n is added to lambda_E, then
+//     lambda_E' = lambda_E - (dt/mu0) C_H lambda_H (for a non-magnetic face
+//     both half-pushes pass lambda_H through; magnetic faces carry the magnet
+//     kernel's curl adjoint here); it stores w = cb lambda_E' and lambda_E =
+//     ca lambda_E' (the class lookup once per edge), and on the design-box
+//     edges adds d J / d eps_edge += (w/dt) (E^n - E^{n+1});
 //   adj_curl_e_kernel:  lambda_H += C_E w;
 //   the magnetic faces then take their own adjoint: the next reverse step's
 //     magnet kernel adds the pending correction as it reads them
@@ -424,19 +425,12 @@ __global__ void adj_fix_kernel(LaunchSet L, AdjSet A)
     }
 }
 
-__global__ void adj_seed_kernel(LaunchSet L, AdjSet A, long long n)
-{
-    const Inst *I = L.insts;
-    const int t = threadIdx.x;
-    if (t >= 3 * A.nprobe) return;
-    const int p = t / 3, c = t % 3;
-    const long long o = (long long)I->probe[p][2] * I->plane + (long long)I->probe[p][1] * I->px + I->probe[p][0];
-    A.lamE[c * I->fstride + o] += (float)A.seed[(n * A.nprobe + p) * 3 + c];
-}
-
-// lambda_E' = lambda_E - (dt/mu0) C_H lambda_H at every edge (i, j, k)
+// Step n's seed dJ/dE at the probe cells, then lambda_E' = lambda_E - (dt/mu0)
+// C_H lambda_H at every edge (i, j, k); stores w = cb lambda_E' and lambda_E =
+// ca lambda_E', and on the design-box edges adds d J / d eps_edge += (w/dt)
+// (E^n - E^{n+1}) from design-tape slots slot and slot + 1.
 template <typename ClsT>
-__global__ void __launch_bounds__(256) adj_curl_h_kernel(LaunchSet L, AdjSet A)
+__global__ void __launch_bounds__(256) adj_curl_h_kernel(LaunchSet L, AdjSet A, long long n, int slot)
 {
     const Inst *I = L.insts;
     const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
@@ -449,15 +443,37 @@ __global__ void __launch_bounds__(256) adj_curl_h_kernel(LaunchSet L, AdjSet A)
     const float cx = curl2a(lz[o], j > 0 ? lz[o - px] : 0.f, I->idy, ly[o], k > 0 ? ly[o - plane] : 0.f, I->idz);
     const float cy = curl2a(lx[o], k > 0 ? lx[o - plane] : 0.f, I->idz, lz[o], i > 0 ? lz[o - 1] : 0.f, I->idx);
     const float cz = curl2a(ly[o], i > 0 ? ly[o - 1] : 0.f, I->idx, lx[o], j > 0 ? lx[o - px] : 0.f, I->idy);
-    const float ex = A.lamE[o] - c2 * cx, ey = A.lamE[fs + o] - c2 * cy, ez = A.lamE[2 * fs + o] - c2 * cz;
+    float l0 = A.lamE[o], l1 = A.lamE[fs + o], l2 = A.lamE[2 * fs + o];
+    for (int p = 0; p < A.nprobe; ++p)
+        if (I->probe[p][0] == i && I->probe[p][1] == j && I->probe[p][2] == k) {
+            const double *sd = A.seed + (n * A.nprobe + p) * 3;
+            l0 += (float)sd[0];
+            l1 += (float)sd[1];
+            l2 += (float)sd[2];
+        }
+    const float ex = l0 - c2 * cx, ey = l1 - c2 * cy, ez = l2 - c2 * cz;
     const int c = (int)static_cast<const ClsT *>(I->cls)[o];
     const float4 Ca = __ldg(I->ctab + 3 * c), Cb = __ldg(I->ctab + 3 * c + 1);
-    A.lamEn[o] = Cb.x * ex;           // w = cb lambda_E'
-    A.lamEn[fs + o] = Cb.y * ey;
-    A.lamEn[2 * fs + o] = Cb.z * ez;
+    const float w[3] = {Cb.x * ex, Cb.y * ey, Cb.z * ez};   // w = cb lambda_E'
+    A.lamEn[o] = w[0];
+    A.lamEn[fs + o] = w[1];
+    A.lamEn[2 * fs + o] = w[2];
     A.lamE[o] = Ca.x * ex;            // lambda_E = ca lambda_E'
     A.lamE[fs + o] = Ca.y * ey;
     A.lamE[2 * fs + o] = Ca.z * ez;
+    if (A.geps) {
+        const int li = i - A.di0, lj = j - A.dj0, lk = k - A.dk0;
+        if (li >= 0 && lj >= 0 && lk >= 0 && li <= A.dbx && lj <= A.dby && lk <= A.dbz) {
+            const int bex = A.dbx + 1, bey = A.dby + 1, ne = bex * bey * (A.dbz + 1);
+            const int r = (lk * bey + lj) * bex + li;
+            for (int q = 0; q < 3; ++q) {
+                if (w[q] == 0.f) continue;
+                const int e = q * ne + r;
+                const float En = A.dtape[(long long)slot * 3 * ne + e], En1 = A.dtape[(long long)(slot + 1) * 3 * ne + e];
+                A.geps[e] += (double)w[q] / I->dt * ((double)En - (double)En1);
+            }
+        }
+    }
 }
 
 // lambda_H += C_E w  (w = cb lambda_E', zero beyond the far walls)
@@ -495,23 +511,6 @@ __global__ void adj_record_design_kernel(LaunchSet L, AdjSet A, int slot, int bu
     A.dtape[(long long)slot * 3 * ne + e] = v;
 }
 
-// d J / d eps_edge += (w/dt) (E^n - E^{n+1}) on the design-box edges
-__global__ void adj_design_kernel(LaunchSet L, AdjSet A, int slot)
-{
-    const Inst *I = L.insts;
-    const int ex = A.dbx + 1, ey = A.dby + 1, ez = A.dbz + 1, ne = ex * ey * ez;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 3 * ne) return;
-    const int comp = e / ne, r = e - comp * ne;
-    const int i = A.di0 + r % ex, j = A.dj0 + (r / ex) % ey, k = A.dk0 + r / (ex * ey);
-    if (i >= I->nx || j >= I->ny || k >= I->nz) return;
-    const long long o = (long long)k * I->plane + (long long)j * I->px + i;
-    const float w = A.lamEn[comp * I->fstride + o];   // cb lambda_E'
-    if (w == 0.f) return;
-    const float En = A.dtape[(long long)slot * 3 * ne + e], En1 = A.dtape[(long long)(slot + 1) * 3 * ne + e];
-    A.geps[e] += (double)w / I->dt * ((double)En - (double)En1);
-}
-
 }  // namespace
 
 long long adj_ws_floats(int bx, int by, int bz, int R)
@@ -532,17 +531,14 @@ cudaError_t adj_record_design(const LaunchSet &L, const AdjSet &A, int slot, int
 // (magnets) and design slots slot, slot+1 (E^n, E^{n+1}).
 cudaError_t adj_reverse_step(const LaunchSet &L, const AdjSet &A, long long n, int slot, cudaStream_t s)
 {
-    if (A.nprobe > 0) adj_seed_kernel<<<1, 3 * A.nprobe, 0, s>>>(L, A, n);
     if (L.ncomp) {
         const cudaError_t e = cudaFuncSetAttribute(adj_mag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, A.fnb_bytes);
         if (e != cudaSuccess) return e;
         adj_mag_kernel<<<L.ncomp, kMagThreads, A.fnb_bytes, s>>>(L, A, slot);
     }
     const dim3 blk(32, 8), grid((A.nx + 31) / 32, (A.ny + 7) / 8, A.nz);
-    const int ne3 = 3 * (A.dbx + 1) * (A.dby + 1) * (A.dbz + 1);
-    if (L.cls16) adj_curl_h_kernel<uint16_t><<<grid, blk, 0, s>>>(L, A);
-    else adj_curl_h_kernel<uint8_t><<<grid, blk, 0, s>>>(L, A);
-    if (A.geps) adj_design_kernel<<<(ne3 + 255) / 256, 256, 0, s>>>(L, A, slot);
+    if (L.cls16) adj_curl_h_kernel<uint16_t><<<grid, blk, 0, s>>>(L, A, n, slot);
+    else adj_curl_h_kernel<uint8_t><<<grid, blk, 0, s>>>(L, A, n, slot);
     adj_curl_e_kernel<<<grid, blk, 0, s>>>(L, A);
     return cudaGetLastError();
 }
