@@ -249,9 +249,22 @@ int fdtd_llg_autotune(fdtd_llg_t h, int32_t trial_steps, int32_t *planes);
  * and the sources and probes), run nsteps steps like fdtd_llg_step while
  * keeping a copy of the state (E, H, walls, M: 6 field arrays + walls + 3
  * floats per magnet cell) every `interval` steps (0: ceil(sqrt(nsteps))), on
- * the device through the handle's allocator.  With magnets the LLG solve must
- * be a fixed map: llg_fixed_iter >= 2 at creation.  Errors: FDTD_E_INVAL,
- * FDTD_E_STATE (not at step 0), FDTD_E_NOSYS (batch), FDTD_E_OOM.
+ * the device through the handle's allocator.  It also records what the
+ * reverse steps read (per step: each magnet region's start state, box-edge
+ * E and Jacobi iterates; E on the design-box edges) for the trailing
+ * segments whose records fit the tape budget (fdtd_llg_set_tape_budget), and
+ * keeps room for one more segment, into which fdtd_llg_adjoint_step
+ * recomputes each earlier segment from its checkpoint.  With magnets the LLG
+ * solve must be a fixed map: llg_fixed_iter >= 2 at creation.  Errors:
+ * FDTD_E_INVAL, FDTD_E_STATE (not at step 0), FDTD_E_NOSYS (batch),
+ * FDTD_E_OOM.
+ *
+ * fdtd_llg_set_tape_budget: bytes that fdtd_llg_run_checkpointed may use for
+ * records taken during the run (on top of the checkpoints and of one
+ * segment's records): < 0 (the default) half the free device memory at that
+ * call, 0 none (every segment is recomputed once, the sqrt(N) checkpointing
+ * alone).  The gradients do not depend on it.  Errors: FDTD_E_INVAL (member
+ * handle).
  *
  * fdtd_llg_adjoint_step: the reverse-time counterpart of fdtd_llg_step over
  * the whole recorded run, i.e. the exact gradient of the discrete forward map
@@ -264,11 +277,13 @@ int fdtd_llg_autotune(fdtd_llg_t h, int32_t trial_steps, int32_t *planes);
  * FP64, either may be NULL: grad_eps[k][j][i], dJ/d eps_r of every cell of the
  * design box given to fdtd_llg_set_materials; *grad_h0, dJ/d |H_bias| (per
  * A/m) along the bias direction (M starts along it whatever its size).  The
- * call may be repeated with other dJ_dE; afterwards the handle's state is
- * that after the first checkpoint interval (read probes and energy before
+ * call may be repeated with other dJ_dE; afterwards the handle's fields hold
+ * the state of the run's last step or, when segments were recomputed, that
+ * after the first checkpoint interval (read probes and energy before
  * calling).  Errors: FDTD_E_STATE (no checkpointed run; grad_eps without a
  * design box), FDTD_E_INVAL, FDTD_E_OOM, FDTD_E_UNSTABLE, FDTD_E_CUDA. */
 int fdtd_llg_run_checkpointed(fdtd_llg_t h, int64_t nsteps, int32_t interval);
+int fdtd_llg_set_tape_budget(fdtd_llg_t h, int64_t bytes);
 int fdtd_llg_adjoint_step(fdtd_llg_t h, const double *dJ_dE, double *grad_eps, double *grad_h0);
 
 /* Spectra and mode fits of probe time series (the E_x spectra behind the

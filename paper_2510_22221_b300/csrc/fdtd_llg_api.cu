@@ -81,6 +81,13 @@ struct Sim {
     long long adj_K = 0;              // steps between checkpoints
     float *ckpt = nullptr;            // ceil(N/K) states: fields of the present buffer, walls, m
     size_t ckpt_floats = 0;
+    // adjoint tapes (run_checkpointed): slots [0, tail) hold the last `tail`
+    // steps of the run (step tail0 + s), recorded as it ran; when tail < N,
+    // slots [tail + 1, tail + 1 + K) take one recomputed segment
+    float *tape = nullptr;            // magnet regions, region-major: slots x mag_tape_floats
+    float *dtape = nullptr;           // design-box edge E: slots + 1 records
+    long long tail = 0, tail0 = 0;
+    long long tape_budget = -1;       // bytes recorded during the run (-1: half the free device memory)
     // CUDA graph of kGraphSteps steps (even: the buffer parity returns), replayed by long step calls
     cudaGraphExec_t graph = nullptr;
     int graph_parity = -1;            // buffer holding the state when the graph starts; -1: none
@@ -610,6 +617,10 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
     S->half_ahead = false;
     S->cur = 0;
     S->adj_N = 0;   // a recorded run belongs to the previous materials
+    S->dfree(S->tape);
+    S->dfree(S->dtape);
+    S->tape = S->dtape = nullptr;
+    S->tail = S->tail0 = 0;
     // ordered on the handle's stream (its kernels may still run)
     CKR(h, cudaMemsetAsync(S->d_ctl, 0, sizeof(StepCtl), S->stream));
     CKR(h, set_device_step(S->d_ctl, 0, S->stream));
@@ -1378,6 +1389,22 @@ static cudaError_t copy_state(Sim *S, float *buf, bool save)
     return e;
 }
 
+// Design-box geometry of the adjoint sets of instance I (nbe edge sites).
+static long long design_set(const Instance &I, AdjSet &A)
+{
+    if (!I.has_design) return 0;
+    A.di0 = I.dbox[0]; A.dj0 = I.dbox[1]; A.dk0 = I.dbox[2];
+    A.dbx = I.dbox[3]; A.dby = I.dbox[4]; A.dbz = I.dbox[5];
+    return (long long)(A.dbx + 1) * (A.dby + 1) * (A.dbz + 1);
+}
+
+extern "C" int fdtd_llg_set_tape_budget(fdtd_llg_t h, int64_t bytes)
+{
+    if (!h || !h->sim || !h->owns) return fail(h, FDTD_E_INVAL, "set_tape_budget needs the handle, not a member");
+    h->sim->tape_budget = bytes < 0 ? -1 : bytes;
+    return FDTD_OK;
+}
+
 extern "C" int fdtd_llg_run_checkpointed(fdtd_llg_t h, int64_t nsteps, int32_t interval)
 {
     if (!h || !h->sim || !h->owns) return fail(h, FDTD_E_INVAL, "run_checkpointed needs the handle, not a member");
@@ -1392,11 +1419,56 @@ extern "C" int fdtd_llg_run_checkpointed(fdtd_llg_t h, int64_t nsteps, int32_t i
     const long long K = interval > 0 ? interval : (long long)std::ceil(std::sqrt((double)nsteps));
     const long long nck = (nsteps + K - 1) / K;
     const size_t sf = state_floats(S->inst[0]);
+    Instance &I = S->inst[0];
+    S->adj_N = 0;
     S->dfree(S->ckpt);
+    S->dfree(S->tape);
+    S->dfree(S->dtape);
+    S->tape = S->dtape = nullptr;
     S->ckpt = (float *)S->dalloc((size_t)nck * sf * sizeof(float));
     if (!S->ckpt) return fail(h, FDTD_E_OOM, "checkpoint allocation failed");
     S->ckpt_floats = sf;
-    S->adj_N = 0;
+    // tapes: the trailing segments that fit the budget are recorded during
+    // this run (their reverse steps need no recomputation); one more segment's
+    // worth of slots serves the recomputation of the earlier ones
+    const int R = std::max(2, S->cfg.llg_fixed_iter);
+    const int nc = (int)I.comps.size();
+    std::vector<long long> tstr(std::max(1, nc), 0);
+    long long per_m = 0;
+    for (int c = 0; c < nc; ++c) per_m += (tstr[c] = mag_tape_floats(I.comps[c].bx, I.comps[c].by, I.comps[c].bz, R));
+    AdjSet Ad{};
+    const long long per_d = 3 * design_set(I, Ad);
+    auto slots = [&](long long T, long long &tail, long long &sm, long long &sd) {
+        tail = T == 0 ? 0 : nsteps - (nck - T) * K;
+        const long long rk = T < nck ? K : 0;
+        sm = tail + (rk ? 1 + rk : 0);
+        sd = tail + 1 + (rk ? rk + 1 : 0);
+        return 4 * (sm * per_m + sd * per_d);
+    };
+    long long budget = S->tape_budget;
+    if (budget < 0) {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        budget = (long long)(fr / 2);
+    }
+    long long T = 0, tail = 0, sm = 0, sd = 0;
+    while (T < nck && slots(T + 1, tail, sm, sd) <= budget) ++T;
+    slots(T, tail, sm, sd);
+    if (per_m) S->tape = (float *)S->dalloc((size_t)(sm * per_m) * sizeof(float));
+    if (per_d) S->dtape = (float *)S->dalloc((size_t)(sd * per_d) * sizeof(float));
+    if ((per_m && !S->tape) || (per_d && !S->dtape)) return fail(h, FDTD_E_OOM, "adjoint tape allocation failed");
+    long long off = 0;
+    for (int c = 0; c < nc; ++c) {
+        I.comps[c].tape = S->tape + off;
+        I.comps[c].tstride = tstr[c];
+        off += sm * tstr[c];
+    }
+    Ad.dtape = S->dtape;
+    S->tail = tail;
+    S->tail0 = nsteps - tail;
+    S->dirty = true;
+    rc = upload_descriptors(h);
+    if (rc) return rc;
     if (!S->half_ahead) {
         LaunchSet L = launch_set(S);
         L.src = L.dst = S->cur;
@@ -1404,9 +1476,27 @@ extern "C" int fdtd_llg_run_checkpointed(fdtd_llg_t h, int64_t nsteps, int32_t i
         S->half_ahead = true;
     }
     for (long long c = 0; c < nck; ++c) {
+        const long long na = c * K, ns = std::min<long long>(K, nsteps - na);
         CKR(h, copy_state(S, S->ckpt + c * sf, true));
-        rc = fdtd_llg_step(h, std::min<long long>(K, nsteps - c * K));
-        if (rc) return rc;
+        if (na < S->tail0) {
+            rc = fdtd_llg_step(h, ns);
+            if (rc) return rc;
+            continue;
+        }
+        LaunchSet L = launch_set(S);   // recorded steps: magnet tape slot n - tail0, design slots after each step
+        L.rec = 1;
+        L.rec_n0 = S->tail0;
+        L.rec_slots = (int)tail;
+        if (na == S->tail0 && per_d) CKR(h, adj_record_design(L, Ad, 0, S->cur, S->stream));
+        for (long long n = na; n < na + ns; ++n) {
+            L.src = S->cur;
+            L.dst = 1 - S->cur;
+            CKR(h, launch_step(L, S->stream, nullptr));
+            S->cur ^= 1;
+            if (per_d) CKR(h, adj_record_design(L, Ad, (int)(n - S->tail0 + 1), S->cur, S->stream));
+        }
+        CKR(h, launch_energy_flush(L, S->stream));
+        S->host_step += ns;
     }
     S->adj_N = nsteps;
     S->adj_K = K;
@@ -1431,8 +1521,6 @@ extern "C" int fdtd_llg_adjoint_step(fdtd_llg_t h, const double *dJ_dE, double *
         return p;
     };
     auto cleanup = [&]() {
-        for (auto &C : I.comps) { C.tape = nullptr; C.tstride = 0; }
-        S->dirty = true;
         cudaStreamSynchronize(S->stream);
         for (void *p : owned) S->dfree(p);
     };
@@ -1443,21 +1531,16 @@ extern "C" int fdtd_llg_adjoint_step(fdtd_llg_t h, const double *dJ_dE, double *
     A.lamW = (float *)alloc(I.n_wall() * 4);
     const int nc = (int)I.comps.size();
     std::vector<long long> ws_off(std::max(1, nc), 0);
-    long long ws_tot = 0, tape_tot = 0;
-    std::vector<long long> toff(std::max(1, nc), 0), tstr(std::max(1, nc), 0);
+    long long ws_tot = 0;
     for (int c = 0; c < nc; ++c) {
         const MagComp &C = I.comps[c];
         ws_off[c] = ws_tot;
         ws_tot += (adj_ws_floats(C.bx, C.by, C.bz, R) + 63) / 64 * 64;
-        tstr[c] = mag_tape_floats(C.bx, C.by, C.bz, R);
-        toff[c] = tape_tot;
-        tape_tot += K * tstr[c];
     }
     A.ws = (float *)alloc(std::max<long long>(ws_tot, 1) * 4);
     long long *d_wsoff = (long long *)alloc(ws_off.size() * sizeof(long long));
     A.ws_off = d_wsoff;
     A.gh0 = (double *)alloc(std::max(1, nc) * sizeof(double));
-    float *tape = (float *)alloc(std::max<long long>(tape_tot, 1) * 4);
     const long long nseed = N * std::max(1, np) * 3;
     double *d_seed = (double *)alloc(nseed * sizeof(double));
     A.seed = d_seed;
@@ -1466,16 +1549,13 @@ extern "C" int fdtd_llg_adjoint_step(fdtd_llg_t h, const double *dJ_dE, double *
     A.R = R;
     for (int c = 0; c < nc; ++c)
         A.fnb_bytes = std::max(A.fnb_bytes, (int)(8 * mag_faces(I.comps[c].bx, I.comps[c].by, I.comps[c].bz)));
-    long long nbe = 0;
-    if (I.has_design) {
-        A.di0 = I.dbox[0]; A.dj0 = I.dbox[1]; A.dk0 = I.dbox[2];
-        A.dbx = I.dbox[3]; A.dby = I.dbox[4]; A.dbz = I.dbox[5];
-        nbe = (long long)(A.dbx + 1) * (A.dby + 1) * (A.dbz + 1);
-        A.dtape = (float *)alloc((size_t)(K + 1) * 3 * nbe * 4);
+    const long long nbe = design_set(I, A);
+    if (nbe) {
+        A.dtape = S->dtape;
         A.geps = (double *)alloc(3 * nbe * sizeof(double));
     }
-    bool ok = A.lamE && A.lamEn && A.lamH && A.lamW && A.ws && d_wsoff && A.gh0 && tape && d_seed &&
-              (!I.has_design || (A.dtape && A.geps));
+    bool ok = A.lamE && A.lamEn && A.lamH && A.lamW && A.ws && d_wsoff && A.gh0 && d_seed &&
+              (!nbe || (A.dtape && A.geps)) && (!nc || S->tape);
     if (!ok) { cleanup(); return fail(h, FDTD_E_OOM, "adjoint buffers: device allocation failed"); }
     cudaError_t e = cudaMemsetAsync(A.lamE, 0, 3 * nf * 4, S->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(A.lamH, 0, 6 * nf * 4, S->stream);
@@ -1487,32 +1567,35 @@ extern "C" int fdtd_llg_adjoint_step(fdtd_llg_t h, const double *dJ_dE, double *
     if (e == cudaSuccess && np) e = cudaMemcpyAsync(d_seed, dJ_dE, nseed * sizeof(double), cudaMemcpyHostToDevice, S->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
     if (e != cudaSuccess) { cleanup(); return fail(h, FDTD_E_CUDA, std::string("adjoint setup: ") + cudaGetErrorString(e)); }
-    for (int c = 0; c < nc; ++c) {
-        I.comps[c].tape = tape + toff[c];
-        I.comps[c].tstride = tstr[c];
-    }
-    S->dirty = true;
     int rc = upload_descriptors(h);
     if (rc) { cleanup(); return rc; }
     LaunchSet L = launch_set(S);
     L.rec = 1;
+    const long long tail = S->tail, tail0 = S->tail0, base = tail + 1;
     for (long long seg = nck - 1; seg >= 0 && e == cudaSuccess; --seg) {
         const long long na = seg * K, nb = std::min(N, na + K);
+        if (na >= tail0) {   // recorded during the run: tape slot n - tail0
+            for (long long n = nb - 1; n >= na && e == cudaSuccess; --n)
+                e = adj_reverse_step(L, A, n, (int)(n - tail0), S->stream);
+            continue;
+        }
+        // recompute the segment from its checkpoint into slots base + (n - na)
         e = copy_state(S, S->ckpt + seg * sf, false);
         // ordered on the handle's stream: earlier segments' kernels may still run
         if (e == cudaSuccess) e = set_device_step(S->d_ctl, na, S->stream);
-        L.rec_n0 = na;
-        L.rec_slots = (int)K;
-        if (e == cudaSuccess && I.has_design) e = adj_record_design(L, A, 0, S->cur, S->stream);
+        L.rec_n0 = na - base;
+        L.rec_slots = (int)(base + K);
+        if (e == cudaSuccess && nbe) e = adj_record_design(L, A, (int)base, S->cur, S->stream);
         for (long long n = na; n < nb && e == cudaSuccess; ++n) {
             L.src = S->cur;
             L.dst = 1 - S->cur;
             e = launch_step(L, S->stream, nullptr);
             S->cur ^= 1;
-            if (e == cudaSuccess && I.has_design) e = adj_record_design(L, A, (int)(n - na + 1), S->cur, S->stream);
+            if (e == cudaSuccess && nbe) e = adj_record_design(L, A, (int)(base + n - na + 1), S->cur, S->stream);
         }
         if (e == cudaSuccess) e = launch_energy_flush(L, S->stream);
-        for (long long n = nb - 1; n >= na && e == cudaSuccess; --n) e = adj_reverse_step(L, A, n, (int)(n - na), S->stream);
+        for (long long n = nb - 1; n >= na && e == cudaSuccess; --n)
+            e = adj_reverse_step(L, A, n, (int)(base + n - na), S->stream);
         S->host_step = nb;
     }
     if (e == cudaSuccess) e = adj_finish(L, A, S->stream);

@@ -257,6 +257,11 @@ class FdtdLlg:
         check(_abi.load().fdtd_llg_run_checkpointed(self._h, int(nsteps), int(interval)), self._h)
         self._adj_steps = int(nsteps)
 
+    def set_tape_budget(self, nbytes: int):
+        """Device bytes the next run_checkpointed may spend on records taken
+        during the run (< 0: half the free memory, 0: recompute every segment)."""
+        check(_abi.load().fdtd_llg_set_tape_budget(self._h, int(nbytes)), self._h)
+
     def adjoint_step(self, dJ_dE, design_shape=None):
         """Gradients of J given dJ/dE at the probes (nsteps x nprobes x 3):
         (dJ/d eps_r of the design cells or None, dJ/d |H_bias| per A/m)."""

@@ -29,8 +29,9 @@ def _reference(w, N, n0):
     return A.gradients(m, N, w.eps_design, float(np.linalg.norm(w.hbias)), n0=n0)
 
 
-def _gpu(w, N, n0, interval=0):
+def _gpu(w, N, n0, interval=0, budget=-1):
     sim = pkg.from_workload(w, probe_capacity=N, llg_fixed_iter=3)
+    sim.set_tape_budget(budget)
     sim.run_checkpointed(N, interval)
     rows = np.stack([sim.probe(p)[:, :3] for p in range(len(w.probes))], axis=1)
     seed = np.zeros_like(rows)
@@ -61,14 +62,20 @@ def test_adjoint_matches_fp64_reference(case):
 
 
 def test_checkpoint_interval_does_not_change_the_gradient():
+    """The interval and the tape budget only move work between the forward
+    run (records kept as it runs) and the reverse sweep (segments recomputed
+    from checkpoints); the gradient is the same to the bit."""
     make, N, n0, _ = CASES["anticross"]
     w = make()
-    _, g0, h0 = _gpu(w, N, n0, interval=0)      # sqrt(N) = 30
-    _, g1, h1 = _gpu(w, N, n0, interval=7)
-    _, g2, h2 = _gpu(w, N, n0, interval=N)      # one segment
-    np.testing.assert_array_equal(g0, g1)
-    np.testing.assert_array_equal(g0, g2)
-    assert h0 == h1 == h2
+    _, g0, h0 = _gpu(w, N, n0, interval=0)               # sqrt(N) = 30, everything recorded during the run
+    runs = [_gpu(w, N, n0, interval=7),
+            _gpu(w, N, n0, interval=N),                  # one segment
+            _gpu(w, N, n0, interval=0, budget=0),        # every segment recomputed
+            _gpu(w, N, n0, interval=7, budget=0),
+            _gpu(w, N, n0, interval=30, budget=2 << 20)]  # the last few segments recorded, the rest recomputed
+    for _, g, h in runs:
+        np.testing.assert_array_equal(g0, g)
+        assert h == h0
 
 
 def test_adjoint_directional_derivatives_equal_gpu_central_differences():
@@ -129,14 +136,15 @@ def test_adjoint_argument_errors():
 
 def test_adjoint_on_a_stream_of_its_own_equals_the_default_stream():
     """The reverse sweep orders every device write on the handle's stream: on
-    a non-blocking stream of the caller's, with many short segments, the
+    a non-blocking stream of the caller's, with many short segments, all
+    recomputed from their checkpoints (no records kept during the run), the
     gradient is bitwise that of the default stream."""
     make, N, n0, _ = CASES["anticross"]
     w = make()
-    _, g_ref, h_ref = _gpu(w, N, n0, interval=9)
+    _, g_ref, h_ref = _gpu(w, N, n0, interval=9, budget=0)
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
-        _, g, h = _gpu(w, N, n0, interval=9)
+        _, g, h = _gpu(w, N, n0, interval=9, budget=0)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(g, g_ref)
     assert h == h_ref
