@@ -707,27 +707,29 @@ static int encode_tensor_maps(fdtd_llg_t h, const Instance &I, Inst &d)
     return FDTD_OK;
 }
 
-// Plane count of the sweep tasks from a wave model: with `slots` CTAs resident
-// at once and tasks of about equal length, the sweep takes ceil(tasks/slots)
-// waves of (planes + 2) plane-times (two extra planes per task: the one below
-// for the curl and the one above for E^{n+1}); pick the count that keeps the
-// most slots busy per unit of work, preferring fewer extra planes on ties.
+// Plane count of the sweep tasks from a cost model.  A task of P planes
+// costs about P + 1.4 plane-times (the plane below, which only loads H, ~0.4,
+// and the extra E^{n+1} plane above, 1); `slots` CTAs drawing the tasks
+// finish after the total over the slots plus, on average, half the longest
+// task.  Fewer, longer tasks cut the per-task planes, shorter ones the tail;
+// the P with the smallest modelled time wins (the smallest on ties).
 static int model_planes(const Sim *S, int slots)
 {
     int best = kSZ, maxnz = 1;
-    double best_eff = -1.0;
+    double best_t = 1e300;
+    const double sl = std::max(1, slots);
     for (const Instance &I : S->inst) maxnz = std::max(maxnz, I.nz);
-    for (int P = 4; P <= std::max(4, std::min(maxnz, 128)); ++P) {
-        double tasks = 0, work = 0;
+    for (int P = 2; P <= std::max(2, std::min(maxnz, 128)); ++P) {
+        double items = 0;
+        int maxt = 0;
         for (const Instance &I : S->inst) {
             const int pk = std::min(P, I.nz), nch = (I.nz + pk - 1) / pk;
             const double cols = (double)((I.nx + kSX - 1) / kSX) * ((I.ny + kSY - 1) / kSY);
-            tasks += cols * nch;
-            work += cols * (I.nz + 2.0 * nch);
+            items += cols * (I.nz + 1.4 * nch);
+            maxt = std::max(maxt, pk);
         }
-        const double waves = std::ceil(tasks / std::max(1, slots));
-        const double eff = work / (std::max(1, slots) * waves * (std::min(P, maxnz) + 2.0));
-        if (eff > best_eff * (1.0 + 1e-3)) { best_eff = eff; best = P; }
+        const double t = items / sl + 0.5 * (maxt + 1.4);
+        if (t < best_t * (1.0 - 1e-9)) { best_t = t; best = P; }
     }
     return best;
 }
