@@ -171,6 +171,14 @@ int fdtd_llg_probe(fdtd_llg_t h, int32_t id, double *out, int64_t cap_rows, int6
  * (oldest first, one per step) to out. */
 int fdtd_llg_energy(fdtd_llg_t h, double *out, int64_t cap, int64_t *written);
 
+/* The newest step's outputs in one call and one stream synchronisation: the
+ * rows of every probe (probe_rows: nprobes x 9 doubles, in add order; may be
+ * NULL) and the energy (*energy; may be NULL; 0 when the handle was created
+ * without energy).  Host memory, caller-owned.  Errors: FDTD_E_INVAL (batch
+ * handle), FDTD_E_STATE (no step yet), and the latched run errors of
+ * fdtd_llg_sync. */
+int fdtd_llg_read_last(fdtd_llg_t h, double *probe_rows, double *energy);
+
 /* Steps completed, and whether H and M are stored half a step ahead of E
  * (1 after the first step; get_field then returns H, M at (n + 1/2) dt). */
 int fdtd_llg_time_state(fdtd_llg_t h, int64_t *step, int32_t *h_half_ahead);

@@ -968,16 +968,21 @@ extern "C" int fdtd_llg_step(fdtd_llg_t h, int64_t nsteps)
     return FDTD_OK;
 }
 
+static int check_status(fdtd_llg_t h, const StepCtl &c)
+{
+    if (c.status & ST_UNSTABLE) return fail(h, FDTD_E_UNSTABLE, "energy is not finite (unstable run)");
+    if (c.status & ST_NOCONV) return fail(h, FDTD_E_LLG_NOCONV, "an LLG solve did not reach llg_tol within llg_max_iter");
+    if (c.status & ST_TIMEOUT) return fail(h, FDTD_E_CUDA, "a field-kernel wait for its tile copies timed out");
+    return FDTD_OK;
+}
+
 static int sync_status(fdtd_llg_t h)
 {
     Sim *S = h->sim;
     CKR(h, cudaStreamSynchronize(S->stream));
     StepCtl c{};
     CKR(h, cudaMemcpy(&c, S->d_ctl, sizeof c, cudaMemcpyDeviceToHost));
-    if (c.status & ST_UNSTABLE) return fail(h, FDTD_E_UNSTABLE, "energy is not finite (unstable run)");
-    if (c.status & ST_NOCONV) return fail(h, FDTD_E_LLG_NOCONV, "an LLG solve did not reach llg_tol within llg_max_iter");
-    if (c.status & ST_TIMEOUT) return fail(h, FDTD_E_CUDA, "a field-kernel wait for its tile copies timed out");
-    return FDTD_OK;
+    return check_status(h, c);
 }
 
 extern "C" int fdtd_llg_sync(fdtd_llg_t h)
@@ -1043,6 +1048,24 @@ extern "C" int fdtd_llg_energy(fdtd_llg_t h, double *out, int64_t cap, int64_t *
     int rc = sync_status(h);
     if (rc) return rc;
     return read_ring(h, I->energy_buf, 1, 0, 1, out, cap, written);
+}
+
+extern "C" int fdtd_llg_read_last(fdtd_llg_t h, double *probe_rows, double *energy)
+{
+    if (!is_member(h)) return fail(h, FDTD_E_INVAL, "read_last needs an instance handle");
+    Sim *S = h->sim;
+    Instance *I = inst_of(h);
+    if (S->host_step < 1) return fail(h, FDTD_E_STATE, "no step has run");
+    const long long slot = (S->host_step - 1) % S->cfg.probe_capacity;
+    const size_t np = I->probes.size();
+    StepCtl c{};
+    if (probe_rows && np)
+        CKR(h, cudaMemcpyAsync(probe_rows, I->probe_buf + slot * np * 9, np * 9 * sizeof(double), cudaMemcpyDeviceToHost,
+                               S->stream));
+    if (energy) CKR(h, cudaMemcpyAsync(energy, I->energy_buf + slot, sizeof(double), cudaMemcpyDeviceToHost, S->stream));
+    CKR(h, cudaMemcpyAsync(&c, S->d_ctl, sizeof c, cudaMemcpyDeviceToHost, S->stream));
+    CKR(h, cudaStreamSynchronize(S->stream));
+    return check_status(h, c);
 }
 
 // ------------------------------------------------------------- fields

@@ -87,6 +87,7 @@ class FdtdLlg:
         self._dims = dims          # (nx, ny, nz)
         self._members = {}
         self._batch_dims = None
+        self._probes = 0           # probes added through this instance handle
 
     # ------------------------------------------------------------- creation
     @classmethod
@@ -171,6 +172,7 @@ class FdtdLlg:
     def add_probe(self, i, j, k) -> int:
         pid = C.c_int32()
         check(_abi.load().fdtd_llg_add_probe(self._h, int(i), int(j), int(k), C.byref(pid)), self._h)
+        self._probes = pid.value + 1
         return pid.value
 
     # -------------------------------------------------------------- run
@@ -212,6 +214,15 @@ class FdtdLlg:
         w = C.c_int64()
         check(lib.fdtd_llg_energy(self._h, out.ctypes.data_as(C.POINTER(C.c_double)), n, C.byref(w)), self._h)
         return out[: w.value]
+
+    def read_last(self):
+        """(rows, energy) of the newest step: rows (nprobes, 9) for every
+        probe, one stream synchronisation."""
+        lib = _abi.load()
+        rows = np.zeros((max(self._probes, 1), 9))
+        e = C.c_double()
+        check(lib.fdtd_llg_read_last(self._h, rows.ctypes.data_as(C.POINTER(C.c_double)), C.byref(e)), self._h)
+        return rows[: self._probes], e.value
 
     def _shape(self, name):
         nx, ny, nz = self._dims

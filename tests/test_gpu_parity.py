@@ -264,6 +264,21 @@ def test_energy_does_not_depend_on_how_the_run_is_split():
         sim.destroy()
 
 
+def test_read_last_returns_the_newest_rows_and_energy():
+    w = W.random_small(8, steps=12)
+    sim = pkg.from_workload(w, probe_capacity=5)   # the ring wraps
+    with pytest.raises(pkg.LLGError):
+        sim.read_last()                              # no step yet
+    for n in range(1, 13):
+        sim.step(1)
+        rows, e = sim.read_last()
+        assert rows.shape == (len(w.probes), 9)
+        for p in range(len(w.probes)):
+            np.testing.assert_array_equal(rows[p], sim.probe(p)[-1])
+        assert e == sim.energy()[-1]
+    sim.destroy()
+
+
 def test_batch_equals_separate_runs_bitwise():
     ws = [W.random_small(s, nx=9 + 7 * s, ny=10, nz=8 + s, steps=25) for s in range(3)]
     dims = [(x.nx, x.ny, x.nz) for x in ws]
