@@ -237,6 +237,18 @@ int fdtd_llg_get_dt(fdtd_llg_t h, double *dt);
  * FDTD_E_INVAL (planes < 0, or a member handle). */
 int fdtd_llg_set_tiling(fdtd_llg_t h, int32_t planes);
 
+/* Tile shape of the field sweep: width 64 (64 x 8 cells per task column) or
+ * 32 (32 x 16), the same 512 cells and the same per-plane copies; 0 (the
+ * default) takes the shape that pads the instances' x-y extents to fewer
+ * cells (64 on ties).  Fields and probe samples do not depend on it.  Takes
+ * effect at the next step.  Errors: FDTD_E_INVAL (not 0, 32 or 64; a member
+ * handle). */
+int fdtd_llg_set_tile_width(fdtd_llg_t h, int32_t width);
+
+/* The tile width in effect; 0 before the first step or sync after materials
+ * were set. */
+int fdtd_llg_get_tile_width(fdtd_llg_t h, int32_t *width);
+
 /* The z-planes per sweep task in effect (resolving planes = 0); *planes is
  * 0 before the first step or sync after materials were set. */
 int fdtd_llg_get_tiling(fdtd_llg_t h, int32_t *planes);
@@ -244,9 +256,12 @@ int fdtd_llg_get_tiling(fdtd_llg_t h, int32_t *planes);
 /* Autotuner of the tiling.  Runs trial_steps real steps (they advance the
  * simulation, fill the probe and energy rings and count in the step number)
  * with each of a fixed list of candidate plane counts plus the model's
- * choice, timed with CUDA events on the handle's stream, and keeps the
- * fastest, which it returns in *planes (may be NULL).  The handle then holds
- * that tiling as if set with fdtd_llg_set_tiling.  Synchronises the stream.
+ * choice, first at the tile width of fewest padded cells and then at the
+ * other width, timed with CUDA events on the handle's stream, and keeps the
+ * fastest (plane count, width); the plane count is returned in *planes (may
+ * be NULL), the width by fdtd_llg_get_tile_width.  The handle then holds
+ * that tiling as if set with fdtd_llg_set_tiling and fdtd_llg_set_tile_width.
+ * Synchronises the stream.
  * Errors: FDTD_E_INVAL (trial_steps < 1, a member handle), those of
  * fdtd_llg_step. */
 int fdtd_llg_autotune(fdtd_llg_t h, int32_t trial_steps, int32_t *planes);

@@ -71,6 +71,8 @@ struct Sim {
     bool stab = false;                // every class table small enough for shared memory
     int tiling = 0;                   // requested z-planes per sweep task (0: model)
     int planes = 0;                   // z-planes per sweep task in effect
+    int tile_width = 0;               // requested sweep tile width (0: fewest padded cells, 32, 64)
+    int sx = 64;                      // sweep tile width in effect (Tile<sx>)
     bool cls16 = false;
     bool dirty = true;
     int nsm = 148;
@@ -673,12 +675,15 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-// The field kernel's TMA boxes: per buffer, H (components 3-5) on kHBX x kHBY
-// and E (components 0-2) on kEBX x kEBY of one z-plane, over a 4-D view
-// (x, y, z, component) of the six arrays; the class ids on kCBX x kEBY.  Reads
-// outside (nx, ny, nz) return zeros.
-static int encode_tensor_maps(fdtd_llg_t h, const Instance &I, Inst &d)
+// The field kernel's TMA boxes for tile width sx: per buffer, H (components
+// 3-5) on HBX x HBY and E (components 0-2) on EBX x EBY of one z-plane, over a
+// 4-D view (x, y, z, component) of the six arrays; the class ids on CBX x EBY.
+// Reads outside (nx, ny, nz) return zeros.
+static int encode_tensor_maps(fdtd_llg_t h, const Instance &I, Inst &d, int sx)
 {
+    const cuuint32_t hbx = sx == 32 ? Tile<32>::HBX : Tile<64>::HBX, hby = sx == 32 ? Tile<32>::HBY : Tile<64>::HBY;
+    const cuuint32_t ebx = sx == 32 ? Tile<32>::EBX : Tile<64>::EBX, eby = sx == 32 ? Tile<32>::EBY : Tile<64>::EBY;
+    const cuuint32_t cb8 = sx == 32 ? Tile<32>::CBX8 : Tile<64>::CBX8, cb16 = sx == 32 ? Tile<32>::CBX16 : Tile<64>::CBX16;
     auto enc = tensor_map_encoder();
     if (!enc) return fail(h, FDTD_E_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     const cuuint32_t es[4] = {1, 1, 1, 1};
@@ -686,7 +691,7 @@ static int encode_tensor_maps(fdtd_llg_t h, const Instance &I, Inst &d)
     for (int b = 0; b < 2; ++b) {
         const cuuint64_t dims[4] = {(cuuint64_t)I.nx, (cuuint64_t)I.ny, (cuuint64_t)I.nz, 6};
         const cuuint64_t strides[3] = {(cuuint64_t)I.px * 4, (cuuint64_t)I.px * I.ny * 4, nf * 4};
-        const cuuint32_t boxH[4] = {kHBX, kHBY, 1, 3}, boxE[4] = {kEBX, kEBY, 1, 3};
+        const cuuint32_t boxH[4] = {hbx, hby, 1, 3}, boxE[4] = {ebx, eby, 1, 3};
         CUresult r = enc(&d.tm[TM_H0 + b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, I.fields[b], dims, strides, boxH, es,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -699,12 +704,25 @@ static int encode_tensor_maps(fdtd_llg_t h, const Instance &I, Inst &d)
     const bool c16 = I.cls_bytes == 2;
     const cuuint64_t cdims[3] = {(cuuint64_t)I.nx, (cuuint64_t)I.ny, (cuuint64_t)I.nz};
     const cuuint64_t cstr[2] = {(cuuint64_t)I.px * I.cls_bytes, (cuuint64_t)I.px * I.ny * I.cls_bytes};
-    const cuuint32_t cbox[3] = {(cuuint32_t)(c16 ? kCBX16 : kCBX8), kEBY, 1};
+    const cuuint32_t cbox[3] = {c16 ? cb16 : cb8, eby, 1};
     const CUresult r = enc(&d.tm[TM_CLS], c16 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, I.cls,
                            cdims, cstr, cbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(h, FDTD_E_CUDA, "cuTensorMapEncodeTiled failed for the class ids");
     return FDTD_OK;
+}
+
+// Sweep tile width: the shape (64 x 8 or 32 x 16) that pads the instances'
+// x-y extents to fewer cells (64 on ties); lanes beyond the grid do no useful
+// work, so the padded count is the sweep's cost in lanes.
+static int choose_width(const Sim *S)
+{
+    long long p64 = 0, p32 = 0;
+    for (const Instance &I : S->inst) {
+        p64 += (long long)((I.nx + 63) / 64) * 64 * ((I.ny + Tile<64>::Y - 1) / Tile<64>::Y) * Tile<64>::Y * I.nz;
+        p32 += (long long)((I.nx + 31) / 32) * 32 * ((I.ny + Tile<32>::Y - 1) / Tile<32>::Y) * Tile<32>::Y * I.nz;
+    }
+    return p32 < p64 ? 32 : 64;
 }
 
 // Plane count of the sweep tasks from a cost model.  A task of P planes
@@ -724,7 +742,8 @@ static int model_planes(const Sim *S, int slots)
         int maxt = 0;
         for (const Instance &I : S->inst) {
             const int pk = std::min(P, I.nz), nch = (I.nz + pk - 1) / pk;
-            const double cols = (double)((I.nx + kSX - 1) / kSX) * ((I.ny + kSY - 1) / kSY);
+            const int sy = kST / (S->sx / 2);
+            const double cols = (double)((I.nx + S->sx - 1) / S->sx) * ((I.ny + sy - 1) / sy);
             items += cols * (I.nz + 1.4 * nch);
             maxt = std::max(maxt, pk);
         }
@@ -739,7 +758,8 @@ static int upload_descriptors(fdtd_llg_t h)
     Sim *S = h->sim;
     if (!S->dirty) return FDTD_OK;
     CKR(h, cudaStreamSynchronize(S->stream));
-    S->planes = S->tiling > 0 ? S->tiling : model_planes(S, S->nsm * std::max(1, step_blocks_per_sm(false, true)));
+    S->sx = S->tile_width ? S->tile_width : choose_width(S);
+    S->planes = S->tiling > 0 ? S->tiling : model_planes(S, S->nsm * std::max(1, step_blocks_per_sm(false, true, S->sx)));
     std::vector<Inst> hi(S->inst.size());
     std::vector<int> tile_inst, ftile_inst;
     std::vector<MagComp> comps;
@@ -788,7 +808,8 @@ static int upload_descriptors(fdtd_llg_t h)
         const int nt = d.ntx * d.nty * d.ntz;
         for (int t = 0; t < nt; ++t) tile_inst.push_back((int)ii);
         d.fkc = std::min(I.nz, S->planes);
-        d.fntx = (I.nx + kSX - 1) / kSX; d.fnty = (I.ny + kSY - 1) / kSY; d.fntz = (I.nz + d.fkc - 1) / d.fkc;
+        const int sy = kST / (S->sx / 2);
+        d.fntx = (I.nx + S->sx - 1) / S->sx; d.fnty = (I.ny + sy - 1) / sy; d.fntz = (I.nz + d.fkc - 1) / d.fkc;
         d.ftile_off = (int)ftile_inst.size();
         const int nft = d.fntx * d.fnty * d.fntz;
         for (int t = 0; t < nft; ++t) ftile_inst.push_back((int)ii);
@@ -822,7 +843,7 @@ static int upload_descriptors(fdtd_llg_t h)
         }
     // TMA descriptors of every instance, after the class width is settled
     for (size_t ii = 0; ii < S->inst.size(); ++ii) {
-        const int rc = encode_tensor_maps(h, S->inst[ii], hi[ii]);
+        const int rc = encode_tensor_maps(h, S->inst[ii], hi[ii], S->sx);
         if (rc) return rc;
     }
     S->dfree(S->d_insts); S->dfree(S->d_tile_inst); S->dfree(S->d_ftile_inst); S->dfree(S->d_comps); S->dfree(S->d_part);
@@ -877,7 +898,8 @@ static LaunchSet launch_set(Sim *S)
     L.nftiles = S->nftiles;
     // persistent field-sweep CTAs: as many as fit at once (late ones, queued
     // behind the magnet CTAs, take what is left of the task counter)
-    L.nfblocks = std::max(1, std::min(S->nftiles, S->nsm * std::max(1, step_blocks_per_sm(S->cls16, S->stab))));
+    L.sx = S->sx;
+    L.nfblocks = std::max(1, std::min(S->nftiles, S->nsm * std::max(1, step_blocks_per_sm(S->cls16, S->stab, S->sx))));
     L.src = S->cur;
     L.dst = 1 - S->cur;
     L.cls16 = S->cls16;
@@ -1306,6 +1328,25 @@ extern "C" int fdtd_llg_set_tiling(fdtd_llg_t h, int32_t planes)
     return FDTD_OK;
 }
 
+extern "C" int fdtd_llg_set_tile_width(fdtd_llg_t h, int32_t width)
+{
+    if (!h || !h->sim) return fail(h, FDTD_E_INVAL, "null handle");
+    if (!h->owns) return fail(h, FDTD_E_INVAL, "set the tile width on the batch handle, not a member");
+    if (width != 0 && width != 32 && width != 64) return fail(h, FDTD_E_INVAL, "tile width must be 0, 32 or 64");
+    if (width != h->sim->tile_width) {
+        h->sim->tile_width = width;
+        h->sim->dirty = true;
+    }
+    return FDTD_OK;
+}
+
+extern "C" int fdtd_llg_get_tile_width(fdtd_llg_t h, int32_t *width)
+{
+    if (!h || !h->sim || !width) return fail(h, FDTD_E_INVAL, "null handle or output");
+    *width = h->sim->dirty ? 0 : h->sim->sx;
+    return FDTD_OK;
+}
+
 extern "C" int fdtd_llg_get_tiling(fdtd_llg_t h, int32_t *planes)
 {
     if (!h || !h->sim || !planes) return fail(h, FDTD_E_INVAL, "null handle or output");
@@ -1319,10 +1360,12 @@ extern "C" int fdtd_llg_autotune(fdtd_llg_t h, int32_t trial_steps, int32_t *pla
     if (!h->owns) return fail(h, FDTD_E_INVAL, "autotune the batch handle, not a member");
     if (trial_steps < 1) return fail(h, FDTD_E_INVAL, "trial_steps must be >= 1");
     Sim *S = h->sim;
-    const int keep = S->tiling;
+    const int keep = S->tiling, keep_w = S->tile_width;
     int rc = fdtd_llg_set_tiling(h, 0);
+    if (!rc) rc = fdtd_llg_set_tile_width(h, 0);
     if (!rc) rc = fdtd_llg_step(h, 1);   // start-up half-push and descriptors
     if (rc) return rc;
+    const int w0 = S->sx;
     std::vector<int> cand = {S->planes, 8, 12, 16, 24, 32, 48, 64};
     int maxnz = 1;
     for (const Instance &I : S->inst) maxnz = std::max(maxnz, I.nz);
@@ -1332,28 +1375,36 @@ extern "C" int fdtd_llg_autotune(fdtd_llg_t h, int32_t trial_steps, int32_t *pla
     cudaEvent_t e0, e1;
     CKR(h, cudaEventCreate(&e0));
     CKR(h, cudaEventCreate(&e1));
-    int best = cand[0];
+    int best = cand[0], best_w = w0;
     float best_ms = -1.f;
-    for (int c : cand) {
-        rc = fdtd_llg_set_tiling(h, c);
-        if (!rc) rc = fdtd_llg_step(h, 1);   // upload the new descriptors outside the timing
-        if (rc) break;
-        cudaEventRecord(e0, S->stream);
-        rc = fdtd_llg_step(h, trial_steps);
-        if (rc) break;
-        cudaEventRecord(e1, S->stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(h, FDTD_E_CUDA, "autotune timing failed"); break; }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (best_ms < 0.f || ms < best_ms) { best_ms = ms; best = c; }
+    // every plane count with the width of fewest padded cells, then the other
+    // width with the same counts
+    for (int wi = 0; wi < 2 && !rc; ++wi) {
+        const int width = wi == 0 ? w0 : (w0 == 64 ? 32 : 64);
+        for (int c : cand) {
+            rc = fdtd_llg_set_tiling(h, c);
+            if (!rc) rc = fdtd_llg_set_tile_width(h, width);
+            if (!rc) rc = fdtd_llg_step(h, 1);   // upload the new descriptors outside the timing
+            if (rc) break;
+            cudaEventRecord(e0, S->stream);
+            rc = fdtd_llg_step(h, trial_steps);
+            if (rc) break;
+            cudaEventRecord(e1, S->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(h, FDTD_E_CUDA, "autotune timing failed"); break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (best_ms < 0.f || ms < best_ms) { best_ms = ms; best = c; best_w = width; }
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) {
         fdtd_llg_set_tiling(h, keep);
+        fdtd_llg_set_tile_width(h, keep_w);
         return rc;
     }
     rc = fdtd_llg_set_tiling(h, best);
+    if (!rc) rc = fdtd_llg_set_tile_width(h, best_w);
     if (planes) *planes = best;
     return rc;
 }

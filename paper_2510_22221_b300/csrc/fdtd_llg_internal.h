@@ -20,26 +20,40 @@ constexpr int kMaxMagMat = 16;
 // each thread marching kKC planes in z.
 constexpr int kTX = 32, kTY = 8, kKC = 16;
 
-// Fused step kernel: one CTA of kST threads per column task of kSX x kSY
-// cells x fkc planes (the host picks fkc; kSZ is the fallback), marching the
-// task in z.  Each z-plane arrives by TMA in one stage of a kNS-deep
-// shared-memory ring: H on
-// the tile extended by one cell on the low x/y sides (box kHBX x kHBY, x
-// starting 4 cells low so that the copy stays 16-byte aligned), E^n and the
-// class ids on the tile extended by one cell on the high x/y sides.  E^{n+1}
-// overwrites E^n in place.  A stage stays live for two planes (as plane k and
-// then as plane k-1), so kNS - 2 planes are in flight while one is computed.
+// Fused step kernel: persistent CTAs of kST threads take column tasks of
+// SX x SY cells x fkc planes (the host picks fkc; kSZ is the fallback) and
+// march them in z.  Each z-plane arrives by TMA in one stage of a kNS-deep
+// shared-memory ring: H on the tile extended by one cell on the low x/y sides
+// (box HBX x HBY, x starting 4 cells low so that the copy stays 16-byte
+// aligned), E^n and the class ids on the tile extended by one cell on the high
+// x/y sides.  E^{n+1} overwrites E^n in place.  A stage stays live for two
+// planes (as plane k and then as plane k-1), so kNS - 2 planes are in flight
+// while one is computed.  Two tile shapes, 64 x 8 and 32 x 16 (each lane owns
+// a cell pair), chosen per handle: the narrow one wastes fewer lanes on grids
+// whose x extent is just above a multiple of 64.  Their boxes hold the same
+// number of values, so both share one stage layout.
 constexpr int kSX = 64, kSY = 8, kSZ = 16, kST = 256, kNS = 4;
 constexpr int kSW = kST / 32;   // warps of a sweep CTA (one energy partial each per task)
-constexpr int kHBX = kSX + 8, kHBY = kSY + 2, kHC = kHBX * kHBY;   // H box, one component
-constexpr int kEBX = kSX + 4, kEBY = kSY + 1, kEC = kEBX * kEBY;   // E box, one component
-constexpr int kCBX8 = kSX + 16, kCBX16 = kSX + 8;                  // class box width (u8 / u16)
+template <int SX>
+struct Tile {
+    static constexpr int LPR = SX / 2;                 // lanes per tile row (one cell pair each)
+    static constexpr int Y = kST / LPR;                // rows: 8 (SX 64) or 16 (SX 32)
+    static constexpr int HBX = SX + 8, HBY = Y + 2, HC = HBX * HBY;   // H box, one component
+    static constexpr int EBX = SX + 4, EBY = Y + 1, EC = EBX * EBY;   // E box, one component
+    static constexpr int CBX8 = SX + 16, CBX16 = SX + 8;              // class box width (u8 / u16)
+};
+static_assert(Tile<32>::HC == Tile<64>::HC && Tile<32>::EC == Tile<64>::EC, "one stage layout for both shapes");
+constexpr int kHBX = Tile<kSX>::HBX, kHBY = Tile<kSX>::HBY, kHC = Tile<kSX>::HC;
+constexpr int kEBX = Tile<kSX>::EBX, kEBY = Tile<kSX>::EBY, kEC = Tile<kSX>::EC;
 constexpr int kStageH = 3 * kHC * 4;                               // 8640 B
 constexpr int kStageE = 3 * kEC * 4;                               // 7344 B
 constexpr int kStageHOff = 0;
 constexpr int kStageEOff = (kStageH + 127) / 128 * 128;
 constexpr int kStageCOff = kStageEOff + (kStageE + 127) / 128 * 128;
-constexpr int kStageBytes = kStageCOff + (kCBX16 * kEBY * 2 + 127) / 128 * 128;
+constexpr int kClsMaxBytes = Tile<32>::CBX16 * Tile<32>::EBY * 2 > Tile<64>::CBX16 * Tile<64>::EBY * 2
+                                 ? Tile<32>::CBX16 * Tile<32>::EBY * 2
+                                 : Tile<64>::CBX16 * Tile<64>::EBY * 2;
+constexpr int kStageBytes = kStageCOff + (kClsMaxBytes + 127) / 128 * 128;
 // Class tables of at most kTabMax entries are staged in shared memory.
 constexpr int kTabMax = 64;
 
@@ -239,6 +253,7 @@ struct LaunchSet {
     int llg_max_iter, llg_fixed_iter;
     int energy;
     bool stab;                          // every instance's class table fits kTabMax
+    int sx;                             // sweep tile width: 64 (64 x 8 tiles) or 32 (32 x 16)
     int rec;                            // magnet kernel writes its tape (adjoint recomputation)
     long long rec_n0;                   // step of tape slot 0
     int rec_slots;                      // slots of the tape
@@ -258,7 +273,7 @@ cudaError_t launch_step(const LaunchSet &L, cudaStream_t s, cudaEvent_t *prof);
 // a run of steps ends.
 cudaError_t launch_energy_flush(const LaunchSet &L, cudaStream_t s);
 int h_half_blocks_per_sm(bool cls16);
-int step_blocks_per_sm(bool cls16, bool stab);
+int step_blocks_per_sm(bool cls16, bool stab, int sx);
 
 // ------------------------------------------------------------- adjoint
 // Device pointers of one reverse sweep (adjoint.cu), single instance.

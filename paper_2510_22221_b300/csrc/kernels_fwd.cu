@@ -694,12 +694,12 @@ __device__ __forceinline__ void cls2(const uint16_t *p, int &c0, int &c1)
     c1 = (int)(v >> 16);
 }
 
-// One CTA per task: column (tx, ty) of kSX x kSY cells, planes [k0, k1).  The
-// CTA walks the items k = k0-1 (H only, for the curl of plane k0), k0, ..., k1
-// (the plane above, for E^{n+1} there; zeros beyond the grid).  Item q lives
-// in stage q % kNS.  Warp w owns row y = w of the tile and each lane the cell
-// pair (x, x+1), x = 2 lane, so shared-memory and global accesses move float2
-// pairs and x neighbours come from the pair itself.  Per item: E^{n+1} of
+// Persistent CTAs drawing tasks: column (tx, ty) of SX x SY cells (Tile<SX>),
+// planes [k0, k1).  The CTA walks the items k = k0-1 (H only, for the curl of
+// plane k0), k0, ..., k1 (the plane above, for E^{n+1} there; zeros beyond the
+// grid).  Item q lives in stage q % kNS.  Each tile row is SX/2 lanes, each
+// lane owning the cell pair (x, x+1), so shared-memory and global accesses
+// move float2 pairs and x neighbours come from the pair itself.  Per item: E^{n+1} of
 // plane k at the tile's own cells, one barrier, then H of plane k-1 and
 // E^{n+1} of plane k at the halo edges that the next item's H update reads (Ex
 // and Ez of the row above the tile, Ey and Ez of the column beyond it).  After
@@ -707,7 +707,7 @@ __device__ __forceinline__ void cls2(const uint16_t *p, int &c0, int &c1)
 // item q + kNS - 2.  The tensor maps zero-fill everything outside the grid and
 // class 0 has zero coefficients, so cells beyond the far walls get E^{n+1} = 0
 // and H = 0 without a branch.
-template <typename ClsT, bool STAB>
+template <typename ClsT, bool STAB, int SX>
 __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
 {
     extern __shared__ __align__(128) unsigned char stg[];
@@ -715,9 +715,12 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
     __shared__ float4 stab[STAB ? 3 * kTabMax : 1];
     __shared__ double sred[kST / 32];
     __shared__ int s_last, s_abort, s_task;
-    constexpr int CBX = sizeof(ClsT) == 1 ? kCBX8 : kCBX16;
-    constexpr unsigned kClsBytes = CBX * kEBY * sizeof(ClsT);
-    static_assert(kST == 32 * kSY && kSX == 64, "one warp per tile row, one cell pair per lane");
+    using TL = Tile<SX>;
+    constexpr int SY = TL::Y, LPR = TL::LPR, HBX = TL::HBX, HC = TL::HC, EBX = TL::EBX, EBY = TL::EBY, EC = TL::EC;
+    constexpr int CBX = sizeof(ClsT) == 1 ? TL::CBX8 : TL::CBX16;
+    constexpr unsigned kClsBytes = CBX * EBY * sizeof(ClsT);
+    static_assert((SX == 64 || SX == 32) && LPR * SY == kST && kClsBytes <= (unsigned)(kStageBytes - kStageCOff),
+                  "one cell pair per lane; the class box fits its stage area");
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const long long n = *(volatile long long *)&L.ctl->step;
     if (tid == 0) {
@@ -754,7 +757,7 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
     const int nx = I->nx, ny = I->ny, nz = I->nz, px = I->px;
     const unsigned plane = (unsigned)I->plane;
     const long long fs = I->fstride;
-    const int i0 = tx * kSX, j0 = ty * kSY, k0 = tz * I->fkc;
+    const int i0 = tx * SX, j0 = ty * SY, k0 = tz * I->fkc;
     const int k1 = min(k0 + I->fkc, nz);
     const int nitems = k1 - k0 + 2;
     const float4 *__restrict__ ctab = I->ctab;
@@ -801,11 +804,11 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
     unsigned smask = 0, pmask = 0;
     for (int s = 0; s < I->nsrc; ++s) {
         const int si = I->src[s][1] - i0, sj = I->src[s][2] - j0;
-        if (si >= 0 && si <= kSX && sj >= 0 && sj <= kSY) smask |= 1u << s;
+        if (si >= 0 && si <= SX && sj >= 0 && sj <= SY) smask |= 1u << s;
     }
     for (int p = 0; p < I->nprobe; ++p) {
         const int pi = I->probe[p][0] - i0, pj = I->probe[p][1] - j0;
-        if (pi >= 0 && pi < kSX && pj >= 0 && pj < kSY && I->probe[p][2] >= k0 && I->probe[p][2] < k1) pmask |= 1u << p;
+        if (pi >= 0 && pi < SX && pj >= 0 && pj < SY && I->probe[p][2] >= k0 && I->probe[p][2] < k1) pmask |= 1u << p;
     }
     const double tn = ((double)n + 0.5) * I->dt;
     // source current (FP64 time evaluation) subtracted from one curl component
@@ -821,15 +824,15 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
     auto probe_row = [&](int pp) { return I->probe_buf + ((long long)(n % I->cap) * I->nprobe + pp) * 9; };
 
     // this thread's cells: (x, y), (x+1, y); output pointers per component
-    const int x = 2 * lane, y = w;
+    const int x = 2 * (lane % LPR), y = w * (32 / LPR) + lane / LPR;
     const int gi = i0 + x, gj = j0 + y;
     const bool in = gi < nx && gj < ny;   // gi + 1 < px always: the pair stays in the padded row
     const unsigned ob = (unsigned)gj * (unsigned)px + (unsigned)gi;
     float *const F0 = I->F[L.dst][0];
     float *const Fx = F0, *const Fy = F0 + fs, *const Fz = F0 + 2 * fs;
     float *const Gx = F0 + 3 * fs, *const Gy = F0 + 4 * fs, *const Gz = F0 + 5 * fs;
-    const int hp = (y + 1) * kHBX + x + 4;   // (x, y) in the H box
-    const int ep = y * kEBX + x;             // (x, y) in the E box
+    const int hp = (y + 1) * HBX + x + 4;   // (x, y) in the H box
+    const int ep = y * EBX + x;             // (x, y) in the E box
     __syncthreads();
 
     float acc = 0.f, acc_c = 0.f;   // energy of this thread's cells, compensated
@@ -854,16 +857,16 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
         float2 nHX, nHY, nHZ, nEX, nEY, nEZ;   // this plane's values of the own cells
         if (q == 0) {
             nHX = ld2(Hc + hp);
-            nHY = ld2(Hc + kHC + hp);
-            nHZ = ld2(Hc + 2 * kHC + hp);
+            nHY = ld2(Hc + HC + hp);
+            nHZ = ld2(Hc + 2 * HC + hp);
             nEX = nEY = nEZ = make_float2(0.f, 0.f);
         } else {
             // ---- E^{n+1} of plane k at the tile's cells, in place over E^n
-            const float2 HX = ld2(Hc + hp), HY = ld2(Hc + kHC + hp), HZ = ld2(Hc + 2 * kHC + hp);
-            const float2 HXj = ld2(Hc + hp - kHBX), HZj = ld2(Hc + 2 * kHC + hp - kHBX);
-            const float hyi = Hc[kHC + hp - 1], hzi = Hc[2 * kHC + hp - 1];
+            const float2 HX = ld2(Hc + hp), HY = ld2(Hc + HC + hp), HZ = ld2(Hc + 2 * HC + hp);
+            const float2 HXj = ld2(Hc + hp - HBX), HZj = ld2(Hc + 2 * HC + hp - HBX);
+            const float hyi = Hc[HC + hp - 1], hzi = Hc[2 * HC + hp - 1];
             const float2 HXk = cHX, HYk = cHY;
-            const float2 EX = ld2(Ec + ep), EY = ld2(Ec + kEC + ep), EZ = ld2(Ec + 2 * kEC + ep);
+            const float2 EX = ld2(Ec + ep), EY = ld2(Ec + EC + ep), EZ = ld2(Ec + 2 * EC + ep);
             int c0, c1;
             cls2(Cc + y * CBX + x, c0, c1);
             float cx0 = curl2(HZ.x, HZj.x, idy, HY.x, HYk.x, idz);
@@ -880,8 +883,8 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
             const float ex0 = e_next(A0.x, EX.x, B0.x, cx0), ey0 = e_next(A0.y, EY.x, B0.y, cy0), ez0 = e_next(A0.z, EZ.x, B0.z, cz0);
             const float ex1 = e_next(A1.x, EX.y, B1.x, cx1), ey1 = e_next(A1.y, EY.y, B1.y, cy1), ez1 = e_next(A1.z, EZ.y, B1.z, cz1);
             st2(Ec + ep, ex0, ex1);
-            st2(Ec + kEC + ep, ey0, ey1);
-            st2(Ec + 2 * kEC + ep, ez0, ez1);
+            st2(Ec + EC + ep, ey0, ey1);
+            st2(Ec + 2 * EC + ep, ez0, ez1);
             nHX = HX;
             nHY = HY;
             nHZ = HZ;
@@ -920,8 +923,8 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
             const float *Ep = reinterpret_cast<const float *>(prv + kStageEOff);
             const ClsT *Cp = reinterpret_cast<const ClsT *>(prv + kStageCOff);
             const float2 EX = cEX, EY = cEY, EZ = cEZ;
-            const float2 EXj = ld2(Ep + ep + kEBX), EZj = ld2(Ep + 2 * kEC + ep + kEBX);
-            const float eyi = Ep[kEC + ep + 2], ezi = Ep[2 * kEC + ep + 2];
+            const float2 EXj = ld2(Ep + ep + EBX), EZj = ld2(Ep + 2 * EC + ep + EBX);
+            const float eyi = Ep[EC + ep + 2], ezi = Ep[2 * EC + ep + 2];
             const float2 EXk = nEX, EYk = nEY;
             const float2 HX = cHX, HY = cHY, HZ = cHZ;
             const float cx0 = curl2(EZj.x, EZ.x, idy, EYk.x, EY.x, idz);
@@ -976,56 +979,59 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
             }
         }
         // ---- E^{n+1} of plane k at the halo edges read by the next item:
-        // warp 0 Ex and warp 1 Ez of row kSY (pairs), warp 2 Ey (lanes 0-7)
-        // and Ez (lanes 8-15) of column kSX
-        if (q > 0 && q + 1 < nitems && (w < 2 || (w == 2 && lane < 16))) {
-            if (w < 2) {
-                const int hr = (kSY + 1) * kHBX + x + 4, er = kSY * kEBX + x;
+        // threads [0, SX) Ex and Ez of row SY (cell pairs), the next 2 SY Ey
+        // and Ez of column SX (64 x 8: warps 0, 1 and half of warp 2; 32 x 16:
+        // warps 0 and 1)
+        if (q > 0 && q + 1 < nitems && tid < SX + 2 * SY) {
+            if (tid < SX) {
+                const int hx = 2 * (tid % LPR);   // pair of row SY
+                const int hr = (SY + 1) * HBX + hx + 4, er = SY * EBX + hx;
+                const int hgi = i0 + hx;
                 int c0, c1;
-                cls2(Cc + kSY * CBX + x, c0, c1);
+                cls2(Cc + SY * CBX + hx, c0, c1);
                 const float4 A0 = tab(3 * c0), B0 = tab(3 * c0 + 1), A1 = tab(3 * c1), B1 = tab(3 * c1 + 1);
-                if (w == 0) {
-                    const float2 HZ = ld2(Hc + 2 * kHC + hr), HZj = ld2(Hc + 2 * kHC + hr - kHBX);
-                    const float2 HY = ld2(Hc + kHC + hr), HYk = ld2(Hp + kHC + hr);
+                if (tid < LPR) {
+                    const float2 HZ = ld2(Hc + 2 * HC + hr), HZj = ld2(Hc + 2 * HC + hr - HBX);
+                    const float2 HY = ld2(Hc + HC + hr), HYk = ld2(Hp + HC + hr);
                     float cx0 = curl2(HZ.x, HZj.x, idy, HY.x, HYk.x, idz), cx1 = curl2(HZ.y, HZj.y, idy, HY.y, HYk.y, idz);
                     if (smask) {
                         float d0 = 0.f, d1 = 0.f;
-                        add_src(gi, j0 + kSY, k, cx0, d0, d1);
-                        add_src(gi + 1, j0 + kSY, k, cx1, d0, d1);
+                        add_src(hgi, j0 + SY, k, cx0, d0, d1);
+                        add_src(hgi + 1, j0 + SY, k, cx1, d0, d1);
                     }
                     const float2 EN = ld2(Ec + er);
                     st2(Ec + er, e_next(A0.x, EN.x, B0.x, cx0), e_next(A1.x, EN.y, B1.x, cx1));
                 } else {
-                    const float2 HY = ld2(Hc + kHC + hr), HX = ld2(Hc + hr), HXj = ld2(Hc + hr - kHBX);
-                    const float hyi = Hc[kHC + hr - 1];
+                    const float2 HY = ld2(Hc + HC + hr), HX = ld2(Hc + hr), HXj = ld2(Hc + hr - HBX);
+                    const float hyi = Hc[HC + hr - 1];
                     float cz0 = curl2(HY.x, hyi, idx, HX.x, HXj.x, idy), cz1 = curl2(HY.y, HY.x, idx, HX.y, HXj.y, idy);
                     if (smask) {
                         float d0 = 0.f, d1 = 0.f;
-                        add_src(gi, j0 + kSY, k, d0, d1, cz0);
-                        add_src(gi + 1, j0 + kSY, k, d0, d1, cz1);
+                        add_src(hgi, j0 + SY, k, d0, d1, cz0);
+                        add_src(hgi + 1, j0 + SY, k, d0, d1, cz1);
                     }
-                    const float2 EN = ld2(Ec + 2 * kEC + er);
-                    st2(Ec + 2 * kEC + er, e_next(A0.z, EN.x, B0.z, cz0), e_next(A1.z, EN.y, B1.z, cz1));
+                    const float2 EN = ld2(Ec + 2 * EC + er);
+                    st2(Ec + 2 * EC + er, e_next(A0.z, EN.x, B0.z, cz0), e_next(A1.z, EN.y, B1.z, cz1));
                 }
             } else {
-                const int yc = lane & 7;
-                const int hc = (yc + 1) * kHBX + kSX + 4, ec = yc * kEBX + kSX;
-                const int c = (int)Cc[yc * CBX + kSX];
+                const int cid = tid - SX, yc = cid % SY;   // cid < SY: Ey, else Ez of row yc
+                const int hc = (yc + 1) * HBX + SX + 4, ec = yc * EBX + SX;
+                const int c = (int)Cc[yc * CBX + SX];
                 const float4 A = tab(3 * c), B = tab(3 * c + 1);
-                if (lane < 8) {
-                    float cy = curl2(Hc[hc], Hp[hc], idz, Hc[2 * kHC + hc], Hc[2 * kHC + hc - 1], idx);
+                if (cid < SY) {
+                    float cy = curl2(Hc[hc], Hp[hc], idz, Hc[2 * HC + hc], Hc[2 * HC + hc - 1], idx);
                     if (smask) {
                         float d0 = 0.f, d1 = 0.f;
-                        add_src(i0 + kSX, j0 + yc, k, d0, cy, d1);
+                        add_src(i0 + SX, j0 + yc, k, d0, cy, d1);
                     }
-                    Ec[kEC + ec] = e_next(A.y, Ec[kEC + ec], B.y, cy);
+                    Ec[EC + ec] = e_next(A.y, Ec[EC + ec], B.y, cy);
                 } else {
-                    float cz = curl2(Hc[kHC + hc], Hc[kHC + hc - 1], idx, Hc[hc], Hc[hc - kHBX], idy);
+                    float cz = curl2(Hc[HC + hc], Hc[HC + hc - 1], idx, Hc[hc], Hc[hc - HBX], idy);
                     if (smask) {
                         float d0 = 0.f, d1 = 0.f;
-                        add_src(i0 + kSX, j0 + yc, k, d0, d1, cz);
+                        add_src(i0 + SX, j0 + yc, k, d0, d1, cz);
                     }
-                    Ec[2 * kEC + ec] = e_next(A.z, Ec[2 * kEC + ec], B.z, cz);
+                    Ec[2 * EC + ec] = e_next(A.z, Ec[2 * EC + ec], B.z, cz);
                 }
             }
         }
@@ -1084,14 +1090,27 @@ int h_half_blocks_per_sm(bool cls16)
 
 static constexpr int kStepSmem = kNS * kStageBytes;
 
+using StepFn = void (*)(LaunchSet);
+// The sweep instantiation for a class width, a class table in shared memory
+// or not, and a tile width (64 or 32).
+static StepFn step_fn(bool cls16, bool stab, int sx)
+{
+    if (sx == 32) {
+        if (cls16) return stab ? step_kernel<uint16_t, true, 32> : step_kernel<uint16_t, false, 32>;
+        return stab ? step_kernel<uint8_t, true, 32> : step_kernel<uint8_t, false, 32>;
+    }
+    if (cls16) return stab ? step_kernel<uint16_t, true, 64> : step_kernel<uint16_t, false, 64>;
+    return stab ? step_kernel<uint8_t, true, 64> : step_kernel<uint8_t, false, 64>;
+}
+
 static cudaError_t step_attrs()
 {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(step_kernel<uint8_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStepSmem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<uint8_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStepSmem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<uint16_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStepSmem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<uint16_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStepSmem);
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < 8 && e == cudaSuccess; ++q)
+        e = cudaFuncSetAttribute(step_fn(q & 1, (q >> 1) & 1, (q & 4) ? 32 : 64), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kStepSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(mag_kernel<true, uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMagSmemMax);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(mag_kernel<true, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMagSmemMax);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(mag_kernel<false, uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMagSmemMax);
@@ -1099,17 +1118,11 @@ static cudaError_t step_attrs()
     return e;
 }
 
-int step_blocks_per_sm(bool cls16, bool stab)
+int step_blocks_per_sm(bool cls16, bool stab, int sx)
 {
     if (step_attrs() != cudaSuccess) return 0;
     int nb = 0;
-    if (cls16) {
-        if (stab) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<uint16_t, true>, kST, kStepSmem);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<uint16_t, false>, kST, kStepSmem);
-    } else {
-        if (stab) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<uint8_t, true>, kST, kStepSmem);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<uint8_t, false>, kST, kStepSmem);
-    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_fn(cls16, stab, sx), kST, kStepSmem);
     return nb;
 }
 
@@ -1159,13 +1172,7 @@ cudaError_t launch_step(const LaunchSet &L, cudaStream_t s, cudaEvent_t *prof)
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = (L.ncomp && !prof) ? 1 : 0;
-    if (L.cls16) {
-        if (L.stab) e = cudaLaunchKernelEx(&cfg, step_kernel<uint16_t, true>, L);
-        else e = cudaLaunchKernelEx(&cfg, step_kernel<uint16_t, false>, L);
-    } else {
-        if (L.stab) e = cudaLaunchKernelEx(&cfg, step_kernel<uint8_t, true>, L);
-        else e = cudaLaunchKernelEx(&cfg, step_kernel<uint8_t, false>, L);
-    }
+    e = cudaLaunchKernelEx(&cfg, step_fn(L.cls16, L.stab, L.sx), L);
     if (e != cudaSuccess) return e;
     if (prof) cudaEventRecord(prof[1], s);
     return cudaGetLastError();

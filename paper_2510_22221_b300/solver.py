@@ -293,6 +293,15 @@ class FdtdLlg:
         """CUDA graphs for long step calls: 1 on, 0 off, -1 automatic."""
         check(_abi.load().fdtd_llg_set_graphs(self._h, int(mode)), self._h)
 
+    def set_tile_width(self, width: int):
+        """Sweep tile shape: 64 (64 x 8), 32 (32 x 16) or 0 (fewest padded cells)."""
+        check(_abi.load().fdtd_llg_set_tile_width(self._h, int(width)), self._h)
+
+    def get_tile_width(self) -> int:
+        w = C.c_int32()
+        check(_abi.load().fdtd_llg_get_tile_width(self._h, C.byref(w)), self._h)
+        return w.value
+
     def get_tiling(self) -> int:
         p = C.c_int32(0)
         check(_abi.load().fdtd_llg_get_tiling(self._h, C.byref(p)), self._h)

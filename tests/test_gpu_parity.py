@@ -304,19 +304,22 @@ def test_batch_equals_separate_runs_bitwise():
 
 @pytest.mark.parametrize("seed", [4, 5])
 def test_tiling_changes_no_field_or_probe_bit(seed):
-    """The z-planes per sweep task only regroup the work: fields, magnet state
-    and probe samples agree to the bit across tilings (the oracle comparisons
-    above run at the default tiling); the energy differs only by the order of
-    its partial sums."""
-    w = W.random_small(seed, nx=70, ny=19, nz=23, steps=30)
+    """The z-planes per sweep task and the tile shape (64 x 8 or 32 x 16) only
+    regroup the work: fields, magnet state and probe samples agree to the bit
+    across tilings (the oracle comparisons above run at the default tiling);
+    the energy differs only by the order of its partial sums."""
+    w = W.random_small(seed, nx=70, ny=30, nz=23, steps=30)
     runs = []
-    for planes in (0, 1, 5, 23, 64):
+    for planes, width in ((0, 0), (1, 64), (5, 32), (23, 64), (64, 32), (7, 64)):
         sim = pkg.from_workload(w, probe_capacity=64)
         sim.set_tiling(planes)
+        sim.set_tile_width(width)
         sim.step(30)
         sim.sync()
         runs.append(sim)
     assert runs[2].get_tiling() == 5 and runs[1].get_tiling() == 1
+    assert runs[0].get_tile_width() == 32   # 70 x 30: 96 x 32 padded cells per plane against 128 x 32
+    assert [r.get_tile_width() for r in runs[1:]] == [64, 32, 64, 32, 64]
     ref = runs[0]
     for sim in runs[1:]:
         for name in ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz", "dMx", "dMz", "Hx_wall", "Hz_wall"):
