@@ -179,6 +179,21 @@ int fdtd_llg_energy(fdtd_llg_t h, double *out, int64_t cap, int64_t *written);
  * fdtd_llg_sync. */
 int fdtd_llg_read_last(fdtd_llg_t h, double *probe_rows, double *energy);
 
+/* Streamed results: from the next step call on, every fdtd_llg_step (and
+ * fdtd_llg_run_checkpointed) of the handle's batch queues, on the handle's
+ * stream after its kernels, copies of its steps' probe rows and energies
+ * into these host rings: step n's rows at rows[(n % capacity) * nprobes * 9
+ * ...] (nprobes x 9 doubles, add order) and its energy at energy[n %
+ * capacity].  Nothing waits for them: they are complete once a synchronising
+ * call returns (fdtd_llg_sync, a read, an event recorded after the step
+ * call).  Steps older than probe_capacity at the end of a call are not
+ * copied.  The rings are caller-owned and must stay valid while streaming;
+ * page-locked memory keeps the copies asynchronous.  Either pointer may be
+ * NULL; both NULL stops streaming.  The call synchronises the stream (copies
+ * into earlier rings complete first).  Errors: FDTD_E_INVAL (batch handle,
+ * capacity < 1). */
+int fdtd_llg_stream_results(fdtd_llg_t h, double *rows, double *energy, int64_t capacity);
+
 /* Steps completed, and whether H and M are stored half a step ahead of E
  * (1 after the first step; get_field then returns H, M at (n + 1/2) dt). */
 int fdtd_llg_time_state(fdtd_llg_t h, int64_t *step, int32_t *h_half_ahead);

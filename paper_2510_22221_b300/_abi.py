@@ -79,6 +79,7 @@ SIGNATURES = {
     "fdtd_llg_read_last": (C.c_int, [_vp, _dp, _dp]),
     "fdtd_llg_set_tile_width": (C.c_int, [_vp, C.c_int32]),
     "fdtd_llg_get_tile_width": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
+    "fdtd_llg_stream_results": (C.c_int, [_vp, _dp, _dp, C.c_int64]),
     "fdtd_llg_adjoint_step": (C.c_int, [_vp, _dp, _dp, _dp]),
     "fdtd_llg_probe_spectrum": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_int32, C.c_int32,
                                          _dp]),

@@ -34,6 +34,9 @@ struct Instance {
     double *probe_buf = nullptr;
     int probe_alloc = -1;             // probes the probe ring was sized for
     double *energy_buf = nullptr;
+    // caller's host rings for streamed results (fdtd_llg_stream_results)
+    double *host_rows = nullptr, *host_energy = nullptr;
+    long long host_cap = 0;
     float *mbuf = nullptr;            // all regions' deviation m (bias frame)
     uint8_t *magmat = nullptr;        // all regions' material maps
     // host descriptions
@@ -942,6 +945,44 @@ static cudaError_t build_graph(Sim *S, LaunchSet L)
     return e;
 }
 
+// Queue on the stream the copies of steps [n0, n1)'s probe rows and energies
+// from the device rings into the instances' host rings (those that stream),
+// after everything queued so far; steps older than the device ring are gone.
+static cudaError_t stream_out(Sim *S, long long n0, long long n1)
+{
+    const long long dcap = S->cfg.probe_capacity;
+    for (Instance &I : S->inst) {
+        if (I.host_cap < 1) continue;
+        const long long np = (long long)I.probes.size();
+        for (long long st = std::max(n0, n1 - dcap); st < n1;) {
+            const long long ds = st % dcap, hs = st % I.host_cap;
+            const long long run = std::min({n1 - st, dcap - ds, I.host_cap - hs});
+            cudaError_t e = cudaSuccess;
+            if (I.host_rows && np)
+                e = cudaMemcpyAsync(I.host_rows + hs * np * 9, I.probe_buf + ds * np * 9, run * np * 9 * sizeof(double),
+                                    cudaMemcpyDeviceToHost, S->stream);
+            if (e == cudaSuccess && I.host_energy)
+                e = cudaMemcpyAsync(I.host_energy + hs, I.energy_buf + ds, run * sizeof(double), cudaMemcpyDeviceToHost,
+                                    S->stream);
+            if (e != cudaSuccess) return e;
+            st += run;
+        }
+    }
+    return cudaSuccess;
+}
+
+extern "C" int fdtd_llg_stream_results(fdtd_llg_t h, double *rows, double *energy, int64_t capacity)
+{
+    if (!is_member(h)) return fail(h, FDTD_E_INVAL, "stream_results needs an instance handle");
+    if ((rows || energy) && capacity < 1) return fail(h, FDTD_E_INVAL, "capacity must be >= 1");
+    Instance *I = inst_of(h);
+    CKR(h, cudaStreamSynchronize(h->sim->stream));   // copies queued into the previous rings are done
+    I->host_rows = rows;
+    I->host_energy = energy;
+    I->host_cap = (rows || energy) ? capacity : 0;
+    return FDTD_OK;
+}
+
 extern "C" int fdtd_llg_step(fdtd_llg_t h, int64_t nsteps)
 {
     if (!h || !h->sim) return fail(h, FDTD_E_INVAL, "null handle");
@@ -986,6 +1027,7 @@ extern "C" int fdtd_llg_step(fdtd_llg_t h, int64_t nsteps)
         S->cur ^= 1;
     }
     if (nsteps > 0) CKR(h, launch_energy_flush(L, S->stream));
+    if (nsteps > 0) CKR(h, stream_out(S, S->host_step, S->host_step + nsteps));
     S->host_step += nsteps;
     return FDTD_OK;
 }
@@ -1572,6 +1614,7 @@ extern "C" int fdtd_llg_run_checkpointed(fdtd_llg_t h, int64_t nsteps, int32_t i
             if (per_d) CKR(h, adj_record_design(L, Ad, (int)(n - S->tail0 + 1), S->cur, S->stream));
         }
         CKR(h, launch_energy_flush(L, S->stream));
+        CKR(h, stream_out(S, S->host_step, S->host_step + ns));
         S->host_step += ns;
     }
     S->adj_N = nsteps;

@@ -224,6 +224,33 @@ class FdtdLlg:
         check(lib.fdtd_llg_read_last(self._h, rows.ctypes.data_as(C.POINTER(C.c_double)), C.byref(e)), self._h)
         return rows[: self._probes], e.value
 
+    def stream_results(self, rows=None, energy=None):
+        """Stream every following step's probe rows and energy into host
+        rings: rows (capacity, nprobes, 9) and energy (capacity,), float64
+        numpy arrays or CPU torch tensors (page-locked ones keep the copies
+        asynchronous); step n goes to slot n % capacity, complete after the
+        next synchronising call.  No arguments stop streaming."""
+
+        def ptr(a):
+            if a is None:
+                return None, 0
+            if hasattr(a, "data_ptr"):
+                if a.dtype != __import__("torch").float64 or a.is_cuda or not a.is_contiguous():
+                    raise ValueError("host rings must be contiguous float64 CPU tensors")
+                return C.cast(a.data_ptr(), C.POINTER(C.c_double)), a.shape[0]
+            if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError("host rings must be contiguous float64 arrays")
+            return a.ctypes.data_as(C.POINTER(C.c_double)), a.shape[0]
+
+        pr, cr = ptr(rows)
+        pe, ce = ptr(energy)
+        if rows is not None and energy is not None and cr != ce:
+            raise ValueError("rows and energy rings need the same capacity")
+        if rows is not None and tuple(rows.shape[1:]) != (self._probes, 9):
+            raise ValueError("rows ring must be (capacity, nprobes, 9)")
+        check(_abi.load().fdtd_llg_stream_results(self._h, pr, pe, int(cr or ce)), self._h)
+        self._rings = (rows, energy)   # kept alive while the library writes into them
+
     def _shape(self, name):
         nx, ny, nz = self._dims
         return {"Hx_wall": (nz, ny), "Hy_wall": (nz, nx), "Hz_wall": (ny, nx)}.get(name, (nz, ny, nx))

@@ -279,6 +279,32 @@ def test_read_last_returns_the_newest_rows_and_energy():
     sim.destroy()
 
 
+def test_streamed_results_equal_the_device_rings():
+    import torch
+
+    w = W.random_small(9, steps=40)
+    sim = pkg.from_workload(w, probe_capacity=64)
+    cap = 7                                        # the host rings wrap
+    rows = torch.zeros((cap, len(w.probes), 9), dtype=torch.float64).pin_memory()
+    energy = torch.zeros(cap, dtype=torch.float64).pin_memory()
+    sim.stream_results(rows, energy)
+    for n in (1, 3, 10, 2, 1, 5):
+        sim.step(n)
+    sim.sync()
+    steps = 22
+    ref_e = sim.energy()
+    for n in range(steps - cap, steps):
+        assert energy[n % cap].item() == ref_e[n]
+        for p in range(len(w.probes)):
+            np.testing.assert_array_equal(rows[n % cap, p].numpy(), sim.probe(p)[n])
+    sim.stream_results()                           # stop: the rings keep their contents
+    before = energy.clone()
+    sim.step(3)
+    sim.sync()
+    assert torch.equal(energy, before)
+    sim.destroy()
+
+
 def test_batch_equals_separate_runs_bitwise():
     ws = [W.random_small(s, nx=9 + 7 * s, ny=10, nz=8 + s, steps=25) for s in range(3)]
     dims = [(x.nx, x.ny, x.nz) for x in ws]
