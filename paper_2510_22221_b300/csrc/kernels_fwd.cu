@@ -86,6 +86,9 @@ __device__ double source_value(const double *p, double t)
 // q, q + blockDim, ... in order and block_sum adds the threads in a fixed
 // tree, so the value is the same whichever CTA or kernel forms it.  Nothing
 // is done unless step m's partials are the pending ones.
+// B loads are in flight at a time (more in the flush kernel, fewer inside the
+// register-bound sweep); the order of the additions does not depend on B.
+template <int B>
 __device__ void reduce_energy(const LaunchSet &L, int ii, long long m, double *sred)
 {
     const int tid = threadIdx.x, nth = blockDim.x;
@@ -96,12 +99,12 @@ __device__ void reduce_energy(const LaunchSet &L, int ii, long long m, double *s
     const int s0 = I->ftile_off * kSW, s1 = (I->ftile_off + I->fntx * I->fnty * I->fntz) * kSW;
     double s = 0.0;
     int q = s0 + tid;
-    for (; q + 7 * nth < s1; q += 8 * nth) {   // eight loads in flight, added in slot order
-        double v[8];
+    for (; q + (B - 1) * nth < s1; q += B * nth) {   // B loads in flight, added in slot order
+        double v[B];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = ld_cg(pf + q + u * nth);
+        for (int u = 0; u < B; ++u) v[u] = ld_cg(pf + q + u * nth);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) s += v[u];
+        for (int u = 0; u < B; ++u) s += v[u];
     }
     for (; q < s1; q += nth) s += ld_cg(pf + q);
     for (int c = I->mag_off + tid; c < I->mag_off + I->nmag; c += nth) s += ld_cg(pm + c);
@@ -746,7 +749,7 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
     const int v = s_task;
     if (v >= nred + L.nftiles || s_abort) break;
     if (v < nred) {
-        reduce_energy(L, v, n - 1, sred);
+        reduce_energy<8>(L, v, n - 1, sred);
         __syncthreads();   // every thread has read s_task before thread 0 draws again
         continue;
     }
@@ -1061,7 +1064,7 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
 __global__ void __launch_bounds__(kST) energy_flush_kernel(LaunchSet L)
 {
     __shared__ double sred[kST / 32];
-    reduce_energy(L, blockIdx.x, *(volatile long long *)&L.ctl->epend, sred);
+    reduce_energy<32>(L, blockIdx.x, *(volatile long long *)&L.ctl->epend, sred);
 }
 
 __global__ void set_step_kernel(StepCtl *ctl, long long n)
