@@ -241,15 +241,15 @@ int fdtd_llg_set_graphs(fdtd_llg_t h, int32_t mode);
 /* The time step (s) shared by every instance of the handle's batch. */
 int fdtd_llg_get_dt(fdtd_llg_t h, double *dt);
 
-/* Tiling of the field sweep.  Each task of the sweep marches a column of
- * 64 x 8 cells through `planes` z-planes (clamped to each instance's nz), so
- * there are sum over instances of ceil(nx/64) ceil(ny/8) ceil(nz/planes)
- * tasks, drawn by persistent CTAs.  planes = 0 (the default) lets the library
- * choose from a cost model (the extra planes each task reads against the
- * tail of the task loop).  The tiling changes only the
- * order in which the energy partial sums are added: fields and probe samples
- * are the same to the bit.  Takes effect at the next step.  Errors:
- * FDTD_E_INVAL (planes < 0, or a member handle). */
+/* Tiling of the field sweep.  Each task of the sweep marches one column of
+ * the tile shape (fdtd_llg_set_tile_width) through `planes` z-planes (the
+ * last task of a column the rest); the tasks are drawn by persistent CTAs.
+ * planes = 0 (the default) lets the library choose from a cost model (each
+ * task also reads about 1.4 planes beyond its own, against the tail of the
+ * task loop).  The tiling changes only the order in which the energy partial
+ * sums are added: fields and probe samples are the same to the bit.  Takes
+ * effect at the next step.  Errors: FDTD_E_INVAL (planes < 0, or a member
+ * handle). */
 int fdtd_llg_set_tiling(fdtd_llg_t h, int32_t planes);
 
 /* Tile shape of the field sweep: width 64 (64 x 8 cells per task column) or

@@ -66,7 +66,7 @@ struct Sim {
     // device control and descriptors
     Inst *d_insts = nullptr;
     int *d_tile_inst = nullptr;
-    int *d_ftile_inst = nullptr;
+    int4 *d_ftile_inst = nullptr;      // sweep task records in claim order
     MagComp *d_comps = nullptr;
     StepCtl *d_ctl = nullptr;
     double *d_part = nullptr;         // part_e | part_h | part_m
@@ -728,12 +728,21 @@ static int choose_width(const Sim *S)
     return p32 < p64 ? 32 : 64;
 }
 
+// Columns (x-y tiles) of an instance at tile width sx.
+static int columns_of(const Instance &I, int sx)
+{
+    const int sy = kST / (sx / 2);
+    return ((I.nx + sx - 1) / sx) * ((I.ny + sy - 1) / sy);
+}
+
 // Plane count of the sweep tasks from a cost model.  A task of P planes
 // costs about P + 1.4 plane-times (the plane below, which only loads H, ~0.4,
 // and the extra E^{n+1} plane above, 1); `slots` CTAs drawing the tasks
 // finish after the total over the slots plus, on average, half the longest
 // task.  Fewer, longer tasks cut the per-task planes, shorter ones the tail;
 // the P with the smallest modelled time wins (the smallest on ties).
+// (Measured against it: a schedule of long tasks drawn first and short ones
+// last was 2 % slower on a 256 x 256 x 128 grid and within 3 % elsewhere.)
 static int model_planes(const Sim *S, int slots)
 {
     int best = kSZ, maxnz = 1;
@@ -745,9 +754,7 @@ static int model_planes(const Sim *S, int slots)
         int maxt = 0;
         for (const Instance &I : S->inst) {
             const int pk = std::min(P, I.nz), nch = (I.nz + pk - 1) / pk;
-            const int sy = kST / (S->sx / 2);
-            const double cols = (double)((I.nx + S->sx - 1) / S->sx) * ((I.ny + sy - 1) / sy);
-            items += cols * (I.nz + 1.4 * nch);
+            items += (double)columns_of(I, S->sx) * (I.nz + 1.4 * nch);
             maxt = std::max(maxt, pk);
         }
         const double t = items / sl + 0.5 * (maxt + 1.4);
@@ -764,7 +771,11 @@ static int upload_descriptors(fdtd_llg_t h)
     S->sx = S->tile_width ? S->tile_width : choose_width(S);
     S->planes = S->tiling > 0 ? S->tiling : model_planes(S, S->nsm * std::max(1, step_blocks_per_sm(false, true, S->sx)));
     std::vector<Inst> hi(S->inst.size());
-    std::vector<int> tile_inst, ftile_inst;
+    std::vector<int> tile_inst;
+    // sweep tasks of `planes` planes: energy slots per instance by column,
+    // then z; claim order plane band by plane band over all instances
+    struct TaskRec { int4 t; int band; };
+    std::vector<TaskRec> recs;
     std::vector<MagComp> comps;
     bool c16 = false;
     int vmax = 0, msmem = 0;
@@ -810,12 +821,22 @@ static int upload_descriptors(fdtd_llg_t h)
         d.tile_off = (int)tile_inst.size();
         const int nt = d.ntx * d.nty * d.ntz;
         for (int t = 0; t < nt; ++t) tile_inst.push_back((int)ii);
-        d.fkc = std::min(I.nz, S->planes);
-        const int sy = kST / (S->sx / 2);
-        d.fntx = (I.nx + S->sx - 1) / S->sx; d.fnty = (I.ny + sy - 1) / sy; d.fntz = (I.nz + d.fkc - 1) / d.fkc;
-        d.ftile_off = (int)ftile_inst.size();
-        const int nft = d.fntx * d.fnty * d.fntz;
-        for (int t = 0; t < nft; ++t) ftile_inst.push_back((int)ii);
+        {
+            const int sy = kST / (S->sx / 2);
+            const int fntx = (I.nx + S->sx - 1) / S->sx, fnty = (I.ny + sy - 1) / sy;
+            if (I.nz > 0xFFFF || fntx > 0xFFFF || fnty > 0x7FFF) return fail(h, FDTD_E_INVAL, "grid too large for the sweep's task records");
+            const int pl = std::min(S->planes, I.nz);
+            d.ftile_off = (int)recs.size();
+            for (int ty = 0; ty < fnty; ++ty)
+                for (int tx = 0; tx < fntx; ++tx)
+                    for (int k = 0, band = 0; k < I.nz; k += pl, ++band) {
+                        TaskRec r;
+                        r.t = make_int4((int)ii, tx | (ty << 16), k | (std::min(I.nz, k + pl) << 16), (int)recs.size());
+                        r.band = band;
+                        recs.push_back(r);
+                    }
+            d.fntask = (int)recs.size() - d.ftile_off;
+        }
         d.mag_off = (int)comps.size();
         d.nmag = (int)I.comps.size();
         for (auto C : I.comps) {
@@ -849,18 +870,25 @@ static int upload_descriptors(fdtd_llg_t h)
         const int rc = encode_tensor_maps(h, S->inst[ii], hi[ii], S->sx);
         if (rc) return rc;
     }
+    // claim order: by z band, then instance and column
+    std::stable_sort(recs.begin(), recs.end(), [](const TaskRec &a, const TaskRec &b) {
+        if (a.band != b.band) return a.band < b.band;
+        return a.t.x < b.t.x;
+    });
+    std::vector<int4> ftask(recs.size());
+    for (size_t q = 0; q < recs.size(); ++q) ftask[q] = recs[q].t;
     S->dfree(S->d_insts); S->dfree(S->d_tile_inst); S->dfree(S->d_ftile_inst); S->dfree(S->d_comps); S->dfree(S->d_part);
     S->d_insts = (Inst *)S->dalloc(hi.size() * sizeof(Inst));
     S->d_tile_inst = (int *)S->dalloc(tile_inst.size() * sizeof(int));
-    S->d_ftile_inst = (int *)S->dalloc(ftile_inst.size() * sizeof(int));
+    S->d_ftile_inst = (int4 *)S->dalloc(std::max<size_t>(1, ftask.size()) * sizeof(int4));
     S->d_comps = (MagComp *)S->dalloc(std::max<size_t>(1, comps.size()) * sizeof(MagComp));
-    const size_t part_stride = ftile_inst.size() * kSW + comps.size();
+    const size_t part_stride = ftask.size() * kSW + comps.size();
     S->d_part = (double *)S->dalloc((2 * part_stride + 1) * sizeof(double));
     if (!S->d_insts || !S->d_tile_inst || !S->d_ftile_inst || !S->d_comps || !S->d_part)
         return fail(h, FDTD_E_OOM, "device allocation failed");
     CKR(h, cudaMemcpy(S->d_insts, hi.data(), hi.size() * sizeof(Inst), cudaMemcpyHostToDevice));
     CKR(h, cudaMemcpy(S->d_tile_inst, tile_inst.data(), tile_inst.size() * sizeof(int), cudaMemcpyHostToDevice));
-    CKR(h, cudaMemcpy(S->d_ftile_inst, ftile_inst.data(), ftile_inst.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CKR(h, cudaMemcpy(S->d_ftile_inst, ftask.data(), ftask.size() * sizeof(int4), cudaMemcpyHostToDevice));
     if (!comps.empty()) CKR(h, cudaMemcpy(S->d_comps, comps.data(), comps.size() * sizeof(MagComp), cudaMemcpyHostToDevice));
     CKR(h, cudaMemset(S->d_part, 0, (2 * part_stride + 1) * sizeof(double)));
     // the pending step's partials are gone with the old buffer (its energy was
@@ -868,7 +896,7 @@ static int upload_descriptors(fdtd_llg_t h)
     CKR(h, cudaMemsetAsync(&S->d_ctl->epend, 0xFF, sizeof(long long), S->stream));
     CKR(h, cudaStreamSynchronize(S->stream));
     S->ntiles = (int)tile_inst.size();
-    S->nftiles = (int)ftile_inst.size();
+    S->nftiles = (int)ftask.size();
     S->ncomp = (int)comps.size();
     S->vmax = vmax;
     S->stab = stab;
@@ -897,7 +925,7 @@ static LaunchSet launch_set(Sim *S)
     L.part_stride = L.nslot_f + S->ncomp;
     L.part_f = S->d_part;
     L.part_m = S->d_part + L.nslot_f;
-    L.ftile_inst = S->d_ftile_inst;
+    L.ftask = S->d_ftile_inst;
     L.nftiles = S->nftiles;
     // persistent field-sweep CTAs: as many as fit at once (late ones, queued
     // behind the magnet CTAs, take what is left of the task counter)

@@ -21,8 +21,8 @@ constexpr int kMaxMagMat = 16;
 constexpr int kTX = 32, kTY = 8, kKC = 16;
 
 // Fused step kernel: persistent CTAs of kST threads take column tasks of
-// SX x SY cells x fkc planes (the host picks fkc; kSZ is the fallback) and
-// march them in z.  Each z-plane arrives by TMA in one stage of a kNS-deep
+// SX x SY cells x a range of z-planes (from the host's schedule) and march
+// them in z.  Each z-plane arrives by TMA in one stage of a kNS-deep
 // shared-memory ring: H on the tile extended by one cell on the low x/y sides
 // (box HBX x HBY, x starting 4 cells low so that the copy stays 16-byte
 // aligned), E^n and the class ids on the tile extended by one cell on the high
@@ -203,7 +203,7 @@ struct alignas(128) Inst {
     double srcp[kMaxSrc][4];              // J0, f0, Tp, tpk
     int probe[kMaxProbe][3];
     int tile_off, ntx, nty, ntz;          // half-push tiles of this instance in the tile list
-    int ftile_off, fntx, fnty, fntz, fkc; // fused-step tasks (kSX x kSY x fkc)
+    int ftile_off, fntask;              // sweep tasks: this instance's energy-partial slots [ftile_off, + fntask)
     int mag_off, nmag;                    // magnet regions of this instance
     MagMat mm[kMaxMagMat];
 };
@@ -242,8 +242,10 @@ struct LaunchSet {
     // (part_m = part_f + nslot_f); set p starts at part_f + p * part_stride
     double *part_f, *part_m;
     int nslot_f, part_stride;
-    const int *ftile_inst;
-    int nftiles;                        // field-sweep tasks
+    // field-sweep tasks in the order CTAs draw them: {instance, tx | ty << 16,
+    // k0 | k1 << 16, energy-partial slot}
+    const int4 *ftask;
+    int nftiles;
     int nfblocks;                       // persistent CTAs of the field sweep
     int mag_smem;                       // dynamic shared memory of the magnet kernel (bytes)
     int src, dst;                       // field buffers read / written by a step

@@ -96,7 +96,7 @@ __device__ void reduce_energy(const LaunchSet &L, int ii, long long m, double *s
     if (!pend) return;
     const Inst *I = L.insts + ii;
     const double *pf = L.part_f + (m & 1) * L.part_stride, *pm = L.part_m + (m & 1) * L.part_stride;
-    const int s0 = I->ftile_off * kSW, s1 = (I->ftile_off + I->fntx * I->fnty * I->fntz) * kSW;
+    const int s0 = I->ftile_off * kSW, s1 = (I->ftile_off + I->fntask) * kSW;
     double s = 0.0;
     int q = s0 + tid;
     for (; q + (B - 1) * nth < s1; q += B * nth) {   // B loads in flight, added in slot order
@@ -753,15 +753,16 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
         __syncthreads();   // every thread has read s_task before thread 0 draws again
         continue;
     }
-    const int t = v - nred;
-    const Inst *I = L.insts + L.ftile_inst[t];
-    const int lt = t - I->ftile_off;
-    const int tx = lt % I->fntx, ty = (lt / I->fntx) % I->fnty, tz = lt / (I->fntx * I->fnty);
-    const int nx = I->nx, ny = I->ny, nz = I->nz, px = I->px;
+    // task t of the host's schedule: instance, column (tx, ty), planes
+    // [k0, k1), slot of its energy partials within the instance's range
+    const int4 tk = L.ftask[v - nred];
+    const Inst *I = L.insts + tk.x;
+    const int tx = (int)((unsigned)tk.y & 0xFFFFu), ty = (int)((unsigned)tk.y >> 16);
+    const int k0 = (int)((unsigned)tk.z & 0xFFFFu), k1 = (int)((unsigned)tk.z >> 16), slot = tk.w;
+    const int nx = I->nx, ny = I->ny, px = I->px;
     const unsigned plane = (unsigned)I->plane;
     const long long fs = I->fstride;
-    const int i0 = tx * SX, j0 = ty * SY, k0 = tz * I->fkc;
-    const int k1 = min(k0 + I->fkc, nz);
+    const int i0 = tx * SX, j0 = ty * SY;
     const int nitems = k1 - k0 + 2;
     const float4 *__restrict__ ctab = I->ctab;
     const bool has_mag = I->nmag > 0;
@@ -1049,7 +1050,7 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
         double e = (double)acc + (double)acc_c;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-        if (lane == 0) pf[(long long)t * kSW + w] = e;
+        if (lane == 0) pf[(long long)slot * kSW + w] = e;
     }
     gbase += nitems;
     }
