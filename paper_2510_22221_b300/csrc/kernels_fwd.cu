@@ -106,7 +106,13 @@ __device__ void reduce_energy(const LaunchSet &L, int ii, long long m, double *s
 #pragma unroll
         for (int u = 0; u < B; ++u) s += v[u];
     }
-    for (; q < s1; q += nth) s += ld_cg(pf + q);
+    for (; q < s1; q += 8 * nth) {   // the rest, eight at a time; slots past the end add +0.0 (partials are >= 0)
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = q + u * nth < s1 ? ld_cg(pf + q + u * nth) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += v[u];
+    }
     for (int c = I->mag_off + tid; c < I->mag_off + I->nmag; c += nth) s += ld_cg(pm + c);
     s = block_sum(s, sred);
     if (tid == 0) {
