@@ -70,6 +70,10 @@ struct Sim {
     MagComp *d_comps = nullptr;
     StepCtl *d_ctl = nullptr;
     double *d_part = nullptr;         // part_e | part_h | part_m
+    int2 *d_ered = nullptr;           // the flush's energy chunks {instance, chunk}
+    double *d_esum = nullptr;         // chunk sums, kEChunks per instance
+    unsigned *d_ecnt = nullptr;       // chunks summed, per instance
+    int nred = 0;
     int ntiles = 0, nftiles = 0, ncomp = 0, vmax = 0, mag_smem = 0;
     bool stab = false;                // every class table small enough for shared memory
     int tiling = 0;                   // requested z-planes per sweep task (0: model)
@@ -877,7 +881,19 @@ static int upload_descriptors(fdtd_llg_t h)
     });
     std::vector<int4> ftask(recs.size());
     for (size_t q = 0; q < recs.size(); ++q) ftask[q] = recs[q].t;
+    // the flush's energy chunks, one CTA each
+    std::vector<int2> ered;
+    for (size_t ii = 0; ii < hi.size(); ++ii)
+        for (int c = 0; c < energy_chunks(hi[ii].fntask); ++c) ered.push_back(make_int2((int)ii, c));
     S->dfree(S->d_insts); S->dfree(S->d_tile_inst); S->dfree(S->d_ftile_inst); S->dfree(S->d_comps); S->dfree(S->d_part);
+    S->dfree(S->d_ered); S->dfree(S->d_esum); S->dfree(S->d_ecnt);
+    S->d_ered = (int2 *)S->dalloc(ered.size() * sizeof(int2));
+    S->d_esum = (double *)S->dalloc(hi.size() * kEChunks * sizeof(double));
+    S->d_ecnt = (unsigned *)S->dalloc(hi.size() * sizeof(unsigned));
+    if (!S->d_ered || !S->d_esum || !S->d_ecnt) return fail(h, FDTD_E_OOM, "device allocation failed");
+    CKR(h, cudaMemcpy(S->d_ered, ered.data(), ered.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    CKR(h, cudaMemset(S->d_ecnt, 0, hi.size() * sizeof(unsigned)));
+    S->nred = (int)ered.size();
     S->d_insts = (Inst *)S->dalloc(hi.size() * sizeof(Inst));
     S->d_tile_inst = (int *)S->dalloc(tile_inst.size() * sizeof(int));
     S->d_ftile_inst = (int4 *)S->dalloc(std::max<size_t>(1, ftask.size()) * sizeof(int4));
@@ -927,6 +943,10 @@ static LaunchSet launch_set(Sim *S)
     L.part_m = S->d_part + L.nslot_f;
     L.ftask = S->d_ftile_inst;
     L.nftiles = S->nftiles;
+    L.ered = S->d_ered;
+    L.nred = S->nred;
+    L.esum = S->d_esum;
+    L.ecnt = S->d_ecnt;
     // persistent field-sweep CTAs: as many as fit at once (late ones, queued
     // behind the magnet CTAs, take what is left of the task counter)
     L.sx = S->sx;

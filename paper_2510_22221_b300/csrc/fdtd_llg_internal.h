@@ -34,6 +34,15 @@ constexpr int kTX = 32, kTY = 8, kKC = 16;
 // number of values, so both share one stage layout.
 constexpr int kSX = 64, kSY = 8, kSZ = 16, kST = 256, kNS = 4;
 constexpr int kSW = kST / 32;   // warps of a sweep CTA (one energy partial each per task)
+constexpr int kEChunks = 8;         // most chunks of one instance's energy sum
+constexpr int kEChunkSlots = 1024;  // most sweep partials in a chunk, unless an instance needs more than kEChunks
+
+// Chunks of the energy sum of an instance with fntask sweep tasks.
+__host__ __device__ inline int energy_chunks(int fntask)
+{
+    const int c = (fntask * kSW + kEChunkSlots - 1) / kEChunkSlots;
+    return c < 1 ? 1 : (c > kEChunks ? kEChunks : c);
+}
 template <int SX>
 struct Tile {
     static constexpr int LPR = SX / 2;                 // lanes per tile row (one cell pair each)
@@ -242,6 +251,12 @@ struct LaunchSet {
     // (part_m = part_f + nslot_f); set p starts at part_f + p * part_stride
     double *part_f, *part_m;
     int nslot_f, part_stride;
+    // the flush's energy chunks: nred records {instance, chunk}, chunk sums
+    // esum[instance * kEChunks + chunk], chunks summed per instance ecnt
+    const int2 *ered;
+    int nred;
+    double *esum;
+    unsigned *ecnt;
     // field-sweep tasks in the order CTAs draw them: {instance, tx | ty << 16,
     // k0 | k1 << 16, energy-partial slot}
     const int4 *ftask;

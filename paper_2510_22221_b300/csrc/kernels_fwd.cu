@@ -80,45 +80,88 @@ __device__ double source_value(const double *p, double t)
 }
 
 
-// The energy of step m of instance ii from that step's partials (written by
-// the step's sweep warps and magnet CTAs), into its ring slot.  Every thread
-// of the CTA calls it with the same arguments; thread q sums the slots
-// q, q + blockDim, ... in order and block_sum adds the threads in a fixed
-// tree, so the value is the same whichever CTA or kernel forms it.  Nothing
-// is done unless step m's partials are the pending ones.
-// B loads are in flight at a time (more in the flush kernel, fewer inside the
-// register-bound sweep); the order of the additions does not depend on B.
+// Step m's energy of an instance is the sum of its partials (written by the
+// step's sweep warps and magnet CTAs) in energy_chunks() fixed chunks, the
+// magnet partials in the last one; the chunk sums are added in chunk order.
+// A chunk is summed by one CTA: thread q adds the chunk's slots q, q + nth,
+// ... in order, B loads in flight (any B gives the same bits), and block_sum
+// adds the threads in a fixed tree.  The value is then the same whether one
+// CTA forms every chunk (a reduction task inside the next step's sweep) or
+// one CTA each (the flush after the last step of a run).  Valid in thread 0.
 template <int B>
-__device__ void reduce_energy(const LaunchSet &L, int ii, long long m, double *sred)
+__device__ double chunk_sum(const Inst *I, int c, int nch, const double *pf, const double *pm, double *sred)
 {
     const int tid = threadIdx.x, nth = blockDim.x;
-    const bool pend = m >= 0 && *(volatile long long *)&L.ctl->epend == m;
-    if (!pend) return;
-    const Inst *I = L.insts + ii;
-    const double *pf = L.part_f + (m & 1) * L.part_stride, *pm = L.part_m + (m & 1) * L.part_stride;
     const int s0 = I->ftile_off * kSW, s1 = (I->ftile_off + I->fntask) * kSW;
+    const int len = (s1 - s0 + nch - 1) / nch, a = s0 + c * len, e = min(s1, a + len);
     double s = 0.0;
-    int q = s0 + tid;
-    for (; q + (B - 1) * nth < s1; q += B * nth) {   // B loads in flight, added in slot order
+    int q = a + tid;
+    for (; q + (B - 1) * nth < e; q += B * nth) {
         double v[B];
 #pragma unroll
         for (int u = 0; u < B; ++u) v[u] = ld_cg(pf + q + u * nth);
 #pragma unroll
         for (int u = 0; u < B; ++u) s += v[u];
     }
-    for (; q < s1; q += 8 * nth) {   // the rest, eight at a time; slots past the end add +0.0 (partials are >= 0)
+    for (; q < e; q += 8 * nth) {   // the rest, eight at a time; slots past the end add +0.0 (partials are >= 0)
         double v[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = q + u * nth < s1 ? ld_cg(pf + q + u * nth) : 0.0;
+        for (int u = 0; u < 8; ++u) v[u] = q + u * nth < e ? ld_cg(pf + q + u * nth) : 0.0;
 #pragma unroll
         for (int u = 0; u < 8; ++u) s += v[u];
     }
-    for (int c = I->mag_off + tid; c < I->mag_off + I->nmag; c += nth) s += ld_cg(pm + c);
-    s = block_sum(s, sred);
-    if (tid == 0) {
-        const double W = s * I->dV;
-        I->energy_buf[m % I->cap] = W;
-        if (!isfinite(W)) atomicOr(&L.ctl->status, ST_UNSTABLE);
+    if (c == nch - 1)
+        for (int k = I->mag_off + tid; k < I->mag_off + I->nmag; k += nth) s += ld_cg(pm + k);
+    return block_sum(s, sred);
+}
+
+__device__ __forceinline__ void store_energy(const LaunchSet &L, const Inst *I, double t, long long m)
+{
+    const double W = t * I->dV;
+    I->energy_buf[m % I->cap] = W;
+    if (!isfinite(W)) atomicOr(&L.ctl->status, ST_UNSTABLE);
+}
+
+__device__ __forceinline__ bool energy_pending(const LaunchSet &L, long long m)
+{
+    return m >= 0 && *(volatile long long *)&L.ctl->epend == m;
+}
+
+// Reduction task of the sweep: every chunk of instance ii, in order.
+template <int B>
+__device__ void reduce_energy(const LaunchSet &L, int ii, long long m, double *sred)
+{
+    if (!energy_pending(L, m)) return;
+    const Inst *I = L.insts + ii;
+    const double *pf = L.part_f + (m & 1) * L.part_stride, *pm = L.part_m + (m & 1) * L.part_stride;
+    const int nch = energy_chunks(I->fntask);
+    double t = 0.0;
+    for (int c = 0; c < nch; ++c) t += chunk_sum<B>(I, c, nch, pf, pm, sred);
+    if (threadIdx.x == 0) store_energy(L, I, t, m);
+}
+
+// Flush CTA r: chunk L.ered[r] = {instance, chunk}; the CTA that sums an
+// instance's last outstanding chunk adds the chunk sums in order.
+template <int B>
+__device__ void reduce_energy_chunk(const LaunchSet &L, int r, long long m, double *sred)
+{
+    if (!energy_pending(L, m)) return;
+    const int2 rt = L.ered[r];
+    const int ii = rt.x, c = rt.y;
+    const Inst *I = L.insts + ii;
+    const double *pf = L.part_f + (m & 1) * L.part_stride, *pm = L.part_m + (m & 1) * L.part_stride;
+    const int nch = energy_chunks(I->fntask);
+    const double s = chunk_sum<B>(I, c, nch, pf, pm, sred);
+    if (threadIdx.x == 0) {
+        L.esum[ii * kEChunks + c] = s;
+        __threadfence();
+        if (atomicAdd(&L.ecnt[ii], 1u) == (unsigned)(nch - 1)) {
+            __threadfence();
+            double t = 0.0;
+            for (int k = 0; k < nch; ++k) t += ld_cg(L.esum + ii * kEChunks + k);
+            store_energy(L, I, t, m);
+            L.ecnt[ii] = 0u;
+        }
     }
 }
 
@@ -1066,12 +1109,12 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
     finish_step(L, n, &s_last);
 }
 
-// The pending step's energy of instance blockIdx.x (after the last step of a
-// run; kST threads, as in the sweep, so that the sums are the same bits).
+// The pending step's energy (after the last step of a run): one CTA per
+// chunk, kST threads as in the sweep, so that the sums are the same bits.
 __global__ void __launch_bounds__(kST) energy_flush_kernel(LaunchSet L)
 {
     __shared__ double sred[kST / 32];
-    reduce_energy<32>(L, blockIdx.x, *(volatile long long *)&L.ctl->epend, sred);
+    reduce_energy_chunk<32>(L, blockIdx.x, *(volatile long long *)&L.ctl->epend, sred);
 }
 
 __global__ void set_step_kernel(StepCtl *ctl, long long n)
@@ -1151,8 +1194,8 @@ cudaError_t launch_half(const LaunchSet &L, cudaStream_t s)
 
 cudaError_t launch_energy_flush(const LaunchSet &L, cudaStream_t s)
 {
-    if (!L.energy || L.ninst < 1) return cudaSuccess;
-    energy_flush_kernel<<<L.ninst, kST, 0, s>>>(L);
+    if (!L.energy || L.nred < 1) return cudaSuccess;
+    energy_flush_kernel<<<L.nred, kST, 0, s>>>(L);
     return cudaGetLastError();
 }
 

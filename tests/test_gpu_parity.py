@@ -264,6 +264,33 @@ def test_energy_does_not_depend_on_how_the_run_is_split():
         sim.destroy()
 
 
+@pytest.mark.parametrize("planes", [1, 2])
+def test_energy_summed_in_chunks_matches_oracle_and_split(planes):
+    """An instance with more sweep tasks sums its energy in several chunks:
+    82 rows make 11 tile rows, 22 columns of 64 x 8; one plane per task gives
+    1342 tasks (10736 partials, the most chunks: 8 of 1342), two planes 682
+    tasks (5456 partials, 6 ragged chunks of 910 and a last of 906).  The
+    in-sweep sum (one CTA per instance) and the flush (one CTA per chunk) add
+    the same chunk sums in the same order: the record is the same bits however
+    the run is split, and within tolerance of the FP64 oracle."""
+    w = W.random_small(9, nx=100, ny=82, nz=61, steps=40)
+    orc = oracle_from_workload(w)
+    out = orc.run(w.steps)
+    a = pkg.from_workload(w, probe_capacity=64)
+    a.set_tiling(planes)
+    a.step(w.steps)
+    assert (a.get_tiling(), a.get_tile_width()) == (planes, 64)
+    ref = a.energy()
+    assert rel_err(ref, out["energy"]) < tol(w.steps)
+    b = pkg.from_workload(w, probe_capacity=64)
+    b.set_tiling(planes)
+    for n in (1, 1, 1, 2, 35):
+        b.step(n)
+    np.testing.assert_array_equal(b.energy(), ref)
+    for sim in (a, b):
+        sim.destroy()
+
+
 def test_read_last_returns_the_newest_rows_and_energy():
     w = W.random_small(8, steps=12)
     sim = pkg.from_workload(w, probe_capacity=5)   # the ring wraps
