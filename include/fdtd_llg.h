@@ -187,9 +187,11 @@ int fdtd_llg_read_last(fdtd_llg_t h, double *probe_rows, double *energy);
  * capacity].  Nothing waits for them: they are complete once a synchronising
  * call returns (fdtd_llg_sync, a read, an event recorded after the step
  * call).  Steps older than probe_capacity at the end of a call are not
- * copied.  The rings are caller-owned and must stay valid while streaming;
- * page-locked memory keeps the copies asynchronous.  Either pointer may be
- * NULL; both NULL stops streaming.  The call synchronises the stream (copies
+ * copied.  The rings are caller-owned and must stay valid while streaming.
+ * Page-locked memory (cudaHostAlloc, or registered and mapped) is written
+ * directly by the kernel that ends each step call, through its device
+ * address; other host memory by copies queued after it.  Either pointer may
+ * be NULL; both NULL stops streaming.  The call synchronises the stream (copies
  * into earlier rings complete first).  Errors: FDTD_E_INVAL (batch handle,
  * capacity < 1). */
 int fdtd_llg_stream_results(fdtd_llg_t h, double *rows, double *energy, int64_t capacity);

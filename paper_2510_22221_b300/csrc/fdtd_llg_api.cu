@@ -35,8 +35,11 @@ struct Instance {
     int probe_alloc = -1;             // probes the probe ring was sized for
     double *energy_buf = nullptr;
     // caller's host rings for streamed results (fdtd_llg_stream_results)
+    // the caller's host rings: pageable ones are filled by copies queued after
+    // each step call (host_*), pinned ones by the flush kernel (ring_mapped)
     double *host_rows = nullptr, *host_energy = nullptr;
     long long host_cap = 0;
+    bool ring_mapped = false;
     float *mbuf = nullptr;            // all regions' deviation m (bias frame)
     uint8_t *magmat = nullptr;        // all regions' material maps
     // host descriptions
@@ -70,6 +73,8 @@ struct Sim {
     MagComp *d_comps = nullptr;
     StepCtl *d_ctl = nullptr;
     double *d_part = nullptr;         // part_e | part_h | part_m
+    HostRing *d_rings = nullptr;      // per instance: the mapped host rings the flush fills
+    bool rings_mapped = false;        // some instance has one
     int2 *d_ered = nullptr;           // the flush's energy chunks {instance, chunk}
     double *d_esum = nullptr;         // chunk sums, kEChunks per instance
     unsigned *d_ecnt = nullptr;       // chunks summed, per instance
@@ -994,8 +999,9 @@ static cudaError_t build_graph(Sim *S, LaunchSet L)
 }
 
 // Queue on the stream the copies of steps [n0, n1)'s probe rows and energies
-// from the device rings into the instances' host rings (those that stream),
-// after everything queued so far; steps older than the device ring are gone.
+// from the device rings into the instances' pageable host rings (those that
+// stream), after everything queued so far; steps older than the device ring
+// are gone.
 static cudaError_t stream_out(Sim *S, long long n0, long long n1)
 {
     const long long dcap = S->cfg.probe_capacity;
@@ -1023,11 +1029,33 @@ extern "C" int fdtd_llg_stream_results(fdtd_llg_t h, double *rows, double *energ
 {
     if (!is_member(h)) return fail(h, FDTD_E_INVAL, "stream_results needs an instance handle");
     if ((rows || energy) && capacity < 1) return fail(h, FDTD_E_INVAL, "capacity must be >= 1");
+    Sim *S = h->sim;
     Instance *I = inst_of(h);
-    CKR(h, cudaStreamSynchronize(h->sim->stream));   // copies queued into the previous rings are done
-    I->host_rows = rows;
-    I->host_energy = energy;
-    I->host_cap = (rows || energy) ? capacity : 0;
+    CKR(h, cudaStreamSynchronize(S->stream));   // copies queued into the previous rings are done
+    // pinned host memory is written by the flush kernel through its device
+    // address; other host memory by copies queued after each step call
+    auto mapped = [](double *p) -> double * {
+        if (!p) return nullptr;
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return pa.type == cudaMemoryTypeHost ? (double *)pa.devicePointer : nullptr;
+    };
+    HostRing R{mapped(rows), mapped(energy), capacity};
+    I->host_rows = R.rows ? nullptr : rows;
+    I->host_energy = R.energy ? nullptr : energy;
+    I->host_cap = (I->host_rows || I->host_energy) ? capacity : 0;
+    I->ring_mapped = R.rows || R.energy;
+    if (!S->d_rings) {
+        S->d_rings = (HostRing *)S->dalloc(S->inst.size() * sizeof(HostRing));
+        if (!S->d_rings) return fail(h, FDTD_E_OOM, "device allocation failed");
+        CKR(h, cudaMemset(S->d_rings, 0, S->inst.size() * sizeof(HostRing)));
+    }
+    CKR(h, cudaMemcpy(S->d_rings + (I - S->inst.data()), &R, sizeof(HostRing), cudaMemcpyHostToDevice));
+    S->rings_mapped = false;
+    for (const Instance &J : S->inst) S->rings_mapped = S->rings_mapped || J.ring_mapped;
     return FDTD_OK;
 }
 
@@ -1074,7 +1102,8 @@ extern "C" int fdtd_llg_step(fdtd_llg_t h, int64_t nsteps)
         }
         S->cur ^= 1;
     }
-    if (nsteps > 0) CKR(h, launch_energy_flush(L, S->stream));
+    const HostRing *rings = S->rings_mapped ? S->d_rings : nullptr;
+    if (nsteps > 0) CKR(h, launch_energy_flush(L, rings, S->host_step, S->host_step + nsteps, S->stream));
     if (nsteps > 0) CKR(h, stream_out(S, S->host_step, S->host_step + nsteps));
     S->host_step += nsteps;
     return FDTD_OK;
@@ -1661,7 +1690,7 @@ extern "C" int fdtd_llg_run_checkpointed(fdtd_llg_t h, int64_t nsteps, int32_t i
             S->cur ^= 1;
             if (per_d) CKR(h, adj_record_design(L, Ad, (int)(n - S->tail0 + 1), S->cur, S->stream));
         }
-        CKR(h, launch_energy_flush(L, S->stream));
+        CKR(h, launch_energy_flush(L, S->rings_mapped ? S->d_rings : nullptr, S->host_step, S->host_step + ns, S->stream));
         CKR(h, stream_out(S, S->host_step, S->host_step + ns));
         S->host_step += ns;
     }
@@ -1760,7 +1789,7 @@ extern "C" int fdtd_llg_adjoint_step(fdtd_llg_t h, const double *dJ_dE, double *
             S->cur ^= 1;
             if (e == cudaSuccess && nbe) e = adj_record_design(L, A, (int)(base + n - na + 1), S->cur, S->stream);
         }
-        if (e == cudaSuccess) e = launch_energy_flush(L, S->stream);
+        if (e == cudaSuccess) e = launch_energy_flush(L, nullptr, 0, 0, S->stream);
         for (long long n = nb - 1; n >= na && e == cudaSuccess; --n)
             e = adj_reverse_step(L, A, n, (int)(base + n - na), S->stream);
         S->host_step = nb;

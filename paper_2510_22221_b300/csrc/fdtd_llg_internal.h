@@ -234,6 +234,16 @@ struct StepCtl {
     int status;             // latched error bits (ST_*)
     unsigned int work;      // next field-sweep task to hand out
     long long epend;        // step whose energy partials await their sums (-1: none)
+    unsigned int eflush;    // instances whose pending energy the flush has summed
+};
+
+// A caller's host ring that step results stream into by device stores
+// (pinned host memory, addressed through its device mapping): per instance,
+// probe rows (cap x nprobe x 9) and energies (cap); NULL: not streamed so.
+struct HostRing {
+    double *rows;
+    double *energy;
+    long long cap;
 };
 enum : int { ST_NOCONV = 1, ST_UNSTABLE = 2, ST_TIMEOUT = 4, ST_TAPE = 8 };
 
@@ -288,7 +298,9 @@ cudaError_t launch_step(const LaunchSet &L, cudaStream_t s, cudaEvent_t *prof);
 // draw its reduction tasks); launch_energy_flush sums the last step's after a
 // run of steps, with the same arithmetic, so the values do not depend on where
 // a run of steps ends.
-cudaError_t launch_energy_flush(const LaunchSet &L, cudaStream_t s);
+// It also copies the call's steps [n0, n1) of probe rows and energies into
+// the host rings `rings` (device array of ninst, or NULL).
+cudaError_t launch_energy_flush(const LaunchSet &L, const HostRing *rings, long long n0, long long n1, cudaStream_t s);
 int h_half_blocks_per_sm(bool cls16);
 int step_blocks_per_sm(bool cls16, bool stab, int sx);
 

@@ -140,31 +140,6 @@ __device__ void reduce_energy(const LaunchSet &L, int ii, long long m, double *s
     if (threadIdx.x == 0) store_energy(L, I, t, m);
 }
 
-// Flush CTA r: chunk L.ered[r] = {instance, chunk}; the CTA that sums an
-// instance's last outstanding chunk adds the chunk sums in order.
-template <int B>
-__device__ void reduce_energy_chunk(const LaunchSet &L, int r, long long m, double *sred)
-{
-    if (!energy_pending(L, m)) return;
-    const int2 rt = L.ered[r];
-    const int ii = rt.x, c = rt.y;
-    const Inst *I = L.insts + ii;
-    const double *pf = L.part_f + (m & 1) * L.part_stride, *pm = L.part_m + (m & 1) * L.part_stride;
-    const int nch = energy_chunks(I->fntask);
-    const double s = chunk_sum<B>(I, c, nch, pf, pm, sred);
-    if (threadIdx.x == 0) {
-        L.esum[ii * kEChunks + c] = s;
-        __threadfence();
-        if (atomicAdd(&L.ecnt[ii], 1u) == (unsigned)(nch - 1)) {
-            __threadfence();
-            double t = 0.0;
-            for (int k = 0; k < nch; ++k) t += ld_cg(L.esum + ii * kEChunks + k);
-            store_energy(L, I, t, m);
-            L.ecnt[ii] = 0u;
-        }
-    }
-}
-
 // Called by every CTA of a step (field and magnet kernels) after its partials
 // are written: the last one advances the step and marks its partials pending.
 __device__ void finish_step(const LaunchSet &L, long long n, int *s_last)
@@ -1109,12 +1084,74 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
     finish_step(L, n, &s_last);
 }
 
-// The pending step's energy (after the last step of a run): one CTA per
-// chunk, kST threads as in the sweep, so that the sums are the same bits.
-__global__ void __launch_bounds__(kST) energy_flush_kernel(LaunchSet L)
+// Steps [n0, n1) of instance I's probe rows and energies from the device
+// rings into the host ring R (every thread of the CTA).  Only the newest
+// min(I->cap, R.cap) steps: the device rings hold the last I->cap, and an
+// older step would share a host slot with a newer one.
+__device__ void copy_out(const Inst *I, const HostRing &R, long long n0, long long n1)
+{
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const long long dcap = I->cap;
+    const long long a = max(n0, n1 - min(dcap, R.cap));
+    if (R.energy)
+        for (long long st = a + tid; st < n1; st += nth) R.energy[st % R.cap] = I->energy_buf[st % dcap];
+    const int w = I->nprobe * 9;
+    if (R.rows && w)
+        for (long long q = tid; q < (n1 - a) * w; q += nth) {
+            const long long st = a + q / w;
+            const int r = (int)(q % w);
+            R.rows[(st % R.cap) * w + r] = I->probe_buf[(st % dcap) * w + r];
+        }
+}
+
+// After the last step of a call.  With the energy on, one CTA per chunk of
+// the pending step's partials (kST threads, as the sweep's reduction task,
+// so that the sums are the same bits): the CTA that sums an instance's last
+// outstanding chunk adds the chunk sums in order, and the CTA that completes
+// the last instance clears the pending step (the next step's sweep then does
+// not sum it again).  With the energy off, one CTA per instance.  The CTA that
+// completes an instance (with nothing pending, its first one) then copies the
+// call's steps [n0, n1) of the instance's results into its host ring.
+__global__ void __launch_bounds__(kST) energy_flush_kernel(LaunchSet L, const HostRing *rings, long long n0, long long n1)
 {
     __shared__ double sred[kST / 32];
-    reduce_energy_chunk<32>(L, blockIdx.x, *(volatile long long *)&L.ctl->epend, sred);
+    __shared__ int s_out;
+    const int tid = threadIdx.x;
+    int ii = blockIdx.x, c = 0;
+    if (L.energy) {
+        const int2 rt = L.ered[blockIdx.x];
+        ii = rt.x;
+        c = rt.y;
+    }
+    const Inst *I = L.insts + ii;
+    const long long m = L.energy ? *(volatile long long *)&L.ctl->epend : -1;
+    if (m >= 0) {
+        const double *pf = L.part_f + (m & 1) * L.part_stride, *pm = L.part_m + (m & 1) * L.part_stride;
+        const int nch = energy_chunks(I->fntask);
+        const double sc = chunk_sum<32>(I, c, nch, pf, pm, sred);
+        if (tid == 0) {
+            int done = 0;
+            L.esum[ii * kEChunks + c] = sc;
+            __threadfence();
+            if (atomicAdd(&L.ecnt[ii], 1u) == (unsigned)(nch - 1)) {
+                __threadfence();
+                double t = 0.0;
+                for (int k = 0; k < nch; ++k) t += __ldcg(L.esum + ii * kEChunks + k);
+                store_energy(L, I, t, m);
+                L.ecnt[ii] = 0u;
+                done = 1;
+                if (atomicAdd(&L.ctl->eflush, 1u) == (unsigned)(L.ninst - 1)) {
+                    L.ctl->eflush = 0u;
+                    L.ctl->epend = -1;
+                }
+            }
+            s_out = done;
+        }
+    } else if (tid == 0) {
+        s_out = c == 0;
+    }
+    __syncthreads();
+    if (s_out && rings && n1 > n0) copy_out(I, rings[ii], n0, n1);
 }
 
 __global__ void set_step_kernel(StepCtl *ctl, long long n)
@@ -1123,6 +1160,7 @@ __global__ void set_step_kernel(StepCtl *ctl, long long n)
     ctl->counter = 0u;
     ctl->work = 0u;
     ctl->epend = -1;
+    ctl->eflush = 0u;
 }
 
 }  // namespace
@@ -1192,10 +1230,11 @@ cudaError_t launch_half(const LaunchSet &L, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_energy_flush(const LaunchSet &L, cudaStream_t s)
+cudaError_t launch_energy_flush(const LaunchSet &L, const HostRing *rings, long long n0, long long n1, cudaStream_t s)
 {
-    if (!L.energy || L.nred < 1) return cudaSuccess;
-    energy_flush_kernel<<<L.nred, kST, 0, s>>>(L);
+    const int grid = L.energy ? L.nred : (rings ? L.ninst : 0);
+    if (grid < 1) return cudaSuccess;
+    energy_flush_kernel<<<grid, kST, 0, s>>>(L, rings, n0, n1);
     return cudaGetLastError();
 }
 

@@ -306,30 +306,46 @@ def test_read_last_returns_the_newest_rows_and_energy():
     sim.destroy()
 
 
-def test_streamed_results_equal_the_device_rings():
+@pytest.mark.parametrize("kind", ["pinned", "pageable", "pinned_energy_off"])
+def test_streamed_results_equal_the_device_rings(kind):
+    """Pinned host rings are written by the kernel that ends each step call,
+    through their device addresses; pageable ones by copies queued after it;
+    with the energy off that kernel still runs, one CTA per instance, for the
+    rows.  The host rings wrap, and one call runs more steps than the device
+    rings hold (only its newest probe_capacity steps are copied)."""
     import torch
 
     w = W.random_small(9, steps=40)
-    sim = pkg.from_workload(w, probe_capacity=64)
-    cap = 7                                        # the host rings wrap
-    rows = torch.zeros((cap, len(w.probes), 9), dtype=torch.float64).pin_memory()
-    energy = torch.zeros(cap, dtype=torch.float64).pin_memory()
+    sim = pkg.from_workload(w, probe_capacity=16, energy=kind != "pinned_energy_off")
+    cap, npr = 7, len(w.probes)
+    if kind == "pageable":
+        rows, energy = np.zeros((cap, npr, 9)), np.zeros(cap)
+    else:
+        rows = torch.zeros((cap, npr, 9), dtype=torch.float64).pin_memory()
+        energy = torch.full((cap,), -1.0, dtype=torch.float64).pin_memory()
     sim.stream_results(rows, energy)
-    for n in (1, 3, 10, 2, 1, 5):
+    for n in (1, 3, 10, 2, 1, 5, 20):
         sim.step(n)
     sim.sync()
-    steps = 22
-    ref_e = sim.energy()
+    steps = 42
+    rows_h, energy_h = rows, energy               # kept alive until the end
+    rows, energy = np.asarray(rows_h), np.asarray(energy_h)
+    ref_e = sim.energy() if kind != "pinned_energy_off" else np.zeros(16)
+    ref_rows = [sim.probe(p) for p in range(npr)]
+    assert len(ref_e) == 16 and all(len(r) == 16 for r in ref_rows)   # steps 26 .. 41
     for n in range(steps - cap, steps):
-        assert energy[n % cap].item() == ref_e[n]
-        for p in range(len(w.probes)):
-            np.testing.assert_array_equal(rows[n % cap, p].numpy(), sim.probe(p)[n])
+        assert energy[n % cap] == ref_e[n - (steps - 16)], n
+        for p in range(npr):
+            np.testing.assert_array_equal(rows[n % cap, p], ref_rows[p][n - (steps - 16)])
+    assert np.any(rows != 0)
     sim.stream_results()                           # stop: the rings keep their contents
-    before = energy.clone()
+    before = (rows.copy(), energy.copy())
     sim.step(3)
     sim.sync()
-    assert torch.equal(energy, before)
+    np.testing.assert_array_equal(rows, before[0])
+    np.testing.assert_array_equal(energy, before[1])
     sim.destroy()
+    del rows_h, energy_h
 
 
 def test_batch_equals_separate_runs_bitwise():
