@@ -2,6 +2,7 @@
 // memory, material preprocessing, magnetic-region discovery, launches.
 #include "../../include/fdtd_llg.h"
 #include "fdtd_llg_internal.h"
+#include "class_assign.h"
 
 #include <cudaTypedefs.h>
 
@@ -11,6 +12,8 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <memory>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -366,17 +369,23 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
     Instance &I = *inst_of(h);
     const int nx = I.nx, ny = I.ny, nz = I.nz;
     const size_t nc = (size_t)nx * ny * nz;
-    // material ids to the host (the caller may pass a device pointer)
-    std::vector<uint8_t> mid(nc);
+    // material ids on the host: the caller's array itself when it is host
+    // memory, a copy when it is device memory
+    std::vector<uint8_t> mid_copy;
+    const uint8_t *mid = mat_id;
     cudaPointerAttributes pa{};
     if (cudaPointerGetAttributes(&pa, mat_id) == cudaSuccess && pa.type == cudaMemoryTypeDevice) {
-        CKR(h, cudaMemcpy(mid.data(), mat_id, nc, cudaMemcpyDeviceToHost));
+        mid_copy.resize(nc);
+        CKR(h, cudaMemcpy(mid_copy.data(), mat_id, nc, cudaMemcpyDeviceToHost));
+        mid = mid_copy.data();
     } else {
         cudaGetLastError();
-        std::memcpy(mid.data(), mat_id, nc);
     }
-    for (size_t c = 0; c < nc; ++c)
-        if (mid[c] >= ntable) return fail(h, FDTD_E_INVAL, "mat_id references a material beyond ntable");
+    {
+        uint8_t top = 0;
+        for (size_t c = 0; c < nc; ++c) top = std::max(top, mid[c]);
+        if (nc && top >= ntable) return fail(h, FDTD_E_INVAL, "mat_id references a material beyond ntable");
+    }
     for (int m = 0; m < ntable; ++m) {
         const fdtd_material &t = table[m];
         if (!(t.eps_r > 0) || t.sigma < 0 || t.Ms < 0 || t.alpha < 0 || (t.Ms > 0 && !(t.gamma > 0)))
@@ -407,17 +416,6 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
     };
     const double dt = S->dt;
     // per-cell class: (ca, cb, eps/2) of the three edges with index (i,j,k) + magnetic-face flags
-    std::unordered_map<ClassKey, int, ClassKeyHash> classes;
-    std::vector<ClassKey> keys;
-    {
-        // class 0: every coefficient zero and no flags; the field kernel reads
-        // it for the cells beyond the far walls, whose E^{n+1} is then zero
-        ClassKey zero;
-        std::memset(&zero, 0, sizeof zero);
-        classes.emplace(zero, 0);
-        keys.push_back(zero);
-    }
-    std::vector<uint16_t> cls(nc);
     auto edge = [&](int comp, int i, int j, int k, float &ca, float &cb, float &he) {
         bool wall;
         if (comp == 0) wall = (j == 0 || k == 0);
@@ -445,90 +443,168 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
         cb = (float)(1.0 / den);
         he = (float)(eps / 2);
     };
-    auto magc = [&](int i, int j, int k) { return table[mid[cid(i, j, k)]].Ms > 0; };
-    // Outside the design box a cell's class depends only on the materials of
-    // the seven cells its three edges and three faces touch and on which walls
-    // it lies against, so classes are memoised on that 59-bit neighbourhood.
-    std::unordered_map<uint64_t, int> by_nbhd;
-    for (int k = 0; k < nz; ++k)
-        for (int j = 0; j < ny; ++j)
-            for (int i = 0; i < nx; ++i) {
-                const int nb[7][3] = {{i, j, k}, {i - 1, j, k}, {i, j - 1, k}, {i, j, k - 1},
-                                      {i, j - 1, k - 1}, {i - 1, j, k - 1}, {i - 1, j - 1, k}};
-                uint64_t nk = 0;
-                bool design_touch = false;
-                for (int q = 0; q < 7; ++q) {
-                    const int ci = nb[q][0], cj = nb[q][1], ck = nb[q][2];
-                    const bool in = ci >= 0 && cj >= 0 && ck >= 0;
-                    nk = (nk << 8) | (in ? mid[cid(ci, cj, ck)] : 0xFFu);
-                    design_touch = design_touch || (in && in_box(ci, cj, ck));
-                }
-                nk = (nk << 3) | (uint64_t)((i == 0) | ((j == 0) << 1) | ((k == 0) << 2));
-                if (!design_touch) {
-                    auto hit = by_nbhd.find(nk);
-                    if (hit != by_nbhd.end()) {
-                        cls[cid(i, j, k)] = (uint16_t)hit->second;
-                        continue;
+    bool magm[256] = {};
+    for (int m = 0; m < ntable; ++m) magm[m] = table[m].Ms > 0;
+    auto magc = [&](int i, int j, int k) { return magm[mid[cid(i, j, k)]]; };
+    // the class of cell (i, j, k) from its edges' coefficients and magnetic faces
+    auto class_key = [&](int i, int j, int k) {
+        ClassKey key;
+        float v[9];
+        edge(0, i, j, k, v[0], v[3], v[6]);
+        edge(1, i, j, k, v[1], v[4], v[7]);
+        edge(2, i, j, k, v[2], v[5], v[8]);
+        for (int q = 0; q < 9; ++q) key.w[q] = fbits(v[q]);
+        uint32_t f = 0;
+        if (magc(i, j, k) || (i > 0 && magc(i - 1, j, k))) f |= CF_MAG_HX;
+        if (magc(i, j, k) || (j > 0 && magc(i, j - 1, k))) f |= CF_MAG_HY;
+        if (magc(i, j, k) || (k > 0 && magc(i, j, k - 1))) f |= CF_MAG_HZ;
+        key.w[9] = f;
+        return key;
+    };
+    // a cell whose edges or faces touch a design cell (its class then
+    // depends on eps_r_design, not only on the materials around it)
+    auto touches_design = [&](int i, int j, int k) {
+        if (!has_design || i < db[0] || j < db[1] || k < db[2] || i > db[0] + db[3] || j > db[1] + db[4] ||
+            k > db[2] + db[5])
+            return false;
+        const int nb[7][3] = {{i, j, k}, {i - 1, j, k}, {i, j - 1, k}, {i, j, k - 1},
+                              {i, j - 1, k - 1}, {i - 1, j, k - 1}, {i - 1, j - 1, k}};
+        for (auto &q : nb)
+            if (q[0] >= 0 && q[1] >= 0 && q[2] >= 0 && in_box(q[0], q[1], q[2])) return true;
+        return false;
+    };
+    // Classes.  Elsewhere a cell's class depends only on its neighbourhood
+    // key (nbhd_key: the materials of the seven cells its edges and faces
+    // touch, and the walls it lies against).  z-slabs, in parallel, list the
+    // distinct keys they meet, each with a cell that has it (along x the key
+    // changes only at material boundaries, so the previous cell's is tried
+    // first), and their magnetic cells in cell order; the keys' classes and
+    // those of the cells touching the design box are formed here, and the
+    // device gives every cell its class (the host writes nothing per cell).
+    struct Slab {
+        std::vector<std::pair<uint64_t, size_t>> keys;
+        std::vector<size_t> mag;
+    };
+    const int nthr = std::max(1, std::min({(int)std::thread::hardware_concurrency(), 16, nz}));
+    std::vector<Slab> slabs(nthr);
+    auto run_slab = [&](int t) {
+        Slab &sl = slabs[t];
+        const int ka = (int)((long long)nz * t / nthr), kb = (int)((long long)nz * (t + 1) / nthr);
+        std::unordered_map<uint64_t, int> seen;
+        const size_t sj = (size_t)nx, sk = (size_t)nx * ny;
+        uint64_t last = ~0ull;
+        for (int k = ka; k < kb; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    const size_t c0 = cid(i, j, k);
+                    if (magm[mid[c0]]) sl.mag.push_back(c0);
+                    if (touches_design(i, j, k)) continue;
+                    uint64_t nk;
+                    if (i > 0 && j > 0 && k > 0) {   // interior: nbhd_key without the wall tests
+                        const uint8_t *m = mid + c0;
+                        nk = (((uint64_t)m[0] << 48) | ((uint64_t)m[-1] << 40) | ((uint64_t)m[-(ptrdiff_t)sj] << 32) |
+                              ((uint64_t)m[-(ptrdiff_t)sk] << 24) | ((uint64_t)m[-(ptrdiff_t)(sj + sk)] << 16) |
+                              ((uint64_t)m[-(ptrdiff_t)(1 + sk)] << 8) | (uint64_t)m[-(ptrdiff_t)(1 + sj)])
+                             << 3;
+                    } else {
+                        nk = nbhd_key(mid, nx, ny, i, j, k);
                     }
+                    if (nk == last) continue;
+                    last = nk;
+                    if (seen.emplace(nk, 0).second) sl.keys.emplace_back(nk, c0);
                 }
-                ClassKey key;
-                float v[9];
-                edge(0, i, j, k, v[0], v[3], v[6]);
-                edge(1, i, j, k, v[1], v[4], v[7]);
-                edge(2, i, j, k, v[2], v[5], v[8]);
-                for (int q = 0; q < 9; ++q) key.w[q] = fbits(v[q]);
-                uint32_t f = 0;
-                if (magc(i, j, k) || (i > 0 && magc(i - 1, j, k))) f |= CF_MAG_HX;
-                if (magc(i, j, k) || (j > 0 && magc(i, j - 1, k))) f |= CF_MAG_HY;
-                if (magc(i, j, k) || (k > 0 && magc(i, j, k - 1))) f |= CF_MAG_HZ;
-                key.w[9] = f;
-                auto it = classes.find(key);
-                int c;
-                if (it == classes.end()) {
-                    c = (int)keys.size();
-                    if (c >= 65536) return fail(h, FDTD_E_INVAL, "more than 65536 distinct edge classes");
-                    classes.emplace(key, c);
-                    keys.push_back(key);
-                } else c = it->second;
-                cls[cid(i, j, k)] = (uint16_t)c;
-                if (!design_touch) by_nbhd.emplace(nk, c);
-            }
+    };
+    {
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nthr; ++t) pool.emplace_back(run_slab, t);
+        run_slab(0);
+        for (auto &th : pool) th.join();
+    }
+    std::unordered_map<ClassKey, int, ClassKeyHash> classes;
+    std::vector<ClassKey> keys;
+    {
+        // class 0: every coefficient zero and no flags; the field kernel reads
+        // it for the cells beyond the far walls, whose E^{n+1} is then zero
+        ClassKey zero;
+        std::memset(&zero, 0, sizeof zero);
+        classes.emplace(zero, 0);
+        keys.push_back(zero);
+    }
+    auto class_of = [&](int i, int j, int k) -> int {
+        const ClassKey key = class_key(i, j, k);
+        auto it = classes.find(key);
+        if (it != classes.end()) return it->second;
+        const int c = (int)keys.size();
+        if (c >= 65536) return -1;
+        classes.emplace(key, c);
+        keys.push_back(key);
+        return c;
+    };
+    const int px = I.px;
+    std::unordered_map<uint64_t, int> key_class;
+    for (const Slab &sl : slabs)
+        for (const auto &kc : sl.keys) {
+            if (key_class.count(kc.first)) continue;
+            const size_t c = kc.second;
+            const int cl = class_of((int)(c % nx), (int)((c / nx) % ny), (int)(c / ((size_t)nx * ny)));
+            if (cl < 0) return fail(h, FDTD_E_INVAL, "more than 65536 distinct edge classes");
+            key_class.emplace(kc.first, cl);
+        }
+    std::vector<long long> over_off;
+    std::vector<uint16_t> over_id;
+    if (has_design)
+        for (int k = db[2]; k <= std::min(nz - 1, db[2] + db[5]); ++k)
+            for (int j = db[1]; j <= std::min(ny - 1, db[1] + db[4]); ++j)
+                for (int i = db[0]; i <= std::min(nx - 1, db[0] + db[3]); ++i)
+                    if (touches_design(i, j, k)) {
+                        const int cl = class_of(i, j, k);
+                        if (cl < 0) return fail(h, FDTD_E_INVAL, "more than 65536 distinct edge classes");
+                        over_off.push_back(((long long)k * ny + j) * px + i);
+                        over_id.push_back((uint16_t)cl);
+                    }
+    std::vector<std::pair<uint64_t, uint16_t>> kc(key_class.begin(), key_class.end());
+    std::sort(kc.begin(), kc.end());
     const int nclass = (int)keys.size();
     const bool c16 = nclass > 256;
-    // magnetic regions: face-connected components of cells with Ms > 0
-    std::vector<int> label(nc, -1);
+    // magnetic regions: face-connected components of cells with Ms > 0,
+    // numbered in the order of their first cell
+    std::unordered_map<size_t, int> label;
+    size_t nmagc = 0;
+    for (const Slab &sl : slabs) nmagc += sl.mag.size();
+    label.reserve(2 * nmagc);
     struct Box { int x0, y0, z0, x1, y1, z1; };
     std::vector<Box> boxes;
     std::vector<size_t> stack;
-    for (size_t c0 = 0; c0 < nc; ++c0) {
-        if (label[c0] >= 0 || table[mid[c0]].Ms <= 0) continue;
-        const int L = (int)boxes.size();
-        Box b{nx, ny, nz, -1, -1, -1};
-        stack.clear();
-        stack.push_back(c0);
-        label[c0] = L;
-        while (!stack.empty()) {
-            const size_t c = stack.back();
-            stack.pop_back();
-            const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((size_t)nx * ny));
-            b.x0 = std::min(b.x0, i); b.y0 = std::min(b.y0, j); b.z0 = std::min(b.z0, k);
-            b.x1 = std::max(b.x1, i); b.y1 = std::max(b.y1, j); b.z1 = std::max(b.z1, k);
-            const int nb[6][3] = {{i - 1, j, k}, {i + 1, j, k}, {i, j - 1, k}, {i, j + 1, k}, {i, j, k - 1}, {i, j, k + 1}};
-            for (auto &q : nb) {
-                if (q[0] < 0 || q[1] < 0 || q[2] < 0 || q[0] >= nx || q[1] >= ny || q[2] >= nz) continue;
-                const size_t cc = cid(q[0], q[1], q[2]);
-                if (label[cc] < 0 && table[mid[cc]].Ms > 0) { label[cc] = L; stack.push_back(cc); }
+    for (const Slab &sl : slabs)
+        for (size_t c0 : sl.mag) {
+            if (label.count(c0)) continue;
+            const int L = (int)boxes.size();
+            Box b{nx, ny, nz, -1, -1, -1};
+            stack.clear();
+            stack.push_back(c0);
+            label.emplace(c0, L);
+            while (!stack.empty()) {
+                const size_t c = stack.back();
+                stack.pop_back();
+                const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((size_t)nx * ny));
+                b.x0 = std::min(b.x0, i); b.y0 = std::min(b.y0, j); b.z0 = std::min(b.z0, k);
+                b.x1 = std::max(b.x1, i); b.y1 = std::max(b.y1, j); b.z1 = std::max(b.z1, k);
+                const int nb[6][3] = {{i - 1, j, k}, {i + 1, j, k}, {i, j - 1, k}, {i, j + 1, k}, {i, j, k - 1}, {i, j, k + 1}};
+                for (auto &q : nb) {
+                    if (q[0] < 0 || q[1] < 0 || q[2] < 0 || q[0] >= nx || q[1] >= ny || q[2] >= nz) continue;
+                    const size_t cc = cid(q[0], q[1], q[2]);
+                    if (magm[mid[cc]] && label.emplace(cc, L).second) stack.push_back(cc);
+                }
             }
+            const long long V = (long long)(b.x1 - b.x0 + 1) * (b.y1 - b.y0 + 1) * (b.z1 - b.z0 + 1);
+            if (V > kMagMaxV)
+                return fail(h, FDTD_E_INVAL, "a magnetic region's bounding box holds " + std::to_string(V) + " cells (maximum " +
+                                                 std::to_string(kMagMaxV) + ")");
+            int qx, py, ps;
+            if (!mag_stage_block(b.x1 - b.x0 + 1, b.y1 - b.y0 + 1, b.z1 - b.z0 + 1, qx, py, ps))
+                return fail(h, FDTD_E_INVAL, "a magnetic region's bounding box has too many faces for one CTA's shared memory");
+            boxes.push_back(b);
         }
-        const long long V = (long long)(b.x1 - b.x0 + 1) * (b.y1 - b.y0 + 1) * (b.z1 - b.z0 + 1);
-        if (V > kMagMaxV)
-            return fail(h, FDTD_E_INVAL, "a magnetic region's bounding box holds " + std::to_string(V) + " cells (maximum " +
-                                             std::to_string(kMagMaxV) + ")");
-        int qx, py, ps;
-        if (!mag_stage_block(b.x1 - b.x0 + 1, b.y1 - b.y0 + 1, b.z1 - b.z0 + 1, qx, py, ps))
-            return fail(h, FDTD_E_INVAL, "a magnetic region's bounding box has too many faces for one CTA's shared memory");
-        boxes.push_back(b);
-    }
     // magnet material table (compact index per magnetic material)
     std::vector<int> mm_index(ntable, 0xFF);
     std::vector<MagMat> mm;
@@ -571,7 +647,8 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
                 for (int li = 0; li < C.bx; ++li) {
                     const int v = (lk * C.by + lj) * C.bx + li;
                     const size_t c = cid(C.x0 + li, C.y0 + lj, C.z0 + lk);
-                    hmat[off + v] = label[c] == (int)L ? (uint8_t)mm_index[mid[c]] : 0xFF;
+                    const auto it = label.find(c);
+                    hmat[off + v] = it != label.end() && it->second == (int)L ? (uint8_t)mm_index[mid[c]] : 0xFF;
                 }
         C.m = I.mbuf + 3 * off;
         C.mat = I.magmat + off;
@@ -586,16 +663,30 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
     bias_frame(u, E);
     // upload: class ids in the padded layout, table, regions; zero the fields
     {
-        std::vector<uint8_t> pad((size_t)I.nz * I.ny * I.px * (c16 ? 2 : 1), 0);
-        for (int k = 0; k < nz; ++k)
-            for (int j = 0; j < ny; ++j)
-                for (int i = 0; i < nx; ++i) {
-                    const size_t o = ((size_t)k * ny + j) * I.px + i;
-                    const uint16_t c = cls[cid(i, j, k)];
-                    if (c16) std::memcpy(pad.data() + 2 * o, &c, 2);
-                    else pad[o] = (uint8_t)c;
-                }
-        CKR(h, cudaMemcpy(I.cls, pad.data(), pad.size(), cudaMemcpyHostToDevice));
+        // class ids on the device: the material ids (the caller's device
+        // array itself, else a copy), the sorted keys and the overrides
+        const size_t nk = kc.size(), no = over_off.size();
+        const size_t o_keys = (nc + 15) / 16 * 16, o_ids = o_keys + nk * 8, o_off = (o_ids + nk * 2 + 15) / 16 * 16,
+                     o_oid = o_off + no * 8, tbytes = o_oid + no * 2 + 16;
+        unsigned char *tmp = (unsigned char *)S->dalloc(tbytes);
+        if (!tmp) return fail(h, FDTD_E_OOM, "device allocation failed");
+        std::vector<uint64_t> hk(nk);
+        std::vector<uint16_t> hid(nk);
+        for (size_t q = 0; q < nk; ++q) { hk[q] = kc[q].first; hid[q] = kc[q].second; }
+        const bool on_dev = !mid_copy.empty();   // mat_id was device memory: read it there
+        cudaError_t e = cudaSuccess;
+        if (!on_dev) e = cudaMemcpyAsync(tmp, mid, nc, cudaMemcpyHostToDevice, S->stream);
+        if (e == cudaSuccess && nk) e = cudaMemcpyAsync(tmp + o_keys, hk.data(), nk * 8, cudaMemcpyHostToDevice, S->stream);
+        if (e == cudaSuccess && nk) e = cudaMemcpyAsync(tmp + o_ids, hid.data(), nk * 2, cudaMemcpyHostToDevice, S->stream);
+        if (e == cudaSuccess && no) e = cudaMemcpyAsync(tmp + o_off, over_off.data(), no * 8, cudaMemcpyHostToDevice, S->stream);
+        if (e == cudaSuccess && no) e = cudaMemcpyAsync(tmp + o_oid, over_id.data(), no * 2, cudaMemcpyHostToDevice, S->stream);
+        if (e == cudaSuccess)
+            e = launch_class_assign(on_dev ? mat_id : tmp, nx, ny, nz, px, (const uint64_t *)(tmp + o_keys),
+                                    (const uint16_t *)(tmp + o_ids), (int)nk, (const long long *)(tmp + o_off),
+                                    (const uint16_t *)(tmp + o_oid), (int)no, I.cls, c16, S->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);   // the host arrays above are released next
+        S->dfree(tmp);
+        CKR(h, e);
         std::vector<float4> tab(3 * (size_t)nclass);
         for (int c = 0; c < nclass; ++c) {
             const uint32_t *w = keys[c].w;
