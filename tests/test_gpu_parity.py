@@ -120,6 +120,51 @@ def test_random_small_every_feature(seed):
     compare_fields(sim, orc, M0, t)
 
 
+@pytest.mark.parametrize("box", [(0, 0, 0, 3, 2, 2), (10, 9, 7, 3, 2, 2)])
+def test_design_box_against_the_walls(box):
+    """Cells whose edges or faces touch a design cell get classes formed from
+    eps_r_design (an override list), every other cell the class of its
+    neighbourhood of materials: a design box against the low walls (its
+    touching cells include wall cells) and one in the far corner (the region
+    of touching cells is clipped by the grid), against the FP64 oracle."""
+    import dataclasses
+
+    w = W.random_small(4, steps=40, design=True)
+    eps = np.random.default_rng(5).uniform(1.0, 12.0, size=(box[5], box[4], box[3]))
+    w = dataclasses.replace(w, design_box=box, eps_design=eps)
+    sim, orc, out, M0 = run_pair(w, w.steps)
+    t = tol(w.steps)
+    for p, (i, j, k) in enumerate(w.probes):
+        errs = probe_errors(sim.probe(p), out["probes"][:, p], M0[:, k, j, i], t, w.steps)
+        assert max(errs) < t, (p, errs)
+    assert rel_err(sim.energy(), out["energy"]) < t
+    compare_fields(sim, orc, M0, t)
+    sim.destroy()
+
+
+def test_materials_from_device_memory_equal_host_memory():
+    """mat_id in device memory (read there by the class kernel, copied for the
+    host's passes) gives the same run, to the bit, as mat_id in host memory."""
+    import torch
+
+    w = W.random_small(6, nx=40, ny=21, nz=19, steps=30, design=True)
+    a = pkg.from_workload(w)
+    b = pkg.FdtdLlg.create(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, courant_factor=w.courant, probe_capacity=w.steps)
+    b.set_materials(torch.from_numpy(w.mat_id.reshape(-1).copy()).cuda(), [pkg.Material(**m) for m in w.materials],
+                    w.hbias, w.eps_design, w.design_box)
+    for s in w.sources:
+        b.set_source(s["comp"], s["i"], s["j"], s["k"], s["J0"], s["f0"], s["Tp"], s["tpk"])
+    for p in w.probes:
+        b.add_probe(*p)
+    a.step(w.steps)
+    b.step(w.steps)
+    for n in ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz", "dMx", "dMy", "dMz"):
+        np.testing.assert_array_equal(a.get_field(n), b.get_field(n))
+    np.testing.assert_array_equal(a.energy(), b.energy())
+    a.destroy()
+    b.destroy()
+
+
 def _large_region(kind, steps):
     """One magnetic region near the size limit of the magnet kernel, touching
     a far wall, in a grid the oracle runs in seconds.  The kernel stages the
