@@ -37,3 +37,118 @@ def job_rate(units_local: float, seconds_local: float, group=None):
     dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
     dist.all_reduce(u, op=dist.ReduceOp.SUM, group=group)
     return float(u.item()) / float(t.item()), float(t.item())
+
+
+# ------------------------------------------------ z-slab domain decomposition
+#
+# One grid over several ranks (the paper's box decomposition, section
+# "Parallelization", along z): rank r owns the cells of planes [a, b) and
+# steps the extended slab [a - ghost, b + ghost) clipped to the grid, whose
+# cut faces it treats as walls.  One step reaches ``step_radius`` cells, so
+# after a step every owned value is exact when ghost >= step_radius; the
+# ghost planes are then refreshed from their owners before the next step.
+# Arrays come in two plane kinds along z: "cell" arrays have nz planes
+# (plane k belongs to cell k) and "face" arrays nz + 1 (plane k is the low z
+# face of cell k, plane nz the top wall, which belongs to the last rank).
+
+
+def step_radius(llg_iterates: int = 0) -> int:
+    """An upper bound on how far along z one full step's values depend on
+    others: one cell for the E push, and per H/M half-push one for the face
+    update plus one per Jacobi iterate of the LLG solve (a fixed count; a
+    tolerance-stopped solve couples a whole magnetic region and must not be
+    cut).  Errors that enter only at the cut faces, as here, reach less far."""
+    return 1 + 2 * (1 + int(llg_iterates))
+
+
+def slab_partition(nz: int, world: int, ghost: int) -> list:
+    """Per rank (a, b, ea, eb): owned cell planes [a, b) (as equal as the
+    planes allow, the lower ranks taking the remainder) and the extended slab
+    [ea, eb) = [a - ghost, b + ghost) clipped to [0, nz)."""
+    if world < 1 or nz < world:
+        raise ValueError("need 1 <= world <= nz")
+    if ghost < 0:
+        raise ValueError("ghost must be >= 0")
+    base, extra = divmod(nz, world)
+    out, a = [], 0
+    for r in range(world):
+        b = a + base + (1 if r < extra else 0)
+        out.append((a, b, max(0, a - ghost), min(nz, b + ghost)))
+        a = b
+    return out
+
+
+def plane_owner(k: int, parts: list, kind: str = "cell") -> int:
+    """Rank owning plane k of an array of the given kind."""
+    nz = parts[-1][1]
+    if kind == "face" and k == nz:
+        return len(parts) - 1
+    for r, (a, b, _, _) in enumerate(parts):
+        if a <= k < b:
+            return r
+    raise ValueError("plane outside the grid")
+
+
+def halo_plan(parts: list, rank: int, kind: str = "cell") -> tuple:
+    """(sends, recvs): lists of (peer, k0, k1) global plane ranges.  recvs are
+    this rank's ghost planes grouped by owner; sends the owned planes that lie
+    in another rank's ghost range."""
+    nz = parts[-1][1]
+    top = nz + 1 if kind == "face" else nz
+
+    def ghosts(r):
+        a, b, ea, eb = parts[r]
+        hi = eb + 1 if kind == "face" and eb == nz else eb
+        own_hi = b + 1 if kind == "face" and b == nz else b
+        return [k for k in range(ea, min(hi, top)) if not (a <= k < own_hi)]
+
+    def runs(ks, owner_of):
+        out = []
+        for k in ks:
+            o = owner_of(k)
+            if out and out[-1][0] == o and out[-1][2] == k:
+                out[-1][2] = k + 1
+            else:
+                out.append([o, k, k + 1])
+        return [tuple(x) for x in out]
+
+    recvs = runs(ghosts(rank), lambda k: plane_owner(k, parts, kind))
+    sends = []
+    for r in range(len(parts)):
+        if r == rank:
+            continue
+        mine = [k for k in ghosts(r) if plane_owner(k, parts, kind) == rank]
+        sends += [(r, k0, k1) for (_, k0, k1) in runs(mine, lambda k: r)]
+    return sends, recvs
+
+
+def exchange_halos(arrays: list, kinds: list, parts: list, rank: int, z_axes=None, group=None) -> None:
+    """Refresh this rank's ghost planes of every array from their owners
+    (point-to-point over the default process group).  arrays: numpy arrays or
+    CPU torch tensors in this rank's extended-slab indexing (local plane k -
+    ea along axis z_axes[i], default 0); kinds: "cell" or "face" per array.
+    Every rank calls it with the same arrays in the same order."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    ea = parts[rank][2]
+    z_axes = z_axes or [0] * len(arrays)
+    reqs, landing = [], []
+    for q, (arr, kind, ax) in enumerate(zip(arrays, kinds, z_axes)):
+        t = torch.from_numpy(arr) if isinstance(arr, np.ndarray) else arr
+        sends, recvs = halo_plan(parts, rank, kind)
+        for peer, k0, k1 in sends:
+            buf = t.narrow(ax, k0 - ea, k1 - k0).contiguous()
+            reqs.append(dist.isend(buf, dst=peer, group=group, tag=q))
+            landing.append(buf)   # kept alive until the waits
+        for peer, k0, k1 in recvs:
+            buf = torch.empty_like(t.narrow(ax, k0 - ea, k1 - k0).contiguous())
+            reqs.append(dist.irecv(buf, src=peer, group=group, tag=q))
+            landing.append((t, ax, k0 - ea, k1 - k0, buf))
+    for r in reqs:
+        r.wait()
+    for item in landing:
+        if isinstance(item, tuple):
+            t, ax, o, n, buf = item
+            t.narrow(ax, o, n).copy_(buf)

@@ -1,6 +1,7 @@
-"""Multi-rank host logic on CPU ranks (gloo, world size 2): the whole-job
-rate (units of all ranks over the slowest rank's time) and the partition of
-a batch's instances over ranks."""
+"""Multi-rank host logic on CPU ranks (gloo): the whole-job rate (units of
+all ranks over the slowest rank's time), the partition of a batch's
+instances over ranks, and the z-slab decomposition of one grid with halo
+exchange, checked on the FP64 oracle against the undivided run."""
 import os
 import socket
 
@@ -8,7 +9,8 @@ import numpy as np
 import pytest
 import torch.multiprocessing as mp
 
-from paper_2510_22221_b300.distributed import job_rate, shard_instances
+from paper_2510_22221_b300.distributed import (exchange_halos, halo_plan, job_rate, shard_instances, slab_partition,
+                                               step_radius)
 
 
 def _free_port():
@@ -54,3 +56,106 @@ def test_shard_instances_balanced_and_complete():
         loads = [int(sum(cells[q] for q in s)) for s in sh]
         assert max(loads) - min(loads) <= int(cells.max())
         assert sh == shard_instances(cells, world)       # deterministic
+
+
+# ------------------------------------------------------------ z slabs
+
+_FIELDS = (("Ex", "face", 0), ("Ey", "face", 0), ("Ez", "cell", 0), ("Hx", "cell", 0), ("Hy", "cell", 0),
+           ("Hz", "face", 0), ("M", "cell", 1))
+_ITER = 3
+
+
+def _slab_workload():
+    """A 13 x 11 x 30 grid with every feature, and at the cut between two
+    ranks (z = 15) a PEC cell, a magnetic region across it and a source."""
+    from paper_2510_22221_b300 import workloads as W
+
+    w = W.random_small(21, nx=13, ny=11, nz=30, steps=14, design=True)
+    mid = w.mat_id.copy()
+    mid[13:18, 4:7, 5:9] = 3
+    src = w.sources + [dict(comp=2, i=6, j=8, k=14, J0=2e6, f0=5e12, Tp=1.2e-13, tpk=2.5e-13)]
+    import dataclasses
+
+    return dataclasses.replace(w, mat_id=mid, sources=src)
+
+
+def _slab_oracle(w, ea, eb):
+    """The oracle on cells [ea, eb) of the workload along z."""
+    import oracle
+    from tests.helpers import oracle_from_workload
+
+    full = oracle_from_workload(w, llg_fixed_iter=_ITER)
+    mats = full.materials
+    srcs = [oracle.Source(comp=s["comp"], ijk=(s["i"], s["j"], s["k"] - ea), J0=s["J0"], f0=s["f0"], Tp=s["Tp"],
+                          tpk=s["tpk"]) for s in w.sources if ea <= s["k"] < eb]
+    eps = None if full.eps_r_cell is None else full.eps_r_cell[ea:eb]
+    return oracle.OracleSim(w.nx, w.ny, eb - ea, w.dx, w.dy, w.dz, full.dt, mats, w.mat_id[ea:eb], w.hbias,
+                            sources=srcs, eps_r_cell=eps, llg_fixed_iter=_ITER)
+
+
+def _slab_worker(rank, world, port, out):
+    import torch.distributed as dist
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    w = _slab_workload()
+    parts = slab_partition(w.nz, world, step_radius(_ITER))
+    a, b, ea, eb = parts[rank]
+    sub = _slab_oracle(w, ea, eb)
+    for _ in range(w.steps):
+        sub.run(1)
+        exchange_halos([getattr(sub, n) for n, _, _ in _FIELDS], [k for _, k, _ in _FIELDS], parts, rank,
+                       z_axes=[ax for _, _, ax in _FIELDS])
+    own = {}
+    for n, kind, ax in _FIELDS:
+        hi = b + 1 if kind == "face" and b == w.nz else b
+        own[n] = np.take(getattr(sub, n), range(a - ea, hi - ea), axis=ax)
+    out[rank] = own
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_z_slabs_with_halo_exchange_equal_the_whole_grid(world):
+    """Each rank steps its slab extended by step_radius ghost planes (cut
+    faces as walls) and refreshes the ghosts from their owners after every
+    step: the owned planes of every field and of M equal the undivided FP64
+    oracle run to the bit, across a PEC cell, a magnetic region (fixed LLG
+    iterates) and a source at the cut."""
+    from tests.helpers import oracle_from_workload
+
+    w = _slab_workload()
+    ref = oracle_from_workload(w, llg_fixed_iter=_ITER)
+    ref.run(w.steps)
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        mp.start_processes(_slab_worker, args=(world, _free_port(), out), nprocs=world, start_method="spawn")
+        res = dict(out)
+    for n, kind, ax in _FIELDS:
+        got = np.concatenate([res[r][n] for r in range(world)], axis=ax)
+        want = getattr(ref, n)
+        assert got.shape == want.shape, n
+        np.testing.assert_array_equal(got, want, err_msg=n)
+    assert np.abs(ref.M).max() > 0 and np.abs(ref.Ez).max() > 0
+
+
+def test_halo_plan_covers_every_ghost_plane_once():
+    """Every ghost plane of every rank is received once from its owner, and
+    what each rank sends is exactly what its peers receive from it."""
+    for nz, world, ghost in ((30, 2, 9), (10, 3, 2), (17, 4, 5), (5, 5, 3)):
+        parts = slab_partition(nz, world, ghost)
+        assert [p[0] for p in parts] == sorted(p[0] for p in parts) and parts[-1][1] == nz
+        for kind, top in (("cell", nz), ("face", nz + 1)):
+            plans = [halo_plan(parts, r, kind) for r in range(world)]
+            for r, (_, recvs) in enumerate(plans):
+                a, b, ea, eb = parts[r]
+                got = sorted(k for (_, k0, k1) in recvs for k in range(k0, k1))
+                hi = min(eb + (1 if kind == "face" and eb == nz else 0), top)
+                own_hi = b + (1 if kind == "face" and b == nz else 0)
+                assert got == [k for k in range(ea, hi) if not (a <= k < own_hi)]
+                for peer, k0, k1 in recvs:
+                    assert (r, k0, k1) in plans[peer][0]
+            sent = sorted((r, p, k0, k1) for r in range(world) for (p, k0, k1) in plans[r][0])
+            recv = sorted((src, r, k0, k1) for r in range(world) for (src, k0, k1) in plans[r][1])
+            assert sent == recv
