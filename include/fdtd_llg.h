@@ -207,6 +207,22 @@ int fdtd_llg_time_state(fdtd_llg_t h, int64_t *step, int32_t *h_half_ahead);
 int fdtd_llg_get_field(fdtd_llg_t h, int32_t which, float *out, size_t count);
 int fdtd_llg_set_field(fdtd_llg_t h, int32_t which, const float *in, size_t count);
 
+/* The stored state of z-planes [k0, k1) (the cells k0 .. k1-1 and their low
+ * faces and edges), copied exactly between the handle and buf (host memory,
+ * float32) without changing the time state: the halo exchange of one grid
+ * split into z-slabs over several handles or processes (the box
+ * decomposition of section "Parallelization").  to_handle = 0 reads the
+ * handle into buf (after a synchronisation; latched run errors are
+ * returned), 1 writes buf into the handle.  buf holds, with P = k1 - k0:
+ * Ex, Ey, Ez, Hx, Hy, Hz (each P x ny x nx, compact layout), the far-wall
+ * normal H of those planes (Hx at x = nx: P x ny; Hy at y = ny: P x nx), then
+ * the magnetisation deviation M - Ms h of the magnetic cells in the frame of
+ * the bias, as stored (3 x P x ny x nx, zero elsewhere; ignored on write
+ * outside magnetic cells): P (9 nx ny + nx + ny) floats.  Errors:
+ * FDTD_E_RANGE (planes outside the grid), FDTD_E_INVAL (batch handle, small
+ * buffer), FDTD_E_STATE (no materials). */
+int fdtd_llg_planes(fdtd_llg_t h, int32_t k0, int32_t k1, float *buf, size_t count, int32_t to_handle);
+
 /* Checkpoint / resume of E, H, M, wall faces, step and time state.
  * buf = NULL: *size receives the byte count needed. */
 int fdtd_llg_save_state(fdtd_llg_t h, void *buf, size_t *size);

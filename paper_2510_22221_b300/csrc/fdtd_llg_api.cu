@@ -1423,6 +1423,68 @@ extern "C" int fdtd_llg_set_field(fdtd_llg_t h, int32_t which, const float *in, 
     return FDTD_OK;
 }
 
+extern "C" int fdtd_llg_planes(fdtd_llg_t h, int32_t k0, int32_t k1, float *buf, size_t count, int32_t to_handle)
+{
+    if (!is_member(h)) return fail(h, FDTD_E_INVAL, "planes needs an instance handle");
+    Instance *I = inst_of(h);
+    if (!I->materials_set) return fail(h, FDTD_E_STATE, "set materials first");
+    const int nx = I->nx, ny = I->ny, nz = I->nz;
+    if (k0 < 0 || k1 > nz || k0 >= k1) return fail(h, FDTD_E_RANGE, "plane range outside the grid");
+    const size_t P = (size_t)(k1 - k0), pl = (size_t)nx * ny;
+    const size_t need = P * (9 * pl + nx + ny);
+    if (!buf || count < need) return fail(h, FDTD_E_INVAL, "buffer too small");
+    int rc = to_handle ? 0 : sync_status(h);
+    if (rc) return rc;
+    CKR(h, cudaStreamSynchronize(h->sim->stream));
+    const size_t nf = I->n_field();
+    const cudaMemcpyKind kind = to_handle ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+    // E and H: six arrays of P planes, rows of nx from the padded rows of px
+    for (int q = 0; q < 6; ++q) {
+        float *dev = I->fields[h->sim->cur] + q * nf + (size_t)k0 * ny * I->px;
+        float *host = buf + q * P * pl;
+        if (to_handle)
+            CKR(h, cudaMemcpy2D(dev, I->px * sizeof(float), host, nx * sizeof(float), nx * sizeof(float), P * ny, kind));
+        else
+            CKR(h, cudaMemcpy2D(host, nx * sizeof(float), dev, I->px * sizeof(float), nx * sizeof(float), P * ny, kind));
+    }
+    // far-wall normal H that has z planes: Hx at x = nx (ny per plane), Hy at y = ny (nx per plane)
+    {
+        float *hx = I->walls + (size_t)k0 * ny, *hy = I->walls + (size_t)ny * nz + (size_t)k0 * nx;
+        float *bx = buf + 6 * P * pl, *by = bx + P * ny;
+        if (to_handle) {
+            CKR(h, cudaMemcpy(hx, bx, P * ny * sizeof(float), kind));
+            CKR(h, cudaMemcpy(hy, by, P * nx * sizeof(float), kind));
+        } else {
+            CKR(h, cudaMemcpy(bx, hx, P * ny * sizeof(float), kind));
+            CKR(h, cudaMemcpy(by, hy, P * nx * sizeof(float), kind));
+        }
+    }
+    // the magnetisation deviation of magnetic cells, as stored (bias frame)
+    float *bm = buf + 6 * P * pl + P * (nx + ny);
+    if (!to_handle) std::fill(bm, bm + 3 * P * pl, 0.f);
+    for (const MagComp &C : I->comps) {
+        const int z0 = std::max(k0, C.z0), z1 = std::min(k1, C.z0 + C.bz);
+        if (z0 >= z1) continue;
+        std::vector<float> m(3 * (size_t)C.V);
+        std::vector<uint8_t> mt(C.V);
+        CKR(h, cudaMemcpy(m.data(), C.m, m.size() * sizeof(float), cudaMemcpyDeviceToHost));
+        CKR(h, cudaMemcpy(mt.data(), C.mat, C.V, cudaMemcpyDeviceToHost));
+        for (int k = z0; k < z1; ++k)
+            for (int lj = 0; lj < C.by; ++lj)
+                for (int li = 0; li < C.bx; ++li) {
+                    const int v = ((k - C.z0) * C.by + lj) * C.bx + li;
+                    if (mt[v] == 0xFF) continue;
+                    const size_t o = ((size_t)(k - k0) * ny + (C.y0 + lj)) * nx + (C.x0 + li);
+                    for (int d = 0; d < 3; ++d) {
+                        if (to_handle) m[(size_t)d * C.V + v] = bm[d * P * pl + o];
+                        else bm[d * P * pl + o] = m[(size_t)d * C.V + v];
+                    }
+                }
+        if (to_handle) CKR(h, cudaMemcpy(C.m, m.data(), m.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    return FDTD_OK;
+}
+
 // ---------------------------------------------------------- checkpoints
 namespace {
 struct StateHeader {

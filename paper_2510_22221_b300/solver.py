@@ -268,6 +268,22 @@ class FdtdLlg:
         check(_abi.load().fdtd_llg_set_field(self._h, FIELDS[name], arr.ctypes.data_as(C.POINTER(C.c_float)),
                                              arr.size), self._h)
 
+    def read_planes(self, k0: int, k1: int) -> np.ndarray:
+        """The stored state of z-planes [k0, k1) as one float32 array (layout
+        of fdtd_llg_planes), exact and without changing the time state."""
+        nx, ny, _ = self._dims
+        out = np.empty((k1 - k0) * (9 * nx * ny + nx + ny), dtype=np.float32)
+        check(_abi.load().fdtd_llg_planes(self._h, int(k0), int(k1), out.ctypes.data_as(C.POINTER(C.c_float)),
+                                          out.size, 0), self._h)
+        return out
+
+    def write_planes(self, k0: int, k1: int, data):
+        """Overwrite the stored state of z-planes [k0, k1) with what
+        read_planes returned (possibly from another handle's slab)."""
+        arr = np.ascontiguousarray(data, dtype=np.float32).reshape(-1)
+        check(_abi.load().fdtd_llg_planes(self._h, int(k0), int(k1), arr.ctypes.data_as(C.POINTER(C.c_float)),
+                                          arr.size, 1), self._h)
+
     def save_state(self) -> bytes:
         lib = _abi.load()
         n = C.c_size_t()
