@@ -487,7 +487,8 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
     };
     const int nthr = std::max(1, std::min({(int)std::thread::hardware_concurrency(), 16, nz}));
     std::vector<Slab> slabs(nthr);
-    auto run_slab = [&](int t) {
+    std::vector<char> slab_failed(nthr, 0);
+    auto scan_slab = [&](int t) {
         Slab &sl = slabs[t];
         const int ka = (int)((long long)nz * t / nthr), kb = (int)((long long)nz * (t + 1) / nthr);
         std::unordered_map<uint64_t, int> seen;
@@ -514,12 +515,26 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
                     if (seen.emplace(nk, 0).second) sl.keys.emplace_back(nk, c0);
                 }
     };
+    auto run_slab = [&](int t) {
+        try {
+            scan_slab(t);
+        } catch (...) {   // an allocation failed: reported below, never thrown across threads
+            slab_failed[t] = 1;
+        }
+    };
     {
+        // slabs whose thread cannot be started run here
         std::vector<std::thread> pool;
-        for (int t = 1; t < nthr; ++t) pool.emplace_back(run_slab, t);
+        try {
+            for (int t = 1; t < nthr; ++t) pool.emplace_back(run_slab, t);
+        } catch (...) {
+        }
+        for (int t = (int)pool.size() + 1; t < nthr; ++t) run_slab(t);
         run_slab(0);
         for (auto &th : pool) th.join();
     }
+    for (char f : slab_failed)
+        if (f) return fail(h, FDTD_E_OOM, "host allocation failed");
     std::unordered_map<ClassKey, int, ClassKeyHash> classes;
     std::vector<ClassKey> keys;
     {
