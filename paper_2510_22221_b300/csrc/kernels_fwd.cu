@@ -286,7 +286,7 @@ __device__ __forceinline__ void sum2_add(float &s, float &c, float x)
 // edges, then per block of edge sites H and the class ids), so that the set-up
 // costs one memory round trip per block instead of one per dependent load,
 // and evaluates E^{n+1} at every box edge with the arithmetic of step_kernel.
-template <bool FUSED, typename ClsT>
+template <bool FUSED, typename ClsT, int CPT>
 __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
 {
     extern __shared__ float smem[];
@@ -460,16 +460,16 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
         for (int v = tid; v < V; v += nth) sD[v] = sD[V + v] = sD[2 * V + v] = 0.f;
         __syncthreads();
         // Jacobi iteration of Eq. llg_tra4 with H_eff^{r-1} from the previous iterate
-        float dl[kMagCPT][3];   // last iterate's change of m, bias frame
+        float dl[CPT][3];   // last iterate's change of m, bias frame
 #pragma unroll
-        for (int q = 0; q < kMagCPT; ++q) dl[q][0] = dl[q][1] = dl[q][2] = 0.f;
+        for (int q = 0; q < CPT; ++q) dl[q][0] = dl[q][1] = dl[q][2] = 0.f;
         int r = 0;
         for (;;) {
             ++r;
             float res = 0.f;
-            float dn[kMagCPT][3];
+            float dn[CPT][3];
 #pragma unroll
-            for (int q = 0; q < kMagCPT; ++q) {
+            for (int q = 0; q < CPT; ++q) {
                 dn[q][0] = dn[q][1] = dn[q][2] = 0.f;
                 const int v = tid + q * nth;
                 if (v >= V) continue;
@@ -534,7 +534,7 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
             }
             __syncthreads();
 #pragma unroll
-            for (int q = 0; q < kMagCPT; ++q) {
+            for (int q = 0; q < CPT; ++q) {
                 const int v = tid + q * nth;
                 if (v < V && smat[v] != 0xFF) {
                     sD[v] = dn[q][0];
@@ -577,7 +577,7 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
         }
         if (rec) eacc += (double)es + (double)ec;
 #pragma unroll
-        for (int q = 0; q < kMagCPT; ++q) {
+        for (int q = 0; q < CPT; ++q) {
             const int v = tid + q * nth;
             if (v < V && smat[v] != 0xFF) {
                 sM[v] += dl[q][0];
@@ -1194,6 +1194,21 @@ static StepFn step_fn(bool cls16, bool stab, int sx)
     return stab ? step_kernel<uint8_t, true, 64> : step_kernel<uint8_t, false, 64>;
 }
 
+// The magnet kernel with c cells per thread (1, 2, 4 or kMagCPT): the fewest
+// that cover the largest region of the launch, so that the per-thread
+// arrays and the unrolled cell loop hold no cells that cannot exist.
+template <bool FUSED, typename ClsT>
+static void (*mag_fn(int c))(LaunchSet)
+{
+    static_assert(kMagCPT == 8, "cells per thread: 1, 2, 4 or 8");
+    if (c <= 1) return mag_kernel<FUSED, ClsT, 1>;
+    if (c <= 2) return mag_kernel<FUSED, ClsT, 2>;
+    if (c <= 4) return mag_kernel<FUSED, ClsT, 4>;
+    return mag_kernel<FUSED, ClsT, 8>;
+}
+
+static int mag_cpt(int vmax) { return vmax <= kMagThreads ? 1 : vmax <= 2 * kMagThreads ? 2 : vmax <= 4 * kMagThreads ? 4 : 8; }
+
 static cudaError_t step_attrs()
 {
     static bool done = false;
@@ -1202,9 +1217,13 @@ static cudaError_t step_attrs()
     for (int q = 0; q < 8 && e == cudaSuccess; ++q)
         e = cudaFuncSetAttribute(step_fn(q & 1, (q >> 1) & 1, (q & 4) ? 32 : 64), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kStepSmem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(mag_kernel<true, uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMagSmemMax);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(mag_kernel<true, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMagSmemMax);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(mag_kernel<false, uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMagSmemMax);
+    for (int c = 1; c <= kMagCPT && e == cudaSuccess; c *= 2) {
+        e = cudaFuncSetAttribute(mag_fn<true, uint8_t>(c), cudaFuncAttributeMaxDynamicSharedMemorySize, kMagSmemMax);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(mag_fn<true, uint16_t>(c), cudaFuncAttributeMaxDynamicSharedMemorySize, kMagSmemMax);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(mag_fn<false, uint8_t>(c), cudaFuncAttributeMaxDynamicSharedMemorySize, kMagSmemMax);
+    }
     done = e == cudaSuccess;
     return e;
 }
@@ -1222,7 +1241,7 @@ cudaError_t launch_half(const LaunchSet &L, cudaStream_t s)
     cudaError_t e = step_attrs();
     if (e != cudaSuccess) return e;
     if (L.ncomp) {
-        mag_kernel<false, uint8_t><<<L.ncomp, kMagThreads, L.mag_smem, s>>>(L);
+        mag_fn<false, uint8_t>(mag_cpt(L.vmax))<<<L.ncomp, kMagThreads, L.mag_smem, s>>>(L);
     }
     const dim3 blk(kTX, kTY);
     if (L.cls16) h_half_kernel<uint16_t><<<L.grid_h, blk, 0, s>>>(L);
@@ -1249,8 +1268,8 @@ cudaError_t launch_step(const LaunchSet &L, cudaStream_t s, cudaEvent_t *prof)
     if (e != cudaSuccess) return e;
     if (L.ncomp) {
         if (prof) cudaEventRecord(prof[2], s);
-        if (L.cls16) mag_kernel<true, uint16_t><<<L.ncomp, kMagThreads, L.mag_smem, s>>>(L);
-        else mag_kernel<true, uint8_t><<<L.ncomp, kMagThreads, L.mag_smem, s>>>(L);
+        if (L.cls16) mag_fn<true, uint16_t>(mag_cpt(L.vmax))<<<L.ncomp, kMagThreads, L.mag_smem, s>>>(L);
+        else mag_fn<true, uint8_t>(mag_cpt(L.vmax))<<<L.ncomp, kMagThreads, L.mag_smem, s>>>(L);
         if (prof) cudaEventRecord(prof[3], s);
     }
     if (prof) cudaEventRecord(prof[0], s);
