@@ -148,3 +148,28 @@ def test_adjoint_on_a_stream_of_its_own_equals_the_default_stream():
     torch.cuda.synchronize()
     np.testing.assert_array_equal(g, g_ref)
     assert h == h_ref
+
+
+@pytest.mark.parametrize("budget", [-1, 0])
+def test_checkpointed_run_streams_its_results(budget):
+    """run_checkpointed streams every step's probe rows and energy into the
+    host rings like step does (pinned rings: written by the kernel that ends
+    each segment), whether its tape records the run or not, and the rings
+    then equal the device records."""
+    w = W.adjoint_small(n=16, steps=120, design=(6, 6, 2), block=(4, 4, 2))
+    N, cap = 120, 50
+    sim = pkg.from_workload(w, probe_capacity=N, llg_fixed_iter=3)
+    sim.set_tape_budget(budget)
+    rows = torch.zeros((cap, len(w.probes), 9), dtype=torch.float64).pin_memory()
+    energy = torch.zeros(cap, dtype=torch.float64).pin_memory()
+    sim.stream_results(rows, energy)
+    sim.run_checkpointed(N, 11)
+    sim.sync()
+    ref_e = sim.energy()
+    ref_rows = [sim.probe(p) for p in range(len(w.probes))]
+    for n in range(N - cap, N):
+        assert energy[n % cap].item() == ref_e[n]
+        for p in range(len(w.probes)):
+            np.testing.assert_array_equal(rows[n % cap, p].numpy(), ref_rows[p][n])
+    sim.stream_results()
+    sim.destroy()
