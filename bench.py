@@ -304,6 +304,8 @@ def main():
     ap.add_argument("--only", choices=["adjoint", "sweep", "large"],
                     help="run just one of the extra measurements and print its JSON object")
     ap.add_argument("--adjoint-steps", type=int, default=4000, help="steps of the adjoint measurement")
+    ap.add_argument("--tiling", type=int, default=0,
+                    help="z-planes per sweep task for the headline run (0: autotune when --steps >= 1000)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -345,7 +347,17 @@ def main():
     sim = pkg.from_workload(w, probe_capacity=K + Wm + 16)
 
     sim.step(Wm)
+    # planes per task and tile width: fixed by --tiling, else the library's
+    # autotuner with real (untimed) steps on runs long enough to repay it,
+    # else its cost model
+    if args.tiling > 0:
+        sim.set_tiling(args.tiling)
+    elif K >= 1000:
+        sim.autotune(trial_steps=64)
+    sim.step(Wm)
     sim.sync()
+    tiling = {"planes_per_task": sim.get_tiling(), "tile": f"{sim.get_tile_width()}x{256 // (sim.get_tile_width() // 2)}",
+              "chosen_by": "--tiling" if args.tiling > 0 else ("autotune" if K >= 1000 else "cost model")}
 
     def barrier():
         if world > 1:
@@ -394,7 +406,7 @@ def main():
             "config": {"workload": w.name, "cells": w.cells, "dx_m": w.dx, "magnet_cells": int((w.mat_id == 3).sum()),
                        "probes": len(w.probes), "energy": "every step, FP64",
                        "l2": "field state 201 MB > 126 MB L2: inputs larger than L2, no flush",
-                       "parallelism": "one independent grid per GPU" if world > 1 else "single GPU"},
+                       "parallelism": "one independent grid per GPU" if world > 1 else "single GPU", "tiling": tiling},
             "hbm_roofline_pct": round(100 * value * 1e6 * ALG_BYTES_PER_CELL_STEP / (world * hbm * 1e9), 2),
             # two kernels per step (magnet, sweep), one energy flush per step call
             "roofline": roofline, "gpu_launches": (2 if passes["mag"]["launches"] else 1) * K + 1, "clocks": clk,

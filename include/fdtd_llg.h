@@ -288,8 +288,10 @@ int fdtd_llg_get_tiling(fdtd_llg_t h, int32_t *planes);
 
 /* Autotuner of the tiling.  Runs trial_steps real steps (they advance the
  * simulation, fill the probe and energy rings and count in the step number)
- * with each of a fixed list of candidate plane counts plus the model's
- * choice, first at the tile width of fewest padded cells and then at the
+ * with each of a fixed list of candidate plane counts (8, 12, 16, 24, 32, 48,
+ * 64), the model's choice and the counts the model rates within 5 % of it
+ * (at most 12: the model does not see how the tasks fill the last wave of
+ * CTAs), first at the tile width of fewest padded cells and then at the
  * other width, timed with CUDA events on the handle's stream, and keeps the
  * fastest (plane count, width); the plane count is returned in *planes (may
  * be NULL), the width by fdtd_llg_get_tile_width.  The handle then holds

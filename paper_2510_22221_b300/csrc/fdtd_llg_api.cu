@@ -858,24 +858,52 @@ static int columns_of(const Instance &I, int sx)
 // the P with the smallest modelled time wins (the smallest on ties).
 // (Measured against it: a schedule of long tasks drawn first and short ones
 // last was 2 % slower on a 256 x 256 x 128 grid and within 3 % elsewhere.)
+// Cost model of the field sweep for P planes per task (in plane-times of one
+// CTA slot): the items each slot reads (a task of p planes costs p + 1.4: the
+// H plane below and the extra E^{n+1} plane above) and half the longest task
+// for the tail.
+static double model_cost(const Sim *S, int P, int slots)
+{
+    double items = 0;
+    int maxt = 0;
+    for (const Instance &I : S->inst) {
+        const int pk = std::min(P, I.nz), nch = (I.nz + pk - 1) / pk;
+        items += (double)columns_of(I, S->sx) * (I.nz + 1.4 * nch);
+        maxt = std::max(maxt, pk);
+    }
+    return items / std::max(1, slots) + 0.5 * (maxt + 1.4);
+}
+
+static int max_planes(const Sim *S)
+{
+    int maxnz = 1;
+    for (const Instance &I : S->inst) maxnz = std::max(maxnz, I.nz);
+    return std::max(2, std::min(maxnz, 128));
+}
+
 static int model_planes(const Sim *S, int slots)
 {
-    int best = kSZ, maxnz = 1;
+    int best = kSZ;
     double best_t = 1e300;
-    const double sl = std::max(1, slots);
-    for (const Instance &I : S->inst) maxnz = std::max(maxnz, I.nz);
-    for (int P = 2; P <= std::max(2, std::min(maxnz, 128)); ++P) {
-        double items = 0;
-        int maxt = 0;
-        for (const Instance &I : S->inst) {
-            const int pk = std::min(P, I.nz), nch = (I.nz + pk - 1) / pk;
-            items += (double)columns_of(I, S->sx) * (I.nz + 1.4 * nch);
-            maxt = std::max(maxt, pk);
-        }
-        const double t = items / sl + 0.5 * (maxt + 1.4);
+    for (int P = 2; P <= max_planes(S); ++P) {
+        const double t = model_cost(S, P, slots);
         if (t < best_t * (1.0 - 1e-9)) { best_t = t; best = P; }
     }
     return best;
+}
+
+// The plane counts the model rates within frac of its best, best first, at
+// most n of them: the model ignores how the tasks fill the last wave of
+// CTAs, which decides between such near ties.
+static std::vector<int> model_near(const Sim *S, int slots, double frac, size_t n)
+{
+    std::vector<std::pair<double, int>> c;
+    for (int P = 2; P <= max_planes(S); ++P) c.emplace_back(model_cost(S, P, slots), P);
+    std::sort(c.begin(), c.end());
+    std::vector<int> out;
+    for (const auto &q : c)
+        if (q.first <= c[0].first * (1.0 + frac) && out.size() < n) out.push_back(q.second);
+    return out;
 }
 
 static int upload_descriptors(fdtd_llg_t h)
@@ -1654,6 +1682,7 @@ extern "C" int fdtd_llg_autotune(fdtd_llg_t h, int32_t trial_steps, int32_t *pla
     if (rc) return rc;
     const int w0 = S->sx;
     std::vector<int> cand = {S->planes, 8, 12, 16, 24, 32, 48, 64};
+    for (int P : model_near(S, S->nsm * std::max(1, step_blocks_per_sm(false, true, S->sx)), 0.05, 12)) cand.push_back(P);
     int maxnz = 1;
     for (const Instance &I : S->inst) maxnz = std::max(maxnz, I.nz);
     for (int &c : cand) c = std::min(c, maxnz);
