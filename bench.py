@@ -414,8 +414,9 @@ def main():
 
     # end to end through the public API: materials from pinned host memory,
     # then every step a step call whose probe rows and energy stream into
-    # pinned host rings (copied after each call, no per-step wait); the
-    # timed region ends when the last step's results are on the host
+    # pinned host rings (written by the kernel that ends each call, no
+    # per-step wait); the timed region ends when the last step's results are
+    # on the host
     ke = K
     mat_pinned = torch.from_numpy(np.ascontiguousarray(w.mat_id).reshape(-1)).pin_memory()
     rows_h = torch.empty((ke, len(w.probes), 9), dtype=torch.float64).pin_memory()
@@ -424,6 +425,8 @@ def main():
     t0 = time.perf_counter()
     sim2 = pkg.FdtdLlg.create(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, courant_factor=w.courant, probe_capacity=ke + 8)
     sim2.set_materials(mat_pinned, [pkg.Material(**m) for m in w.materials], w.hbias)
+    sim2.set_tiling(tiling["planes_per_task"])      # the tiling tuned above, reused as a user would
+    sim2.set_tile_width(sim.get_tile_width())
     for s in w.sources:
         sim2.set_source(s["comp"], s["i"], s["j"], s["k"], s["J0"], s["f0"], s["Tp"], s["tpk"])
     for p in w.probes:
@@ -440,8 +443,9 @@ def main():
     line["e2e"] = {"value": round(world * w.cells * ke / te / 1e6, 1), "unit": UNIT,
                    "h2d_bytes_per_step": round((w.cells + 64 * len(w.materials)) / ke, 1),
                    "d2h_bytes_per_step": 8 * (9 * len(w.probes) + 1), "steps": ke,
-                   "includes": "create + set_materials (host preprocessing, H2D) + per step: step call and D2H of the "
-                               "step's probe rows and energy into pinned host rings; one synchronisation at the end"}
+                   "includes": "create + set_materials (host preprocessing, H2D) + the headline run's tiling + per step: "
+                               "step call and D2H of the step's probe rows and energy into pinned host rings; one "
+                               "synchronisation at the end"}
 
     if not args.no_extra and rank == 0:
         adj = adjoint_ratio(torch, pkg, W, steps=args.adjoint_steps, n0=args.adjoint_steps * 3 // 4)
