@@ -1,7 +1,9 @@
 """Parity at full size: the 256x256x128 strip resonator and the 512x512x256
 eight-strip array, run as the benchmark runs them (whole grid, default
 tiling, a stream of their own), against the FP64 oracle on outputs it can
-compute one by one (arxiv 2510.22221, section "Numerical Model").
+compute one by one (arxiv 2510.22221, section "Numerical Model"); the
+64-cube bias sweep and the 128x128x64 design grid, which the oracle runs
+whole, cell by cell (at the end of this file).
 
 An explicit Yee step reaches one cell further per step: E^{n+1} at a cell
 uses H^{n+1/2} of that cell and its low neighbours, which use E^n of the cell
@@ -159,3 +161,102 @@ def test_full_size_window_equals_oracle(full_run, which):
     scale = max(max(float(np.abs(v).max()) for v in dm.values()), m_floor(float(np.abs(M0).max()), orc.step) / t)
     for n, v in dm.items():
         assert rel_err(got["d" + n][sl], v, scale) < t, n
+
+
+# ------------------------------------------------ configs 2 and 3 in full
+
+def _seed_patch(w, rng_seed):
+    """Seeded E (three (nz, ny, nx) arrays) on the first magnetic region's box
+    grown by two cells, 1 kV/m scale: real field and magnet dynamics from the
+    first step (the drives start far below that within a few dozen steps)."""
+    cells = _film0(w)
+    lo = np.maximum(cells.min(0) - 2, 0)
+    hi = np.minimum(cells.max(0) + 3, [w.nz, w.ny, w.nx])
+    rng = np.random.default_rng(rng_seed)
+    out = []
+    for _ in range(3):
+        a = np.zeros((w.nz, w.ny, w.nx), dtype=np.float32)
+        a[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]] = 1e3 * rng.standard_normal(tuple(hi - lo))
+        out.append(a)
+    return out
+
+
+def _compare_whole(got, probes, w, patch, dt, steps, llg_fixed_iter=0):
+    """Every cell of E, H and the change of M, and the probes, against the
+    FP64 oracle run of the whole workload from the same patch."""
+    orc = oracle_from_workload(w, dt=dt, llg_fixed_iter=llg_fixed_iter)
+    for name, a in zip(("Ex", "Ey", "Ez"), patch):
+        getattr(orc, name)[: w.nz, : w.ny, : w.nx] = a
+    M0 = orc.M.copy()
+    out = orc.run(steps)
+    t = tol(steps)
+    for p, (i, j, k) in enumerate(w.probes):
+        errs = probe_errors(probes[p], out["probes"][:, p], M0[:, k, j, i], t, steps)
+        assert max(errs) < t, (p, errs)
+    orc.half_push()
+    ref = compact(orc)
+    for fam in (("Ex", "Ey", "Ez"), ("Hx", "Hy", "Hz")):
+        scale = max(float(np.abs(ref[n]).max()) for n in fam)
+        assert scale > 0
+        for n in fam:
+            assert rel_err(got[n], ref[n], scale) < t, n
+    dm = {n: ref[n] - M0[d] for d, n in enumerate(("Mx", "My", "Mz"))}
+    scale = max(max(float(np.abs(v).max()) for v in dm.values()), m_floor(float(np.abs(M0).max()), orc.step) / t)
+    assert max(float(np.abs(v).max()) for v in dm.values()) > 1e3 * m_floor(float(np.abs(M0).max()), orc.step)
+    for n, v in dm.items():
+        assert rel_err(got["d" + n], v, scale) < t, n
+
+
+_NAMES = ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz", "dMx", "dMy", "dMz")
+
+
+def test_bias_sweep_batch_members_equal_oracle():
+    """The 64-cube bias sweep as the benchmark builds it (one batch, its
+    common time step): the smallest and the largest cube against the oracle
+    run of that cube alone, every cell."""
+    import torch
+
+    steps = 30
+    ws = W.bias_sweep(steps=steps)
+    order = np.argsort([w.cells for w in ws])
+    picks = [int(order[0]), int(order[-1])]
+    with torch.cuda.stream(torch.cuda.Stream()):
+        batch = pkg.FdtdLlg.create_batch([(w.nx, w.ny, w.nz) for w in ws], [(w.dx, w.dy, w.dz) for w in ws],
+                                         courant_factor=0.5, probe_capacity=steps)
+        for q, w in enumerate(ws):
+            pkg.configure(batch.batch_member(q), w)
+        patches = {q: _seed_patch(ws[q], 100 + q) for q in picks}
+        for q in picks:
+            for n, a in zip(("Ex", "Ey", "Ez"), patches[q]):
+                batch.batch_member(q).set_field(n, a)
+        batch.step(steps)
+        batch.sync()
+        dt = batch.dt
+        res = {}
+        for q in picks:
+            m = batch.batch_member(q)
+            res[q] = ({n: m.get_field(n) for n in _NAMES}, [m.probe(p) for p in range(len(ws[q].probes))])
+        batch.destroy()
+    for q in picks:
+        _compare_whole(res[q][0], res[q][1], ws[q], patches[q], dt, steps)
+
+
+def test_adjoint_design_grid_forward_equals_oracle():
+    """The 128 x 128 x 64 design case's forward run (three fixed LLG iterates,
+    as the adjoint uses) against the oracle, every cell."""
+    import torch
+
+    steps = 30
+    w = W.adjoint_design(steps=steps)
+    patch = _seed_patch(w, 7)
+    with torch.cuda.stream(torch.cuda.Stream()):
+        sim = pkg.from_workload(w, probe_capacity=steps, llg_fixed_iter=3)
+        for n, a in zip(("Ex", "Ey", "Ez"), patch):
+            sim.set_field(n, a)
+        sim.step(steps)
+        sim.sync()
+        got = {n: sim.get_field(n) for n in _NAMES}
+        probes = [sim.probe(p) for p in range(len(w.probes))]
+        dt = sim.dt
+        sim.destroy()
+    _compare_whole(got, probes, w, patch, dt, steps, llg_fixed_iter=3)
