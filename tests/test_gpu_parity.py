@@ -393,6 +393,37 @@ def test_streamed_results_equal_the_device_rings(kind):
     del rows_h, energy_h
 
 
+def test_batch_members_stream_into_their_own_rings():
+    """Each member of a batch streams into rings of its own: one pinned
+    (written by the flush kernel), one pageable (queued copies), one not
+    streaming; the rings equal each member's device records."""
+    import torch
+
+    ws = [W.random_small(s, nx=13 + 2 * s, ny=11, nz=9 + s, steps=30) for s in (1, 2, 3)]
+    b = pkg.FdtdLlg.create_batch([(w.nx, w.ny, w.nz) for w in ws], [(w.dx, w.dy, w.dz) for w in ws],
+                                 courant_factor=0.6, probe_capacity=32)
+    for q, w in enumerate(ws):
+        pkg.configure(b.batch_member(q), w)
+    cap = 9
+    rings = {0: (torch.zeros((cap, 3, 9), dtype=torch.float64).pin_memory(),
+                 torch.zeros(cap, dtype=torch.float64).pin_memory()),
+             1: (np.zeros((cap, 3, 9)), np.zeros(cap))}
+    for q, (r, e) in rings.items():
+        b.batch_member(q).stream_results(r, e)
+    for n in (4, 1, 20):
+        b.step(n)
+    b.sync()
+    for q, (r, e) in rings.items():
+        m = b.batch_member(q)
+        r, e = np.asarray(r), np.asarray(e)
+        ref_e, ref_rows = m.energy(), [m.probe(p) for p in range(3)]
+        for n in range(25 - cap, 25):
+            assert e[n % cap] == ref_e[n], (q, n)
+            for p in range(3):
+                np.testing.assert_array_equal(r[n % cap, p], ref_rows[p][n])
+    b.destroy()
+
+
 def test_batch_equals_separate_runs_bitwise():
     ws = [W.random_small(s, nx=9 + 7 * s, ny=10, nz=8 + s, steps=25) for s in range(3)]
     dims = [(x.nx, x.ny, x.nz) for x in ws]
