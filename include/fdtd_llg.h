@@ -249,11 +249,13 @@ int fdtd_llg_set_profiling(fdtd_llg_t h, int32_t on);
 int fdtd_llg_read_profile(fdtd_llg_t h, fdtd_llg_profile *out, int32_t reset);
 
 /* CUDA graphs for long step calls: mode 1 captures kGraphSteps (32) steps
- * once and replays the graph, 0 launches kernel by kernel, -1 (default) uses
- * graphs when the batch holds at most 2^21 cells (steps short enough for
- * launch overhead to matter).  Graphs are used only on a stream that can be
- * captured (not the legacy default stream) and never while profiling.
- * Results are the same to the bit either way.  Errors: FDTD_E_INVAL. */
+ * once and replays the graph, 0 launches kernel by kernel, -1 (default)
+ * behaves as 1 (replay shortens the gap between one step's kernels and the
+ * next step's at every grid size measured: 86.6 -> 84.5 us per step on
+ * 256x256x128, 537 -> 535 us on 512x512x256).  Graphs are used only for calls
+ * of at least 2 kGraphSteps steps, on a stream that can be captured (not the
+ * legacy default stream), and never while profiling.  Results are the same to
+ * the bit either way.  Errors: FDTD_E_INVAL. */
 int fdtd_llg_set_graphs(fdtd_llg_t h, int32_t mode);
 
 /* The time step (s) shared by every instance of the handle's batch. */

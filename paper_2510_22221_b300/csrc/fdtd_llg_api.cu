@@ -109,7 +109,7 @@ struct Sim {
     cudaGraphExec_t graph = nullptr;
     int graph_parity = -1;            // buffer holding the state when the graph starts; -1: none
     bool graph_off = false;           // capture failed once on this stream: launch step by step
-    int graph_mode = -1;              // 1 always, 0 never, -1 when a step is launch-bound
+    int graph_mode = -1;              // 1 always, 0 never, -1 default (as 1)
     std::vector<void *> allocs;
     std::string err;
     // profiling: event pairs recorded around launches
@@ -1104,9 +1104,6 @@ static LaunchSet launch_set(Sim *S)
 // Steps per CUDA graph: long step calls on a stream that can be captured
 // replay one graph of kGraphSteps steps instead of launching kernel by kernel.
 constexpr int64_t kGraphSteps = 32;
-// By default graphs serve launch-bound steps only: below this many cells a
-// step's kernels run for less than their launch overhead.
-constexpr long long kGraphCells = 2LL << 20;
 
 static bool capturable(cudaStream_t s) { return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread; }
 
@@ -1208,9 +1205,7 @@ extern "C" int fdtd_llg_step(fdtd_llg_t h, int64_t nsteps)
         S->half_ahead = true;
     }
     int64_t s = 0;
-    long long cells = 0;
-    for (const Instance &I : S->inst) cells += (long long)I.nx * I.ny * I.nz;
-    const bool want = S->graph_mode == 1 || (S->graph_mode < 0 && cells <= kGraphCells);
+    const bool want = S->graph_mode != 0;   // -1 (default): replay shortens the gaps between steps at every size
     if (want && !S->profiling && !S->graph_off && nsteps >= 2 * kGraphSteps && capturable(S->stream)) {
         if ((!S->graph || S->graph_parity != S->cur) && build_graph(S, L) != cudaSuccess) {
             cudaGetLastError();   // not fatal: this stream is stepped launch by launch
