@@ -254,7 +254,8 @@ int fdtd_llg_read_profile(fdtd_llg_t h, fdtd_llg_profile *out, int32_t reset);
  * next step's at every grid size measured: 86.6 -> 84.5 us per step on
  * 256x256x128, 537 -> 535 us on 512x512x256).  Graphs are used only for calls
  * of at least 2 kGraphSteps steps, on a stream that can be captured (not the
- * legacy default stream), and never while profiling.  Results are the same to
+ * legacy default stream), and never while profiling; a one-step call replays
+ * a graph of its step and the flush that ends it.  Results are the same to
  * the bit either way.  Errors: FDTD_E_INVAL. */
 int fdtd_llg_set_graphs(fdtd_llg_t h, int32_t mode);
 

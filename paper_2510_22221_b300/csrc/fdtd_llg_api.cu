@@ -108,6 +108,7 @@ struct Sim {
     // CUDA graph of kGraphSteps steps (even: the buffer parity returns), replayed by long step calls
     cudaGraphExec_t graph = nullptr;
     int graph_parity = -1;            // buffer holding the state when the graph starts; -1: none
+    cudaGraphExec_t graph1[2] = {nullptr, nullptr};   // one-step calls (step and flush), by starting buffer
     bool graph_off = false;           // capture failed once on this stream: launch step by step
     int graph_mode = -1;              // 1 always, 0 never, -1 default (as 1)
     std::vector<void *> allocs;
@@ -154,6 +155,8 @@ struct Sim {
         }
         allocs.clear();
         if (graph) cudaGraphExecDestroy(graph);
+        for (auto g1 : graph1)
+            if (g1) cudaGraphExecDestroy(g1);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -906,6 +909,8 @@ static std::vector<int> model_near(const Sim *S, int slots, double frac, size_t 
     return out;
 }
 
+static void drop_graph1(Sim *S);
+
 static int upload_descriptors(fdtd_llg_t h)
 {
     Sim *S = h->sim;
@@ -1060,6 +1065,7 @@ static int upload_descriptors(fdtd_llg_t h)
     S->dirty = false;
     if (S->graph) { cudaGraphExecDestroy(S->graph); S->graph = nullptr; }   // its launch set is stale
     S->graph_parity = -1;
+    drop_graph1(S);
     return FDTD_OK;
 }
 
@@ -1108,6 +1114,32 @@ constexpr int64_t kGraphSteps = 32;
 static bool capturable(cudaStream_t s) { return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread; }
 
 // (Re)build the graph of kGraphSteps steps starting from buffer S->cur.
+static void drop_graph1(Sim *S)
+{
+    for (auto &g1 : S->graph1)
+        if (g1) { cudaGraphExecDestroy(g1); g1 = nullptr; }
+}
+
+// The graph of a one-step call starting from buffer S->cur: the step's two
+// kernels and the flush, which takes the step from the device counter.
+static cudaError_t build_graph1(Sim *S, LaunchSet L)
+{
+    cudaGraphExec_t &g1 = S->graph1[S->cur];
+    if (g1) { cudaGraphExecDestroy(g1); g1 = nullptr; }
+    cudaError_t e = cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    L.src = S->cur;
+    L.dst = 1 - S->cur;
+    e = launch_step(L, S->stream, nullptr);
+    if (e == cudaSuccess) e = launch_energy_flush(L, S->rings_mapped ? S->d_rings : nullptr, -1, -1, S->stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(S->stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g1, g, 0);
+    if (g) cudaGraphDestroy(g);
+    return e;
+}
+
 static cudaError_t build_graph(Sim *S, LaunchSet L)
 {
     if (S->graph) { cudaGraphExecDestroy(S->graph); S->graph = nullptr; }
@@ -1187,6 +1219,7 @@ extern "C" int fdtd_llg_stream_results(fdtd_llg_t h, double *rows, double *energ
     CKR(h, cudaMemcpy(S->d_rings + (I - S->inst.data()), &R, sizeof(HostRing), cudaMemcpyHostToDevice));
     S->rings_mapped = false;
     for (const Instance &J : S->inst) S->rings_mapped = S->rings_mapped || J.ring_mapped;
+    drop_graph1(S);   // they pass the rings to the flush
     return FDTD_OK;
 }
 
@@ -1213,6 +1246,20 @@ extern "C" int fdtd_llg_step(fdtd_llg_t h, int64_t nsteps)
         }
         if (S->graph)
             for (; s + kGraphSteps <= nsteps; s += kGraphSteps) CKR(h, cudaGraphLaunch(S->graph, S->stream));
+    }
+    if (want && nsteps == 1 && !S->profiling && !S->graph_off && capturable(S->stream)) {
+        // a one-step call: one replayed graph of the step and its flush
+        if (!S->graph1[S->cur] && build_graph1(S, L) != cudaSuccess) {
+            cudaGetLastError();
+            S->graph_off = true;
+        }
+        if (S->graph1[S->cur]) {
+            CKR(h, cudaGraphLaunch(S->graph1[S->cur], S->stream));
+            S->cur ^= 1;
+            CKR(h, stream_out(S, S->host_step, S->host_step + 1));
+            S->host_step += 1;
+            return FDTD_OK;
+        }
     }
     for (; s < nsteps; ++s) {
         L.src = S->cur;

@@ -1111,12 +1111,17 @@ __device__ void copy_out(const Inst *I, const HostRing &R, long long n0, long lo
 // the last instance clears the pending step (the next step's sweep then does
 // not sum it again).  With the energy off, one CTA per instance.  The CTA that
 // completes an instance (with nothing pending, its first one) then copies the
-// call's steps [n0, n1) of the instance's results into its host ring.
+// call's steps [n0, n1) of the instance's results into its host ring (n1 < 0:
+// the one step that the device step counter last completed).
 __global__ void __launch_bounds__(kST) energy_flush_kernel(LaunchSet L, const HostRing *rings, long long n0, long long n1)
 {
     __shared__ double sred[kST / 32];
     __shared__ int s_out;
     const int tid = threadIdx.x;
+    if (n1 < 0) {   // a replayed one-step call: the step just completed
+        n1 = *(volatile long long *)&L.ctl->step;
+        n0 = n1 - 1;
+    }
     int ii = blockIdx.x, c = 0;
     if (L.energy) {
         const int2 rt = L.ered[blockIdx.x];
