@@ -51,12 +51,15 @@ class _Problem(C.Structure):
         ("llg_tol", C.c_double),
         ("llg_max_iter", C.c_int32),
         ("llg_fixed_iter", C.c_int32),
+        ("pml_n", C.c_int32 * 3), ("pml_pad_", C.c_int32),
+        ("pml_order", C.c_double), ("pml_scale", C.c_double),
+        ("pml_kappa_max", C.c_double), ("pml_alpha_max", C.c_double),
     ]
 
 
 class _State(C.Structure):
     _fields_ = [("Ex", _dp), ("Ey", _dp), ("Ez", _dp), ("Hx", _dp), ("Hy", _dp), ("Hz", _dp),
-                ("M", _dp), ("step", C.c_int64)]
+                ("M", _dp), ("step", C.c_int64), ("psi", _dp)]
 
 
 _lib = None
@@ -80,6 +83,8 @@ def lib():
         _lib.orc_source_value.restype = C.c_double
         _lib.orc_llg_trapezoid.argtypes = [_dp, _dp, _dp, C.c_double, C.c_double, C.c_double, _dp]
         _lib.orc_llg_trapezoid.restype = None
+        _lib.orc_psi_size.argtypes = [C.POINTER(_Problem)]
+        _lib.orc_psi_size.restype = C.c_int64
         for nm in ("orc_mu0", "orc_eps0", "orc_c0"):
             getattr(_lib, nm).restype = C.c_double
             getattr(_lib, nm).argtypes = []
@@ -134,6 +139,17 @@ class Material:
 
 
 @dataclass
+class Pml:
+    """Convolutional PML (reading R15 of the oracle: CFS stretch, graded
+    sigma, kappa, alpha) in the first and last ``n[a]`` cells of each axis."""
+    n: tuple = (8, 8, 8)         # layers per axis (0: none on that axis)
+    order: float = 3.0           # grading exponent m
+    scale: float = 1.0           # sigma_max / (0.8 (m+1) / (eta0 d))
+    kappa_max: float = 1.0
+    alpha_max: float = 0.0       # S/m
+
+
+@dataclass
 class Source:
     comp: int                    # 0: Jx on an Ex edge, 1: Jy, 2: Jz
     ijk: tuple
@@ -153,7 +169,7 @@ class OracleSim:
 
     def __init__(self, nx, ny, nz, dx, dy, dz, dt, materials, mat_id, hbias,
                  sources=(), probes=(), eps_r_cell=None, llg_tol=1e-6, llg_max_iter=50,
-                 llg_fixed_iter=0):
+                 llg_fixed_iter=0, pml=None):
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.dx, self.dy, self.dz, self.dt = float(dx), float(dy), float(dz), float(dt)
         self.materials = list(materials)
@@ -177,6 +193,7 @@ class OracleSim:
         self._spar = np.array(pars, dtype=np.float64).reshape(-1, 4)
         self._probe = np.array(list(probes), dtype=np.int32).reshape(-1, 3)
         self.llg_tol, self.llg_max_iter, self.llg_fixed_iter = llg_tol, llg_max_iter, llg_fixed_iter
+        self.pml = pml
         n = (self.nx, self.ny, self.nz)
         self.Ex = np.zeros((nz + 1, ny + 1, nx))
         self.Ey = np.zeros((nz + 1, ny, nx + 1))
@@ -193,6 +210,7 @@ class OracleSim:
         for d in range(3):
             self.M[d] = Ms * u[d]
         del n
+        self.psi = np.zeros(lib().orc_psi_size(C.byref(self._problem()))) if pml is not None else None
 
     # -- ctypes marshalling
     def _problem(self):
@@ -207,6 +225,11 @@ class OracleSim:
         P.nsrc, P.nprobe = self._src.shape[0], self._probe.shape[0]
         P.src, P.src_par, P.probe = _p(self._src, _ip), _p(self._spar), _p(self._probe, _ip)
         P.llg_tol, P.llg_max_iter, P.llg_fixed_iter = self.llg_tol, self.llg_max_iter, self.llg_fixed_iter
+        if self.pml is not None:
+            for a in range(3):
+                P.pml_n[a] = int(self.pml.n[a])
+            P.pml_order, P.pml_scale = float(self.pml.order), float(self.pml.scale)
+            P.pml_kappa_max, P.pml_alpha_max = float(self.pml.kappa_max), float(self.pml.alpha_max)
         return P
 
     def _state(self):
@@ -218,6 +241,7 @@ class OracleSim:
         S.Ex, S.Ey, S.Ez = _p(self.Ex), _p(self.Ey), _p(self.Ez)
         S.Hx, S.Hy, S.Hz = _p(self.Hx), _p(self.Hy), _p(self.Hz)
         S.M, S.step = _p(self.M), self.step
+        S.psi = _p(self.psi) if self.psi is not None else None
         return S
 
     def run(self, nsteps: int):
@@ -229,6 +253,8 @@ class OracleSim:
         energy = np.zeros(nsteps)
         iters = np.zeros((nsteps, 2), dtype=np.int32)
         rc = lib().orc_run(C.byref(P), C.byref(S), nsteps, _p(probes), _p(energy), _p(iters, _ip))
+        if rc == -2:
+            raise ValueError("PML layers set without their memory")
         if rc < 0:
             raise MemoryError("oracle allocation failed")
         self.step = S.step
@@ -250,6 +276,18 @@ class OracleSim:
         lib().orc_div_b(C.byref(P), C.byref(S), _p(out))
         return out
 
+    def psi_blocks(self) -> dict:
+        """The PML memories by name ('Ex|y': Ex's memory of d/dy, ...), each in
+        its component's staggered shape."""
+        names = ["Ex|y", "Ex|z", "Ey|z", "Ey|x", "Ez|x", "Ez|y", "Hx|y", "Hx|z", "Hy|z", "Hy|x", "Hz|x", "Hz|y"]
+        out, off = {}, 0
+        for nm in names:
+            shape = getattr(self, nm[:2]).shape
+            sz = int(np.prod(shape))
+            out[nm] = self.psi[off: off + sz].reshape(shape)
+            off += sz
+        return out
+
     def copy_fields(self) -> dict:
         return {nm: getattr(self, nm).copy() for nm in ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz", "M")}
 
@@ -259,5 +297,5 @@ class OracleSim:
             setattr(self, nm, np.array(np.broadcast_to(v, cur.shape), dtype=np.float64, order="C", copy=True))
 
 
-__all__ = ["build", "OracleSim", "Material", "Source", "courant_dt", "source_value", "llg_trapezoid",
+__all__ = ["build", "OracleSim", "Material", "Source", "Pml", "courant_dt", "source_value", "llg_trapezoid",
            "mu0", "eps0", "c0"]

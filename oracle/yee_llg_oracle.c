@@ -41,6 +41,22 @@
  *   R7  Energy W = sum_edges eps E^2/2 dV + sum_faces mu0 H^2/2 dV
  *                + sum_cells mu0 (|H0| Ms - H0.M) dV, the last term evaluated
  *       as mu0 |H0|/(2 Ms) |M - Ms h|^2 (equal on |M| = Ms).
+ *   R15 Absorbing layers (the paper's device is bounded by PMLs whose
+ *       formulation it does not give): the convolutional PML of Roden and
+ *       Gedney (2000) with the complex-frequency-shifted stretch
+ *       s = kappa + sigma / (alpha + j w eps0) on each axis.  Every
+ *       derivative d/da of the two curls becomes (1/kappa_a) d/da plus a
+ *       memory psi with psi <- b psi + c d/da, b = exp(-(sigma/kappa + alpha)
+ *       dt/eps0), c = sigma (b - 1) / (kappa (sigma + kappa alpha)).  The
+ *       layers fill the first and last pml_n[a] cells of axis a (inside the
+ *       grid, ended by its PEC walls); at depth rho in [0, 1] (rho = 1 on the
+ *       wall) sigma = sigma_max rho^m, kappa = 1 + (kappa_max - 1) rho^m,
+ *       alpha = alpha_max (1 - rho), sigma_max = scale 0.8 (m+1)/(eta0 d_a).
+ *       Time placement: the E memory is updated from H^{n+1/2} in the E push;
+ *       the H memory from E^n, and its whole-step term -(dt/mu0)[(1/kappa-1)
+ *       dE + psi] enters before the first half-push, so that H^{n-1/2} ->
+ *       H^{n+1/2} is the standard CPML leapfrog update while H^{n+1} (probes,
+ *       energy) stays the mean of the two half-step values' plain pushes.
  *
  * Array layout: C order with i fastest.  Full staggered sizes:
  *   Ex nx*(ny+1)*(nz+1)  Ey (nx+1)*ny*(nz+1)  Ez (nx+1)*(ny+1)*nz
@@ -72,11 +88,19 @@ typedef struct {
     double llg_tol;
     int32_t llg_max_iter;
     int32_t llg_fixed_iter;    /* > 0: always exactly this many iterations   */
+    /* convolutional PML (R15); pml_n[a] = 0 on every axis: none              */
+    int32_t pml_n[3];          /* layers at both ends of axis x, y, z        */
+    int32_t pml_pad_;
+    double pml_order;          /* grading exponent m                         */
+    double pml_scale;          /* sigma_max in units of 0.8 (m+1)/(eta0 d)   */
+    double pml_kappa_max;      /* kappa at the outer wall (>= 1)             */
+    double pml_alpha_max;      /* CFS alpha at the inner face (S/m)          */
 } orc_problem;
 
 typedef struct {
     double *Ex, *Ey, *Ez, *Hx, *Hy, *Hz, *M;
     int64_t step;
+    double *psi;               /* PML memory, orc_psi_size doubles; NULL without PML */
 } orc_state;
 
 /* ---------------------------------------------------------------- indexing */
@@ -224,6 +248,119 @@ void orc_llg_trapezoid(const double Mn[3], const double He_n[3], const double He
     for (int q = 0; q < 3; ++q) Mt[q] = (b[q] + ab * a[q] - axb[q]) / (1.0 + aa);
     double nrm = sqrt(dot3(Mt, Mt));
     for (int q = 0; q < 3; ++q) Mout[q] = Ms * Mt[q] / nrm;
+}
+
+/* ------------------------------------------------------------------ PML, R15 */
+static int pml_on(const orc_problem *p)
+{
+    return p->pml_n[0] > 0 || p->pml_n[1] > 0 || p->pml_n[2] > 0;
+}
+
+/* b, c and kappa of the stretch on axis a at coordinate x (in cells, integer
+ * or half-integer); outside the layers b = 1, c = 0, kappa = 1. */
+static void pml_coef(const orc_problem *p, int a, double x, double *b, double *c, double *kap)
+{
+    const int n = a == 0 ? NX : a == 1 ? NY : NZ, d = p->pml_n[a];
+    const double del = a == 0 ? p->dx : a == 1 ? p->dy : p->dz;
+    double rho = 0.0;
+    if (d > 0) {
+        if (x < d) rho = (d - x) / d;
+        else if (x > n - d) rho = (x - (n - d)) / d;
+    }
+    *b = 1.0; *c = 0.0; *kap = 1.0;
+    if (rho <= 0.0) return;
+    const double eta0 = ORC_MU0 * ORC_C0;
+    const double smax = p->pml_scale * 0.8 * (p->pml_order + 1.0) / (eta0 * del);
+    const double g = pow(rho, p->pml_order);
+    const double sig = smax * g, k = 1.0 + (p->pml_kappa_max - 1.0) * g, al = p->pml_alpha_max * (1.0 - rho);
+    *b = exp(-(sig / k + al) * p->dt / ORC_EPS0);
+    *c = sig > 0.0 ? sig * (*b - 1.0) / (k * (sig + k * al)) : 0.0;
+    *kap = k;
+}
+
+/* psi blocks, each the full staggered size of its component:
+ * E: Ex|y Ex|z Ey|z Ey|x Ez|x Ez|y, then H: Hx|y Hx|z Hy|z Hy|x Hz|x Hz|y
+ * (component | axis of the stretched derivative). */
+int64_t orc_psi_size(const orc_problem *p)
+{
+    return 2 * (nEx(p) + nEy(p) + nEz(p) + nHx(p) + nHy(p) + nHz(p));
+}
+static double *psi_block(const orc_problem *p, const orc_state *s, int blk)
+{
+    const int64_t sz[12] = {nEx(p), nEx(p), nEy(p), nEy(p), nEz(p), nEz(p),
+                            nHx(p), nHx(p), nHy(p), nHy(p), nHz(p), nHz(p)};
+    double *q = s->psi;
+    for (int i = 0; i < blk; ++i) q += sz[i];
+    return q;
+}
+
+/* One stretched derivative term: the memory at q advanced with derivative
+ * g, returning g / kappa + psi. */
+static double pml_term(const orc_problem *p, int a, double x, double *q, double g)
+{
+    double b, c, k;
+    pml_coef(p, a, x, &b, &c, &k);
+    *q = b * *q + c * g;
+    return g / k + *q;
+}
+
+/* The H side of R15 before the first half-push: H -= (dt/mu0) times the
+ * stretched curl of E^n minus the plain one, memories advanced from E^n. */
+static void pml_h_update(const orc_problem *p, orc_state *s)
+{
+    const double f = p->dt / ORC_MU0;
+    double *qxy = psi_block(p, s, 6), *qxz = psi_block(p, s, 7), *qyz = psi_block(p, s, 8);
+    double *qyx = psi_block(p, s, 9), *qzx = psi_block(p, s, 10), *qzy = psi_block(p, s, 11);
+    for (int k = 0; k < NZ; ++k)
+        for (int j = 0; j < NY; ++j)
+            for (int i = 0; i <= NX; ++i) {   /* Hx at (i, j+1/2, k+1/2) */
+                const int64_t h = iHx(p, i, j, k);
+                const double dyEz = (s->Ez[iEz(p, i, j + 1, k)] - s->Ez[iEz(p, i, j, k)]) / p->dy;
+                const double dzEy = (s->Ey[iEy(p, i, j, k + 1)] - s->Ey[iEy(p, i, j, k)]) / p->dz;
+                const double st = pml_term(p, 1, j + 0.5, qxy + h, dyEz) - pml_term(p, 2, k + 0.5, qxz + h, dzEy);
+                s->Hx[h] -= f * (st - (dyEz - dzEy));
+            }
+    for (int k = 0; k < NZ; ++k)
+        for (int j = 0; j <= NY; ++j)
+            for (int i = 0; i < NX; ++i) {   /* Hy at (i+1/2, j, k+1/2) */
+                const int64_t h = iHy(p, i, j, k);
+                const double dzEx = (s->Ex[iEx(p, i, j, k + 1)] - s->Ex[iEx(p, i, j, k)]) / p->dz;
+                const double dxEz = (s->Ez[iEz(p, i + 1, j, k)] - s->Ez[iEz(p, i, j, k)]) / p->dx;
+                const double st = pml_term(p, 2, k + 0.5, qyz + h, dzEx) - pml_term(p, 0, i + 0.5, qyx + h, dxEz);
+                s->Hy[h] -= f * (st - (dzEx - dxEz));
+            }
+    for (int k = 0; k <= NZ; ++k)
+        for (int j = 0; j < NY; ++j)
+            for (int i = 0; i < NX; ++i) {   /* Hz at (i+1/2, j+1/2, k) */
+                const int64_t h = iHz(p, i, j, k);
+                const double dxEy = (s->Ey[iEy(p, i + 1, j, k)] - s->Ey[iEy(p, i, j, k)]) / p->dx;
+                const double dyEx = (s->Ex[iEx(p, i, j + 1, k)] - s->Ex[iEx(p, i, j, k)]) / p->dy;
+                const double st = pml_term(p, 0, i + 0.5, qzx + h, dxEy) - pml_term(p, 1, j + 0.5, qzy + h, dyEx);
+                s->Hz[h] -= f * (st - (dxEy - dyEx));
+            }
+}
+
+/* Stretched curl of H at an interior edge of component comp (E side of R15). */
+static double pml_curl_h(const orc_problem *p, orc_state *s, int comp, int i, int j, int k)
+{
+    if (comp == 0) {   /* Ex at (i+1/2, j, k) */
+        const int64_t e = iEx(p, i, j, k);
+        const double dyHz = (s->Hz[iHz(p, i, j, k)] - s->Hz[iHz(p, i, j - 1, k)]) / p->dy;
+        const double dzHy = (s->Hy[iHy(p, i, j, k)] - s->Hy[iHy(p, i, j, k - 1)]) / p->dz;
+        return pml_term(p, 1, j, psi_block(p, s, 0) + e, dyHz) - pml_term(p, 2, k, psi_block(p, s, 1) + e, dzHy);
+    }
+    if (comp == 1) {   /* Ey at (i, j+1/2, k) */
+        const int64_t e = iEy(p, i, j, k);
+        const double dzHx = (s->Hx[iHx(p, i, j, k)] - s->Hx[iHx(p, i, j, k - 1)]) / p->dz;
+        const double dxHz = (s->Hz[iHz(p, i, j, k)] - s->Hz[iHz(p, i - 1, j, k)]) / p->dx;
+        return pml_term(p, 2, k, psi_block(p, s, 2) + e, dzHx) - pml_term(p, 0, i, psi_block(p, s, 3) + e, dxHz);
+    }
+    {                  /* Ez at (i, j, k+1/2) */
+        const int64_t e = iEz(p, i, j, k);
+        const double dxHy = (s->Hy[iHy(p, i, j, k)] - s->Hy[iHy(p, i - 1, j, k)]) / p->dx;
+        const double dyHx = (s->Hx[iHx(p, i, j, k)] - s->Hx[iHx(p, i, j - 1, k)]) / p->dy;
+        return pml_term(p, 0, i, psi_block(p, s, 4) + e, dxHy) - pml_term(p, 1, j, psi_block(p, s, 5) + e, dyHx);
+    }
 }
 
 /* ---------------------------------------------------------------- workspace */
@@ -429,6 +566,7 @@ static int half_push(const orc_problem *p, orc_state *s, orc_ws *w, int *noconv,
 static void e_push(const orc_problem *p, orc_state *s, const orc_ws *w, double t_half)
 {
     const double dt = p->dt;
+    const int pml = pml_on(p) && s->psi;
     /* new values into the workspace first would be needed only if the update
        read E neighbours; it reads only H, so in-place is exact. */
     for (int k = 0; k <= NZ; ++k)
@@ -437,7 +575,7 @@ static void e_push(const orc_problem *p, orc_state *s, const orc_ws *w, double t
                 int64_t e = iEx(p, i, j, k);
                 edge_coef cf = w->cx[e];
                 if (cf.frozen) { s->Ex[e] = 0.0; continue; }
-                double curl = curlH_x(p, s, i, j, k);
+                double curl = pml ? pml_curl_h(p, s, 0, i, j, k) : curlH_x(p, s, i, j, k);
                 double J = 0.0;
                 for (int q = 0; q < p->nsrc; ++q)
                     if (p->src[4 * q] == 0 && p->src[4 * q + 1] == i && p->src[4 * q + 2] == j && p->src[4 * q + 3] == k)
@@ -450,7 +588,7 @@ static void e_push(const orc_problem *p, orc_state *s, const orc_ws *w, double t
                 int64_t e = iEy(p, i, j, k);
                 edge_coef cf = w->cy[e];
                 if (cf.frozen) { s->Ey[e] = 0.0; continue; }
-                double curl = curlH_y(p, s, i, j, k);
+                double curl = pml ? pml_curl_h(p, s, 1, i, j, k) : curlH_y(p, s, i, j, k);
                 double J = 0.0;
                 for (int q = 0; q < p->nsrc; ++q)
                     if (p->src[4 * q] == 1 && p->src[4 * q + 1] == i && p->src[4 * q + 2] == j && p->src[4 * q + 3] == k)
@@ -463,7 +601,7 @@ static void e_push(const orc_problem *p, orc_state *s, const orc_ws *w, double t
                 int64_t e = iEz(p, i, j, k);
                 edge_coef cf = w->cz[e];
                 if (cf.frozen) { s->Ez[e] = 0.0; continue; }
-                double curl = curlH_z(p, s, i, j, k);
+                double curl = pml ? pml_curl_h(p, s, 2, i, j, k) : curlH_z(p, s, i, j, k);
                 double J = 0.0;
                 for (int q = 0; q < p->nsrc; ++q)
                     if (p->src[4 * q] == 2 && p->src[4 * q + 1] == i && p->src[4 * q + 2] == j && p->src[4 * q + 3] == k)
@@ -560,16 +698,18 @@ static void record_probes(const orc_problem *p, const orc_state *s, double *row)
  *   probe_out  nsteps*nprobe*9: E,H,M at every probe after each step
  *   energy_out nsteps: W after each step
  *   iters_out  nsteps*2: LLG iterations of the two half-pushes
- * Returns 0, or 1 when an LLG solve hit llg_max_iter, or -1 on allocation
- * failure. */
+ * Returns 0, or 1 when an LLG solve hit llg_max_iter, -1 on allocation
+ * failure, -2 when PML layers are set but s->psi is NULL. */
 int orc_run(const orc_problem *p, orc_state *s, int64_t nsteps,
             double *probe_out, double *energy_out, int32_t *iters_out)
 {
+    if (pml_on(p) && !s->psi) return -2;
     orc_ws w;
     if (ws_init(p, &w)) return -1;
     int noconv = 0;
     for (int64_t n = 0; n < nsteps; ++n) {
         double t_half = ((double)s->step + 0.5) * p->dt;
+        if (pml_on(p) && s->psi) pml_h_update(p, s);
         int it1 = half_push(p, s, &w, &noconv, NULL);
         e_push(p, s, &w, t_half);
         int it2 = half_push(p, s, &w, &noconv, NULL);

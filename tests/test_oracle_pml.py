@@ -1,0 +1,129 @@
+"""Pins of the oracle's absorbing layers (reading R15: the convolutional PML of
+Roden and Gedney with the complex-frequency-shifted stretch; the paper bounds
+its device with PMLs but gives no formulation).
+
+Each pin checks the oracle against something other than itself:
+  * vanishing layers (sigma = 0, kappa = 1, alpha = 0) leave the scheme
+    exactly the PEC-box scheme, bit for bit;
+  * a matched layer reflects little: a line source's field at a probe agrees
+    with the same run in a grid so large that its walls' echo arrives after
+    the window, while a plain PEC wall at the layer's place echoes strongly;
+  * the three 2-D orientations (plates normal to z, x, y) are rotations of
+    one problem, so their probe series agree to rounding: a wrong index,
+    sign or axis in any of the twelve memories breaks the agreement;
+  * energy leaves a box lined with layers on every face.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import Material, OracleSim, Pml, Source
+
+DX = 1e-3
+F0 = 30e9
+
+
+def _plates(orient, n, steps, pml=None, pad=0, d=10):
+    """2-D run: axis `orient` is one cell thick (PEC plates), the line
+    current flows along it at the centre, the probe sits 3 cells away."""
+    N = [n + 2 * pad] * 3
+    N[orient] = 1
+    dt = oracle.courant_dt(DX, DX, DX, 0.99)
+    c = [N[0] // 2, N[1] // 2, N[2] // 2]
+    c[orient] = 0
+    pr = list(c)
+    pr[(orient + 1) % 3] += 3
+    src = Source(comp=orient, ijk=tuple(c), J0=1.0, f0=F0, Tp=0.5 / F0, tpk=1.5 / F0)
+    pm = None
+    if pml is not None:
+        layers = [d, d, d]
+        layers[orient] = 0
+        pm = Pml(n=tuple(layers), **pml)
+    sim = OracleSim(*N, DX, DX, DX, dt, [Material()], np.zeros((N[2], N[1], N[0]), np.uint8), (0, 0, 0),
+                    sources=[src], probes=[tuple(pr)], pml=pm)
+    r = sim.run(steps)
+    return r["probes"][:, 0, orient], r["energy"]
+
+
+@pytest.fixture(scope="module")
+def reference():
+    # walls 120 cells from the source: their echo reaches the probe after
+    # ~237 cells of travel, beyond the 300-step window (~170 cells)
+    ref, _ = _plates(2, 40, 300, pad=100)
+    return ref
+
+
+@pytest.mark.parametrize("orient", [2, 0, 1])
+def test_layers_absorb_what_a_wall_echoes(reference, orient):
+    a, ea = _plates(orient, 40, 300, pml={})
+    b, eb = _plates(orient, 40, 300)
+    m = np.abs(reference).max()
+    assert np.abs(a - reference).max() / m < 2e-3      # about -66 dB
+    assert np.abs(b - reference).max() / m > 0.3       # the PEC wall's echo
+    assert ea[-1] / ea.max() < 1e-5                    # the pulse has left
+    assert eb[-1] / eb.max() > 0.9                     # a PEC box keeps it
+
+
+def test_three_orientations_are_one_problem():
+    runs = [_plates(o, 40, 200, pml=dict(kappa_max=3.0, alpha_max=0.2))[0] for o in (2, 0, 1)]
+    m = np.abs(runs[0]).max()
+    for r in runs[1:]:
+        assert np.abs(r - runs[0]).max() / m < 1e-12
+
+
+def test_stretched_and_shifted_layers_still_absorb(reference):
+    a, _ = _plates(2, 40, 300, pml=dict(kappa_max=5.0, alpha_max=0.5))
+    assert np.abs(a - reference).max() / np.abs(reference).max() < 1e-2
+
+
+def _box(pml, nsteps=40, n=12):
+    rng = np.random.default_rng(7)
+    mats = [Material(), Material(eps_r=4.0, sigma=0.02), Material(Ms=1.4e5, alpha=0.01)]
+    mid = np.zeros((n, n, n), np.uint8)
+    mid[3:9, 2:10, 4:8] = 1
+    mid[5:7, 5:7, 5:7] = 2
+    dt = oracle.courant_dt(DX, DX, DX, 0.9)
+    src = Source(comp=0, ijk=(6, 4, 4), J0=1e3, f0=F0)
+    sim = OracleSim(n, n, n, DX, DX, DX, dt, mats, mid, (0.0, 0.0, 8e4), sources=[src],
+                    probes=[(6, 6, 6), (2, 2, 2)], pml=pml)
+    for nm in ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz"):
+        a = getattr(sim, nm)
+        sim.set_fields(**{nm: rng.standard_normal(a.shape)})
+    r = sim.run(nsteps)
+    return sim, r
+
+
+def test_vanishing_layers_are_the_pec_box_exactly():
+    s0, r0 = _box(None)
+    s1, r1 = _box(Pml(n=(3, 4, 2), scale=0.0, kappa_max=1.0, alpha_max=0.0))
+    for nm in ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz", "M"):
+        assert np.array_equal(getattr(s0, nm), getattr(s1, nm)), nm
+    assert np.array_equal(r0["probes"], r1["probes"])
+    assert np.array_equal(r0["energy"], r1["energy"])
+    assert all(not np.any(v) for v in s1.psi_blocks().values())
+
+
+def test_layers_change_only_the_layers_at_first():
+    """One step from the same state: with layers 2 cells deep, H and E change
+    only within reach of the layers (the memory terms start from zero, so
+    the first step differs from the PEC box only where sigma or kappa act)."""
+    s0, _ = _box(None, nsteps=1)
+    s1, _ = _box(Pml(n=(2, 2, 2), kappa_max=2.0), nsteps=1)
+    dEx = np.abs(s0.Ex - s1.Ex)                        # (nz+1, ny+1, nx)
+    assert dEx.max() > 0
+    inner = dEx[4:-4, 4:-4, 4:-4]                      # two cells beyond the layers' reach
+    assert inner.max() == 0
+
+
+def test_energy_leaves_a_box_lined_on_every_face():
+    n, d = 20, 5
+    dt = oracle.courant_dt(DX, DX, DX, 0.99)
+    # a one-period Gaussian (DC content exp(-2 pi^2), switched on at 1 % of its
+    # peak): a point current with a net charge leaves a static dipole field
+    # that no layer absorbs (here ~2e-5 of the peak energy)
+    src = Source(comp=2, ijk=(10, 10, 10), J0=1.0, f0=F0)
+    sims = [OracleSim(n, n, n, DX, DX, DX, dt, [Material()], np.zeros((n, n, n), np.uint8), (0, 0, 0),
+                      sources=[src], pml=p) for p in (Pml(n=(d, d, d)), None)]
+    ea, eb = (s.run(400)["energy"] for s in sims)
+    assert ea[-1] / ea.max() < 1e-4
+    assert eb[-1] / eb.max() > 0.1     # the PEC box keeps what the source left in it
