@@ -276,6 +276,43 @@ def large_run(torch, pkg, W, steps=1000, warmup=10):
             "hbm_roofline_pct": round(100 * value * 1e6 * ALG_BYTES_PER_CELL_STEP / (hbm * 1e9), 2)}
 
 
+def pml_run(torch, pkg, W, steps=2000, warmup=20, layers=(10, 10, 8)):
+    """The 256 x 256 x 128 strip resonator lined with absorbing layers
+    (convolutional PML) against the same grid with bare PEC walls, on one
+    box, same tiling: throughput of both and the cost of the layers' two
+    passes per layer cell.  A cell in one axis's layers moves ~89 B per step
+    in the two passes (E read 12, H read + write of two components 16, the
+    axis's two H memories read + write 16; then H read 12, E 16, two E
+    memories 16, class id 1; neighbour values from L1/L2)."""
+    stream = torch.cuda.current_stream()
+    out = {}
+    for tag, w in (("plain", W.strip_resonator(steps=steps)), ("layers", W.strip_resonator_pml(steps=steps, layers=layers))):
+        sim = pkg.from_workload(w, probe_capacity=steps + warmup + 8)
+        sim.step(warmup)
+        sim.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+        sim.sync()
+        sec = e0.elapsed_time(e1) * 1e-3
+        sim.destroy()
+        out[tag] = {"workload": w.name, "mcells_per_s": round(w.cells * steps / sec / 1e6, 1),
+                    "ms_per_step": round(sec * 1e3 / steps, 5)}
+    nx, ny, nz = 256, 256, 128
+    dx, dy, dz = layers
+    layer_cells = nx * ny * nz - (nx - 2 * dx) * (ny - 2 * dy) * (nz - 2 * dz)
+    extra = out["layers"]["ms_per_step"] - out["plain"]["ms_per_step"]
+    out["layers"]["layers"] = list(layers)
+    out["layer_cells"] = layer_cells
+    out["layer_cost_ms_per_step"] = round(extra, 5)
+    hbm, _ = peaks()
+    if extra > 0:
+        out["layer_passes_gbs"] = round(89 * layer_cells / (extra * 1e-3) / 1e9, 1)
+        out["layer_passes_hbm_pct"] = round(100 * out["layer_passes_gbs"] / hbm, 1)
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -300,8 +337,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
-    ap.add_argument("--no-extra", action="store_true", help="skip the adjoint, batched-sweep and 512x512x256 measurements")
-    ap.add_argument("--only", choices=["adjoint", "sweep", "large"],
+    ap.add_argument("--no-extra", action="store_true", help="skip the adjoint, batched-sweep, 512x512x256 and absorbing-layer measurements")
+    ap.add_argument("--only", choices=["adjoint", "sweep", "large", "pml"],
                     help="run just one of the extra measurements and print its JSON object")
     ap.add_argument("--adjoint-steps", type=int, default=4000, help="steps of the adjoint measurement")
     ap.add_argument("--tiling", type=int, default=0,
@@ -321,6 +358,8 @@ def main():
             out = adjoint_ratio(torch, pkg, W, steps=args.adjoint_steps, n0=args.adjoint_steps * 3 // 4)
         elif args.only == "sweep":
             out = batch_sweep(torch, pkg, W)
+        elif args.only == "pml":
+            out = pml_run(torch, pkg, W)
         else:
             out = large_run(torch, pkg, W)
         print(json.dumps(out), flush=True)
@@ -453,6 +492,7 @@ def main():
         line["adjoint_forward_ratio"] = adj["adjoint_forward_ratio"]
         line["batch_sweep"] = batch_sweep(torch, pkg, W)
         line["large_run"] = large_run(torch, pkg, W)
+        line["pml_run"] = pml_run(torch, pkg, W)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w, 12)
     if rank == 0:

@@ -139,6 +139,27 @@ int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const fdtd_mater
                            int32_t ntable, const double hbias[3], const double *eps_r_design,
                            const int32_t design_box[6]);
 
+/* Absorbing layers (the paper's device is bounded by PMLs, section
+ * "Modeling Setup", which it does not formulate): the convolutional PML of
+ * Roden and Gedney with the complex-frequency-shifted stretch
+ * s = kappa + sigma / (alpha + j w eps0) in the first and last layers[a] cells
+ * of axis a (x, y, z), inside the grid and ended by its PEC walls.  At depth
+ * rho in [0, 1] (1 on the wall): sigma = scale 0.8 (order+1) / (eta0 d_a)
+ * rho^order, kappa = 1 + (kappa_max - 1) rho^order, alpha = alpha_max
+ * (1 - rho) (S/m).  The memories start at 0 (again at every
+ * fdtd_llg_set_materials and set_pml) and are part of save_state.
+ * H read back from the handle is H^{n+1/2} before the whole-step CPML term
+ * of step n+1 (applied at that step's start); probes and the energy use the
+ * plain midpoint H^{n}, as without layers.  layers = {0, 0, 0} removes them.
+ * Errors: FDTD_E_INVAL (layers < 0 or more than half an axis, order < 0,
+ * scale < 0, kappa_max < 1, alpha_max < 0, magnetic cells inside the
+ * layers, a material with sigma >= 2 eps / dt); FDTD_E_STATE after
+ * fdtd_llg_run_checkpointed.  Not covered by the adjoint
+ * (fdtd_llg_run_checkpointed: FDTD_E_NOSYS) nor by writes of
+ * fdtd_llg_planes (FDTD_E_NOSYS). */
+int fdtd_llg_set_pml(fdtd_llg_t h, const int32_t layers[3], double order, double scale, double kappa_max,
+                     double alpha_max);
+
 /* Point current density on one edge (section "Modeling Setup": modulated
  * Gaussian J = J0 exp(-(t - t_peak)^2 / (2 Tp^2)) cos(2 pi f0 t)); comp 0/1/2
  * selects an Ex/Ey/Ez edge with the indices of the layout above.  Tp = 0 ->

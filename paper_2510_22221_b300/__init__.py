@@ -28,4 +28,7 @@ def configure(sim, w):
         sim.set_source(s["comp"], s["i"], s["j"], s["k"], s["J0"], s["f0"], s["Tp"], s["tpk"])
     for p in w.probes:
         sim.add_probe(*p)
+    if getattr(w, "pml", None):
+        q = w.pml
+        sim.set_pml(q["layers"], q["order"], q["scale"], q["kappa_max"], q["alpha_max"])
     return sim

@@ -55,6 +55,7 @@ SIGNATURES = {
     "fdtd_llg_create_batch": (C.c_int, [C.POINTER(Config), C.c_int32, C.POINTER(_vp)]),
     "fdtd_llg_batch_member": (C.c_int, [_vp, C.c_int32, C.POINTER(_vp)]),
     "fdtd_llg_set_materials": (C.c_int, [_vp, _vp, C.POINTER(MaterialC), C.c_int32, _dp, _dp, C.POINTER(C.c_int32)]),
+    "fdtd_llg_set_pml": (C.c_int, [_vp, C.POINTER(C.c_int32), C.c_double, C.c_double, C.c_double, C.c_double]),
     "fdtd_llg_set_source": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double,
                                       C.c_double, C.c_double]),
     "fdtd_llg_add_probe": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),

@@ -3,6 +3,7 @@
 #include "../../include/fdtd_llg.h"
 #include "fdtd_llg_internal.h"
 #include "class_assign.h"
+#include "pml.h"
 
 #include <cudaTypedefs.h>
 
@@ -57,6 +58,16 @@ struct Instance {
     int dbox[6] = {0, 0, 0, 0, 0, 0}; // design box: i0, j0, k0, bx, by, bz
     double u[3] = {0, 0, 1};          // bias direction
     float R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};   // bias frame rows (e1, e2, e3 = u)
+    // absorbing layers (fdtd_llg_set_pml): layers per axis, grading
+    // (order, scale, kappa_max, alpha_max), device memories and coefficients
+    int pml_n[3] = {0, 0, 0};
+    double pml_par[4] = {3, 1, 1, 0};
+    float *psi[3] = {nullptr, nullptr, nullptr};
+    float4 *pco[3] = {nullptr, nullptr, nullptr};
+    long long pvol[3] = {0, 0, 0};
+    bool ca_nonpos = false;           // some edge class has cb != 0 and ca <= 0
+    bool has_pml() const { return pml_n[0] > 0 || pml_n[1] > 0 || pml_n[2] > 0; }
+    size_t pml_floats() const { return 4 * (size_t)(pvol[0] + pvol[1] + pvol[2]); }
     size_t n_field() const { return (size_t)nz * ny * px; }
     size_t n_wall() const { return (size_t)ny * nz + (size_t)nx * nz + (size_t)nx * ny; }
 };
@@ -82,6 +93,8 @@ struct Sim {
     double *d_esum = nullptr;         // chunk sums, kEChunks per instance
     unsigned *d_ecnt = nullptr;       // chunks summed, per instance
     int nred = 0;
+    // absorbing layers: the launch descriptor of each lined instance
+    std::vector<PmlLaunch> pml;
     int ntiles = 0, nftiles = 0, ncomp = 0, vmax = 0, mag_smem = 0;
     bool stab = false;                // every class table small enough for shared memory
     int tiling = 0;                   // requested z-planes per sweep task (0: model)
@@ -362,6 +375,22 @@ extern "C" void fdtd_llg_destroy(fdtd_llg_t h)
 }
 
 // --------------------------------------------------------- set_materials
+// The absorbing layers need every magnetic cell outside them (the magnet
+// kernel owns those faces) and ca > 0 on every edge that they correct (the
+// E pass folds the CPML term into E^n through cb/ca).
+static int pml_check(fdtd_llg_t h, const Instance &I)
+{
+    const int n[3] = {I.nx, I.ny, I.nz};
+    for (const MagComp &C : I.comps) {
+        const int lo[3] = {C.x0, C.y0, C.z0}, ext[3] = {C.bx, C.by, C.bz};
+        for (int a = 0; a < 3; ++a)
+            if (I.pml_n[a] > 0 && (lo[a] < I.pml_n[a] || lo[a] + ext[a] > n[a] - I.pml_n[a]))
+                return fail(h, FDTD_E_INVAL, "magnetic cells inside the absorbing layers");
+    }
+    if (I.ca_nonpos) return fail(h, FDTD_E_INVAL, "absorbing layers need sigma < 2 eps / dt in every material");
+    return FDTD_OK;
+}
+
 extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const fdtd_material *table, int32_t ntable,
                                       const double hbias[3], const double *eps_r_design, const int32_t design_box[6])
 {
@@ -706,6 +735,7 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
         S->dfree(tmp);
         CKR(h, e);
         std::vector<float4> tab(3 * (size_t)nclass);
+        bool ca_nonpos = false;
         for (int c = 0; c < nclass; ++c) {
             const uint32_t *w = keys[c].w;
             float v[9];
@@ -713,10 +743,12 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
             float flag;
             std::memcpy(&flag, &w[9], 4);
             tab[3 * c] = make_float4(v[0], v[1], v[2], flag);
+            for (int q = 0; q < 3; ++q) ca_nonpos = ca_nonpos || (v[3 + q] != 0.f && v[q] <= 0.f);
             tab[3 * c + 1] = make_float4(v[3], v[4], v[5], 0.f);
             tab[3 * c + 2] = make_float4(v[6], v[7], v[8], 0.f);
         }
         CKR(h, cudaMemcpy(I.ctab, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice));
+        I.ca_nonpos = ca_nonpos;
         if (totV) {
             CKR(h, cudaMemset(I.mbuf, 0, 3 * totV * sizeof(float)));
             CKR(h, cudaMemcpy(I.magmat, hmat.data(), hmat.size(), cudaMemcpyHostToDevice));
@@ -734,6 +766,12 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
     for (int q = 0; q < 9; ++q) I.R[q] = (float)E[q];
     I.materials_set = true;
     I.has_design = has_design;
+    if (I.has_pml()) {
+        const int rc = pml_check(h, I);
+        if (rc) return rc;
+        for (int a = 0; a < 3; ++a)
+            if (I.psi[a]) CKR(h, cudaMemset(I.psi[a], 0, 4 * (size_t)I.pvol[a] * sizeof(float)));
+    }
     std::memcpy(I.dbox, db, sizeof db);
     // a batch's step count restarts with any instance's materials
     S->host_step = 0;
@@ -748,6 +786,80 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
     CKR(h, cudaMemsetAsync(S->d_ctl, 0, sizeof(StepCtl), S->stream));
     CKR(h, set_device_step(S->d_ctl, 0, S->stream));
     CKR(h, cudaStreamSynchronize(S->stream));
+    S->dirty = true;
+    return FDTD_OK;
+}
+
+// {b, c, 1/kappa - 1, 0} of the CPML recursion at depth rho (0 inner face,
+// 1 the wall): sigma = smax rho^m, kappa = 1 + (kmax - 1) rho^m,
+// alpha = amax (1 - rho); b = exp(-(sigma/kappa + alpha) dt/eps0),
+// c = sigma (b - 1) / (kappa (sigma + kappa alpha)).
+static float4 pml_coefficients(double rho, double smax, const double *par, double dt)
+{
+    double sig = 0, kap = 1, al = par[3];
+    if (rho > 0) {
+        const double g = std::pow(rho, par[0]);
+        sig = smax * g;
+        kap = 1 + (par[2] - 1) * g;
+        al = par[3] * (1 - rho);
+    }
+    const double b = std::exp(-(sig / kap + al) * dt / kEps0);
+    const double c = sig > 0 ? sig * (b - 1) / (kap * (sig + kap * al)) : 0.0;
+    return make_float4((float)b, (float)c, (float)(1 / kap - 1), 0.f);
+}
+
+extern "C" int fdtd_llg_set_pml(fdtd_llg_t h, const int32_t layers[3], double order, double scale, double kappa_max,
+                                double alpha_max)
+{
+    if (!is_member(h)) return fail(h, FDTD_E_INVAL, "set_pml needs an instance handle (use fdtd_llg_batch_member)");
+    if (!layers) return fail(h, FDTD_E_INVAL, "null layers");
+    Sim *S = h->sim;
+    Instance &I = *inst_of(h);
+    const int n[3] = {I.nx, I.ny, I.nz};
+    for (int a = 0; a < 3; ++a)
+        if (layers[a] < 0 || 2 * layers[a] > n[a]) return fail(h, FDTD_E_INVAL, "layers must be >= 0 and at most half the axis");
+    if (6 * I.n_field() >= (1ull << 31))
+        return fail(h, FDTD_E_INVAL, "grid too large for the layers' 32-bit offsets (6 nx' ny nz >= 2^31)");
+    if (!(order >= 0) || !(scale >= 0) || !(kappa_max >= 1) || !(alpha_max >= 0))
+        return fail(h, FDTD_E_INVAL, "need order >= 0, scale >= 0, kappa_max >= 1, alpha_max >= 0");
+    if (S->adj_N) return fail(h, FDTD_E_STATE, "a checkpointed run is recorded; set the materials again first");
+    CKR(h, cudaStreamSynchronize(S->stream));
+    const int old[3] = {I.pml_n[0], I.pml_n[1], I.pml_n[2]};
+    for (int a = 0; a < 3; ++a) I.pml_n[a] = layers[a];
+    if (I.materials_set && I.has_pml()) {
+        const int rc = pml_check(h, I);
+        if (rc) {
+            for (int a = 0; a < 3; ++a) I.pml_n[a] = old[a];
+            return rc;
+        }
+    }
+    const double par[4] = {order, scale, kappa_max, alpha_max};
+    std::memcpy(I.pml_par, par, sizeof par);
+    const double del[3] = {I.dx, I.dy, I.dz};
+    for (int a = 0; a < 3; ++a) {
+        S->dfree(I.psi[a]);
+        S->dfree(I.pco[a]);
+        I.psi[a] = nullptr;
+        I.pco[a] = nullptr;
+        I.pvol[a] = 0;
+        const int d = layers[a];
+        if (d == 0) continue;
+        const long long other = (long long)n[(a + 1) % 3] * n[(a + 2) % 3];
+        I.pvol[a] = 2LL * d * other;
+        I.psi[a] = (float *)S->dalloc(4 * (size_t)I.pvol[a] * sizeof(float));
+        I.pco[a] = (float4 *)S->dalloc((size_t)4 * d * sizeof(float4));
+        if (!I.psi[a] || !I.pco[a]) return fail(h, FDTD_E_OOM, "device allocation failed");
+        CKR(h, cudaMemset(I.psi[a], 0, 4 * (size_t)I.pvol[a] * sizeof(float)));
+        const double smax = scale * 0.8 * (order + 1) / (kMu0 * kC0 * del[a]);
+        std::vector<float4> co((size_t)4 * d);
+        for (int t = 0; t < d; ++t) {
+            co[2 * t] = pml_coefficients((double)(d - t) / d, smax, par, S->dt);                      // low side, E
+            co[2 * t + 1] = pml_coefficients((d - t - 0.5) / d, smax, par, S->dt);                     // low side, H
+            co[2 * (d + t)] = pml_coefficients((double)t / d, smax, par, S->dt);                       // high side, E
+            co[2 * (d + t) + 1] = pml_coefficients((t + 0.5) / d, smax, par, S->dt);                   // high side, H
+        }
+        CKR(h, cudaMemcpy(I.pco[a], co.data(), co.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    }
     S->dirty = true;
     return FDTD_OK;
 }
@@ -1062,6 +1174,53 @@ static int upload_descriptors(fdtd_llg_t h)
     S->stab = stab;
     S->mag_smem = msmem;
     S->cls16 = c16;
+    {
+        // absorbing layers: per lined instance, its descriptor and the disjoint
+        // boxes of its layer cells, each box a range of whole blocks
+        S->pml.clear();
+        for (size_t ii = 0; ii < S->inst.size(); ++ii) {
+            const Instance &I = S->inst[ii];
+            if (!I.has_pml()) continue;
+            PmlLaunch q;
+            std::memset(&q, 0, sizeof q);
+            const int dx = I.pml_n[0], dy = I.pml_n[1], dz = I.pml_n[2];
+            auto add = [&](int i0, int j0, int k0, int bx, int by, int bz, int axes) {
+                if (bx <= 0 || by <= 0 || bz <= 0) return;
+                // multipliers ceil(2^32 / d) where every dividend times d stays below
+                // 2^32 (exact quotients); 0: the kernel divides
+                const unsigned long long vol = (unsigned long long)bx * by * bz;
+                const unsigned mbx = bx > 1 && vol * bx < (1ull << 32) ? (unsigned)(0xFFFFFFFFull / (unsigned)bx + 1) : 0u;
+                const unsigned mby = by > 1 && (unsigned long long)by * by * bz < (1ull << 32)
+                                         ? (unsigned)(0xFFFFFFFFull / (unsigned)by + 1) : 0u;
+                q.box[q.nbox] = PmlBox{i0, j0, k0, bx, by, bz, mbx, mby, axes};
+                q.blk[q.nbox + 1] = q.blk[q.nbox] + (int)(((long long)bx * by * bz + 255) / 256);
+                ++q.nbox;
+            };
+            add(0, 0, 0, I.nx, I.ny, dz, 7);                                // z layers: whole planes
+            if (dz) add(0, 0, I.nz - dz, I.nx, I.ny, dz, 7);
+            add(0, 0, dz, I.nx, dy, I.nz - 2 * dz, 3);                       // y layers between them
+            if (dy) add(0, I.ny - dy, dz, I.nx, dy, I.nz - 2 * dz, 3);
+            add(0, dy, dz, dx, I.ny - 2 * dy, I.nz - 2 * dz, 1);             // x layers in the rest
+            if (dx) add(I.nx - dx, dy, dz, dx, I.ny - 2 * dy, I.nz - 2 * dz, 1);
+            for (int a = 0; a < 3; ++a) {
+                q.pd[a] = I.pml_n[a];
+                q.psi[a] = I.psi[a];
+                q.pco[a] = I.pco[a];
+                q.pvol[a] = (unsigned)I.pvol[a];
+            }
+            q.F[0] = I.fields[0];
+            q.F[1] = I.fields[1];
+            q.fs = (unsigned)I.n_field();
+            q.plane = (unsigned)((size_t)I.ny * I.px);
+            q.n[0] = I.nx; q.n[1] = I.ny; q.n[2] = I.nz;
+            q.px = I.px;
+            q.id[0] = (float)(1.0 / I.dx); q.id[1] = (float)(1.0 / I.dy); q.id[2] = (float)(1.0 / I.dz);
+            q.dtmu = 2.f * (float)(S->dt / (2.0 * kMu0));
+            q.cls = I.cls;
+            q.ctab = I.ctab;
+            S->pml.push_back(q);
+        }
+    }
     S->dirty = false;
     if (S->graph) { cudaGraphExecDestroy(S->graph); S->graph = nullptr; }   // its launch set is stale
     S->graph_parity = -1;
@@ -1130,7 +1289,8 @@ static cudaError_t build_graph1(Sim *S, LaunchSet L)
     if (e != cudaSuccess) return e;
     L.src = S->cur;
     L.dst = 1 - S->cur;
-    e = launch_step(L, S->stream, nullptr);
+    e = launch_pml(S->pml.data(), (int)S->pml.size(), L.src, L.cls16, S->stream);
+    if (e == cudaSuccess) e = launch_step(L, S->stream, nullptr);
     if (e == cudaSuccess) e = launch_energy_flush(L, S->rings_mapped ? S->d_rings : nullptr, -1, -1, S->stream);
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(S->stream, &g);
@@ -1149,7 +1309,8 @@ static cudaError_t build_graph(Sim *S, LaunchSet L)
     for (int64_t q = 0; q < kGraphSteps && e == cudaSuccess; ++q) {
         L.src = cur;
         L.dst = 1 - cur;
-        e = launch_step(L, S->stream, nullptr);
+        e = launch_pml(S->pml.data(), (int)S->pml.size(), L.src, L.cls16, S->stream);
+        if (e == cudaSuccess) e = launch_step(L, S->stream, nullptr);
         cur ^= 1;
     }
     cudaGraph_t g = nullptr;
@@ -1270,6 +1431,7 @@ extern "C" int fdtd_llg_step(fdtd_llg_t h, int64_t nsteps)
             for (auto &e : ev) e = S->take_event();
             prof = ev;
         }
+        CKR(h, launch_pml(S->pml.data(), (int)S->pml.size(), L.src, L.cls16, S->stream));
         CKR(h, launch_step(L, S->stream, prof));
         if (prof) {
             S->recs.push_back({0, ev[0], ev[1]});
@@ -1515,6 +1677,8 @@ extern "C" int fdtd_llg_planes(fdtd_llg_t h, int32_t k0, int32_t k1, float *buf,
     if (!I->materials_set) return fail(h, FDTD_E_STATE, "set materials first");
     const int nx = I->nx, ny = I->ny, nz = I->nz;
     if (k0 < 0 || k1 > nz || k0 >= k1) return fail(h, FDTD_E_RANGE, "plane range outside the grid");
+    if (to_handle && I->has_pml())
+        return fail(h, FDTD_E_NOSYS, "planes cannot be written into a handle with absorbing layers (their memories are not exchanged)");
     const size_t P = (size_t)(k1 - k0), pl = (size_t)nx * ny;
     const size_t need = P * (9 * pl + nx + ny);
     if (!buf || count < need) return fail(h, FDTD_E_INVAL, "buffer too small");
@@ -1587,6 +1751,7 @@ static size_t state_bytes(const Instance &I)
     size_t b = sizeof(StateHeader) + 6 * (size_t)I.nx * I.ny * I.nz * sizeof(float);
     b += I.n_wall() * sizeof(float);
     for (auto &C : I.comps) b += 3 * (size_t)C.V * sizeof(float);
+    b += I.pml_floats() * sizeof(float);   // the absorbing layers' memories
     return b;
 }
 
@@ -1617,6 +1782,11 @@ extern "C" int fdtd_llg_save_state(fdtd_llg_t h, void *buf, size_t *size)
         CKR(h, cudaMemcpy(p, C.m, 3 * (size_t)C.V * sizeof(float), cudaMemcpyDeviceToHost));
         p += 3 * (size_t)C.V * sizeof(float);
     }
+    for (int a = 0; a < 3; ++a)
+        if (I->pvol[a]) {
+            CKR(h, cudaMemcpy(p, I->psi[a], 4 * (size_t)I->pvol[a] * sizeof(float), cudaMemcpyDeviceToHost));
+            p += 4 * (size_t)I->pvol[a] * sizeof(float);
+        }
     *size = need;
     return FDTD_OK;
 }
@@ -1647,6 +1817,11 @@ extern "C" int fdtd_llg_load_state(fdtd_llg_t h, const void *buf, size_t size)
         CKR(h, cudaMemcpy(C.m, p, 3 * (size_t)C.V * sizeof(float), cudaMemcpyHostToDevice));
         p += 3 * (size_t)C.V * sizeof(float);
     }
+    for (int a = 0; a < 3; ++a)
+        if (I->pvol[a]) {
+            CKR(h, cudaMemcpy(I->psi[a], p, 4 * (size_t)I->pvol[a] * sizeof(float), cudaMemcpyHostToDevice));
+            p += 4 * (size_t)I->pvol[a] * sizeof(float);
+        }
     Sim *S = h->sim;
     S->host_step = hd.step;
     S->half_ahead = hd.half_ahead != 0;
@@ -1844,6 +2019,7 @@ extern "C" int fdtd_llg_run_checkpointed(fdtd_llg_t h, int64_t nsteps, int32_t i
     if (!h || !h->sim || !h->owns) return fail(h, FDTD_E_INVAL, "run_checkpointed needs the handle, not a member");
     Sim *S = h->sim;
     if (S->inst.size() != 1) return fail(h, FDTD_E_NOSYS, "the adjoint supports single-instance handles");
+    if (S->inst[0].has_pml()) return fail(h, FDTD_E_NOSYS, "the adjoint does not cover absorbing layers");
     if (nsteps < 1 || interval < 0) return fail(h, FDTD_E_INVAL, "nsteps must be >= 1 and interval >= 0");
     if (S->host_step != 0) return fail(h, FDTD_E_STATE, "run_checkpointed starts at step 0 (set the materials again)");
     int rc = upload_descriptors(h);

@@ -165,6 +165,13 @@ class FdtdLlg:
         del keep, des_np
         check(rc, self._h)
 
+    def set_pml(self, layers, order=3.0, scale=1.0, kappa_max=1.0, alpha_max=0.0):
+        """Absorbing layers (convolutional PML) in the first and last
+        ``layers[a]`` cells of axis a; ``(0, 0, 0)`` removes them."""
+        arr = (C.c_int32 * 3)(*(int(v) for v in layers))
+        check(_abi.load().fdtd_llg_set_pml(self._h, arr, float(order), float(scale), float(kappa_max),
+                                           float(alpha_max)), self._h)
+
     def set_source(self, comp, i, j, k, J0, f0, Tp=0.0, t_peak=0.0):
         check(_abi.load().fdtd_llg_set_source(self._h, int(comp), int(i), int(j), int(k), float(J0), float(f0),
                                               float(Tp), float(t_peak)), self._h)

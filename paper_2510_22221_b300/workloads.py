@@ -36,6 +36,7 @@ class Workload:
     eps_design: np.ndarray | None = None # (nk, nj, ni) eps_r over design_box
     design_box: tuple | None = None      # (i0, j0, k0, ni, nj, nk)
     note: str = ""
+    pml: dict | None = None              # absorbing layers: layers (x, y, z), order, scale, kappa_max, alpha_max
 
     @property
     def cells(self) -> int:
@@ -248,6 +249,38 @@ def random_small(seed, nx=13, ny=11, nz=9, steps=40, magnets=True, sigma=0.0, de
     h0 = h0 / np.linalg.norm(h0) * (2.0 / MU0)
     return Workload(f"random_small_{seed}", nx, ny, nz, 1e-6, 1.3e-6, 0.8e-6, 0.6, steps, mats, mid, h0, src, probes,
                     eps_design=eps, design_box=box, note="feature coverage")
+
+
+def pml_small(seed, nx=30, ny=26, nz=22, steps=60, layers=(6, 5, 4), kappa_max=1.0, alpha_max=0.0) -> Workload:
+    """Ragged grid bounded by absorbing layers: a lossy substrate and a PEC
+    strip that run into the layers (a line ended by them), a magnetic block
+    in the middle clear of the layers, two sources (one inside the layers),
+    probes inside the layers, beside the block and in the far corner; bias of
+    2 T in a random direction."""
+    rng = np.random.default_rng(seed)
+    mats = [material(), material(eps_r=4.0, sigma=2e3), material(pec=True),
+            material(eps_r=2.0, Ms=1.4e5, alpha=0.01, gamma=1.76e11)]
+    mid = np.zeros((nz, ny, nx), dtype=np.uint8)
+    mid[: nz // 3] = 1
+    mid[nz // 3, ny // 2 - 1:ny // 2 + 1, :] = 2
+    mid[nz // 2 - 1:nz // 2 + 1, ny // 2 - 2:ny // 2 + 2, nx // 2 - 3:nx // 2 + 3] = 3
+    src = [dict(comp=1, i=nx // 2 - 5, j=ny // 2 + 3, k=nz // 2, J0=3e6, f0=4e12, Tp=2e-13, tpk=4e-13),
+           dict(comp=2, i=2, j=ny // 2 + 4, k=nz // 2 + 1, J0=-2e6, f0=7e12, Tp=1.5e-13, tpk=3e-13)]
+    probes = [(nx // 2 + 5, ny // 2, nz // 2), (2, 3, 2), (nx - 2, ny - 2, nz - 2)]
+    h0 = rng.normal(size=3)
+    h0 = h0 / np.linalg.norm(h0) * (2.0 / MU0)
+    return Workload(f"pml_small_{seed}", nx, ny, nz, 1e-6, 1.3e-6, 0.8e-6, 0.6, steps, mats, mid, h0, src, probes,
+                    note="absorbing layers, lossy substrate and strip running into them, magnet clear of them",
+                    pml=dict(layers=tuple(layers), order=3.0, scale=1.0, kappa_max=kappa_max, alpha_max=alpha_max))
+
+
+def strip_resonator_pml(nx=256, ny=256, nz=128, steps=20000, layers=(10, 10, 8)) -> Workload:
+    """The strip resonator with absorbing layers lining every face instead of
+    bare PEC walls (the paper bounds its device by PMLs)."""
+    w = strip_resonator(nx, ny, nz, steps, name=f"strip_resonator_pml_{nx}x{ny}x{nz}")
+    w.pml = dict(layers=tuple(layers), order=3.0, scale=1.0, kappa_max=1.0, alpha_max=0.0)
+    w.note += f", absorbing layers {layers}"
+    return w
 
 
 CONFIGS = {

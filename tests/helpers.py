@@ -4,7 +4,7 @@ arrays."""
 import numpy as np
 
 import oracle
-from oracle import Material as OMaterial, OracleSim, Source as OSource
+from oracle import Material as OMaterial, OracleSim, Pml as OPml, Source as OSource
 
 
 def oracle_from_workload(w, llg_tol=1e-6, llg_max_iter=50, llg_fixed_iter=0, dt=None):
@@ -14,8 +14,14 @@ def oracle_from_workload(w, llg_tol=1e-6, llg_max_iter=50, llg_fixed_iter=0, dt=
     srcs = [OSource(comp=s["comp"], ijk=(s["i"], s["j"], s["k"]), J0=s["J0"], f0=s["f0"], Tp=s["Tp"], tpk=s["tpk"])
             for s in w.sources]
     eps = w.eps_r_cell() if w.eps_design is not None else None
+    pml = None
+    if getattr(w, "pml", None):
+        q = w.pml
+        pml = OPml(n=tuple(q["layers"]), order=q["order"], scale=q["scale"], kappa_max=q["kappa_max"],
+                   alpha_max=q["alpha_max"])
     return OracleSim(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, dt, mats, w.mat_id, w.hbias, sources=srcs, probes=w.probes,
-                     eps_r_cell=eps, llg_tol=llg_tol, llg_max_iter=llg_max_iter, llg_fixed_iter=llg_fixed_iter)
+                     eps_r_cell=eps, llg_tol=llg_tol, llg_max_iter=llg_max_iter, llg_fixed_iter=llg_fixed_iter,
+                     pml=pml)
 
 
 def compact(sim_oracle):
