@@ -65,7 +65,7 @@ struct Instance {
     float *psi[3] = {nullptr, nullptr, nullptr};
     float4 *pco[3] = {nullptr, nullptr, nullptr};
     long long pvol[3] = {0, 0, 0};
-    bool ca_nonpos = false;           // some edge class has cb != 0 and ca <= 0
+    bool ca_nonpos = false;           // some edge class has cb != 0 and ca = 0 (sigma = 2 eps / dt)
     bool has_pml() const { return pml_n[0] > 0 || pml_n[1] > 0 || pml_n[2] > 0; }
     size_t pml_floats() const { return 4 * (size_t)(pvol[0] + pvol[1] + pvol[2]); }
     size_t n_field() const { return (size_t)nz * ny * px; }
@@ -376,8 +376,9 @@ extern "C" void fdtd_llg_destroy(fdtd_llg_t h)
 
 // --------------------------------------------------------- set_materials
 // The absorbing layers need every magnetic cell outside them (the magnet
-// kernel owns those faces) and ca > 0 on every edge that they correct (the
-// E pass folds the CPML term into E^n through cb/ca).
+// kernel owns those faces) and ca != 0 on every edge that they correct (the
+// E pass folds the CPML term into E^n through cb/ca; ca < 0, a good
+// conductor, is fine: the sweep multiplies the folded value by ca again).
 static int pml_check(fdtd_llg_t h, const Instance &I)
 {
     const int n[3] = {I.nx, I.ny, I.nz};
@@ -387,7 +388,7 @@ static int pml_check(fdtd_llg_t h, const Instance &I)
             if (I.pml_n[a] > 0 && (lo[a] < I.pml_n[a] || lo[a] + ext[a] > n[a] - I.pml_n[a]))
                 return fail(h, FDTD_E_INVAL, "magnetic cells inside the absorbing layers");
     }
-    if (I.ca_nonpos) return fail(h, FDTD_E_INVAL, "absorbing layers need sigma < 2 eps / dt in every material");
+    if (I.ca_nonpos) return fail(h, FDTD_E_INVAL, "absorbing layers need sigma != 2 eps / dt in every material (ca = 0)");
     return FDTD_OK;
 }
 
@@ -743,7 +744,7 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
             float flag;
             std::memcpy(&flag, &w[9], 4);
             tab[3 * c] = make_float4(v[0], v[1], v[2], flag);
-            for (int q = 0; q < 3; ++q) ca_nonpos = ca_nonpos || (v[3 + q] != 0.f && v[q] <= 0.f);
+            for (int q = 0; q < 3; ++q) ca_nonpos = ca_nonpos || (v[3 + q] != 0.f && std::fabs(v[q]) < 1e-12f);
             tab[3 * c + 1] = make_float4(v[3], v[4], v[5], 0.f);
             tab[3 * c + 2] = make_float4(v[6], v[7], v[8], 0.f);
         }

@@ -283,6 +283,51 @@ def strip_resonator_pml(nx=256, ny=256, nz=128, steps=20000, layers=(10, 10, 8))
     return w
 
 
+def cpw_device(steps=1000, layers=(10, 10, 10), h0_oe=2000.0, metal="sigma", film=True) -> Workload:
+    """The paper's CPW resonator (section "Modeling Setup") on its own
+    120 x 250 x 1000 grid of 5 x 19 x 1 um cells (dt = 2.94e-15 s at CFL 0.9):
+    silicon substrate (eps_r 11.4) 500 um thick (z < 500), a 2 um metal
+    layer on it (z 500-501: ground planes 250 um wide at both x edges,
+    centre line 50 um wide with 25 um gaps, 198 cells = 3.76 mm long, gaps of
+    10 cells = 190 um to feeding patches of 16 cells = 304 um at both y ends),
+    a permalloy film (4 pi Ms = 1.2e4 G, alpha 0.003) 5 um thick and 30 um
+    wide on the centre line, 148 cells = 2.81 mm long, split by one
+    non-magnetic cell at its middle so that each half fits one magnet CTA;
+    bias H0 along y; absorbing layers on all six faces (the substrate, the
+    grounds and the feeding patches run into them).  Metal: sigma = 1e11 S/m
+    ("sigma") or PEC ("pec").  The voltage port is replaced by an x-directed
+    current in the gap beside the first feeding patch, f0 = 16 GHz,
+    Tp = 0.0625 ns; probes beside the film's middle and at the line's end.
+    film=False leaves the film out (the bare resonator)."""
+    nx, ny, nz = 120, 250, 1000
+    dx, dy, dz = 5e-6, 19e-6, 1e-6
+    metal_m = material(pec=True) if metal == "pec" else material(eps_r=1.0, sigma=1e11)
+    py_ms = 1.2e4 / (4 * np.pi) * 1e3          # 4 pi Ms in gauss -> Ms in A/m
+    mats = [material(), material(eps_r=11.4), metal_m, material(eps_r=1.0, Ms=py_ms, alpha=3e-3, gamma=1.76e11)]
+    mid = np.zeros((nz, ny, nx), dtype=np.uint8)
+    zs = 500
+    mid[:zs] = 1
+    m = mid[zs:zs + 2]                           # the metal layer (view)
+    m[:, :, :50] = 2                             # ground planes
+    m[:, :, 70:] = 2
+    y0 = (ny - 198) // 2                         # centre line y 26..223
+    m[:, y0:y0 + 198, 55:65] = 2
+    m[:, :16, 55:65] = 2                         # feeding patches
+    m[:, ny - 16:, 55:65] = 2
+    fy0 = ny // 2 - 74                           # film y 51..198, split at 125
+    if film:
+        mid[zs + 2:zs + 7, fy0:fy0 + 148, 57:63] = 3
+        mid[zs + 2:zs + 7, ny // 2, 57:63] = 0
+    src = [dict(comp=0, i=52, j=13, k=zs, J0=1.0, f0=16e9, Tp=0.0625e-9, tpk=0.0)]
+    probes = [(56, ny // 2 + 30, zs + 8), (60, y0 + 2, zs + 2)]
+    h0 = h0_oe * 1e3 / (4 * np.pi)              # oersted -> A/m
+    return Workload(f"cpw_device_{nx}x{ny}x{nz}", nx, ny, nz, dx, dy, dz, 0.9, steps, mats, mid,
+                    np.array([0.0, h0, 0.0]), src, probes,
+                    note=f"paper's CPW resonator, {'permalloy film on the centre line' if film else 'no film'}, H0 {h0_oe} Oe along y, "
+                         f"absorbing layers {layers}, metal {metal}",
+                    pml=dict(layers=tuple(layers), order=3.0, scale=1.0, kappa_max=1.0, alpha_max=0.0))
+
+
 CONFIGS = {
     "cavity_block_32": cavity_block,
     "strip_resonator_256x256x128": strip_resonator,

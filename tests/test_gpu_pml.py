@@ -166,3 +166,40 @@ def test_full_size_corner_window_equals_oracle():
             assert rel_err(got, ref[n], scale) < t, n
     # the layers took energy out of the patch's field
     assert np.abs(ref["Ex"][:, :, :layers[0]]).max() > 0
+
+
+def test_cpw_device_window_equals_oracle():
+    """The paper's CPW device at full size (120 x 250 x 1000, sigma = 1e11 S/m
+    metal, layers on all six faces) for 20 steps from its drive beside the
+    first feeding patch.  The oracle runs a window holding the whole x extent
+    (its real layers), the low-y layers, the drive and 22 cells of reach in
+    y and z; the window's own layers at its high-y end and both z cuts lie
+    beyond that reach and see only zero fields."""
+    w = W.cpw_device(steps=FULL_STEPS)
+    reach = FULL_STEPS + 2
+    s0 = w.sources[0]
+    d = w.pml["layers"]
+    j1 = s0["j"] + reach + d[1] + 1
+    k0, k1 = s0["k"] - reach - d[2] - 1, s0["k"] + reach + d[2] + 2
+    ms = np.array([m["Ms"] for m in w.materials])[w.mat_id]
+    mag = np.argwhere(ms > 0)
+    # the film starts along the bias (no torque): it stays still unless the
+    # drive's field reaches it, which it does not within the window's steps
+    assert np.all(mag[:, 1] > s0["j"] + reach)
+    sim = pkg.from_workload(w, probe_capacity=FULL_STEPS)
+    sim.step(FULL_STEPS)
+    ww = W.Workload("cpw_window", w.nx, j1, k1 - k0, w.dx, w.dy, w.dz, w.courant, FULL_STEPS, w.materials,
+                    np.ascontiguousarray(w.mat_id[k0:k1, :j1, :]), w.hbias,
+                    [dict(s0, k=s0["k"] - k0)], [], pml=w.pml)
+    orc = oracle_from_workload(ww)
+    orc.run(FULL_STEPS)
+    orc.half_push()
+    ref = compact(orc)
+    t = tol(FULL_STEPS)
+    for fam in ("E", "H"):
+        names = FAMILIES[fam][:3]
+        scale = max(float(np.abs(ref[n]).max()) for n in names)
+        assert scale > 0
+        for n in names:
+            got = sim.get_field(n)[k0:k1, :j1, :].astype(np.float64)
+            assert rel_err(got, ref[n], scale) < t, n
