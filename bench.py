@@ -338,16 +338,18 @@ def cpw_device_run(torch, pkg, W, steps=1000, warmup=20, paper_steps=1_700_000):
             "seconds_per_bias_point": round(sec / steps * paper_steps, 1)}
 
 
-def cpw_resonance(torch, pkg, W, steps=700_000, skip=150_000, decim=1000):
-    """The bare CPW resonator of the paper (no film) rung by its 16 GHz
-    pulse: ESPRIT on the line-end probe's Ez after the drive has ended
-    (decimated to 1000 dt = 2.94 ps, Nyquist 170 GHz) gives the resonator's
-    modes; the paper tunes the fundamental to f_p = 15.2 GHz."""
+def cpw_resonance(torch, pkg, W, steps=700_000, skip=150_000, decim=1000, film=False, h0_oe=2000.0):
+    """The paper's CPW resonator rung by its 16 GHz pulse: ESPRIT on the
+    line-end probe's Ez after the drive has ended (decimated to 1000 dt =
+    2.94 ps, Nyquist 170 GHz) gives the modes.  Without the film: the bare
+    resonator, which the paper tunes to f_p = 15.2 GHz.  With the film at a
+    bias whose Kittel frequency meets the resonator's: the two hybrid modes,
+    whose splitting is 2g (the paper: ~670 MHz)."""
     import numpy as np
 
     from paper_2510_22221_b300 import spectra
 
-    w = W.cpw_device(steps=steps, film=False)
+    w = W.cpw_device(steps=steps, film=film, h0_oe=h0_oe)
     sim = pkg.from_workload(w, probe_capacity=steps)
     dt = sim.dt
     t0 = time.time()
@@ -358,7 +360,8 @@ def cpw_resonance(torch, pkg, W, steps=700_000, skip=150_000, decim=1000):
     sim.destroy()
     x = x - x.mean()
     out = {"workload": w.name, "steps": steps, "wall_s": round(wall, 1), "samples": int(x.size),
-           "record_ns": round(x.size * dt * decim * 1e9, 3), "paper_f_p_ghz": 15.2}
+           "record_ns": round(x.size * dt * decim * 1e9, 3), "film": film, "h0_oe": h0_oe, "paper_f_p_ghz": 15.2,
+           "paper_2g_mhz": 670}
     # cross-check: peak of the Hann-windowed, 16x zero-padded DFT in 5-40 GHz
     nf = 16 * x.size
     spec = np.abs(np.fft.rfft(x * np.hanning(x.size), nf))
@@ -405,6 +408,8 @@ def main():
                     help="run just one of the extra measurements and print its JSON object")
     ap.add_argument("--adjoint-steps", type=int, default=4000, help="steps of the adjoint measurement")
     ap.add_argument("--cpw-steps", type=int, default=700_000, help="steps of the CPW resonance measurement (--only cpw_fp)")
+    ap.add_argument("--cpw-film", action="store_true", help="--only cpw_fp with the permalloy film (hybrid modes)")
+    ap.add_argument("--cpw-h0", type=float, default=2000.0, help="bias of --only cpw_fp, oersted")
     ap.add_argument("--tiling", type=int, default=0,
                     help="z-planes per sweep task for the headline run (0: autotune when --steps >= 1000)")
     args = ap.parse_args()
@@ -427,7 +432,7 @@ def main():
         elif args.only == "cpw":
             out = cpw_device_run(torch, pkg, W)
         elif args.only == "cpw_fp":
-            out = cpw_resonance(torch, pkg, W, steps=args.cpw_steps)
+            out = cpw_resonance(torch, pkg, W, steps=args.cpw_steps, film=args.cpw_film, h0_oe=args.cpw_h0)
         else:
             out = large_run(torch, pkg, W)
         print(json.dumps(out), flush=True)
