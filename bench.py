@@ -343,8 +343,9 @@ def cpw_resonance(torch, pkg, W, steps=700_000, skip=150_000, decim=1000, film=F
     line-end probe's Ez after the drive has ended (decimated to 1000 dt =
     2.94 ps, Nyquist 170 GHz) gives the modes.  Without the film: the bare
     resonator, which the paper tunes to f_p = 15.2 GHz.  With the film at a
-    bias whose Kittel frequency meets the resonator's: the two hybrid modes,
-    whose splitting is 2g (the paper: ~670 MHz)."""
+    bias near the crossing of the film's resonance with the resonator's: the
+    two hybrid modes, whose splitting is smallest, 2g, at the crossing (the
+    paper: ~670 MHz)."""
     import numpy as np
 
     from paper_2510_22221_b300 import spectra
