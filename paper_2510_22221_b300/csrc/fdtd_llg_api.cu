@@ -769,7 +769,10 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
     I.has_design = has_design;
     if (I.has_pml()) {
         const int rc = pml_check(h, I);
-        if (rc) return rc;
+        if (rc) {
+            I.materials_set = false;   // stepping refuses until materials and layers agree
+            return rc;
+        }
         for (int a = 0; a < 3; ++a)
             if (I.psi[a]) CKR(h, cudaMemset(I.psi[a], 0, 4 * (size_t)I.pvol[a] * sizeof(float)));
     }

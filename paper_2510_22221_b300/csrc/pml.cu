@@ -26,7 +26,7 @@ __device__ __forceinline__ bool layer_of(int q, int n, int d, int &s, int &t)
 // parameters, so the first global loads are the fields', all issued before
 // any store.
 template <bool HPASS, typename ClsT>
-__global__ void __launch_bounds__(kPT) pml_kernel(const PmlLaunch P, int src)
+__global__ void __launch_bounds__(kPT, 5) pml_kernel(const PmlLaunch P, int src)
 {
     const int blk = blockIdx.x;
     PmlBox B = P.box[0];
