@@ -11,7 +11,11 @@ Each pin checks the oracle against something other than itself:
   * the three 2-D orientations (plates normal to z, x, y) are rotations of
     one problem, so their probe series agree to rounding: a wrong index,
     sign or axis in any of the twelve memories breaks the agreement;
-  * energy leaves a box lined with layers on every face.
+  * energy leaves a box lined with layers on every face;
+  * an anisotropic problem rotated cyclically stays one problem, and a
+    centred source's field stays mirror-symmetric across the low and high
+    layers, to the last bit.
+The grading of the CFS alpha is not pinned beyond "the layers still absorb".
 """
 import numpy as np
 import pytest
@@ -127,3 +131,55 @@ def test_energy_leaves_a_box_lined_on_every_face():
     ea, eb = (s.run(400)["energy"] for s in sims)
     assert ea[-1] / ea.max() < 1e-4
     assert eb[-1] / eb.max() > 0.1     # the PEC box keeps what the source left in it
+
+
+def _plates_aniso(orient, steps=160):
+    """Plates normal to axis `orient`; the in-plane axes a1 = orient+1 and
+    a2 = orient+2 (mod 3) get different sizes (40, 48), spacings (1.0, 1.3
+    mm) and layers (10, 6), the thin axis 0.8 mm: cyclic relabellings of one
+    problem, which the curl equations map onto each other exactly."""
+    a1, a2 = (orient + 1) % 3, (orient + 2) % 3
+    N, D, L = [0] * 3, [0.0] * 3, [0] * 3
+    N[orient], N[a1], N[a2] = 1, 40, 48
+    D[orient], D[a1], D[a2] = 0.8e-3, 1.0e-3, 1.3e-3
+    L[orient], L[a1], L[a2] = 0, 10, 6
+    dt = oracle.courant_dt(*D, 0.95)
+    c = [0, 0, 0]
+    c[a1], c[a2] = 20, 24
+    pr = list(c)
+    pr[a1] += 3
+    pr[a2] -= 2
+    src = Source(comp=orient, ijk=tuple(c), J0=1.0, f0=F0, Tp=0.5 / F0, tpk=1.5 / F0)
+    sim = OracleSim(*N, *D, dt, [Material()], np.zeros((N[2], N[1], N[0]), np.uint8), (0, 0, 0),
+                    sources=[src], probes=[tuple(pr)],
+                    pml=Pml(n=tuple(L), order=3.0, scale=1.3, kappa_max=2.5, alpha_max=0.3))
+    return sim.run(steps)["probes"][:, 0, orient]
+
+
+def test_anisotropic_problem_rotated_is_one_problem():
+    """Distinct extents, spacings and layer counts per axis: a profile read
+    on the wrong axis or graded with the wrong spacing breaks the equality."""
+    runs = [_plates_aniso(o) for o in (2, 0, 1)]
+    m = np.abs(runs[0]).max()
+    assert m > 0
+    for r in runs[1:]:
+        assert np.abs(r - runs[0]).max() / m < 1e-12
+
+
+def test_centred_line_field_is_mirror_symmetric():
+    """A line current at the centre node of a square lined on both sides:
+    the field must be the same at mirrored nodes, low layers against high
+    ones, to the last bit (the depths rho of mirrored positions are equal
+    exactly); a grading that treats the two sides differently breaks it."""
+    n, d = 40, 10
+    dt = oracle.courant_dt(DX, DX, DX, 0.99)
+    src = Source(comp=2, ijk=(n // 2, n // 2, 0), J0=1.0, f0=F0, Tp=0.5 / F0, tpk=1.5 / F0)
+    sim = OracleSim(n, n, 1, DX, DX, DX, dt, [Material()], np.zeros((1, n, n), np.uint8), (0, 0, 0),
+                    sources=[src], pml=Pml(n=(d, d, 0), kappa_max=2.0, alpha_max=0.2))
+    sim.run(150)                              # the pulse has crossed the layers and come back
+    ez = sim.Ez[0]                            # (ny+1, nx+1) nodes
+    m = np.abs(ez).max()
+    assert np.abs(ez[:, n // 2 + 15]).max() > 1e-6 * m     # field inside the high x layers
+    assert np.array_equal(ez, ez[:, ::-1])
+    assert np.array_equal(ez, ez[::-1, :])
+    assert np.array_equal(ez, ez.T)
