@@ -154,7 +154,8 @@ int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const fdtd_mater
  * Errors: FDTD_E_INVAL (layers < 0 or more than half an axis, order < 0,
  * scale < 0, kappa_max < 1, alpha_max < 0, magnetic cells inside the
  * layers, a material with sigma = 2 eps / dt, where ca = 0; good conductors,
- * ca < 0, are allowed); FDTD_E_STATE after
+ * ca < 0, are allowed; a grid with 6 nz ny nx' >= 2^31, nx' = nx rounded up
+ * to 32, beyond the layer passes' 32-bit offsets); FDTD_E_STATE after
  * fdtd_llg_run_checkpointed.  Not covered by the adjoint
  * (fdtd_llg_run_checkpointed: FDTD_E_NOSYS) nor by writes of
  * fdtd_llg_planes (FDTD_E_NOSYS). */

@@ -14,7 +14,7 @@
  *   |M| = Ms and iterated until the domain-wide maximum of
  *   |M^{r} - M^{r-1}| / Ms falls below the tolerance.
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open:
  *   R1  Yee layout, cell (i,j,k) spans [i,i+1]x[j,j+1]x[k,k+1] cells:
  *       Ex(i+1/2,j,k) Ey(i,j+1/2,k) Ez(i,j,k+1/2) on edges,
  *       Hx(i,j+1/2,k+1/2) Hy(i+1/2,j,k+1/2) Hz(i+1/2,j+1/2,k) on faces,
