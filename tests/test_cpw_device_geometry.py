@@ -4,11 +4,17 @@ substrate and metal thickness, ground, gap and centre-line widths, the
 film's thickness, width and length, the feeding patches and gap capacitors,
 and the materials."""
 import numpy as np
+import pytest
 
 import oracle
 from paper_2510_22221_b300 import workloads as W
 
 UM = 1e-6
+
+
+@pytest.fixture(scope="module")
+def w():
+    return W.cpw_device()
 
 
 def _runs(a):
@@ -21,16 +27,14 @@ def _runs(a):
     return out
 
 
-def test_grid_and_time_step():
-    w = W.cpw_device()
+def test_grid_and_time_step(w):
     assert (w.nx, w.ny, w.nz) == (120, 250, 1000)
     assert np.isclose(w.nx * w.dx, 0.6e-3) and np.isclose(w.ny * w.dy, 4.75e-3) and np.isclose(w.nz * w.dz, 1e-3)
     dt = oracle.courant_dt(w.dx, w.dy, w.dz, w.courant)
     assert abs(dt - 2.94e-15) < 0.005e-15             # printed 2.94e-15 s at CFL 0.9
 
 
-def test_layers_of_the_stack():
-    w = W.cpw_device()
+def test_layers_of_the_stack(w):
     m = w.mat_id
     eps = np.array([q["eps_r"] for q in w.materials])
     sig = np.array([q["sigma"] for q in w.materials])
@@ -41,8 +45,7 @@ def test_layers_of_the_stack():
     assert eps[runs[2][0]] == 1.0 and sig[runs[2][0]] == 0.0              # vacuum above
 
 
-def test_coplanar_cross_section_and_film():
-    w = W.cpw_device()
+def test_coplanar_cross_section_and_film(w):
     sig = np.array([q["sigma"] for q in w.materials])
     ms = np.array([q["Ms"] for q in w.materials])
     metal = sig[w.mat_id[500, w.ny // 2 + 20]] > 0     # a cross-section of the metal layer (x)
@@ -62,8 +65,7 @@ def test_coplanar_cross_section_and_film():
     assert [q["alpha"] for q in w.materials if q["Ms"] > 0] == [3e-3]
 
 
-def test_line_gaps_and_feeding_patches():
-    w = W.cpw_device()
+def test_line_gaps_and_feeding_patches(w):
     sig = np.array([q["sigma"] for q in w.materials])
     along = (sig[w.mat_id[500, :, 60]] > 0).astype(int)   # down the centre of the line (y)
     runs = _runs(along)
