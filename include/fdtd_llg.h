@@ -271,15 +271,19 @@ int fdtd_llg_set_profiling(fdtd_llg_t h, int32_t on);
  * record afterwards. */
 int fdtd_llg_read_profile(fdtd_llg_t h, fdtd_llg_profile *out, int32_t reset);
 
-/* CUDA graphs for long step calls: mode 1 captures kGraphSteps (32) steps
- * once and replays the graph, 0 launches kernel by kernel, -1 (default)
- * behaves as 1 (replay shortens the gap between one step's kernels and the
- * next step's at every grid size measured: 86.6 -> 84.5 us per step on
- * 256x256x128, 537 -> 535 us on 512x512x256).  Graphs are used only for calls
- * of at least 2 kGraphSteps steps, on a stream that can be captured (not the
- * legacy default stream), and never while profiling; a one-step call replays
- * a graph of its step and the flush that ends it.  Results are the same to
- * the bit either way.  Errors: FDTD_E_INVAL. */
+/* CUDA graphs for step calls: mode 1 replays captured graphs, 0 launches
+ * kernel by kernel, -1 (default) behaves as 1 (replay shortens the gap
+ * between one step's kernels and the next step's at every grid size
+ * measured: 86.6 -> 84.5 us per step on 256x256x128, 537 -> 535 us on
+ * 512x512x256).  A call of n >= 2 steps replays floor(n / 32) times a graph
+ * of 32 steps, then a graph of the remaining n mod 32 steps; each graph is
+ * captured on first use (per starting buffer) and kept until the handle's
+ * launch set changes (tiling, materials, layers, sources, probes), so a
+ * short call repeated costs its capture once.  A one-step call replays a
+ * graph of its step and the flush that ends it.  Graphs are used only on a
+ * stream that can be captured (not the legacy default stream) and never
+ * while profiling.  Results are the same to the bit either way.
+ * Errors: FDTD_E_INVAL. */
 int fdtd_llg_set_graphs(fdtd_llg_t h, int32_t mode);
 
 /* The time step (s) shared by every instance of the handle's batch. */
@@ -422,7 +426,11 @@ int fdtd_llg_fit_coupling(const double *f_plus, const double *f_minus, int32_t n
  * with FDTD_E_INVAL.  The first call on a device looks up that array's device
  * address (with that device current); make that first call before any stream
  * capture.  Every call shares the array and overwrites the slots it reads, so
- * calls that overlap on the GPU (other streams, other threads) race.  No
+ * calls that overlap on the GPU (other streams, other threads) race.  The
+ * looked-up address is kept for the life of the process: after a
+ * cudaDeviceReset the library must be unloaded and loaded again before this
+ * entry point is used on that device.  A CUDA error already pending on the
+ * calling thread is reported (FDTD_E_CUDA) and left pending.  No
  * cudaMalloc, cudaFree or allocating library routine is called.  Errors:
  * FDTD_E_INVAL, FDTD_E_UNSTABLE (dt above the Courant limit), FDTD_E_CUDA;
  * message in fdtd_llg_last_error(NULL). */

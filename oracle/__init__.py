@@ -26,9 +26,12 @@ _LIB = os.path.join(_HERE, "_yee_llg_oracle.so")
 
 
 def build(force: bool = False) -> str:
-    """Compile the C oracle into ``oracle/_yee_llg_oracle.so`` (gcc, -O2)."""
+    """Compile the C oracle into ``oracle/_yee_llg_oracle.so`` (gcc, -O2,
+    OpenMP over z-planes)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", _LIB + ".tmp", _SRC,
+                               "-lm"])
+        os.replace(_LIB + ".tmp", _LIB)
     return _LIB
 
 
@@ -85,10 +88,21 @@ def lib():
         _lib.orc_llg_trapezoid.restype = None
         _lib.orc_psi_size.argtypes = [C.POINTER(_Problem)]
         _lib.orc_psi_size.restype = C.c_int64
+        _lib.orc_set_threads.argtypes = [C.c_int]
+        _lib.orc_set_threads.restype = C.c_int
+        # one thread unless asked: the tests run many small problems, and the
+        # timed baselines state the count they use
+        _lib.orc_set_threads(int(os.environ.get("ORACLE_THREADS", "1")))
         for nm in ("orc_mu0", "orc_eps0", "orc_c0"):
             getattr(_lib, nm).restype = C.c_double
             getattr(_lib, nm).argtypes = []
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's parallel loops (<= 0: every host core); returns
+    the count now in use.  Results do not depend on it (see the C header)."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def _p(a, ct=_dp):
@@ -297,5 +311,5 @@ class OracleSim:
             setattr(self, nm, np.array(np.broadcast_to(v, cur.shape), dtype=np.float64, order="C", copy=True))
 
 
-__all__ = ["build", "OracleSim", "Material", "Source", "Pml", "courant_dt", "source_value", "llg_trapezoid",
+__all__ = ["build", "set_threads", "OracleSim", "Material", "Source", "Pml", "courant_dt", "source_value", "llg_trapezoid",
            "mu0", "eps0", "c0"]

@@ -58,6 +58,12 @@
  *       H^{n+1/2} is the standard CPML leapfrog update while H^{n+1} (probes,
  *       energy) stays the mean of the two half-step values' plain pushes.
  *
+ * Threads: built with -fopenmp, the loops over z-planes (and over the
+ * magnetic cells of an LLG iterate) are split across threads.  Every value
+ * is computed by the same expression in the same order whatever the thread
+ * count; the energy sums each z-plane separately and adds the plane sums in
+ * plane order, so its bits do not depend on the thread count either.
+ *
  * Array layout: C order with i fastest.  Full staggered sizes:
  *   Ex nx*(ny+1)*(nz+1)  Ey (nx+1)*ny*(nz+1)  Ez (nx+1)*(ny+1)*nz
  *   Hx (nx+1)*ny*nz      Hy nx*(ny+1)*nz      Hz nx*ny*(nz+1)
@@ -67,6 +73,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_PI 3.14159265358979323846
 #define ORC_MU0 (4.0e-7 * ORC_PI)
@@ -183,6 +192,23 @@ double orc_courant_dt(double dx, double dy, double dz, double cfl)
 }
 
 double orc_mu0(void) { return ORC_MU0; }
+
+/* Threads of the parallel loops (<= 0: all available); returns the count in use. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n <= 0) n = omp_get_num_procs();
+    omp_set_num_threads(n);
+    return n;
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+/* A loop is split across threads only when it has at least this many
+ * elements (small grids run faster on one thread). */
+#define ORC_PAR_MIN 32768
 double orc_eps0(void) { return ORC_EPS0; }
 double orc_c0(void) { return ORC_C0; }
 
@@ -311,6 +337,7 @@ static void pml_h_update(const orc_problem *p, orc_state *s)
     const double f = p->dt / ORC_MU0;
     double *qxy = psi_block(p, s, 6), *qxz = psi_block(p, s, 7), *qyz = psi_block(p, s, 8);
     double *qyx = psi_block(p, s, 9), *qzx = psi_block(p, s, 10), *qzy = psi_block(p, s, 11);
+#pragma omp parallel for schedule(static) if (nC(p) >= ORC_PAR_MIN)
     for (int k = 0; k < NZ; ++k)
         for (int j = 0; j < NY; ++j)
             for (int i = 0; i <= NX; ++i) {   /* Hx at (i, j+1/2, k+1/2) */
@@ -320,6 +347,7 @@ static void pml_h_update(const orc_problem *p, orc_state *s)
                 const double st = pml_term(p, 1, j + 0.5, qxy + h, dyEz) - pml_term(p, 2, k + 0.5, qxz + h, dzEy);
                 s->Hx[h] -= f * (st - (dyEz - dzEy));
             }
+#pragma omp parallel for schedule(static) if (nC(p) >= ORC_PAR_MIN)
     for (int k = 0; k < NZ; ++k)
         for (int j = 0; j <= NY; ++j)
             for (int i = 0; i < NX; ++i) {   /* Hy at (i+1/2, j, k+1/2) */
@@ -329,6 +357,7 @@ static void pml_h_update(const orc_problem *p, orc_state *s)
                 const double st = pml_term(p, 2, k + 0.5, qyz + h, dzEx) - pml_term(p, 0, i + 0.5, qyx + h, dxEz);
                 s->Hy[h] -= f * (st - (dzEx - dxEz));
             }
+#pragma omp parallel for schedule(static) if (nC(p) >= ORC_PAR_MIN)
     for (int k = 0; k <= NZ; ++k)
         for (int j = 0; j < NY; ++j)
             for (int i = 0; i < NX; ++i) {   /* Hz at (i+1/2, j+1/2, k) */
@@ -402,12 +431,15 @@ static int ws_init(const orc_problem *p, orc_ws *w)
     w->nm = 0;
     for (int64_t c = 0; c < nc; ++c)
         if (cell_Ms(p, c) > 0.0) w->mcell[w->nm++] = c;
+#pragma omp parallel for schedule(static) if (nC(p) >= ORC_PAR_MIN)
     for (int k = 0; k <= NZ; ++k)
         for (int j = 0; j <= NY; ++j)
             for (int i = 0; i < NX; ++i) w->cx[iEx(p, i, j, k)] = edge_material(p, 0, i, j, k);
+#pragma omp parallel for schedule(static) if (nC(p) >= ORC_PAR_MIN)
     for (int k = 0; k <= NZ; ++k)
         for (int j = 0; j < NY; ++j)
             for (int i = 0; i <= NX; ++i) w->cy[iEy(p, i, j, k)] = edge_material(p, 1, i, j, k);
+#pragma omp parallel for schedule(static) if (nC(p) >= ORC_PAR_MIN)
     for (int k = 0; k < NZ; ++k)
         for (int j = 0; j <= NY; ++j)
             for (int i = 0; i <= NX; ++i) w->cz[iEz(p, i, j, k)] = edge_material(p, 2, i, j, k);
@@ -458,14 +490,17 @@ static int half_push(const orc_problem *p, orc_state *s, orc_ws *w, int *noconv,
     const int64_t nc = nC(p);
 
     /* H^* = H - (h/mu0) curl E  (Eq. iterate_H without the M terms) */
+#pragma omp parallel for schedule(static) if (nC(p) >= ORC_PAR_MIN)
     for (int k = 0; k < NZ; ++k)
         for (int j = 0; j < NY; ++j)
             for (int i = 0; i <= NX; ++i)
                 w->Hsx[iHx(p, i, j, k)] = s->Hx[iHx(p, i, j, k)] - c * curlE_x(p, s, i, j, k);
+#pragma omp parallel for schedule(static) if (nC(p) >= ORC_PAR_MIN)
     for (int k = 0; k < NZ; ++k)
         for (int j = 0; j <= NY; ++j)
             for (int i = 0; i < NX; ++i)
                 w->Hsy[iHy(p, i, j, k)] = s->Hy[iHy(p, i, j, k)] - c * curlE_y(p, s, i, j, k);
+#pragma omp parallel for schedule(static) if (nC(p) >= ORC_PAR_MIN)
     for (int k = 0; k <= NZ; ++k)
         for (int j = 0; j < NY; ++j)
             for (int i = 0; i < NX; ++i)
@@ -475,6 +510,7 @@ static int half_push(const orc_problem *p, orc_state *s, orc_ws *w, int *noconv,
     double res = 0.0;
     if (w->nm > 0) {
         /* fixed part of each cell's solve: b (Eq. llg_tra6) and the M^n term of a */
+#pragma omp parallel for schedule(static) if (w->nm >= ORC_PAR_MIN / 8)
         for (int64_t q = 0; q < w->nm; ++q) {
             int64_t cc = w->mcell[q];
             int i, j, k;
@@ -499,6 +535,7 @@ static int half_push(const orc_problem *p, orc_state *s, orc_ws *w, int *noconv,
         for (;;) {
             ++iters;
             res = 0.0;
+#pragma omp parallel for schedule(static) reduction(max : res) if (w->nm >= ORC_PAR_MIN / 8)
             for (int64_t q = 0; q < w->nm; ++q) {
                 int64_t cc = w->mcell[q];
                 int i, j, k;
@@ -545,12 +582,15 @@ static int half_push(const orc_problem *p, orc_state *s, orc_ws *w, int *noconv,
     }
 
     /* (H, M)^{n+1} = (H, M)^{n+1,r} */
+#pragma omp parallel for schedule(static) if (nC(p) >= ORC_PAR_MIN)
     for (int k = 0; k < NZ; ++k)
         for (int j = 0; j < NY; ++j)
             for (int i = 0; i <= NX; ++i) s->Hx[iHx(p, i, j, k)] = face_x(p, w, w->dM, i, j, k);
+#pragma omp parallel for schedule(static) if (nC(p) >= ORC_PAR_MIN)
     for (int k = 0; k < NZ; ++k)
         for (int j = 0; j <= NY; ++j)
             for (int i = 0; i < NX; ++i) s->Hy[iHy(p, i, j, k)] = face_y(p, w, w->dM, i, j, k);
+#pragma omp parallel for schedule(static) if (nC(p) >= ORC_PAR_MIN)
     for (int k = 0; k <= NZ; ++k)
         for (int j = 0; j < NY; ++j)
             for (int i = 0; i < NX; ++i) s->Hz[iHz(p, i, j, k)] = face_z(p, w, w->dM, i, j, k);
@@ -569,6 +609,7 @@ static void e_push(const orc_problem *p, orc_state *s, const orc_ws *w, double t
     const int pml = pml_on(p) && s->psi;
     /* new values into the workspace first would be needed only if the update
        read E neighbours; it reads only H, so in-place is exact. */
+#pragma omp parallel for schedule(static) if (nC(p) >= ORC_PAR_MIN)
     for (int k = 0; k <= NZ; ++k)
         for (int j = 0; j <= NY; ++j)
             for (int i = 0; i < NX; ++i) {
@@ -582,6 +623,7 @@ static void e_push(const orc_problem *p, orc_state *s, const orc_ws *w, double t
                         J += orc_source_value(p->src_par + 4 * q, t_half);
                 s->Ex[e] = (curl - (cf.sig / 2 - cf.eps / dt) * s->Ex[e] - J) / (cf.sig / 2 + cf.eps / dt);
             }
+#pragma omp parallel for schedule(static) if (nC(p) >= ORC_PAR_MIN)
     for (int k = 0; k <= NZ; ++k)
         for (int j = 0; j < NY; ++j)
             for (int i = 0; i <= NX; ++i) {
@@ -595,6 +637,7 @@ static void e_push(const orc_problem *p, orc_state *s, const orc_ws *w, double t
                         J += orc_source_value(p->src_par + 4 * q, t_half);
                 s->Ey[e] = (curl - (cf.sig / 2 - cf.eps / dt) * s->Ey[e] - J) / (cf.sig / 2 + cf.eps / dt);
             }
+#pragma omp parallel for schedule(static) if (nC(p) >= ORC_PAR_MIN)
     for (int k = 0; k < NZ; ++k)
         for (int j = 0; j <= NY; ++j)
             for (int i = 0; i <= NX; ++i) {
@@ -611,15 +654,36 @@ static void e_push(const orc_problem *p, orc_state *s, const orc_ws *w, double t
 }
 
 /* ------------------------------------------------------------ energy, R7 */
+/* Sum of w[e] v[e]^2 over nplanes z-planes of psize entries each: every
+ * plane summed on its own (entries in order), then the plane sums in order,
+ * so that the result does not depend on the thread count. */
+static double plane_sum_sq(const double *v, const edge_coef *cf, double wconst, int64_t nplanes, int64_t psize,
+                           double *part)
+{
+#pragma omp parallel for schedule(static) if (nplanes * psize >= ORC_PAR_MIN)
+    for (int64_t k = 0; k < nplanes; ++k) {
+        double s = 0.0;
+        for (int64_t e = k * psize; e < (k + 1) * psize; ++e) s += 0.5 * (cf ? cf[e].eps : wconst) * v[e] * v[e];
+        part[k] = s;
+    }
+    double t = 0.0;
+    for (int64_t k = 0; k < nplanes; ++k) t += part[k];
+    return t;
+}
+
 static double energy_ws(const orc_problem *p, const orc_state *s, const orc_ws *w)
 {
-    double We = 0.0, Wh = 0.0, Wz = 0.0;
-    for (int64_t e = 0; e < nEx(p); ++e) We += 0.5 * w->cx[e].eps * s->Ex[e] * s->Ex[e];
-    for (int64_t e = 0; e < nEy(p); ++e) We += 0.5 * w->cy[e].eps * s->Ey[e] * s->Ey[e];
-    for (int64_t e = 0; e < nEz(p); ++e) We += 0.5 * w->cz[e].eps * s->Ez[e] * s->Ez[e];
-    for (int64_t f = 0; f < nHx(p); ++f) Wh += 0.5 * ORC_MU0 * s->Hx[f] * s->Hx[f];
-    for (int64_t f = 0; f < nHy(p); ++f) Wh += 0.5 * ORC_MU0 * s->Hy[f] * s->Hy[f];
-    for (int64_t f = 0; f < nHz(p); ++f) Wh += 0.5 * ORC_MU0 * s->Hz[f] * s->Hz[f];
+    double *part = malloc(sizeof(double) * (NZ + 1));
+    if (!part) return NAN;
+    /* staggered sizes are (planes in z) x (entries per plane) */
+    double We = plane_sum_sq(s->Ex, w->cx, 0.0, NZ + 1, (int64_t)NX * (NY + 1), part)
+              + plane_sum_sq(s->Ey, w->cy, 0.0, NZ + 1, (int64_t)(NX + 1) * NY, part)
+              + plane_sum_sq(s->Ez, w->cz, 0.0, NZ, (int64_t)(NX + 1) * (NY + 1), part);
+    double Wh = plane_sum_sq(s->Hx, NULL, ORC_MU0, NZ, (int64_t)(NX + 1) * NY, part)
+              + plane_sum_sq(s->Hy, NULL, ORC_MU0, NZ, (int64_t)NX * (NY + 1), part)
+              + plane_sum_sq(s->Hz, NULL, ORC_MU0, NZ + 1, (int64_t)NX * NY, part);
+    free(part);
+    double Wz = 0.0;
     /* mu0 (|H0| Ms - H0.M) equals mu0 |H0| / (2 Ms) |M - Ms h|^2 when |M| = Ms
      * (h = H0/|H0|); the second form is evaluated because the first cancels
      * to rounding noise (and can turn negative) for small precession angles. */
@@ -653,6 +717,7 @@ double orc_energy(const orc_problem *p, const orc_state *s)
 void orc_div_b(const orc_problem *p, const orc_state *s, double *out)
 {
     const int64_t nc = nC(p);
+#pragma omp parallel for schedule(static) if (nC(p) >= ORC_PAR_MIN)
     for (int k = 0; k < NZ; ++k)
         for (int j = 0; j < NY; ++j)
             for (int i = 0; i < NX; ++i) {

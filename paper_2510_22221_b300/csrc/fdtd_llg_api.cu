@@ -13,7 +13,9 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -122,6 +124,9 @@ struct Sim {
     cudaGraphExec_t graph = nullptr;
     int graph_parity = -1;            // buffer holding the state when the graph starts; -1: none
     cudaGraphExec_t graph1[2] = {nullptr, nullptr};   // one-step calls (step and flush), by starting buffer
+    // graphs of r steps (0 < r < kGraphSteps) by starting buffer, built on
+    // first use: the part of a call that the kGraphSteps graph does not cover
+    cudaGraphExec_t graph_r[32][2] = {};
     bool graph_off = false;           // capture failed once on this stream: launch step by step
     int graph_mode = -1;              // 1 always, 0 never, -1 default (as 1)
     std::vector<void *> allocs;
@@ -170,6 +175,9 @@ struct Sim {
         if (graph) cudaGraphExecDestroy(graph);
         for (auto g1 : graph1)
             if (g1) cudaGraphExecDestroy(g1);
+        for (auto &gr : graph_r)
+            for (auto g : gr)
+                if (g) cudaGraphExecDestroy(g);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -1026,14 +1034,45 @@ static std::vector<int> model_near(const Sim *S, int slots, double frac, size_t 
 }
 
 static void drop_graph1(Sim *S);
+static void drop_graph_r(Sim *S);
+
+// Tilings that fdtd_llg_autotune found in this process, by the shape of the
+// batch (every instance's extents, magnet regions and absorbing layers): a
+// handle of the same shape whose tiling and tile width are both left to the
+// library starts from the tuned pair instead of the cost model, so the
+// choice does not depend on which handle, or how long a run, was tuned.
+static std::mutex g_tune_mu;
+static std::map<std::vector<long long>, std::pair<int, int>> g_tuned;   // shape -> (planes, width)
+
+static std::vector<long long> tune_key(const Sim *S)
+{
+    std::vector<long long> k;
+    for (const Instance &I : S->inst) {
+        k.push_back(I.nx);
+        k.push_back(I.ny);
+        k.push_back(I.nz);
+        k.push_back((long long)I.comps.size());
+        k.push_back(((long long)I.pml_n[0] << 40) | ((long long)I.pml_n[1] << 20) | I.pml_n[2]);
+    }
+    return k;
+}
 
 static int upload_descriptors(fdtd_llg_t h)
 {
     Sim *S = h->sim;
     if (!S->dirty) return FDTD_OK;
     CKR(h, cudaStreamSynchronize(S->stream));
-    S->sx = S->tile_width ? S->tile_width : choose_width(S);
-    S->planes = S->tiling > 0 ? S->tiling : model_planes(S, S->nsm * std::max(1, step_blocks_per_sm(false, true, S->sx)));
+    int want_w = S->tile_width, want_p = S->tiling;
+    if (!want_w && want_p <= 0) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        const auto it = g_tuned.find(tune_key(S));
+        if (it != g_tuned.end()) {
+            want_p = it->second.first;
+            want_w = it->second.second;
+        }
+    }
+    S->sx = want_w ? want_w : choose_width(S);
+    S->planes = want_p > 0 ? want_p : model_planes(S, S->nsm * std::max(1, step_blocks_per_sm(false, true, S->sx)));
     std::vector<Inst> hi(S->inst.size());
     std::vector<int> tile_inst;
     // sweep tasks of `planes` planes: energy slots per instance by column,
@@ -1229,6 +1268,7 @@ static int upload_descriptors(fdtd_llg_t h)
     if (S->graph) { cudaGraphExecDestroy(S->graph); S->graph = nullptr; }   // its launch set is stale
     S->graph_parity = -1;
     drop_graph1(S);
+    drop_graph_r(S);
     return FDTD_OK;
 }
 
@@ -1276,11 +1316,43 @@ constexpr int64_t kGraphSteps = 32;
 
 static bool capturable(cudaStream_t s) { return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread; }
 
-// (Re)build the graph of kGraphSteps steps starting from buffer S->cur.
+static_assert(kGraphSteps <= 32, "graph_r holds graphs of fewer than 32 steps");
+
 static void drop_graph1(Sim *S)
 {
     for (auto &g1 : S->graph1)
         if (g1) { cudaGraphExecDestroy(g1); g1 = nullptr; }
+}
+
+static void drop_graph_r(Sim *S)
+{
+    for (auto &gr : S->graph_r)
+        for (auto &g : gr)
+            if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+}
+
+// Capture n steps starting from buffer S->cur (the absorbing-layer passes and
+// the step's kernels, no flush) and instantiate them into *out.
+static cudaError_t capture_steps(Sim *S, LaunchSet L, int64_t n, cudaGraphExec_t *out)
+{
+    *out = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    int cur = S->cur;
+    for (int64_t q = 0; q < n && e == cudaSuccess; ++q) {
+        L.src = cur;
+        L.dst = 1 - cur;
+        e = launch_pml(S->pml.data(), (int)S->pml.size(), L.src, L.cls16, S->stream);
+        if (e == cudaSuccess) e = launch_step(L, S->stream, nullptr);
+        cur ^= 1;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(S->stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    if (e != cudaSuccess) *out = nullptr;
+    if (g) cudaGraphDestroy(g);
+    return e;
 }
 
 // The graph of a one-step call starting from buffer S->cur: the step's two
@@ -1304,24 +1376,11 @@ static cudaError_t build_graph1(Sim *S, LaunchSet L)
     return e;
 }
 
+// (Re)build the graph of kGraphSteps steps starting from buffer S->cur.
 static cudaError_t build_graph(Sim *S, LaunchSet L)
 {
     if (S->graph) { cudaGraphExecDestroy(S->graph); S->graph = nullptr; }
-    cudaError_t e = cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return e;
-    int cur = S->cur;
-    for (int64_t q = 0; q < kGraphSteps && e == cudaSuccess; ++q) {
-        L.src = cur;
-        L.dst = 1 - cur;
-        e = launch_pml(S->pml.data(), (int)S->pml.size(), L.src, L.cls16, S->stream);
-        if (e == cudaSuccess) e = launch_step(L, S->stream, nullptr);
-        cur ^= 1;
-    }
-    cudaGraph_t g = nullptr;
-    const cudaError_t e2 = cudaStreamEndCapture(S->stream, &g);
-    if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&S->graph, g, 0);
-    if (g) cudaGraphDestroy(g);
+    const cudaError_t e = capture_steps(S, L, kGraphSteps, &S->graph);
     S->graph_parity = e == cudaSuccess ? S->cur : -1;
     return e;
 }
@@ -1404,13 +1463,31 @@ extern "C" int fdtd_llg_step(fdtd_llg_t h, int64_t nsteps)
     }
     int64_t s = 0;
     const bool want = S->graph_mode != 0;   // -1 (default): replay shortens the gaps between steps at every size
-    if (want && !S->profiling && !S->graph_off && nsteps >= 2 * kGraphSteps && capturable(S->stream)) {
-        if ((!S->graph || S->graph_parity != S->cur) && build_graph(S, L) != cudaSuccess) {
-            cudaGetLastError();   // not fatal: this stream is stepped launch by launch
-            S->graph_off = true;
+    if (want && !S->profiling && !S->graph_off && nsteps >= 2 && capturable(S->stream)) {
+        // whole graphs of kGraphSteps steps, then one cached graph of the
+        // remaining r < kGraphSteps steps, so that calls of any length (a
+        // short call repeated, as a serving loop makes them) replay graphs
+        if (nsteps >= kGraphSteps) {
+            if ((!S->graph || S->graph_parity != S->cur) && build_graph(S, L) != cudaSuccess) {
+                cudaGetLastError();   // not fatal: this stream is stepped launch by launch
+                S->graph_off = true;
+            }
+            if (S->graph)
+                for (; s + kGraphSteps <= nsteps; s += kGraphSteps) CKR(h, cudaGraphLaunch(S->graph, S->stream));
         }
-        if (S->graph)
-            for (; s + kGraphSteps <= nsteps; s += kGraphSteps) CKR(h, cudaGraphLaunch(S->graph, S->stream));
+        const int64_t r = nsteps - s;
+        if (r > 0 && !S->graph_off) {
+            cudaGraphExec_t &gr = S->graph_r[r][S->cur];
+            if (!gr && capture_steps(S, L, r, &gr) != cudaSuccess) {
+                cudaGetLastError();
+                S->graph_off = true;
+            }
+            if (gr) {
+                CKR(h, cudaGraphLaunch(gr, S->stream));
+                s += r;
+                if (r & 1) S->cur ^= 1;
+            }
+        }
     }
     if (want && nsteps == 1 && !S->profiling && !S->graph_off && capturable(S->stream)) {
         // a one-step call: one replayed graph of the step and its flush
@@ -1942,6 +2019,10 @@ extern "C" int fdtd_llg_autotune(fdtd_llg_t h, int32_t trial_steps, int32_t *pla
     }
     rc = fdtd_llg_set_tiling(h, best);
     if (!rc) rc = fdtd_llg_set_tile_width(h, best_w);
+    if (!rc) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[tune_key(S)] = {best, best_w};
+    }
     if (planes) *planes = best;
     return rc;
 }

@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kTX *kTY) noalloc_e_push_kernel(float *__restr
     const int tx = b % ntx, ty = (b / ntx) % nty, tz = b / (ntx * nty);
     const int i = tx * kTX + threadIdx.x, j = ty * kTY + threadIdx.y;
     const long long plane = (long long)nx * ny;
-    float acc = 0.f;
+    double acc = 0.0;   // E^2 of this thread's edges, summed in FP64
     if (i < nx && j < ny) {
         const int k0 = tz * kKC, k1 = min(k0 + kKC, nz);
         long long o = (long long)k0 * plane + (long long)j * nx + i;
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kTX *kTY) noalloc_e_push_kernel(float *__restr
             Ex[o] = ex;
             Ey[o] = ey;
             Ez[o] = ez;
-            acc += ex * ex + ey * ey + ez * ez;
+            acc += (double)ex * ex + (double)ey * ey + (double)ez * ez;
             hx_km = hx;
             hy_km = hy;
         }
@@ -113,14 +113,19 @@ extern "C" int fdtd_llg_e_push_noalloc(float *Ex, float *Ey, float *Ez, const fl
         return noalloc_fail(FDTD_E_INVAL, "dx, dy, dz, dt and eps_r must be > 0 and sigma >= 0");
     if (dt * kC0 * std::sqrt(1.0 / (dx * dx) + 1.0 / (dy * dy) + 1.0 / (dz * dz)) > 1.0 + 1e-12)
         return noalloc_fail(FDTD_E_UNSTABLE, "dt exceeds the 3-D Courant limit");
-    const long long nb = (long long)((nx + kTX - 1) / kTX) * ((ny + kTY - 1) / kTY) * ((nz + kKC - 1) / kKC);
-    if (nb > kNoAllocMaxBlocks) {
+    const long long nb = (((long long)nx + kTX - 1) / kTX) * (((long long)ny + kTY - 1) / kTY) *
+                         (((long long)nz + kKC - 1) / kKC);
+    if (nb <= 0 || nb > kNoAllocMaxBlocks) {
         char msg[200];
         std::snprintf(msg, sizeof msg,
                       "grid needs %lld blocks of 32x8x16 cells; fdtd_llg_e_push_noalloc is limited to %d "
                       "(its partial sums live in a fixed device array)", nb, kNoAllocMaxBlocks);
         return noalloc_fail(FDTD_E_INVAL, msg);
     }
+    // an error left pending by earlier work on this thread is not this
+    // call's: report it and leave it pending rather than clear it below
+    if (cudaPeekAtLastError() != cudaSuccess)
+        return noalloc_fail(FDTD_E_CUDA, "a CUDA error was already pending before fdtd_llg_e_push_noalloc");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices)
         return noalloc_fail(FDTD_E_CUDA, "no usable current CUDA device");
@@ -144,7 +149,10 @@ extern "C" int fdtd_llg_e_push_noalloc(float *Ex, float *Ey, float *Ez, const fl
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     noalloc_e_push_kernel<<<(unsigned)nb, dim3(kTX, kTY), 0, s>>>(Ex, Ey, Ez, Hx, Hy, Hz, nx, ny, nz, (float)(1.0 / dx),
                                                                  (float)(1.0 / dy), (float)(1.0 / dz), ca, cb, scratch);
-    if (w_e) noalloc_energy_kernel<<<1, 256, 0, s>>>(scratch, (int)nb, 0.5 * eps * dx * dy * dz, w_e);
-    if (cudaGetLastError() != cudaSuccess) return noalloc_fail(FDTD_E_CUDA, "kernel launch failed");
+    if (cudaGetLastError() != cudaSuccess) return noalloc_fail(FDTD_E_CUDA, "E push kernel launch failed");
+    if (w_e) {
+        noalloc_energy_kernel<<<1, 256, 0, s>>>(scratch, (int)nb, 0.5 * eps * dx * dy * dz, w_e);
+        if (cudaGetLastError() != cudaSuccess) return noalloc_fail(FDTD_E_CUDA, "energy kernel launch failed");
+    }
     return FDTD_OK;
 }

@@ -16,3 +16,16 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def golden_dir():
     return os.path.join(ROOT, "tests", "golden")
+
+
+def pytest_sessionfinish(session, exitstatus):
+    path = os.environ.get("FDTD_PARITY_LOG")
+    if not path:
+        return
+    import json
+
+    from tests.helpers import PARITY_LOG
+
+    with open(path, "a") as f:
+        for r in PARITY_LOG:
+            f.write(json.dumps(r) + "\n")

@@ -1,6 +1,8 @@
 """Shared test helpers: build the oracle and the CUDA solver from one workload,
 and map between the oracle's full staggered arrays and the library's compact
 arrays."""
+import os
+
 import numpy as np
 
 import oracle
@@ -45,3 +47,14 @@ def dropped_values(sim_oracle):
     nx, ny, nz = o.nx, o.ny, o.nz
     parts = [o.Ex[nz], o.Ex[:, ny], o.Ey[nz], o.Ey[:, :, nx], o.Ez[:, ny], o.Ez[:, :, nx]]
     return max(float(np.abs(p).max()) for p in parts)
+
+
+# Measured errors of the parity tests (GPU against the FP64 oracle), with the
+# bound each was checked against; written out at the end of the session to the
+# file named by FDTD_PARITY_LOG (JSON lines), if that variable is set.
+PARITY_LOG = []
+
+
+def record(quantity, measured, bound, **extra):
+    test = os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0]
+    PARITY_LOG.append(dict(test=test, quantity=quantity, measured=float(measured), bound=float(bound), **extra))

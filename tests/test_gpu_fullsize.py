@@ -27,8 +27,8 @@ import pytest
 
 import paper_2510_22221_b300 as pkg
 from paper_2510_22221_b300 import workloads as W
-from tests.helpers import compact, oracle_from_workload
-from tests.test_gpu_parity import m_floor, probe_errors, rel_err, tol
+from tests.helpers import compact, oracle_from_workload, record
+from tests.test_gpu_parity import check_probes, m_floor, probe_errors, rel_err, tol, tol_m
 
 pytestmark = pytest.mark.gpu
 
@@ -149,18 +149,19 @@ def test_full_size_window_equals_oracle(full_run, which):
     for q, p in enumerate(keep):
         i, j, k = c.probes[q]
         errs = probe_errors(probes[p], out["probes"][:, q], M0[:, k, j, i], t, STEPS)
-        assert max(errs) < t, (p, errs)
+        check_probes(errs, t, STEPS, p)
     orc.half_push()
     ref = compact(orc)
     for fam in (("Ex", "Ey", "Ez"), ("Hx", "Hy", "Hz")):
         scale = max(float(np.abs(ref[n]).max()) for n in fam)
         assert scale > 0
         for n in fam:
-            assert rel_err(got[n][sl], ref[n], scale) < t, n
+            _chk(n, rel_err(got[n][sl], ref[n], scale), t, STEPS)
     dm = {n: ref[n] - M0[d] for d, n in enumerate(("Mx", "My", "Mz"))}
-    scale = max(max(float(np.abs(v).max()) for v in dm.values()), m_floor(float(np.abs(M0).max()), orc.step) / t)
+    tm = tol_m(STEPS)
+    scale = max(max(float(np.abs(v).max()) for v in dm.values()), m_floor(float(np.abs(M0).max()), orc.step) / tm)
     for n, v in dm.items():
-        assert rel_err(got["d" + n][sl], v, scale) < t, n
+        _chk("d" + n, rel_err(got["d" + n][sl], v, scale), tm, STEPS)
 
 
 # ------------------------------------------------ configs 2 and 3 in full
@@ -192,22 +193,28 @@ def _compare_whole(got, probes, w, patch, dt, steps, llg_fixed_iter=0):
     t = tol(steps)
     for p, (i, j, k) in enumerate(w.probes):
         errs = probe_errors(probes[p], out["probes"][:, p], M0[:, k, j, i], t, steps)
-        assert max(errs) < t, (p, errs)
+        check_probes(errs, t, steps, p)
     orc.half_push()
     ref = compact(orc)
     for fam in (("Ex", "Ey", "Ez"), ("Hx", "Hy", "Hz")):
         scale = max(float(np.abs(ref[n]).max()) for n in fam)
         assert scale > 0
         for n in fam:
-            assert rel_err(got[n], ref[n], scale) < t, n
+            _chk(n, rel_err(got[n], ref[n], scale), t, steps)
     dm = {n: ref[n] - M0[d] for d, n in enumerate(("Mx", "My", "Mz"))}
-    scale = max(max(float(np.abs(v).max()) for v in dm.values()), m_floor(float(np.abs(M0).max()), orc.step) / t)
+    tm = tol_m(steps)
+    scale = max(max(float(np.abs(v).max()) for v in dm.values()), m_floor(float(np.abs(M0).max()), orc.step) / tm)
     assert max(float(np.abs(v).max()) for v in dm.values()) > 1e3 * m_floor(float(np.abs(M0).max()), orc.step)
     for n, v in dm.items():
-        assert rel_err(got["d" + n], v, scale) < t, n
+        _chk("d" + n, rel_err(got["d" + n], v, scale), tm, steps)
 
 
 _NAMES = ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz", "dMx", "dMy", "dMz")
+
+
+def _chk(name, err, t, steps):
+    record(f"field {name}", err, t, steps=steps)
+    assert err < t, name
 
 
 def test_bias_sweep_batch_members_equal_oracle():

@@ -1,26 +1,36 @@
 """CUDA path vs the FP64 oracle, element by element, on the same seeded
 inputs, through the C ABI (arxiv 2510.22221, section "Numerical Model").
 
-Tolerance.  Fields are FP32 (unit roundoff u = 6e-8).  Each update rounds a
-handful of times and the leap-frog neither damps nor amplifies roundoff, so
-after N steps the deviation from FP64 is ~u sqrt(N) typical, bounded by ~c u N
-with c of order ten; the tests use max|gpu - fp64| <= TOL(N) * scale with
-TOL(N) = 20 u N, floored at 2e-5 (the FP32 rounding of the coefficients
-themselves, ~u relative per update, enters every step).  FP32 errors are
-absolute at the size of the largest nearby values, so the scale is the
-largest FP64 value of the same family (E: Ex, Ey, Ez; H: the three H
-components and the wall faces; M: the change of M from its start) at the
-probe or over the grid, not the component's own largest value: a component a
-thousand times weaker than its neighbours carries the same absolute error.
-The oracle stores M whole (|M| = Ms ~ 1e5 A/m), so its own M rounds by
-~2^-53 Ms at every normalisation; the change of M is therefore compared with
-an absolute floor of 16 * 2^-53 * Ms * sqrt(2N + 2) on top of TOL(N)."""
+Tolerances.  Fields are FP32 (unit roundoff u = 6e-8).  Each update rounds a
+handful of times; the leap-frog neither damps nor amplifies that rounding, so
+it adds up like a random walk, ~u sqrt(N) after N steps, while the FP32
+rounding of the update coefficients shifts each resonance's frequency by ~u
+and drifts its phase linearly in N.  The bounds are calibrated on the errors
+these tests measured (every test records them; FDTD_PARITY_LOG writes them
+out): the E and H families 0.8-9 u sqrt(N) over 20-400 steps and 30 u sqrt(N)
+for a tilted magnetisation, 0.13 u N on the 2000-step cavity (a rung mode:
+phase drift); the change of M up to 60 u sqrt(N); the energy below
+0.5 u sqrt(N).  So
+
+    E, H         TOL(N)   = u (30 sqrt(N) + 5 N)
+    change of M  TOL_M(N) = u (300 sqrt(N) + 5 N)
+    energy       TOL_W(N) = 10 u sqrt(N)
+
+each a bound on max|gpu - fp64| / scale.  FP32 errors are absolute at the size
+of the largest nearby values, so the scale is the largest FP64 value of the
+same family (E: Ex, Ey, Ez; H: the three H components and the wall faces; M:
+the change of M from its start) at the probe or over the grid, not the
+component's own largest value: a component a thousand times weaker than its
+neighbours carries the same absolute error.  The oracle stores M whole
+(|M| = Ms ~ 1e5 A/m), so its own M rounds by ~2^-53 Ms at every
+normalisation; the change of M is therefore compared with an absolute floor
+of 16 * 2^-53 * Ms * sqrt(2N + 2) on top of TOL_M(N)."""
 import numpy as np
 import pytest
 
 import paper_2510_22221_b300 as pkg
 from paper_2510_22221_b300 import workloads as W
-from tests.helpers import compact, dropped_values, oracle_from_workload
+from tests.helpers import compact, dropped_values, oracle_from_workload, record
 
 pytestmark = pytest.mark.gpu
 
@@ -28,7 +38,18 @@ U32 = 6e-8
 
 
 def tol(n):
-    return max(2e-5, 20 * U32 * n)
+    """Bound for the E and H families after n steps (module docstring)."""
+    return U32 * (30.0 * np.sqrt(n) + 5.0 * n)
+
+
+def tol_m(n):
+    """Bound for the change of M after n steps."""
+    return U32 * (300.0 * np.sqrt(n) + 5.0 * n)
+
+
+def tol_w(n):
+    """Bound for the energy record over n steps."""
+    return U32 * 10.0 * np.sqrt(max(n, 1))
 
 
 def rel_err(a, b, scale=None):
@@ -48,7 +69,9 @@ def m_floor(Ms_max, n):
 
 
 def probe_errors(g, ref, M0cell, t=None, n=0):
-    """Per-component errors of a probe series (rows x 9) with family scales."""
+    """Per-component errors of a probe series (rows x 9) with family scales
+    (t given: the change of M is scaled no lower than the oracle's rounding
+    floor over TOL_M(n))."""
     g = np.asarray(g, np.float64).copy()
     ref = np.asarray(ref, np.float64).copy()
     for d in range(3):
@@ -59,7 +82,7 @@ def probe_errors(g, ref, M0cell, t=None, n=0):
         fam = slice(3 * (c // 3), 3 * (c // 3) + 3)
         scale = float(np.abs(ref[:, fam]).max())
         if c >= 6 and t is not None:
-            scale = max(scale, m_floor(float(np.abs(M0cell).max()), n) / t)
+            scale = max(scale, m_floor(float(np.abs(M0cell).max()), n) / tol_m(n))
         errs.append(rel_err(g[:, c], ref[:, c], scale))
     return errs
 
@@ -84,15 +107,34 @@ def compare_fields(sim, orc, M0, t):
         ref[n] = ref[n] - M0[d]
         got[n] = sim.get_field("d" + n).astype(np.float64)
     errs = {}
+    tm = tol_m(orc.step)
     for key, fam in FAMILIES.items():
         scale = max(float(np.abs(ref[n]).max()) for n in fam)
         if key == "M":
-            scale = max(scale, m_floor(float(np.abs(M0).max()), orc.step) / t)
+            scale = max(scale, m_floor(float(np.abs(M0).max()), orc.step) / tm)
         for n in fam:
             errs[n] = rel_err(got[n], ref[n], scale)
-    bad = {k: v for k, v in errs.items() if v > t}
+    bound = {n: (tm if key == "M" else t) for key, fam in FAMILIES.items() for n in fam}
+    for key, fam in FAMILIES.items():
+        record(f"field {key}", max(errs[n] for n in fam), bound[fam[0]], steps=int(orc.step))
+    bad = {k: v for k, v in errs.items() if v > bound[k]}
     assert not bad, (bad, errs)
     return errs
+
+
+def check_probes(errs, t, n, p=0):
+    """Probe errors by family: E and H against t, the change of M against TOL_M(n)."""
+    tm = tol_m(n)
+    for key, sl, b in (("E", slice(0, 3), t), ("H", slice(3, 6), t), ("M", slice(6, 9), tm)):
+        record(f"probe {p} {key}", max(errs[sl]), b, steps=n)
+    assert max(errs[:6]) < t and max(errs[6:]) < tm, (p, errs)
+
+
+def check_energy(got, ref, t, n):
+    """The energy record against TOL_W(n) (t, the field bound, is not used)."""
+    e = rel_err(got, ref)
+    record("energy", e, tol_w(n), steps=n)
+    assert e < tol_w(n)
 
 
 def test_cavity_block_probe_energy_and_fields():
@@ -102,9 +144,9 @@ def test_cavity_block_probe_energy_and_fields():
     assert g.shape == (w.steps, 9)
     t = tol(w.steps)
     errs = probe_errors(g, out["probes"][:, 0], np.zeros(3))
-    assert max(errs) < t, errs
+    check_probes(errs, t, w.steps)
     assert np.all(g[:, 6:] == 0)          # the probe cell is outside the block
-    assert rel_err(sim.energy(), out["energy"]) < t
+    check_energy(sim.energy(), out["energy"], t, w.steps)
     compare_fields(sim, orc, M0, t)
 
 
@@ -115,8 +157,8 @@ def test_random_small_every_feature(seed):
     t = tol(w.steps)
     for p, (i, j, k) in enumerate(w.probes):
         errs = probe_errors(sim.probe(p), out["probes"][:, p], M0[:, k, j, i], t, w.steps)
-        assert max(errs) < t, (p, errs)
-    assert rel_err(sim.energy(), out["energy"]) < t
+        check_probes(errs, t, w.steps, p)
+    check_energy(sim.energy(), out["energy"], t, w.steps)
     compare_fields(sim, orc, M0, t)
 
 
@@ -136,8 +178,8 @@ def test_design_box_against_the_walls(box):
     t = tol(w.steps)
     for p, (i, j, k) in enumerate(w.probes):
         errs = probe_errors(sim.probe(p), out["probes"][:, p], M0[:, k, j, i], t, w.steps)
-        assert max(errs) < t, (p, errs)
-    assert rel_err(sim.energy(), out["energy"]) < t
+        check_probes(errs, t, w.steps, p)
+    check_energy(sim.energy(), out["energy"], t, w.steps)
     compare_fields(sim, orc, M0, t)
     sim.destroy()
 
@@ -204,8 +246,8 @@ def test_large_region_staged_in_blocks(kind):
     t = tol(w.steps)
     for p, (i, j, k) in enumerate(w.probes):
         errs = probe_errors(sim.probe(p), out["probes"][:, p], M0[:, k, j, i], t, w.steps)
-        assert max(errs) < t, (p, errs)
-    assert rel_err(sim.energy(), out["energy"]) < t
+        check_probes(errs, t, w.steps, p)
+    check_energy(sim.energy(), out["energy"], t, w.steps)
     compare_fields(sim, orc, M0, t)
     sim.destroy()
 
@@ -326,7 +368,7 @@ def test_energy_summed_in_chunks_matches_oracle_and_split(planes):
     a.step(w.steps)
     assert (a.get_tiling(), a.get_tile_width()) == (planes, 64)
     ref = a.energy()
-    assert rel_err(ref, out["energy"]) < tol(w.steps)
+    check_energy(ref, out["energy"], tol(w.steps), w.steps)
     b = pkg.from_workload(w, probe_capacity=64)
     b.set_tiling(planes)
     for n in (1, 1, 1, 2, 35):
