@@ -286,6 +286,26 @@ int fdtd_llg_read_profile(fdtd_llg_t h, fdtd_llg_profile *out, int32_t reset);
  * Errors: FDTD_E_INVAL. */
 int fdtd_llg_set_graphs(fdtd_llg_t h, int32_t mode);
 
+/* Magnet CTAs per magnetic region (section "Numerical Model": the LLG solve
+ * of Eqs. llg_tra4-6 with Eq. iterate_H, Jacobi-iterated over a region).  A
+ * region's box is split along its longest axis into `ctas` slabs, one per CTA
+ * of a thread-block cluster; after each Jacobi iterate the CTAs exchange the
+ * change of M of the layers beside each cut through distributed shared memory
+ * and take the cluster's largest residual, so fields and M are the same to
+ * the bit for every split (the energy's partial sums are grouped per CTA).
+ * 0 (default): about 128 cells per CTA in the largest region while the
+ * magnet CTAs of all regions number at most one per SM, and never fewer than
+ * the slabs need to fit; at most 8 and at most the shortest split extent of
+ * any region of the batch.  Each CTA has one thread per slab cell (128 to
+ * 512).  A
+ * region fits when its largest slab holds at most 4096 cells and fits one
+ * CTA's shared memory, so a region's box may hold up to ~32768 cells.
+ * get_magnet_cluster returns the count in effect (0 before the first step or
+ * without magnets).  Errors: FDTD_E_INVAL (ctas outside 0..8; at the next
+ * step, a split longer than a region or a slab too large). */
+int fdtd_llg_set_magnet_cluster(fdtd_llg_t h, int32_t ctas);
+int fdtd_llg_get_magnet_cluster(fdtd_llg_t h, int32_t *ctas);
+
 /* The time step (s) shared by every instance of the handle's batch. */
 int fdtd_llg_get_dt(fdtd_llg_t h, double *dt);
 

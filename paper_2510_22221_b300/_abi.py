@@ -73,6 +73,8 @@ SIGNATURES = {
     "fdtd_llg_read_profile": (C.c_int, [_vp, C.POINTER(Profile), C.c_int32]),
     "fdtd_llg_get_dt": (C.c_int, [_vp, _dp]),
     "fdtd_llg_set_graphs": (C.c_int, [_vp, C.c_int32]),
+    "fdtd_llg_set_magnet_cluster": (C.c_int, [_vp, C.c_int32]),
+    "fdtd_llg_get_magnet_cluster": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
     "fdtd_llg_set_tiling": (C.c_int, [_vp, C.c_int32]),
     "fdtd_llg_get_tiling": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
     "fdtd_llg_autotune": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_int32)]),

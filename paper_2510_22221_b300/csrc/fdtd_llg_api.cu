@@ -98,6 +98,9 @@ struct Sim {
     // absorbing layers: the launch descriptor of each lined instance
     std::vector<PmlLaunch> pml;
     int ntiles = 0, nftiles = 0, ncomp = 0, vmax = 0, mag_smem = 0;
+    int mag_cs = 1, mag_xs = 0;       // magnet CTAs per region (cluster size) and exported floats per layer
+    int mag_cluster = 0;              // requested magnet CTAs per region (0: automatic)
+    int mag_cs_need = 1, mag_cs_fast = 1;   // fewest magnet CTAs per region that fit; the fast split
     bool stab = false;                // every class table small enough for shared memory
     int tiling = 0;                   // requested z-planes per sweep task (0: model)
     int planes = 0;                   // z-planes per sweep task in effect
@@ -387,6 +390,28 @@ extern "C" void fdtd_llg_destroy(fdtd_llg_t h)
 // kernel owns those faces) and ca != 0 on every edge that they correct (the
 // E pass folds the CPML term into E^n through cb/ca; ca < 0, a good
 // conductor, is fine: the sweep multiplies the folded value by ca again).
+// Whether a region's bounding box bx x by x bz can run: split along its
+// longest axis into up to kMagClusterMax slabs, one per CTA of a cluster,
+// its largest slab must hold at most kMagMaxV cells and fit one CTA's shared
+// memory beside the exchange area of its cross-section.
+static bool mag_region_fits(int bx, int by, int bz, std::string &why)
+{
+    const int a = mag_split_axis(bx, by, bz);
+    const int ext = a == 0 ? bx : (a == 1 ? by : bz);
+    const int cs = std::min(kMagClusterMax, ext);
+    int sx, sy, sz, qx, py, ps;
+    mag_slab_box(bx, by, bz, cs, sx, sy, sz);
+    const int xs = cs > 1 ? mag_cross_section(bx, by, bz) : 0;
+    const long long V = (long long)bx * by * bz, sv = (long long)sx * sy * sz;
+    if (sv > kMagMaxV || !mag_stage_block(sx, sy, sz, qx, py, ps, xs, xs)) {
+        why = "a magnetic region's bounding box (" + std::to_string(bx) + " x " + std::to_string(by) + " x " +
+              std::to_string(bz) + " = " + std::to_string(V) + " cells) does not fit " + std::to_string(cs) +
+              " magnet CTAs: each holds at most " + std::to_string(kMagMaxV) + " cells of a slab along the box's longest axis";
+        return false;
+    }
+    return true;
+}
+
 static int pml_check(fdtd_llg_t h, const Instance &I)
 {
     const int n[3] = {I.nx, I.ny, I.nz};
@@ -652,13 +677,8 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
                     if (magm[mid[cc]] && label.emplace(cc, L).second) stack.push_back(cc);
                 }
             }
-            const long long V = (long long)(b.x1 - b.x0 + 1) * (b.y1 - b.y0 + 1) * (b.z1 - b.z0 + 1);
-            if (V > kMagMaxV)
-                return fail(h, FDTD_E_INVAL, "a magnetic region's bounding box holds " + std::to_string(V) + " cells (maximum " +
-                                                 std::to_string(kMagMaxV) + ")");
-            int qx, py, ps;
-            if (!mag_stage_block(b.x1 - b.x0 + 1, b.y1 - b.y0 + 1, b.z1 - b.z0 + 1, qx, py, ps))
-                return fail(h, FDTD_E_INVAL, "a magnetic region's bounding box has too many faces for one CTA's shared memory");
+            std::string why;
+            if (!mag_region_fits(b.x1 - b.x0 + 1, b.y1 - b.y0 + 1, b.z1 - b.z0 + 1, why)) return fail(h, FDTD_E_INVAL, why);
             boxes.push_back(b);
         }
     // magnet material table (compact index per magnetic material)
@@ -1042,7 +1062,8 @@ static void drop_graph_r(Sim *S);
 // library starts from the tuned pair instead of the cost model, so the
 // choice does not depend on which handle, or how long a run, was tuned.
 static std::mutex g_tune_mu;
-static std::map<std::vector<long long>, std::pair<int, int>> g_tuned;   // shape -> (planes, width)
+struct Tuned { int planes, width, mag_cs; };
+static std::map<std::vector<long long>, Tuned> g_tuned;   // shape -> tuned choices (mag_cs 0: the automatic one)
 
 static std::vector<long long> tune_key(const Sim *S)
 {
@@ -1062,13 +1083,16 @@ static int upload_descriptors(fdtd_llg_t h)
     Sim *S = h->sim;
     if (!S->dirty) return FDTD_OK;
     CKR(h, cudaStreamSynchronize(S->stream));
-    int want_w = S->tile_width, want_p = S->tiling;
-    if (!want_w && want_p <= 0) {
+    int want_w = S->tile_width, want_p = S->tiling, want_cs = S->mag_cluster;
+    {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         const auto it = g_tuned.find(tune_key(S));
         if (it != g_tuned.end()) {
-            want_p = it->second.first;
-            want_w = it->second.second;
+            if (!want_w && want_p <= 0) {
+                want_p = it->second.planes;
+                want_w = it->second.width;
+            }
+            if (!want_cs) want_cs = it->second.mag_cs;
         }
     }
     S->sx = want_w ? want_w : choose_width(S);
@@ -1144,13 +1168,66 @@ static int upload_descriptors(fdtd_llg_t h)
         d.nmag = (int)I.comps.size();
         for (auto C : I.comps) {
             C.inst = (int)ii;
-            mag_stage_block(C.bx, C.by, C.bz, C.qx, C.py, C.ps);
+            C.ax = mag_split_axis(C.bx, C.by, C.bz);
             comps.push_back(C);
-            vmax = std::max(vmax, C.V);
-            msmem = std::max(msmem, (int)mag_smem_bytes(C.bx, C.by, C.bz, C.qx, C.py, C.ps));
         }
         for (size_t m = 0; m < I.mm.size(); ++m) d.mm[m] = I.mm[m];
         c16 = c16 || I.cls_bytes == 2;
+    }
+    // magnet CTAs per region: the requested count, else as set out below
+    // (the autotuner may also time the other choice); never more than the
+    // shortest split extent of any region (no empty slab) nor kMagClusterMax
+    int mcs = 1, mxs = 0;
+    if (!comps.empty()) {
+        int maxV = 0, minext = kMagClusterMax;
+        for (const MagComp &C : comps) {
+            maxV = std::max(maxV, C.V);
+            minext = std::min(minext, C.ax == 0 ? C.bx : (C.ax == 1 ? C.by : C.bz));
+        }
+        // fewest CTAs per region whose slabs fit one CTA
+        int need = 1;
+        for (const MagComp &C : comps) {
+            int c = 1;
+            for (; c < kMagClusterMax; ++c) {
+                int sx, sy, sz, qx, py, ps;
+                mag_slab_box(C.bx, C.by, C.bz, c, sx, sy, sz);
+                const int x = c > 1 ? mag_cross_section(C.bx, C.by, C.bz) : 0;
+                if ((long long)sx * sy * sz <= kMagMaxV && mag_stage_block(sx, sy, sz, qx, py, ps, x, x)) break;
+            }
+            need = std::max(need, c);
+        }
+        // split further, to about kMagCtaCells cells per CTA, only where the
+        // magnet kernel would outlast the field sweep running beside it (a
+        // small grid with a large region): split CTAs displace sweep CTAs
+        // from more SMs.  Model: the sweep at ~5 TB/s over every cell; the
+        // magnet kernel in one CTA ~15 us + 40 us per 1024 cells of the
+        // largest region.  Measured per step: 128x128x64 with a 1024-cell
+        // block 43 -> 33 us on 8 CTAs; 256x256x128 with a 1280-cell film 84 us
+        // on 1 CTA, 84-87 us on 2-8; the 64-cube sweep 338 us on 1, 349-370
+        // on 2-4.
+        long long cells = 0;
+        for (const Instance &I : S->inst) cells += (long long)I.nx * I.ny * I.nz;
+        const double t_sweep = (double)cells * 49.0 / 5.0e6, t_mag = 15.0 + 40.0 * maxV / 1024.0;
+        const int fast = std::min({kMagClusterMax, minext, (maxV + kMagCtaCells - 1) / kMagCtaCells});
+        S->mag_cs_fast = std::max(need, fast);
+        S->mag_cs_need = need;
+        mcs = want_cs > 0 ? want_cs : (t_mag > t_sweep ? std::max(need, fast) : need);
+        if (mcs > minext)
+            return fail(h, FDTD_E_INVAL, "magnet cluster of " + std::to_string(mcs) + " CTAs splits a region only " +
+                                             std::to_string(minext) + " cells long");
+        if (mcs > 1)
+            for (const MagComp &C : comps) mxs = std::max(mxs, mag_cross_section(C.bx, C.by, C.bz));
+        for (MagComp &C : comps) {
+            int sx, sy, sz;
+            mag_slab_box(C.bx, C.by, C.bz, mcs, sx, sy, sz);
+            const int hxs = mcs > 1 ? mag_cross_section(C.bx, C.by, C.bz) : 0;
+            if ((long long)sx * sy * sz > kMagMaxV || !mag_stage_block(sx, sy, sz, C.qx, C.py, C.ps, mxs, hxs))
+                return fail(h, FDTD_E_INVAL, "a magnetic region (" + std::to_string(C.bx) + " x " + std::to_string(C.by) +
+                                                 " x " + std::to_string(C.bz) + ") does not fit " + std::to_string(mcs) +
+                                                 " magnet CTAs; the batch's smallest region limits the split");
+            vmax = std::max(vmax, sx * sy * sz);
+            msmem = std::max(msmem, (int)mag_cta_smem(sx, sy, sz, C.qx, C.py, C.ps, mxs, hxs));
+        }
     }
     if (c16)
         for (size_t ii = 0; ii < S->inst.size(); ++ii) {
@@ -1197,7 +1274,7 @@ static int upload_descriptors(fdtd_llg_t h)
     S->d_tile_inst = (int *)S->dalloc(tile_inst.size() * sizeof(int));
     S->d_ftile_inst = (int4 *)S->dalloc(std::max<size_t>(1, ftask.size()) * sizeof(int4));
     S->d_comps = (MagComp *)S->dalloc(std::max<size_t>(1, comps.size()) * sizeof(MagComp));
-    const size_t part_stride = ftask.size() * kSW + comps.size();
+    const size_t part_stride = ftask.size() * kSW + comps.size() * mcs;
     S->d_part = (double *)S->dalloc((2 * part_stride + 1) * sizeof(double));
     if (!S->d_insts || !S->d_tile_inst || !S->d_ftile_inst || !S->d_comps || !S->d_part)
         return fail(h, FDTD_E_OOM, "device allocation failed");
@@ -1213,6 +1290,8 @@ static int upload_descriptors(fdtd_llg_t h)
     S->ntiles = (int)tile_inst.size();
     S->nftiles = (int)ftask.size();
     S->ncomp = (int)comps.size();
+    S->mag_cs = mcs;
+    S->mag_xs = mxs;
     S->vmax = vmax;
     S->stab = stab;
     S->mag_smem = msmem;
@@ -1286,7 +1365,9 @@ static LaunchSet launch_set(Sim *S)
     L.stab = S->stab;
     L.ctl = S->d_ctl;
     L.nslot_f = S->nftiles * kSW;
-    L.part_stride = L.nslot_f + S->ncomp;
+    L.part_stride = L.nslot_f + S->ncomp * S->mag_cs;
+    L.mag_cs = S->mag_cs;
+    L.mag_xs = S->mag_xs;
     L.part_f = S->d_part;
     L.part_m = S->d_part + L.nslot_f;
     L.ftask = S->d_ftile_inst;
@@ -1914,6 +1995,25 @@ extern "C" int fdtd_llg_load_state(fdtd_llg_t h, const void *buf, size_t size)
 }
 
 // ------------------------------------------------------------- profiling
+extern "C" int fdtd_llg_set_magnet_cluster(fdtd_llg_t h, int32_t ctas)
+{
+    if (!h || !h->sim || !h->owns) return fail(h, FDTD_E_INVAL, "set the magnet cluster on the handle, not a member");
+    if (ctas < 0 || ctas > kMagClusterMax)
+        return fail(h, FDTD_E_INVAL, "magnet CTAs per region must be 0 (automatic) to " + std::to_string(kMagClusterMax));
+    if (ctas != h->sim->mag_cluster) {
+        h->sim->mag_cluster = ctas;
+        h->sim->dirty = true;
+    }
+    return FDTD_OK;
+}
+
+extern "C" int fdtd_llg_get_magnet_cluster(fdtd_llg_t h, int32_t *ctas)
+{
+    if (!h || !h->sim || !ctas) return fail(h, FDTD_E_INVAL, "null handle or output");
+    *ctas = h->sim->dirty ? 0 : (h->sim->ncomp ? h->sim->mag_cs : 0);
+    return FDTD_OK;
+}
+
 extern "C" int fdtd_llg_set_graphs(fdtd_llg_t h, int32_t mode)
 {
     if (!h || !h->sim || !h->owns) return fail(h, FDTD_E_INVAL, "set graphs on the handle, not a member");
@@ -1989,7 +2089,7 @@ extern "C" int fdtd_llg_autotune(fdtd_llg_t h, int32_t trial_steps, int32_t *pla
     cudaEvent_t e0, e1;
     CKR(h, cudaEventCreate(&e0));
     CKR(h, cudaEventCreate(&e1));
-    int best = cand[0], best_w = w0;
+    int best = cand[0], best_w = w0, best_cs = 0;
     float best_ms = -1.f;
     // every plane count with the width of fewest padded cells, then the other
     // width with the same counts
@@ -2019,9 +2119,35 @@ extern "C" int fdtd_llg_autotune(fdtd_llg_t h, int32_t trial_steps, int32_t *pla
     }
     rc = fdtd_llg_set_tiling(h, best);
     if (!rc) rc = fdtd_llg_set_tile_width(h, best_w);
+    // with magnets and no split requested: the fewest magnet CTAs per region
+    // against the fast split, at the chosen tiling
+    if (!rc && S->ncomp && S->mag_cluster == 0 && S->mag_cs_need != S->mag_cs_fast) {
+        float t[2] = {0.f, 0.f};
+        const int opt[2] = {S->mag_cs_need, S->mag_cs_fast};
+        cudaEvent_t a0, a1;
+        CKR(h, cudaEventCreate(&a0));
+        CKR(h, cudaEventCreate(&a1));
+        for (int q = 0; q < 2 && !rc; ++q) {
+            rc = fdtd_llg_set_magnet_cluster(h, opt[q]);
+            if (!rc) rc = fdtd_llg_step(h, 1);
+            if (rc) break;
+            cudaEventRecord(a0, S->stream);
+            rc = fdtd_llg_step(h, trial_steps);
+            if (rc) break;
+            cudaEventRecord(a1, S->stream);
+            if (cudaEventSynchronize(a1) != cudaSuccess) { rc = fail(h, FDTD_E_CUDA, "autotune timing failed"); break; }
+            cudaEventElapsedTime(&t[q], a0, a1);
+        }
+        cudaEventDestroy(a0);
+        cudaEventDestroy(a1);
+        if (!rc) best_cs = t[1] < t[0] ? opt[1] : opt[0];
+        const int r2 = fdtd_llg_set_magnet_cluster(h, 0);
+        if (!rc) rc = r2;
+    }
     if (!rc) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[tune_key(S)] = {best, best_w};
+        g_tuned[tune_key(S)] = {best, best_w, best_cs};
+        S->dirty = true;   // the tuned magnet split takes effect at the next step
     }
     if (planes) *planes = best;
     return rc;
@@ -2111,6 +2237,12 @@ extern "C" int fdtd_llg_run_checkpointed(fdtd_llg_t h, int64_t nsteps, int32_t i
     if (rc) return rc;
     if (S->ncomp && S->cfg.llg_fixed_iter < 2)
         return fail(h, FDTD_E_INVAL, "with magnets the adjoint needs llg_fixed_iter >= 2 (a fixed LLG map)");
+    for (const MagComp &C : S->inst[0].comps) {   // the reverse magnet kernel holds a region in one CTA
+        int qx, py, ps;
+        if (C.V > kMagMaxV || !mag_stage_block(C.bx, C.by, C.bz, qx, py, ps))
+            return fail(h, FDTD_E_NOSYS, "the adjoint covers magnetic regions of at most " + std::to_string(kMagMaxV) +
+                                             " cells that fit one CTA");
+    }
     const long long K = interval > 0 ? interval : (long long)std::ceil(std::sqrt((double)nsteps));
     const long long nck = (nsteps + K - 1) / K;
     const size_t sf = state_floats(S->inst[0]);

@@ -66,13 +66,17 @@ constexpr int kStageBytes = kStageCOff + (kClsMaxBytes + 127) / 128 * 128;
 // Class tables of at most kTabMax entries are staged in shared memory.
 constexpr int kTabMax = 64;
 
-// Magnet kernel: one CTA per face-connected magnetic region, whose bounding
-// box holds at most kMagMaxV cells, kMagCPT cells per thread, and whose cells
-// and faces fit in one CTA's shared memory (mag_smem_bytes).
+// Magnet kernel: each face-connected magnetic region is split along its
+// longest axis into cs slabs (1 <= cs <= kMagClusterMax, one per CTA of a
+// thread-block cluster, the same cs for every region of a launch); a slab's
+// box holds at most kMagMaxV cells, kMagCPT cells per thread, and its cells,
+// faces and edges fit one CTA's shared memory (mag_cta_smem).
 constexpr int kMagThreads = 512;
 constexpr int kMagMaxV = 4096;
 constexpr int kMagCPT = kMagMaxV / kMagThreads;
 constexpr int kMagSmemMax = 226 * 1024;   // 227 KB per CTA less the static shared memory
+constexpr int kMagClusterMax = 8;         // portable cluster size
+constexpr int kMagCtaCells = 128;         // cells per CTA the automatic split aims at
 inline long long mag_faces(int bx, int by, int bz)
 {
     return (long long)(bx + 1) * by * bz + (long long)bx * (by + 1) * bz + (long long)bx * by * (bz + 1);
@@ -105,23 +109,47 @@ inline long long mag_smem_bytes(int bx, int by, int bz, int qx, int py, int ps)
     const long long e = mag_edges(bx, by, bz);
     return 4 * (3 * V + mag_faces(bx, by, bz) + (e > 3 * V ? e : 3 * V) + mag_stage_floats(bx, by, bz, qx, py, ps)) + V;
 }
+// Dynamic shared memory of a magnet CTA whose slab box is bx x by x bz, in a
+// launch whose exchange area holds xs floats per layer (0 without a cluster):
+// the exports [2 parities][2 layers][xs], the slab's arrays, and the halo
+// material bytes of the layers below and above the slab (hxs each, when split).
+inline long long mag_cta_smem(int bx, int by, int bz, int qx, int py, int ps, int xs, int hxs)
+{
+    return 16LL * xs + mag_smem_bytes(bx, by, bz, qx, py, ps) + 2LL * hxs;
+}
 // Block of the staged box (the box has (bx+1)(by+1)(bz+1) edge sites): whole
 // x rows and y columns with as many z planes as fit, else one plane and as
 // many rows as fit, else one row and as many sites as fit; false when not
-// even one site fits (the region is too large for one CTA).
-inline bool mag_stage_block(int bx, int by, int bz, int &qx, int &py, int &ps)
+// even one site fits (the slab is too large for one CTA).  xs, hxs: as in
+// mag_cta_smem.
+inline bool mag_stage_block(int bx, int by, int bz, int &qx, int &py, int &ps, int xs = 0, int hxs = 0)
 {
     qx = bx + 1;
     py = by + 1;
     for (ps = bz + 1; ps >= 1; --ps)
-        if (mag_smem_bytes(bx, by, bz, qx, py, ps) <= kMagSmemMax) return true;
+        if (mag_cta_smem(bx, by, bz, qx, py, ps, xs, hxs) <= kMagSmemMax) return true;
     ps = 1;
     for (py = by; py >= 1; --py)
-        if (mag_smem_bytes(bx, by, bz, qx, py, ps) <= kMagSmemMax) return true;
+        if (mag_cta_smem(bx, by, bz, qx, py, ps, xs, hxs) <= kMagSmemMax) return true;
     py = 1;
     for (qx = bx; qx >= 1; --qx)
-        if (mag_smem_bytes(bx, by, bz, qx, py, ps) <= kMagSmemMax) return true;
+        if (mag_cta_smem(bx, by, bz, qx, py, ps, xs, hxs) <= kMagSmemMax) return true;
     return false;
+}
+// The split axis of a region's box (its longest; z, then y, on ties), and the
+// box of the largest of its cs slabs.
+inline int mag_split_axis(int bx, int by, int bz) { return (bz >= by && bz >= bx) ? 2 : (by >= bx ? 1 : 0); }
+inline void mag_slab_box(int bx, int by, int bz, int cs, int &sx, int &sy, int &sz)
+{
+    const int a = mag_split_axis(bx, by, bz);
+    sx = bx; sy = by; sz = bz;
+    int &e = a == 0 ? sx : (a == 1 ? sy : sz);
+    e = (e + cs - 1) / cs;
+}
+inline int mag_cross_section(int bx, int by, int bz)
+{
+    const int a = mag_split_axis(bx, by, bz);
+    return a == 0 ? by * bz : (a == 1 ? bx * bz : bx * by);
 }
 
 #ifdef __CUDACC__
@@ -220,6 +248,7 @@ struct alignas(128) Inst {
 struct MagComp {
     int inst;
     int x0, y0, z0, bx, by, bz, V;
+    int ax;                 // split axis of the box (mag_split_axis)
     int qx, py, ps;         // edge sites per staged block in x, y, z (mag_stage_block)
     float *m;               // deviation M - Ms h in the bias frame: 3 blocks of V
     const uint8_t *mat;     // V: magnet material index, 0xFF outside this region
@@ -254,11 +283,14 @@ struct LaunchSet {
     int ntiles;
     const MagComp *comps;
     int ncomp;
-    int vmax;
+    int vmax;               // largest slab box of the launch (cells)
+    int mag_cs;             // magnet CTAs per region (cluster size)
+    int mag_xs;             // floats per exported layer (largest cross-section; 0 when mag_cs = 1)
     StepCtl *ctl;
     // energy partials of one step, two sets used by step parity: part_f[t *
-    // kSW + w] per sweep task t and warp w, then part_m[c] per magnet region
-    // (part_m = part_f + nslot_f); set p starts at part_f + p * part_stride
+    // kSW + w] per sweep task t and warp w, then part_m[c * mag_cs + r] per
+    // magnet CTA r of region c (part_m = part_f + nslot_f); set p starts at
+    // part_f + p * part_stride
     double *part_f, *part_m;
     int nslot_f, part_stride;
     // the flush's energy chunks: nred records {instance, chunk}, chunk sums

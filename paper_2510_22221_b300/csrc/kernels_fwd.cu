@@ -33,6 +33,10 @@
 // in a fixed order and advances the device step counter (no extra launch).
 #include "fdtd_llg_internal.h"
 
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
+
 namespace fl {
 
 namespace {
@@ -89,7 +93,7 @@ __device__ double source_value(const double *p, double t)
 // CTA forms every chunk (a reduction task inside the next step's sweep) or
 // one CTA each (the flush after the last step of a run).  Valid in thread 0.
 template <int B>
-__device__ double chunk_sum(const Inst *I, int c, int nch, const double *pf, const double *pm, double *sred)
+__device__ double chunk_sum(const Inst *I, int c, int nch, const double *pf, const double *pm, int mcs, double *sred)
 {
     const int tid = threadIdx.x, nth = blockDim.x;
     const int s0 = I->ftile_off * kSW, s1 = (I->ftile_off + I->fntask) * kSW;
@@ -111,7 +115,7 @@ __device__ double chunk_sum(const Inst *I, int c, int nch, const double *pf, con
         for (int u = 0; u < 8; ++u) s += v[u];
     }
     if (c == nch - 1)
-        for (int k = I->mag_off + tid; k < I->mag_off + I->nmag; k += nth) s += ld_cg(pm + k);
+        for (int k = I->mag_off * mcs + tid; k < (I->mag_off + I->nmag) * mcs; k += nth) s += ld_cg(pm + k);
     return block_sum(s, sred);
 }
 
@@ -136,7 +140,7 @@ __device__ void reduce_energy(const LaunchSet &L, int ii, long long m, double *s
     const double *pf = L.part_f + (m & 1) * L.part_stride, *pm = L.part_m + (m & 1) * L.part_stride;
     const int nch = energy_chunks(I->fntask);
     double t = 0.0;
-    for (int c = 0; c < nch; ++c) t += chunk_sum<B>(I, c, nch, pf, pm, sred);
+    for (int c = 0; c < nch; ++c) t += chunk_sum<B>(I, c, nch, pf, pm, L.mag_cs, sred);
     if (threadIdx.x == 0) store_energy(L, I, t, m);
 }
 
@@ -149,7 +153,7 @@ __device__ void finish_step(const LaunchSet &L, long long n, int *s_last)
     if (tid == 0) {
         __threadfence();
         const unsigned prev = atomicAdd(&L.ctl->counter, 1u);
-        *s_last = (prev == (unsigned)(L.nfblocks + L.ncomp) - 1u);
+        *s_last = (prev == (unsigned)(L.nfblocks + L.ncomp * L.mag_cs) - 1u);
     }
     __syncthreads();
     if (!*s_last) return;
@@ -281,44 +285,87 @@ __device__ __forceinline__ void sum2_add(float &s, float &c, float x)
 
 // FUSED: a full step (two half-pushes), H^{n+1/2} from buffer src, results to
 // buffer dst, curl of E^{n+1}.  Otherwise: the start-up half-push, in place on
-// buffer src, curl of the stored E.  The CTA first copies what it reads of
-// buffer src into shared memory with asynchronous copies (m, E at the box
-// edges, then per block of edge sites H and the class ids), so that the set-up
-// costs one memory round trip per block instead of one per dependent load,
-// and evaluates E^{n+1} at every box edge with the arithmetic of step_kernel.
-template <bool FUSED, typename ClsT, int CPT>
+// buffer src, curl of the stored E.
+//
+// A region is split along its longest axis A (C.ax) into L.mag_cs slabs, one
+// per CTA of a thread-block cluster (L.mag_cs = 1: one CTA, no cluster).  A
+// CTA holds the cells of its slab and every face and edge of the slab's box,
+// so the faces on a cut plane are evaluated by the CTAs on both sides, with
+// the same operands in the same order, and written by the one above the cut
+// (or, on the region's far face, by the last CTA).  What couples the slabs is
+// the A-component of the change of M of the layer beside a cut (a face normal
+// to A subtracts half the change of each adjacent cell; the cell means of H
+// read it the same way): after every Jacobi iterate each CTA exports that
+// component of its first and last layer into shared memory, double-buffered
+// by the iterate's parity, and reads its neighbours' exports through
+// distributed shared memory after one cluster barrier.  The residual test
+// takes the maximum over the cluster, so every CTA stops at the same iterate.
+// Each cell and face sees the same values in the same order as with one CTA:
+// fields, M and the adjoint tape (written in the region's own indexing) do
+// not depend on the split; only the energy partials are grouped per CTA.
+//
+// CL: the launch splits regions (L.mag_cs > 1); without it none of the
+// cluster code is compiled in and a CTA holds a whole region.
+//
+// Set-up of a CTA: it copies what it reads of buffer src into shared memory
+// with asynchronous copies (m, E at the slab box's edges, then per block of
+// edge sites H and the class ids), so that the set-up costs one memory round
+// trip per block instead of one per dependent load, and evaluates E^{n+1} at
+// every edge of the slab box with the arithmetic of step_kernel.
+template <bool FUSED, typename ClsT, int CPT, bool CL>
 __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
 {
     extern __shared__ float smem[];
     __shared__ float sredf[kMagThreads / 32];
     __shared__ double sredd[kMagThreads / 32];
     __shared__ MagMat smm[kMaxMagMat];
+    __shared__ float sres[2];   // this CTA's residual by iterate parity, read by the cluster
     __shared__ int s_last;
     // in a full step the field sweep, launched right behind this kernel on the
     // same stream, may start now: it writes only non-magnetic faces and E of
     // buffer dst and reads nothing this kernel writes
     if (FUSED) asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-    const MagComp C = L.comps[blockIdx.x];
+    const int cs = CL ? L.mag_cs : 1;
+    const int rank = CL ? (int)cg::this_cluster().block_rank() : 0;
+    const MagComp C = L.comps[blockIdx.x / cs];
     const Inst *I = L.insts + C.inst;
     const int tid = threadIdx.x, nth = blockDim.x;
-    const int V = C.V, bx = C.bx, by = C.by, bz = C.bz, bxy = bx * by;
+    // the region's box, the split axis A and this CTA's slab [a0, a1) along it
+    const int A = C.ax;
+    const int ext = A == 0 ? C.bx : (A == 1 ? C.by : C.bz);
+    const int a0 = rank * ext / cs, a1 = (rank + 1) * ext / cs;
+    const bool lo_cut = CL && a0 > 0, hi_cut = CL && a1 < ext, last = !CL || rank == cs - 1;
+    const int wo0 = A == 0 ? a0 : 0, wo1 = A == 1 ? a0 : 0, wo2 = A == 2 ? a0 : 0;   // slab origin in the region box
+    const int bx = A == 0 ? a1 - a0 : C.bx, by = A == 1 ? a1 - a0 : C.by, bz = A == 2 ? a1 - a0 : C.bz;
+    const int bA = a1 - a0, bxy = bx * by;
+    const int V = bx * by * bz;
+    const int RBx = C.bx, RBy = C.by, RV = C.V;
+    const int gx0 = C.x0 + wo0, gy0 = C.y0 + wo1, gz0 = C.z0 + wo2;            // slab origin in the grid
     const int nfx = (bx + 1) * by * bz, nfy = bx * (by + 1) * bz, nfz = bx * by * (bz + 1);
     const int nf = nfx + nfy + nfz;
     const int ex = bx + 1, exy = (bx + 1) * (by + 1), ne = exy * (bz + 1);
+    // the region's own face and edge numbering (tape layout)
+    const int RnfX = (RBx + 1) * RBy * C.bz, RnfY = RBx * (RBy + 1) * C.bz;
+    const int Rnf = RnfX + RnfY + RBx * RBy * (C.bz + 1);
+    const int Rne = (RBx + 1) * (RBy + 1) * (C.bz + 1);
+    // cross-section of the region normal to A (the slab's other two extents)
+    const int XS = A == 0 ? by * bz : (A == 1 ? bx * bz : bx * by);
     const BoxDiv BD(bx, by);
-    float *sM = smem;            // m (bias frame), 3 blocks of V
-    float *sH = sM + 3 * V;      // face H: H^s of the half-push, then its result
-    float *sE = sH + nf;         // E at the box edges, 3 blocks of ne (until the faces are set up)
-    float *sD = sE;              // then M^{r} - M^{n} of the current iterate (global axes), 3 blocks of V
+    float *sX = smem;                    // exports [parity][low layer, high layer][L.mag_xs]: one offset in every CTA
+    float *sM = smem + 4 * L.mag_xs;     // m (bias frame), 3 blocks of V
+    float *sH = sM + 3 * V;              // face H: H^s of the half-push, then its result
+    float *sE = sH + nf;                 // E at the box edges, 3 blocks of ne (until the faces are set up)
+    float *sD = sE;                      // then M^{r} - M^{n} of the current iterate (global axes), 3 blocks of V
     // stage of one block of at most qx x py x ps edge sites: H of buffer src
     // on the block grown by one cell on its low sides, then the class id of
     // each site; once the edges and faces are set up the area holds sC
     const int sst = (C.qx + 1) * (C.py + 1) * (C.ps + 1);
     float *sS = sE + (3 * ne > 3 * V ? 3 * ne : 3 * V);
-    float *sC = sS;              // (dt/2mu0) curl E at the face
+    float *sC = sS;                      // (dt/2mu0) curl E at the face
     uint16_t *scl = reinterpret_cast<uint16_t *>(sS + 3 * sst);
     const int narea = max(nf, 3 * sst + (C.qx * C.py * C.ps + 1) / 2);
     uint8_t *smat = reinterpret_cast<uint8_t *>(sS + narea);
+    uint8_t *shalo = smat + V;           // magnet material of the layer below the slab, then of the layer above (XS each)
     const long long n = *(volatile long long *)&L.ctl->step;
     const float ch = I->ch, h0n = I->h0n;
     float *Fs = I->F[L.src][0];
@@ -329,13 +376,59 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
 #pragma unroll
     for (int q = 0; q < 9; ++q) R[q] = I->R[q];
 
-    // m, the material ids and E^n at every box edge: one batch of
-    // asynchronous copies (edges beyond the far walls are zero)
+    // slab-local cell (li, lj, lk) -> the region's cell index; the position of
+    // a cell (or of a face normal to A) in the cross-section normal to A
+    auto rcell = [&](int li, int lj, int lk) { return ((lk + wo2) * RBy + lj + wo1) * RBx + li + wo0; };
+    // the region's index of slab cell v (the same index without a split)
+    auto rcell_v = [&](int v) {
+        if constexpr (!CL) return v;
+        int li, lj, lk;
+        cell_decode(v, BD, li, lj, lk);
+        return rcell(li, lj, lk);
+    };
+    auto xsec = [&](int li, int lj, int lk) { return A == 0 ? lk * by + lj : (A == 1 ? lk * bx + li : lj * bx + li); };
+    auto acoord = [&](int li, int lj, int lk) { return A == 0 ? li : (A == 1 ? lj : lk); };
+    // whether the cells below (inl) and above (inr) face f belong to the
+    // region, the cells beyond a cut read from the staged halo layers
+    auto sides = [&](int a, int fi, int fj, int fk, int vl, int vr, bool &inl, bool &inr) {
+        if constexpr (CL) {
+            inl = vl >= 0 ? smat[vl] != 0xFF : (a == A && lo_cut && shalo[xsec(fi, fj, fk)] != 0xFF);
+            inr = vr >= 0 ? smat[vr] != 0xFF : (a == A && hi_cut && shalo[XS + xsec(fi, fj, fk)] != 0xFF);
+        } else {
+            inl = vl >= 0 && smat[vl] != 0xFF;
+            inr = vr >= 0 && smat[vr] != 0xFF;
+        }
+    };
+    // faces written (and counted in the energy) by this CTA
+    auto owned = [&](int a, int fi, int fj, int fk) { return !CL || a != A || acoord(fi, fj, fk) < bA || last; };
+    auto rface = [&](int a, int fi, int fj, int fk) {
+        const int i = fi + wo0, j = fj + wo1, k = fk + wo2;
+        if (a == 0) return (k * RBy + j) * (RBx + 1) + i;
+        if (a == 1) return RnfX + (k * (RBy + 1) + j) * RBx + i;
+        return RnfX + RnfY + (k * RBy + j) * RBx + i;
+    };
+
+    // m, the material ids (with the halo layers) and E^n at every box edge:
+    // one batch of asynchronous copies (edges beyond the far walls are zero)
     for (int v = tid; v < V; v += nth) {
-        smat[v] = C.mat[v];
-        cp_async4(sM + v, C.m + v);
-        cp_async4(sM + V + v, C.m + V + v);
-        cp_async4(sM + 2 * V + v, C.m + 2 * V + v);
+        const int rv = rcell_v(v);
+        smat[v] = C.mat[rv];
+        cp_async4(sM + v, C.m + rv);
+        cp_async4(sM + V + v, C.m + RV + rv);
+        cp_async4(sM + 2 * V + v, C.m + 2 * RV + rv);
+    }
+    for (int t = tid; t < (CL ? 2 * XS : 0); t += nth) {
+        const int side = t >= XS, q = t - side * XS;
+        const int la = side ? bA : -1;   // slab-local A coordinate of the halo layer
+        uint8_t mv = 0xFF;
+        if (side ? hi_cut : lo_cut) {
+            int li, lj, lk;
+            if (A == 0) { li = la; lj = q % by; lk = q / by; }
+            else if (A == 1) { lj = la; li = q % bx; lk = q / bx; }
+            else { lk = la; li = q % bx; lj = q / bx; }
+            mv = C.mat[rcell(li, lj, lk)];
+        }
+        shalo[t] = mv;
     }
     if (tid < kMaxMagMat) smm[tid] = I->mm[tid];
     {
@@ -343,7 +436,7 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
         for (int e = tid; e < 3 * ne; e += nth) {
             const int comp = e >= 2 * ne ? 2 : (e >= ne ? 1 : 0), r = e - comp * ne;
             const unsigned q1 = dex.div(r), q2 = dey.div(q1);
-            const int i = C.x0 + r - (int)(q1 * ex), j = C.y0 + (int)(q1 - q2 * (by + 1)), k = C.z0 + (int)q2;
+            const int i = gx0 + r - (int)(q1 * ex), j = gy0 + (int)(q1 - q2 * (by + 1)), k = gz0 + (int)q2;
             if (i < nx && j < ny && k < nz) cp_async4(sE + e, Fs + comp * fs + k * plane + (long long)j * px + i);
             else sE[e] = 0.f;
         }
@@ -364,7 +457,7 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
         for (int q = tid; q < 3 * nsc; q += nth) {
             const int c = q >= 2 * nsc ? 2 : (q >= nsc ? 1 : 0), r = q - c * nsc;
             const unsigned kk = dsxy.div(r), r2 = r - kk * SXY, jj = dsx.div(r2), ii = r2 - jj * SX;
-            const float *src = h_src(I, Fs, c, C.x0 + xa - 1 + (int)ii, C.y0 + ya - 1 + (int)jj, C.z0 + za - 1 + (int)kk);
+            const float *src = h_src(I, Fs, c, gx0 + xa - 1 + (int)ii, gy0 + ya - 1 + (int)jj, gz0 + za - 1 + (int)kk);
             float *dst = sS + c * sst + r;
             if (src) cp_async4(dst, src);
             else *dst = 0.f;
@@ -372,13 +465,13 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
         if (FUSED) {
             for (int q = tid; q < nsite; q += nth) {
                 const unsigned q1 = dbx.div(q), q2 = dby.div(q1);
-                const int i = C.x0 + xa + q - (int)(q1 * nbx), j = C.y0 + ya + (int)(q1 - q2 * nby), k = C.z0 + za + (int)q2;
+                const int i = gx0 + xa + q - (int)(q1 * nbx), j = gy0 + ya + (int)(q1 - q2 * nby), k = gz0 + za + (int)q2;
                 scl[q] = (i < nx && j < ny && k < nz) ? (uint16_t) static_cast<const ClsT *>(I->cls)[k * plane + (long long)j * px + i] : 0;
             }
         }
         cp_async_wait_all();
         __syncthreads();
-        // stage value of H component c at box-local cell (li, lj, lk), each
+        // stage value of H component c at slab-local cell (li, lj, lk), each
         // index at most one below the block
         auto hs = [&](int c, int li, int lj, int lk) {
             return sS[c * sst + (lk - za + 1) * SXY + (lj - ya + 1) * SX + li - xa + 1];
@@ -388,7 +481,7 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
                 const int comp = q >= 2 * nsite ? 2 : (q >= nsite ? 1 : 0), r = q - comp * nsite;
                 const unsigned q1 = dbx.div(r), q2 = dby.div(q1);
                 const int li = xa + r - (int)(q1 * nbx), lj = ya + (int)(q1 - q2 * nby), lk = za + (int)q2;
-                const int i = C.x0 + li, j = C.y0 + lj, k = C.z0 + lk;
+                const int i = gx0 + li, j = gy0 + lj, k = gz0 + lk;
                 if (i >= nx || j >= ny || k >= nz) continue;
                 float cu;
                 if (comp == 0)
@@ -401,9 +494,9 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
                     if (I->src[so][0] == comp && I->src[so][1] == i && I->src[so][2] == j && I->src[so][3] == k)
                         cu = __fsub_rn(cu, (float)source_value(I->srcp[so], ((double)n + 0.5) * I->dt));
                 const int c = scl[r];
-                const float4 A = __ldg(I->ctab + 3 * c), B = __ldg(I->ctab + 3 * c + 1);
-                const float ca = comp == 0 ? A.x : (comp == 1 ? A.y : A.z);
-                const float cb = comp == 0 ? B.x : (comp == 1 ? B.y : B.z);
+                const float4 Ac = __ldg(I->ctab + 3 * c), Bc = __ldg(I->ctab + 3 * c + 1);
+                const float ca = comp == 0 ? Ac.x : (comp == 1 ? Ac.y : Ac.z);
+                const float cb = comp == 0 ? Bc.x : (comp == 1 ? Bc.y : Bc.z);
                 const int e = comp * ne + (lk * (by + 1) + lj) * ex + li;
                 sE[e] = e_next(ca, sE[e], cb, cu);
             }
@@ -412,20 +505,22 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
             int a, fi, fj, fk, vl, vr;
             face_decode(f, BD, bx, by, bz, a, fi, fj, fk, vl, vr);
             if (fi < xa || fi >= xb || fj < ya || fj >= yb || fk < za || fk >= zb) continue;
-            const bool own = (vl >= 0 && smat[vl] != 0xFF) || (vr >= 0 && smat[vr] != 0xFF);
-            sH[f] = own ? hs(a, fi, fj, fk) : 0.f;
+            bool inl, inr;
+            sides(a, fi, fj, fk, vl, vr, inl, inr);
+            sH[f] = (inl || inr) ? hs(a, fi, fj, fk) : 0.f;
         }
     }
     __syncthreads();
-    // (dt/2mu0) curl E at every face of the region
+    // (dt/2mu0) curl E at every face of the slab box
     {
         const float *Ex = sE, *Ey = Ex + ne, *Ez = Ey + ne;
         for (int f = tid; f < nf; f += nth) {
             int a, fi, fj, fk, vl, vr;
             face_decode(f, BD, bx, by, bz, a, fi, fj, fk, vl, vr);
-            const bool own = (vl >= 0 && smat[vl] != 0xFF) || (vr >= 0 && smat[vr] != 0xFF);
+            bool inl, inr;
+            sides(a, fi, fj, fk, vl, vr, inl, inr);
             float c = 0.f;
-            if (own) {
+            if (inl || inr) {
                 const int e0 = fk * exy + fj * ex + fi;
                 float cu;
                 if (a == 0) cu = curl2(Ez[e0 + ex], Ez[e0], I->idy, Ey[e0 + exy], Ey[e0], I->idz);
@@ -437,7 +532,8 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
         }
     }
     __syncthreads();
-    // adjoint recording (mag_tape_floats): this step's tape slot, else NULL
+    // adjoint recording (mag_tape_floats, the region's indexing): this step's
+    // tape slot, else NULL; each CTA writes its own cells, faces and edges
     float *T = nullptr;
     if (FUSED && L.rec && C.tape) {
         if (n < L.rec_n0 || n - L.rec_n0 >= L.rec_slots || L.llg_fixed_iter < 1) {
@@ -448,11 +544,34 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
     }
     const int RI = L.llg_fixed_iter;
     if (T) {   // m and face H at the start of the step, E^{n+1} at the box edges
-        for (int v = tid; v < 3 * V; v += nth) T[v] = sM[v];
-        for (int f = tid; f < nf; f += nth) T[3 * V + f] = sH[f];
-        for (int e = tid; e < 3 * ne; e += nth) T[3 * V + nf + e] = sE[e];
+        for (int v = tid; v < V; v += nth) {
+            const int rv = rcell_v(v);
+            for (int d = 0; d < 3; ++d) T[d * RV + rv] = sM[d * V + v];
+        }
+        for (int f = tid; f < nf; f += nth) {
+            int a, fi, fj, fk, vl, vr;
+            face_decode(f, BD, bx, by, bz, a, fi, fj, fk, vl, vr);
+            if (owned(a, fi, fj, fk)) T[3 * RV + rface(a, fi, fj, fk)] = sH[f];
+        }
+        const UDiv dex(ex), dey(by + 1);
+        for (int e = tid; e < 3 * ne; e += nth) {
+            const int comp = e >= 2 * ne ? 2 : (e >= ne ? 1 : 0), r = e - comp * ne;
+            const unsigned q1 = dex.div(r), q2 = dey.div(q1);
+            const int li = r - (int)(q1 * ex), lj = (int)(q1 - q2 * (by + 1)), lk = (int)q2;
+            if (acoord(li, lj, lk) < bA || last)
+                T[3 * RV + Rnf + comp * Rne + ((lk + wo2) * (RBy + 1) + lj + wo1) * (RBx + 1) + li + wo0] = sE[e];
+        }
     }
     __syncthreads();   // sE becomes sD
+
+    // the exports of the CTA below (its high layer) and above (its low layer)
+    // in parity 0; parity p is 2 p L.mag_xs floats further
+    const float *pxl = nullptr, *pxh = nullptr;
+    if constexpr (CL) {
+        cg::cluster_group cl = cg::this_cluster();
+        if (lo_cut) pxl = cl.map_shared_rank(sX + L.mag_xs, rank - 1);
+        if (hi_cut) pxh = cl.map_shared_rank(sX, rank + 1);
+    }
 
     double eacc = 0.0;
     const int nhalf = FUSED ? 2 : 1;
@@ -468,6 +587,9 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
             ++r;
             float res = 0.f;
             float dn[CPT][3];
+            // the neighbours' exports of the previous iterate (none in the first: the change starts at zero)
+            const int po = 2 * ((r - 1) & 1) * L.mag_xs;
+            const float *nl = (r > 1 && pxl) ? pxl + po : nullptr, *nh = (r > 1 && pxh) ? pxh + po : nullptr;
 #pragma unroll
             for (int q = 0; q < CPT; ++q) {
                 dn[q][0] = dn[q][1] = dn[q][2] = 0.f;
@@ -486,9 +608,16 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
                 const float ay_ = 0.5f * ((hy0 - sC[fy0]) + (hy1 - sC[fy0 + bx]));
                 const float az_ = 0.5f * ((hz0 - sC[fz0]) + (hz1 - sC[fz0 + bxy]));
                 const float d0 = sD[v], d1 = sD[V + v], d2 = sD[2 * V + v];
-                const float dxm = li > 0 ? sD[v - 1] : 0.f, dxp = li < bx - 1 ? sD[v + 1] : 0.f;
-                const float dym = lj > 0 ? sD[V + v - bx] : 0.f, dyp = lj < by - 1 ? sD[V + v + bx] : 0.f;
-                const float dzm = lk > 0 ? sD[2 * V + v - bxy] : 0.f, dzp = lk < bz - 1 ? sD[2 * V + v + bxy] : 0.f;
+                float dxm = li > 0 ? sD[v - 1] : 0.f, dxp = li < bx - 1 ? sD[v + 1] : 0.f;
+                float dym = lj > 0 ? sD[V + v - bx] : 0.f, dyp = lj < by - 1 ? sD[V + v + bx] : 0.f;
+                float dzm = lk > 0 ? sD[2 * V + v - bxy] : 0.f, dzp = lk < bz - 1 ? sD[2 * V + v + bxy] : 0.f;
+                if (CL && (nl || nh)) {   // neighbours across a cut: the other CTA's export
+                    const int la = acoord(li, lj, lk), xq = xsec(li, lj, lk);
+                    const float lo = (nl && la == 0) ? nl[xq] : 0.f, hi = (nh && la == bA - 1) ? nh[xq] : 0.f;
+                    if (A == 0) { if (nl && la == 0) dxm = lo; if (nh && la == bA - 1) dxp = hi; }
+                    else if (A == 1) { if (nl && la == 0) dym = lo; if (nh && la == bA - 1) dyp = hi; }
+                    else { if (nl && la == 0) dzm = lo; if (nh && la == bA - 1) dzp = hi; }
+                }
                 float hex, hey, hez;   // H_eff^{r-1} in the bias frame
                 to_frame(R, ax_ - 0.25f * (dxm + 2.f * d0 + dxp), ay_ - 0.25f * (dym + 2.f * d1 + dyp),
                          az_ - 0.25f * (dzm + 2.f * d2 + dzp), hex, hey, hez);
@@ -541,14 +670,38 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
                     sD[V + v] = dn[q][1];
                     sD[2 * V + v] = dn[q][2];
                 }
-                if (T && v < V && r <= RI) {   // iterate r of half-push hp (zero outside the region)
-                    float *TD = T + 3 * V + nf + 3 * ne + (long long)((hp * RI + r - 1) * 3) * V;
-                    TD[v] = dn[q][0];
-                    TD[V + v] = dn[q][1];
-                    TD[2 * V + v] = dn[q][2];
+            }
+            if (T && r <= RI) {   // iterate r of half-push hp (zero outside the region); this thread's own cells
+                float *TD = T + 3 * RV + Rnf + 3 * Rne + (long long)((hp * RI + r - 1) * 3) * RV;
+                for (int v = tid; v < V; v += nth) {
+                    const int rv = rcell_v(v);
+                    TD[rv] = sD[v];
+                    TD[RV + rv] = sD[V + v];
+                    TD[2 * RV + rv] = sD[2 * V + v];
                 }
             }
-            res = block_max(res, sredf);
+            res = block_max(res, sredf);   // also orders every sD write before the exports below
+            if constexpr (CL) {
+                // the A-component of the change of M on the first and last
+                // layer (zero outside the region) for the CTAs beside this one
+                float *xw = sX + 2 * (r & 1) * L.mag_xs;
+                const float *dA = sD + A * V;
+                const int st = A == 0 ? 1 : (A == 1 ? bx : bxy), last_off = (bA - 1) * st;
+                for (int t = tid; t < XS; t += nth) {
+                    const int p = t % (A == 0 ? by : bx), q = t / (A == 0 ? by : bx);
+                    // cell of cross-section t on layer 0: A = x: (0, p, q); y: (p, 0, q); z: (p, q, 0)
+                    const int v0 = A == 0 ? (q * by + p) * bx : (A == 1 ? q * bxy + p : q * bx + p);
+                    xw[t] = dA[v0];
+                    xw[L.mag_xs + t] = dA[v0 + last_off];
+                }
+                // every CTA's iterate is complete and exported; then the
+                // residual is the cluster's maximum
+                if (tid == 0) sres[r & 1] = res;
+                cg::cluster_group cl = cg::this_cluster();
+                cl.sync();   // every CTA's iterate is complete and exported
+                if (L.llg_fixed_iter <= 0)
+                    for (int q = 0; q < cs; ++q) res = fmaxf(res, *cl.map_shared_rank(&sres[r & 1], q));
+            }
             if (L.llg_fixed_iter > 0) {
                 if (r >= L.llg_fixed_iter) break;
             } else {
@@ -562,18 +715,22 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
             }
         }
 
-        // faces: H = H^s - (dt/2mu0) curl E - (dM_low + dM_high)/2
+        // faces: H = H^s - (dt/2mu0) curl E - (dM_low + dM_high)/2, the cells
+        // beyond a cut from the other CTA's last export
+        const float *fl = pxl ? pxl + 2 * (r & 1) * L.mag_xs : nullptr, *fh = pxh ? pxh + 2 * (r & 1) * L.mag_xs : nullptr;
         const bool rec = FUSED && hp == 0;
         float es = 0.f, ec = 0.f;   // face energy of this thread, compensated
         for (int f = tid; f < nf; f += nth) {
             int a, fi, fj, fk, vl, vr;
             face_decode(f, BD, bx, by, bz, a, fi, fj, fk, vl, vr);
-            const bool inl = vl >= 0 && smat[vl] != 0xFF, inr = vr >= 0 && smat[vr] != 0xFF;
+            bool inl, inr;
+            sides(a, fi, fj, fk, vl, vr, inl, inr);
             if (!inl && !inr) continue;
-            const float dlv = inl ? sD[a * V + vl] : 0.f, drv = inr ? sD[a * V + vr] : 0.f;
+            const float dlv = inl ? (vl >= 0 ? sD[a * V + vl] : fl[xsec(fi, fj, fk)]) : 0.f;
+            const float drv = inr ? (vr >= 0 ? sD[a * V + vr] : fh[xsec(fi, fj, fk)]) : 0.f;
             const float h = (sH[f] - sC[f]) - 0.5f * (dlv + drv);
             sH[f] = h;
-            if (rec) sum2_add(es, ec, h * h);
+            if (rec && owned(a, fi, fj, fk)) sum2_add(es, ec, h * h);
         }
         if (rec) eacc += (double)es + (double)ec;
 #pragma unroll
@@ -587,9 +744,16 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
         }
         __syncthreads();
         if (T && hp == 0) {   // face H and m after the first half-push
-            float *TH = T + 3 * V + nf + 3 * ne + 6LL * RI * V;
-            for (int f = tid; f < nf; f += nth) TH[f] = sH[f];
-            for (int v = tid; v < 3 * V; v += nth) TH[nf + v] = sM[v];
+            float *TH = T + 3 * RV + Rnf + 3 * Rne + 6LL * RI * RV;
+            for (int f = tid; f < nf; f += nth) {
+                int a, fi, fj, fk, vl, vr;
+                face_decode(f, BD, bx, by, bz, a, fi, fj, fk, vl, vr);
+                if (owned(a, fi, fj, fk)) TH[rface(a, fi, fj, fk)] = sH[f];
+            }
+            for (int v = tid; v < V; v += nth) {
+                const int rv = rcell_v(v);
+                for (int d = 0; d < 3; ++d) TH[Rnf + d * RV + rv] = sM[d * V + v];
+            }
         }
         if (rec) {
             eacc *= 0.5 * kMu0;
@@ -602,22 +766,35 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
                 z += (qx * qx + qy * qy + qz * qz) * smm[m].inv_Ms;
             }
             eacc += (double)z * (0.5 * kMu0 * (double)h0n);
-            // probe samples of magnetic faces and of M at step n+1
+            // probe samples of the magnetic faces and cells this CTA owns, at step n+1
             for (int p = tid; p < I->nprobe; p += nth) {
-                const int pi = I->probe[p][0] - C.x0, pj = I->probe[p][1] - C.y0, pk = I->probe[p][2] - C.z0;
+                const int pi = I->probe[p][0] - gx0, pj = I->probe[p][1] - gy0, pk = I->probe[p][2] - gz0;
                 if (pi < 0 || pj < 0 || pk < 0 || pi > bx || pj > by || pk > bz) continue;
                 double *row = I->probe_buf + ((long long)(n % I->cap) * I->nprobe + p) * 9;
-                if (pj < by && pk < bz) {
-                    const bool l = pi > 0 && smat[(pk * by + pj) * bx + pi - 1] != 0xFF;
-                    if (l || (pi < bx && smat[(pk * by + pj) * bx + pi] != 0xFF)) row[3] = sH[(pk * by + pj) * (bx + 1) + pi];
-                }
-                if (pi < bx && pk < bz) {
-                    const bool l = pj > 0 && smat[(pk * by + pj - 1) * bx + pi] != 0xFF;
-                    if (l || (pj < by && smat[(pk * by + pj) * bx + pi] != 0xFF)) row[4] = sH[nfx + (pk * (by + 1) + pj) * bx + pi];
-                }
-                if (pi < bx && pj < by) {
-                    const bool l = pk > 0 && smat[((pk - 1) * by + pj) * bx + pi] != 0xFF;
-                    if (l || (pk < bz && smat[(pk * by + pj) * bx + pi] != 0xFF)) row[5] = sH[nfx + nfy + (pk * by + pj) * bx + pi];
+                // the face of axis a at the probe cell's low side, if it is a magnetic face of this CTA
+                auto face_at = [&](int a) -> int {
+                    if ((a != 0 && pi >= bx) || (a != 1 && pj >= by) || (a != 2 && pk >= bz)) return -1;
+                    int f, vl = -1, vr = -1;
+                    if (a == 0) {
+                        f = (pk * by + pj) * (bx + 1) + pi;
+                        if (pi > 0) vl = (pk * by + pj) * bx + pi - 1;
+                        if (pi < bx) vr = (pk * by + pj) * bx + pi;
+                    } else if (a == 1) {
+                        f = nfx + (pk * (by + 1) + pj) * bx + pi;
+                        if (pj > 0) vl = (pk * by + pj - 1) * bx + pi;
+                        if (pj < by) vr = (pk * by + pj) * bx + pi;
+                    } else {
+                        f = nfx + nfy + (pk * by + pj) * bx + pi;
+                        if (pk > 0) vl = ((pk - 1) * by + pj) * bx + pi;
+                        if (pk < bz) vr = (pk * by + pj) * bx + pi;
+                    }
+                    bool inl, inr;
+                    sides(a, pi, pj, pk, vl, vr, inl, inr);
+                    return ((inl || inr) && owned(a, pi, pj, pk)) ? f : -1;
+                };
+                for (int a = 0; a < 3; ++a) {
+                    const int f = face_at(a);
+                    if (f >= 0) row[3 + a] = sH[f];
                 }
                 if (pi < bx && pj < by && pk < bz) {
                     const int vc = (pk * by + pj) * bx + pi;
@@ -632,22 +809,28 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
                 }
             }
         }
-        __syncthreads();
+        // the other CTAs have read this half-push's exports before the next
+        // one writes them (and before any CTA of the cluster exits)
+        if constexpr (CL) cg::this_cluster().sync();
+        else __syncthreads();
     }
-    // results: the magnetic faces of the output buffer (and far-wall arrays), m
+    // results: the magnetic faces this CTA owns in the output buffer (and the
+    // far-wall arrays), m of its cells
     for (int f = tid; f < nf; f += nth) {
         int a, fi, fj, fk, vl, vr;
         face_decode(f, BD, bx, by, bz, a, fi, fj, fk, vl, vr);
-        const bool own = (vl >= 0 && smat[vl] != 0xFF) || (vr >= 0 && smat[vr] != 0xFF);
-        if (!own) continue;
-        const int i = C.x0 + fi, j = C.y0 + fj, k = C.z0 + fk;
+        bool inl, inr;
+        sides(a, fi, fj, fk, vl, vr, inl, inr);
+        if (!(inl || inr) || !owned(a, fi, fj, fk)) continue;
+        const int i = gx0 + fi, j = gy0 + fj, k = gz0 + fk;
         float *out = a == 0 ? hx_ptr(I, Fd, i, j, k) : (a == 1 ? hy_ptr(I, Fd, i, j, k) : hz_ptr(I, Fd, i, j, k));
         *out = sH[f];
     }
     for (int v = tid; v < V; v += nth) {
-        C.m[v] = sM[v];
-        C.m[V + v] = sM[V + v];
-        C.m[2 * V + v] = sM[2 * V + v];
+        const int rv = rcell_v(v);
+        C.m[rv] = sM[v];
+        C.m[RV + rv] = sM[V + v];
+        C.m[2 * RV + rv] = sM[2 * V + v];
     }
     if (FUSED) {
         const double s = block_sum(eacc, sredd);
@@ -1133,7 +1316,7 @@ __global__ void __launch_bounds__(kST) energy_flush_kernel(LaunchSet L, const Ho
     if (m >= 0) {
         const double *pf = L.part_f + (m & 1) * L.part_stride, *pm = L.part_m + (m & 1) * L.part_stride;
         const int nch = energy_chunks(I->fntask);
-        const double sc = chunk_sum<32>(I, c, nch, pf, pm, sred);
+        const double sc = chunk_sum<32>(I, c, nch, pf, pm, L.mag_cs, sred);
         if (tid == 0) {
             int done = 0;
             L.esum[ii * kEChunks + c] = sc;
@@ -1202,17 +1385,33 @@ static StepFn step_fn(bool cls16, bool stab, int sx)
 // The magnet kernel with c cells per thread (1, 2, 4 or kMagCPT): the fewest
 // that cover the largest region of the launch, so that the per-thread
 // arrays and the unrolled cell loop hold no cells that cannot exist.
-template <bool FUSED, typename ClsT>
-static void (*mag_fn(int c))(LaunchSet)
+template <bool FUSED, typename ClsT, bool CL>
+static void (*mag_fn_cl(int c))(LaunchSet)
 {
     static_assert(kMagCPT == 8, "cells per thread: 1, 2, 4 or 8");
-    if (c <= 1) return mag_kernel<FUSED, ClsT, 1>;
-    if (c <= 2) return mag_kernel<FUSED, ClsT, 2>;
-    if (c <= 4) return mag_kernel<FUSED, ClsT, 4>;
-    return mag_kernel<FUSED, ClsT, 8>;
+    if (c <= 1) return mag_kernel<FUSED, ClsT, 1, CL>;
+    if (c <= 2) return mag_kernel<FUSED, ClsT, 2, CL>;
+    if (c <= 4) return mag_kernel<FUSED, ClsT, 4, CL>;
+    return mag_kernel<FUSED, ClsT, 8, CL>;
+}
+// the instantiation for c cells per thread, split over a cluster or not
+template <bool FUSED, typename ClsT>
+static void (*mag_fn(int c, bool cl))(LaunchSet)
+{
+    return cl ? mag_fn_cl<FUSED, ClsT, true>(c) : mag_fn_cl<FUSED, ClsT, false>(c);
 }
 
 static int mag_cpt(int vmax) { return vmax <= kMagThreads ? 1 : vmax <= 2 * kMagThreads ? 2 : vmax <= 4 * kMagThreads ? 4 : 8; }
+// Threads of a magnet CTA: one per cell of the launch's largest slab when it
+// holds at most kMagThreads cells (rounded up to a power of two, at least
+// 128), so that small slabs leave the SM's registers to the field sweep
+// running beside them; kMagThreads otherwise.
+static int mag_threads(int vmax)
+{
+    int t = 128;
+    while (t < vmax && t < kMagThreads) t *= 2;
+    return t;
+}
 
 static cudaError_t step_attrs()
 {
@@ -1222,13 +1421,14 @@ static cudaError_t step_attrs()
     for (int q = 0; q < 8 && e == cudaSuccess; ++q)
         e = cudaFuncSetAttribute(step_fn(q & 1, (q >> 1) & 1, (q & 4) ? 32 : 64), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kStepSmem);
-    for (int c = 1; c <= kMagCPT && e == cudaSuccess; c *= 2) {
-        e = cudaFuncSetAttribute(mag_fn<true, uint8_t>(c), cudaFuncAttributeMaxDynamicSharedMemorySize, kMagSmemMax);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(mag_fn<true, uint16_t>(c), cudaFuncAttributeMaxDynamicSharedMemorySize, kMagSmemMax);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(mag_fn<false, uint8_t>(c), cudaFuncAttributeMaxDynamicSharedMemorySize, kMagSmemMax);
-    }
+    for (int c = 1; c <= kMagCPT && e == cudaSuccess; c *= 2)
+        for (int cl = 0; cl < 2 && e == cudaSuccess; ++cl) {
+            e = cudaFuncSetAttribute(mag_fn<true, uint8_t>(c, cl), cudaFuncAttributeMaxDynamicSharedMemorySize, kMagSmemMax);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(mag_fn<true, uint16_t>(c, cl), cudaFuncAttributeMaxDynamicSharedMemorySize, kMagSmemMax);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(mag_fn<false, uint8_t>(c, cl), cudaFuncAttributeMaxDynamicSharedMemorySize, kMagSmemMax);
+        }
     done = e == cudaSuccess;
     return e;
 }
@@ -1241,12 +1441,31 @@ int step_blocks_per_sm(bool cls16, bool stab, int sx)
     return nb;
 }
 
+// The magnet kernel fn over every region, L.mag_cs CTAs (one cluster) each.
+static cudaError_t launch_mag(void (*fn)(LaunchSet), const LaunchSet &L, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(L.ncomp * L.mag_cs);
+    cfg.blockDim = dim3(mag_threads(L.vmax));
+    cfg.dynamicSmemBytes = L.mag_smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = L.mag_cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = L.mag_cs > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, fn, L);
+}
+
 cudaError_t launch_half(const LaunchSet &L, cudaStream_t s)
 {
     cudaError_t e = step_attrs();
     if (e != cudaSuccess) return e;
     if (L.ncomp) {
-        mag_fn<false, uint8_t>(mag_cpt(L.vmax))<<<L.ncomp, kMagThreads, L.mag_smem, s>>>(L);
+        e = launch_mag(mag_fn<false, uint8_t>(mag_cpt(L.vmax), L.mag_cs > 1), L, s);
+        if (e != cudaSuccess) return e;
     }
     const dim3 blk(kTX, kTY);
     if (L.cls16) h_half_kernel<uint16_t><<<L.grid_h, blk, 0, s>>>(L);
@@ -1273,8 +1492,9 @@ cudaError_t launch_step(const LaunchSet &L, cudaStream_t s, cudaEvent_t *prof)
     if (e != cudaSuccess) return e;
     if (L.ncomp) {
         if (prof) cudaEventRecord(prof[2], s);
-        if (L.cls16) mag_fn<true, uint16_t>(mag_cpt(L.vmax))<<<L.ncomp, kMagThreads, L.mag_smem, s>>>(L);
-        else mag_fn<true, uint8_t>(mag_cpt(L.vmax))<<<L.ncomp, kMagThreads, L.mag_smem, s>>>(L);
+        e = launch_mag(L.cls16 ? mag_fn<true, uint16_t>(mag_cpt(L.vmax), L.mag_cs > 1)
+                               : mag_fn<true, uint8_t>(mag_cpt(L.vmax), L.mag_cs > 1), L, s);
+        if (e != cudaSuccess) return e;
         if (prof) cudaEventRecord(prof[3], s);
     }
     if (prof) cudaEventRecord(prof[0], s);

@@ -343,6 +343,15 @@ class FdtdLlg:
         """CUDA graphs for long step calls: 1 on, 0 off, -1 automatic."""
         check(_abi.load().fdtd_llg_set_graphs(self._h, int(mode)), self._h)
 
+    def set_magnet_cluster(self, ctas: int):
+        """Magnet CTAs per magnetic region (0: automatic, 1..8)."""
+        check(_abi.load().fdtd_llg_set_magnet_cluster(self._h, int(ctas)), self._h)
+
+    def get_magnet_cluster(self) -> int:
+        v = C.c_int32()
+        check(_abi.load().fdtd_llg_get_magnet_cluster(self._h, C.byref(v)), self._h)
+        return v.value
+
     def set_tile_width(self, width: int):
         """Sweep tile shape: 64 (64 x 8), 32 (32 x 16) or 0 (fewest padded cells)."""
         check(_abi.load().fdtd_llg_set_tile_width(self._h, int(width)), self._h)

@@ -3,7 +3,7 @@ tests.  Calls only the FP64 oracle (``oracle/``) and the seeded workload
 generators; nothing here comes from the CUDA path.
 
     python tests/golden/make_reference_runs.py strip   [--steps N]
-    python tests/golden/make_reference_runs.py sweep   [--steps N] [--instances K]
+    python tests/golden/make_reference_runs.py sweep   [--steps N] [--stride S]
 
 ``strip``: the 256 x 256 x 128 strip resonator (8.39 M cells, the FP32
 throughput configuration) for 20000 steps; stores every 100th probe row, the
@@ -13,7 +13,8 @@ time series).
 
 ``sweep``: the 64-cube bias sweep (uneven cubes 48^3-96^3, bias 0.05-0.15 T)
 for 10000 steps at the batch's common time step (0.5 x the Courant limit of
-the finest cube); per cube the |DFT| of the probe's E_x over 1.5-4.5 GHz and
+the finest cube), every 4th cube (16 cubes over the whole bias range); per
+cube the |DFT| of the probe's E_x over 1.5-4.5 GHz and
 the ESPRIT modes of its E_x trace after the first fifth of the run (the
 polariton pair, section "Results"), then the fit of Eq. omega_pm over the
 cubes whose two modes are both clearly present.
@@ -90,8 +91,8 @@ def strip(steps, out):
     print(f"wrote {out}: {steps} steps in {wall:.0f} s")
 
 
-def sweep(steps, ninst, out):
-    ws = W.bias_sweep(steps=steps)[:ninst]
+def sweep(steps, stride, out):
+    ws = W.bias_sweep(steps=steps)[::stride]
     dmin = min(min(w.dx, w.dy, w.dz) for w in W.bias_sweep(steps=steps))
     dt = oracle.courant_dt(dmin, dmin, dmin, ws[0].courant)
     freqs = np.linspace(SWEEP["fmin"], SWEEP["fmax"], SWEEP["nfreq"])
@@ -104,7 +105,7 @@ def sweep(steps, ninst, out):
         spec = S.dft_magnitude(tr, dt, freqs, kind="hann")
         f, a, amp, Q = S.strongest_in_band(S.matrix_pencil(tr[skip:], dt, SWEEP["order"], SWEEP["pencil"]),
                                            SWEEP["fmin"], SWEEP["fmax"], 2)
-        per.append({"name": w.name, "n": w.nx, "bias_T": float(w.hbias[2] * W.MU0), "spectrum": spec.tolist(),
+        per.append({"name": w.name, "index": q * stride, "n": w.nx, "bias_T": float(w.hbias[2] * W.MU0), "spectrum": spec.tolist(),
                     "modes_hz": f.tolist(), "decay": a.tolist(), "amp": amp.tolist(), "q": Q.tolist()})
         print(f"  {w.name}: modes {np.round(f / 1e9, 4)} amp {amp}", flush=True)
     wall = time.time() - t0
@@ -118,7 +119,7 @@ def sweep(steps, ninst, out):
         "what": "FP64 oracle runs of the 64-cube bias sweep (seeded workload bias_sweep), one cube at a time",
         "cite": "section 'Results' (E_x spectra vs bias, ESPRIT polariton pairs), Eq. omega_pm (the fit)",
         "made_by": "python tests/golden/make_reference_runs.py sweep",
-        "steps": steps, "dt": dt, "instances": len(ws), "threads": THREADS[0], "wall_s": round(wall, 1),
+        "steps": steps, "dt": dt, "instances": len(ws), "stride": stride, "threads": THREADS[0], "wall_s": round(wall, 1),
         "settings": SWEEP, "freqs": [freqs[0], freqs[-1], len(freqs)], "skip": skip,
         "per_instance": per, "pairs": pairs, "fit": fit,
     }
@@ -131,7 +132,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("which", choices=["strip", "sweep"])
     ap.add_argument("--steps", type=int, default=0)
-    ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--stride", type=int, default=4, help="every stride-th cube of the 64 (4: 16 cubes over the whole bias range)")
     ap.add_argument("--out", default="")
     ap.add_argument("--threads", type=int, default=0, help="oracle threads (0: every host core)")
     a = ap.parse_args()
@@ -139,7 +140,7 @@ def main():
     if a.which == "strip":
         strip(a.steps or STRIP["steps"], a.out or os.path.join(HERE, "strip_resonator_256x256x128_fp64.json"))
     else:
-        sweep(a.steps or SWEEP["steps"], a.instances, a.out or os.path.join(HERE, "bias_sweep_64_fp64.json"))
+        sweep(a.steps or SWEEP["steps"], a.stride, a.out or os.path.join(HERE, "bias_sweep_64_fp64.json"))
 
 
 if __name__ == "__main__":

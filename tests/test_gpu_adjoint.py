@@ -29,9 +29,10 @@ def _reference(w, N, n0):
     return A.gradients(m, N, w.eps_design, float(np.linalg.norm(w.hbias)), n0=n0)
 
 
-def _gpu(w, N, n0, interval=0, budget=-1):
+def _gpu(w, N, n0, interval=0, budget=-1, cluster=0):
     sim = pkg.from_workload(w, probe_capacity=N, llg_fixed_iter=3)
     sim.set_tape_budget(budget)
+    sim.set_magnet_cluster(cluster)
     sim.run_checkpointed(N, interval)
     rows = np.stack([sim.probe(p)[:, :3] for p in range(len(w.probes))], axis=1)
     seed = np.zeros_like(rows)
@@ -76,6 +77,20 @@ def test_checkpoint_interval_does_not_change_the_gradient():
     for _, g, h in runs:
         np.testing.assert_array_equal(g0, g)
         assert h == h0
+
+
+def test_split_magnet_records_the_same_tape():
+    """The forward magnet kernel writes the adjoint's records in the region's
+    own indexing whatever the number of CTAs it is split over, so the
+    gradient is the same to the bit with the region on 1, 2 or 4 CTAs."""
+    make, N, n0, _ = CASES["design16"]
+    w = make()
+    J1, g1, h1 = _gpu(w, N, n0, cluster=1)
+    for cs in (2, 4):
+        J, g, h = _gpu(w, N, n0, cluster=cs)
+        assert J == J1
+        np.testing.assert_array_equal(g, g1)
+        assert h == h1
 
 
 def test_adjoint_directional_derivatives_equal_gpu_central_differences():
