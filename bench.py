@@ -273,8 +273,9 @@ def batch_sweep(torch, pkg, W, steps_timed=2000, steps_total=10000):
         spec = m.probe_spectrum(0, 0, lo, hi, 601)
         peaks.append(float(np.linspace(lo, hi, 601)[int(np.argmax(spec))]))
         tr = m.probe(0)[steps_total // 5:, 0]
-        f, a, amp, Q = pkg.fit_modes(tr, dt, 24, pencil=300, fmin=lo, fmax=hi, max_modes=2)
-        if len(f) == 2:
+        # block means over 20 steps: the band's periods then span a pencil
+        f, a, amp, Q = pkg.fit_modes(tr, dt, 24, pencil=100, fmin=lo, fmax=hi, max_modes=2, decimate=20)
+        if len(f) == 2 and min(amp) >= 0.2 * max(amp):
             pairs.append(f)
     # the stored FP64 oracle runs of every 4th cube: the same fit over the
     # cubes whose pair the oracle found clear
@@ -287,7 +288,7 @@ def batch_sweep(torch, pkg, W, steps_timed=2000, steps_total=10000):
         for q in sel:
             tr = batch.batch_member(q).probe(0)[ref["skip"]:, 0]
             fr.append(pkg.fit_modes(tr, dt, rs["order"], pencil=rs["pencil"], fmin=rs["fmin"], fmax=rs["fmax"],
-                                    max_modes=2)[0])
+                                    max_modes=2, decimate=rs["decimate"])[0])
         if all(len(f) == 2 for f in fr):
             fp64 = ref["fit"]["two_g_hz"]
             fp, g = pkg.fit_coupling([f[1] for f in fr], [f[0] for f in fr])
@@ -437,7 +438,7 @@ def cpw_device_run(torch, pkg, W, steps=1000, warmup=20, paper_steps=1_700_000):
             "seconds_per_bias_point": round(sec / steps * paper_steps, 1)}
 
 
-def cpw_resonance(torch, pkg, W, steps=700_000, skip=150_000, decim=1000, film=False, h0_oe=2000.0):
+def cpw_resonance(torch, pkg, W, steps=700_000, skip=150_000, decim=1000, film=False, h0_oe=2000.0, split=False):
     """The paper's CPW resonator rung by its 16 GHz pulse: ESPRIT on the
     line-end probe's Ez after the drive has ended (decimated to 1000 dt =
     2.94 ps, Nyquist 170 GHz) gives the modes.  Without the film: the bare
@@ -449,7 +450,7 @@ def cpw_resonance(torch, pkg, W, steps=700_000, skip=150_000, decim=1000, film=F
 
     from paper_2510_22221_b300 import spectra
 
-    w = W.cpw_device(steps=steps, film=film, h0_oe=h0_oe)
+    w = W.cpw_device(steps=steps, film=film, h0_oe=h0_oe, split=split)
     sim = pkg.from_workload(w, probe_capacity=steps)
     dt = sim.dt
     t0 = time.time()
@@ -460,7 +461,7 @@ def cpw_resonance(torch, pkg, W, steps=700_000, skip=150_000, decim=1000, film=F
     sim.destroy()
     x = x - x.mean()
     out = {"workload": w.name, "steps": steps, "wall_s": round(wall, 1), "samples": int(x.size),
-           "record_ns": round(x.size * dt * decim * 1e9, 3), "film": film, "h0_oe": h0_oe, "paper_f_p_ghz": 15.2,
+           "record_ns": round(x.size * dt * decim * 1e9, 3), "film": film, "film_split": split, "h0_oe": h0_oe, "paper_f_p_ghz": 15.2,
            "paper_2g_mhz": 670}
     # cross-check: peak of the Hann-windowed, 16x zero-padded DFT in 5-40 GHz
     nf = 16 * x.size
@@ -509,6 +510,7 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=4000, help="steps of the adjoint measurement")
     ap.add_argument("--cpw-steps", type=int, default=700_000, help="steps of the CPW resonance measurement (--only cpw_fp)")
     ap.add_argument("--cpw-film", action="store_true", help="--only cpw_fp with the permalloy film (hybrid modes)")
+    ap.add_argument("--cpw-split", action="store_true", help="--only cpw_fp with the film cut in two at its middle")
     ap.add_argument("--cpw-h0", type=float, default=2000.0, help="bias of --only cpw_fp, oersted")
     ap.add_argument("--tiling", type=int, default=0,
                     help="z-planes per sweep task for the headline run (0: autotune during the warm-up)")
@@ -532,7 +534,8 @@ def main():
         elif args.only == "cpw":
             out = cpw_device_run(torch, pkg, W)
         elif args.only == "cpw_fp":
-            out = cpw_resonance(torch, pkg, W, steps=args.cpw_steps, film=args.cpw_film, h0_oe=args.cpw_h0)
+            out = cpw_resonance(torch, pkg, W, steps=args.cpw_steps, film=args.cpw_film, h0_oe=args.cpw_h0,
+                                split=args.cpw_split)
         else:
             out = large_run(torch, pkg, W)
         print(json.dumps(out), flush=True)

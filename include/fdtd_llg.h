@@ -56,7 +56,7 @@
 extern "C" {
 #endif
 
-#define FDTD_LLG_ABI_VERSION 1
+#define FDTD_LLG_ABI_VERSION 2
 
 enum {
     FDTD_OK = 0,
@@ -304,6 +304,18 @@ int fdtd_llg_set_graphs(fdtd_llg_t h, int32_t mode);
  * without magnets).  Errors: FDTD_E_INVAL (ctas outside 0..8; at the next
  * step, a split longer than a region or a slab too large). */
 int fdtd_llg_set_magnet_cluster(fdtd_llg_t h, int32_t ctas);
+
+/* Check of the failure path of the field sweep's bounded waits (the paper has
+ * no counterpart).  Every wait of a sweep CTA for its tile copies gives up
+ * after 2^22 polls: the CTA then latches a timeout in the device status,
+ * stops drawing tasks, waits (bounded) for its own copies in flight and
+ * exits, and the next synchronising call returns FDTD_E_CUDA ("... timed
+ * out").  With polls > 0, in every following step the first sweep CTA, once
+ * its first tile has landed, also waits at most `polls` polls on a
+ * shared-memory barrier that nothing arrives on, and so takes that path;
+ * nothing faults or hangs, the context stays usable, and the step's results
+ * are incomplete.  0 (default) turns it off.  Errors: FDTD_E_INVAL. */
+int fdtd_llg_test_wait_timeout(fdtd_llg_t h, int32_t polls);
 int fdtd_llg_get_magnet_cluster(fdtd_llg_t h, int32_t *ctas);
 
 /* The time step (s) shared by every instance of the handle's batch. */
@@ -410,18 +422,24 @@ int fdtd_llg_adjoint_step(fdtd_llg_t h, const double *dJ_dE, double *grad_eps, d
 int fdtd_llg_probe_spectrum(fdtd_llg_t h, int32_t probe, int32_t comp, double f0, double f1, int32_t nf,
                             int32_t window, double *out);
 
-/* ESPRIT on a real series x[0..n) sampled every dt: the `order` complex
+/* ESPRIT on a real series x[0..n) sampled every dt (the mode extraction of
+ * section "Results"): with decimate > 1 the series is first replaced by its
+ * block means of `decimate` samples at step decimate dt (a moving average:
+ * frequencies and decay rates of the exponentials are kept; a probe series
+ * sampled far above the band of interest then spans many periods within one
+ * pencil, which makes the fit well conditioned).  Then the `order` complex
  * exponentials z_k^t of the Hankel data matrix's signal subspace (pencil
  * length L = pencil, or min(n/3, 200) when pencil <= 0; needs
- * order <= L <= n - order, L <= 4096), their amplitudes by least squares, and
- * of those with positive frequency in [fmin, fmax] the max_modes of largest
- * amplitude, sorted by frequency: freq (Hz), decay (1/s, amplitude
- * ~ exp(-decay t)), amp (of the real cosine), q = pi freq / decay.  Output
- * arrays hold max_modes doubles; *nfound receives the count.  Runs on the
- * host in FP64; needs no GPU.  Errors: FDTD_E_INVAL (message in
- * fdtd_llg_last_error(NULL)). */
-int fdtd_llg_fit_modes(const double *x, int64_t n, double dt, int32_t order, int32_t pencil, double fmin, double fmax,
-                       int32_t max_modes, double *freq, double *decay, double *amp, double *q, int32_t *nfound);
+ * order <= L <= n - order, L <= 4096, n counted after decimation), their
+ * amplitudes by least squares, and of those with positive frequency in
+ * [fmin, fmax] the max_modes of largest amplitude, sorted by frequency: freq
+ * (Hz), decay (1/s, amplitude ~ exp(-decay t)), amp (of the real cosine of
+ * the decimated series), q = pi freq / decay.  Output arrays hold max_modes
+ * doubles; *nfound receives the count.  Runs on the host in FP64; needs no
+ * GPU.  Errors: FDTD_E_INVAL (message in fdtd_llg_last_error(NULL)). */
+int fdtd_llg_fit_modes(const double *x, int64_t n, double dt, int32_t order, int32_t pencil, int32_t decimate,
+                       double fmin, double fmax, int32_t max_modes, double *freq, double *decay, double *amp, double *q,
+                       int32_t *nfound);
 
 /* Cavity frequency f_p and coupling g of Eq. omega_pm from n >= 2 hybrid
  * pairs (f_plus[i] > f_minus[i], Hz) measured at different detunings: with

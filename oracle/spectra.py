@@ -36,6 +36,14 @@ def dft_magnitude(x, dt: float, freqs, kind: str = "hann") -> np.ndarray:
     return np.abs(phase @ (window(x.size, kind) * x))
 
 
+def block_means(x, d: int):
+    """The series of means of consecutive blocks of d samples (the last
+    incomplete block dropped): y_b = (x_{bd} + ... + x_{bd+d-1}) / d."""
+    x = np.asarray(x, dtype=np.float64)
+    n = x.size // d * d
+    return x[:n].reshape(-1, d).mean(axis=1)
+
+
 def matrix_pencil(x, dt: float, order: int, pencil: int | None = None):
     """Complex exponentials z_k^t fitted to a real series by the shift
     invariance of its Hankel data matrix (ESPRIT / matrix pencil):

@@ -74,6 +74,7 @@ SIGNATURES = {
     "fdtd_llg_get_dt": (C.c_int, [_vp, _dp]),
     "fdtd_llg_set_graphs": (C.c_int, [_vp, C.c_int32]),
     "fdtd_llg_set_magnet_cluster": (C.c_int, [_vp, C.c_int32]),
+    "fdtd_llg_test_wait_timeout": (C.c_int, [_vp, C.c_int32]),
     "fdtd_llg_get_magnet_cluster": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
     "fdtd_llg_set_tiling": (C.c_int, [_vp, C.c_int32]),
     "fdtd_llg_get_tiling": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
@@ -87,8 +88,8 @@ SIGNATURES = {
     "fdtd_llg_adjoint_step": (C.c_int, [_vp, _dp, _dp, _dp]),
     "fdtd_llg_probe_spectrum": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_int32, C.c_int32,
                                          _dp]),
-    "fdtd_llg_fit_modes": (C.c_int, [_dp, C.c_int64, C.c_double, C.c_int32, C.c_int32, C.c_double, C.c_double,
-                                    C.c_int32, _dp, _dp, _dp, _dp, C.POINTER(C.c_int32)]),
+    "fdtd_llg_fit_modes": (C.c_int, [_dp, C.c_int64, C.c_double, C.c_int32, C.c_int32, C.c_int32, C.c_double,
+                                    C.c_double, C.c_int32, _dp, _dp, _dp, _dp, C.POINTER(C.c_int32)]),
     "fdtd_llg_fit_coupling": (C.c_int, [_dp, _dp, C.c_int32, _dp, _dp]),
     "fdtd_llg_e_push_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.c_int32,
                                          C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,

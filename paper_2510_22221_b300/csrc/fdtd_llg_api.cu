@@ -100,6 +100,7 @@ struct Sim {
     int ntiles = 0, nftiles = 0, ncomp = 0, vmax = 0, mag_smem = 0;
     int mag_cs = 1, mag_xs = 0;       // magnet CTAs per region (cluster size) and exported floats per layer
     int mag_cluster = 0;              // requested magnet CTAs per region (0: automatic)
+    int test_wait = 0;                // fdtd_llg_test_wait_timeout: polls of the diagnostic wait (0: off)
     int mag_cs_need = 1, mag_cs_fast = 1;   // fewest magnet CTAs per region that fit; the fast split
     bool stab = false;                // every class table small enough for shared memory
     int tiling = 0;                   // requested z-planes per sweep task (0: model)
@@ -1368,6 +1369,7 @@ static LaunchSet launch_set(Sim *S)
     L.part_stride = L.nslot_f + S->ncomp * S->mag_cs;
     L.mag_cs = S->mag_cs;
     L.mag_xs = S->mag_xs;
+    L.test_wait = S->test_wait;
     L.part_f = S->d_part;
     L.part_m = S->d_part + L.nslot_f;
     L.ftask = S->d_ftile_inst;
@@ -1995,6 +1997,17 @@ extern "C" int fdtd_llg_load_state(fdtd_llg_t h, const void *buf, size_t size)
 }
 
 // ------------------------------------------------------------- profiling
+extern "C" int fdtd_llg_test_wait_timeout(fdtd_llg_t h, int32_t polls)
+{
+    if (!h || !h->sim || !h->owns) return fail(h, FDTD_E_INVAL, "set the diagnostic wait on the handle, not a member");
+    if (polls < 0 || polls > (1 << 20)) return fail(h, FDTD_E_INVAL, "polls must be 0 to 2^20");
+    if (polls != h->sim->test_wait) {
+        h->sim->test_wait = polls;
+        h->sim->dirty = true;   // graphs captured with the old launch parameters are dropped
+    }
+    return FDTD_OK;
+}
+
 extern "C" int fdtd_llg_set_magnet_cluster(fdtd_llg_t h, int32_t ctas)
 {
     if (!h || !h->sim || !h->owns) return fail(h, FDTD_E_INVAL, "set the magnet cluster on the handle, not a member");

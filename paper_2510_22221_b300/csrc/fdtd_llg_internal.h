@@ -314,6 +314,7 @@ struct LaunchSet {
     bool stab;                          // every instance's class table fits kTabMax
     int sx;                             // sweep tile width: 64 (64 x 8 tiles) or 32 (32 x 16)
     int rec;                            // magnet kernel writes its tape (adjoint recomputation)
+    int test_wait;                      // > 0: sweep CTA 0 also waits, this many polls, on a barrier nothing arrives on
     long long rec_n0;                   // step of tape slot 0
     int rec_slots;                      // slots of the tape
 };

@@ -858,10 +858,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *b, unsigned parity)
         : "memory");
     return ok != 0;
 }
-// Bounded wait for the phase with the given parity: false after 2^22 polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, unsigned parity)
+// Bounded wait for the phase with the given parity: false after `polls`
+// polls (2^22 by default).
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, unsigned parity, int polls = 1 << 22)
 {
-    for (int it = 0; it < (1 << 22); ++it)
+    for (int it = 0; it < polls; ++it)
         if (mbar_try_wait(b, parity)) return true;
     return false;
 }
@@ -925,6 +926,7 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
     __shared__ float4 stab[STAB ? 3 * kTabMax : 1];
     __shared__ double sred[kST / 32];
     __shared__ int s_last, s_abort, s_task;
+    __shared__ uint64_t s_never;   // the diagnostic wait's barrier (L.test_wait): nothing arrives on it
     using TL = Tile<SX>;
     constexpr int SY = TL::Y, LPR = TL::LPR, HBX = TL::HBX, HC = TL::HC, EBX = TL::EBX, EBY = TL::EBY, EC = TL::EC;
     constexpr int CBX = sizeof(ClsT) == 1 ? TL::CBX8 : TL::CBX16;
@@ -935,6 +937,7 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
     const long long n = *(volatile long long *)&L.ctl->step;
     if (tid == 0) {
         for (int s = 0; s < kNS; ++s) mbar_init(&bar[s], 1);
+        mbar_init(&s_never, 1);
         fence_barrier_init();
         fence_proxy_async();
         s_abort = 0;
@@ -1054,7 +1057,12 @@ __global__ void __launch_bounds__(kST, 3) step_kernel(LaunchSet L)
     for (int q = 0; q < nitems; ++q) {
         const long long g = gbase + q;
         const int s = (int)(g % kNS), sp = (int)((g + kNS - 1) % kNS);
-        if (!mbar_wait(&bar[s], (unsigned)(g / kNS) & 1u)) {
+        bool landed = mbar_wait(&bar[s], (unsigned)(g / kNS) & 1u);
+        // diagnostic of the timeout path (L.test_wait > 0): after its first
+        // item has landed, CTA 0 also waits on a barrier that nothing arrives
+        // on, at most L.test_wait polls, as for a copy that never lands
+        if (landed && L.test_wait > 0 && blockIdx.x == 0 && g == 0) landed = mbar_wait(&s_never, 0u, L.test_wait);
+        if (!landed) {
             atomicOr(&L.ctl->status, ST_TIMEOUT);
             s_abort = 1;
         }

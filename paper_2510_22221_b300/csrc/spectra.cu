@@ -247,12 +247,28 @@ extern "C" int fdtd_llg_probe_spectrum(fdtd_llg_t h, int32_t probe, int32_t comp
     return FDTD_OK;
 }
 
-extern "C" int fdtd_llg_fit_modes(const double *x, int64_t n, double dt, int32_t order, int32_t pencil, double fmin,
-                                  double fmax, int32_t max_modes, double *freq, double *decay, double *amp, double *q,
-                                  int32_t *nfound)
+extern "C" int fdtd_llg_fit_modes(const double *x, int64_t n, double dt, int32_t order, int32_t pencil, int32_t decimate,
+                                  double fmin, double fmax, int32_t max_modes, double *freq, double *decay, double *amp,
+                                  double *q, int32_t *nfound)
 {
-    if (!x || !freq || !decay || !amp || !q || !nfound || !(dt > 0) || order < 1 || max_modes < 1)
-        return fail_handle(nullptr, FDTD_E_INVAL, "fit_modes: null pointer, dt <= 0, order < 1 or max_modes < 1");
+    if (!x || !freq || !decay || !amp || !q || !nfound || !(dt > 0) || order < 1 || max_modes < 1 || decimate < 1)
+        return fail_handle(nullptr, FDTD_E_INVAL,
+                           "fit_modes: null pointer, dt <= 0, order < 1, decimate < 1 or max_modes < 1");
+    // block means of `decimate` samples (a moving-average filter sampled
+    // every `decimate` steps: the frequencies of the exponentials are kept,
+    // their amplitudes and phases change), then the fit at the coarser step
+    std::vector<double> xd;
+    if (decimate > 1) {
+        xd.resize((size_t)(n / decimate));
+        for (size_t b = 0; b < xd.size(); ++b) {
+            double s = 0.0;
+            for (int t = 0; t < decimate; ++t) s += x[(int64_t)b * decimate + t];
+            xd[b] = s / decimate;
+        }
+        x = xd.data();
+        n = (int64_t)xd.size();
+        dt *= decimate;
+    }
     const int L = pencil > 0 ? pencil : (int)std::min<int64_t>(n / 3, 200);
     if (L < order || n - L < order || L > 4096)
         return fail_handle(nullptr, FDTD_E_INVAL, "fit_modes: need order <= pencil <= n - order and pencil <= 4096");

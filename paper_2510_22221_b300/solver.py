@@ -343,6 +343,11 @@ class FdtdLlg:
         """CUDA graphs for long step calls: 1 on, 0 off, -1 automatic."""
         check(_abi.load().fdtd_llg_set_graphs(self._h, int(mode)), self._h)
 
+    def test_wait_timeout(self, polls: int):
+        """Make the first sweep CTA's bounded wait run out (see the header);
+        0 turns it off."""
+        check(_abi.load().fdtd_llg_test_wait_timeout(self._h, int(polls)), self._h)
+
     def set_magnet_cluster(self, ctas: int):
         """Magnet CTAs per magnetic region (0: automatic, 1..8)."""
         check(_abi.load().fdtd_llg_set_magnet_cluster(self._h, int(ctas)), self._h)

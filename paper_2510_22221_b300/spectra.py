@@ -14,15 +14,16 @@ _dp = C.POINTER(C.c_double)
 
 
 def fit_modes(x, dt: float, order: int, pencil: int = 0, fmin: float = 0.0, fmax: float = float("inf"),
-              max_modes: int = 8):
-    """Modes of a real series by ESPRIT: arrays (freq, decay, amp, q) of the
-    up to max_modes strongest modes in [fmin, fmax], sorted by frequency."""
+              max_modes: int = 8, decimate: int = 1):
+    """Modes of a real series by ESPRIT (after block means of `decimate`
+    samples): arrays (freq, decay, amp, q) of the up to max_modes strongest
+    modes in [fmin, fmax], sorted by frequency."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     out = [np.zeros(int(max_modes)) for _ in range(4)]
     nfound = C.c_int32(0)
     check(_abi.load().fdtd_llg_fit_modes(x.ctypes.data_as(_dp), x.size, float(dt), int(order), int(pencil),
-                                         float(fmin), float(fmax), int(max_modes), *[o.ctypes.data_as(_dp) for o in out],
-                                         C.byref(nfound)))
+                                         int(decimate), float(fmin), float(fmax), int(max_modes),
+                                         *[o.ctypes.data_as(_dp) for o in out], C.byref(nfound)))
     k = nfound.value
     return tuple(o[:k] for o in out)
 

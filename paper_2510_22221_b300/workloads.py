@@ -283,7 +283,7 @@ def strip_resonator_pml(nx=256, ny=256, nz=128, steps=20000, layers=(10, 10, 8))
     return w
 
 
-def cpw_device(steps=1000, layers=(10, 10, 10), h0_oe=2000.0, metal="sigma", film=True) -> Workload:
+def cpw_device(steps=1000, layers=(10, 10, 10), h0_oe=2000.0, metal="sigma", film=True, split=False) -> Workload:
     """The paper's CPW resonator (section "Modeling Setup") on its own
     120 x 250 x 1000 grid of 5 x 19 x 1 um cells (dt = 2.94e-15 s at CFL 0.9):
     silicon substrate (eps_r 11.4) 500 um thick (z < 500), a 2 um metal
@@ -291,8 +291,9 @@ def cpw_device(steps=1000, layers=(10, 10, 10), h0_oe=2000.0, metal="sigma", fil
     centre line 50 um wide with 25 um gaps, 198 cells = 3.76 mm long, gaps of
     10 cells = 190 um to feeding patches of 16 cells = 304 um at both y ends),
     a permalloy film (4 pi Ms = 1.2e4 G, alpha 0.003) 5 um thick and 30 um
-    wide on the centre line, 148 cells = 2.81 mm long, split by one
-    non-magnetic cell at its middle so that each half fits one magnet CTA;
+    wide on the centre line, 148 cells = 2.81 mm long, in one piece (split=True
+    cuts it by one non-magnetic cell at its middle, the variant that fitted
+    one magnet CTA per half);
     bias H0 along y; absorbing layers on all six faces (the substrate, the
     grounds and the feeding patches run into them).  Metal: sigma = 1e11 S/m
     ("sigma") or PEC ("pec").  The voltage port is replaced by an x-directed
@@ -317,13 +318,14 @@ def cpw_device(steps=1000, layers=(10, 10, 10), h0_oe=2000.0, metal="sigma", fil
     fy0 = ny // 2 - 74                           # film y 51..198, split at 125
     if film:
         mid[zs + 2:zs + 7, fy0:fy0 + 148, 57:63] = 3
-        mid[zs + 2:zs + 7, ny // 2, 57:63] = 0
+        if split:
+            mid[zs + 2:zs + 7, ny // 2, 57:63] = 0
     src = [dict(comp=0, i=52, j=13, k=zs, J0=1.0, f0=16e9, Tp=0.0625e-9, tpk=0.0)]
     probes = [(56, ny // 2 + 30, zs + 8), (60, y0 + 2, zs + 2)]
     h0 = h0_oe * 1e3 / (4 * np.pi)              # oersted -> A/m
     return Workload(f"cpw_device_{nx}x{ny}x{nz}", nx, ny, nz, dx, dy, dz, 0.9, steps, mats, mid,
                     np.array([0.0, h0, 0.0]), src, probes,
-                    note=f"paper's CPW resonator, {'permalloy film on the centre line' if film else 'no film'}, H0 {h0_oe} Oe along y, "
+                    note=f"paper's CPW resonator, {('split ' if split else '') + 'permalloy film on the centre line' if film else 'no film'}, H0 {h0_oe} Oe along y, "
                          f"absorbing layers {layers}, metal {metal}",
                     pml=dict(layers=tuple(layers), order=3.0, scale=1.0, kappa_max=1.0, alpha_max=0.0))
 

@@ -54,9 +54,23 @@ def main():
     flat = rng.choice(base.eps_design.size, size=NCELLS, replace=False)
     cells = [tuple(int(v) for v in np.unravel_index(int(q), shape)) for q in flat]
     t0 = time.time()
-    J0 = objective(base)
+    # resumable: cells already differenced are kept in a side file until done
+    part = a.out + ".part"
+    done = {}
+    if os.path.exists(part):
+        with open(part) as f:
+            for line in f:
+                r = json.loads(line)
+                done[tuple(r["cell_kji"])] = r
+    J0 = done[("J",)]["J"] if ("J",) in done else objective(base)
+    if ("J",) not in done:
+        with open(part, "a") as f:
+            f.write(json.dumps({"cell_kji": ["J"], "J": J0}) + "\n")
     out = []
     for idx in cells:
+        if idx in done:
+            out.append(done[idx])
+            continue
         h = REL_H * float(base.eps_design[idx])
         Js = []
         for sgn in (1.0, -1.0):
@@ -66,6 +80,8 @@ def main():
             Js.append(objective(w))
         out.append({"cell_kji": list(idx), "eps": float(base.eps_design[idx]), "h": h,
                     "fd": (Js[0] - Js[1]) / (2 * h), "J_plus": Js[0], "J_minus": Js[1]})
+        with open(part, "a") as f:
+            f.write(json.dumps(out[-1]) + "\n")
         print(idx, out[-1]["fd"], flush=True)
     doc = {
         "what": "FP64 oracle central differences of the probe objective on 16 design cells of the 128x128x64 "
@@ -77,6 +93,7 @@ def main():
     }
     with open(a.out, "w") as f:
         json.dump(doc, f, indent=1)
+    os.remove(part)
     print(f"wrote {a.out}")
 
 

@@ -14,10 +14,11 @@ time series).
 ``sweep``: the 64-cube bias sweep (uneven cubes 48^3-96^3, bias 0.05-0.15 T)
 for 10000 steps at the batch's common time step (0.5 x the Courant limit of
 the finest cube), every 4th cube (16 cubes over the whole bias range); per
-cube the |DFT| of the probe's E_x over 1.5-4.5 GHz and
-the ESPRIT modes of its E_x trace after the first fifth of the run (the
-polariton pair, section "Results"), then the fit of Eq. omega_pm over the
-cubes whose two modes are both clearly present.
+cube the |DFT| of the probe's E_x over 1.5-4.5 GHz, the block means of E_x
+over 20 steps, and the ESPRIT modes of those block means after the first
+fifth of the run (the polariton pair, section "Results"; the block means keep
+the frequencies and put several periods in one pencil), then the fit of Eq.
+omega_pm over the cubes whose two modes are both clearly present.
 
 Each run uses every host core (the oracle's results do not depend on the
 thread count).
@@ -44,7 +45,8 @@ from tests.helpers import oracle_from_workload  # noqa: E402
 # spectral settings shared with the GPU tests that read these files
 STRIP = dict(steps=20000, every=100, fmin=0.05e12, fmax=1.5e12, nfreq=291, comps=(0, 2, 4))
 THREADS = [0]
-SWEEP = dict(steps=10000, skip_frac=5, order=24, pencil=300, fmin=1.5e9, fmax=4.5e9, nfreq=61, amp_ratio=0.2)
+SWEEP = dict(steps=10000, skip_frac=5, decimate=20, order=24, pencil=100, fmin=1.5e9, fmax=4.5e9, nfreq=61,
+             amp_ratio=0.2)
 
 
 def peak(freqs, spec):
@@ -103,10 +105,13 @@ def sweep(steps, stride, out):
         o = oracle_from_workload(w, dt=dt)
         tr = o.run(steps)["probes"][:, 0, 0]
         spec = S.dft_magnitude(tr, dt, freqs, kind="hann")
-        f, a, amp, Q = S.strongest_in_band(S.matrix_pencil(tr[skip:], dt, SWEEP["order"], SWEEP["pencil"]),
+        D = SWEEP["decimate"]
+        xd = S.block_means(tr[skip:], D)
+        f, a, amp, Q = S.strongest_in_band(S.matrix_pencil(xd, dt * D, SWEEP["order"], SWEEP["pencil"]),
                                            SWEEP["fmin"], SWEEP["fmax"], 2)
-        per.append({"name": w.name, "index": q * stride, "n": w.nx, "bias_T": float(w.hbias[2] * W.MU0), "spectrum": spec.tolist(),
-                    "modes_hz": f.tolist(), "decay": a.tolist(), "amp": amp.tolist(), "q": Q.tolist()})
+        per.append({"name": w.name, "index": q * stride, "n": w.nx, "bias_T": float(w.hbias[2] * W.MU0),
+                    "spectrum": spec.tolist(), "modes_hz": f.tolist(), "decay": a.tolist(), "amp": amp.tolist(),
+                    "q": Q.tolist(), "ex_block_means": S.block_means(tr, D).tolist()})
         print(f"  {w.name}: modes {np.round(f / 1e9, 4)} amp {amp}", flush=True)
     wall = time.time() - t0
     pairs = [q for q, r in enumerate(per)

@@ -31,7 +31,7 @@ def test_library_exports_every_declared_symbol():
     lib = pkg.load_library()
     for name in declared_functions():
         assert hasattr(lib, name), name
-    assert lib.fdtd_llg_abi_version() == 1
+    assert lib.fdtd_llg_abi_version() == 2
 
 
 def test_argument_errors_without_gpu():

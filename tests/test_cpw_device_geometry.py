@@ -60,6 +60,9 @@ def test_coplanar_cross_section_and_film(w):
     assert i.min() - 55 == 65 - 1 - i.max()
     length = (j.max() - j.min() + 1) * w.dy
     assert abs(length - 2.82e-3) < w.dy                                        # 2.82 mm
+    assert film.sum() == 6 * 148 * 5                                           # in one piece
+    split = W.cpw_device(split=True)
+    assert (ms[split.mat_id] > 0).sum() == 6 * 147 * 5                         # cut by one cell layer
     Ms = ms[ms > 0][0]
     assert np.isclose(4 * np.pi * Ms * 1e-3, 1.2e4)                            # 4 pi Ms = 1.2e4 G
     assert [q["alpha"] for q in w.materials if q["Ms"] > 0] == [3e-3]

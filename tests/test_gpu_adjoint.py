@@ -16,6 +16,7 @@ import paper_2510_22221_b300 as pkg
 from oracle import adjoint as A
 from paper_2510_22221_b300 import workloads as W
 from paper_2510_22221_b300.autograd import probe_energy
+from tests.helpers import record
 
 pytestmark = pytest.mark.gpu
 
@@ -45,6 +46,9 @@ def _gpu(w, N, n0, interval=0, budget=-1, cluster=0):
 
 CASES = {
     "design16": (lambda: W.adjoint_small(n=16, steps=260, design=(6, 6, 2), block=(4, 4, 2)), 260, 160, 1e-4),
+    # the 24^3 analogue of the 128x128x64 design case (8x8x2 design cells, a
+    # 4x4x2 YIG block, 400 steps, the objective over the last quarter)
+    "design24": (lambda: W.adjoint_small(n=24, steps=400), 400, 300, 1e-3),
     "anticross": (lambda: W.anticrossing_sweep(n_inst=1, b_lo=0.05, b_hi=0.05, steps=900, design=(4, 3, 1))[0], 900,
                   500, 1e-3),
 }
@@ -57,9 +61,14 @@ def test_adjoint_matches_fp64_reference(case):
     J, ge, gh = _gpu(w, N, n0)
     Jo, geo, gho = _reference(w, N, n0)
     assert J == pytest.approx(Jo, rel=1e-5)
-    assert np.linalg.norm(ge - geo) / np.linalg.norm(geo) < 1e-4
-    assert np.abs(ge - geo).max() < 1e-4 * np.abs(geo).max()
-    assert gh == pytest.approx(gho, rel=tol_h)
+    en = np.linalg.norm(ge - geo) / np.linalg.norm(geo)
+    em = np.abs(ge - geo).max() / np.abs(geo).max()
+    eh = abs(gh - gho) / abs(gho)
+    record("grad eps norm", en, 1e-4, steps=N)
+    record("grad eps max", em, 1e-4, steps=N)
+    record("grad h0", eh, tol_h, steps=N)
+    assert en < 1e-4 and em < 1e-4
+    assert eh < tol_h
 
 
 def test_checkpoint_interval_does_not_change_the_gradient():
@@ -96,7 +105,7 @@ def test_split_magnet_records_the_same_tape():
 def test_adjoint_directional_derivatives_equal_gpu_central_differences():
     """Central differences of the FP32 forward run itself, along a random
     direction and along the gradient, over all design cells at once (a single
-    cell moves J by less than the FP32 rounding of J)."""
+    cell moves J by less than the FP32 rounding of J), to 1e-3."""
     make, N, n0, _ = CASES["design16"]
     w = make()
     J, ge, gh = _gpu(w, N, n0)
@@ -110,10 +119,53 @@ def test_adjoint_directional_derivatives_equal_gpu_central_differences():
         sim.destroy()
         return float((rows[n0:] ** 2).sum())
 
-    for d in (np.random.default_rng(7).standard_normal(w.eps_design.shape), ge / np.abs(ge).max()):
-        h = 1e-2
+    # step 0.05 along a max-normalised direction: the FP32 rounding of J
+    # (~1e-6 of J) is then ~1e-5 of the difference, and the O(h^2) term stays
+    # below it (measured 2.5e-5 for both directions; 1e-4-2.5e-4 at h = 0.01,
+    # where the rounding dominates)
+    h = 5e-2
+    for name, d in (("random", np.random.default_rng(7).standard_normal(w.eps_design.shape)),
+                    ("gradient", ge / np.abs(ge).max())):
+        d = d / np.abs(d).max()
         fd = (J_at(w.eps_design + h * d) - J_at(w.eps_design - h * d)) / (2 * h)
-        assert float((ge * d).sum()) == pytest.approx(fd, rel=5e-3)
+        e = abs(float((ge * d).sum()) - fd) / abs(fd)
+        record(f"directional {name} h={h}", e, 1e-3, steps=N)
+        assert e < 1e-3, (name, e)
+
+
+def test_design_case_gradient_equals_fp64_central_differences_on_16_cells():
+    """The 128 x 128 x 64 design case at full size (4000 steps, the objective
+    over the last 1000, three fixed LLG iterates): the GPU gradient (FP32
+    forward run and reverse sweep, FP64 sums) at 16 random design cells
+    against central differences of the FP64 oracle's objective, stored by
+    tests/golden/make_adjoint_fd.py (relative step 1e-3 of each cell's eps_r):
+    to 1e-3 over the 16 cells (2-norm), to 1e-2 cell by cell."""
+    import json
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "adjoint_design_fd16_fp64.json")
+    with open(path) as f:
+        ref = json.load(f)
+    N, n0 = ref["steps"], ref["n0"]
+    w = W.adjoint_design(steps=N)
+    J, ge, gh = _gpu(w, N, n0)
+    eJ = abs(J - ref["J"]) / ref["J"]
+    record("J vs fp64", eJ, 1e-4, steps=N)
+    assert eJ < 1e-4
+    errs = {}
+    for c in ref["cells"]:
+        idx = tuple(c["cell_kji"])
+        errs[idx] = abs(ge[idx] - c["fd"]) / abs(c["fd"])
+        record(f"cell {idx}", errs[idx], 1e-3, steps=N)
+    g = np.array([ge[tuple(c["cell_kji"])] for c in ref["cells"]])
+    fd = np.array([c["fd"] for c in ref["cells"]])
+    en = float(np.linalg.norm(g - fd) / np.linalg.norm(fd))
+    record("cells norm", en, 1e-3, steps=N)
+    # measured: 9.4e-4 over the 16 cells; per cell 8e-6 to 2e-3 where the
+    # gradient is within 20x of the largest, 6.4e-3 on the smallest (200x
+    # below it), where the FP32 trajectories' rounding weighs most
+    assert en < 1e-3, (en, errs)
+    assert max(errs.values()) < 1e-2, errs
 
 
 def test_autograd_function_returns_the_library_gradients():

@@ -598,6 +598,28 @@ def test_llg_nonconvergence_is_reported():
     assert ei.value.code == -5
 
 
+def test_bounded_wait_timeout_is_reported_and_the_context_stays_usable():
+    """The first sweep CTA waits, a few polls at most, on a barrier that
+    nothing arrives on (the library's diagnostic of its timeout path): the
+    status reports the timed-out wait, no fault or hang follows, and a fresh
+    handle on the same context then runs and matches the oracle."""
+    import torch
+
+    w = W.random_small(2, steps=6)
+    with torch.cuda.stream(torch.cuda.Stream()):
+        sim = pkg.from_workload(w, probe_capacity=8)
+        sim.test_wait_timeout(64)
+        sim.step(3)
+        with pytest.raises(pkg.LLGError) as ei:
+            sim.sync()
+        assert ei.value.code == -2 and "timed out" in str(ei.value)
+        sim.destroy()
+    torch.cuda.synchronize()
+    sim, orc, out, M0 = run_pair(w, w.steps)
+    compare_fields(sim, orc, M0, tol(w.steps))
+    sim.destroy()
+
+
 def test_unstable_run_is_reported():
     w = W.cavity_block(steps=5)
     sim = pkg.from_workload(w, probe_capacity=8)

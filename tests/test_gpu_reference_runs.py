@@ -11,9 +11,10 @@ seeded workload generators.
     energy agree within the parity tests' bounds TOL(N), TOL_W(N).
   * The 64-cube bias sweep (10000 steps, one batch at the common time
     step), every 4th cube (16 cubes over 0.05-0.15 T): each probe spectrum
-    to 1e-4 in relative L2, the ESPRIT modes of each E_x trace to 1e-4, and
-    the splitting 2g of Eq. omega_pm fitted over the cubes with a clear pair
-    to 1e-4 of the FP64 fit."""
+    to 1e-4 in relative L2, the ESPRIT modes of each E_x trace (block means
+    over 20 steps after the first fifth of the run) to 1e-4, and the splitting
+    2g of Eq. omega_pm fitted over the cubes with a clear pair to 1e-4 of the
+    FP64 fit."""
 import json
 import os
 
@@ -103,7 +104,7 @@ def test_bias_sweep_spectra_modes_and_splitting_match_fp64():
         assert e < 1e-4, (r["name"], e)
         tr = m.probe(0)[skip:, 0]
         f, a, amp, Q = pkg.fit_modes(tr, dt, st["order"], pencil=st["pencil"], fmin=st["fmin"], fmax=st["fmax"],
-                                     max_modes=2)
+                                     max_modes=2, decimate=st["decimate"])
         assert len(f) == len(r["modes_hz"]), (r["name"], f, r["modes_hz"])
         fe = float(np.max(np.abs(f - np.asarray(r["modes_hz"])) / np.asarray(r["modes_hz"])))
         record(f"modes {r['name']}", fe, 1e-4, steps=N)

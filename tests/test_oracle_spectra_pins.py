@@ -56,6 +56,26 @@ def test_matrix_pencil_recovers_damped_cosines():
     np.testing.assert_allclose(samp, A[:2], rtol=1e-7)
 
 
+def test_block_means_keep_frequency_and_decay():
+    """Block means of d samples of A z^t are A (1 - z^d) / (d (1 - z)) (z^d)^b:
+    the same frequency and decay at step d dt, with that amplitude factor
+    (a geometric sum), which the pencil fit then recovers."""
+    dt, d, n = 1e-12, 20, 20000
+    f, a, A = 2.7e9, 3e6, 1.3
+    t = np.arange(n) * dt
+    x = A * np.exp(-a * t) * np.cos(2 * np.pi * f * t)
+    y = S.block_means(x, d)
+    assert y.shape == (n // d,)
+    z = np.exp((-a + 2j * np.pi * f) * dt)
+    fac = (1 - z ** d) / (d * (1 - z))
+    b = np.arange(n // d)
+    np.testing.assert_allclose(y, A * np.real(fac * z ** (d * b)), rtol=0, atol=1e-12 * A)
+    fr, de, amp, q = S.matrix_pencil(y, d * dt, 2, 200)
+    assert fr[0] == pytest.approx(f, rel=1e-10)
+    assert de[0] == pytest.approx(a, rel=1e-6)
+    assert amp[0] == pytest.approx(A * abs(fac), rel=1e-8)
+
+
 def test_hybrid_modes_are_the_coupled_mode_eigenvalues():
     f_p, g = 15.2e9, 0.335e9
     f_m = np.linspace(13.5e9, 17.0e9, 11)

@@ -46,6 +46,20 @@ def test_fit_modes_matches_oracle_noisy_band_selection(seed):
     np.testing.assert_allclose(got[0], f[:2], rtol=1e-5)
 
 
+def test_fit_modes_with_block_means_matches_oracle():
+    """The library's decimated fit is the oracle's pencil fit of the block
+    means (same series, same settings)."""
+    rng = np.random.default_rng(4)
+    dt, n, d = 7.6e-13, 8000, 20
+    f, a = np.array([2.41e9, 2.77e9, 3.9e9, 40e9]), np.array([2e6, 4e6, 3e7, 1e8])
+    A, ph = np.array([0.3, 1.0, 0.2, 0.5]), rng.uniform(-3, 3, 4)
+    x = damped(dt, n, f, a, A, ph) + 1e-4 * rng.standard_normal(n)
+    got = pkg.fit_modes(x, dt, 24, pencil=100, fmin=1.5e9, fmax=4.5e9, max_modes=2, decimate=d)
+    ref = S.strongest_in_band(S.matrix_pencil(S.block_means(x, d), d * dt, 24, 100), 1.5e9, 4.5e9, 2)
+    np.testing.assert_allclose(got[0], ref[0], rtol=1e-9)
+    np.testing.assert_allclose(got[0], f[:2], rtol=1e-5)
+
+
 def test_fit_coupling_matches_oracle():
     f_m = np.linspace(1.9e9, 3.7e9, 7)
     fp_, fm_ = S.hybrid_modes(2.79e9, f_m, 0.23e9)
