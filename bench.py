@@ -353,6 +353,41 @@ def precision_vs_fp64(torch, pkg, W):
             "reference": "FP64 oracle, tests/golden/strip_resonator_256x256x128_fp64.json"}
 
 
+def sharded_sweep(torch, pkg, W, world, rank, steps=2000, warmup=20):
+    """Config 2 over several GPUs: the 64 cubes shared out by cell count
+    (shard_instances), each rank advancing its share as one batch at the
+    sweep's common time step; no collective on the data path.  Whole-job
+    rate = every rank's cell-updates / the slowest rank's time (total work
+    fixed: strong scaling)."""
+    import math
+
+    from paper_2510_22221_b300.distributed import job_rate, shard_instances
+
+    ws = W.bias_sweep(steps=steps)
+    mine = shard_instances([w.cells for w in ws], world)[rank]
+    dmin = min(w.dx for w in ws)
+    dt = ws[0].courant * dmin / (299792458.0 * math.sqrt(3.0))   # the cubes' common Courant step
+    sub = [ws[q] for q in mine]
+    b = pkg.FdtdLlg.create_batch([(x.nx, x.ny, x.nz) for x in sub], [(x.dx, x.dy, x.dz) for x in sub], dt=dt,
+                                 probe_capacity=64)
+    for q, x in enumerate(sub):
+        pkg.configure(b.batch_member(q), x)
+    b.step(warmup)
+    b.sync()
+    stream = torch.cuda.current_stream()
+    torch.distributed.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(steps)
+    e1.record(stream)
+    b.sync()
+    cells = sum(x.cells for x in sub)
+    rate, sec = job_rate(float(cells) * steps, e0.elapsed_time(e1) * 1e-3)
+    b.destroy()
+    return {"instances": len(ws), "ranks": world, "instances_per_rank": len(mine), "steps": steps,
+            "mcells_per_s": round(rate / 1e6, 1), "seconds": round(sec, 4), "scaling": "strong"}
+
+
 def large_run(torch, pkg, W, steps=1000, warmup=10):
     """Config 4: the 512 x 512 x 256 eight-strip array (67 M cells, eight
     3072-cell YIG films, alpha 1e-4, strong drive); FP32 fields, FP64 energy
@@ -380,10 +415,12 @@ def pml_run(torch, pkg, W, steps=2000, warmup=20, layers=(10, 10, 8)):
     """The 256 x 256 x 128 strip resonator lined with absorbing layers
     (convolutional PML) against the same grid with bare PEC walls, on one
     box, same tiling: throughput of both and the cost of the layers' two
-    passes per layer cell.  A cell in one axis's layers moves ~89 B per step
-    in the two passes (E read 12, H read + write of two components 16, the
-    axis's two H memories read + write 16; then H read 12, E 16, two E
-    memories 16, class id 1; neighbour values from L1/L2)."""
+    passes per layer cell.  Algorithmic bytes of a cell in one axis's layers,
+    81 B per step: the H pass reads the two E components it differentiates
+    (8), reads and writes the two H components it corrects (16) and the
+    axis's two H memories (16); the E pass the same with H and E swapped
+    (40) plus the class id (1); neighbour values come from L1/L2 (ncu: 80 B
+    of DRAM traffic per layer cell over both passes)."""
     stream = torch.cuda.current_stream()
     out = {}
     for tag, w in (("plain", W.strip_resonator(steps=steps)), ("layers", W.strip_resonator_pml(steps=steps, layers=layers))):
@@ -408,7 +445,7 @@ def pml_run(torch, pkg, W, steps=2000, warmup=20, layers=(10, 10, 8)):
     out["layer_cost_ms_per_step"] = round(extra, 5)
     hbm, _ = peaks()
     if extra > 0:
-        out["layer_passes_gbs"] = round(89 * layer_cells / (extra * 1e-3) / 1e9, 1)
+        out["layer_passes_gbs"] = round(81 * layer_cells / (extra * 1e-3) / 1e9, 1)
         out["layer_passes_hbm_pct"] = round(100 * out["layer_passes_gbs"] / hbm, 1)
     return out
 
@@ -672,6 +709,8 @@ def main():
                                "step call and D2H of the step's probe rows and energy into pinned host rings; one "
                                "synchronisation at the end"}
 
+    if world > 1 and not args.no_extra:   # every rank takes part
+        line["batch_sweep_sharded"] = sharded_sweep(torch, pkg, W, world, rank)
     if not args.no_extra and rank == 0:
         adj = adjoint_ratio(torch, pkg, W, steps=args.adjoint_steps, n0=args.adjoint_steps * 3 // 4)
         line["adjoint"] = adj

@@ -246,6 +246,16 @@ int fdtd_llg_set_field(fdtd_llg_t h, int32_t which, const float *in, size_t coun
  * buffer), FDTD_E_STATE (no materials). */
 int fdtd_llg_planes(fdtd_llg_t h, int32_t k0, int32_t k1, float *buf, size_t count, int32_t to_handle);
 
+/* fdtd_llg_planes with buf in device memory (of the handle's GPU): the same
+ * layout, queued on the handle's stream with no synchronisation and no host
+ * round trip, so that a halo exchange between slabs stays on the GPUs (the
+ * buffer then travels by NCCL send/recv or a peer copy; ghost-cell exchange
+ * of section "Parallelization").  Reads see every step queued before the
+ * call; writes are seen by every step queued after it.  The caller orders
+ * its own use of buf with the handle's stream.  Errors as fdtd_llg_planes,
+ * and FDTD_E_INVAL when buf is not device memory. */
+int fdtd_llg_planes_device(fdtd_llg_t h, int32_t k0, int32_t k1, float *buf, size_t count, int32_t to_handle);
+
 /* Checkpoint / resume of E, H, M, wall faces, step and time state.
  * buf = NULL: *size receives the byte count needed. */
 int fdtd_llg_save_state(fdtd_llg_t h, void *buf, size_t *size);

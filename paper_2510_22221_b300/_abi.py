@@ -67,6 +67,7 @@ SIGNATURES = {
     "fdtd_llg_get_field": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_float), C.c_size_t]),
     "fdtd_llg_set_field": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_float), C.c_size_t]),
     "fdtd_llg_planes": (C.c_int, [_vp, C.c_int32, C.c_int32, C.POINTER(C.c_float), C.c_size_t, C.c_int32]),
+    "fdtd_llg_planes_device": (C.c_int, [_vp, C.c_int32, C.c_int32, _vp, C.c_size_t, C.c_int32]),
     "fdtd_llg_save_state": (C.c_int, [_vp, _vp, C.POINTER(C.c_size_t)]),
     "fdtd_llg_load_state": (C.c_int, [_vp, _vp, C.c_size_t]),
     "fdtd_llg_set_profiling": (C.c_int, [_vp, C.c_int32]),

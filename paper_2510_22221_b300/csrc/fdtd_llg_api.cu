@@ -1910,6 +1910,74 @@ struct StateHeader {
 constexpr uint32_t kMagic = 0x4c4c4446u;   // "FDLL"
 }  // namespace
 
+// The magnetisation deviation of region C's cells in planes [k0, k1) between
+// the region's array and a plane buffer bm (3 x P x ny x nx, zero outside
+// magnetic cells on read; ignored there on write).
+__global__ void planes_m_kernel(MagComp C, int k0, int k1, int nx, int ny, float *bm, int to_handle)
+{
+    const int z0 = max(k0, C.z0), z1 = min(k1, C.z0 + C.bz);
+    const long long n = (long long)(z1 - z0) * C.by * C.bx;
+    const size_t P = (size_t)(k1 - k0), pl = (size_t)nx * ny;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const int li = (int)(q % C.bx), lj = (int)((q / C.bx) % C.by), k = z0 + (int)(q / ((long long)C.bx * C.by));
+        const int v = ((k - C.z0) * C.by + lj) * C.bx + li;
+        if (C.mat[v] == 0xFF) continue;
+        const size_t o = ((size_t)(k - k0) * ny + (C.y0 + lj)) * nx + (C.x0 + li);
+        for (int d = 0; d < 3; ++d) {
+            if (to_handle) C.m[(size_t)d * C.V + v] = bm[d * P * pl + o];
+            else bm[d * P * pl + o] = C.m[(size_t)d * C.V + v];
+        }
+    }
+}
+
+extern "C" int fdtd_llg_planes_device(fdtd_llg_t h, int32_t k0, int32_t k1, float *buf, size_t count, int32_t to_handle)
+{
+    if (!is_member(h)) return fail(h, FDTD_E_INVAL, "planes needs an instance handle");
+    Instance *I = inst_of(h);
+    Sim *S = h->sim;
+    if (!I->materials_set) return fail(h, FDTD_E_STATE, "set materials first");
+    const int nx = I->nx, ny = I->ny, nz = I->nz;
+    if (k0 < 0 || k1 > nz || k0 >= k1) return fail(h, FDTD_E_RANGE, "plane range outside the grid");
+    if (to_handle && I->has_pml())
+        return fail(h, FDTD_E_NOSYS, "planes cannot be written into a handle with absorbing layers (their memories are not exchanged)");
+    const size_t P = (size_t)(k1 - k0), pl = (size_t)nx * ny;
+    const size_t need = P * (9 * pl + nx + ny);
+    if (!buf || count < need) return fail(h, FDTD_E_INVAL, "buffer too small");
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, buf) != cudaSuccess || pa.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return fail(h, FDTD_E_INVAL, "planes_device needs a device buffer");
+    }
+    const size_t nf = I->n_field();
+    cudaStream_t st = S->stream;
+    const cudaMemcpyKind kind = cudaMemcpyDeviceToDevice;
+    for (int q = 0; q < 6; ++q) {
+        float *dev = I->fields[S->cur] + q * nf + (size_t)k0 * ny * I->px;
+        float *b = buf + q * P * pl;
+        if (to_handle)
+            CKR(h, cudaMemcpy2DAsync(dev, I->px * sizeof(float), b, nx * sizeof(float), nx * sizeof(float), P * ny, kind, st));
+        else
+            CKR(h, cudaMemcpy2DAsync(b, nx * sizeof(float), dev, I->px * sizeof(float), nx * sizeof(float), P * ny, kind, st));
+    }
+    float *hx = I->walls + (size_t)k0 * ny, *hy = I->walls + (size_t)ny * nz + (size_t)k0 * nx;
+    float *bx = buf + 6 * P * pl, *by = bx + P * ny;
+    if (to_handle) {
+        CKR(h, cudaMemcpyAsync(hx, bx, P * ny * sizeof(float), kind, st));
+        CKR(h, cudaMemcpyAsync(hy, by, P * nx * sizeof(float), kind, st));
+    } else {
+        CKR(h, cudaMemcpyAsync(bx, hx, P * ny * sizeof(float), kind, st));
+        CKR(h, cudaMemcpyAsync(by, hy, P * nx * sizeof(float), kind, st));
+    }
+    float *bm = buf + 6 * P * pl + P * (nx + ny);
+    if (!to_handle) CKR(h, cudaMemsetAsync(bm, 0, 3 * P * pl * sizeof(float), st));
+    for (const MagComp &C : I->comps) {
+        if (std::max(k0, C.z0) >= std::min(k1, C.z0 + C.bz)) continue;
+        planes_m_kernel<<<64, 256, 0, st>>>(C, k0, k1, nx, ny, bm, to_handle);
+        CKR(h, cudaGetLastError());
+    }
+    return FDTD_OK;
+}
+
 static size_t state_bytes(const Instance &I)
 {
     size_t b = sizeof(StateHeader) + 6 * (size_t)I.nx * I.ny * I.nz * sizeof(float);

@@ -12,8 +12,11 @@
 //   E pass: psi_E from that H^{n+1/2}; E^n += (cb/ca) [(1/kappa - 1) dH + psi_E],
 //           so that the sweep's ca E^n + cb curl H equals
 //           ca E^n + cb (curl H + the CPML terms).
-// Each thread owns one cell of the layers (its three edges and three faces),
-// so both passes write every value once and need no atomics.
+// Each pass is one kernel per lined axis (x, then y, then z), one thread per
+// cell of that axis's two slabs: it advances the axis's two memories of the
+// cell and adds the axis's terms to the cell's two components, so no value
+// is written by two threads of one kernel (no atomics), and a cell in the
+// layers of several axes takes their terms in a fixed order.
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -62,7 +65,8 @@ __host__ __device__ inline unsigned pml_index(int a, int s, int t, int d, int nx
 }
 
 // The H pass then the E pass of every lined instance on stream s, for field
-// buffer src (plain launches, two per instance; nothing when P is empty).
+// buffer src (plain launches, one per lined axis and pass; nothing when P is
+// empty).
 cudaError_t launch_pml(const PmlLaunch *P, int np, int src, bool cls16, cudaStream_t s);
 
 }  // namespace fl

@@ -1,6 +1,8 @@
-"""Host logic of runs over several GPUs, one process per GPU (torchrun): the
-partition of a batch's instances over the ranks and the whole-job rate.
-There is no collective on the data path: every rank advances its own grids.
+"""Runs over several GPUs, one process per GPU (torchrun): the partition of a
+batch's instances over the ranks (no collective on the data path: every rank
+advances its own grids), the whole-job rate, and one grid split into z-slabs
+(the paper's box decomposition) whose ghost planes are exchanged between
+device buffers after every step.
 """
 from __future__ import annotations
 
@@ -152,3 +154,65 @@ def exchange_halos(arrays: list, kinds: list, parts: list, rank: int, z_axes=Non
         if isinstance(item, tuple):
             t, ax, o, n, buf = item
             t.narrow(ax, o, n).copy_(buf)
+
+
+def slab_ghost(nz: int, world: int, magnetic_planes, llg_iterates: int = 0) -> int:
+    """Ghost planes per cut side for a z-slab split of nz planes over `world`
+    ranks: step_radius(llg_iterates) when a magnetic cell lies within that
+    distance of a cut (the Jacobi iterates of a region couple it across the
+    cut), else 3: one plane for the E push and one per H half-push."""
+    full = step_radius(llg_iterates)
+    cuts = [b for (_, b, _, _) in slab_partition(nz, world, 0)][:-1]
+    near = any(abs(k - c) <= full for k in magnetic_planes for c in cuts)
+    return full if near else step_radius(0)
+
+
+def _plane_buffer(slab, k0: int, k1: int):
+    """A buffer for the slab's local planes [k0, k1)."""
+    import torch
+
+    return torch.empty(slab.plane_floats(k0, k1), dtype=getattr(slab, "plane_dtype", torch.float32),
+                       device=getattr(slab, "device", "cuda"))
+
+
+def exchange_slab_planes(slab, parts: list, rank: int, group=None) -> None:
+    """Refresh this rank's ghost planes of one slab from their owners, buffer
+    to buffer: the owned planes that other ranks need are copied into buffers
+    on the slab's device (fdtd_llg_planes_device: queued on the handle's
+    stream, no host round trip), sent and received point-to-point in one
+    batch over the process group (NCCL between GPUs), and written into the
+    ghost planes.  slab: an instance handle (FdtdLlg) or any object with
+    plane_floats, read_planes_device and write_planes_device (and device,
+    plane_dtype for its buffers).  Every rank calls it after every step."""
+    import torch.distributed as dist
+
+    sends, recvs = halo_plan(parts, rank, "cell")
+    ea = parts[rank][2]
+    ops, keep, landing = [], [], []
+    for peer, k0, k1 in sends:
+        buf = _plane_buffer(slab, k0 - ea, k1 - ea)
+        slab.read_planes_device(k0 - ea, k1 - ea, buf)
+        keep.append(buf)
+        ops.append(dist.P2POp(dist.isend, buf, peer, group))
+    for peer, k0, k1 in recvs:
+        buf = _plane_buffer(slab, k0 - ea, k1 - ea)
+        ops.append(dist.P2POp(dist.irecv, buf, peer, group))
+        landing.append((k0, k1, buf))
+    if ops:
+        for req in dist.batch_isend_irecv(ops):
+            req.wait()
+    for k0, k1, buf in landing:
+        slab.write_planes_device(k0 - ea, k1 - ea, buf)
+
+
+def exchange_slab_planes_local(slabs: list, parts: list) -> None:
+    """The same exchange for slabs that all live in this process (one GPU,
+    one stream): each ghost range is copied from its owner's planes through a
+    device buffer.  Only owned planes are read and only ghost planes written,
+    so the order of the copies does not matter."""
+    for r, slab in enumerate(slabs):
+        _, recvs = halo_plan(parts, r, "cell")
+        for peer, k0, k1 in recvs:
+            buf = _plane_buffer(slabs[peer], k0 - parts[peer][2], k1 - parts[peer][2])
+            slabs[peer].read_planes_device(k0 - parts[peer][2], k1 - parts[peer][2], buf)
+            slab.write_planes_device(k0 - parts[r][2], k1 - parts[r][2], buf)

@@ -291,6 +291,28 @@ class FdtdLlg:
         check(_abi.load().fdtd_llg_planes(self._h, int(k0), int(k1), arr.ctypes.data_as(C.POINTER(C.c_float)),
                                           arr.size, 1), self._h)
 
+    def plane_floats(self, k0: int, k1: int) -> int:
+        """Floats of the stored state of z-planes [k0, k1) (layout of fdtd_llg_planes)."""
+        nx, ny, _ = self._dims
+        return (k1 - k0) * (9 * nx * ny + nx + ny)
+
+    def read_planes_device(self, k0: int, k1: int, out):
+        """Queue on the handle's stream a copy of the stored state of z-planes
+        [k0, k1) into `out` (a float32 CUDA tensor of plane_floats elements),
+        with no synchronisation."""
+        if not (out.is_cuda and out.dtype.is_floating_point and out.element_size() == 4 and out.is_contiguous()):
+            raise ValueError("out must be a contiguous float32 CUDA tensor")
+        check(_abi.load().fdtd_llg_planes_device(self._h, int(k0), int(k1), C.c_void_p(out.data_ptr()), out.numel(), 0),
+              self._h)
+
+    def write_planes_device(self, k0: int, k1: int, data):
+        """Queue on the handle's stream the overwrite of z-planes [k0, k1) from
+        `data` (a float32 CUDA tensor laid out as read_planes_device writes it)."""
+        if not (data.is_cuda and data.element_size() == 4 and data.is_contiguous()):
+            raise ValueError("data must be a contiguous float32 CUDA tensor")
+        check(_abi.load().fdtd_llg_planes_device(self._h, int(k0), int(k1), C.c_void_p(data.data_ptr()), data.numel(), 1),
+              self._h)
+
     def save_state(self) -> bytes:
         lib = _abi.load()
         n = C.c_size_t()

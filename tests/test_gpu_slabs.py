@@ -76,3 +76,38 @@ def test_planes_round_trip_and_errors():
         with pytest.raises(pkg.LLGError):
             sim.read_planes(k0, k1)
     sim.destroy()
+
+
+@pytest.mark.parametrize("world,far", [(2, False), (3, False), (2, True)])
+def test_gpu_slab_handles_exchange_device_buffers(world, far):
+    """The slabs as separate handles on one GPU whose ghost planes are
+    refreshed after every step through device buffers (fdtd_llg_planes_device:
+    queued copies on the handles' stream, no host round trip), with the ghost
+    width that slab_ghost gives (nine planes with a magnet at a cut, three
+    with none near one): the owned planes equal the undivided run to the bit."""
+    from paper_2510_22221_b300.distributed import exchange_slab_planes_local, slab_ghost
+    from tests.test_multirank import _far_magnet_workload
+
+    w = _far_magnet_workload() if far else _slab_workload()
+    mag = sorted({int(k) for k in np.nonzero(np.isin(w.mat_id, (3, 4)))[0]})
+    ghost = slab_ghost(w.nz, world, mag, _ITER)
+    assert ghost == (3 if far else 9)
+    parts = slab_partition(w.nz, world, ghost)
+    whole = pkg.from_workload(w, llg_fixed_iter=_ITER)
+    slabs = []
+    for (_, _, ea, eb) in parts:
+        s = _slab(w, ea, eb)
+        h = pkg.FdtdLlg.create(s.nx, s.ny, s.nz, s.dx, s.dy, s.dz, dt=whole.dt, llg_fixed_iter=_ITER,
+                               probe_capacity=w.steps)
+        pkg.configure(h, s)
+        slabs.append(h)
+    for _ in range(w.steps):
+        for h in slabs:
+            h.step(1)
+        whole.step(1)
+        exchange_slab_planes_local(slabs, parts)
+    for r, (a, b, ea, eb) in enumerate(parts):
+        np.testing.assert_array_equal(slabs[r].read_planes(a - ea, b - ea), whole.read_planes(a, b), err_msg=str(r))
+    np.testing.assert_array_equal(slabs[-1].get_field("Hz_wall"), whole.get_field("Hz_wall"))
+    for h in slabs:
+        h.destroy()

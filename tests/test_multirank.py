@@ -159,3 +159,101 @@ def test_halo_plan_covers_every_ghost_plane_once():
             sent = sorted((r, p, k0, k1) for r in range(world) for (p, k0, k1) in plans[r][0])
             recv = sorted((src, r, k0, k1) for r in range(world) for (src, k0, k1) in plans[r][1])
             assert sent == recv
+
+
+# ------------------------------------------- slabs through plane buffers
+
+class _OracleSlab:
+    """An oracle slab seen through the plane-buffer interface of the GPU
+    handles (plane_floats / read_planes_device / write_planes_device): the
+    planes [k0, k1) of every field and of M, flattened in a fixed order, in
+    CPU FP64 tensors."""
+    plane_dtype = None
+    device = "cpu"
+
+    def __init__(self, sim):
+        import torch
+
+        self.sim = sim
+        self.plane_dtype = torch.float64
+
+    def _views(self, k0, k1):
+        return [np.take(getattr(self.sim, n), range(k0, k1), axis=ax) for n, _, ax in _FIELDS]
+
+    def plane_floats(self, k0, k1):
+        return sum(v.size for v in self._views(k0, k1))
+
+    def read_planes_device(self, k0, k1, out):
+        import torch
+
+        out.copy_(torch.from_numpy(np.concatenate([v.ravel() for v in self._views(k0, k1)])))
+
+    def write_planes_device(self, k0, k1, data):
+        flat = data.numpy()
+        o = 0
+        for (n, _, ax), v in zip(_FIELDS, self._views(k0, k1)):
+            arr = getattr(self.sim, n)
+            idx = [slice(None)] * arr.ndim
+            idx[ax] = slice(k0, k1)
+            arr[tuple(idx)] = flat[o:o + v.size].reshape(v.shape)
+            o += v.size
+
+
+def _far_magnet_workload():
+    """The slab workload with its magnetic region moved away from the cuts
+    (z 2-4), so that three ghost planes are enough."""
+    import dataclasses
+
+    w = _slab_workload()
+    mid = w.mat_id.copy()
+    mid[mid == 3] = 0
+    mid[mid == 4] = 0
+    mid[2:5, 4:7, 5:9] = 3
+    return dataclasses.replace(w, mat_id=mid)
+
+
+def _buffer_worker(rank, world, port, far, out):
+    import torch.distributed as dist
+
+    from paper_2510_22221_b300.distributed import exchange_slab_planes, slab_ghost
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    w = _far_magnet_workload() if far else _slab_workload()
+    mag = sorted({int(k) for k in np.nonzero(np.isin(w.mat_id, (3, 4)))[0]})
+    parts = slab_partition(w.nz, world, slab_ghost(w.nz, world, mag, _ITER))
+    a, b, ea, eb = parts[rank]
+    sub = _OracleSlab(_slab_oracle(w, ea, eb))
+    for _ in range(w.steps):
+        sub.sim.run(1)
+        exchange_slab_planes(sub, parts, rank)
+    own = {}
+    for n, kind, ax in _FIELDS:
+        hi = b + 1 if kind == "face" and b == w.nz else b
+        own[n] = np.take(getattr(sub.sim, n), range(a - ea, hi - ea), axis=ax)
+    out[rank] = (own, parts[rank][2] - parts[rank][0] if rank else parts[rank][3] - parts[rank][1])
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,far", [(2, False), (3, False), (2, True)])
+def test_slab_plane_buffers_exchanged_point_to_point_equal_the_whole_grid(world, far):
+    """The exchange driver of the GPU slabs (owned planes into buffers, one
+    batch of point-to-point sends and receives, buffers into the ghost
+    planes), run on CPU ranks with oracle slabs: the owned planes equal the
+    undivided FP64 run to the bit, with nine ghost planes where a magnetic
+    region lies at a cut and three where none is near one."""
+    from tests.helpers import oracle_from_workload
+
+    w = _far_magnet_workload() if far else _slab_workload()
+    ref = oracle_from_workload(w, llg_fixed_iter=_ITER)
+    ref.run(w.steps)
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        mp.start_processes(_buffer_worker, args=(world, _free_port(), far, out), nprocs=world, start_method="spawn")
+        res = dict(out)
+    assert abs(res[0][1]) == (3 if far else 9)
+    for n, kind, ax in _FIELDS:
+        got = np.concatenate([res[r][0][n] for r in range(world)], axis=ax)
+        np.testing.assert_array_equal(got, getattr(ref, n), err_msg=n)
