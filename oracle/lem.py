@@ -154,7 +154,7 @@ def train_grad(theta_np, u_np, target_np, h_np, lam, kappa, alpha, h0, d, dt):
     (g,) = torch.autograd.grad(tot, theta)
     with torch.no_grad():
         rec, out = forward(theta, u, target.shape[0], d, dt)
-    return dict(total=float(tot), rec=float(lr), pred=float(lp), phy=float(lf), grad=g.numpy(),
+    return dict(total=float(tot.detach()), rec=float(lr.detach()), pred=float(lp.detach()), phy=float(lf.detach()), grad=g.numpy(),
                 recon=rec.numpy(), out=out.numpy())
 
 

@@ -1,4 +1,5 @@
-"""ctypes declarations of the C ABI in include/fdtd_llg.h (marshalling only)."""
+"""ctypes declarations of the C ABI in include/fdtd_llg.h and include/lem_surrogate.h
+(marshalling only)."""
 from __future__ import annotations
 
 import ctypes as C
@@ -36,6 +37,15 @@ class MaterialC(C.Structure):
 
 class Profile(C.Structure):
     _fields_ = [("launches", C.c_int64 * 3), ("ms", C.c_double * 3), ("cells", C.c_int64)]
+
+
+class LemShape(C.Structure):
+    _fields_ = [("d", C.c_int32), ("m", C.c_int32), ("batch", C.c_int32), ("t_in", C.c_int32),
+                ("t_out", C.c_int32), ("dt", C.c_float)]
+
+
+class LemPhysics(C.Structure):
+    _fields_ = [("lam", C.c_float), ("kappa", C.c_float), ("alpha", C.c_float), ("h0", C.c_float)]
 
 
 class LLGError(RuntimeError):
@@ -95,6 +105,17 @@ SIGNATURES = {
     "fdtd_llg_e_push_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.c_int32,
                                          C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
                                          _vp, _vp]),
+    "fdtd_llg_lem_param_count": (C.c_longlong, [C.c_int32, C.c_int32]),
+    "fdtd_llg_lem_workspace_bytes": (C.c_int, [C.POINTER(LemShape), C.POINTER(C.c_size_t)]),
+    "fdtd_llg_lem_views": (C.c_int, [C.POINTER(LemShape), _vp, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp),
+                                     C.POINTER(_vp)]),
+    "fdtd_llg_lem_forward": (C.c_int, [C.POINTER(LemShape), _vp, _vp, _vp, _vp]),
+    "fdtd_llg_lem_loss": (C.c_int, [C.POINTER(LemShape), C.POINTER(LemPhysics), _vp, _vp, _vp, _vp, _vp]),
+    "fdtd_llg_lem_backward": (C.c_int, [C.POINTER(LemShape), _vp, _vp, _vp, _vp]),
+    "fdtd_llg_lem_adam": (C.c_int, [C.c_longlong, _vp, _vp, _vp, _vp, C.c_float, C.c_float, C.c_float, C.c_float,
+                                    C.c_int32, _vp]),
+    "fdtd_llg_lem_train_step": (C.c_int, [C.POINTER(LemShape), C.POINTER(LemPhysics), _vp, _vp, _vp, _vp, _vp, _vp,
+                                          C.c_float, C.c_int32, _vp, _vp]),
     "fdtd_llg_destroy": (None, [_vp]),
     "fdtd_llg_last_error": (C.c_char_p, [_vp]),
     "fdtd_llg_abi_version": (C.c_int, []),

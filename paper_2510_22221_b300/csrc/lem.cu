@@ -1,0 +1,918 @@
+// Kernels of the physics-informed sequence surrogate (include/lem_surrogate.h):
+// the LEM encoder-decoder forward pass (Eq. discrete_lem), the data and
+// trapezoidal-LLG physics losses (Eqs. ml_tra1-3 with Eqs. llg_tra4-6), the
+// back-propagation through both stacks, the gate-gradient sums that give the
+// weight gradients, and Adam.
+//
+// Recurrent kernels.  One CTA advances kBT = 8 sequences through every step of
+// both stacks, with the two cells' weights of the stack in shared memory
+// (about 200 KB at D = 64) and the states beside them; 4 D threads, thread
+// (g, i) owning hidden unit i of sequences g and g + 4.  The time loop is
+// sequential, so a step costs a chain of dependent phases (gates and z, one
+// barrier, y, one barrier, per cell; the head) rather than bandwidth; the
+// batch is spread over ceil(batch / 8) CTAs.  Activations of every step are
+// saved (y, z, the two sigmoid gates and the two tanh values) for the
+// reverse pass.
+//
+// Weight gradients.  The reverse kernel stores the gradients of the four gate
+// pre-activations of every step; each weight gradient is then a sum over
+// (step, sequence) rows of an outer product with a saved activation, summed
+// by row chunks into partials and the partials in chunk order, so the result
+// is the same bits for any batch split.
+#include "../../include/fdtd_llg.h"
+#include "../../include/lem_surrogate.h"
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <vector>
+
+namespace fl {
+void set_last_error(const char *msg);
+}
+
+namespace {
+
+constexpr int kG = 4;            // sequence groups per CTA
+constexpr int kR = 2;            // sequences per thread
+constexpr int kBT = kG * kR;     // sequences per CTA
+constexpr int kMMax = 4;         // largest input / output width
+constexpr int kQ = 6;            // saved values per unit and step: y, z, s1, s2, tz, ty
+constexpr int kKC = 2048;        // rows per chunk of the weight-gradient sums
+constexpr int kLossThreads = 256;
+
+__host__ __device__ inline long long cell_params(int d, int mc) { return 4LL * d * d + 4LL * d * mc + 4LL * d; }
+__host__ __device__ inline int cell_width(int c, int m, int d) { return (c & 1) ? d : m; }
+// offset of cell c (0 enc0, 1 enc1, 2 dec0, 3 dec1); c = 4: the head Wo
+__host__ __device__ inline long long cell_offset(int c, int d, int m)
+{
+    long long o = 0;
+    for (int q = 0; q < c; ++q) o += cell_params(d, cell_width(q, m, d));
+    return o;
+}
+
+__device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+// Work-space layout (offsets in bytes, 256-aligned)
+struct Layout {
+    size_t act[2][2];   // [phase][layer] -> [T_ph + 1][B][kQ][D]
+    size_t dg[2][2];    // [phase][layer] -> [T_ph][B][4][D]
+    size_t xdec;        // [t_out][B][m] decoder inputs
+    size_t recon, out, drec, dout, dot;
+    size_t lpart, loss; // per-block loss partials [nblk][3] (double), losses [4] (double)
+    size_t grad;        // [P] float
+    size_t wpart;       // weight-gradient partials (float)
+    size_t total;
+    int nlblk;
+    long long nwpart;
+};
+
+struct WProd {
+    const float *A, *A2, *B, *B2;   // B == nullptr: the constant 1
+    long long lda, ldb, K1, K;
+    int aoff, boff, R, J;
+    long long goff, poff;
+    int chunk0, nchunk;
+};
+constexpr int kMaxProd = 17;
+struct WProdSet {
+    WProd p[kMaxProd];
+    int np, nchunks;
+};
+
+bool shape_ok(const fdtd_llg_lem_shape *s)
+{
+    return s && (s->d == 16 || s->d == 32 || s->d == 64) && s->m >= 1 && s->m <= kMMax && s->batch >= 1 &&
+           s->t_in >= 1 && s->t_out >= 1 && (long long)s->t_in + s->t_out <= 65536 && s->dt > 0.f &&
+           std::isfinite(s->dt);
+}
+
+size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+Layout layout(const fdtd_llg_lem_shape *s)
+{
+    Layout L{};
+    const size_t B = s->batch, D = s->d, m = s->m;
+    const size_t T[2] = {(size_t)s->t_in, (size_t)s->t_out};
+    size_t o = 0;
+    for (int ph = 0; ph < 2; ++ph)
+        for (int l = 0; l < 2; ++l) {
+            L.act[ph][l] = o;
+            o += al((T[ph] + 1) * B * kQ * D * sizeof(float));
+        }
+    for (int ph = 0; ph < 2; ++ph)
+        for (int l = 0; l < 2; ++l) {
+            L.dg[ph][l] = o;
+            o += al(T[ph] * B * 4 * D * sizeof(float));
+        }
+    L.xdec = o; o += al(T[1] * B * m * sizeof(float));
+    L.recon = o; o += al(T[0] * B * m * sizeof(float));
+    L.out = o; o += al(T[1] * B * m * sizeof(float));
+    L.drec = o; o += al(T[0] * B * m * sizeof(float));
+    L.dout = o; o += al(T[1] * B * m * sizeof(float));
+    L.dot = o; o += al(T[1] * B * m * sizeof(float));
+    const size_t nl = (T[0] * B * m + T[1] * B + kLossThreads - 1) / kLossThreads;
+    L.nlblk = (int)nl;
+    L.lpart = o; o += al(nl * 3 * sizeof(double));
+    L.loss = o; o += al(4 * sizeof(double));
+    L.grad = o; o += al((size_t)fdtd_llg_lem_param_count(s->d, s->m) * sizeof(float));
+    // partials: per product ceil(K / kKC) chunks of R x J
+    long long np = 0;
+    for (int ph = 0; ph < 2; ++ph) {
+        const long long K = (long long)T[ph] * B, nc = (K + kKC - 1) / kKC;
+        for (int l = 0; l < 2; ++l) {
+            const long long mc = l ? D : m;
+            np += nc * (3 * D * D + D * D + 4 * D * mc + 4 * D);
+        }
+    }
+    np += ((long long)(T[0] + T[1]) * B + kKC - 1) / kKC * (long long)(m * D);
+    L.nwpart = np;
+    L.wpart = o; o += al((size_t)np * sizeof(float));
+    L.total = o;
+    return L;
+}
+
+struct LemArgs {
+    int B, m, t_in, t_out;
+    float dt;
+    const float *theta, *u;
+    unsigned char *w;   // work space base
+    Layout L;
+};
+
+template <typename T>
+__device__ __forceinline__ T *wp(const LemArgs &A, size_t off)
+{
+    return reinterpret_cast<T *>(A.w + off);
+}
+
+}  // namespace
+
+namespace {
+
+// Shared-memory floats of the recurrent kernels for width D
+template <int D>
+constexpr int fwd_smem_floats()
+{
+    return 3 * 4 * D * D + 4 * kMMax * D + 2 * 4 * D + kMMax * D + 2 * 2 * kBT * D + kBT * kMMax;
+}
+template <int D>
+constexpr int bwd_smem_floats()
+{
+    return 3 * 4 * D * D + 4 * kMMax * D + kMMax * D + 2 * 4 * kBT * D + 2 * kBT * kMMax;
+}
+
+// Weights of cell c into shared memory.  TR: W and V transposed ([q][j][i],
+// unit i fastest, for the forward products W y), else as stored ([q][i][j],
+// for the reverse products W^T g).  V goes to V1 (width D) or V0 (width m).
+template <int D, bool TR>
+__device__ void load_cell(const float *theta, int c, int m, float *W, float *V, float *bb)
+{
+    const int mc = (c & 1) ? D : m;
+    const float *src = theta + cell_offset(c, D, m);
+    for (int e = threadIdx.x; e < 4 * D * D; e += blockDim.x) {
+        const int q = e / (D * D), r = e % (D * D), i = r / D, j = r % D;
+        W[TR ? (q * D + j) * D + i : e] = src[e];
+    }
+    src += 4 * D * D;
+    for (int e = threadIdx.x; e < 4 * D * mc; e += blockDim.x) {
+        const int q = e / (D * mc), r = e % (D * mc), i = r / mc, j = r % mc;
+        V[TR ? (q * mc + j) * D + i : e] = src[e];
+    }
+    src += 4 * D * mc;
+    if (bb)
+        for (int e = threadIdx.x; e < 4 * D; e += blockDim.x) bb[e] = src[e];
+}
+
+// Forward pass of kBT sequences (see the file comment).  Thread (g, i) =
+// (tid / D, tid % D) owns unit i of sequences g and g + kG.
+template <int D>
+__global__ void __launch_bounds__(kG *D, 1) lem_fwd_kernel(LemArgs A)
+{
+    extern __shared__ float sm[];
+    float *WT0 = sm, *WT1 = WT0 + 4 * D * D, *VT1 = WT1 + 4 * D * D, *VT0 = VT1 + 4 * D * D;
+    float *bb0 = VT0 + 4 * kMMax * D, *bb1 = bb0 + 4 * D, *Wo = bb1 + 4 * D;
+    float *Y = Wo + kMMax * D, *Z = Y + 2 * kBT * D, *X = Z + 2 * kBT * D;
+    const int tid = threadIdx.x, i = tid % D, g = tid / D, m = A.m, B = A.B;
+    const int b0 = blockIdx.x * kBT;
+    const float dt = A.dt;
+    for (int e = tid; e < m * D; e += blockDim.x) Wo[e] = A.theta[cell_offset(4, D, m) + e];
+    for (int e = tid; e < 2 * kBT * D; e += blockDim.x) Y[e] = Z[e] = 0.f;
+    for (int ph = 0; ph < 2; ++ph) {
+        const int T = ph ? A.t_out : A.t_in;
+        float *act[2] = {wp<float>(A, A.L.act[ph][0]), wp<float>(A, A.L.act[ph][1])};
+        float *res = wp<float>(A, ph ? A.L.out : A.L.recon);
+        float *xdec = wp<float>(A, A.L.xdec);
+        __syncthreads();   // the previous phase is done with the weights
+        load_cell<D, true>(A.theta, 2 * ph, m, WT0, VT0, bb0);
+        load_cell<D, true>(A.theta, 2 * ph + 1, m, WT1, VT1, bb1);
+        // the first input: u_0 (encoder) or 0 (decoder)
+        for (int t = tid; t < kBT * m; t += blockDim.x) {
+            const int s = t / m, c = t % m, b = b0 + s;
+            const float v = (ph == 0 && b < B) ? A.u[(long long)b * m + c] : 0.f;
+            X[s * kMMax + c] = v;
+            if (ph == 1 && b < B) xdec[(long long)b * m + c] = 0.f;
+        }
+        // slot 0 of the saved activations: the initial states
+        for (int l = 0; l < 2; ++l)
+            for (int r = 0; r < kR; ++r) {
+                const int s = g + kG * r, b = b0 + s;
+                if (b < B) {
+                    float *a = act[l] + (long long)b * kQ * D + i;
+                    a[0] = Y[(l * kBT + s) * D + i];
+                    a[D] = Z[(l * kBT + s) * D + i];
+                }
+            }
+        __syncthreads();
+        for (int n = 0; n < T; ++n) {
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+                const float *WT = l ? WT1 : WT0, *VT = l ? VT1 : VT0, *bb = l ? bb1 : bb0;
+                const int mi = l ? D : m, xs = l ? D : kMMax;
+                const float *xin = l ? Y : X;   // layer 1 reads layer 0's y_n
+                float s1[kR], s2[kR], tz[kR], ay[kR], yp[kR], zn[kR];
+#pragma unroll
+                for (int r = 0; r < kR; ++r) {
+                    const int s = g + kG * r;
+                    float a1 = bb[i], a2 = bb[D + i], az = bb[2 * D + i], a4 = bb[3 * D + i];
+                    const float *x = xin + s * xs;
+                    for (int c = 0; c < mi; ++c) {
+                        const float xv = x[c];
+                        a1 = fmaf(VT[(0 * mi + c) * D + i], xv, a1);
+                        a2 = fmaf(VT[(1 * mi + c) * D + i], xv, a2);
+                        az = fmaf(VT[(2 * mi + c) * D + i], xv, az);
+                        a4 = fmaf(VT[(3 * mi + c) * D + i], xv, a4);
+                    }
+                    const float *yv = Y + (l * kBT + s) * D;
+#pragma unroll 8
+                    for (int j = 0; j < D; ++j) {
+                        const float yj = yv[j];
+                        a1 = fmaf(WT[(0 * D + j) * D + i], yj, a1);
+                        a2 = fmaf(WT[(1 * D + j) * D + i], yj, a2);
+                        az = fmaf(WT[(2 * D + j) * D + i], yj, az);
+                    }
+                    yp[r] = yv[i];
+                    const float zp = Z[(l * kBT + s) * D + i];
+                    s1[r] = sigm(a1);
+                    s2[r] = sigm(a2);
+                    tz[r] = tanhf(az);
+                    const float h1 = dt * s1[r];
+                    zn[r] = fmaf(h1, tz[r], (1.f - h1) * zp);
+                    ay[r] = a4;
+                }
+                __syncthreads();   // every read of this cell's y_{n-1} and input is done
+#pragma unroll
+                for (int r = 0; r < kR; ++r) Z[(l * kBT + g + kG * r) * D + i] = zn[r];
+                __syncthreads();
+#pragma unroll
+                for (int r = 0; r < kR; ++r) {
+                    const int s = g + kG * r, b = b0 + s;
+                    const float *zv = Z + (l * kBT + s) * D;
+                    float a4 = ay[r];
+#pragma unroll 8
+                    for (int j = 0; j < D; ++j) a4 = fmaf(WT[(3 * D + j) * D + i], zv[j], a4);
+                    const float ty = tanhf(a4), h2 = dt * s2[r];
+                    const float yn = fmaf(h2, ty, (1.f - h2) * yp[r]);
+                    Y[(l * kBT + s) * D + i] = yn;
+                    if (b < B) {
+                        float *a = act[l] + ((long long)(n + 1) * B + b) * kQ * D + i;
+                        a[0] = yn;
+                        a[D] = zn[r];
+                        a[2 * D] = s1[r];
+                        a[3 * D] = s2[r];
+                        a[4 * D] = tz[r];
+                        a[5 * D] = ty;
+                    }
+                }
+                __syncthreads();
+            }
+            // the head: o = Wo y of the top cell; the next input
+            for (int t = tid; t < kBT * m; t += blockDim.x) {
+                const int s = t / m, c = t % m, b = b0 + s;
+                const float *yv = Y + (kBT + s) * D;
+                float o = 0.f;
+                for (int k = 0; k < D; ++k) o = fmaf(Wo[c * D + k], yv[k], o);
+                if (b < B) res[((long long)n * B + b) * m + c] = o;
+                if (n + 1 < T) {
+                    float x;
+                    if (ph == 0) x = b < B ? A.u[((long long)(n + 1) * B + b) * m + c] : 0.f;
+                    else {
+                        x = o;
+                        if (b < B) xdec[((long long)(n + 1) * B + b) * m + c] = o;
+                    }
+                    X[s * kMMax + c] = x;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace
+
+namespace {
+
+// ------------------------------------------------------------------ losses
+// A value with its derivatives along two directions (p and q): forward-mode
+// differentiation of the trapezoidal LLG map for the physics-loss gradient.
+struct Dual {
+    float v, a, b;
+};
+__device__ __forceinline__ Dual dmk(float v) { return {v, 0.f, 0.f}; }
+__device__ __forceinline__ Dual operator+(Dual x, Dual y) { return {x.v + y.v, x.a + y.a, x.b + y.b}; }
+__device__ __forceinline__ Dual operator-(Dual x, Dual y) { return {x.v - y.v, x.a - y.a, x.b - y.b}; }
+__device__ __forceinline__ Dual operator-(Dual x) { return {-x.v, -x.a, -x.b}; }
+__device__ __forceinline__ Dual operator*(Dual x, Dual y) { return {x.v * y.v, x.a * y.v + x.v * y.a, x.b * y.v + x.v * y.b}; }
+__device__ __forceinline__ Dual operator*(float s, Dual x) { return {s * x.v, s * x.a, s * x.b}; }
+__device__ __forceinline__ Dual operator/(Dual x, Dual y)
+{
+    const float r = 1.f / y.v, q = x.v * r;
+    return {q, (x.a - q * y.a) * r, (x.b - q * y.b) * r};
+}
+__device__ __forceinline__ Dual dsqrt(Dual x)
+{
+    const float s = sqrtf(x.v), h = 0.5f / s;
+    return {s, x.a * h, x.b * h};
+}
+__device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ float mkv(float v, float) { return v; }
+__device__ __forceinline__ Dual mkv(float v, Dual) { return dmk(v); }
+
+// One trapezoidal LLG step of m = (p, q, 1) (Eqs. llg_tra4-6): a = -(kappa
+// H^{k+1} + alpha m), b = m - kappa m x H^k, M~ = (b + (a.b) a - a x b) /
+// (1 + |a|^2), normalised to |m|; returns its two transverse components.
+template <typename T>
+__device__ void llg_map(T p, T q, const float *hk, const float *hk1, float kappa, float alpha, float h0, T &Fp, T &Fq)
+{
+    const T one = mkv(1.f, p);
+    const float H0x = hk[0], H0y = hk[1], H0z = hk[2] + h0;
+    const float H1x = hk1[0], H1y = hk1[1], H1z = hk1[2] + h0;
+    // m x H^k
+    const T cx = q * mkv(H0z, p) - one * mkv(H0y, p);
+    const T cy = one * mkv(H0x, p) - p * mkv(H0z, p);
+    const T cz = p * mkv(H0y, p) - q * mkv(H0x, p);
+    const T bx = p - kappa * cx, by = q - kappa * cy, bz = one - kappa * cz;
+    const T ax = -(mkv(kappa * H1x, p) + alpha * p), ay = -(mkv(kappa * H1y, p) + alpha * q),
+            az = -(mkv(kappa * H1z, p) + alpha * one);
+    const T ab = ax * bx + ay * by + az * bz;
+    const T den = one + ax * ax + ay * ay + az * az;
+    // a x b
+    const T xx = ay * bz - az * by, xy = az * bx - ax * bz, xz = ax * by - ay * bx;
+    const T mx = (bx + ab * ax - xx) / den, my = (by + ab * ay - xy) / den, mz = (bz + ab * az - xz) / den;
+    const T s = dsqrt(p * p + q * q + one) / dsqrt(mx * mx + my * my + mz * mz);
+    Fp = mx * s;
+    Fq = my * s;
+}
+
+__device__ double block_sum_d(double v, double *sh)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int q = 0; q < nw; ++q) t += sh[q];   // the same order in every thread
+    return t;
+}
+
+struct LossArgs {
+    int B, m, t_in, t_out;
+    float lam, kappa, alpha, h0;
+    const float *u, *target, *h, *recon, *out;
+    float *drec, *dout;
+    double *lpart;
+};
+
+// One thread per reconstructed value, then one per (predicted step,
+// sequence).  Per-block sums of the three losses go to lpart in block order.
+__global__ void __launch_bounds__(kLossThreads) lem_loss_kernel(LossArgs A)
+{
+    __shared__ double sh[kLossThreads / 32];
+    const long long NR = (long long)A.t_in * A.B * A.m, NP = (long long)A.t_out * A.B;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double lr = 0.0, lp = 0.0, lf = 0.0;
+    if (t < NR) {
+        const float e = A.recon[t] - A.u[t];
+        lr = (double)e * e;
+        A.drec[t] = 2.f * e / (float)NR;
+    } else if (t < NR + NP) {
+        const long long q = t - NR;
+        const int k = (int)(q / A.B), m = A.m;
+        const long long o = q * m;
+        float dv[kMMax];
+        for (int c = 0; c < m; ++c) {
+            const float e = A.out[o + c] - A.target[o + c];
+            lp += (double)e * e;
+            dv[c] = 2.f * e / (float)(NP * m);
+        }
+        if (m == 2 && A.t_out > 1 && A.h) {
+            const float cf = A.lam / (float)((long long)(A.t_out - 1) * A.B);
+            const float *hk = A.h + q * 3;
+            if (k + 1 < A.t_out) {   // pair (k, k+1): residual and its derivative in o_k
+                Dual Fp, Fq;
+                llg_map(Dual{A.out[o], 1.f, 0.f}, Dual{A.out[o + 1], 0.f, 1.f}, hk, hk + (long long)A.B * 3, A.kappa,
+                        A.alpha, A.h0, Fp, Fq);
+                const float rp = Fp.v - A.out[o + (long long)A.B * m], rq = Fq.v - A.out[o + (long long)A.B * m + 1];
+                lf = ((double)rp * rp + (double)rq * rq) / (2.0 * (double)(A.t_out - 1) * A.B);
+                dv[0] += cf * (Fp.a * rp + Fq.a * rq);
+                dv[1] += cf * (Fp.b * rp + Fq.b * rq);
+            }
+            if (k >= 1) {   // pair (k-1, k): the residual's direct term in o_k
+                const long long op = o - (long long)A.B * m;
+                float Fp, Fq;
+                llg_map(A.out[op], A.out[op + 1], hk - (long long)A.B * 3, hk, A.kappa, A.alpha, A.h0, Fp, Fq);
+                dv[0] -= cf * (Fp - A.out[o]);
+                dv[1] -= cf * (Fq - A.out[o + 1]);
+            }
+        }
+        for (int c = 0; c < m; ++c) A.dout[o + c] = dv[c];
+    }
+    lr = block_sum_d(lr, sh);
+    lp = block_sum_d(lp, sh);
+    lf = block_sum_d(lf, sh);
+    if (threadIdx.x == 0) {
+        A.lpart[3 * blockIdx.x] = lr;
+        A.lpart[3 * blockIdx.x + 1] = lp;
+        A.lpart[3 * blockIdx.x + 2] = lf;
+    }
+}
+
+// The four losses from the block partials, summed in block order.
+__global__ void lem_loss_final_kernel(const double *lpart, int nblk, long long NR, long long NPM, double lam,
+                                      double *loss)
+{
+    __shared__ double sh[kLossThreads / 32];
+    double s[3];
+    for (int c = 0; c < 3; ++c) {
+        double v = 0.0;
+        for (int q = threadIdx.x; q < nblk; q += blockDim.x) v += lpart[3 * q + c];
+        s[c] = block_sum_d(v, sh);
+    }
+    if (threadIdx.x == 0) {
+        const double r = s[0] / (double)NR, p = s[1] / (double)NPM;
+        loss[0] = r + p + lam * s[2];
+        loss[1] = r;
+        loss[2] = p;
+        loss[3] = s[2];
+    }
+}
+
+}  // namespace
+
+namespace {
+
+// ---------------------------------------------------------------- reverse
+// Back-propagation through both stacks for kBT sequences: the decoder's steps
+// in reverse (with the output feedback: the gradient of step k's input is
+// added to the gradient of output k-1), then the encoder's.  Thread (g, i)
+// carries dL/dy and dL/dz of unit i of its two sequences for both cells in
+// registers; the gate gradients of each step go to shared memory for the
+// products with W^T and V^T and to the work space for the weight sums.
+template <int D>
+__global__ void __launch_bounds__(kG *D, 1) lem_bwd_kernel(LemArgs A)
+{
+    extern __shared__ float sm[];
+    float *W0 = sm, *W1 = W0 + 4 * D * D, *V1 = W1 + 4 * D * D, *V0 = V1 + 4 * D * D;
+    float *Wo = V0 + 4 * kMMax * D, *DG = Wo + kMMax * D;   // DG [2][4][kBT][D]
+    float *DO = DG + 2 * 4 * kBT * D, *FB = DO + kBT * kMMax;
+    const int tid = threadIdx.x, i = tid % D, g = tid / D, m = A.m, B = A.B;
+    const int b0 = blockIdx.x * kBT;
+    const float dt = A.dt;
+    for (int e = tid; e < m * D; e += blockDim.x) Wo[e] = A.theta[cell_offset(4, D, m) + e];
+    for (int e = tid; e < kBT * kMMax; e += blockDim.x) FB[e] = 0.f;
+    float dy[2][kR], dz[2][kR];
+#pragma unroll
+    for (int l = 0; l < 2; ++l)
+#pragma unroll
+        for (int r = 0; r < kR; ++r) dy[l][r] = dz[l][r] = 0.f;
+    for (int ph = 1; ph >= 0; --ph) {
+        const int T = ph ? A.t_out : A.t_in;
+        const float *act[2] = {wp<float>(A, A.L.act[ph][0]), wp<float>(A, A.L.act[ph][1])};
+        float *dgo[2] = {wp<float>(A, A.L.dg[ph][0]), wp<float>(A, A.L.dg[ph][1])};
+        const float *dsrc = wp<float>(A, ph ? A.L.dout : A.L.drec);
+        float *dot = wp<float>(A, A.L.dot);
+        __syncthreads();   // the previous phase is done with the weights
+        load_cell<D, false>(A.theta, 2 * ph, m, W0, V0, nullptr);
+        load_cell<D, false>(A.theta, 2 * ph + 1, m, W1, V1, nullptr);
+        __syncthreads();
+        for (int n = T - 1; n >= 0; --n) {
+            // gradient at the head's output: the loss's, plus (decoder) the
+            // feedback from step n+1's input
+            for (int t = tid; t < kBT * m; t += blockDim.x) {
+                const int s = t / m, c = t % m, b = b0 + s;
+                float v = 0.f;
+                if (b < B) {
+                    v = dsrc[((long long)n * B + b) * m + c];
+                    if (ph) {
+                        v += FB[s * kMMax + c];
+                        dot[((long long)n * B + b) * m + c] = v;
+                    }
+                }
+                DO[s * kMMax + c] = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < kR; ++r) {
+                const int s = g + kG * r;
+                float a = dy[1][r];
+                for (int c = 0; c < m; ++c) a = fmaf(Wo[c * D + i], DO[s * kMMax + c], a);
+                dy[1][r] = a;
+            }
+#pragma unroll
+            for (int l = 1; l >= 0; --l) {
+                const float *W = l ? W1 : W0;
+                float *dgl = DG + l * 4 * kBT * D;
+                float yp[kR], zp[kR], S1[kR], TZ[kR], dg2[kR], dyp[kR];
+#pragma unroll
+                for (int r = 0; r < kR; ++r) {
+                    const int s = g + kG * r, b = min(b0 + s, B - 1);
+                    const float *a0 = act[l] + ((long long)n * B + b) * kQ * D + i;        // slot n: y_{n-1}, z_{n-1}
+                    const float *a1 = act[l] + ((long long)(n + 1) * B + b) * kQ * D + i;  // slot n+1: this step
+                    yp[r] = a0[0];
+                    zp[r] = a0[D];
+                    S1[r] = a1[2 * D];
+                    const float S2 = a1[3 * D];
+                    TZ[r] = a1[4 * D];
+                    const float TY = a1[5 * D];
+                    const float gy = dy[l][r];
+                    dg2[r] = gy * (TY - yp[r]) * dt * S2 * (1.f - S2);
+                    dgl[(3 * kBT + s) * D + i] = gy * dt * S2 * (1.f - TY * TY);
+                    dyp[r] = gy * (1.f - dt * S2);
+                }
+                __syncthreads();
+                float dzp[kR];
+#pragma unroll
+                for (int r = 0; r < kR; ++r) {
+                    const int s = g + kG * r, b = b0 + s;
+                    const float *gy = dgl + (3 * kBT + s) * D;
+                    float dzt = dz[l][r];
+#pragma unroll 8
+                    for (int k = 0; k < D; ++k) dzt = fmaf(W[(3 * D + k) * D + i], gy[k], dzt);
+                    const float dg1 = dzt * (TZ[r] - zp[r]) * dt * S1[r] * (1.f - S1[r]);
+                    const float dgz = dzt * dt * S1[r] * (1.f - TZ[r] * TZ[r]);
+                    dzp[r] = dzt * (1.f - dt * S1[r]);
+                    dgl[(0 * kBT + s) * D + i] = dg1;
+                    dgl[(1 * kBT + s) * D + i] = dg2[r];
+                    dgl[(2 * kBT + s) * D + i] = dgz;
+                    if (b < B) {
+                        float *o = dgo[l] + ((long long)n * B + b) * 4 * D + i;
+                        o[0] = dg1;
+                        o[D] = dg2[r];
+                        o[2 * D] = dgz;
+                        o[3 * D] = gy[i];
+                    }
+                }
+                __syncthreads();
+#pragma unroll
+                for (int r = 0; r < kR; ++r) {
+                    const int s = g + kG * r;
+                    const float *g1 = dgl + (0 * kBT + s) * D, *g2 = dgl + (1 * kBT + s) * D, *gz = dgl + (2 * kBT + s) * D;
+                    float a = dyp[r];
+#pragma unroll 8
+                    for (int k = 0; k < D; ++k) {
+                        a = fmaf(W[(0 * D + k) * D + i], g1[k], a);
+                        a = fmaf(W[(1 * D + k) * D + i], g2[k], a);
+                        a = fmaf(W[(2 * D + k) * D + i], gz[k], a);
+                    }
+                    dy[l][r] = a;
+                    dz[l][r] = dzp[r];
+                    if (l == 1) {   // the input of cell 1 is cell 0's y_n
+                        const float *gy = dgl + (3 * kBT + s) * D;
+                        float x = 0.f;
+#pragma unroll 8
+                        for (int k = 0; k < D; ++k) {
+                            x = fmaf(V1[(0 * D + k) * D + i], g1[k], x);
+                            x = fmaf(V1[(1 * D + k) * D + i], g2[k], x);
+                            x = fmaf(V1[(2 * D + k) * D + i], gz[k], x);
+                            x = fmaf(V1[(3 * D + k) * D + i], gy[k], x);
+                        }
+                        dy[0][r] += x;
+                    }
+                }
+            }
+            // decoder: the gradient of this step's input (the previous output)
+            if (ph)
+                for (int t = tid; t < kBT * m; t += blockDim.x) {
+                    const int s = t / m, c = t % m;
+                    float x = 0.f;
+                    for (int q = 0; q < 4; ++q) {
+                        const float *gq = DG + (q * kBT + s) * D;
+                        for (int k = 0; k < D; ++k) x = fmaf(V0[(q * D + k) * m + c], gq[k], x);
+                    }
+                    FB[s * kMMax + c] = x;
+                }
+        }
+    }
+}
+
+}  // namespace
+
+namespace {
+
+// --------------------------------------------------------- weight sums
+// Partial sums over one chunk of kKC rows of one product: C[r][j] =
+// sum_k A[k][aoff + r] B[k][boff + j] (B absent: 1), rows k >= K1 from the
+// second segment.  Thread (rt, jt) accumulates an 8 x 8 block.
+__global__ void __launch_bounds__(256) lem_wgrad_kernel(WProdSet S, float *part)
+{
+    __shared__ float sa[32][4 * 64 + 1];
+    __shared__ float sb[32][64 + 1];
+    int p = 0;
+    while (p + 1 < S.np && (int)blockIdx.x >= S.p[p + 1].chunk0) ++p;
+    const WProd &P = S.p[p];
+    const int chunk = blockIdx.x - P.chunk0, tid = threadIdx.x;
+    const long long k0 = (long long)chunk * kKC, k1 = min(k0 + kKC, P.K);
+    const int RT = (P.R + 7) / 8, JT = (P.J + 7) / 8, rt = tid % RT, jt = tid / RT;
+    const bool act = tid < RT * JT;
+    float acc[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+    for (long long kb = k0; kb < k1; kb += 32) {
+        const int nk = (int)min(32LL, k1 - kb);
+        for (int e = tid; e < nk * P.R; e += blockDim.x) {
+            const int kk = e / P.R, r = e % P.R;
+            const long long row = kb + kk;
+            const float *src = row < P.K1 ? P.A + row * P.lda : P.A2 + (row - P.K1) * P.lda;
+            sa[kk][r] = src[P.aoff + r];
+        }
+        for (int e = tid; e < nk * P.J; e += blockDim.x) {
+            const int kk = e / P.J, j = e % P.J;
+            const long long row = kb + kk;
+            float v = 1.f;
+            if (P.B) {
+                const float *src = row < P.K1 ? P.B + row * P.ldb : P.B2 + (row - P.K1) * P.ldb;
+                v = src[P.boff + j];
+            }
+            sb[kk][j] = v;
+        }
+        __syncthreads();
+        if (act)
+            for (int kk = 0; kk < nk; ++kk) {
+                float av[8], bv[8];
+#pragma unroll
+                for (int a = 0; a < 8; ++a) av[a] = (rt * 8 + a < P.R) ? sa[kk][rt * 8 + a] : 0.f;
+#pragma unroll
+                for (int b = 0; b < 8; ++b) bv[b] = (jt * 8 + b < P.J) ? sb[kk][jt * 8 + b] : 0.f;
+#pragma unroll
+                for (int a = 0; a < 8; ++a)
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+            }
+        __syncthreads();
+    }
+    if (!act) return;
+    float *o = part + P.poff + (long long)chunk * P.R * P.J;
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const int r = rt * 8 + a, j = jt * 8 + b;
+            if (r < P.R && j < P.J) o[(long long)r * P.J + j] = acc[a][b];
+        }
+}
+
+// Every output of every product: the sum of its chunk partials in chunk
+// order, into the gradient vector.
+__global__ void lem_wreduce_kernel(WProdSet S, const float *part, float *grad)
+{
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int p = 0; p < S.np; ++p) {
+        const WProd &P = S.p[p];
+        const long long n = (long long)P.R * P.J;
+        if (e < n) {
+            float s = 0.f;
+            for (int c = 0; c < P.nchunk; ++c) s += part[P.poff + c * n + e];
+            grad[P.goff + e] = s;
+            return;
+        }
+        e -= n;
+    }
+}
+
+__global__ void lem_adam_kernel(long long n, float *th, const float *g, float *mo, float *ve, float lr, float b1,
+                                float b2, float eps, float c1, float c2)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const float gq = g[q];
+    const float mq = fmaf(b1, mo[q], (1.f - b1) * gq);
+    const float vq = fmaf(b2, ve[q], (1.f - b2) * gq * gq);
+    mo[q] = mq;
+    ve[q] = vq;
+    th[q] -= lr * (mq / c1) / (sqrtf(vq / c2) + eps);
+}
+
+int fail(int code, const char *msg)
+{
+    fl::set_last_error(msg);
+    return code;
+}
+int cuda_fail(cudaError_t e, const char *where)
+{
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s: %s", where, cudaGetErrorString(e));
+    fl::set_last_error(buf);
+    return FDTD_E_CUDA;
+}
+
+LemArgs args(const fdtd_llg_lem_shape *s, const float *theta, const float *u, void *work)
+{
+    LemArgs A{};
+    A.B = s->batch;
+    A.m = s->m;
+    A.t_in = s->t_in;
+    A.t_out = s->t_out;
+    A.dt = s->dt;
+    A.theta = theta;
+    A.u = u;
+    A.w = static_cast<unsigned char *>(work);
+    A.L = layout(s);
+    return A;
+}
+
+WProdSet products(const fdtd_llg_lem_shape *s, const LemArgs &A)
+{
+    WProdSet S{};
+    const int D = s->d, m = s->m, B = s->batch;
+    const long long rowq = (long long)kQ * D;
+    auto f = [&](size_t off) { return reinterpret_cast<const float *>(A.w + off); };
+    long long poff = 0;
+    int chunk0 = 0;
+    auto add = [&](WProd P) {
+        P.nchunk = (int)((P.K + kKC - 1) / kKC);
+        P.chunk0 = chunk0;
+        P.poff = poff;
+        chunk0 += P.nchunk;
+        poff += (long long)P.nchunk * P.R * P.J;
+        S.p[S.np++] = P;
+    };
+    for (int ph = 0; ph < 2; ++ph)
+        for (int l = 0; l < 2; ++l) {
+            const int c = 2 * ph + l, mc = cell_width(c, m, D);
+            const long long base = cell_offset(c, D, m), K = (long long)(ph ? s->t_out : s->t_in) * B;
+            const float *dg = f(A.L.dg[ph][l]), *act = f(A.L.act[ph][l]);
+            WProd P{};
+            P.A = P.A2 = dg;
+            P.lda = 4LL * D;
+            P.K1 = P.K = K;
+            // W1, W2, Wz against y_{n-1} (slot n)
+            P.aoff = 0; P.R = 3 * D; P.B = P.B2 = act; P.ldb = rowq; P.boff = 0; P.J = D; P.goff = base;
+            add(P);
+            // Wy against z_n (slot n+1)
+            P.aoff = 3 * D; P.R = D; P.B = P.B2 = act + (long long)B * rowq; P.boff = D; P.goff = base + 3LL * D * D;
+            add(P);
+            // V against the cell input
+            P.aoff = 0; P.R = 4 * D; P.boff = 0; P.goff = base + 4LL * D * D;
+            if (l) { P.B = P.B2 = f(A.L.act[ph][0]) + (long long)B * rowq; P.ldb = rowq; P.J = D; }
+            else { P.B = P.B2 = ph ? f(A.L.xdec) : A.u; P.ldb = m; P.J = m; }
+            add(P);
+            // biases
+            P.B = P.B2 = nullptr; P.ldb = 0; P.J = 1; P.goff = base + 4LL * D * D + 4LL * D * mc;
+            add(P);
+        }
+    WProd H{};
+    H.A = f(A.L.drec); H.A2 = f(A.L.dot); H.lda = m; H.aoff = 0; H.R = m;
+    H.B = f(A.L.act[0][1]) + (long long)B * rowq; H.B2 = f(A.L.act[1][1]) + (long long)B * rowq;
+    H.ldb = rowq; H.boff = 0; H.J = D;
+    H.K1 = (long long)s->t_in * B; H.K = (long long)(s->t_in + s->t_out) * B;
+    H.goff = cell_offset(4, D, m);
+    add(H);
+    S.nchunks = chunk0;
+    return S;
+}
+
+template <int D>
+cudaError_t launch_fwd(const LemArgs &A, cudaStream_t st)
+{
+    constexpr int smem = fwd_smem_floats<D>() * (int)sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(lem_fwd_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    lem_fwd_kernel<D><<<(A.B + kBT - 1) / kBT, kG * D, smem, st>>>(A);
+    return cudaGetLastError();
+}
+template <int D>
+cudaError_t launch_bwd(const LemArgs &A, cudaStream_t st)
+{
+    constexpr int smem = bwd_smem_floats<D>() * (int)sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(lem_bwd_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    lem_bwd_kernel<D><<<(A.B + kBT - 1) / kBT, kG * D, smem, st>>>(A);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+extern "C" long long fdtd_llg_lem_param_count(int d, int m)
+{
+    if (!(d == 16 || d == 32 || d == 64) || m < 1 || m > kMMax) return 0;
+    return cell_offset(4, d, m) + (long long)m * d;
+}
+
+extern "C" int fdtd_llg_lem_workspace_bytes(const fdtd_llg_lem_shape *s, size_t *bytes)
+{
+    if (!shape_ok(s) || !bytes) return fail(FDTD_E_INVAL, "lem: bad shape (d in {16,32,64}, 1 <= m <= 4, sizes >= 1)");
+    *bytes = layout(s).total;
+    return FDTD_OK;
+}
+
+extern "C" int fdtd_llg_lem_views(const fdtd_llg_lem_shape *s, void *work, float **recon, float **out, float **grad,
+                                  double **loss)
+{
+    if (!shape_ok(s) || !work) return fail(FDTD_E_INVAL, "lem_views: bad shape or NULL work space");
+    const Layout L = layout(s);
+    unsigned char *w = static_cast<unsigned char *>(work);
+    if (recon) *recon = reinterpret_cast<float *>(w + L.recon);
+    if (out) *out = reinterpret_cast<float *>(w + L.out);
+    if (grad) *grad = reinterpret_cast<float *>(w + L.grad);
+    if (loss) *loss = reinterpret_cast<double *>(w + L.loss);
+    return FDTD_OK;
+}
+
+extern "C" int fdtd_llg_lem_forward(const fdtd_llg_lem_shape *s, const float *theta, const float *u, void *work,
+                                    void *stream)
+{
+    if (!shape_ok(s) || !theta || !u || !work) return fail(FDTD_E_INVAL, "lem_forward: bad shape or NULL pointer");
+    const LemArgs A = args(s, theta, u, work);
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = s->d == 64 ? launch_fwd<64>(A, st) : s->d == 32 ? launch_fwd<32>(A, st) : launch_fwd<16>(A, st);
+    return e == cudaSuccess ? FDTD_OK : cuda_fail(e, "lem_forward");
+}
+
+extern "C" int fdtd_llg_lem_loss(const fdtd_llg_lem_shape *s, const fdtd_llg_lem_physics *p, const float *u,
+                                 const float *target, const float *h, void *work, void *stream)
+{
+    if (!shape_ok(s) || !p || !u || !target || !work) return fail(FDTD_E_INVAL, "lem_loss: bad shape or NULL pointer");
+    if (p->lam != 0.f && !h) return fail(FDTD_E_INVAL, "lem_loss: the physics term needs h");
+    if (p->lam != 0.f && s->m != 2) return fail(FDTD_E_INVAL, "lem_loss: the physics term needs m = 2");
+    const Layout L = layout(s);
+    unsigned char *w = static_cast<unsigned char *>(work);
+    LossArgs A{};
+    A.B = s->batch; A.m = s->m; A.t_in = s->t_in; A.t_out = s->t_out;
+    A.lam = p->lam; A.kappa = p->kappa; A.alpha = p->alpha; A.h0 = p->h0;
+    A.u = u; A.target = target; A.h = h;
+    A.recon = reinterpret_cast<const float *>(w + L.recon);
+    A.out = reinterpret_cast<const float *>(w + L.out);
+    A.drec = reinterpret_cast<float *>(w + L.drec);
+    A.dout = reinterpret_cast<float *>(w + L.dout);
+    A.lpart = reinterpret_cast<double *>(w + L.lpart);
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    lem_loss_kernel<<<L.nlblk, kLossThreads, 0, st>>>(A);
+    const long long NR = (long long)s->t_in * s->batch * s->m, NPM = (long long)s->t_out * s->batch * s->m;
+    lem_loss_final_kernel<<<1, kLossThreads, 0, st>>>(A.lpart, L.nlblk, NR, NPM, (double)p->lam,
+                                                       reinterpret_cast<double *>(w + L.loss));
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FDTD_OK : cuda_fail(e, "lem_loss");
+}
+
+extern "C" int fdtd_llg_lem_backward(const fdtd_llg_lem_shape *s, const float *theta, const float *u, void *work,
+                                     void *stream)
+{
+    if (!shape_ok(s) || !theta || !u || !work) return fail(FDTD_E_INVAL, "lem_backward: bad shape or NULL pointer");
+    const LemArgs A = args(s, theta, u, work);
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = s->d == 64 ? launch_bwd<64>(A, st) : s->d == 32 ? launch_bwd<32>(A, st) : launch_bwd<16>(A, st);
+    if (e != cudaSuccess) return cuda_fail(e, "lem_backward");
+    const WProdSet S = products(s, A);
+    float *part = reinterpret_cast<float *>(A.w + A.L.wpart), *grad = reinterpret_cast<float *>(A.w + A.L.grad);
+    lem_wgrad_kernel<<<S.nchunks, 256, 0, st>>>(S, part);
+    const long long P = fdtd_llg_lem_param_count(s->d, s->m);
+    lem_wreduce_kernel<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(S, part, grad);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? FDTD_OK : cuda_fail(e, "lem_backward");
+}
+
+extern "C" int fdtd_llg_lem_adam(long long n, float *theta, const float *grad, float *mom, float *vel, float lr,
+                                 float beta1, float beta2, float eps, int t, void *stream)
+{
+    if (n < 1 || !theta || !grad || !mom || !vel || t < 1 || !(beta1 >= 0.f && beta1 < 1.f) ||
+        !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+        return fail(FDTD_E_INVAL, "lem_adam: bad argument");
+    const float c1 = (float)(1.0 - std::pow((double)beta1, t)), c2 = (float)(1.0 - std::pow((double)beta2, t));
+    lem_adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        n, theta, grad, mom, vel, lr, beta1, beta2, eps, c1, c2);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FDTD_OK : cuda_fail(e, "lem_adam");
+}
+
+extern "C" int fdtd_llg_lem_train_step(const fdtd_llg_lem_shape *s, const fdtd_llg_lem_physics *p, float *theta,
+                                       const float *u, const float *target, const float *h, float *mom, float *vel,
+                                       float lr, int t, void *work, void *stream)
+{
+    int r = fdtd_llg_lem_forward(s, theta, u, work, stream);
+    if (r == FDTD_OK) r = fdtd_llg_lem_loss(s, p, u, target, h, work, stream);
+    if (r == FDTD_OK) r = fdtd_llg_lem_backward(s, theta, u, work, stream);
+    if (r == FDTD_OK) {
+        float *grad = nullptr;
+        fdtd_llg_lem_views(s, work, nullptr, nullptr, &grad, nullptr);
+        r = fdtd_llg_lem_adam(fdtd_llg_lem_param_count(s->d, s->m), theta, grad, mom, vel, lr, 0.9f, 0.999f, 1e-8f, t,
+                              stream);
+    }
+    return r;
+}

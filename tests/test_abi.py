@@ -72,3 +72,20 @@ def test_product_package_does_not_import_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "yee_llg_oracle" not in src, f
+
+
+def test_surrogate_argument_errors_without_gpu():
+    """The surrogate's entry points refuse bad shapes before touching a GPU."""
+    lib = pkg.load_library()
+    assert lib.fdtd_llg_lem_param_count(64, 2) == 4 * (4 * 64 * 64 + 4 * 64) + 4 * 64 * (2 + 64 + 2 + 64) + 2 * 64
+    assert lib.fdtd_llg_lem_param_count(48, 2) == 0 and lib.fdtd_llg_lem_param_count(64, 5) == 0
+    s = _abi.LemShape()
+    s.d, s.m, s.batch, s.t_in, s.t_out, s.dt = 64, 2, 512, 200, 400, 1.0
+    n = C.c_size_t()
+    assert lib.fdtd_llg_lem_workspace_bytes(C.byref(s), C.byref(n)) == 0 and n.value > 0
+    s.d = 40
+    assert lib.fdtd_llg_lem_workspace_bytes(C.byref(s), C.byref(n)) == -1
+    assert b"shape" in lib.fdtd_llg_last_error(None)
+    s.d, s.dt = 64, 0.0
+    assert lib.fdtd_llg_lem_forward(C.byref(s), None, None, None, None) == -1
+    assert lib.fdtd_llg_lem_adam(0, None, None, None, None, 1e-3, 0.9, 0.999, 1e-8, 1, None) == -1
