@@ -517,6 +517,79 @@ def cpw_resonance(torch, pkg, W, steps=700_000, skip=150_000, decim=1000, film=F
     return out
 
 
+def surrogate_run(torch, steps=10, warmup=3, d=64, m=2, B=512, t_in=200, t_out=400):
+    """The physics-informed LEM surrogate at the paper's last curriculum stage
+    (hidden width 64, 200 input samples, 400 predicted, batch 512, physics
+    weight on): CUDA-event times of the forward pass, of one gradient
+    (forward, losses, back-propagation, weight sums) and of one training step
+    (the gradient and Adam), on synthetic damped-precession sequences."""
+    import ctypes as C
+
+    import numpy as np
+
+    from paper_2510_22221_b300 import _abi
+    from paper_2510_22221_b300.surrogate import LemSurrogate, kappa_of
+
+    rng = np.random.default_rng(0)
+    t = np.arange(t_in + t_out)[:, None]
+    w = rng.uniform(0.05, 0.3, B)[None, :]
+    ph = rng.uniform(0, 2 * np.pi, B)[None, :]
+    env = np.exp(-t / 2000.0)
+    seq = 0.1 * env[..., None] * np.stack([np.cos(w * t + ph), np.sin(w * t + ph)], -1)
+    seq = (seq + rng.normal(0, 1e-3, seq.shape)).astype(np.float32)
+    h = rng.normal(0, 300.0, (t_out, B, 3)).astype(np.float32)
+    S = LemSurrogate(d=d, m=m, dt=1.0, seed=0)
+    u, tg, hh = S._dev(seq[:t_in]), S._dev(seq[t_in:]), S._dev(h)
+    phys = dict(lam=1e3, kappa=kappa_of(1.76e11, 1e-12), alpha=1e-3, h0=8e4)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, n):
+        for _ in range(warmup):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    s = S._shape(B, t_in, t_out)
+    ws = S._work(s)
+    lib, st, wp = _abi.load(), S._stream(), C.c_void_p(ws.data_ptr())
+    pt, pu = C.c_void_p(S.theta.data_ptr()), C.c_void_p(u.data_ptr())
+    pp = S._phys(**phys)
+
+    def fwd():
+        _abi.check(lib.fdtd_llg_lem_forward(C.byref(s), pt, pu, wp, st))
+
+    def grad():
+        fwd()
+        _abi.check(lib.fdtd_llg_lem_loss(C.byref(s), C.byref(pp), pu, C.c_void_p(tg.data_ptr()),
+                                         C.c_void_p(hh.data_ptr()), wp, st))
+        _abi.check(lib.fdtd_llg_lem_backward(C.byref(s), pt, pu, wp, st))
+
+    ms_fwd = timed(fwd, steps)
+    ms_grad = timed(grad, steps)
+    ms_step = timed(lambda: S.train_step(u, tg, hh, lr=1e-4, read_loss=False, **phys), steps)
+    loss = S.train_step(u, tg, hh, lr=1e-4, **phys)
+    # algorithmic FLOPs: per step and sequence 12 D^2 + 4 D m + m D multiply-adds
+    # forward (both stacks, head), as many in the reverse products, and
+    # 2 K per parameter for the weight sums (K = steps x batch of its stack)
+    mac = 12 * d * d + 4 * d * m + m * d
+    f_fwd = 2.0 * mac * (t_in + t_out) * B
+    cell = lambda mc: 4 * d * d + 4 * d * mc + 4 * d
+    f_w = 2.0 * (cell(m) + cell(d)) * (t_in + t_out) * B + 2.0 * m * d * (t_in + t_out) * B
+    peak = 148 * 128 * 2 * 2.032e9 / 1e12   # FP32 FMA lanes x 2 x max SM clock
+    return {"workload": f"lem_d{d}_B{B}_T{t_in}+{t_out}", "params": S.nparam, "steps": steps,
+            "ms_forward": round(ms_fwd, 4), "ms_gradient": round(ms_grad, 4), "ms_train_step": round(ms_step, 4),
+            "sequences_per_s": round(B / (ms_step * 1e-3), 1),
+            "gflop_per_step": round((2 * f_fwd + f_w) / 1e9, 2),
+            "tflops_train_step": round((2 * f_fwd + f_w) / (ms_step * 1e-3) / 1e12, 2),
+            "fp32_alu_peak_tflops": round(peak, 1), "losses": [float(x) for x in loss]}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -542,7 +615,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-extra", action="store_true", help="skip the adjoint, batched-sweep, 512x512x256 and absorbing-layer measurements")
-    ap.add_argument("--only", choices=["adjoint", "sweep", "large", "pml", "cpw", "cpw_fp"],
+    ap.add_argument("--only", choices=["adjoint", "sweep", "large", "pml", "cpw", "cpw_fp", "surrogate"],
                     help="run just one of the extra measurements and print its JSON object")
     ap.add_argument("--adjoint-steps", type=int, default=4000, help="steps of the adjoint measurement")
     ap.add_argument("--cpw-steps", type=int, default=700_000, help="steps of the CPW resonance measurement (--only cpw_fp)")
@@ -570,6 +643,8 @@ def main():
             out = pml_run(torch, pkg, W)
         elif args.only == "cpw":
             out = cpw_device_run(torch, pkg, W)
+        elif args.only == "surrogate":
+            out = surrogate_run(torch)
         elif args.only == "cpw_fp":
             out = cpw_resonance(torch, pkg, W, steps=args.cpw_steps, film=args.cpw_film, h0_oe=args.cpw_h0,
                                 split=args.cpw_split)
@@ -719,6 +794,7 @@ def main():
         line["large_run"] = large_run(torch, pkg, W)
         line["pml_run"] = pml_run(torch, pkg, W)
         line["cpw_device"] = cpw_device_run(torch, pkg, W)
+        line["surrogate"] = surrogate_run(torch)
         line["precision_vs_fp64"] = precision_vs_fp64(torch, pkg, W)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w, 12)

@@ -4,13 +4,13 @@
 // back-propagation through both stacks, the gate-gradient sums that give the
 // weight gradients, and Adam.
 //
-// Recurrent kernels.  One CTA advances kBT = 8 sequences through every step of
-// both stacks, with the two cells' weights of the stack in shared memory
-// (about 200 KB at D = 64) and the states beside them; 4 D threads, thread
-// (g, i) owning hidden unit i of sequences g and g + 4.  The time loop is
+// Recurrent kernels.  One CTA advances 4 R sequences (R = 1 or 2) through
+// every step of both stacks, with the two cells' weights of the stack in
+// shared memory (about 200 KB at D = 64) and the states beside them; 4 D
+// threads, thread (g, i) owning hidden unit i of sequences g + 4 r.  The time loop is
 // sequential, so a step costs a chain of dependent phases (gates and z, one
 // barrier, y, one barrier, per cell; the head) rather than bandwidth; the
-// batch is spread over ceil(batch / 8) CTAs.  Activations of every step are
+// batch is spread over ceil(batch / 4 R) CTAs.  Activations of every step are
 // saved (y, z, the two sigmoid gates and the two tanh values) for the
 // reverse pass.
 //
@@ -36,8 +36,8 @@ void set_last_error(const char *msg);
 namespace {
 
 constexpr int kG = 4;            // sequence groups per CTA
-constexpr int kR = 2;            // sequences per thread
-constexpr int kBT = kG * kR;     // sequences per CTA
+// sequences per thread R (1 or 2, chosen at launch so that the batch covers
+// the SMs); a CTA holds kG R sequences
 constexpr int kMMax = 4;         // largest input / output width
 constexpr int kQ = 6;            // saved values per unit and step: y, z, s1, s2, tz, ty
 constexpr int kKC = 2048;        // rows per chunk of the weight-gradient sums
@@ -153,15 +153,15 @@ __device__ __forceinline__ T *wp(const LemArgs &A, size_t off)
 namespace {
 
 // Shared-memory floats of the recurrent kernels for width D
-template <int D>
+template <int D, int R>
 constexpr int fwd_smem_floats()
 {
-    return 3 * 4 * D * D + 4 * kMMax * D + 2 * 4 * D + kMMax * D + 2 * 2 * kBT * D + kBT * kMMax;
+    return 3 * 4 * D * D + 4 * kMMax * D + 2 * 4 * D + kMMax * D + 2 * 2 * (kG * R) * D + (kG * R) * kMMax;
 }
-template <int D>
+template <int D, int R>
 constexpr int bwd_smem_floats()
 {
-    return 3 * 4 * D * D + 4 * kMMax * D + kMMax * D + 2 * 4 * kBT * D + 2 * kBT * kMMax;
+    return 3 * 4 * D * D + 4 * kMMax * D + kMMax * D + 2 * 4 * (kG * R) * D + 2 * (kG * R) * kMMax;
 }
 
 // Weights of cell c into shared memory.  TR: W and V transposed ([q][j][i],
@@ -186,11 +186,12 @@ __device__ void load_cell(const float *theta, int c, int m, float *W, float *V, 
         for (int e = threadIdx.x; e < 4 * D; e += blockDim.x) bb[e] = src[e];
 }
 
-// Forward pass of kBT sequences (see the file comment).  Thread (g, i) =
-// (tid / D, tid % D) owns unit i of sequences g and g + kG.
-template <int D>
+// Forward pass of kG R sequences (see the file comment).  Thread (g, i) =
+// (tid / D, tid % D) owns unit i of sequences g + kG r, r < R.
+template <int D, int R>
 __global__ void __launch_bounds__(kG *D, 1) lem_fwd_kernel(LemArgs A)
 {
+    constexpr int kR = R, kBT = kG * R;
     extern __shared__ float sm[];
     float *WT0 = sm, *WT1 = WT0 + 4 * D * D, *VT1 = WT1 + 4 * D * D, *VT0 = VT1 + 4 * D * D;
     float *bb0 = VT0 + 4 * kMMax * D, *bb1 = bb0 + 4 * D, *Wo = bb1 + 4 * D;
@@ -466,15 +467,16 @@ __global__ void lem_loss_final_kernel(const double *lpart, int nblk, long long N
 namespace {
 
 // ---------------------------------------------------------------- reverse
-// Back-propagation through both stacks for kBT sequences: the decoder's steps
+// Back-propagation through both stacks for kG R sequences: the decoder's steps
 // in reverse (with the output feedback: the gradient of step k's input is
 // added to the gradient of output k-1), then the encoder's.  Thread (g, i)
 // carries dL/dy and dL/dz of unit i of its two sequences for both cells in
 // registers; the gate gradients of each step go to shared memory for the
 // products with W^T and V^T and to the work space for the weight sums.
-template <int D>
+template <int D, int R>
 __global__ void __launch_bounds__(kG *D, 1) lem_bwd_kernel(LemArgs A)
 {
+    constexpr int kR = R, kBT = kG * R;
     extern __shared__ float sm[];
     float *W0 = sm, *W1 = W0 + 4 * D * D, *V1 = W1 + 4 * D * D, *V0 = V1 + 4 * D * D;
     float *Wo = V0 + 4 * kMMax * D, *DG = Wo + kMMax * D;   // DG [2][4][kBT][D]
@@ -616,18 +618,21 @@ namespace {
 // --------------------------------------------------------- weight sums
 // Partial sums over one chunk of kKC rows of one product: C[r][j] =
 // sum_k A[k][aoff + r] B[k][boff + j] (B absent: 1), rows k >= K1 from the
-// second segment.  Thread (rt, jt) accumulates an 8 x 8 block.
+// second segment.  Thread (rt, jt) of group q accumulates an 8 x 8 block over
+// the staged rows kk = q (mod G), G = 256 / (threads per block of outputs);
+// the groups' blocks are then added in group order.
 __global__ void __launch_bounds__(256) lem_wgrad_kernel(WProdSet S, float *part)
 {
-    __shared__ float sa[32][4 * 64 + 1];
-    __shared__ float sb[32][64 + 1];
+    __shared__ __align__(16) float sa[32][4 * 64 + 4];
+    __shared__ __align__(16) float sb[32][64 + 4];
     int p = 0;
     while (p + 1 < S.np && (int)blockIdx.x >= S.p[p + 1].chunk0) ++p;
     const WProd &P = S.p[p];
     const int chunk = blockIdx.x - P.chunk0, tid = threadIdx.x;
     const long long k0 = (long long)chunk * kKC, k1 = min(k0 + kKC, P.K);
-    const int RT = (P.R + 7) / 8, JT = (P.J + 7) / 8, rt = tid % RT, jt = tid / RT;
-    const bool act = tid < RT * JT;
+    const int RT = (P.R + 7) / 8, JT = (P.J + 7) / 8, NB = RT * JT, G = 256 / NB;
+    const int q = tid / NB, rt = (tid % NB) % RT, jt = (tid % NB) / RT;
+    const bool act = q < G;
     float acc[8][8];
 #pragma unroll
     for (int a = 0; a < 8; ++a)
@@ -653,12 +658,13 @@ __global__ void __launch_bounds__(256) lem_wgrad_kernel(WProdSet S, float *part)
         }
         __syncthreads();
         if (act)
-            for (int kk = 0; kk < nk; ++kk) {
-                float av[8], bv[8];
-#pragma unroll
-                for (int a = 0; a < 8; ++a) av[a] = (rt * 8 + a < P.R) ? sa[kk][rt * 8 + a] : 0.f;
-#pragma unroll
-                for (int b = 0; b < 8; ++b) bv[b] = (jt * 8 + b < P.J) ? sb[kk][jt * 8 + b] : 0.f;
+            for (int kk = q; kk < nk; kk += G) {
+                const float4 a0 = *reinterpret_cast<const float4 *>(&sa[kk][rt * 8]);
+                const float4 a1 = *reinterpret_cast<const float4 *>(&sa[kk][rt * 8 + 4]);
+                const float4 b0 = *reinterpret_cast<const float4 *>(&sb[kk][jt * 8]);
+                const float4 b1 = *reinterpret_cast<const float4 *>(&sb[kk][jt * 8 + 4]);
+                const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
                 for (int a = 0; a < 8; ++a)
 #pragma unroll
@@ -666,7 +672,30 @@ __global__ void __launch_bounds__(256) lem_wgrad_kernel(WProdSet S, float *part)
             }
         __syncthreads();
     }
-    if (!act) return;
+    // groups 1 .. G-1 add their blocks into group 0's, one group at a time
+    // (sa as the exchange buffer, R x J <= 8192 floats whenever G > 1)
+    float *xb = &sa[0][0];
+    for (int g = 1; g < G; ++g) {
+        if (q == g)
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    const int r = rt * 8 + a, j = jt * 8 + b;
+                    if (r < P.R && j < P.J) xb[r * P.J + j] = acc[a][b];
+                }
+        __syncthreads();
+        if (q == 0)
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    const int r = rt * 8 + a, j = jt * 8 + b;
+                    if (r < P.R && j < P.J) acc[a][b] += xb[r * P.J + j];
+                }
+        __syncthreads();
+    }
+    if (q != 0) return;
     float *o = part + P.poff + (long long)chunk * P.R * P.J;
 #pragma unroll
     for (int a = 0; a < 8; ++a)
@@ -787,23 +816,45 @@ WProdSet products(const fdtd_llg_lem_shape *s, const LemArgs &A)
     return S;
 }
 
+// Sequences per thread: 2 once the batch fills every SM with two-per-thread
+// CTAs (each weight load then feeds two sequences), else 1 (more CTAs).
+int seq_per_thread(int B)
+{
+    static int nsm = 0;
+    if (!nsm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 148;
+    }
+    return (B + 2 * kG - 1) / (2 * kG) >= nsm ? 2 : 1;
+}
+template <int D, int R>
+cudaError_t launch_fwd_r(const LemArgs &A, cudaStream_t st)
+{
+    constexpr int smem = fwd_smem_floats<D, R>() * (int)sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(lem_fwd_kernel<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    lem_fwd_kernel<D, R><<<(A.B + kG * R - 1) / (kG * R), kG * D, smem, st>>>(A);
+    return cudaGetLastError();
+}
+template <int D, int R>
+cudaError_t launch_bwd_r(const LemArgs &A, cudaStream_t st)
+{
+    constexpr int smem = bwd_smem_floats<D, R>() * (int)sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(lem_bwd_kernel<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    lem_bwd_kernel<D, R><<<(A.B + kG * R - 1) / (kG * R), kG * D, smem, st>>>(A);
+    return cudaGetLastError();
+}
 template <int D>
 cudaError_t launch_fwd(const LemArgs &A, cudaStream_t st)
 {
-    constexpr int smem = fwd_smem_floats<D>() * (int)sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(lem_fwd_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    lem_fwd_kernel<D><<<(A.B + kBT - 1) / kBT, kG * D, smem, st>>>(A);
-    return cudaGetLastError();
+    return seq_per_thread(A.B) == 2 ? launch_fwd_r<D, 2>(A, st) : launch_fwd_r<D, 1>(A, st);
 }
 template <int D>
 cudaError_t launch_bwd(const LemArgs &A, cudaStream_t st)
 {
-    constexpr int smem = bwd_smem_floats<D>() * (int)sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(lem_bwd_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    lem_bwd_kernel<D><<<(A.B + kBT - 1) / kBT, kG * D, smem, st>>>(A);
-    return cudaGetLastError();
+    return seq_per_thread(A.B) == 2 ? launch_bwd_r<D, 2>(A, st) : launch_bwd_r<D, 1>(A, st);
 }
 
 }  // namespace

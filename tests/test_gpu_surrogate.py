@@ -119,8 +119,8 @@ def test_adam_and_train_step_match_the_oracle_and_the_parts():
 @gpu
 def test_gradient_is_the_same_bits_every_run_and_for_a_padded_batch():
     """Fixed-order sums: two runs give the same bits; a batch that is not a
-    multiple of the 8 sequences of a CTA pads without changing the values of
-    the real sequences' outputs."""
+    multiple of a CTA's sequences pads without changing the values of the
+    real sequences' outputs."""
     d, m, B, T_in, T_out = 32, 2, 13, 20, 10
     theta, u, tg, h = _case(d, m, B, T_in, T_out, seed=5)
     S = _surrogate(theta, d, m)
@@ -130,6 +130,25 @@ def test_gradient_is_the_same_bits_every_run_and_for_a_padded_batch():
     _, o_all = S.forward(u, T_out)
     _, o_one = S.forward(u[:, 3:4], T_out)
     assert np.array_equal(o_all.cpu().numpy()[:, 3], o_one.cpu().numpy()[:, 0])
+
+
+@gpu
+def test_two_sequences_per_thread_give_the_same_bits():
+    """A batch large enough for two sequences per thread (a CTA of 8 instead
+    of 4) gives every sequence the same bits as a small batch, and matches
+    the oracle on sampled sequences."""
+    d, m, B, T_in, T_out = 16, 2, 1300, 24, 12
+    theta, u, tg, h = _case(d, m, B, T_in, T_out, seed=9)
+    S = _surrogate(theta, d, m)
+    rec, out = S.forward(u, T_out)
+    pick = [0, 5, 777, 1299]
+    rec_s, out_s = S.forward(u[:, pick], T_out)
+    assert np.array_equal(out.cpu().numpy()[:, pick], out_s.cpu().numpy())
+    assert np.array_equal(rec.cpu().numpy()[:, pick], rec_s.cpu().numpy())
+    r = O.train_grad(theta, u[:, pick], tg[:, pick], h[:, pick], d=d, dt=0.9, **PHYS)
+    assert np.abs(out_s.cpu().numpy() - r["out"]).max() < TOL_OUT
+    loss, g = S.gradient(u, tg, h, **PHYS)
+    assert np.all(np.isfinite(g.cpu().numpy()))
 
 
 @gpu
