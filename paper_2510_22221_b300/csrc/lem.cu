@@ -616,15 +616,35 @@ __global__ void __launch_bounds__(kG *D, 1) lem_bwd_kernel(LemArgs A)
 namespace {
 
 // --------------------------------------------------------- weight sums
+// Asynchronous global -> shared copies (completion by groups)
+__device__ __forceinline__ void cpa4(float *dst, const float *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa16(float *dst, const float *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+constexpr int kWRows = 32;                  // rows per staged tile
+constexpr int kWA = 4 * 64 + 4, kWB = 64 + 4;   // row strides of the staged A and B tiles
+constexpr int kWgradSmem = 2 * kWRows * (kWA + kWB) * (int)sizeof(float);
+
 // Partial sums over one chunk of kKC rows of one product: C[r][j] =
 // sum_k A[k][aoff + r] B[k][boff + j] (B absent: 1), rows k >= K1 from the
-// second segment.  Thread (rt, jt) of group q accumulates an 8 x 8 block over
-// the staged rows kk = q (mod G), G = 256 / (threads per block of outputs);
-// the groups' blocks are then added in group order.
+// second segment.  Tiles of 32 rows are staged by asynchronous copies, two
+// buffers deep (the next tile lands while this one is summed).  Thread (rt,
+// jt) of group q accumulates an 8 x 8 block over the staged rows kk = q (mod
+// G), G = 256 / (threads per block of outputs); the groups' blocks are then
+// added in group order.
 __global__ void __launch_bounds__(256) lem_wgrad_kernel(WProdSet S, float *part)
 {
-    __shared__ __align__(16) float sa[32][4 * 64 + 4];
-    __shared__ __align__(16) float sb[32][64 + 4];
+    extern __shared__ __align__(16) float wsm[];
     int p = 0;
     while (p + 1 < S.np && (int)blockIdx.x >= S.p[p + 1].chunk0) ++p;
     const WProd &P = S.p[p];
@@ -633,36 +653,70 @@ __global__ void __launch_bounds__(256) lem_wgrad_kernel(WProdSet S, float *part)
     const int RT = (P.R + 7) / 8, JT = (P.J + 7) / 8, NB = RT * JT, G = 256 / NB;
     const int q = tid / NB, rt = (tid % NB) % RT, jt = (tid % NB) / RT;
     const bool act = q < G;
+    // 16-byte copies where rows, offsets and widths allow them
+    const bool va = (P.lda % 4 == 0) && (P.aoff % 4 == 0) && (P.R % 4 == 0);
+    const bool vb = P.B && (P.ldb % 4 == 0) && (P.boff % 4 == 0) && (P.J % 4 == 0);
+    auto sa = [&](int buf, int kk) { return wsm + (buf * kWRows + kk) * kWA; };
+    auto sb = [&](int buf, int kk) { return wsm + 2 * kWRows * kWA + (buf * kWRows + kk) * kWB; };
+    auto stage = [&](int buf, long long kb) {
+        const int nk = (int)min((long long)kWRows, k1 - kb);
+        if (va) {
+            const int w = P.R / 4;
+            for (int e = tid; e < nk * w; e += blockDim.x) {
+                const int kk = e / w, r = (e % w) * 4;
+                const long long row = kb + kk;
+                const float *src = row < P.K1 ? P.A + row * P.lda : P.A2 + (row - P.K1) * P.lda;
+                cpa16(sa(buf, kk) + r, src + P.aoff + r);
+            }
+        } else {
+            for (int e = tid; e < nk * P.R; e += blockDim.x) {
+                const int kk = e / P.R, r = e % P.R;
+                const long long row = kb + kk;
+                const float *src = row < P.K1 ? P.A + row * P.lda : P.A2 + (row - P.K1) * P.lda;
+                cpa4(sa(buf, kk) + r, src + P.aoff + r);
+            }
+        }
+        if (!P.B) {
+            for (int e = tid; e < nk * P.J; e += blockDim.x) sb(buf, e / P.J)[e % P.J] = 1.f;
+        } else if (vb) {
+            const int w = P.J / 4;
+            for (int e = tid; e < nk * w; e += blockDim.x) {
+                const int kk = e / w, j = (e % w) * 4;
+                const long long row = kb + kk;
+                const float *src = row < P.K1 ? P.B + row * P.ldb : P.B2 + (row - P.K1) * P.ldb;
+                cpa16(sb(buf, kk) + j, src + P.boff + j);
+            }
+        } else {
+            for (int e = tid; e < nk * P.J; e += blockDim.x) {
+                const int kk = e / P.J, j = e % P.J;
+                const long long row = kb + kk;
+                const float *src = row < P.K1 ? P.B + row * P.ldb : P.B2 + (row - P.K1) * P.ldb;
+                cpa4(sb(buf, kk) + j, src + P.boff + j);
+            }
+        }
+        cpa_commit();
+    };
     float acc[8][8];
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
         for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
-    for (long long kb = k0; kb < k1; kb += 32) {
-        const int nk = (int)min(32LL, k1 - kb);
-        for (int e = tid; e < nk * P.R; e += blockDim.x) {
-            const int kk = e / P.R, r = e % P.R;
-            const long long row = kb + kk;
-            const float *src = row < P.K1 ? P.A + row * P.lda : P.A2 + (row - P.K1) * P.lda;
-            sa[kk][r] = src[P.aoff + r];
-        }
-        for (int e = tid; e < nk * P.J; e += blockDim.x) {
-            const int kk = e / P.J, j = e % P.J;
-            const long long row = kb + kk;
-            float v = 1.f;
-            if (P.B) {
-                const float *src = row < P.K1 ? P.B + row * P.ldb : P.B2 + (row - P.K1) * P.ldb;
-                v = src[P.boff + j];
-            }
-            sb[kk][j] = v;
+    stage(0, k0);
+    int buf = 0;
+    for (long long kb = k0; kb < k1; kb += kWRows, buf ^= 1) {
+        const int nk = (int)min((long long)kWRows, k1 - kb);
+        if (kb + kWRows < k1) {
+            stage(buf ^ 1, kb + kWRows);
+            cpa_wait<1>();
+        } else {
+            cpa_wait<0>();
         }
         __syncthreads();
         if (act)
             for (int kk = q; kk < nk; kk += G) {
-                const float4 a0 = *reinterpret_cast<const float4 *>(&sa[kk][rt * 8]);
-                const float4 a1 = *reinterpret_cast<const float4 *>(&sa[kk][rt * 8 + 4]);
-                const float4 b0 = *reinterpret_cast<const float4 *>(&sb[kk][jt * 8]);
-                const float4 b1 = *reinterpret_cast<const float4 *>(&sb[kk][jt * 8 + 4]);
+                const float *ra = sa(buf, kk) + rt * 8, *rb = sb(buf, kk) + jt * 8;
+                const float4 a0 = *reinterpret_cast<const float4 *>(ra), a1 = *reinterpret_cast<const float4 *>(ra + 4);
+                const float4 b0 = *reinterpret_cast<const float4 *>(rb), b1 = *reinterpret_cast<const float4 *>(rb + 4);
                 const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
                 const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -670,11 +724,11 @@ __global__ void __launch_bounds__(256) lem_wgrad_kernel(WProdSet S, float *part)
 #pragma unroll
                     for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
             }
-        __syncthreads();
+        __syncthreads();   // this buffer is free for the tile after next
     }
     // groups 1 .. G-1 add their blocks into group 0's, one group at a time
-    // (sa as the exchange buffer, R x J <= 8192 floats whenever G > 1)
-    float *xb = &sa[0][0];
+    // (the A buffers as the exchange area: R x J <= 8192 floats whenever G > 1)
+    float *xb = wsm;
     for (int g = 1; g < G; ++g) {
         if (q == g)
 #pragma unroll
@@ -932,7 +986,9 @@ extern "C" int fdtd_llg_lem_backward(const fdtd_llg_lem_shape *s, const float *t
     if (e != cudaSuccess) return cuda_fail(e, "lem_backward");
     const WProdSet S = products(s, A);
     float *part = reinterpret_cast<float *>(A.w + A.L.wpart), *grad = reinterpret_cast<float *>(A.w + A.L.grad);
-    lem_wgrad_kernel<<<S.nchunks, 256, 0, st>>>(S, part);
+    e = cudaFuncSetAttribute(lem_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgradSmem);
+    if (e != cudaSuccess) return cuda_fail(e, "lem_backward");
+    lem_wgrad_kernel<<<S.nchunks, 256, kWgradSmem, st>>>(S, part);
     const long long P = fdtd_llg_lem_param_count(s->d, s->m);
     lem_wreduce_kernel<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(S, part, grad);
     e = cudaGetLastError();
