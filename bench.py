@@ -419,8 +419,7 @@ def pml_run(torch, pkg, W, steps=2000, warmup=20, layers=(10, 10, 8)):
     81 B per step: the H pass reads the two E components it differentiates
     (8), reads and writes the two H components it corrects (16) and the
     axis's two H memories (16); the E pass the same with H and E swapped
-    (40) plus the class id (1); neighbour values come from L1/L2 (ncu: 80 B
-    of DRAM traffic per layer cell over both passes)."""
+    (40) plus the class id (1); neighbour values come from L1/L2."""
     stream = torch.cuda.current_stream()
     out = {}
     for tag, w in (("plain", W.strip_resonator(steps=steps)), ("layers", W.strip_resonator_pml(steps=steps, layers=layers))):
@@ -515,6 +514,38 @@ def cpw_resonance(torch, pkg, W, steps=700_000, skip=150_000, decim=1000, film=F
     except Exception as exc:   # the DFT peak above still reports the resonance
         out["fit_error"] = str(exc)
     return out
+
+
+def cpu_table(torch, pkg, W, seconds_cap=10.0):
+    """The FP64 oracle on every configuration's workload (a bounded sample of
+    full steps, one thread and all cores), and the GPU on config 0's 32^3
+    cavity (L2-resident; 2000 steps, CUDA events): the per-configuration
+    table of the CPU baseline."""
+    rows = {}
+    cfg = {"config0_cavity_block_32": (W.cavity_block(steps=2000), 2000),
+           "config1_strip_resonator_256x256x128": (W.strip_resonator(steps=20), 20),
+           "config3_adjoint_design_128x128x64": (W.adjoint_design(steps=50), 50),
+           "config4_multi_strip_512x512x256": (W.multi_strip(steps=3), 3)}
+    sweep = W.bias_sweep(steps=50)
+    big = max(range(len(sweep)), key=lambda q: sweep[q].cells)
+    cfg["config2_bias_sweep_cube0"] = (sweep[0], 50)
+    cfg[f"config2_bias_sweep_cube{big}_largest"] = (sweep[big], 50)
+    for name, (w, n) in cfg.items():
+        rows[name] = cpu_baseline(w, n, seconds_cap=seconds_cap)
+    w = W.cavity_block(steps=2000)
+    sim = pkg.from_workload(w, probe_capacity=2100)
+    sim.step(20)
+    sim.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    e0.record(stream)
+    sim.step(2000)
+    e1.record(stream)
+    sim.sync()
+    ms = e0.elapsed_time(e1)
+    sim.destroy()
+    rows["config0_gpu"] = {"mcells_per_s": round(w.cells * 2000 / (ms * 1e-3) / 1e6, 1), "us_per_step": round(ms, 4) / 2}
+    return rows
 
 
 def surrogate_run(torch, steps=10, warmup=3, d=64, m=2, B=512, t_in=200, t_out=400):
@@ -615,7 +646,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-extra", action="store_true", help="skip the adjoint, batched-sweep, 512x512x256 and absorbing-layer measurements")
-    ap.add_argument("--only", choices=["adjoint", "sweep", "large", "pml", "cpw", "cpw_fp", "surrogate"],
+    ap.add_argument("--only", choices=["adjoint", "sweep", "large", "pml", "cpw", "cpw_fp", "surrogate", "cpu_table"],
                     help="run just one of the extra measurements and print its JSON object")
     ap.add_argument("--adjoint-steps", type=int, default=4000, help="steps of the adjoint measurement")
     ap.add_argument("--cpw-steps", type=int, default=700_000, help="steps of the CPW resonance measurement (--only cpw_fp)")
@@ -645,6 +676,8 @@ def main():
             out = cpw_device_run(torch, pkg, W)
         elif args.only == "surrogate":
             out = surrogate_run(torch)
+        elif args.only == "cpu_table":
+            out = cpu_table(torch, pkg, W)
         elif args.only == "cpw_fp":
             out = cpw_resonance(torch, pkg, W, steps=args.cpw_steps, film=args.cpw_film, h0_oe=args.cpw_h0,
                                 split=args.cpw_split)
