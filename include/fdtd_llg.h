@@ -404,7 +404,9 @@ int fdtd_llg_autotune(fdtd_llg_t h, int32_t trial_steps, int32_t *planes);
  * row, probe p, Ex/Ey/Ez of its cell).  Reverse sweep segment by segment
  * from the last checkpoint: each segment's forward steps are recomputed
  * (recording what the reverse step needs), then reversed step by step on the
- * GPU (FP32 adjoint fields, FP64 gradient accumulation).  Outputs, host,
+ * GPU (FP32 adjoint fields, FP64 gradient accumulation; each magnet region
+ * reversed over as many CTAs of a thread-block cluster as the forward magnet
+ * kernel uses, fdtd_llg_set_magnet_cluster).  Outputs, host,
  * FP64, either may be NULL: grad_eps[k][j][i], dJ/d eps_r of every cell of the
  * design box given to fdtd_llg_set_materials; *grad_h0, dJ/d |H_bias| (per
  * A/m) along the bias direction (M starts along it whatever its size).  The

@@ -26,6 +26,10 @@
 // C_E^T = C_H on the Yee grid, so the transposed curls are the forward curls.
 #include "fdtd_llg_internal.h"
 
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
+
 namespace fl {
 
 namespace {
@@ -209,15 +213,28 @@ __device__ void cell_inputs(const MagComp &C, const BoxDiv &BD, const Inst *I, c
     mm[2] = m[2 * V + v];
 }
 
+// A region's reverse pass may be split over the cs CTAs of a thread-block
+// cluster: CTA rank takes every cell and face index in the blocks
+// rank * nth + [0, nth) of each cs * nth (part0 = rank * nth, pstep = cs *
+// nth), all of its data in the region's global workspace, and every barrier
+// of the pass is the cluster's (release and acquire at cluster scope, so the
+// other CTAs' workspace writes are visible after it).
+__device__ __forceinline__ void region_sync(int cs)
+{
+    if (cs > 1) cg::this_cluster().sync();
+    else __syncthreads();
+}
+
 // Reverse of one half-push.  In: lamHout (faces), lamM (adjoint of the output
 // m, bias frame; overwritten with the adjoint of the input m).  Out: lamHin,
 // lamC (faces); *gh0 accumulates d J / d |H_bias| of this thread's cells.
 __device__ void rev_half(const MagComp &C, const BoxDiv &BD, const FaceNb *fnb, const Inst *I, const float *R9,
                          const uint8_t *smat, int V, int nf, int R, const float *Hs, const float *Cc, const float *m,
                          const float *D, RegionWS &W, const float *lamHout, float *lamHin, float *lamC, double *gh0, int nfx,
-                         int nfy)
+                         int nfy, int cs)
 {
-    const int tid = threadIdx.x, nth = blockDim.x;
+    const int tid = threadIdx.x + (cs > 1 ? (int)cg::this_cluster().block_rank() : 0) * blockDim.x;
+    const int nth = blockDim.x * cs;
     const int bx = C.bx, by = C.by, bxy = bx * by;
     // direct terms of H_out = H* - P D^R, H* = Hs - C; adjoint of D^R and of dl^R
     for (int f = tid; f < nf; f += nth) {
@@ -240,7 +257,7 @@ __device__ void rev_half(const MagComp &C, const BoxDiv &BD, const FaceNb *fnb, 
         to_fr(R9, lD, l);   // D = R^T dl, so the adjoint of dl is R times that of D
         for (int a = 0; a < 3; ++a) W.lamDl[a * V + v] = W.lamM[a * V + v] + l[a];
     }
-    __syncthreads();
+    region_sync(cs);
     double g = 0.0;
     for (int r = R; r >= 1; --r) {
         const float *Dp = r >= 2 ? D + 3 * V * (r - 2) : nullptr;
@@ -268,7 +285,7 @@ __device__ void rev_half(const MagComp &C, const BoxDiv &BD, const FaceNb *fnb, 
                 W.lamA[a * V + v] += lg[a];
             }
         }
-        __syncthreads();
+        region_sync(cs);
         if (r >= 2) {
             // h depends on D^{r-1} through -1/4 (D_{v-1} + 2 D_v + D_{v+1}) per component
             for (int v = tid; v < V; v += nth) {
@@ -290,7 +307,7 @@ __device__ void rev_half(const MagComp &C, const BoxDiv &BD, const FaceNb *fnb, 
                 to_fr(R9, lD, l);
                 for (int a = 0; a < 3; ++a) W.lamDl[a * V + v] = l[a];
             }
-            __syncthreads();
+            region_sync(cs);
         }
     }
     *gh0 += g;
@@ -302,7 +319,7 @@ __device__ void rev_half(const MagComp &C, const BoxDiv &BD, const FaceNb *fnb, 
         from_fr(R9, l, gq);
         for (int a = 0; a < 3; ++a) W.lamHsm[a * V + v] = gq[a];
     }
-    __syncthreads();
+    region_sync(cs);
     for (int f = tid; f < nf; f += nth) {
         const FaceNb q = fnb[f];
         const int a = face_axis(f, nfx, nfy);
@@ -312,21 +329,24 @@ __device__ void rev_half(const MagComp &C, const BoxDiv &BD, const FaceNb *fnb, 
         lamHin[f] += sA + sH;
         lamC[f] -= sA;
     }
-    __syncthreads();
+    region_sync(cs);
 }
 
 __global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSet A, int slot)
 {
-    extern __shared__ FaceNb fnb[];   // nf entries
+    extern __shared__ FaceNb fnb[];   // nf entries (every CTA of a region holds the whole table)
     __shared__ double sred[kMagThreads / 32];
-    const MagComp C = L.comps[blockIdx.x];
+    const int cs = A.cs, rc = blockIdx.x / cs;
+    const int rank = cs > 1 ? (int)cg::this_cluster().block_rank() : 0;
+    const MagComp C = L.comps[rc];
     const Inst *I = L.insts + C.inst;
-    const int tid = threadIdx.x, nth = blockDim.x;
+    // this CTA's part of the region's cells and faces (see region_sync)
+    const int tid = threadIdx.x + rank * blockDim.x, nth = blockDim.x * cs;
     const int V = C.V, bx = C.bx, by = C.by, bz = C.bz;
     const int nfx = (bx + 1) * by * bz, nfy = bx * (by + 1) * bz, nf = nfx + nfy + bx * by * (bz + 1);
     const int ex = bx + 1, exy = (bx + 1) * (by + 1), ne = exy * (bz + 1);
     const int R = A.R;
-    float *wsb = A.ws + A.ws_off[blockIdx.x];
+    float *wsb = A.ws + A.ws_off[rc];
     uint8_t *smat = reinterpret_cast<uint8_t *>(wsb);              // V bytes, rounded up to floats
     RegionWS W = carve(wsb + (V + 3) / 4, nf, V);
     float R9[9];
@@ -342,10 +362,11 @@ __global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSe
     const BoxDiv BD(bx, by);
     for (int v = tid; v < V; v += nth) smat[v] = C.mat[v];
     const float ch = I->ch;
-    for (int f = tid; f < nf; f += nth) {
+    for (int f = threadIdx.x; f < nf; f += blockDim.x) {
         int a, fi, fj, fk, vl, vr;
         face_decode(f, BD, bx, by, bz, a, fi, fj, fk, vl, vr);
         fnb[f] = {vl >= 0 && C.mat[vl] != 0xFF ? vl : -1, vr >= 0 && C.mat[vr] != 0xFF ? vr : -1};
+        if ((f / (int)blockDim.x) % cs != rank) continue;   // the workspace entries of another CTA's faces
         const int e0 = fk * exy + fj * ex + fi;
         float cu = 0.f;
         if (a == 0) cu = curl2a(Ez[e0 + ex], Ez[e0], I->idy, Ey[e0 + exy], Ey[e0], I->idz);
@@ -361,16 +382,16 @@ __global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSe
                                  W.fix[f]
                            : 0.f;
     }
-    __syncthreads();
+    region_sync(cs);
     // reverse: second half-push, then the first
     double g = 0.0;
-    rev_half(C, BD, fnb, I, R9, smat, V, nf, R, Hs2, W.C, m2, D2, W, W.lamHout, W.lamHin, W.lamC, &g, nfx, nfy);
+    rev_half(C, BD, fnb, I, R9, smat, V, nf, R, Hs2, W.C, m2, D2, W, W.lamHout, W.lamHin, W.lamC, &g, nfx, nfy, cs);
     for (int f = tid; f < nf; f += nth) {
         W.lamHout[f] = W.lamHin[f];      // adjoint of H^{n+1}
         W.fix[f] = W.lamC[f];            // curl adjoint of the second half-push
     }
-    __syncthreads();
-    rev_half(C, BD, fnb, I, R9, smat, V, nf, R, Hs1, W.C, m1, D1, W, W.lamHout, W.lamHin, W.lamC, &g, nfx, nfy);
+    region_sync(cs);
+    rev_half(C, BD, fnb, I, R9, smat, V, nf, R, Hs1, W.C, m1, D1, W, W.lamHout, W.lamHin, W.lamC, &g, nfx, nfy, cs);
     // write back: for a magnetic face the curl sweep must see q/2 with
     // q = -(lamC1 + lamC2) (a plain face contributes 2 lambda_H); afterwards
     // the face takes lamHin, restored from fix by the next reverse step's
@@ -391,15 +412,18 @@ __global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSe
             W.fix[f] = W.lamHin[f] - 0.5f * q;
         }
     }
-    // block sum of d J / d |H_bias|, fixed order
+    // block sum of d J / d |H_bias|, fixed order (one partial per CTA)
     for (int o = 16; o > 0; o >>= 1) g += __shfl_down_sync(0xffffffffu, g, o);
-    if ((tid & 31) == 0) sred[tid >> 5] = g;
+    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = g;
     __syncthreads();
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
         double s = 0.0;
-        for (int w = 0; w < nth / 32; ++w) s += sred[w];
+        for (int w = 0; w < (int)blockDim.x / 32; ++w) s += sred[w];
         A.gh0[blockIdx.x] += s;
     }
+    // no CTA of the cluster exits while another may still read the workspace
+    // it wrote (all reads of this step are done at the last barrier)
+    if (cs > 1) cg::this_cluster().sync();
 }
 
 // magnetic faces: lambda_H = (value after the curl sweep) - q/2 + lamHin
@@ -534,7 +558,20 @@ cudaError_t adj_reverse_step(const LaunchSet &L, const AdjSet &A, long long n, i
     if (L.ncomp) {
         const cudaError_t e = cudaFuncSetAttribute(adj_mag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, A.fnb_bytes);
         if (e != cudaSuccess) return e;
-        adj_mag_kernel<<<L.ncomp, kMagThreads, A.fnb_bytes, s>>>(L, A, slot);
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(L.ncomp * A.cs);
+        cfg.blockDim = dim3(kMagThreads);
+        cfg.dynamicSmemBytes = A.fnb_bytes;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = A.cs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = A.cs > 1 ? 1 : 0;
+        const cudaError_t e2 = cudaLaunchKernelEx(&cfg, adj_mag_kernel, L, A, slot);
+        if (e2 != cudaSuccess) return e2;
     }
     const dim3 blk(32, 8), grid((A.nx + 31) / 32, (A.ny + 7) / 8, A.nz);
     if (L.cls16) adj_curl_h_kernel<uint16_t><<<grid, blk, 0, s>>>(L, A, n, slot);

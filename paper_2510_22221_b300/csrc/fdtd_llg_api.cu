@@ -2449,7 +2449,8 @@ extern "C" int fdtd_llg_adjoint_step(fdtd_llg_t h, const double *dJ_dE, double *
     A.ws = (float *)alloc(std::max<long long>(ws_tot, 1) * 4);
     long long *d_wsoff = (long long *)alloc(ws_off.size() * sizeof(long long));
     A.ws_off = d_wsoff;
-    A.gh0 = (double *)alloc(std::max(1, nc) * sizeof(double));
+    const int ngh = std::max(1, nc) * kMagClusterMax;   // one partial per magnet CTA
+    A.gh0 = (double *)alloc(ngh * sizeof(double));
     const long long nseed = N * std::max(1, np) * 3;
     double *d_seed = (double *)alloc(nseed * sizeof(double));
     A.seed = d_seed;
@@ -2470,7 +2471,7 @@ extern "C" int fdtd_llg_adjoint_step(fdtd_llg_t h, const double *dJ_dE, double *
     if (e == cudaSuccess) e = cudaMemsetAsync(A.lamH, 0, 6 * nf * 4, S->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(A.lamW, 0, I.n_wall() * 4, S->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(A.ws, 0, std::max<long long>(ws_tot, 1) * 4, S->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(A.gh0, 0, std::max(1, nc) * sizeof(double), S->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(A.gh0, 0, ngh * sizeof(double), S->stream);
     if (e == cudaSuccess && A.geps) e = cudaMemsetAsync(A.geps, 0, 3 * nbe * sizeof(double), S->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_wsoff, ws_off.data(), ws_off.size() * sizeof(long long), cudaMemcpyHostToDevice, S->stream);
     if (e == cudaSuccess && np) e = cudaMemcpyAsync(d_seed, dJ_dE, nseed * sizeof(double), cudaMemcpyHostToDevice, S->stream);
@@ -2480,6 +2481,7 @@ extern "C" int fdtd_llg_adjoint_step(fdtd_llg_t h, const double *dJ_dE, double *
     if (rc) { cleanup(); return rc; }
     LaunchSet L = launch_set(S);
     L.rec = 1;
+    A.cs = std::max(1, L.mag_cs);   // the reverse magnet kernel splits regions as the forward one does
     const long long tail = S->tail, tail0 = S->tail0, base = tail + 1;
     for (long long seg = nck - 1; seg >= 0 && e == cudaSuccess; --seg) {
         const long long na = seg * K, nb = std::min(N, na + K);
@@ -2509,7 +2511,7 @@ extern "C" int fdtd_llg_adjoint_step(fdtd_llg_t h, const double *dJ_dE, double *
     }
     if (e == cudaSuccess) e = adj_finish(L, A, S->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
-    std::vector<double> gh(std::max(1, nc), 0.0), ge(3 * nbe, 0.0);
+    std::vector<double> gh(ngh, 0.0), ge(3 * nbe, 0.0);
     if (e == cudaSuccess) e = cudaMemcpy(gh.data(), A.gh0, gh.size() * sizeof(double), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && nbe) e = cudaMemcpy(ge.data(), A.geps, ge.size() * sizeof(double), cudaMemcpyDeviceToHost);
     StepCtl st{};
@@ -2520,7 +2522,7 @@ extern "C" int fdtd_llg_adjoint_step(fdtd_llg_t h, const double *dJ_dE, double *
     if (st.status & ST_TAPE) return fail(h, FDTD_E_CUDA, "adjoint recomputation: a step fell outside its tape");
     if (grad_h0) {
         double s = 0.0;
-        for (int c = 0; c < nc; ++c) s += gh[c];
+        for (int c = 0; c < nc * A.cs; ++c) s += gh[c];
         *grad_h0 = s;
     }
     if (grad_eps && I.has_design) {

@@ -346,7 +346,8 @@ struct AdjSet {
     float *lamW;            // adjoint of the far-wall normal H (walls layout)
     float *ws;              // per-region workspace (ws_off[region] floats in)
     const long long *ws_off;
-    double *gh0;            // per region: d J / d |H_bias|
+    double *gh0;            // per magnet CTA (region c, rank r at c * cs + r): d J / d |H_bias|
+    int cs;                 // CTAs per region of adj_mag_kernel (a thread-block cluster when > 1)
     const double *seed;     // [nsteps][nprobe][3]: dJ/dE at the probe edges
     int nprobe;
     int nx, ny, nz;         // the instance's grid
