@@ -358,9 +358,11 @@ int fdtd_llg_get_tile_width(fdtd_llg_t h, int32_t *width);
  * 0 before the first step or sync after materials were set. */
 int fdtd_llg_get_tiling(fdtd_llg_t h, int32_t *planes);
 
-/* Autotuner of the tiling.  Runs trial_steps real steps (they advance the
- * simulation, fill the probe and energy rings and count in the step number)
- * with each of a fixed list of candidate plane counts (8, 12, 16, 24, 32, 48,
+/* Autotuner of the tiling.  Runs 3 trial_steps real steps per candidate (they
+ * advance the simulation, fill the probe and energy rings and count in the
+ * step number: one untimed call that builds the candidate's CUDA graphs, then
+ * the faster of two timed calls) with each of a fixed list of candidate plane
+ * counts (8, 12, 16, 24, 32, 48,
  * 64), the model's choice and the counts the model rates within 5 % of it
  * (at most 12: the model does not see how the tasks fill the last wave of
  * CTAs), first at the tile width of fewest padded cells and then at the
