@@ -223,6 +223,17 @@ int fdtd_llg_stream_results(fdtd_llg_t h, double *rows, double *energy, int64_t 
  * (1 after the first step; get_field then returns H, M at (n + 1/2) dt). */
 int fdtd_llg_time_state(fdtd_llg_t h, int64_t *step, int32_t *h_half_ahead);
 
+/* Diagnostic (section "Numerical Model", B = mu0 (H + M)): the discrete
+ * divergence of B / mu0 = H + M_face at every cell centre of the present
+ * state, M_face the mean of the magnetisation of the cells beside a face
+ * (zero outside magnets), in FP64 from the FP32 state, into out (host,
+ * caller-owned, nx*ny*nz values, compact layout).  The state holds H and M
+ * half a step ahead after the first step.  The leap-frog keeps
+ * div(B^n - B^0) at rounding.  Synchronises the stream.  Errors:
+ * FDTD_E_INVAL (batch handle, small buffer), FDTD_E_STATE (no materials),
+ * FDTD_E_CUDA. */
+int fdtd_llg_div_b(fdtd_llg_t h, double *out, size_t count);
+
 /* Read / write one field in the compact host layout (float32).  set_field
  * declares the state to be at integer time (H, M not half a step ahead).
  * FDTD_F_M* / FDTD_F_DM* entries outside magnets are zero and ignored on

@@ -75,6 +75,7 @@ SIGNATURES = {
     "fdtd_llg_energy": (C.c_int, [_vp, _dp, C.c_int64, _i64p]),
     "fdtd_llg_time_state": (C.c_int, [_vp, _i64p, C.POINTER(C.c_int32)]),
     "fdtd_llg_get_field": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_float), C.c_size_t]),
+    "fdtd_llg_div_b": (C.c_int, [_vp, _dp, C.c_size_t]),
     "fdtd_llg_set_field": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_float), C.c_size_t]),
     "fdtd_llg_planes": (C.c_int, [_vp, C.c_int32, C.c_int32, C.POINTER(C.c_float), C.c_size_t, C.c_int32]),
     "fdtd_llg_planes_device": (C.c_int, [_vp, C.c_int32, C.c_int32, _vp, C.c_size_t, C.c_int32]),

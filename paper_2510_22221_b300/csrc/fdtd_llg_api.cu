@@ -4,6 +4,7 @@
 #include "fdtd_llg_internal.h"
 #include "class_assign.h"
 #include "pml.h"
+#include "diag.h"
 
 #include <cudaTypedefs.h>
 
@@ -1748,6 +1749,38 @@ static int magnet_read(fdtd_llg_t h, Instance &I, std::vector<std::vector<double
         out.push_back(std::move(g));
         mats.push_back(std::move(mt));
     }
+    return FDTD_OK;
+}
+
+extern "C" int fdtd_llg_div_b(fdtd_llg_t h, double *out, size_t count)
+{
+    if (!is_member(h)) return fail(h, FDTD_E_INVAL, "div_b needs an instance handle");
+    Instance *I = inst_of(h);
+    const size_t nc = (size_t)I->nx * I->ny * I->nz;
+    if (!out || count < nc) return fail(h, FDTD_E_INVAL, "output too small");
+    int rc = sync_status(h);
+    if (rc) return rc;
+    rc = upload_descriptors(h);
+    if (rc) return rc;
+    Sim *S = h->sim;
+    const int idx = h->index < 0 ? 0 : h->index;
+    double *dM = nullptr, *dout = nullptr;
+    MagComp *dc = nullptr;
+    const size_t ncomp = I->comps.size();
+    cudaError_t e = cudaMalloc(&dM, 3 * nc * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&dout, nc * sizeof(double));
+    if (e == cudaSuccess && ncomp) e = cudaMalloc(&dc, ncomp * sizeof(MagComp));
+    if (e == cudaSuccess && ncomp)
+        e = cudaMemcpyAsync(dc, I->comps.data(), ncomp * sizeof(MagComp), cudaMemcpyHostToDevice, S->stream);
+    if (e == cudaSuccess)
+        e = launch_div_b(S->d_insts + idx, dc, (int)ncomp, S->cur, (long long)nc, I->dx, I->dy, I->dz, dM, dout,
+                         S->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, nc * sizeof(double), cudaMemcpyDeviceToHost, S->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    cudaFree(dM);
+    cudaFree(dout);
+    cudaFree(dc);
+    if (e != cudaSuccess) return fail(h, FDTD_E_CUDA, std::string("div_b: ") + cudaGetErrorString(e));
     return FDTD_OK;
 }
 

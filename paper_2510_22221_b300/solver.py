@@ -262,6 +262,14 @@ class FdtdLlg:
         nx, ny, nz = self._dims
         return {"Hx_wall": (nz, ny), "Hy_wall": (nz, nx), "Hz_wall": (ny, nx)}.get(name, (nz, ny, nx))
 
+    def div_b(self) -> np.ndarray:
+        """div(H + M_face) at every cell centre of the present state, FP64,
+        shape (nz, ny, nx)."""
+        n = int(self._dims[0]) * int(self._dims[1]) * int(self._dims[2])
+        out = np.zeros(n)
+        check(_abi.load().fdtd_llg_div_b(self._h, out.ctypes.data_as(C.POINTER(C.c_double)), n), self._h)
+        return out.reshape(self._dims[2], self._dims[1], self._dims[0])
+
     def get_field(self, name: str) -> np.ndarray:
         shp = self._shape(name)
         out = np.zeros(shp, dtype=np.float32)
