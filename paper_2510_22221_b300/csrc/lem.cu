@@ -7,12 +7,16 @@
 // Recurrent kernels.  One CTA advances 4 R sequences (R = 1 or 2) through
 // every step of both stacks, with the two cells' weights of the stack in
 // shared memory (about 200 KB at D = 64) and the states beside them; 4 D
-// threads, thread (g, i) owning hidden unit i of sequences g + 4 r.  The time loop is
-// sequential, so a step costs a chain of dependent phases (gates and z, one
-// barrier, y, one barrier, per cell; the head) rather than bandwidth; the
-// batch is spread over ceil(batch / 4 R) CTAs.  Activations of every step are
-// saved (y, z, the two sigmoid gates and the two tanh values) for the
-// reverse pass.
+// threads.  In a product W y (or W^T g) thread (i, r) sums, for output i,
+// the summed indices of quarter r for every sequence of the CTA, so each
+// weight read from shared memory serves all 4 R sequences; the 4 lanes of
+// an output then reduce-scatter by warp shuffles, lane r keeping the sums of
+// sequences r + 4 rr, whose element-wise updates it makes.  The time loop is
+// sequential, so a step costs a chain of dependent phases (the gates and z,
+// one barrier, y, one barrier, per cell; the head, one barrier) rather than
+// bandwidth; the batch is spread over ceil(batch / 4 R) CTAs.  Activations
+// of every step are saved (y, z, the two sigmoid gates and the two tanh
+// values) for the reverse pass.
 //
 // Weight gradients.  The reverse kernel stores the gradients of the four gate
 // pre-activations of every step; each weight gradient is then a sum over
@@ -161,43 +165,85 @@ constexpr int fwd_smem_floats()
 template <int D, int R>
 constexpr int bwd_smem_floats()
 {
-    return 3 * 4 * D * D + 4 * kMMax * D + kMMax * D + 2 * 4 * (kG * R) * D + 2 * (kG * R) * kMMax;
+    return 3 * 4 * D * D + 4 * kMMax * D + kMMax * D + 2 * 4 * (kG * R) * D + (kG * R) * kMMax;
 }
 
-// Weights of cell c into shared memory.  TR: W and V transposed ([q][j][i],
-// unit i fastest, for the forward products W y), else as stored ([q][i][j],
-// for the reverse products W^T g).  V goes to V1 (width D) or V0 (width m).
-template <int D, bool TR>
+// Position of entry (o, k) of a D x D product matrix (output o, summed
+// index k) in shared memory: k in blocks of 16, each block a [D][16] slab, so
+// that lane (o, r) reads the float4 of k = 16 t + 4 r .. + 3 and the 32 lanes
+// of a warp (8 outputs x 4 quarters) read 512 contiguous bytes.
+template <int D>
+__device__ __forceinline__ int qx(int o, int k)
+{
+    return ((k >> 4) * D + o) * 16 + (k & 15);
+}
+
+// Weights of cell c into shared memory.  W (and V of a width-D input) in
+// the product layout qx: REV false for the forward products (output = row
+// i, summed index = column j), true for the reverse products W^T g (output =
+// column, summed index = row).  The m-wide input weights of a first cell:
+// [q][c][i] forward, as stored ([q][i][c]) reverse.
+template <int D, bool REV>
 __device__ void load_cell(const float *theta, int c, int m, float *W, float *V, float *bb)
 {
     const int mc = (c & 1) ? D : m;
     const float *src = theta + cell_offset(c, D, m);
     for (int e = threadIdx.x; e < 4 * D * D; e += blockDim.x) {
-        const int q = e / (D * D), r = e % (D * D), i = r / D, j = r % D;
-        W[TR ? (q * D + j) * D + i : e] = src[e];
+        const int q = e / (D * D), rc = e % (D * D), row = rc / D, col = rc % D;
+        W[q * D * D + (REV ? qx<D>(col, row) : qx<D>(row, col))] = src[e];
     }
     src += 4 * D * D;
     for (int e = threadIdx.x; e < 4 * D * mc; e += blockDim.x) {
-        const int q = e / (D * mc), r = e % (D * mc), i = r / mc, j = r % mc;
-        V[TR ? (q * mc + j) * D + i : e] = src[e];
+        const int q = e / (D * mc), rc = e % (D * mc), row = rc / mc, col = rc % mc;
+        if (mc == D) V[q * D * D + (REV ? qx<D>(col, row) : qx<D>(row, col))] = src[e];
+        else V[REV ? e : (q * mc + col) * D + row] = src[e];
     }
     src += 4 * D * mc;
     if (bb)
         for (int e = threadIdx.x; e < 4 * D; e += blockDim.x) bb[e] = src[e];
 }
 
-// Forward pass of kG R sequences (see the file comment).  Thread (g, i) =
-// (tid / D, tid % D) owns unit i of sequences g + kG r, r < R.
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ float dot4(float4 w, float4 v, float a)
+{
+    return fmaf(w.w, v.w, fmaf(w.z, v.z, fmaf(w.y, v.y, fmaf(w.x, v.x, a))));
+}
+
+// Reduce-scatter over the 4 lanes (o, 0..3) of one output: lane r holds
+// the quarter-r partials a0..a3 of sequences 0..3 of a group and gets the
+// whole sum of sequence r.  Every sequence's sum is (q0 + q2) + (q1 + q3)
+// of its quarter partials, whichever lane finishes it.
+__device__ __forceinline__ float rs4(float a0, float a1, float a2, float a3, int r)
+{
+    const bool hi = r & 2, lo = r & 1;
+    float k0 = hi ? a2 : a0, k1 = hi ? a3 : a1;
+    k0 += __shfl_xor_sync(0xffffffffu, hi ? a0 : a2, 2);
+    k1 += __shfl_xor_sync(0xffffffffu, hi ? a1 : a3, 2);
+    return (lo ? k1 : k0) + __shfl_xor_sync(0xffffffffu, lo ? k0 : k1, 1);
+}
+
+// Sum over the 32 lanes of a warp (the same bits in every lane)
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Forward pass of kG R sequences (see the file comment).  Thread (i, r) =
+// (tid / 4, tid % 4): in the products, output unit i over the summed
+// indices of quarter r for every sequence of the CTA; in the element-wise
+// updates, unit i of sequences r + 4 rr, rr < R.
 template <int D, int R>
 __global__ void __launch_bounds__(kG *D, 1) lem_fwd_kernel(LemArgs A)
 {
-    constexpr int kR = R, kBT = kG * R;
-    extern __shared__ float sm[];
-    float *WT0 = sm, *WT1 = WT0 + 4 * D * D, *VT1 = WT1 + 4 * D * D, *VT0 = VT1 + 4 * D * D;
-    float *bb0 = VT0 + 4 * kMMax * D, *bb1 = bb0 + 4 * D, *Wo = bb1 + 4 * D;
+    constexpr int kBT = kG * R, kT = D / 16, kNW = D / 8, kHO = (kBT * kMMax + kNW - 1) / kNW;
+    extern __shared__ __align__(16) float sm[];
+    float *W0 = sm, *W1 = W0 + 4 * D * D, *V1 = W1 + 4 * D * D, *V0 = V1 + 4 * D * D;
+    float *bb0 = V0 + 4 * kMMax * D, *bb1 = bb0 + 4 * D, *Wo = bb1 + 4 * D;
     float *Y = Wo + kMMax * D, *Z = Y + 2 * kBT * D, *X = Z + 2 * kBT * D;
-    const int tid = threadIdx.x, i = tid % D, g = tid / D, m = A.m, B = A.B;
-    const int b0 = blockIdx.x * kBT;
+    const int tid = threadIdx.x, i = tid >> 2, r = tid & 3, lane = tid & 31, warp = tid >> 5;
+    const int m = A.m, B = A.B, b0 = blockIdx.x * kBT;
     const float dt = A.dt;
     for (int e = tid; e < m * D; e += blockDim.x) Wo[e] = A.theta[cell_offset(4, D, m) + e];
     for (int e = tid; e < 2 * kBT * D; e += blockDim.x) Y[e] = Z[e] = 0.f;
@@ -207,8 +253,8 @@ __global__ void __launch_bounds__(kG *D, 1) lem_fwd_kernel(LemArgs A)
         float *res = wp<float>(A, ph ? A.L.out : A.L.recon);
         float *xdec = wp<float>(A, A.L.xdec);
         __syncthreads();   // the previous phase is done with the weights
-        load_cell<D, true>(A.theta, 2 * ph, m, WT0, VT0, bb0);
-        load_cell<D, true>(A.theta, 2 * ph + 1, m, WT1, VT1, bb1);
+        load_cell<D, false>(A.theta, 2 * ph, m, W0, V0, bb0);
+        load_cell<D, false>(A.theta, 2 * ph + 1, m, W1, V1, bb1);
         // the first input: u_0 (encoder) or 0 (decoder)
         for (int t = tid; t < kBT * m; t += blockDim.x) {
             const int s = t / m, c = t % m, b = b0 + s;
@@ -217,9 +263,11 @@ __global__ void __launch_bounds__(kG *D, 1) lem_fwd_kernel(LemArgs A)
             if (ph == 1 && b < B) xdec[(long long)b * m + c] = 0.f;
         }
         // slot 0 of the saved activations: the initial states
+#pragma unroll
         for (int l = 0; l < 2; ++l)
-            for (int r = 0; r < kR; ++r) {
-                const int s = g + kG * r, b = b0 + s;
+#pragma unroll
+            for (int rr = 0; rr < R; ++rr) {
+                const int s = r + kG * rr, b = b0 + s;
                 if (b < B) {
                     float *a = act[l] + (long long)b * kQ * D + i;
                     a[0] = Y[(l * kBT + s) * D + i];
@@ -228,82 +276,135 @@ __global__ void __launch_bounds__(kG *D, 1) lem_fwd_kernel(LemArgs A)
             }
         __syncthreads();
         for (int n = 0; n < T; ++n) {
+            // the encoder's next input, fetched now for the head at the end of the step
+            float un[kHO];
+#pragma unroll
+            for (int h = 0; h < kHO; ++h) {
+                const int o = warp + h * kNW, s = o / m, c = o % m, b = b0 + s;
+                un[h] = (ph == 0 && n + 1 < T && lane == 0 && o < kBT * m && b < B)
+                            ? A.u[((long long)(n + 1) * B + b) * m + c]
+                            : 0.f;
+            }
 #pragma unroll
             for (int l = 0; l < 2; ++l) {
-                const float *WT = l ? WT1 : WT0, *VT = l ? VT1 : VT0, *bb = l ? bb1 : bb0;
-                const int mi = l ? D : m, xs = l ? D : kMMax;
-                const float *xin = l ? Y : X;   // layer 1 reads layer 0's y_n
-                float s1[kR], s2[kR], tz[kR], ay[kR], yp[kR], zn[kR];
+                const float *W = l ? W1 : W0, *bb = l ? bb1 : bb0;
+                const float *yv = Y + l * kBT * D, *xv = Y;   // cell 1's input is cell 0's y_n
+                constexpr int kNQ = 4;
+                float acc[kNQ][kBT];
 #pragma unroll
-                for (int r = 0; r < kR; ++r) {
-                    const int s = g + kG * r;
-                    float a1 = bb[i], a2 = bb[D + i], az = bb[2 * D + i], a4 = bb[3 * D + i];
-                    const float *x = xin + s * xs;
-                    for (int c = 0; c < mi; ++c) {
-                        const float xv = x[c];
-                        a1 = fmaf(VT[(0 * mi + c) * D + i], xv, a1);
-                        a2 = fmaf(VT[(1 * mi + c) * D + i], xv, a2);
-                        az = fmaf(VT[(2 * mi + c) * D + i], xv, az);
-                        a4 = fmaf(VT[(3 * mi + c) * D + i], xv, a4);
+                for (int q = 0; q < kNQ; ++q)
+#pragma unroll
+                    for (int s = 0; s < kBT; ++s) acc[q][s] = 0.f;
+                // gates: W y_{n-1} (+ V x_n for cell 1), quarter r of the summed index
+#pragma unroll
+                for (int t = 0; t < kT; ++t) {
+                    const int wo = (t * D + i) * 16 + 4 * r, vo = 16 * t + 4 * r;
+                    float4 w[3];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) w[q] = ld4(W + q * D * D + wo);
+#pragma unroll
+                    for (int s = 0; s < kBT; ++s) {
+                        const float4 y4 = ld4(yv + s * D + vo);
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) acc[q][s] = dot4(w[q], y4, acc[q][s]);
                     }
-                    const float *yv = Y + (l * kBT + s) * D;
-#pragma unroll 8
-                    for (int j = 0; j < D; ++j) {
-                        const float yj = yv[j];
-                        a1 = fmaf(WT[(0 * D + j) * D + i], yj, a1);
-                        a2 = fmaf(WT[(1 * D + j) * D + i], yj, a2);
-                        az = fmaf(WT[(2 * D + j) * D + i], yj, az);
+                    if (l) {
+                        float4 v[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) v[q] = ld4(V1 + q * D * D + wo);
+#pragma unroll
+                        for (int s = 0; s < kBT; ++s) {
+                            const float4 x4 = ld4(xv + s * D + vo);
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) acc[q][s] = dot4(v[q], x4, acc[q][s]);
+                        }
                     }
-                    yp[r] = yv[i];
-                    const float zp = Z[(l * kBT + s) * D + i];
-                    s1[r] = sigm(a1);
-                    s2[r] = sigm(a2);
-                    tz[r] = tanhf(az);
-                    const float h1 = dt * s1[r];
-                    zn[r] = fmaf(h1, tz[r], (1.f - h1) * zp);
-                    ay[r] = a4;
                 }
-                __syncthreads();   // every read of this cell's y_{n-1} and input is done
+                float s1[R], s2[R], ay[R], yp[R], zn[R], tz[R];
 #pragma unroll
-                for (int r = 0; r < kR; ++r) Z[(l * kBT + g + kG * r) * D + i] = zn[r];
+                for (int rr = 0; rr < R; ++rr) {
+                    float g[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        g[q] = (q < 3 || l) ? rs4(acc[q][4 * rr], acc[q][4 * rr + 1], acc[q][4 * rr + 2],
+                                                  acc[q][4 * rr + 3], r)
+                                            : 0.f;
+                    const int s = r + kG * rr;
+                    float a1 = bb[i], a2 = bb[D + i], az = bb[2 * D + i], a4 = bb[3 * D + i];
+                    if (!l) {
+                        const float *x = X + s * kMMax;
+                        for (int c = 0; c < m; ++c) {
+                            const float xc = x[c];
+                            a1 = fmaf(V0[(0 * m + c) * D + i], xc, a1);
+                            a2 = fmaf(V0[(1 * m + c) * D + i], xc, a2);
+                            az = fmaf(V0[(2 * m + c) * D + i], xc, az);
+                            a4 = fmaf(V0[(3 * m + c) * D + i], xc, a4);
+                        }
+                    }
+                    a1 += g[0];
+                    a2 += g[1];
+                    az += g[2];
+                    ay[rr] = a4 + g[3];
+                    yp[rr] = yv[s * D + i];
+                    const float zp = Z[(l * kBT + s) * D + i];
+                    s1[rr] = sigm(a1);
+                    s2[rr] = sigm(a2);
+                    tz[rr] = tanhf(az);
+                    const float h1 = dt * s1[rr];
+                    zn[rr] = fmaf(h1, tz[rr], (1.f - h1) * zp);
+                    // z_n of unit i: read by no other thread before the barrier
+                    Z[(l * kBT + s) * D + i] = zn[rr];
+                }
                 __syncthreads();
+                // y gate: a4 += W_4 z_n
+                float a4p[kBT];
 #pragma unroll
-                for (int r = 0; r < kR; ++r) {
-                    const int s = g + kG * r, b = b0 + s;
-                    const float *zv = Z + (l * kBT + s) * D;
-                    float a4 = ay[r];
-#pragma unroll 8
-                    for (int j = 0; j < D; ++j) a4 = fmaf(WT[(3 * D + j) * D + i], zv[j], a4);
-                    const float ty = tanhf(a4), h2 = dt * s2[r];
-                    const float yn = fmaf(h2, ty, (1.f - h2) * yp[r]);
+                for (int s = 0; s < kBT; ++s) a4p[s] = 0.f;
+                const float *zv = Z + l * kBT * D;
+#pragma unroll
+                for (int t = 0; t < kT; ++t) {
+                    const float4 w = ld4(W + 3 * D * D + (t * D + i) * 16 + 4 * r);
+#pragma unroll
+                    for (int s = 0; s < kBT; ++s) a4p[s] = dot4(w, ld4(zv + s * D + 16 * t + 4 * r), a4p[s]);
+                }
+#pragma unroll
+                for (int rr = 0; rr < R; ++rr) {
+                    const float a4 = ay[rr] + rs4(a4p[4 * rr], a4p[4 * rr + 1], a4p[4 * rr + 2], a4p[4 * rr + 3], r);
+                    const int s = r + kG * rr, b = b0 + s;
+                    const float ty = tanhf(a4), h2 = dt * s2[rr];
+                    const float yn = fmaf(h2, ty, (1.f - h2) * yp[rr]);
                     Y[(l * kBT + s) * D + i] = yn;
                     if (b < B) {
                         float *a = act[l] + ((long long)(n + 1) * B + b) * kQ * D + i;
                         a[0] = yn;
-                        a[D] = zn[r];
-                        a[2 * D] = s1[r];
-                        a[3 * D] = s2[r];
-                        a[4 * D] = tz[r];
+                        a[D] = zn[rr];
+                        a[2 * D] = s1[rr];
+                        a[3 * D] = s2[rr];
+                        a[4 * D] = tz[rr];
                         a[5 * D] = ty;
                     }
                 }
                 __syncthreads();
             }
-            // the head: o = Wo y of the top cell; the next input
-            for (int t = tid; t < kBT * m; t += blockDim.x) {
-                const int s = t / m, c = t % m, b = b0 + s;
-                const float *yv = Y + (kBT + s) * D;
-                float o = 0.f;
-                for (int k = 0; k < D; ++k) o = fmaf(Wo[c * D + k], yv[k], o);
-                if (b < B) res[((long long)n * B + b) * m + c] = o;
-                if (n + 1 < T) {
-                    float x;
-                    if (ph == 0) x = b < B ? A.u[((long long)(n + 1) * B + b) * m + c] : 0.f;
-                    else {
-                        x = o;
-                        if (b < B) xdec[((long long)(n + 1) * B + b) * m + c] = o;
+            // the head: o = Wo y of the top cell, one warp per output; the next input
+#pragma unroll
+            for (int h = 0; h < kHO; ++h) {
+                const int o = warp + h * kNW;
+                if (o < kBT * m) {
+                    const int s = o / m, c = o % m, b = b0 + s;
+                    const float *yv = Y + (kBT + s) * D;
+                    float p = 0.f;
+#pragma unroll
+                    for (int k = lane; k < D; k += 32) p = fmaf(Wo[c * D + k], yv[k], p);
+                    p = warp_sum(p);
+                    if (lane == 0) {
+                        if (b < B) res[((long long)n * B + b) * m + c] = p;
+                        if (n + 1 < T) {
+                            const float x = ph == 0 ? un[h] : p;
+                            if (ph == 1 && b < B) xdec[((long long)(n + 1) * B + b) * m + c] = p;
+                            X[s * kMMax + c] = x;
+                        }
                     }
-                    X[s * kMMax + c] = x;
                 }
             }
             __syncthreads();
@@ -467,30 +568,45 @@ __global__ void lem_loss_final_kernel(const double *lpart, int nblk, long long N
 namespace {
 
 // ---------------------------------------------------------------- reverse
+// The saved values of one unit, sequence and step that the reverse step
+// reads: y_{n-1}, z_{n-1} (slot n) and the gates and tanh values of step n
+// (slot n + 1).
+struct Saved {
+    float yp, zp, s1, s2, tz, ty;
+};
+template <int D>
+__device__ __forceinline__ Saved fetch_saved(const float *act, int B, int n, int b, int i)
+{
+    const float *a0 = act + ((long long)n * B + b) * kQ * D + i;
+    const float *a1 = act + ((long long)(n + 1) * B + b) * kQ * D + i;
+    return {a0[0], a0[D], a1[2 * D], a1[3 * D], a1[4 * D], a1[5 * D]};
+}
+
 // Back-propagation through both stacks for kG R sequences: the decoder's steps
-// in reverse (with the output feedback: the gradient of step k's input is
-// added to the gradient of output k-1), then the encoder's.  Thread (g, i)
-// carries dL/dy and dL/dz of unit i of its two sequences for both cells in
-// registers; the gate gradients of each step go to shared memory for the
-// products with W^T and V^T and to the work space for the weight sums.
+// in reverse (with the output feedback: the gradient of step k+1's input is
+// added to the gradient of output k), then the encoder's.  Thread (i, r) =
+// (tid / 4, tid % 4) carries dL/dy and dL/dz of unit i of sequences r + 4 rr
+// for both cells in registers and, in the products W^T g, sums quarter r of
+// the summed index for every sequence of the CTA.  The gate gradients of
+// each step go to shared memory for those products and to the work space
+// for the weight sums; the saved activations are fetched one step ahead.
 template <int D, int R>
 __global__ void __launch_bounds__(kG *D, 1) lem_bwd_kernel(LemArgs A)
 {
-    constexpr int kR = R, kBT = kG * R;
-    extern __shared__ float sm[];
+    constexpr int kBT = kG * R, kT = D / 16, kNW = D / 8, kHO = (kBT * kMMax + kNW - 1) / kNW;
+    extern __shared__ __align__(16) float sm[];
     float *W0 = sm, *W1 = W0 + 4 * D * D, *V1 = W1 + 4 * D * D, *V0 = V1 + 4 * D * D;
     float *Wo = V0 + 4 * kMMax * D, *DG = Wo + kMMax * D;   // DG [2][4][kBT][D]
-    float *DO = DG + 2 * 4 * kBT * D, *FB = DO + kBT * kMMax;
-    const int tid = threadIdx.x, i = tid % D, g = tid / D, m = A.m, B = A.B;
-    const int b0 = blockIdx.x * kBT;
+    float *DO = DG + 2 * 4 * kBT * D;
+    const int tid = threadIdx.x, i = tid >> 2, r = tid & 3, lane = tid & 31, warp = tid >> 5;
+    const int m = A.m, B = A.B, b0 = blockIdx.x * kBT;
     const float dt = A.dt;
     for (int e = tid; e < m * D; e += blockDim.x) Wo[e] = A.theta[cell_offset(4, D, m) + e];
-    for (int e = tid; e < kBT * kMMax; e += blockDim.x) FB[e] = 0.f;
-    float dy[2][kR], dz[2][kR];
+    float dy[2][R], dz[2][R];
 #pragma unroll
     for (int l = 0; l < 2; ++l)
 #pragma unroll
-        for (int r = 0; r < kR; ++r) dy[l][r] = dz[l][r] = 0.f;
+        for (int rr = 0; rr < R; ++rr) dy[l][rr] = dz[l][rr] = 0.f;
     for (int ph = 1; ph >= 0; --ph) {
         const int T = ph ? A.t_out : A.t_in;
         const float *act[2] = {wp<float>(A, A.L.act[ph][0]), wp<float>(A, A.L.act[ph][1])};
@@ -498,115 +614,155 @@ __global__ void __launch_bounds__(kG *D, 1) lem_bwd_kernel(LemArgs A)
         const float *dsrc = wp<float>(A, ph ? A.L.dout : A.L.drec);
         float *dot = wp<float>(A, A.L.dot);
         __syncthreads();   // the previous phase is done with the weights
-        load_cell<D, false>(A.theta, 2 * ph, m, W0, V0, nullptr);
-        load_cell<D, false>(A.theta, 2 * ph + 1, m, W1, V1, nullptr);
+        load_cell<D, true>(A.theta, 2 * ph, m, W0, V0, nullptr);
+        load_cell<D, true>(A.theta, 2 * ph + 1, m, W1, V1, nullptr);
+        // step T-1's saved values and loss gradients
+        Saved sv[2][R];
+        float dl[kHO];
+#pragma unroll
+        for (int l = 0; l < 2; ++l)
+#pragma unroll
+            for (int rr = 0; rr < R; ++rr) sv[l][rr] = fetch_saved<D>(act[l], B, T - 1, min(b0 + r + kG * rr, B - 1), i);
+#pragma unroll
+        for (int h = 0; h < kHO; ++h) {
+            const int o = warp + h * kNW, b = b0 + o / m;
+            dl[h] = (lane == 0 && o < kBT * m && b < B) ? dsrc[((long long)(T - 1) * B + b) * m + o % m] : 0.f;
+        }
         __syncthreads();
         for (int n = T - 1; n >= 0; --n) {
             // gradient at the head's output: the loss's, plus (decoder) the
-            // feedback from step n+1's input
-            for (int t = tid; t < kBT * m; t += blockDim.x) {
-                const int s = t / m, c = t % m, b = b0 + s;
-                float v = 0.f;
-                if (b < B) {
-                    v = dsrc[((long long)n * B + b) * m + c];
-                    if (ph) {
-                        v += FB[s * kMMax + c];
-                        dot[((long long)n * B + b) * m + c] = v;
+            // feedback from step n+1's input through cell 0's input weights
+            // (cell 0's gate gradients of step n+1 are still in DG)
+#pragma unroll
+            for (int h = 0; h < kHO; ++h) {
+                const int o = warp + h * kNW;
+                if (o < kBT * m) {
+                    const int s = o / m, c = o % m, b = b0 + s;
+                    float fb = 0.f;
+                    if (ph && n + 1 < T) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+#pragma unroll
+                            for (int k = lane; k < D; k += 32)
+                                fb = fmaf(V0[(q * D + k) * m + c], DG[(q * kBT + s) * D + k], fb);
+                        fb = warp_sum(fb);
                     }
+                    if (lane == 0) {
+                        float v = 0.f;
+                        if (b < B) {
+                            v = dl[h];
+                            if (ph) {
+                                v += fb;
+                                dot[((long long)n * B + b) * m + c] = v;
+                            }
+                        }
+                        DO[s * kMMax + c] = v;
+                    }
+                    // the next step's loss gradient
+                    dl[h] = (lane == 0 && n > 0 && b < B) ? dsrc[((long long)(n - 1) * B + b) * m + c] : 0.f;
                 }
-                DO[s * kMMax + c] = v;
             }
+            // the next step's saved values
+            Saved nx[2][R];
+#pragma unroll
+            for (int l = 0; l < 2; ++l)
+#pragma unroll
+                for (int rr = 0; rr < R; ++rr)
+                    nx[l][rr] = fetch_saved<D>(act[l], B, n > 0 ? n - 1 : 0, min(b0 + r + kG * rr, B - 1), i);
             __syncthreads();
 #pragma unroll
-            for (int r = 0; r < kR; ++r) {
-                const int s = g + kG * r;
-                float a = dy[1][r];
+            for (int rr = 0; rr < R; ++rr) {
+                const int s = r + kG * rr;
+                float a = dy[1][rr];
                 for (int c = 0; c < m; ++c) a = fmaf(Wo[c * D + i], DO[s * kMMax + c], a);
-                dy[1][r] = a;
+                dy[1][rr] = a;
             }
 #pragma unroll
             for (int l = 1; l >= 0; --l) {
                 const float *W = l ? W1 : W0;
                 float *dgl = DG + l * 4 * kBT * D;
-                float yp[kR], zp[kR], S1[kR], TZ[kR], dg2[kR], dyp[kR];
+                float dg2[R], dgy[R], dyp[R];
 #pragma unroll
-                for (int r = 0; r < kR; ++r) {
-                    const int s = g + kG * r, b = min(b0 + s, B - 1);
-                    const float *a0 = act[l] + ((long long)n * B + b) * kQ * D + i;        // slot n: y_{n-1}, z_{n-1}
-                    const float *a1 = act[l] + ((long long)(n + 1) * B + b) * kQ * D + i;  // slot n+1: this step
-                    yp[r] = a0[0];
-                    zp[r] = a0[D];
-                    S1[r] = a1[2 * D];
-                    const float S2 = a1[3 * D];
-                    TZ[r] = a1[4 * D];
-                    const float TY = a1[5 * D];
-                    const float gy = dy[l][r];
-                    dg2[r] = gy * (TY - yp[r]) * dt * S2 * (1.f - S2);
-                    dgl[(3 * kBT + s) * D + i] = gy * dt * S2 * (1.f - TY * TY);
-                    dyp[r] = gy * (1.f - dt * S2);
+                for (int rr = 0; rr < R; ++rr) {
+                    const Saved &v = sv[l][rr];
+                    const float gy = dy[l][rr];
+                    dg2[rr] = gy * (v.ty - v.yp) * dt * v.s2 * (1.f - v.s2);
+                    dgy[rr] = gy * dt * v.s2 * (1.f - v.ty * v.ty);
+                    dgl[(3 * kBT + r + kG * rr) * D + i] = dgy[rr];
+                    dyp[rr] = gy * (1.f - dt * v.s2);
                 }
                 __syncthreads();
-                float dzp[kR];
+                // dz: W_4^T of the y gate's gradient
+                float az[kBT];
 #pragma unroll
-                for (int r = 0; r < kR; ++r) {
-                    const int s = g + kG * r, b = b0 + s;
-                    const float *gy = dgl + (3 * kBT + s) * D;
-                    float dzt = dz[l][r];
-#pragma unroll 8
-                    for (int k = 0; k < D; ++k) dzt = fmaf(W[(3 * D + k) * D + i], gy[k], dzt);
-                    const float dg1 = dzt * (TZ[r] - zp[r]) * dt * S1[r] * (1.f - S1[r]);
-                    const float dgz = dzt * dt * S1[r] * (1.f - TZ[r] * TZ[r]);
-                    dzp[r] = dzt * (1.f - dt * S1[r]);
+                for (int s = 0; s < kBT; ++s) az[s] = 0.f;
+#pragma unroll
+                for (int t = 0; t < kT; ++t) {
+                    const float4 w = ld4(W + 3 * D * D + (t * D + i) * 16 + 4 * r);
+#pragma unroll
+                    for (int s = 0; s < kBT; ++s) az[s] = dot4(w, ld4(dgl + (3 * kBT + s) * D + 16 * t + 4 * r), az[s]);
+                }
+                float dzp[R];
+#pragma unroll
+                for (int rr = 0; rr < R; ++rr) {
+                    const Saved &v = sv[l][rr];
+                    const int s = r + kG * rr, b = b0 + s;
+                    const float dzt = dz[l][rr] + rs4(az[4 * rr], az[4 * rr + 1], az[4 * rr + 2], az[4 * rr + 3], r);
+                    const float dg1 = dzt * (v.tz - v.zp) * dt * v.s1 * (1.f - v.s1);
+                    const float dgz = dzt * dt * v.s1 * (1.f - v.tz * v.tz);
+                    dzp[rr] = dzt * (1.f - dt * v.s1);
                     dgl[(0 * kBT + s) * D + i] = dg1;
-                    dgl[(1 * kBT + s) * D + i] = dg2[r];
+                    dgl[(1 * kBT + s) * D + i] = dg2[rr];
                     dgl[(2 * kBT + s) * D + i] = dgz;
                     if (b < B) {
                         float *o = dgo[l] + ((long long)n * B + b) * 4 * D + i;
                         o[0] = dg1;
-                        o[D] = dg2[r];
+                        o[D] = dg2[rr];
                         o[2 * D] = dgz;
-                        o[3 * D] = gy[i];
+                        o[3 * D] = dgy[rr];
                     }
                 }
                 __syncthreads();
+                // dy_{n-1}: W^T of the other three gates; cell 1 also gives
+                // cell 0's dy_n through V^T of all four
+                float ay[kBT], ax[kBT];
 #pragma unroll
-                for (int r = 0; r < kR; ++r) {
-                    const int s = g + kG * r;
-                    const float *g1 = dgl + (0 * kBT + s) * D, *g2 = dgl + (1 * kBT + s) * D, *gz = dgl + (2 * kBT + s) * D;
-                    float a = dyp[r];
-#pragma unroll 8
-                    for (int k = 0; k < D; ++k) {
-                        a = fmaf(W[(0 * D + k) * D + i], g1[k], a);
-                        a = fmaf(W[(1 * D + k) * D + i], g2[k], a);
-                        a = fmaf(W[(2 * D + k) * D + i], gz[k], a);
+                for (int s = 0; s < kBT; ++s) ay[s] = ax[s] = 0.f;
+#pragma unroll
+                for (int t = 0; t < kT; ++t) {
+                    const int wo = (t * D + i) * 16 + 4 * r, go = 16 * t + 4 * r;
+                    float4 w[3];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) w[q] = ld4(W + q * D * D + wo);
+                    float4 v[4];
+                    if (l) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) v[q] = ld4(V1 + q * D * D + wo);
                     }
-                    dy[l][r] = a;
-                    dz[l][r] = dzp[r];
-                    if (l == 1) {   // the input of cell 1 is cell 0's y_n
-                        const float *gy = dgl + (3 * kBT + s) * D;
-                        float x = 0.f;
-#pragma unroll 8
-                        for (int k = 0; k < D; ++k) {
-                            x = fmaf(V1[(0 * D + k) * D + i], g1[k], x);
-                            x = fmaf(V1[(1 * D + k) * D + i], g2[k], x);
-                            x = fmaf(V1[(2 * D + k) * D + i], gz[k], x);
-                            x = fmaf(V1[(3 * D + k) * D + i], gy[k], x);
+#pragma unroll
+                    for (int s = 0; s < kBT; ++s) {
+                        float4 g[4];
+#pragma unroll
+                        for (int q = 0; q < (l ? 4 : 3); ++q) g[q] = ld4(dgl + (q * kBT + s) * D + go);
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) ay[s] = dot4(w[q], g[q], ay[s]);
+                        if (l) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) ax[s] = dot4(v[q], g[q], ax[s]);
                         }
-                        dy[0][r] += x;
                     }
+                }
+#pragma unroll
+                for (int rr = 0; rr < R; ++rr) {
+                    dy[l][rr] = dyp[rr] + rs4(ay[4 * rr], ay[4 * rr + 1], ay[4 * rr + 2], ay[4 * rr + 3], r);
+                    dz[l][rr] = dzp[rr];
+                    if (l) dy[0][rr] += rs4(ax[4 * rr], ax[4 * rr + 1], ax[4 * rr + 2], ax[4 * rr + 3], r);
                 }
             }
-            // decoder: the gradient of this step's input (the previous output)
-            if (ph)
-                for (int t = tid; t < kBT * m; t += blockDim.x) {
-                    const int s = t / m, c = t % m;
-                    float x = 0.f;
-                    for (int q = 0; q < 4; ++q) {
-                        const float *gq = DG + (q * kBT + s) * D;
-                        for (int k = 0; k < D; ++k) x = fmaf(V0[(q * D + k) * m + c], gq[k], x);
-                    }
-                    FB[s * kMMax + c] = x;
-                }
+#pragma unroll
+            for (int l = 0; l < 2; ++l)
+#pragma unroll
+                for (int rr = 0; rr < R; ++rr) sv[l][rr] = nx[l][rr];
         }
     }
 }
