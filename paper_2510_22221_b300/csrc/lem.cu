@@ -156,16 +156,26 @@ __device__ __forceinline__ T *wp(const LemArgs &A, size_t off)
 
 namespace {
 
+// Row stride of the per-sequence state rows in shared memory: D + 8, so
+// that the element-wise updates of 4 sequences x 8 units in a warp fall in
+// distinct banks; a multiple of 4 floats, for the float4 reads.
+template <int D>
+__host__ __device__ constexpr int row_stride()
+{
+    return D + 8;
+}
+
 // Shared-memory floats of the recurrent kernels for width D
 template <int D, int R>
 constexpr int fwd_smem_floats()
 {
-    return 3 * 4 * D * D + 4 * kMMax * D + 2 * 4 * D + kMMax * D + 2 * 2 * (kG * R) * D + (kG * R) * kMMax;
+    return 3 * 4 * D * D + 4 * kMMax * D + 2 * 4 * D + kMMax * D + 2 * 2 * (kG * R) * row_stride<D>() +
+           (kG * R) * kMMax;
 }
 template <int D, int R>
 constexpr int bwd_smem_floats()
 {
-    return 3 * 4 * D * D + 4 * kMMax * D + kMMax * D + 2 * 4 * (kG * R) * D + (kG * R) * kMMax;
+    return 3 * 4 * D * D + 4 * kMMax * D + kMMax * D + 2 * 4 * (kG * R) * row_stride<D>() + (kG * R) * kMMax;
 }
 
 // Position of entry (o, k) of a D x D product matrix (output o, summed
@@ -238,15 +248,16 @@ template <int D, int R>
 __global__ void __launch_bounds__(kG *D, 1) lem_fwd_kernel(LemArgs A)
 {
     constexpr int kBT = kG * R, kT = D / 16, kNW = D / 8, kHO = (kBT * kMMax + kNW - 1) / kNW;
+    constexpr int SD = row_stride<D>();
     extern __shared__ __align__(16) float sm[];
     float *W0 = sm, *W1 = W0 + 4 * D * D, *V1 = W1 + 4 * D * D, *V0 = V1 + 4 * D * D;
     float *bb0 = V0 + 4 * kMMax * D, *bb1 = bb0 + 4 * D, *Wo = bb1 + 4 * D;
-    float *Y = Wo + kMMax * D, *Z = Y + 2 * kBT * D, *X = Z + 2 * kBT * D;
+    float *Y = Wo + kMMax * D, *Z = Y + 2 * kBT * SD, *X = Z + 2 * kBT * SD;
     const int tid = threadIdx.x, i = tid >> 2, r = tid & 3, lane = tid & 31, warp = tid >> 5;
     const int m = A.m, B = A.B, b0 = blockIdx.x * kBT;
     const float dt = A.dt;
     for (int e = tid; e < m * D; e += blockDim.x) Wo[e] = A.theta[cell_offset(4, D, m) + e];
-    for (int e = tid; e < 2 * kBT * D; e += blockDim.x) Y[e] = Z[e] = 0.f;
+    for (int e = tid; e < 2 * kBT * SD; e += blockDim.x) Y[e] = Z[e] = 0.f;
     for (int ph = 0; ph < 2; ++ph) {
         const int T = ph ? A.t_out : A.t_in;
         float *act[2] = {wp<float>(A, A.L.act[ph][0]), wp<float>(A, A.L.act[ph][1])};
@@ -270,8 +281,8 @@ __global__ void __launch_bounds__(kG *D, 1) lem_fwd_kernel(LemArgs A)
                 const int s = r + kG * rr, b = b0 + s;
                 if (b < B) {
                     float *a = act[l] + (long long)b * kQ * D + i;
-                    a[0] = Y[(l * kBT + s) * D + i];
-                    a[D] = Z[(l * kBT + s) * D + i];
+                    a[0] = Y[(l * kBT + s) * SD + i];
+                    a[D] = Z[(l * kBT + s) * SD + i];
                 }
             }
         __syncthreads();
@@ -288,7 +299,7 @@ __global__ void __launch_bounds__(kG *D, 1) lem_fwd_kernel(LemArgs A)
 #pragma unroll
             for (int l = 0; l < 2; ++l) {
                 const float *W = l ? W1 : W0, *bb = l ? bb1 : bb0;
-                const float *yv = Y + l * kBT * D, *xv = Y;   // cell 1's input is cell 0's y_n
+                const float *yv = Y + l * kBT * SD, *xv = Y;   // cell 1's input is cell 0's y_n
                 constexpr int kNQ = 4;
                 float acc[kNQ][kBT];
 #pragma unroll
@@ -304,7 +315,7 @@ __global__ void __launch_bounds__(kG *D, 1) lem_fwd_kernel(LemArgs A)
                     for (int q = 0; q < 3; ++q) w[q] = ld4(W + q * D * D + wo);
 #pragma unroll
                     for (int s = 0; s < kBT; ++s) {
-                        const float4 y4 = ld4(yv + s * D + vo);
+                        const float4 y4 = ld4(yv + s * SD + vo);
 #pragma unroll
                         for (int q = 0; q < 3; ++q) acc[q][s] = dot4(w[q], y4, acc[q][s]);
                     }
@@ -314,7 +325,7 @@ __global__ void __launch_bounds__(kG *D, 1) lem_fwd_kernel(LemArgs A)
                         for (int q = 0; q < 4; ++q) v[q] = ld4(V1 + q * D * D + wo);
 #pragma unroll
                         for (int s = 0; s < kBT; ++s) {
-                            const float4 x4 = ld4(xv + s * D + vo);
+                            const float4 x4 = ld4(xv + s * SD + vo);
 #pragma unroll
                             for (int q = 0; q < 4; ++q) acc[q][s] = dot4(v[q], x4, acc[q][s]);
                         }
@@ -345,27 +356,27 @@ __global__ void __launch_bounds__(kG *D, 1) lem_fwd_kernel(LemArgs A)
                     a2 += g[1];
                     az += g[2];
                     ay[rr] = a4 + g[3];
-                    yp[rr] = yv[s * D + i];
-                    const float zp = Z[(l * kBT + s) * D + i];
+                    yp[rr] = yv[s * SD + i];
+                    const float zp = Z[(l * kBT + s) * SD + i];
                     s1[rr] = sigm(a1);
                     s2[rr] = sigm(a2);
                     tz[rr] = tanhf(az);
                     const float h1 = dt * s1[rr];
                     zn[rr] = fmaf(h1, tz[rr], (1.f - h1) * zp);
                     // z_n of unit i: read by no other thread before the barrier
-                    Z[(l * kBT + s) * D + i] = zn[rr];
+                    Z[(l * kBT + s) * SD + i] = zn[rr];
                 }
                 __syncthreads();
                 // y gate: a4 += W_4 z_n
                 float a4p[kBT];
 #pragma unroll
                 for (int s = 0; s < kBT; ++s) a4p[s] = 0.f;
-                const float *zv = Z + l * kBT * D;
+                const float *zv = Z + l * kBT * SD;
 #pragma unroll
                 for (int t = 0; t < kT; ++t) {
                     const float4 w = ld4(W + 3 * D * D + (t * D + i) * 16 + 4 * r);
 #pragma unroll
-                    for (int s = 0; s < kBT; ++s) a4p[s] = dot4(w, ld4(zv + s * D + 16 * t + 4 * r), a4p[s]);
+                    for (int s = 0; s < kBT; ++s) a4p[s] = dot4(w, ld4(zv + s * SD + 16 * t + 4 * r), a4p[s]);
                 }
 #pragma unroll
                 for (int rr = 0; rr < R; ++rr) {
@@ -373,7 +384,7 @@ __global__ void __launch_bounds__(kG *D, 1) lem_fwd_kernel(LemArgs A)
                     const int s = r + kG * rr, b = b0 + s;
                     const float ty = tanhf(a4), h2 = dt * s2[rr];
                     const float yn = fmaf(h2, ty, (1.f - h2) * yp[rr]);
-                    Y[(l * kBT + s) * D + i] = yn;
+                    Y[(l * kBT + s) * SD + i] = yn;
                     if (b < B) {
                         float *a = act[l] + ((long long)(n + 1) * B + b) * kQ * D + i;
                         a[0] = yn;
@@ -392,7 +403,7 @@ __global__ void __launch_bounds__(kG *D, 1) lem_fwd_kernel(LemArgs A)
                 const int o = warp + h * kNW;
                 if (o < kBT * m) {
                     const int s = o / m, c = o % m, b = b0 + s;
-                    const float *yv = Y + (kBT + s) * D;
+                    const float *yv = Y + (kBT + s) * SD;
                     float p = 0.f;
 #pragma unroll
                     for (int k = lane; k < D; k += 32) p = fmaf(Wo[c * D + k], yv[k], p);
@@ -594,10 +605,11 @@ template <int D, int R>
 __global__ void __launch_bounds__(kG *D, 1) lem_bwd_kernel(LemArgs A)
 {
     constexpr int kBT = kG * R, kT = D / 16, kNW = D / 8, kHO = (kBT * kMMax + kNW - 1) / kNW;
+    constexpr int SD = row_stride<D>();
     extern __shared__ __align__(16) float sm[];
     float *W0 = sm, *W1 = W0 + 4 * D * D, *V1 = W1 + 4 * D * D, *V0 = V1 + 4 * D * D;
-    float *Wo = V0 + 4 * kMMax * D, *DG = Wo + kMMax * D;   // DG [2][4][kBT][D]
-    float *DO = DG + 2 * 4 * kBT * D;
+    float *Wo = V0 + 4 * kMMax * D, *DG = Wo + kMMax * D;   // DG [2][4][kBT][SD]
+    float *DO = DG + 2 * 4 * kBT * SD;
     const int tid = threadIdx.x, i = tid >> 2, r = tid & 3, lane = tid & 31, warp = tid >> 5;
     const int m = A.m, B = A.B, b0 = blockIdx.x * kBT;
     const float dt = A.dt;
@@ -644,7 +656,7 @@ __global__ void __launch_bounds__(kG *D, 1) lem_bwd_kernel(LemArgs A)
                         for (int q = 0; q < 4; ++q)
 #pragma unroll
                             for (int k = lane; k < D; k += 32)
-                                fb = fmaf(V0[(q * D + k) * m + c], DG[(q * kBT + s) * D + k], fb);
+                                fb = fmaf(V0[(q * D + k) * m + c], DG[(q * kBT + s) * SD + k], fb);
                         fb = warp_sum(fb);
                     }
                     if (lane == 0) {
@@ -680,7 +692,7 @@ __global__ void __launch_bounds__(kG *D, 1) lem_bwd_kernel(LemArgs A)
 #pragma unroll
             for (int l = 1; l >= 0; --l) {
                 const float *W = l ? W1 : W0;
-                float *dgl = DG + l * 4 * kBT * D;
+                float *dgl = DG + l * 4 * kBT * SD;
                 float dg2[R], dgy[R], dyp[R];
 #pragma unroll
                 for (int rr = 0; rr < R; ++rr) {
@@ -688,7 +700,7 @@ __global__ void __launch_bounds__(kG *D, 1) lem_bwd_kernel(LemArgs A)
                     const float gy = dy[l][rr];
                     dg2[rr] = gy * (v.ty - v.yp) * dt * v.s2 * (1.f - v.s2);
                     dgy[rr] = gy * dt * v.s2 * (1.f - v.ty * v.ty);
-                    dgl[(3 * kBT + r + kG * rr) * D + i] = dgy[rr];
+                    dgl[(3 * kBT + r + kG * rr) * SD + i] = dgy[rr];
                     dyp[rr] = gy * (1.f - dt * v.s2);
                 }
                 __syncthreads();
@@ -700,7 +712,7 @@ __global__ void __launch_bounds__(kG *D, 1) lem_bwd_kernel(LemArgs A)
                 for (int t = 0; t < kT; ++t) {
                     const float4 w = ld4(W + 3 * D * D + (t * D + i) * 16 + 4 * r);
 #pragma unroll
-                    for (int s = 0; s < kBT; ++s) az[s] = dot4(w, ld4(dgl + (3 * kBT + s) * D + 16 * t + 4 * r), az[s]);
+                    for (int s = 0; s < kBT; ++s) az[s] = dot4(w, ld4(dgl + (3 * kBT + s) * SD + 16 * t + 4 * r), az[s]);
                 }
                 float dzp[R];
 #pragma unroll
@@ -711,9 +723,9 @@ __global__ void __launch_bounds__(kG *D, 1) lem_bwd_kernel(LemArgs A)
                     const float dg1 = dzt * (v.tz - v.zp) * dt * v.s1 * (1.f - v.s1);
                     const float dgz = dzt * dt * v.s1 * (1.f - v.tz * v.tz);
                     dzp[rr] = dzt * (1.f - dt * v.s1);
-                    dgl[(0 * kBT + s) * D + i] = dg1;
-                    dgl[(1 * kBT + s) * D + i] = dg2[rr];
-                    dgl[(2 * kBT + s) * D + i] = dgz;
+                    dgl[(0 * kBT + s) * SD + i] = dg1;
+                    dgl[(1 * kBT + s) * SD + i] = dg2[rr];
+                    dgl[(2 * kBT + s) * SD + i] = dgz;
                     if (b < B) {
                         float *o = dgo[l] + ((long long)n * B + b) * 4 * D + i;
                         o[0] = dg1;
@@ -743,7 +755,7 @@ __global__ void __launch_bounds__(kG *D, 1) lem_bwd_kernel(LemArgs A)
                     for (int s = 0; s < kBT; ++s) {
                         float4 g[4];
 #pragma unroll
-                        for (int q = 0; q < (l ? 4 : 3); ++q) g[q] = ld4(dgl + (q * kBT + s) * D + go);
+                        for (int q = 0; q < (l ? 4 : 3); ++q) g[q] = ld4(dgl + (q * kBT + s) * SD + go);
 #pragma unroll
                         for (int q = 0; q < 3; ++q) ay[s] = dot4(w[q], g[q], ay[s]);
                         if (l) {
