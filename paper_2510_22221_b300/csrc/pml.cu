@@ -17,11 +17,16 @@ constexpr int kPT = 256;
 // the cell's index in the axis's memory arrays (pml_index), so the memories
 // move coalesced and neighbouring threads hold neighbouring cells along x
 // (along the layer index for AX = x).  A cell in the layers of several axes
-// is updated by each axis's kernel in turn (x, then y, then z).
+// is updated by each axis's kernel in turn (x, then y, then z).  Launched
+// as the programmatic dependent of the kernel before it (all but the first
+// of a step): the cell's memories, coefficients and class id, which no other
+// kernel of the chain writes, are loaded before the wait for that kernel's
+// fields.
 template <bool HPASS, typename ClsT, int AX>
 __global__ void __launch_bounds__(kPT) pml_axis_kernel(const PmlLaunch P, int src)
 {
     constexpr int B = (AX + 1) % 3, CC = (AX + 2) % 3;
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     const unsigned q = blockIdx.x * kPT + threadIdx.x;
     const unsigned vol = P.pvol[AX];
     if (q >= vol) return;
@@ -46,19 +51,21 @@ __global__ void __launch_bounds__(kPT) pml_axis_kernel(const PmlLaunch P, int sr
     const float *__restrict__ D = F + (HPASS ? 0 : 3 * fs);   // the differentiated field
     float *const T = F + (HPASS ? 3 * fs : 0);                // the corrected field
     float *const ps = P.psi[AX] + (HPASS ? 2 * vol : 0u) + q;
-    // loads first: own and neighbour values of D, targets, memories, coefficients
-    const float dc = __ldg(D + CC * fs + off), db = __ldg(D + B * fs + off);
-    float dcn = 0.f, dbn = 0.f;
-    const bool nb = HPASS ? c + 1 < n : c > 0;   // the wall's edges (index n; E at 0) hold 0
-    if (nb) {
-        dcn = __ldg(D + CC * fs + (HPASS ? off + st : off - st));
-        dbn = __ldg(D + B * fs + (HPASS ? off + st : off - st));
-    }
-    const float tb = T[B * fs + off], tc = T[CC * fs + off];
+    // memories, coefficients and class id: written by no kernel of the chain
     const float p1 = ps[0], p2 = ps[vol];
     const float4 co = __ldg(P.pco[AX] + (s * d + t) * 2 + (HPASS ? 1 : 0));
     int cl = 0;
     if (!HPASS) cl = (int)static_cast<const ClsT *>(P.cls)[off];
+    // the fields, once the kernel before this one has finished
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    const float dc = D[CC * fs + off], db = D[B * fs + off];
+    float dcn = 0.f, dbn = 0.f;
+    const bool nb = HPASS ? c + 1 < n : c > 0;   // the wall's edges (index n; E at 0) hold 0
+    if (nb) {
+        dcn = D[CC * fs + (HPASS ? off + st : off - st)];
+        dbn = D[B * fs + (HPASS ? off + st : off - st)];
+    }
+    const float tb = T[B * fs + off], tc = T[CC * fs + off];
     float g1 = 0.f, g2 = 0.f;   // d/dAX of component c (enters b) and of component b (enters c)
     if (HPASS) {
         g1 = (dcn - dc) * P.id[AX];
@@ -83,22 +90,46 @@ __global__ void __launch_bounds__(kPT) pml_axis_kernel(const PmlLaunch P, int sr
     }
 }
 
-template <bool HPASS, typename ClsT>
-static void launch_axes(const PmlLaunch &P, int src, cudaStream_t s)
+// One axis's kernel of a pass; every launch but the first of the chain is a
+// programmatic dependent of the one before it.
+template <bool HPASS, typename ClsT, int AX>
+static cudaError_t launch_axis(const PmlLaunch &P, int src, cudaStream_t s, bool &first)
 {
-    if (P.pd[0] > 0) pml_axis_kernel<HPASS, ClsT, 0><<<(P.pvol[0] + kPT - 1) / kPT, kPT, 0, s>>>(P, src);
-    if (P.pd[1] > 0) pml_axis_kernel<HPASS, ClsT, 1><<<(P.pvol[1] + kPT - 1) / kPT, kPT, 0, s>>>(P, src);
-    if (P.pd[2] > 0) pml_axis_kernel<HPASS, ClsT, 2><<<(P.pvol[2] + kPT - 1) / kPT, kPT, 0, s>>>(P, src);
+    if (P.pd[AX] <= 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((P.pvol[AX] + kPT - 1) / kPT);
+    cfg.blockDim = dim3(kPT);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = first ? 0 : 1;
+    first = false;
+    return cudaLaunchKernelEx(&cfg, pml_axis_kernel<HPASS, ClsT, AX>, P, src);
+}
+
+template <bool HPASS, typename ClsT>
+static cudaError_t launch_axes(const PmlLaunch &P, int src, cudaStream_t s, bool &first)
+{
+    cudaError_t e = launch_axis<HPASS, ClsT, 0>(P, src, s, first);
+    if (e == cudaSuccess) e = launch_axis<HPASS, ClsT, 1>(P, src, s, first);
+    if (e == cudaSuccess) e = launch_axis<HPASS, ClsT, 2>(P, src, s, first);
+    return e;
 }
 
 }  // namespace
 
 cudaError_t launch_pml(const PmlLaunch *P, int np, int src, bool cls16, cudaStream_t s)
 {
+    // the first kernel waits for all earlier work of the stream (a plain
+    // launch: the magnet kernel of the previous step may outlast its sweep)
+    bool first = true;
     for (int q = 0; q < np; ++q) {
-        launch_axes<true, uint8_t>(P[q], src, s);
-        if (cls16) launch_axes<false, uint16_t>(P[q], src, s);
-        else launch_axes<false, uint8_t>(P[q], src, s);
+        cudaError_t e = launch_axes<true, uint8_t>(P[q], src, s, first);
+        if (e == cudaSuccess)
+            e = cls16 ? launch_axes<false, uint16_t>(P[q], src, s, first) : launch_axes<false, uint8_t>(P[q], src, s, first);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }

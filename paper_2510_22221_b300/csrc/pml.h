@@ -65,8 +65,9 @@ __host__ __device__ inline unsigned pml_index(int a, int s, int t, int d, int nx
 }
 
 // The H pass then the E pass of every lined instance on stream s, for field
-// buffer src (plain launches, one per lined axis and pass; nothing when P is
-// empty).
+// buffer src: one launch per lined axis and pass, the first a plain launch
+// and each later one a programmatic dependent of the one before it (which
+// it waits for before touching the fields); nothing when P is empty.
 cudaError_t launch_pml(const PmlLaunch *P, int np, int src, bool cls16, cudaStream_t s);
 
 }  // namespace fl
