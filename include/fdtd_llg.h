@@ -132,9 +132,16 @@ int fdtd_llg_batch_member(fdtd_llg_t batch, int32_t i, fdtd_llg_t *member);
  * eps_r_design (nullable): per-cell eps_r over the box design_box =
  * {i0, j0, k0, ni, nj, nk} (compact in that box, host), overriding the table's
  * eps_r there.  Resets E, H to 0 and M to Ms h in magnetic cells, and the
- * batch's step count to 0.  Each face-connected magnetic region must fit in a
- * bounding box of at most 4096 cells; at most 16 magnetic materials.
- * Errors: FDTD_E_INVAL (bad id, table, box or magnet region). */
+ * batch's step count to 0.  Each face-connected magnetic region is cut
+ * along its bounding box's longest axis into at most 8 slabs (one CTA of a
+ * thread-block cluster each), and each slab's box must hold at most 4096
+ * cells; at most 16 magnetic materials.  The distinct neighbourhoods (the
+ * material ids of a cell and of the six cells below it along one or two
+ * axes) are listed on the device: at most 2^20 of them.  The host reads
+ * nothing per cell except, when mat_id is device memory, one copy of it.
+ * Errors: FDTD_E_INVAL (an id >= ntable, bad table, box or magnet region,
+ * too many distinct neighbourhoods or more than 65536 edge classes),
+ * FDTD_E_OOM. */
 int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const fdtd_material *table,
                            int32_t ntable, const double hbias[3], const double *eps_r_design,
                            const int32_t design_box[6]);

@@ -37,4 +37,37 @@ cudaError_t launch_class_assign(const uint8_t *mid, int nx, int ny, int nz, int 
                                 const uint16_t *ids, int nkeys, const long long *over_off, const uint16_t *over_id,
                                 int nover, void *cls, bool c16, cudaStream_t s);
 
+// What the host needs of a grid's material ids before it forms the classes
+// (device memory, filled by launch_key_scan):
+//  * the distinct neighbourhood keys of the cells outside the design box's
+//    reach, each with its first cell (the lowest linear index that has it),
+//    in an open-addressing hash set of cap slots (cap a power of two, at
+//    most 2^24; empty slots hold kKeyEmpty, first cells start at ~0);
+//  * the magnetic cells (material ids flagged in mag), in no fixed order:
+//    their number in *mcount, the first mcap of them in mlist;
+//  * the largest material id in *top;
+//  * *overflow != 0 if a key found no free slot.
+struct KeyScan {
+    unsigned long long *tk, *first;   // [cap] keys and first cells
+    unsigned cap;
+    unsigned long long *mlist;        // [mcap] magnetic cells
+    unsigned long long mcap;
+    unsigned long long *mcount;
+    unsigned *top, *overflow;
+    unsigned long long *kout, *fout;  // [cap] the occupied slots, compacted by launch_key_compact
+    unsigned *kcount;
+};
+constexpr unsigned long long kKeyEmpty = ~0ull;   // keys are below 2^59
+
+// mag: bit m set when material m is magnetic.  has_design with box db =
+// (x0, y0, z0, bx, by, bz): a cell whose edges or faces touch a design cell
+// is left out of the key set (its class depends on eps_r_design).  Resets
+// the set and the counters first; asynchronous on stream s.
+cudaError_t launch_key_scan(const uint8_t *mid, int nx, int ny, int nz, const uint64_t mag[4], bool has_design,
+                            const int db[6], const KeyScan &K, cudaStream_t s);
+// The occupied slots of the key set into kout / fout (in slot order, which
+// depends on the insertion order: the host sorts them), their number in
+// *kcount; asynchronous on stream s.
+cudaError_t launch_key_compact(const KeyScan &K, cudaStream_t s);
+
 }  // namespace fl

@@ -17,7 +17,6 @@
 #include <map>
 #include <memory>
 #include <mutex>
-#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -245,6 +244,25 @@ Instance *inst_of(fdtd_llg_t h)
 
 bool is_member(fdtd_llg_t h) { return h && h->sim && h->index >= 0; }
 
+// Device temporaries of one call, released (after the handle's stream has
+// drained) when the call returns, on every path.
+struct DevTemps {
+    Sim *S;
+    std::vector<void *> p;
+    void *get(size_t bytes)
+    {
+        void *q = S->dalloc(bytes);
+        if (q) p.push_back(q);
+        return q;
+    }
+    ~DevTemps()
+    {
+        if (p.empty()) return;
+        cudaStreamSynchronize(S->stream);
+        for (void *q : p) S->dfree(q);
+    }
+};
+
 // ------------------------------------------------------- edge coefficients
 struct ClassKey {
     uint32_t w[10];
@@ -449,11 +467,6 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
     } else {
         cudaGetLastError();
     }
-    {
-        uint8_t top = 0;
-        for (size_t c = 0; c < nc; ++c) top = std::max(top, mid[c]);
-        if (nc && top >= ntable) return fail(h, FDTD_E_INVAL, "mat_id references a material beyond ntable");
-    }
     for (int m = 0; m < ntable; ++m) {
         const fdtd_material &t = table[m];
         if (!(t.eps_r > 0) || t.sigma < 0 || t.Ms < 0 || t.alpha < 0 || (t.Ms > 0 && !(t.gamma > 0)))
@@ -543,66 +556,72 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
     };
     // Classes.  Elsewhere a cell's class depends only on its neighbourhood
     // key (nbhd_key: the materials of the seven cells its edges and faces
-    // touch, and the walls it lies against).  z-slabs, in parallel, list the
-    // distinct keys they meet, each with a cell that has it (along x the key
-    // changes only at material boundaries, so the previous cell's is tried
-    // first), and their magnetic cells in cell order; the keys' classes and
-    // those of the cells touching the design box are formed here, and the
-    // device gives every cell its class (the host writes nothing per cell).
-    struct Slab {
-        std::vector<std::pair<uint64_t, size_t>> keys;
-        std::vector<size_t> mag;
-    };
-    const int nthr = std::max(1, std::min({(int)std::thread::hardware_concurrency(), 16, nz}));
-    std::vector<Slab> slabs(nthr);
-    std::vector<char> slab_failed(nthr, 0);
-    auto scan_slab = [&](int t) {
-        Slab &sl = slabs[t];
-        const int ka = (int)((long long)nz * t / nthr), kb = (int)((long long)nz * (t + 1) / nthr);
-        std::unordered_map<uint64_t, int> seen;
-        const size_t sj = (size_t)nx, sk = (size_t)nx * ny;
-        uint64_t last = ~0ull;
-        for (int k = ka; k < kb; ++k)
-            for (int j = 0; j < ny; ++j)
-                for (int i = 0; i < nx; ++i) {
-                    const size_t c0 = cid(i, j, k);
-                    if (magm[mid[c0]]) sl.mag.push_back(c0);
-                    if (touches_design(i, j, k)) continue;
-                    uint64_t nk;
-                    if (i > 0 && j > 0 && k > 0) {   // interior: nbhd_key without the wall tests
-                        const uint8_t *m = mid + c0;
-                        nk = (((uint64_t)m[0] << 48) | ((uint64_t)m[-1] << 40) | ((uint64_t)m[-(ptrdiff_t)sj] << 32) |
-                              ((uint64_t)m[-(ptrdiff_t)sk] << 24) | ((uint64_t)m[-(ptrdiff_t)(sj + sk)] << 16) |
-                              ((uint64_t)m[-(ptrdiff_t)(1 + sk)] << 8) | (uint64_t)m[-(ptrdiff_t)(1 + sj)])
-                             << 3;
-                    } else {
-                        nk = nbhd_key(mid, nx, ny, i, j, k);
-                    }
-                    if (nk == last) continue;
-                    last = nk;
-                    if (seen.emplace(nk, 0).second) sl.keys.emplace_back(nk, c0);
-                }
-    };
-    auto run_slab = [&](int t) {
-        try {
-            scan_slab(t);
-        } catch (...) {   // an allocation failed: reported below, never thrown across threads
-            slab_failed[t] = 1;
-        }
-    };
-    {
-        // slabs whose thread cannot be started run here
-        std::vector<std::thread> pool;
-        try {
-            for (int t = 1; t < nthr; ++t) pool.emplace_back(run_slab, t);
-        } catch (...) {
-        }
-        for (int t = (int)pool.size() + 1; t < nthr; ++t) run_slab(t);
-        run_slab(0);
-        for (auto &th : pool) th.join();
+    // touch, and the walls it lies against).  The device lists the distinct
+    // keys, each with its first cell, and the magnetic cells; the keys'
+    // classes, formed here in the order of their first cells, and those of
+    // the cells touching the design box are the host's work, and the device
+    // gives every cell its class (the host reads and writes nothing per
+    // cell).  The material ids go to the device first (the caller's device
+    // array itself when it is one).
+    const bool on_dev = !mid_copy.empty();
+    DevTemps tmpd{S};
+    const uint8_t *dmid = mat_id;
+    if (!on_dev) {
+        uint8_t *d = (uint8_t *)tmpd.get(nc);
+        if (!d) return fail(h, FDTD_E_OOM, "device allocation failed");
+        CKR(h, cudaMemcpyAsync(d, mid, nc, cudaMemcpyHostToDevice, S->stream));
+        dmid = d;
     }
-    for (char f : slab_failed)
-        if (f) return fail(h, FDTD_E_OOM, "host allocation failed");
+    uint64_t magw[4] = {0, 0, 0, 0};
+    for (int m = 0; m < ntable; ++m)
+        if (magm[m]) magw[m >> 6] |= 1ull << (m & 63);
+    KeyScan K{};
+    K.cap = 1024;
+    while (K.cap < 2 * std::min(nc, (size_t)1 << 19)) K.cap *= 2;
+    K.mcap = std::max<unsigned long long>(1, std::min<unsigned long long>(nc, 1ull << 16));
+    K.tk = (unsigned long long *)tmpd.get((size_t)K.cap * 8);
+    K.first = (unsigned long long *)tmpd.get((size_t)K.cap * 8);
+    K.kout = (unsigned long long *)tmpd.get((size_t)K.cap * 8);
+    K.fout = (unsigned long long *)tmpd.get((size_t)K.cap * 8);
+    K.mlist = (unsigned long long *)tmpd.get((size_t)K.mcap * 8);
+    unsigned char *cnt = (unsigned char *)tmpd.get(32);
+    if (!K.tk || !K.first || !K.kout || !K.fout || !K.mlist || !cnt) return fail(h, FDTD_E_OOM, "device allocation failed");
+    K.mcount = (unsigned long long *)cnt;
+    K.top = (unsigned *)(cnt + 8);
+    K.overflow = (unsigned *)(cnt + 12);
+    K.kcount = (unsigned *)(cnt + 16);
+    struct {
+        unsigned long long mcount;
+        unsigned top, overflow, kcount, pad;
+    } hc{};
+    for (int pass = 0; pass < 2; ++pass) {
+        CKR(h, launch_key_scan(dmid, nx, ny, nz, magw, has_design, db, K, S->stream));
+        CKR(h, launch_key_compact(K, S->stream));
+        CKR(h, cudaMemcpyAsync(&hc, cnt, sizeof hc, cudaMemcpyDeviceToHost, S->stream));
+        CKR(h, cudaStreamSynchronize(S->stream));
+        if (hc.mcount <= K.mcap) break;
+        // more magnetic cells than the list holds: again with room for all
+        K.mlist = (unsigned long long *)tmpd.get((size_t)hc.mcount * 8);
+        if (!K.mlist) return fail(h, FDTD_E_OOM, "device allocation failed");
+        K.mcap = hc.mcount;
+    }
+    if (nc && hc.top >= (unsigned)ntable) return fail(h, FDTD_E_INVAL, "mat_id references a material beyond ntable");
+    if (hc.overflow)
+        return fail(h, FDTD_E_INVAL, "more than " + std::to_string(K.cap) + " distinct material neighbourhoods");
+    std::vector<std::pair<uint64_t, uint64_t>> first_key(hc.kcount);   // (first cell, key)
+    std::vector<size_t> magcells(hc.mcount);
+    {
+        std::vector<unsigned long long> kk(hc.kcount), ff(hc.kcount), mm(hc.mcount);
+        if (hc.kcount) {
+            CKR(h, cudaMemcpy(kk.data(), K.kout, hc.kcount * 8ull, cudaMemcpyDeviceToHost));
+            CKR(h, cudaMemcpy(ff.data(), K.fout, hc.kcount * 8ull, cudaMemcpyDeviceToHost));
+        }
+        if (hc.mcount) CKR(h, cudaMemcpy(mm.data(), K.mlist, hc.mcount * 8ull, cudaMemcpyDeviceToHost));
+        for (size_t q = 0; q < kk.size(); ++q) first_key[q] = {ff[q], kk[q]};
+        std::sort(first_key.begin(), first_key.end());
+        for (size_t q = 0; q < mm.size(); ++q) magcells[q] = (size_t)mm[q];
+        std::sort(magcells.begin(), magcells.end());
+    }
     std::unordered_map<ClassKey, int, ClassKeyHash> classes;
     std::vector<ClassKey> keys;
     {
@@ -625,14 +644,12 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
     };
     const int px = I.px;
     std::unordered_map<uint64_t, int> key_class;
-    for (const Slab &sl : slabs)
-        for (const auto &kc : sl.keys) {
-            if (key_class.count(kc.first)) continue;
-            const size_t c = kc.second;
-            const int cl = class_of((int)(c % nx), (int)((c / nx) % ny), (int)(c / ((size_t)nx * ny)));
-            if (cl < 0) return fail(h, FDTD_E_INVAL, "more than 65536 distinct edge classes");
-            key_class.emplace(kc.first, cl);
-        }
+    for (const auto &fk : first_key) {
+        const size_t c = (size_t)fk.first;
+        const int cl = class_of((int)(c % nx), (int)((c / nx) % ny), (int)(c / ((size_t)nx * ny)));
+        if (cl < 0) return fail(h, FDTD_E_INVAL, "more than 65536 distinct edge classes");
+        key_class.emplace(fk.second, cl);
+    }
     std::vector<long long> over_off;
     std::vector<uint16_t> over_id;
     if (has_design)
@@ -652,37 +669,34 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
     // magnetic regions: face-connected components of cells with Ms > 0,
     // numbered in the order of their first cell
     std::unordered_map<size_t, int> label;
-    size_t nmagc = 0;
-    for (const Slab &sl : slabs) nmagc += sl.mag.size();
-    label.reserve(2 * nmagc);
+    label.reserve(2 * magcells.size());
     struct Box { int x0, y0, z0, x1, y1, z1; };
     std::vector<Box> boxes;
     std::vector<size_t> stack;
-    for (const Slab &sl : slabs)
-        for (size_t c0 : sl.mag) {
-            if (label.count(c0)) continue;
-            const int L = (int)boxes.size();
-            Box b{nx, ny, nz, -1, -1, -1};
-            stack.clear();
-            stack.push_back(c0);
-            label.emplace(c0, L);
-            while (!stack.empty()) {
-                const size_t c = stack.back();
-                stack.pop_back();
-                const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((size_t)nx * ny));
-                b.x0 = std::min(b.x0, i); b.y0 = std::min(b.y0, j); b.z0 = std::min(b.z0, k);
-                b.x1 = std::max(b.x1, i); b.y1 = std::max(b.y1, j); b.z1 = std::max(b.z1, k);
-                const int nb[6][3] = {{i - 1, j, k}, {i + 1, j, k}, {i, j - 1, k}, {i, j + 1, k}, {i, j, k - 1}, {i, j, k + 1}};
-                for (auto &q : nb) {
-                    if (q[0] < 0 || q[1] < 0 || q[2] < 0 || q[0] >= nx || q[1] >= ny || q[2] >= nz) continue;
-                    const size_t cc = cid(q[0], q[1], q[2]);
-                    if (magm[mid[cc]] && label.emplace(cc, L).second) stack.push_back(cc);
-                }
+    for (size_t c0 : magcells) {
+        if (label.count(c0)) continue;
+        const int L = (int)boxes.size();
+        Box b{nx, ny, nz, -1, -1, -1};
+        stack.clear();
+        stack.push_back(c0);
+        label.emplace(c0, L);
+        while (!stack.empty()) {
+            const size_t c = stack.back();
+            stack.pop_back();
+            const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((size_t)nx * ny));
+            b.x0 = std::min(b.x0, i); b.y0 = std::min(b.y0, j); b.z0 = std::min(b.z0, k);
+            b.x1 = std::max(b.x1, i); b.y1 = std::max(b.y1, j); b.z1 = std::max(b.z1, k);
+            const int nb[6][3] = {{i - 1, j, k}, {i + 1, j, k}, {i, j - 1, k}, {i, j + 1, k}, {i, j, k - 1}, {i, j, k + 1}};
+            for (auto &q : nb) {
+                if (q[0] < 0 || q[1] < 0 || q[2] < 0 || q[0] >= nx || q[1] >= ny || q[2] >= nz) continue;
+                const size_t cc = cid(q[0], q[1], q[2]);
+                if (magm[mid[cc]] && label.emplace(cc, L).second) stack.push_back(cc);
             }
-            std::string why;
-            if (!mag_region_fits(b.x1 - b.x0 + 1, b.y1 - b.y0 + 1, b.z1 - b.z0 + 1, why)) return fail(h, FDTD_E_INVAL, why);
-            boxes.push_back(b);
         }
+        std::string why;
+        if (!mag_region_fits(b.x1 - b.x0 + 1, b.y1 - b.y0 + 1, b.z1 - b.z0 + 1, why)) return fail(h, FDTD_E_INVAL, why);
+        boxes.push_back(b);
+    }
     // magnet material table (compact index per magnetic material)
     std::vector<int> mm_index(ntable, 0xFF);
     std::vector<MagMat> mm;
@@ -741,25 +755,23 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
     bias_frame(u, E);
     // upload: class ids in the padded layout, table, regions; zero the fields
     {
-        // class ids on the device: the material ids (the caller's device
-        // array itself, else a copy), the sorted keys and the overrides
+        // class ids on the device: from the material ids there, the sorted
+        // keys and the overrides
         const size_t nk = kc.size(), no = over_off.size();
-        const size_t o_keys = (nc + 15) / 16 * 16, o_ids = o_keys + nk * 8, o_off = (o_ids + nk * 2 + 15) / 16 * 16,
+        const size_t o_keys = 0, o_ids = o_keys + nk * 8, o_off = (o_ids + nk * 2 + 15) / 16 * 16,
                      o_oid = o_off + no * 8, tbytes = o_oid + no * 2 + 16;
         unsigned char *tmp = (unsigned char *)S->dalloc(tbytes);
         if (!tmp) return fail(h, FDTD_E_OOM, "device allocation failed");
         std::vector<uint64_t> hk(nk);
         std::vector<uint16_t> hid(nk);
         for (size_t q = 0; q < nk; ++q) { hk[q] = kc[q].first; hid[q] = kc[q].second; }
-        const bool on_dev = !mid_copy.empty();   // mat_id was device memory: read it there
         cudaError_t e = cudaSuccess;
-        if (!on_dev) e = cudaMemcpyAsync(tmp, mid, nc, cudaMemcpyHostToDevice, S->stream);
-        if (e == cudaSuccess && nk) e = cudaMemcpyAsync(tmp + o_keys, hk.data(), nk * 8, cudaMemcpyHostToDevice, S->stream);
+        if (nk) e = cudaMemcpyAsync(tmp + o_keys, hk.data(), nk * 8, cudaMemcpyHostToDevice, S->stream);
         if (e == cudaSuccess && nk) e = cudaMemcpyAsync(tmp + o_ids, hid.data(), nk * 2, cudaMemcpyHostToDevice, S->stream);
         if (e == cudaSuccess && no) e = cudaMemcpyAsync(tmp + o_off, over_off.data(), no * 8, cudaMemcpyHostToDevice, S->stream);
         if (e == cudaSuccess && no) e = cudaMemcpyAsync(tmp + o_oid, over_id.data(), no * 2, cudaMemcpyHostToDevice, S->stream);
         if (e == cudaSuccess)
-            e = launch_class_assign(on_dev ? mat_id : tmp, nx, ny, nz, px, (const uint64_t *)(tmp + o_keys),
+            e = launch_class_assign(dmid, nx, ny, nz, px, (const uint64_t *)(tmp + o_keys),
                                     (const uint16_t *)(tmp + o_ids), (int)nk, (const long long *)(tmp + o_off),
                                     (const uint16_t *)(tmp + o_oid), (int)no, I.cls, c16, S->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);   // the host arrays above are released next

@@ -207,6 +207,52 @@ def test_materials_from_device_memory_equal_host_memory():
     b.destroy()
 
 
+def test_many_small_magnet_regions_against_the_oracle():
+    """73 728 magnetic cells in 9216 face-disjoint 2x2x2 blocks of two
+    materials: more magnetic cells than the device scan's first list holds
+    (65 536), so set_materials lists them in a second pass; every block is its
+    own region.  Against the FP64 oracle after 10 steps: every stored field
+    value, the energy and the probe beside the sources (in 10 steps the
+    signal reaches none of the others)."""
+    import dataclasses
+
+    nx, ny, nz = 72, 72, 48
+    w = W.random_small(3, nx=nx, ny=ny, nz=nz, steps=10, magnets=False)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    mid = w.mat_id.copy()
+    blocks = (i % 3 < 2) & (j % 3 < 2) & (k % 3 < 2)
+    mid[blocks] = np.where((i[blocks] // 3 + j[blocks] // 3 + k[blocks] // 3) % 2 == 0, 3, 4).astype(np.uint8)
+    assert blocks.sum() == 73728
+    w = dataclasses.replace(w, mat_id=mid)
+    sim, orc, out, M0 = run_pair(w, w.steps)
+    t = tol(w.steps)
+    pi, pj, pk = w.probes[0]
+    errs = probe_errors(sim.probe(0), out["probes"][:, 0], M0[:, pk, pj, pi], t, w.steps)
+    check_probes(errs, t, w.steps, 0)
+    check_energy(sim.energy(), out["energy"], t, w.steps)
+    compare_fields(sim, orc, M0, t)
+    sim.destroy()
+
+
+def test_material_id_beyond_the_table_is_refused():
+    """An id >= ntable anywhere in mat_id (found by the device scan) is
+    refused with FDTD_E_INVAL, from host and from device memory, and the
+    instance stays without materials (stepping refuses)."""
+    import torch
+
+    w = W.random_small(2, steps=4)
+    mid = w.mat_id.copy()
+    mid[w.nz - 1, w.ny - 1, w.nx - 1] = len(w.materials)
+    for arr in (mid.reshape(-1), torch.from_numpy(mid.reshape(-1).copy()).cuda()):
+        sim = pkg.FdtdLlg.create(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, courant_factor=w.courant, probe_capacity=4)
+        with pytest.raises(pkg.LLGError) as ei:
+            sim.set_materials(arr, [pkg.Material(**m) for m in w.materials], w.hbias)
+        assert ei.value.code == -1 and "beyond ntable" in str(ei.value)
+        with pytest.raises(pkg.LLGError):
+            sim.step(1)
+        sim.destroy()
+
+
 def _large_region(kind, steps):
     """One magnetic region near the size limit of the magnet kernel, touching
     a far wall, in a grid the oracle runs in seconds.  The kernel stages the
