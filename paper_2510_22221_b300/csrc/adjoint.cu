@@ -162,19 +162,22 @@ __device__ __forceinline__ float *hz_at(const Inst *I, float *F0, int i, int j, 
 }
 
 // Workspace of one region (floats), nf faces, V cells:
-//   C, lamHout, lamHin, lamC, fix (5 nf);  lamM, lamDl, lamA, lamHsm, lamHg (5 x 3V).
+//   C, lamHout, lamHin, lamC, fix (5 nf);  lamM, lamDl, lamA, lamHsm, lamHg[2] (6 x 3V).
 // fix carries the magnetic faces' pending correction from one reverse step to
-// the next; everything the forward step computed comes from the tape.
+// the next; everything the forward step computed comes from the tape.  lamHg
+// is double-buffered by the parity of the iterate, so a cell's new value
+// never overwrites one that a neighbour may still read.
 struct RegionWS {
     float *C, *lamHout, *lamHin, *lamC, *fix;
-    float *lamM, *lamDl, *lamA, *lamHsm, *lamHg;
+    float *lamM, *lamDl, *lamA, *lamHsm, *lamHg[2];
 };
 __device__ __forceinline__ RegionWS carve(float *w, int nf, int V)
 {
     RegionWS r;
     r.C = w; r.lamHout = r.C + nf; r.lamHin = r.lamHout + nf; r.lamC = r.lamHin + nf; r.fix = r.lamC + nf;
     float *p = r.fix + nf;
-    r.lamM = p; r.lamDl = p + 3 * V; r.lamA = p + 6 * V; r.lamHsm = p + 9 * V; r.lamHg = p + 12 * V;
+    r.lamM = p; r.lamDl = p + 3 * V; r.lamA = p + 6 * V; r.lamHsm = p + 9 * V;
+    r.lamHg[0] = p + 12 * V; r.lamHg[1] = p + 15 * V;
     return r;
 }
 
@@ -228,6 +231,10 @@ __device__ __forceinline__ void region_sync(int cs)
 // Reverse of one half-push.  In: lamHout (faces), lamM (adjoint of the output
 // m, bias frame; overwritten with the adjoint of the input m).  Out: lamHin,
 // lamC (faces); *gh0 accumulates d J / d |H_bias| of this thread's cells.
+// A thread keeps the same cells and faces in every loop, so only what a loop
+// reads of other threads' cells or faces needs a barrier before it: one after
+// each iterate's cell pass (the neighbours' lamHg, and at the end their lamA
+// and lamHsm for the faces).  The caller separates two calls by a barrier.
 __device__ void rev_half(const MagComp &C, const BoxDiv &BD, const FaceNb *fnb, const Inst *I, const float *R9,
                          const uint8_t *smat, int V, int nf, int R, const float *Hs, const float *Cc, const float *m,
                          const float *D, RegionWS &W, const float *lamHout, float *lamHin, float *lamC, double *gh0, int nfx,
@@ -236,11 +243,7 @@ __device__ void rev_half(const MagComp &C, const BoxDiv &BD, const FaceNb *fnb, 
     const int tid = threadIdx.x + (cs > 1 ? (int)cg::this_cluster().block_rank() : 0) * blockDim.x;
     const int nth = blockDim.x * cs;
     const int bx = C.bx, by = C.by, bxy = bx * by;
-    // direct terms of H_out = H* - P D^R, H* = Hs - C; adjoint of D^R and of dl^R
-    for (int f = tid; f < nf; f += nth) {
-        lamHin[f] = lamHout[f];
-        lamC[f] = -lamHout[f];
-    }
+    // direct terms of H_out = H* - P D^R, H* = Hs - C: the adjoint of dl^R
     for (int v = tid; v < V; v += nth) {
         for (int a = 0; a < 3; ++a) W.lamA[a * V + v] = W.lamHsm[a * V + v] = 0.f;
         if (smat[v] == 0xFF) {
@@ -257,14 +260,14 @@ __device__ void rev_half(const MagComp &C, const BoxDiv &BD, const FaceNb *fnb, 
         to_fr(R9, lD, l);   // D = R^T dl, so the adjoint of dl is R times that of D
         for (int a = 0; a < 3; ++a) W.lamDl[a * V + v] = W.lamM[a * V + v] + l[a];
     }
-    region_sync(cs);
     double g = 0.0;
     for (int r = R; r >= 1; --r) {
         const float *Dp = r >= 2 ? D + 3 * V * (r - 2) : nullptr;
+        float *lamHg = W.lamHg[r & 1];
         for (int v = tid; v < V; v += nth) {
             const int mt = smat[v];
             if (mt == 0xFF) {
-                W.lamHg[v] = W.lamHg[V + v] = W.lamHg[2 * V + v] = 0.f;
+                lamHg[v] = lamHg[V + v] = lamHg[2 * V + v] = 0.f;
                 continue;
             }
             float hs[3], h[3], mm[3];
@@ -273,15 +276,22 @@ __device__ void rev_half(const MagComp &C, const BoxDiv &BD, const FaceNb *fnb, 
             // J^T lambda in one reverse pass: gin = (m, hs, h) adjoints
             float gin[9];
             llg_inc_vjp(mm, hs, h, I->mm[mt], ld, gin, gin + 3, gin + 6);
+            float lsm[3];
             for (int a = 0; a < 3; ++a) {
                 W.lamM[a * V + v] += gin[a];
-                W.lamHsm[a * V + v] += gin[3 + a];   // bias frame, converted below
+                lsm[a] = W.lamHsm[a * V + v] + gin[3 + a];   // bias frame
             }
+            if (r == 1) {   // the last iterate: hs's adjoint to global axes
+                float gq[3];
+                from_fr(R9, lsm, gq);
+                for (int a = 0; a < 3; ++a) lsm[a] = gq[a];
+            }
+            for (int a = 0; a < 3; ++a) W.lamHsm[a * V + v] = lsm[a];
             g += (double)gin[5] + (double)gin[8];     // |H_bias| enters hs and h on e3
             float lh[3] = {gin[6], gin[7], gin[8]}, lg[3];
             from_fr(R9, lh, lg);
             for (int a = 0; a < 3; ++a) {
-                W.lamHg[a * V + v] = lg[a];
+                lamHg[a * V + v] = lg[a];
                 W.lamA[a * V + v] += lg[a];
             }
         }
@@ -299,37 +309,27 @@ __device__ void rev_half(const MagComp &C, const BoxDiv &BD, const FaceNb *fnb, 
                 const bool lo[3] = {li > 0, lj > 0, lk > 0}, hi[3] = {li < bx - 1, lj < by - 1, lk < C.bz - 1};
                 float lD[3];
                 for (int a = 0; a < 3; ++a) {
-                    const float gm = lo[a] ? W.lamHg[a * V + v - st[a]] : 0.f;
-                    const float gp = hi[a] ? W.lamHg[a * V + v + st[a]] : 0.f;
-                    lD[a] = -0.25f * (gm + 2.f * W.lamHg[a * V + v] + gp);
+                    const float gm = lo[a] ? lamHg[a * V + v - st[a]] : 0.f;
+                    const float gp = hi[a] ? lamHg[a * V + v + st[a]] : 0.f;
+                    lD[a] = -0.25f * (gm + 2.f * lamHg[a * V + v] + gp);
                 }
                 float l[3];
                 to_fr(R9, lD, l);
                 for (int a = 0; a < 3; ++a) W.lamDl[a * V + v] = l[a];
             }
-            region_sync(cs);
         }
     }
     *gh0 += g;
     // faces: A = mean(Hs - C), hs = R mean(Hs) + bias
-    for (int v = tid; v < V; v += nth) {
-        if (smat[v] == 0xFF) continue;
-        const float l[3] = {W.lamHsm[v], W.lamHsm[V + v], W.lamHsm[2 * V + v]};
-        float gq[3];
-        from_fr(R9, l, gq);
-        for (int a = 0; a < 3; ++a) W.lamHsm[a * V + v] = gq[a];
-    }
-    region_sync(cs);
     for (int f = tid; f < nf; f += nth) {
         const FaceNb q = fnb[f];
         const int a = face_axis(f, nfx, nfy);
         float sA = 0.f, sH = 0.f;
         if (q.vl >= 0) { sA += 0.5f * W.lamA[a * V + q.vl]; sH += 0.5f * W.lamHsm[a * V + q.vl]; }
         if (q.vr >= 0) { sA += 0.5f * W.lamA[a * V + q.vr]; sH += 0.5f * W.lamHsm[a * V + q.vr]; }
-        lamHin[f] += sA + sH;
-        lamC[f] -= sA;
+        lamHin[f] = lamHout[f] + (sA + sH);
+        lamC[f] = -lamHout[f] - sA;
     }
-    region_sync(cs);
 }
 
 __global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSet A, int slot)
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSe
     // reverse: second half-push, then the first
     double g = 0.0;
     rev_half(C, BD, fnb, I, R9, smat, V, nf, R, Hs2, W.C, m2, D2, W, W.lamHout, W.lamHin, W.lamC, &g, nfx, nfy, cs);
-    for (int f = tid; f < nf; f += nth) {
+    for (int f = tid; f < nf; f += nth) {   // the faces rev_half gave this thread
         W.lamHout[f] = W.lamHin[f];      // adjoint of H^{n+1}
         W.fix[f] = W.lamC[f];            // curl adjoint of the second half-push
     }
@@ -541,7 +541,7 @@ long long adj_ws_floats(int bx, int by, int bz, int R)
 {
     (void)R;
     const long long V = (long long)bx * by * bz;
-    return (V + 3) / 4 + 5 * mag_faces(bx, by, bz) + 15 * V;
+    return (V + 3) / 4 + 5 * mag_faces(bx, by, bz) + 18 * V;
 }
 
 cudaError_t adj_record_design(const LaunchSet &L, const AdjSet &A, int slot, int buf, cudaStream_t s)
