@@ -63,7 +63,7 @@ __device__ void llg_inc_vjp(const float m[3], const float hs[3], const float h[3
     cross3(M, S, MxS);
     for (int c = 0; c < 3; ++c) r[c] = -k * MxS[c];
     const float ar = dot3(a, r);
-    const float inv1 = 1.f / (1.f + dot3(a, a));
+    const float inv1 = __frcp_rn(1.f + dot3(a, a));
     cross3(a, r, axr);
     for (int c = 0; c < 3; ++c) {
         u[c] = r[c] + ar * a[c] - axr[c];
@@ -72,9 +72,12 @@ __device__ void llg_inc_vjp(const float m[3], const float hs[3], const float h[3
     }
     const float nM2 = dot3(M, M);
     const float md2 = 2.f * dot3(M, d) + dot3(d, d);
-    const float nM = sqrtf(nM2), nMt = sqrtf(nM2 + md2);
-    const float P = nMt * (nM + nMt);
-    const float s1 = -md2 / P;
+    // reciprocals from the intrinsics (the chain's latency; the adjoint
+    // tolerates their last-bit differences from the forward's sqrt and divide)
+    const float rnM = rsqrtf(nM2), rnMt = rsqrtf(nM2 + md2);
+    const float nM = nM2 * rnM, nMt = (nM2 + md2) * rnMt;
+    const float P = nMt * (nM + nMt), rP = __frcp_rn(P);
+    const float s1 = -md2 * rP;
     // dl = d + s1 (M + d)
     float gd[3], gM[3];
     for (int c = 0; c < 3; ++c) {
@@ -83,12 +86,12 @@ __device__ void llg_inc_vjp(const float m[3], const float hs[3], const float h[3
     }
     const float gs1 = dot3(ld, Md);
     // s1 = -md2 / P, P = nMt nM + nMt^2
-    float gmd2 = -gs1 / P;
-    const float gP = gs1 * md2 / (P * P);
+    float gmd2 = -gs1 * rP;
+    const float gP = gs1 * md2 * rP * rP;
     const float gnMt = gP * (nM + 2.f * nMt), gnM = gP * nMt;
-    const float gt = gnMt / (2.f * nMt);       // nMt = sqrt(nM2 + md2)
+    const float gt = 0.5f * gnMt * rnMt;       // nMt = sqrt(nM2 + md2)
     gmd2 += gt;
-    const float gnM2 = gt + gnM / (2.f * nM);
+    const float gnM2 = gt + 0.5f * gnM * rnM;
     // md2 = 2 M.d + d.d,  nM2 = M.M
     for (int c = 0; c < 3; ++c) {
         gM[c] += 2.f * gmd2 * d[c] + 2.f * gnM2 * M[c];
@@ -201,9 +204,12 @@ __device__ void cell_inputs(const MagComp &C, const BoxDiv &BD, const Inst *I, c
     if (Dprev) {
         const int st[3] = {1, bx, bxy};
         const bool lo[3] = {li > 0, lj > 0, lk > 0}, hi[3] = {li < bx - 1, lj < by - 1, lk < C.bz - 1};
+        // the neighbours' values are loaded with their material ids, not
+        // after them (a non-magnetic cell's tape entry is in bounds, unused)
         for (int a = 0; a < 3; ++a) {
-            const float dm = lo[a] && smat[v - st[a]] != 0xFF ? Dprev[a * V + v - st[a]] : 0.f;
-            const float dp = hi[a] && smat[v + st[a]] != 0xFF ? Dprev[a * V + v + st[a]] : 0.f;
+            const float dmv = lo[a] ? Dprev[a * V + v - st[a]] : 0.f, dpv = hi[a] ? Dprev[a * V + v + st[a]] : 0.f;
+            const bool ml = lo[a] && smat[v - st[a]] != 0xFF, mh = hi[a] && smat[v + st[a]] != 0xFF;
+            const float dm = ml ? dmv : 0.f, dp = mh ? dpv : 0.f;
             A[a] -= 0.25f * (dm + 2.f * Dprev[a * V + v] + dp);
         }
     }
@@ -273,13 +279,19 @@ __device__ void rev_half(const MagComp &C, const BoxDiv &BD, const FaceNb *fnb, 
             float hs[3], h[3], mm[3];
             cell_inputs(C, BD, I, R9, smat, V, Hs, Cc, Dp, m, v, hs, h, mm, nfx, nfy);
             const float ld[3] = {W.lamDl[v], W.lamDl[V + v], W.lamDl[2 * V + v]};
+            // the cell's accumulators, loaded before the arithmetic
+            float lM[3], lsm[3], lA[3];
+            for (int a = 0; a < 3; ++a) {
+                lM[a] = W.lamM[a * V + v];
+                lsm[a] = W.lamHsm[a * V + v];
+                lA[a] = W.lamA[a * V + v];
+            }
             // J^T lambda in one reverse pass: gin = (m, hs, h) adjoints
             float gin[9];
             llg_inc_vjp(mm, hs, h, I->mm[mt], ld, gin, gin + 3, gin + 6);
-            float lsm[3];
             for (int a = 0; a < 3; ++a) {
-                W.lamM[a * V + v] += gin[a];
-                lsm[a] = W.lamHsm[a * V + v] + gin[3 + a];   // bias frame
+                W.lamM[a * V + v] = lM[a] + gin[a];
+                lsm[a] += gin[3 + a];   // bias frame
             }
             if (r == 1) {   // the last iterate: hs's adjoint to global axes
                 float gq[3];
@@ -292,7 +304,7 @@ __device__ void rev_half(const MagComp &C, const BoxDiv &BD, const FaceNb *fnb, 
             from_fr(R9, lh, lg);
             for (int a = 0; a < 3; ++a) {
                 lamHg[a * V + v] = lg[a];
-                W.lamA[a * V + v] += lg[a];
+                W.lamA[a * V + v] = lA[a] + lg[a];
             }
         }
         region_sync(cs);
