@@ -346,7 +346,7 @@ __device__ void rev_half(const MagComp &C, const BoxDiv &BD, const FaceNb *fnb, 
 
 __global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSet A, int slot)
 {
-    extern __shared__ FaceNb fnb[];   // nf entries (every CTA of a region holds the whole table)
+    extern __shared__ FaceNb fnb[];   // nf entries (every CTA of a region holds the whole table), then V material ids
     __shared__ double sred[kMagThreads / 32];
     const int cs = A.cs, rc = blockIdx.x / cs;
     const int rank = cs > 1 ? (int)cg::this_cluster().block_rank() : 0;
@@ -359,8 +359,8 @@ __global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSe
     const int ex = bx + 1, exy = (bx + 1) * (by + 1), ne = exy * (bz + 1);
     const int R = A.R;
     float *wsb = A.ws + A.ws_off[rc];
-    uint8_t *smat = reinterpret_cast<uint8_t *>(wsb);              // V bytes, rounded up to floats
     RegionWS W = carve(wsb + (V + 3) / 4, nf, V);
+    uint8_t *smat = reinterpret_cast<uint8_t *>(fnb + nf);   // the box's material ids, in shared memory
     float R9[9];
     for (int q = 0; q < 9; ++q) R9[q] = I->R[q];
     // the forward step's records (mag_tape_floats): m and faces at its start,
@@ -372,13 +372,18 @@ __global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSe
     const float *D1 = T + 3 * V + nf + 3 * ne, *D2 = D1 + 3LL * R * V;
     const float *Hs2 = D2 + 3LL * R * V, *m2 = Hs2 + nf;
     const BoxDiv BD(bx, by);
-    for (int v = tid; v < V; v += nth) smat[v] = C.mat[v];
-    const float ch = I->ch;
+    for (int v = threadIdx.x; v < V; v += blockDim.x) smat[v] = C.mat[v];
+    __syncthreads();
     for (int f = threadIdx.x; f < nf; f += blockDim.x) {
         int a, fi, fj, fk, vl, vr;
         face_decode(f, BD, bx, by, bz, a, fi, fj, fk, vl, vr);
-        fnb[f] = {vl >= 0 && C.mat[vl] != 0xFF ? vl : -1, vr >= 0 && C.mat[vr] != 0xFF ? vr : -1};
-        if ((f / (int)blockDim.x) % cs != rank) continue;   // the workspace entries of another CTA's faces
+        fnb[f] = {vl >= 0 && smat[vl] != 0xFF ? vl : -1, vr >= 0 && smat[vr] != 0xFF ? vr : -1};
+    }
+    const float ch = I->ch;
+    // this CTA's faces (each written to fnb by the same thread above)
+    for (int f = tid; f < nf; f += nth) {
+        int a, fi, fj, fk, vl, vr;
+        face_decode(f, BD, bx, by, bz, a, fi, fj, fk, vl, vr);
         const int e0 = fk * exy + fj * ex + fi;
         float cu = 0.f;
         if (a == 0) cu = curl2a(Ez[e0 + ex], Ez[e0], I->idy, Ey[e0 + exy], Ey[e0], I->idz);
@@ -388,7 +393,7 @@ __global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSe
         // adjoint of the step's output faces (H^{n+3/2}): field arrays or
         // walls, plus the correction the later step left pending in fix
         const int i = C.x0 + fi, j = C.y0 + fj, k = C.z0 + fk;
-        const bool own = (vl >= 0 && C.mat[vl] != 0xFF) || (vr >= 0 && C.mat[vr] != 0xFF);
+        const bool own = fnb[f].vl >= 0 || fnb[f].vr >= 0;
         W.lamHout[f] = own ? *(a == 0 ? hx_at(I, A.lamH, i, j, k, A.lamW)
                                       : (a == 1 ? hy_at(I, A.lamH, i, j, k, A.lamW) : hz_at(I, A.lamH, i, j, k, A.lamW))) +
                                  W.fix[f]

@@ -2506,7 +2506,8 @@ extern "C" int fdtd_llg_adjoint_step(fdtd_llg_t h, const double *dJ_dE, double *
     A.nx = I.nx; A.ny = I.ny; A.nz = I.nz;
     A.R = R;
     for (int c = 0; c < nc; ++c)
-        A.fnb_bytes = std::max(A.fnb_bytes, (int)(8 * mag_faces(I.comps[c].bx, I.comps[c].by, I.comps[c].bz)));
+        A.fnb_bytes = std::max(A.fnb_bytes, (int)(8 * mag_faces(I.comps[c].bx, I.comps[c].by, I.comps[c].bz) +
+                                                  (I.comps[c].V + 15) / 16 * 16));
     const long long nbe = design_set(I, A);
     if (nbe) {
         A.dtape = S->dtape;

@@ -352,7 +352,7 @@ struct AdjSet {
     int nprobe;
     int nx, ny, nz;         // the instance's grid
     int R;                  // Jacobi iterates of every LLG solve (fixed)
-    int fnb_bytes;          // dynamic shared memory of adj_mag_kernel: 8 bytes per face of the largest region
+    int fnb_bytes;          // dynamic shared memory of adj_mag_kernel: 8 bytes per face and 1 per cell of the largest region
     // design box (superset of the edges whose eps depends on a design cell)
     int di0, dj0, dk0, dbx, dby, dbz;   // cells; edges span (dbx+1)(dby+1)(dbz+1) per component
     float *dtape;           // [slot][3][dbz+1][dby+1][dbx+1]: E at the design-box edges after step rec_n0+slot-1
