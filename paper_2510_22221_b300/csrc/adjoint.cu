@@ -18,7 +18,11 @@
 //     both half-pushes pass lambda_H through; magnetic faces carry the magnet
 //     kernel's curl adjoint here); it stores w = cb lambda_E' and lambda_E =
 //     ca lambda_E' (the class lookup once per edge), and on the design-box
-//     edges adds d J / d eps_edge += (w/dt) (E^n - E^{n+1});
+//     edges adds d J / d eps_edge += (w/dt) (E^n - E^{n+1}).  It runs beside
+//     the magnet kernel (its programmatic dependent) with the magnetic faces
+//     left out of its curls; adj_face_fix_kernel then writes the faces'
+//     values from the magnet kernel and adds their part to the edges beside
+//     them (lists built once per reverse sweep);
 //   adj_curl_e_kernel:  lambda_H += C_E w;
 //   the magnetic faces then take their own adjoint: the next reverse step's
 //     magnet kernel adds the pending correction as it reads them
@@ -165,14 +169,17 @@ __device__ __forceinline__ float *hz_at(const Inst *I, float *F0, int i, int j, 
 }
 
 // Workspace of one region (floats), nf faces, V cells:
-//   C, lamHout, lamHin, lamC, fix (5 nf);  lamM, lamDl, lamA, lamHsm, lamHg[2] (6 x 3V).
+//   C, lamHout, lamHin, lamC, fix (5 nf);  lamM, lamDl, lamA, lamHsm, lamHg[2] (6 x 3V);
+//   dq (nf).
 // fix carries the magnetic faces' pending correction from one reverse step to
 // the next; everything the forward step computed comes from the tape.  lamHg
 // is double-buffered by the parity of the iterate, so a cell's new value
-// never overwrites one that a neighbour may still read.
+// never overwrites one that a neighbour may still read.  dq: the value a
+// magnetic face must show the curl sweep (q/2, for adj_face_fix_kernel).
 struct RegionWS {
     float *C, *lamHout, *lamHin, *lamC, *fix;
     float *lamM, *lamDl, *lamA, *lamHsm, *lamHg[2];
+    float *dq;
 };
 __device__ __forceinline__ RegionWS carve(float *w, int nf, int V)
 {
@@ -181,6 +188,7 @@ __device__ __forceinline__ RegionWS carve(float *w, int nf, int V)
     float *p = r.fix + nf;
     r.lamM = p; r.lamDl = p + 3 * V; r.lamA = p + 6 * V; r.lamHsm = p + 9 * V;
     r.lamHg[0] = p + 12 * V; r.lamHg[1] = p + 15 * V;
+    r.dq = p + 18 * V;
     return r;
 }
 
@@ -348,6 +356,10 @@ __global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSe
 {
     extern __shared__ FaceNb fnb[];   // nf entries (every CTA of a region holds the whole table), then V material ids
     __shared__ double sred[kMagThreads / 32];
+    // the curl sweep adj_curl_h, launched right behind this kernel, may start
+    // now: it reads nothing this kernel writes (it leaves the magnetic faces,
+    // whose values this kernel sends to the workspace, out of its curls)
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     const int cs = A.cs, rc = blockIdx.x / cs;
     const int rank = cs > 1 ? (int)cg::this_cluster().block_rank() : 0;
     const MagComp C = L.comps[rc];
@@ -412,7 +424,9 @@ __global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSe
     // write back: for a magnetic face the curl sweep must see q/2 with
     // q = -(lamC1 + lamC2) (a plain face contributes 2 lambda_H); afterwards
     // the face takes lamHin, restored from fix by the next reverse step's
-    // magnet kernel (or adj_fix_kernel after the last)
+    // magnet kernel (or adj_fix_kernel after the last).  The curl sweep,
+    // running beside this kernel, leaves magnetic faces out of its curls;
+    // adj_face_fix_kernel adds their q/2 afterwards and writes it to them.
     for (int f = tid; f < nf; f += nth) {
         if (fnb[f].vl < 0 && fnb[f].vr < 0) continue;
         int a, fi, fj, fk, vl, vr;
@@ -425,7 +439,7 @@ __global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSe
             *p = W.lamHin[f];            // the sweeps never touch the wall arrays
             W.fix[f] = 0.f;
         } else {
-            *p = 0.5f * q;
+            W.dq[f] = 0.5f * q;
             W.fix[f] = W.lamHin[f] - 0.5f * q;
         }
     }
@@ -481,9 +495,34 @@ __global__ void __launch_bounds__(256) adj_curl_h_kernel(LaunchSet L, AdjSet A, 
     const long long o = (long long)k * plane + (long long)j * px + i;
     const float *lx = A.lamH + 3 * fs, *ly = A.lamH + 4 * fs, *lz = A.lamH + 5 * fs;
     const float c2 = 2.f * I->ch;   // dt / mu0: both half-pushes
-    const float cx = curl2a(lz[o], j > 0 ? lz[o - px] : 0.f, I->idy, ly[o], k > 0 ? ly[o - plane] : 0.f, I->idz);
-    const float cy = curl2a(lx[o], k > 0 ? lx[o - plane] : 0.f, I->idz, lz[o], i > 0 ? lz[o - 1] : 0.f, I->idx);
-    const float cz = curl2a(ly[o], i > 0 ? ly[o - 1] : 0.f, I->idx, lx[o], j > 0 ? lx[o - px] : 0.f, I->idy);
+    const int c = (int)static_cast<const ClsT *>(I->cls)[o];
+    const float4 Ca = __ldg(I->ctab + 3 * c), Cb = __ldg(I->ctab + 3 * c + 1);
+    // faces at o, o-1, o-px, o-plane; a magnetic one (flag of the class of
+    // the cell it bounds from below) counts 0 here: the magnet kernel runs
+    // beside this one and adj_face_fix_kernel adds its part
+    float hx0 = lx[o], hy0 = ly[o], hz0 = lz[o];
+    float hzj = j > 0 ? lz[o - px] : 0.f, hxj = j > 0 ? lx[o - px] : 0.f;
+    float hyk = k > 0 ? ly[o - plane] : 0.f, hxk = k > 0 ? lx[o - plane] : 0.f;
+    float hzi = i > 0 ? lz[o - 1] : 0.f, hyi = i > 0 ? ly[o - 1] : 0.f;
+    if (L.ncomp) {
+        auto flags = [&](long long oc) {
+            return __float_as_uint(__ldg(I->ctab + 3 * (int)static_cast<const ClsT *>(I->cls)[oc]).w);
+        };
+        const unsigned f0 = __float_as_uint(Ca.w);
+        const unsigned fi = i > 0 ? flags(o - 1) : 0u, fj = j > 0 ? flags(o - px) : 0u, fk = k > 0 ? flags(o - plane) : 0u;
+        if (f0 & CF_MAG_HX) hx0 = 0.f;
+        if (f0 & CF_MAG_HY) hy0 = 0.f;
+        if (f0 & CF_MAG_HZ) hz0 = 0.f;
+        if (fi & CF_MAG_HY) hyi = 0.f;
+        if (fi & CF_MAG_HZ) hzi = 0.f;
+        if (fj & CF_MAG_HX) hxj = 0.f;
+        if (fj & CF_MAG_HZ) hzj = 0.f;
+        if (fk & CF_MAG_HX) hxk = 0.f;
+        if (fk & CF_MAG_HY) hyk = 0.f;
+    }
+    const float cx = curl2a(hz0, hzj, I->idy, hy0, hyk, I->idz);
+    const float cy = curl2a(hx0, hxk, I->idz, hz0, hzi, I->idx);
+    const float cz = curl2a(hy0, hyi, I->idx, hx0, hxj, I->idy);
     float l0 = A.lamE[o], l1 = A.lamE[fs + o], l2 = A.lamE[2 * fs + o];
     for (int p = 0; p < A.nprobe; ++p)
         if (I->probe[p][0] == i && I->probe[p][1] == j && I->probe[p][2] == k) {
@@ -493,8 +532,6 @@ __global__ void __launch_bounds__(256) adj_curl_h_kernel(LaunchSet L, AdjSet A, 
             l2 += (float)sd[2];
         }
     const float ex = l0 - c2 * cx, ey = l1 - c2 * cy, ez = l2 - c2 * cz;
-    const int c = (int)static_cast<const ClsT *>(I->cls)[o];
-    const float4 Ca = __ldg(I->ctab + 3 * c), Cb = __ldg(I->ctab + 3 * c + 1);
     const float w[3] = {Cb.x * ex, Cb.y * ey, Cb.z * ez};   // w = cb lambda_E'
     A.lamEn[o] = w[0];
     A.lamEn[fs + o] = w[1];
@@ -537,6 +574,49 @@ __global__ void __launch_bounds__(256) adj_curl_e_kernel(LaunchSet L, AdjSet A)
     A.lamH[5 * fs + o] += cz;
 }
 
+// After adj_mag_kernel and adj_curl_h_kernel (which ran side by side, the
+// sweep's curls without the magnetic faces): the magnetic faces take the
+// values the magnet kernel left in the workspace (lambda_H = dq), and each
+// edge beside them their part of lambda_E' = lambda_E - (dt/mu0) C_H
+// lambda_H, d = -(dt/mu0) times the sum of coefficient x dq over its listed
+// faces, passed on as adj_curl_h_kernel passes lambda_E': w += cb d, lambda_E
+// += ca d, and on a design-box edge d J / d eps_edge += (cb d / dt) (E^n -
+// E^{n+1}).
+__global__ void __launch_bounds__(256) adj_face_fix_kernel(LaunchSet L, AdjSet A, int slot)
+{
+    const Inst *I = L.insts;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < A.nmf) {
+        A.lamH[A.mf_lam[q]] = A.ws[A.mf_ws[q]];
+        return;
+    }
+    const int e = q - A.nmf;
+    if (e >= A.nfe) return;
+    float sum = 0.f;
+    for (int c = A.fe_start[e]; c < A.fe_start[e + 1]; ++c) sum = fmaf(A.fc_coef[c], A.ws[A.fc_ws[c]], sum);
+    const float d = -(2.f * I->ch) * sum;
+    const int comp = A.fe_comp[e];
+    const long long o = A.fe_off[e], fs = I->fstride;
+    const int cl = L.cls16 ? (int)static_cast<const uint16_t *>(I->cls)[o] : (int)static_cast<const uint8_t *>(I->cls)[o];
+    const float4 Ca = __ldg(I->ctab + 3 * cl), Cb = __ldg(I->ctab + 3 * cl + 1);
+    const float ca = comp == 0 ? Ca.x : (comp == 1 ? Ca.y : Ca.z), cb = comp == 0 ? Cb.x : (comp == 1 ? Cb.y : Cb.z);
+    const float dw = cb * d;
+    A.lamEn[comp * fs + o] += dw;
+    A.lamE[comp * fs + o] += ca * d;
+    if (A.geps && dw != 0.f) {
+        const long long plane = I->plane;
+        const int px = I->px;
+        const int k = (int)(o / plane), j = (int)((o % plane) / px), i = (int)(o % px);
+        const int li = i - A.di0, lj = j - A.dj0, lk = k - A.dk0;
+        if (li >= 0 && lj >= 0 && lk >= 0 && li <= A.dbx && lj <= A.dby && lk <= A.dbz) {
+            const int bex = A.dbx + 1, bey = A.dby + 1, ne = bex * bey * (A.dbz + 1);
+            const int ed = comp * ne + (lk * bey + lj) * bex + li;
+            const float En = A.dtape[(long long)slot * 3 * ne + ed], En1 = A.dtape[(long long)(slot + 1) * 3 * ne + ed];
+            A.geps[ed] += (double)dw / I->dt * ((double)En - (double)En1);
+        }
+    }
+}
+
 // E at the design-box edges after the current step, from buffer buf, into slot
 __global__ void adj_record_design_kernel(LaunchSet L, AdjSet A, int slot, int buf)
 {
@@ -558,7 +638,13 @@ long long adj_ws_floats(int bx, int by, int bz, int R)
 {
     (void)R;
     const long long V = (long long)bx * by * bz;
-    return (V + 3) / 4 + 5 * mag_faces(bx, by, bz) + 18 * V;
+    return (V + 3) / 4 + 6 * mag_faces(bx, by, bz) + 18 * V;
+}
+
+long long adj_dq_index(int bx, int by, int bz, int f)
+{
+    const long long V = (long long)bx * by * bz;
+    return (V + 3) / 4 + 5 * mag_faces(bx, by, bz) + 18 * V + f;
 }
 
 cudaError_t adj_record_design(const LaunchSet &L, const AdjSet &A, int slot, int buf, cudaStream_t s)
@@ -590,9 +676,24 @@ cudaError_t adj_reverse_step(const LaunchSet &L, const AdjSet &A, long long n, i
         const cudaError_t e2 = cudaLaunchKernelEx(&cfg, adj_mag_kernel, L, A, slot);
         if (e2 != cudaSuccess) return e2;
     }
+    // the curl sweep beside the magnet kernel (its programmatic dependent,
+    // with no wait: the two share no data, see adj_face_fix_kernel), then the
+    // faces' changes (a plain launch: after both), then the second sweep
     const dim3 blk(32, 8), grid((A.nx + 31) / 32, (A.ny + 7) / 8, A.nz);
-    if (L.cls16) adj_curl_h_kernel<uint16_t><<<grid, blk, 0, s>>>(L, A, n, slot);
-    else adj_curl_h_kernel<uint8_t><<<grid, blk, 0, s>>>(L, A, n, slot);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = blk;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = L.ncomp ? 1 : 0;
+    const cudaError_t e3 = L.cls16 ? cudaLaunchKernelEx(&cfg, adj_curl_h_kernel<uint16_t>, L, A, n, slot)
+                                   : cudaLaunchKernelEx(&cfg, adj_curl_h_kernel<uint8_t>, L, A, n, slot);
+    if (e3 != cudaSuccess) return e3;
+    const int nfix = A.nmf + A.nfe;
+    if (L.ncomp && nfix > 0) adj_face_fix_kernel<<<(nfix + 255) / 256, 256, 0, s>>>(L, A, slot);
     adj_curl_e_kernel<<<grid, blk, 0, s>>>(L, A);
     return cudaGetLastError();
 }

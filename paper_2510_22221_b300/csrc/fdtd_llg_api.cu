@@ -2508,6 +2508,95 @@ extern "C" int fdtd_llg_adjoint_step(fdtd_llg_t h, const double *dJ_dE, double *
     for (int c = 0; c < nc; ++c)
         A.fnb_bytes = std::max(A.fnb_bytes, (int)(8 * mag_faces(I.comps[c].bx, I.comps[c].by, I.comps[c].bz) +
                                                   (I.comps[c].V + 15) / 16 * 16));
+    // the magnet regions' faces and the edges whose curl of H reads them:
+    // adj_curl_h runs beside the magnet kernel with those faces left out;
+    // adj_face_fix_kernel writes their values and adds their part afterwards
+    std::vector<long long> mf_lam, mf_ws, fe_off, fc_ws;
+    std::vector<int> fe_comp, fe_start(1, 0);
+    std::vector<float> fc_coef;
+    {
+        const float id[3] = {(float)(1.0 / I.dx), (float)(1.0 / I.dy), (float)(1.0 / I.dz)};
+        const long long fsz = (long long)I.n_field(), plane = (long long)I.ny * I.px;
+        std::map<std::pair<int, long long>, std::vector<std::pair<long long, float>>> edges;
+        for (int c = 0; c < nc; ++c) {
+            const MagComp &C = I.comps[c];
+            std::vector<uint8_t> mat(C.V);
+            if (cudaMemcpy(mat.data(), C.mat, C.V, cudaMemcpyDeviceToHost) != cudaSuccess) {
+                cleanup();
+                return fail(h, FDTD_E_CUDA, "adjoint setup: reading the magnet regions failed");
+            }
+            const int bx = C.bx, by = C.by, bz = C.bz;
+            const int nfx = (bx + 1) * by * bz, nfy = bx * (by + 1) * bz, nfz = bx * by * (bz + 1);
+            auto magc = [&](int li, int lj, int lk) {
+                return li >= 0 && lj >= 0 && lk >= 0 && li < bx && lj < by && lk < bz && mat[(lk * by + lj) * bx + li] != 0xFF;
+            };
+            for (int f = 0; f < nfx + nfy + nfz; ++f) {
+                int a, fi, fj, fk;   // the magnet kernel's face numbering
+                if (f < nfx) {
+                    a = 0; fi = f % (bx + 1); fj = (f / (bx + 1)) % by; fk = f / ((bx + 1) * by);
+                } else if (f < nfx + nfy) {
+                    const int g = f - nfx;
+                    a = 1; fi = g % bx; fj = (g / bx) % (by + 1); fk = g / (bx * (by + 1));
+                } else {
+                    const int g = f - nfx - nfy;
+                    a = 2; fi = g % bx; fj = (g / bx) % by; fk = g / (bx * by);
+                }
+                if (!magc(fi - (a == 0), fj - (a == 1), fk - (a == 2)) && !magc(fi, fj, fk)) continue;
+                const int i = C.x0 + fi, j = C.y0 + fj, k = C.z0 + fk;
+                if ((a == 0 && i == I.nx) || (a == 1 && j == I.ny) || (a == 2 && k == I.nz)) continue;   // wall: the kernel writes it
+                const long long wsi = ws_off[c] + adj_dq_index(bx, by, bz, f);
+                mf_lam.push_back((3 + a) * fsz + k * plane + (long long)j * I.px + i);
+                mf_ws.push_back(wsi);
+                // the edges (component, offset) whose C_H lambda_H holds this
+                // face, and its coefficient there (the curls of adj_curl_h_kernel)
+                struct Term { int comp, di, dj, dk; float coef; };
+                Term t[4];
+                if (a == 0) { t[0] = {1, 0, 0, 0, id[2]}; t[1] = {1, 0, 0, 1, -id[2]}; t[2] = {2, 0, 0, 0, -id[1]}; t[3] = {2, 0, 1, 0, id[1]}; }
+                else if (a == 1) { t[0] = {0, 0, 0, 0, -id[2]}; t[1] = {0, 0, 0, 1, id[2]}; t[2] = {2, 0, 0, 0, id[0]}; t[3] = {2, 1, 0, 0, -id[0]}; }
+                else { t[0] = {0, 0, 0, 0, id[1]}; t[1] = {0, 0, 1, 0, -id[1]}; t[2] = {1, 0, 0, 0, -id[0]}; t[3] = {1, 1, 0, 0, id[0]}; }
+                for (const Term &q : t) {
+                    const int ei = i + q.di, ej = j + q.dj, ek = k + q.dk;
+                    if (ei >= I.nx || ej >= I.ny || ek >= I.nz) continue;   // not an edge the sweep updates
+                    edges[{q.comp, ek * plane + (long long)ej * I.px + ei}].push_back({wsi, q.coef});
+                }
+            }
+        }
+        for (auto &kv : edges) {
+            fe_comp.push_back(kv.first.first);
+            fe_off.push_back(kv.first.second);
+            for (auto &cq : kv.second) {
+                fc_ws.push_back(cq.first);
+                fc_coef.push_back(cq.second);
+            }
+            fe_start.push_back((int)fc_ws.size());
+        }
+    }
+    A.nmf = (int)mf_lam.size();
+    A.nfe = (int)fe_off.size();
+    long long *d_mf = (long long *)alloc(std::max<size_t>(1, 2 * mf_lam.size()) * sizeof(long long));
+    long long *d_feo = (long long *)alloc(std::max<size_t>(1, fe_off.size() + fc_ws.size()) * sizeof(long long));
+    int *d_fei = (int *)alloc((fe_comp.size() + fe_start.size()) * sizeof(int));
+    float *d_fcc = (float *)alloc(std::max<size_t>(1, fc_coef.size()) * sizeof(float));
+    if (!d_mf || !d_feo || !d_fei || !d_fcc) { cleanup(); return fail(h, FDTD_E_OOM, "adjoint buffers: device allocation failed"); }
+    A.mf_lam = d_mf; A.mf_ws = d_mf + mf_lam.size();
+    A.fe_off = d_feo; A.fc_ws = d_feo + fe_off.size();
+    A.fe_comp = d_fei; A.fe_start = d_fei + fe_comp.size();
+    A.fc_coef = d_fcc;
+    {
+        cudaError_t e = cudaSuccess;
+        auto up = [&](void *dst, const void *src, size_t bytes) {
+            if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, S->stream);
+        };
+        up(d_mf, mf_lam.data(), mf_lam.size() * 8);
+        up(d_mf + mf_lam.size(), mf_ws.data(), mf_ws.size() * 8);
+        up(d_feo, fe_off.data(), fe_off.size() * 8);
+        up(d_feo + fe_off.size(), fc_ws.data(), fc_ws.size() * 8);
+        up(d_fei, fe_comp.data(), fe_comp.size() * 4);
+        up(d_fei + fe_comp.size(), fe_start.data(), fe_start.size() * 4);
+        up(d_fcc, fc_coef.data(), fc_coef.size() * 4);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);   // before the host lists are released
+        if (e != cudaSuccess) { cleanup(); return fail(h, FDTD_E_CUDA, std::string("adjoint setup: ") + cudaGetErrorString(e)); }
+    }
     const long long nbe = design_set(I, A);
     if (nbe) {
         A.dtape = S->dtape;

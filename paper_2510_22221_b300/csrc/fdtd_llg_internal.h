@@ -357,8 +357,23 @@ struct AdjSet {
     int di0, dj0, dk0, dbx, dby, dbz;   // cells; edges span (dbx+1)(dby+1)(dbz+1) per component
     float *dtape;           // [slot][3][dbz+1][dby+1][dbx+1]: E at the design-box edges after step rec_n0+slot-1
     double *geps;           // per design-box edge: d J / d eps_edge (FP64)
+    // The curl sweep adj_curl_h runs beside adj_mag_kernel with the magnetic
+    // faces left out of its curls; the magnet kernel puts those faces' values
+    // in its workspace, which adj_face_fix_kernel then writes to the faces
+    // (nmf of them: lambda_H offset, workspace index) and, times the curl's
+    // coefficients, adds to the edges beside them (nfe edges: component, cell
+    // offset, and the contributions fe_start[e] .. fe_start[e+1] - 1:
+    // workspace index and coefficient).  Lists in a fixed order, so the sums
+    // are the same bits every run.
+    int nmf, nfe;
+    const long long *mf_lam, *mf_ws;
+    const int *fe_comp, *fe_start;
+    const long long *fe_off, *fc_ws;
+    const float *fc_coef;
 };
 long long adj_ws_floats(int bx, int by, int bz, int R);
+// workspace index (within the region's workspace) of the change of face f
+long long adj_dq_index(int bx, int by, int bz, int f);
 // stream-ordered write of the device step counter (and clear of the CTA count)
 cudaError_t set_device_step(StepCtl *ctl, long long n, cudaStream_t s);
 cudaError_t adj_record_design(const LaunchSet &L, const AdjSet &A, int slot, int buf, cudaStream_t s);
