@@ -644,7 +644,7 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
                 const float ry = by_ - mm.kappa * (Mz * hex - mx * hez);
                 const float rz = bz_ - mm.kappa * (mx * hey - my * hex);
                 const float ar = ax * rx + ay * ry + az * rz;
-                const float inv1 = 1.f / (1.f + ax * ax + ay * ay + az * az);
+                const float inv1 = __frcp_rn(1.f + ax * ax + ay * ay + az * az);
                 const float ddx = (rx + ar * ax - (ay * rz - az * ry)) * inv1;
                 const float ddy = (ry + ar * ay - (az * rx - ax * rz)) * inv1;
                 const float ddz = (rz + ar * az - (ax * ry - ay * rx)) * inv1;
@@ -652,14 +652,19 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
                 // s1 = |M^n|/|M~| - 1 = -(2 M^n.d + |d|^2) / (|M~| (|M^n| + |M~|))
                 const float nM2 = mx * mx + my * my + Mz * Mz;
                 const float md2 = 2.f * (mx * ddx + my * ddy + Mz * ddz) + (ddx * ddx + ddy * ddy + ddz * ddz);
-                const float nM = sqrtf(nM2), nMt = sqrtf(nM2 + md2);
-                const float s1 = -md2 / (nMt * (nM + nMt));
+                // (reciprocal square roots and one reciprocal: s1 is second
+                // order in d, so their last-bit errors leave |M| at FP32 rounding)
+                const float rnM = rsqrtf(nM2), rnMt = rsqrtf(nM2 + md2);
+                const float nM = nM2 * rnM, nMt = (nM2 + md2) * rnMt;
+                const float s1 = -md2 * __frcp_rn(nMt * (nM + nMt));
                 dl[q][0] = ddx + s1 * (mx + ddx);
                 dl[q][1] = ddy + s1 * (my + ddy);
                 dl[q][2] = ddz + s1 * (Mz + ddz);
                 from_frame(R, dl[q][0], dl[q][1], dl[q][2], dn[q][0], dn[q][1], dn[q][2]);
-                const float e0 = dn[q][0] - d0, e1 = dn[q][1] - d1, e2 = dn[q][2] - d2;
-                res = fmaxf(res, sqrtf(e0 * e0 + e1 * e1 + e2 * e2) * mm.inv_Ms);
+                if (L.llg_fixed_iter <= 0) {   // the residual decides only a tolerance-stopped solve
+                    const float e0 = dn[q][0] - d0, e1 = dn[q][1] - d1, e2 = dn[q][2] - d2;
+                    res = fmaxf(res, sqrtf(e0 * e0 + e1 * e1 + e2 * e2) * mm.inv_Ms);
+                }
             }
             __syncthreads();
 #pragma unroll
@@ -680,7 +685,9 @@ __global__ void __launch_bounds__(kMagThreads) mag_kernel(LaunchSet L)
                     TD[2 * RV + rv] = sD[2 * V + v];
                 }
             }
-            res = block_max(res, sredf);   // also orders every sD write before the exports below
+            // (either also orders every sD write before the exports below)
+            if (L.llg_fixed_iter <= 0) res = block_max(res, sredf);
+            else __syncthreads();
             if constexpr (CL) {
                 // the A-component of the change of M on the first and last
                 // layer (zero outside the region) for the CTAs beside this one
