@@ -44,8 +44,27 @@ def _gpu(w, N, n0, interval=0, budget=-1, cluster=0):
     return J, ge, gh
 
 
+def _touching():
+    """The 16^3 case with the design box moved against the YIG block (design
+    edges beside magnetic faces) and a second 1x2x2 YIG block diagonal to
+    the first's corner: two regions whose faces share edges."""
+    import dataclasses
+
+    w = W.adjoint_small(n=16, steps=260, design=(6, 6, 2), block=(4, 4, 2))
+    x0, y0, z0, dx_, dy_, dz_ = w.design_box
+    mid = w.mat_id.copy()
+    xs = np.nonzero(mid.any(axis=(0, 1)))[0]
+    ys = np.nonzero(mid.any(axis=(0, 2)))[0]
+    zs = np.nonzero(mid.any(axis=(1, 2)))[0]
+    box = (int(xs[0]) - dx_, y0, z0, dx_, dy_, dz_)              # ends where the block starts
+    mid[zs[0]:zs[-1] + 1, ys[-1] + 1:ys[-1] + 3, xs[-1] + 1] = 1   # touches the block's corner edge only
+    return dataclasses.replace(w, mat_id=mid, design_box=box)
+
+
 CASES = {
     "design16": (lambda: W.adjoint_small(n=16, steps=260, design=(6, 6, 2), block=(4, 4, 2)), 260, 160, 1e-4),
+    # design edges beside magnetic faces, and two regions sharing edges
+    "touching16": (_touching, 260, 160, 1e-3),
     # the 24^3 analogue of the 128x128x64 design case (8x8x2 design cells, a
     # 4x4x2 YIG block, 400 steps, the objective over the last quarter)
     "design24": (lambda: W.adjoint_small(n=24, steps=400), 400, 300, 1e-3),
