@@ -575,35 +575,50 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
     uint64_t magw[4] = {0, 0, 0, 0};
     for (int m = 0; m < ntable; ++m)
         if (magm[m]) magw[m >> 6] |= 1ull << (m & 63);
+    // the key set starts small (a grid has few distinct neighbourhoods) and
+    // grows sixteenfold whenever a scan overflows it, up to 2^20 slots; its
+    // arrays and the counters share one allocation
     KeyScan K{};
-    K.cap = 1024;
-    while (K.cap < 2 * std::min(nc, (size_t)1 << 19)) K.cap *= 2;
+    K.cap = 64;
+    while (K.cap < 4096 && K.cap < 2 * nc) K.cap *= 2;
     K.mcap = std::max<unsigned long long>(1, std::min<unsigned long long>(nc, 1ull << 16));
-    K.tk = (unsigned long long *)tmpd.get((size_t)K.cap * 8);
-    K.first = (unsigned long long *)tmpd.get((size_t)K.cap * 8);
-    K.kout = (unsigned long long *)tmpd.get((size_t)K.cap * 8);
-    K.fout = (unsigned long long *)tmpd.get((size_t)K.cap * 8);
+    auto alloc_set = [&]() -> bool {
+        unsigned char *p = (unsigned char *)tmpd.get((size_t)K.cap * 32 + 32);
+        if (!p) return false;
+        K.tk = (unsigned long long *)p;
+        K.first = K.tk + K.cap;
+        K.kout = K.first + K.cap;
+        K.fout = K.kout + K.cap;
+        unsigned char *cnt = p + (size_t)K.cap * 32;
+        K.mcount = (unsigned long long *)cnt;
+        K.top = (unsigned *)(cnt + 8);
+        K.overflow = (unsigned *)(cnt + 12);
+        K.kcount = (unsigned *)(cnt + 16);
+        return true;
+    };
     K.mlist = (unsigned long long *)tmpd.get((size_t)K.mcap * 8);
-    unsigned char *cnt = (unsigned char *)tmpd.get(32);
-    if (!K.tk || !K.first || !K.kout || !K.fout || !K.mlist || !cnt) return fail(h, FDTD_E_OOM, "device allocation failed");
-    K.mcount = (unsigned long long *)cnt;
-    K.top = (unsigned *)(cnt + 8);
-    K.overflow = (unsigned *)(cnt + 12);
-    K.kcount = (unsigned *)(cnt + 16);
+    if (!K.mlist || !alloc_set()) return fail(h, FDTD_E_OOM, "device allocation failed");
     struct {
         unsigned long long mcount;
         unsigned top, overflow, kcount, pad;
     } hc{};
-    for (int pass = 0; pass < 2; ++pass) {
+    for (int pass = 0; pass < 8; ++pass) {
         CKR(h, launch_key_scan(dmid, nx, ny, nz, magw, has_design, db, K, S->stream));
         CKR(h, launch_key_compact(K, S->stream));
-        CKR(h, cudaMemcpyAsync(&hc, cnt, sizeof hc, cudaMemcpyDeviceToHost, S->stream));
+        CKR(h, cudaMemcpyAsync(&hc, K.mcount, sizeof hc, cudaMemcpyDeviceToHost, S->stream));
         CKR(h, cudaStreamSynchronize(S->stream));
-        if (hc.mcount <= K.mcap) break;
-        // more magnetic cells than the list holds: again with room for all
-        K.mlist = (unsigned long long *)tmpd.get((size_t)hc.mcount * 8);
-        if (!K.mlist) return fail(h, FDTD_E_OOM, "device allocation failed");
-        K.mcap = hc.mcount;
+        if (hc.overflow && K.cap < (1u << 20)) {   // again with a larger set
+            K.cap = std::min(K.cap * 16, 1u << 20);
+            if (!alloc_set()) return fail(h, FDTD_E_OOM, "device allocation failed");
+            continue;
+        }
+        if (hc.mcount > K.mcap) {   // more magnetic cells than the list holds: again with room for all
+            K.mlist = (unsigned long long *)tmpd.get((size_t)hc.mcount * 8);
+            if (!K.mlist) return fail(h, FDTD_E_OOM, "device allocation failed");
+            K.mcap = hc.mcount;
+            continue;
+        }
+        break;
     }
     if (nc && hc.top >= (unsigned)ntable) return fail(h, FDTD_E_INVAL, "mat_id references a material beyond ntable");
     if (hc.overflow)

@@ -234,6 +234,28 @@ def test_many_small_magnet_regions_against_the_oracle():
     sim.destroy()
 
 
+def test_many_neighbourhoods_grow_the_device_key_set():
+    """200 materials with the same properties under random ids: 8640
+    distinct neighbourhoods (more than the device key set's first 4096
+    slots, so set_materials scans again with a larger set) that all form
+    the classes of plain vacuum, so the run equals, to the bit, the same
+    grid with every id 0."""
+    import dataclasses
+
+    w = W.random_small(5, nx=24, ny=20, nz=18, steps=20, magnets=False)
+    w = dataclasses.replace(w, materials=[W.material() for _ in range(200)], eps_design=None, design_box=None)
+    ids = np.random.default_rng(1).integers(0, 200, size=w.mat_id.shape).astype(np.uint8)
+    a = pkg.from_workload(dataclasses.replace(w, mat_id=ids), probe_capacity=w.steps)
+    b = pkg.from_workload(dataclasses.replace(w, mat_id=np.zeros_like(ids)), probe_capacity=w.steps)
+    a.step(w.steps)
+    b.step(w.steps)
+    for n in ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz"):
+        np.testing.assert_array_equal(a.get_field(n), b.get_field(n))
+    np.testing.assert_array_equal(a.energy(), b.energy())
+    a.destroy()
+    b.destroy()
+
+
 def test_material_id_beyond_the_table_is_refused():
     """An id >= ntable anywhere in mat_id (found by the device scan) is
     refused with FDTD_E_INVAL, from host and from device memory, and the
