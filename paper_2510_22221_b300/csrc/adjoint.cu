@@ -16,17 +16,20 @@
 //   adj_curl_h_kernel:  the probe seed dJ/dE^n is added to lambda_E, then
 //     lambda_E' = lambda_E - (dt/mu0) C_H lambda_H (for a non-magnetic face
 //     both half-pushes pass lambda_H through; magnetic faces carry the magnet
-//     kernel's curl adjoint here); it stores w = cb lambda_E' and lambda_E =
-//     ca lambda_E' (the class lookup once per edge), and on the design-box
-//     edges adds d J / d eps_edge += (w/dt) (E^n - E^{n+1}).  It runs beside
-//     the magnet kernel (its programmatic dependent) with the magnetic faces
-//     left out of its curls; adj_face_fix_kernel then writes the faces'
-//     values from the magnet kernel and adds their part to the edges beside
-//     them (lists built once per reverse sweep);
-//   adj_curl_e_kernel:  lambda_H += C_E w;
+//     kernel's curl adjoint here); it stores w = cb lambda_E' (per step
+//     parity) and lambda_E = ca lambda_E' (the class lookup once per edge),
+//     and on the design-box edges adds d J / d eps_edge += (w/dt) (E^n -
+//     E^{n+1}).  Its curls leave the magnetic faces out; adj_face_fix_kernel
+//     then writes those faces' values from the magnet kernel and adds their
+//     part to the edges beside them (lists built once per reverse sweep);
+//   adj_curl_e_kernel:  lambda_H += C_E w, except at the magnetic faces, to
+//     which the next reverse step's magnet kernel adds C_E w as it reads them
+//     (adj_fix_kernel after the last);
 //   the magnetic faces then take their own adjoint: the next reverse step's
 //     magnet kernel adds the pending correction as it reads them
 //     (adj_fix_kernel applies the last one after the sweep).
+// So the magnet kernel of a step shares no data with the two curl sweeps
+// beside which it runs (on a second stream, adj_reverse_step).
 // C_E^T = C_H on the Yee grid, so the transposed curls are the forward curls.
 #include "fdtd_llg_internal.h"
 
@@ -144,6 +147,21 @@ __device__ __forceinline__ void from_fr(const float *R, const float l[3], float 
 __device__ __forceinline__ float curl2a(float a1, float b1, float i1, float a2, float b2, float i2)
 {
     return __fsub_rn(__fmul_rn(__fsub_rn(a1, b1), i1), __fmul_rn(__fsub_rn(a2, b2), i2));
+}
+
+// Component a of C_E w at the face (i, j, k) of the field arrays (w zero
+// beyond the far walls): what adj_curl_e_kernel adds to lambda_H there, with
+// its arithmetic, for the magnetic faces that it leaves to the magnet kernels.
+__device__ __forceinline__ float face_curl_w(const Inst *I, const float *w, int a, int i, int j, int k)
+{
+    const long long fs = I->fstride, plane = I->plane;
+    const int px = I->px;
+    const long long o = (long long)k * plane + (long long)j * px + i;
+    const float *wx = w, *wy = w + fs, *wz = w + 2 * fs;
+    const bool xi = i + 1 < I->nx, yj = j + 1 < I->ny, zk = k + 1 < I->nz;
+    if (a == 0) return curl2a(yj ? wz[o + px] : 0.f, wz[o], I->idy, zk ? wy[o + plane] : 0.f, wy[o], I->idz);
+    if (a == 1) return curl2a(zk ? wx[o + plane] : 0.f, wx[o], I->idz, xi ? wz[o + 1] : 0.f, wz[o], I->idx);
+    return curl2a(xi ? wy[o + 1] : 0.f, wy[o], I->idx, yj ? wx[o + px] : 0.f, wx[o], I->idy);
 }
 
 // Magnetic neighbours of face f (cells on its low and high side, -1 where
@@ -352,14 +370,10 @@ __device__ void rev_half(const MagComp &C, const BoxDiv &BD, const FaceNb *fnb, 
     }
 }
 
-__global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSet A, int slot)
+__global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSet A, int slot, int wpar)
 {
     extern __shared__ FaceNb fnb[];   // nf entries (every CTA of a region holds the whole table), then V material ids
     __shared__ double sred[kMagThreads / 32];
-    // the curl sweep adj_curl_h, launched right behind this kernel, may start
-    // now: it reads nothing this kernel writes (it leaves the magnetic faces,
-    // whose values this kernel sends to the workspace, out of its curls)
-    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     const int cs = A.cs, rc = blockIdx.x / cs;
     const int rank = cs > 1 ? (int)cg::this_cluster().block_rank() : 0;
     const MagComp C = L.comps[rc];
@@ -406,10 +420,18 @@ __global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSe
         // walls, plus the correction the later step left pending in fix
         const int i = C.x0 + fi, j = C.y0 + fj, k = C.z0 + fk;
         const bool own = fnb[f].vl >= 0 || fnb[f].vr >= 0;
-        W.lamHout[f] = own ? *(a == 0 ? hx_at(I, A.lamH, i, j, k, A.lamW)
-                                      : (a == 1 ? hy_at(I, A.lamH, i, j, k, A.lamW) : hz_at(I, A.lamH, i, j, k, A.lamW))) +
-                                 W.fix[f]
-                           : 0.f;
+        // the adjoint of the step's output face: lambda_H, with C_E w of the
+        // later step added here for a magnetic face off the far walls (the
+        // H-curl sweep leaves those faces out), then the pending correction
+        float lh = 0.f;
+        if (own) {
+            const bool wall = (a == 0 && i == I->nx) || (a == 1 && j == I->ny) || (a == 2 && k == I->nz);
+            lh = *(a == 0 ? hx_at(I, A.lamH, i, j, k, A.lamW)
+                          : (a == 1 ? hy_at(I, A.lamH, i, j, k, A.lamW) : hz_at(I, A.lamH, i, j, k, A.lamW)));
+            if (!wall) lh = lh + face_curl_w(I, A.lamEn[wpar], a, i, j, k);
+            lh = lh + W.fix[f];
+        }
+        W.lamHout[f] = lh;
     }
     region_sync(cs);
     // reverse: second half-push, then the first
@@ -457,8 +479,9 @@ __global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSe
     if (cs > 1) cg::this_cluster().sync();
 }
 
-// magnetic faces: lambda_H = (value after the curl sweep) - q/2 + lamHin
-__global__ void adj_fix_kernel(LaunchSet L, AdjSet A)
+// magnetic faces after the last reverse step: lambda_H = (q/2 + C_E w of
+// that step, which the H-curl sweep left out) + (lamHin - q/2)
+__global__ void adj_fix_kernel(LaunchSet L, AdjSet A, int wpar)
 {
     const MagComp C = L.comps[blockIdx.x];
     const Inst *I = L.insts + C.inst;
@@ -476,7 +499,7 @@ __global__ void adj_fix_kernel(LaunchSet L, AdjSet A)
         const bool wall = (a == 0 && i == I->nx) || (a == 1 && j == I->ny) || (a == 2 && k == I->nz);
         if (wall) continue;
         float *p = a == 0 ? hx_at(I, A.lamH, i, j, k, A.lamW) : (a == 1 ? hy_at(I, A.lamH, i, j, k, A.lamW) : hz_at(I, A.lamH, i, j, k, A.lamW));
-        *p += W.fix[f];
+        *p = (*p + face_curl_w(I, A.lamEn[wpar], a, i, j, k)) + W.fix[f];
     }
 }
 
@@ -533,9 +556,10 @@ __global__ void __launch_bounds__(256) adj_curl_h_kernel(LaunchSet L, AdjSet A, 
         }
     const float ex = l0 - c2 * cx, ey = l1 - c2 * cy, ez = l2 - c2 * cz;
     const float w[3] = {Cb.x * ex, Cb.y * ey, Cb.z * ez};   // w = cb lambda_E'
-    A.lamEn[o] = w[0];
-    A.lamEn[fs + o] = w[1];
-    A.lamEn[2 * fs + o] = w[2];
+    float *wn = A.lamEn[n & 1];
+    wn[o] = w[0];
+    wn[fs + o] = w[1];
+    wn[2 * fs + o] = w[2];
     A.lamE[o] = Ca.x * ex;            // lambda_E = ca lambda_E'
     A.lamE[fs + o] = Ca.y * ey;
     A.lamE[2 * fs + o] = Ca.z * ez;
@@ -554,8 +578,11 @@ __global__ void __launch_bounds__(256) adj_curl_h_kernel(LaunchSet L, AdjSet A, 
     }
 }
 
-// lambda_H += C_E w  (w = cb lambda_E', zero beyond the far walls)
-__global__ void __launch_bounds__(256) adj_curl_e_kernel(LaunchSet L, AdjSet A)
+// lambda_H += C_E w  (w = cb lambda_E' of a step of parity par, zero beyond
+// the far walls) at every face except the magnetic ones: the next reverse
+// step's magnet kernel adds C_E w to those as it reads them (adj_fix_kernel
+// after the last), so this sweep can run beside it
+__global__ void __launch_bounds__(256) adj_curl_e_kernel(LaunchSet L, AdjSet A, int par)
 {
     const Inst *I = L.insts;
     const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
@@ -563,15 +590,20 @@ __global__ void __launch_bounds__(256) adj_curl_e_kernel(LaunchSet L, AdjSet A)
     const long long fs = I->fstride, plane = I->plane;
     const int px = I->px;
     const long long o = (long long)k * plane + (long long)j * px + i;
-    const float *wx_ = A.lamEn, *wy_ = A.lamEn + fs, *wz_ = A.lamEn + 2 * fs;
+    const float *wx_ = A.lamEn[par], *wy_ = wx_ + fs, *wz_ = wx_ + 2 * fs;
     const bool xi = i + 1 < I->nx, yj = j + 1 < I->ny, zk = k + 1 < I->nz;
     const float wx = wx_[o], wy = wy_[o], wz = wz_[o];
     const float cx = curl2a(yj ? wz_[o + px] : 0.f, wz, I->idy, zk ? wy_[o + plane] : 0.f, wy, I->idz);
     const float cy = curl2a(zk ? wx_[o + plane] : 0.f, wx, I->idz, xi ? wz_[o + 1] : 0.f, wz, I->idx);
     const float cz = curl2a(xi ? wy_[o + 1] : 0.f, wy, I->idx, yj ? wx_[o + px] : 0.f, wx, I->idy);
-    A.lamH[3 * fs + o] += cx;
-    A.lamH[4 * fs + o] += cy;
-    A.lamH[5 * fs + o] += cz;
+    unsigned fl = 0u;   // the magnetic-face flags of cell o's class
+    if (L.ncomp) {
+        const int c = L.cls16 ? (int)static_cast<const uint16_t *>(I->cls)[o] : (int)static_cast<const uint8_t *>(I->cls)[o];
+        fl = __float_as_uint(__ldg(I->ctab + 3 * c).w);
+    }
+    if (!(fl & CF_MAG_HX)) A.lamH[3 * fs + o] += cx;
+    if (!(fl & CF_MAG_HY)) A.lamH[4 * fs + o] += cy;
+    if (!(fl & CF_MAG_HZ)) A.lamH[5 * fs + o] += cz;
 }
 
 // After adj_mag_kernel and adj_curl_h_kernel (which ran side by side, the
@@ -582,7 +614,7 @@ __global__ void __launch_bounds__(256) adj_curl_e_kernel(LaunchSet L, AdjSet A)
 // faces, passed on as adj_curl_h_kernel passes lambda_E': w += cb d, lambda_E
 // += ca d, and on a design-box edge d J / d eps_edge += (cb d / dt) (E^n -
 // E^{n+1}).
-__global__ void __launch_bounds__(256) adj_face_fix_kernel(LaunchSet L, AdjSet A, int slot)
+__global__ void __launch_bounds__(256) adj_face_fix_kernel(LaunchSet L, AdjSet A, int slot, int par)
 {
     const Inst *I = L.insts;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -601,7 +633,7 @@ __global__ void __launch_bounds__(256) adj_face_fix_kernel(LaunchSet L, AdjSet A
     const float4 Ca = __ldg(I->ctab + 3 * cl), Cb = __ldg(I->ctab + 3 * cl + 1);
     const float ca = comp == 0 ? Ca.x : (comp == 1 ? Ca.y : Ca.z), cb = comp == 0 ? Cb.x : (comp == 1 ? Cb.y : Cb.z);
     const float dw = cb * d;
-    A.lamEn[comp * fs + o] += dw;
+    A.lamEn[par][comp * fs + o] += dw;
     A.lamE[comp * fs + o] += ca * d;
     if (A.geps && dw != 0.f) {
         const long long plane = I->plane;
@@ -655,17 +687,29 @@ cudaError_t adj_record_design(const LaunchSet &L, const AdjSet &A, int slot, int
 }
 
 // Reverse of forward step n, whose records sit in tape slot `slot`
-// (magnets) and design slots slot, slot+1 (E^n, E^{n+1}).
-cudaError_t adj_reverse_step(const LaunchSet &L, const AdjSet &A, long long n, int slot, cudaStream_t s)
+// (magnets) and design slots slot, slot+1 (E^n, E^{n+1}).  On stream st.b,
+// after everything now on s (the face fix of step n+1, a segment's
+// recomputation): the magnet kernel.  On s beside it: the H-curl sweep of
+// step n+1 (deferred from the previous call) and the E-curl sweep of step
+// n; then, after the magnet kernel, the face fix.  The H-curl sweep of step
+// n waits for the next call (or adj_finish).  The two share no data: the
+// sweeps leave the magnetic faces to the magnet kernels, and w is kept per
+// step parity (the magnet kernel reads step n+1's, the E-curl sweep writes
+// step n's).
+cudaError_t adj_reverse_step(const LaunchSet &L, const AdjSet &A, long long n, int slot, cudaStream_t s,
+                             AdjStreams &st)
 {
+    const dim3 blk(32, 8), grid((A.nx + 31) / 32, (A.ny + 7) / 8, A.nz);
     if (L.ncomp) {
-        const cudaError_t e = cudaFuncSetAttribute(adj_mag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, A.fnb_bytes);
+        cudaError_t e = cudaFuncSetAttribute(adj_mag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, A.fnb_bytes);
+        if (e == cudaSuccess) e = cudaEventRecord(st.a_ready, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st.b, st.a_ready, 0);
         if (e != cudaSuccess) return e;
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(L.ncomp * A.cs);
         cfg.blockDim = dim3(kMagThreads);
         cfg.dynamicSmemBytes = A.fnb_bytes;
-        cfg.stream = s;
+        cfg.stream = st.b;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
         at[0].val.clusterDim.x = A.cs;
@@ -673,35 +717,36 @@ cudaError_t adj_reverse_step(const LaunchSet &L, const AdjSet &A, long long n, i
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = A.cs > 1 ? 1 : 0;
-        const cudaError_t e2 = cudaLaunchKernelEx(&cfg, adj_mag_kernel, L, A, slot);
-        if (e2 != cudaSuccess) return e2;
+        e = cudaLaunchKernelEx(&cfg, adj_mag_kernel, L, A, slot, (int)((n + 1) & 1));
+        if (e == cudaSuccess) e = cudaEventRecord(st.mag_done, st.b);
+        if (e != cudaSuccess) return e;
     }
-    // the curl sweep beside the magnet kernel (its programmatic dependent,
-    // with no wait: the two share no data, see adj_face_fix_kernel), then the
-    // faces' changes (a plain launch: after both), then the second sweep
-    const dim3 blk(32, 8), grid((A.nx + 31) / 32, (A.ny + 7) / 8, A.nz);
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = grid;
-    cfg.blockDim = blk;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = L.ncomp ? 1 : 0;
-    const cudaError_t e3 = L.cls16 ? cudaLaunchKernelEx(&cfg, adj_curl_h_kernel<uint16_t>, L, A, n, slot)
-                                   : cudaLaunchKernelEx(&cfg, adj_curl_h_kernel<uint8_t>, L, A, n, slot);
-    if (e3 != cudaSuccess) return e3;
+    if (st.pending >= 0) adj_curl_e_kernel<<<grid, blk, 0, s>>>(L, A, (int)(st.pending & 1));
+    st.pending = -1;
+    if (L.cls16) adj_curl_h_kernel<uint16_t><<<grid, blk, 0, s>>>(L, A, n, slot);
+    else adj_curl_h_kernel<uint8_t><<<grid, blk, 0, s>>>(L, A, n, slot);
     const int nfix = A.nmf + A.nfe;
-    if (L.ncomp && nfix > 0) adj_face_fix_kernel<<<(nfix + 255) / 256, 256, 0, s>>>(L, A, slot);
-    adj_curl_e_kernel<<<grid, blk, 0, s>>>(L, A);
+    if (L.ncomp) {
+        const cudaError_t e = cudaStreamWaitEvent(s, st.mag_done, 0);
+        if (e != cudaSuccess) return e;
+        if (nfix > 0) adj_face_fix_kernel<<<(nfix + 255) / 256, 256, 0, s>>>(L, A, slot, (int)(n & 1));
+    }
+    st.pending = n;
     return cudaGetLastError();
 }
 
-// The magnetic faces' pending correction of the last reverse step.
-cudaError_t adj_finish(const LaunchSet &L, const AdjSet &A, cudaStream_t s)
+// The H-curl sweep of the last reverse step, then the magnetic faces' C_E w
+// and pending correction.
+cudaError_t adj_finish(const LaunchSet &L, const AdjSet &A, cudaStream_t s, AdjStreams &st)
 {
-    if (L.ncomp) adj_fix_kernel<<<L.ncomp, 256, 0, s>>>(L, A);
+    const dim3 blk(32, 8), grid((A.nx + 31) / 32, (A.ny + 7) / 8, A.nz);
+    int par = 0;
+    if (st.pending >= 0) {
+        par = (int)(st.pending & 1);
+        adj_curl_e_kernel<<<grid, blk, 0, s>>>(L, A, par);
+    }
+    st.pending = -1;
+    if (L.ncomp) adj_fix_kernel<<<L.ncomp, 256, 0, s>>>(L, A, par);
     return cudaGetLastError();
 }
 

@@ -2498,7 +2498,8 @@ extern "C" int fdtd_llg_adjoint_step(fdtd_llg_t h, const double *dJ_dE, double *
     };
     AdjSet A{};
     A.lamE = (float *)alloc(3 * nf * 4);
-    A.lamEn = (float *)alloc(3 * nf * 4);
+    A.lamEn[0] = (float *)alloc(3 * nf * 4);
+    A.lamEn[1] = (float *)alloc(3 * nf * 4);
     A.lamH = (float *)alloc(6 * nf * 4);
     A.lamW = (float *)alloc(I.n_wall() * 4);
     const int nc = (int)I.comps.size();
@@ -2617,10 +2618,11 @@ extern "C" int fdtd_llg_adjoint_step(fdtd_llg_t h, const double *dJ_dE, double *
         A.dtape = S->dtape;
         A.geps = (double *)alloc(3 * nbe * sizeof(double));
     }
-    bool ok = A.lamE && A.lamEn && A.lamH && A.lamW && A.ws && d_wsoff && A.gh0 && d_seed &&
+    bool ok = A.lamE && A.lamEn[0] && A.lamEn[1] && A.lamH && A.lamW && A.ws && d_wsoff && A.gh0 && d_seed &&
               (!nbe || (A.dtape && A.geps)) && (!nc || S->tape);
     if (!ok) { cleanup(); return fail(h, FDTD_E_OOM, "adjoint buffers: device allocation failed"); }
     cudaError_t e = cudaMemsetAsync(A.lamE, 0, 3 * nf * 4, S->stream);
+    for (int q = 0; q < 2 && e == cudaSuccess; ++q) e = cudaMemsetAsync(A.lamEn[q], 0, 3 * nf * 4, S->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(A.lamH, 0, 6 * nf * 4, S->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(A.lamW, 0, I.n_wall() * 4, S->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(A.ws, 0, std::max<long long>(ws_tot, 1) * 4, S->stream);
@@ -2635,12 +2637,36 @@ extern "C" int fdtd_llg_adjoint_step(fdtd_llg_t h, const double *dJ_dE, double *
     LaunchSet L = launch_set(S);
     L.rec = 1;
     A.cs = std::max(1, L.mag_cs);   // the reverse magnet kernel splits regions as the forward one does
+    // the second stream of the reverse steps and its two events (released,
+    // after both streams drain, when this call returns)
+    AdjStreams ast{};
+    ast.pending = -1;
+    struct StreamsGuard {
+        AdjStreams &st;
+        ~StreamsGuard()
+        {
+            if (st.b) cudaStreamSynchronize(st.b);
+            if (st.a_ready) cudaEventDestroy(st.a_ready);
+            if (st.mag_done) cudaEventDestroy(st.mag_done);
+            if (st.b) cudaStreamDestroy(st.b);
+        }
+    } ast_guard{ast};
+    {
+        // the highest priority: the magnet kernel's cluster takes SMs before
+        // the blocks of the sweeps launched beside it
+        int lo = 0, hi = 0;
+        e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ast.b, cudaStreamNonBlocking, hi);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ast.a_ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ast.mag_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) { cleanup(); return fail(h, FDTD_E_CUDA, std::string("adjoint setup: ") + cudaGetErrorString(e)); }
     const long long tail = S->tail, tail0 = S->tail0, base = tail + 1;
     for (long long seg = nck - 1; seg >= 0 && e == cudaSuccess; --seg) {
         const long long na = seg * K, nb = std::min(N, na + K);
         if (na >= tail0) {   // recorded during the run: tape slot n - tail0
             for (long long n = nb - 1; n >= na && e == cudaSuccess; --n)
-                e = adj_reverse_step(L, A, n, (int)(n - tail0), S->stream);
+                e = adj_reverse_step(L, A, n, (int)(n - tail0), S->stream, ast);
             continue;
         }
         // recompute the segment from its checkpoint into slots base + (n - na)
@@ -2659,16 +2685,18 @@ extern "C" int fdtd_llg_adjoint_step(fdtd_llg_t h, const double *dJ_dE, double *
         }
         if (e == cudaSuccess) e = launch_energy_flush(L, nullptr, 0, 0, S->stream);
         for (long long n = nb - 1; n >= na && e == cudaSuccess; --n)
-            e = adj_reverse_step(L, A, n, (int)(base + n - na), S->stream);
+            e = adj_reverse_step(L, A, n, (int)(base + n - na), S->stream, ast);
         S->host_step = nb;
     }
-    if (e == cudaSuccess) e = adj_finish(L, A, S->stream);
+    if (e == cudaSuccess) e = adj_finish(L, A, S->stream, ast);
     if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ast.b);
     std::vector<double> gh(ngh, 0.0), ge(3 * nbe, 0.0);
     if (e == cudaSuccess) e = cudaMemcpy(gh.data(), A.gh0, gh.size() * sizeof(double), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && nbe) e = cudaMemcpy(ge.data(), A.geps, ge.size() * sizeof(double), cudaMemcpyDeviceToHost);
     StepCtl st{};
     if (e == cudaSuccess) e = cudaMemcpy(&st, S->d_ctl, sizeof st, cudaMemcpyDeviceToHost);
+    cudaStreamSynchronize(ast.b);   // on every path: no magnet kernel still reads the buffers freed next
     cleanup();
     if (e != cudaSuccess) return fail(h, FDTD_E_CUDA, std::string("adjoint: ") + cudaGetErrorString(e));
     if (st.status & ST_UNSTABLE) return fail(h, FDTD_E_UNSTABLE, "adjoint recomputation: energy not finite");

@@ -341,7 +341,7 @@ int step_blocks_per_sm(bool cls16, bool stab, int sx);
 // Device pointers of one reverse sweep (adjoint.cu), single instance.
 struct AdjSet {
     float *lamE;            // adjoint of E^{n+1} (3 field arrays, fstride apart), then of E^n
-    float *lamEn;           // lambda_E' = lambda_E - (dt/mu0) C_H lambda_H (3 arrays)
+    float *lamEn[2];        // w = cb lambda_E' (3 arrays) of the reverse steps of each parity
     float *lamH;            // adjoint of H (3 field arrays)
     float *lamW;            // adjoint of the far-wall normal H (walls layout)
     float *ws;              // per-region workspace (ws_off[region] floats in)
@@ -377,8 +377,17 @@ long long adj_dq_index(int bx, int by, int bz, int f);
 // stream-ordered write of the device step counter (and clear of the CTA count)
 cudaError_t set_device_step(StepCtl *ctl, long long n, cudaStream_t s);
 cudaError_t adj_record_design(const LaunchSet &L, const AdjSet &A, int slot, int buf, cudaStream_t s);
-cudaError_t adj_reverse_step(const LaunchSet &L, const AdjSet &A, long long n, int slot, cudaStream_t s);
-cudaError_t adj_finish(const LaunchSet &L, const AdjSet &A, cudaStream_t s);
+// The second stream of a reverse sweep: the magnet kernel of step n runs on
+// b, beside the H-curl sweep of step n+1 (deferred: pending) and the E-curl
+// sweep of step n on the handle's stream.
+struct AdjStreams {
+    cudaStream_t b;
+    cudaEvent_t a_ready, mag_done;
+    long long pending;      // the step whose H-curl sweep is still to launch, or -1
+};
+cudaError_t adj_reverse_step(const LaunchSet &L, const AdjSet &A, long long n, int slot, cudaStream_t s,
+                             AdjStreams &st);
+cudaError_t adj_finish(const LaunchSet &L, const AdjSet &A, cudaStream_t s, AdjStreams &st);
 
 // fdtd_llg_last_error(NULL) message for entry points without a handle.
 void set_last_error(const char *msg);
