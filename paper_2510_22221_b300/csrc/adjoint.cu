@@ -370,6 +370,134 @@ __device__ void rev_half(const MagComp &C, const BoxDiv &BD, const FaceNb *fnb, 
     }
 }
 
+// rev_half when the region has no more cells than the cluster has threads:
+// thread tid owns cell v = tid (if v < V), whose face-derived inputs (mean H^s
+// and mean H^s - C), start-of-step m and own accumulators (adjoints of m, of
+// dl, of hs, the sum of the h adjoints) stay in registers through the
+// iterates, and whose tape values D^{r-1} for the next iterate are fetched
+// while the present one computes.  Only lamHg (read by the neighbours) and,
+// at the end, lamA, lamHsm and lamM go through the workspace.  The same
+// float operations in the same order as rev_half: the same bits.
+__device__ void rev_half_1(const MagComp &C, const BoxDiv &BD, const FaceNb *fnb, const Inst *I, const float *R9,
+                           const uint8_t *smat, int V, int nf, int R, const float *Hs, const float *Cc, const float *m,
+                           const float *D, RegionWS &W, const float *lamHout, float *lamHin, float *lamC, double *gh0,
+                           int nfx, int nfy, int cs)
+{
+    const int tid = threadIdx.x + (cs > 1 ? (int)cg::this_cluster().block_rank() : 0) * blockDim.x;
+    const int nth = blockDim.x * cs;
+    const int bx = C.bx, by = C.by, bxy = bx * by;
+    const int v = tid;
+    const bool in = v < V, has = in && smat[v] != 0xFF;
+    const int mt = in ? smat[v] : 0xFF;
+    int li = 0, lj = 0, lk = 0;
+    if (in) cell_decode(v, BD, li, lj, lk);
+    const int st[3] = {1, bx, bxy};
+    const bool lo[3] = {li > 0, lj > 0, lk > 0}, hi[3] = {li < bx - 1, lj < by - 1, lk < C.bz - 1};
+    bool ml[3], mh[3];   // magnetic neighbours below and above
+    for (int a = 0; a < 3; ++a) {
+        ml[a] = in && lo[a] && smat[v - st[a]] != 0xFF;
+        mh[a] = in && hi[a] && smat[v + st[a]] != 0xFF;
+    }
+    float Hm[3] = {0.f, 0.f, 0.f}, A0[3] = {0.f, 0.f, 0.f}, mm[3] = {0.f, 0.f, 0.f};
+    float lM[3] = {0.f, 0.f, 0.f}, lDl[3] = {0.f, 0.f, 0.f};
+    if (has) {
+        const int fx0 = (lk * by + lj) * (bx + 1) + li, fy0 = nfx + (lk * (by + 1) + lj) * bx + li,
+                  fz0 = nfx + nfy + (lk * by + lj) * bx + li;
+        const int f0[3] = {fx0, fy0, fz0}, f1[3] = {fx0 + 1, fy0 + bx, fz0 + bxy};
+        for (int a = 0; a < 3; ++a) {
+            Hm[a] = 0.5f * (Hs[f0[a]] + Hs[f1[a]]);
+            A0[a] = 0.5f * ((Hs[f0[a]] - Cc[f0[a]]) + (Hs[f1[a]] - Cc[f1[a]]));
+            mm[a] = m[a * V + v];
+            lM[a] = W.lamM[a * V + v];
+        }
+        // direct terms of H_out = H* - P D^R, H* = Hs - C: the adjoint of dl^R
+        const float lD[3] = {-0.5f * (lamHout[fx0] + lamHout[fx0 + 1]), -0.5f * (lamHout[fy0] + lamHout[fy0 + bx]),
+                             -0.5f * (lamHout[fz0] + lamHout[fz0 + bxy])};
+        float l[3];
+        to_fr(R9, lD, l);   // D = R^T dl, so the adjoint of dl is R times that of D
+        for (int a = 0; a < 3; ++a) lDl[a] = lM[a] + l[a];
+    }
+    // D^{r-1} at the cell and its neighbours along each axis (0 where not magnetic)
+    float dc[3], dm[3], dp[3];
+    auto fetch = [&](int r) {
+        const float *Dp = D + 3 * V * (r - 2);
+        for (int a = 0; a < 3; ++a) {
+            const float dmv = lo[a] && has ? Dp[a * V + v - st[a]] : 0.f, dpv = hi[a] && has ? Dp[a * V + v + st[a]] : 0.f;
+            dc[a] = has ? Dp[a * V + v] : 0.f;
+            dm[a] = ml[a] ? dmv : 0.f;
+            dp[a] = mh[a] ? dpv : 0.f;
+        }
+    };
+    if (R >= 2) fetch(R);
+    float lsm[3] = {0.f, 0.f, 0.f}, lA[3] = {0.f, 0.f, 0.f};
+    double g = 0.0;
+    for (int r = R; r >= 1; --r) {
+        float *lamHg = W.lamHg[r & 1];
+        if (has) {
+            float A[3] = {A0[0], A0[1], A0[2]};
+            if (r >= 2)
+                for (int a = 0; a < 3; ++a) A[a] -= 0.25f * (dm[a] + 2.f * dc[a] + dp[a]);
+            if (r - 1 >= 2) fetch(r - 1);   // the next iterate's tape values, while this one computes
+            float hs[3], h[3];
+            to_fr(R9, Hm, hs);
+            to_fr(R9, A, h);
+            hs[2] += I->h0n;
+            h[2] += I->h0n;
+            // J^T lambda in one reverse pass: gin = (m, hs, h) adjoints
+            float gin[9];
+            llg_inc_vjp(mm, hs, h, I->mm[mt], lDl, gin, gin + 3, gin + 6);
+            for (int a = 0; a < 3; ++a) {
+                lM[a] = lM[a] + gin[a];
+                lsm[a] += gin[3 + a];   // bias frame
+            }
+            if (r == 1) {   // the last iterate: hs's adjoint to global axes
+                float gq[3];
+                from_fr(R9, lsm, gq);
+                for (int a = 0; a < 3; ++a) lsm[a] = gq[a];
+            }
+            g += (double)gin[5] + (double)gin[8];     // |H_bias| enters hs and h on e3
+            float lh[3] = {gin[6], gin[7], gin[8]}, lg[3];
+            from_fr(R9, lh, lg);
+            for (int a = 0; a < 3; ++a) {
+                lamHg[a * V + v] = lg[a];
+                lA[a] = lA[a] + lg[a];
+            }
+        } else if (in) {
+            lamHg[v] = lamHg[V + v] = lamHg[2 * V + v] = 0.f;
+        }
+        if (r == 1 && in)   // what the face loop reads of the neighbours, and m's adjoint
+            for (int a = 0; a < 3; ++a) {
+                W.lamA[a * V + v] = lA[a];
+                W.lamHsm[a * V + v] = lsm[a];
+                W.lamM[a * V + v] = lM[a];
+            }
+        region_sync(cs);
+        if (r >= 2) {
+            // h depends on D^{r-1} through -1/4 (D_{v-1} + 2 D_v + D_{v+1}) per component
+            if (has) {
+                float lD[3];
+                for (int a = 0; a < 3; ++a) {
+                    const float gm = lo[a] ? lamHg[a * V + v - st[a]] : 0.f;
+                    const float gp = hi[a] ? lamHg[a * V + v + st[a]] : 0.f;
+                    lD[a] = -0.25f * (gm + 2.f * lamHg[a * V + v] + gp);
+                }
+                to_fr(R9, lD, lDl);
+            }
+        }
+    }
+    *gh0 += g;
+    // faces: A = mean(Hs - C), hs = R mean(Hs) + bias
+    for (int f = tid; f < nf; f += nth) {
+        const FaceNb q = fnb[f];
+        const int a = face_axis(f, nfx, nfy);
+        float sA = 0.f, sH = 0.f;
+        if (q.vl >= 0) { sA += 0.5f * W.lamA[a * V + q.vl]; sH += 0.5f * W.lamHsm[a * V + q.vl]; }
+        if (q.vr >= 0) { sA += 0.5f * W.lamA[a * V + q.vr]; sH += 0.5f * W.lamHsm[a * V + q.vr]; }
+        lamHin[f] = lamHout[f] + (sA + sH);
+        lamC[f] = -lamHout[f] - sA;
+    }
+}
+
 __global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSet A, int slot, int wpar)
 {
     extern __shared__ FaceNb fnb[];   // nf entries (every CTA of a region holds the whole table), then V material ids
@@ -436,13 +564,16 @@ __global__ void __launch_bounds__(kMagThreads) adj_mag_kernel(LaunchSet L, AdjSe
     region_sync(cs);
     // reverse: second half-push, then the first
     double g = 0.0;
-    rev_half(C, BD, fnb, I, R9, smat, V, nf, R, Hs2, W.C, m2, D2, W, W.lamHout, W.lamHin, W.lamC, &g, nfx, nfy, cs);
+    const bool one = V <= nth;   // one cell per thread: rev_half_1
+    if (one) rev_half_1(C, BD, fnb, I, R9, smat, V, nf, R, Hs2, W.C, m2, D2, W, W.lamHout, W.lamHin, W.lamC, &g, nfx, nfy, cs);
+    else rev_half(C, BD, fnb, I, R9, smat, V, nf, R, Hs2, W.C, m2, D2, W, W.lamHout, W.lamHin, W.lamC, &g, nfx, nfy, cs);
     for (int f = tid; f < nf; f += nth) {   // the faces rev_half gave this thread
         W.lamHout[f] = W.lamHin[f];      // adjoint of H^{n+1}
         W.fix[f] = W.lamC[f];            // curl adjoint of the second half-push
     }
     region_sync(cs);
-    rev_half(C, BD, fnb, I, R9, smat, V, nf, R, Hs1, W.C, m1, D1, W, W.lamHout, W.lamHin, W.lamC, &g, nfx, nfy, cs);
+    if (one) rev_half_1(C, BD, fnb, I, R9, smat, V, nf, R, Hs1, W.C, m1, D1, W, W.lamHout, W.lamHin, W.lamC, &g, nfx, nfy, cs);
+    else rev_half(C, BD, fnb, I, R9, smat, V, nf, R, Hs1, W.C, m1, D1, W, W.lamHout, W.lamHin, W.lamC, &g, nfx, nfy, cs);
     // write back: for a magnetic face the curl sweep must see q/2 with
     // q = -(lamC1 + lamC2) (a plain face contributes 2 lambda_H); afterwards
     // the face takes lamHin, restored from fix by the next reverse step's
