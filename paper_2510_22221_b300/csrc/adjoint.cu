@@ -658,7 +658,10 @@ __global__ void __launch_bounds__(256) adj_curl_h_kernel(LaunchSet L, AdjSet A, 
     float hzj = j > 0 ? lz[o - px] : 0.f, hxj = j > 0 ? lx[o - px] : 0.f;
     float hyk = k > 0 ? ly[o - plane] : 0.f, hxk = k > 0 ? lx[o - plane] : 0.f;
     float hzi = i > 0 ? lz[o - 1] : 0.f, hyi = i > 0 ? ly[o - 1] : 0.f;
-    if (L.ncomp) {
+    // (only cells in the box of the magnetic faces, or one above it, read a
+    // magnetic face here)
+    if (L.ncomp && i >= A.mlo[0] && j >= A.mlo[1] && k >= A.mlo[2] && i <= A.mhi[0] + 1 && j <= A.mhi[1] + 1 &&
+        k <= A.mhi[2] + 1) {
         auto flags = [&](long long oc) {
             return __float_as_uint(__ldg(I->ctab + 3 * (int)static_cast<const ClsT *>(I->cls)[oc]).w);
         };
@@ -727,8 +730,8 @@ __global__ void __launch_bounds__(256) adj_curl_e_kernel(LaunchSet L, AdjSet A, 
     const float cx = curl2a(yj ? wz_[o + px] : 0.f, wz, I->idy, zk ? wy_[o + plane] : 0.f, wy, I->idz);
     const float cy = curl2a(zk ? wx_[o + plane] : 0.f, wx, I->idz, xi ? wz_[o + 1] : 0.f, wz, I->idx);
     const float cz = curl2a(xi ? wy_[o + 1] : 0.f, wy, I->idx, yj ? wx_[o + px] : 0.f, wx, I->idy);
-    unsigned fl = 0u;   // the magnetic-face flags of cell o's class
-    if (L.ncomp) {
+    unsigned fl = 0u;   // the magnetic-face flags of cell o's class (none outside the box of those faces)
+    if (L.ncomp && i >= A.mlo[0] && j >= A.mlo[1] && k >= A.mlo[2] && i <= A.mhi[0] && j <= A.mhi[1] && k <= A.mhi[2]) {
         const int c = L.cls16 ? (int)static_cast<const uint16_t *>(I->cls)[o] : (int)static_cast<const uint8_t *>(I->cls)[o];
         fl = __float_as_uint(__ldg(I->ctab + 3 * c).w);
     }

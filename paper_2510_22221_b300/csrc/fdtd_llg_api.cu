@@ -2589,6 +2589,17 @@ extern "C" int fdtd_llg_adjoint_step(fdtd_llg_t h, const double *dJ_dE, double *
     }
     A.nmf = (int)mf_lam.size();
     A.nfe = (int)fe_off.size();
+    // the box of every magnetic face: a face of a region box lies at cell
+    // indices x0 .. x0 + bx (and so on)
+    A.mlo[0] = A.mlo[1] = A.mlo[2] = 1 << 30;
+    A.mhi[0] = A.mhi[1] = A.mhi[2] = -1;
+    for (const MagComp &C : I.comps) {
+        const int lo[3] = {C.x0, C.y0, C.z0}, hi[3] = {C.x0 + C.bx, C.y0 + C.by, C.z0 + C.bz};
+        for (int a = 0; a < 3; ++a) {
+            A.mlo[a] = std::min(A.mlo[a], lo[a]);
+            A.mhi[a] = std::max(A.mhi[a], hi[a]);
+        }
+    }
     long long *d_mf = (long long *)alloc(std::max<size_t>(1, 2 * mf_lam.size()) * sizeof(long long));
     long long *d_feo = (long long *)alloc(std::max<size_t>(1, fe_off.size() + fc_ws.size()) * sizeof(long long));
     int *d_fei = (int *)alloc((fe_comp.size() + fe_start.size()) * sizeof(int));

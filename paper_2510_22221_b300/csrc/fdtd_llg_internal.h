@@ -366,6 +366,7 @@ struct AdjSet {
     // workspace index and coefficient).  Lists in a fixed order, so the sums
     // are the same bits every run.
     int nmf, nfe;
+    int mlo[3], mhi[3];     // box of every magnetic face (cell indices, inclusive; empty when mlo > mhi)
     const long long *mf_lam, *mf_ws;
     const int *fe_comp, *fe_start;
     const long long *fe_off, *fc_ws;
