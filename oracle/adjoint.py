@@ -262,4 +262,7 @@ def gradients(model: TorchStep, nsteps: int, eps_design, h0: float, n0: int, seg
     h = torch.tensor(float(h0), dtype=torch.float64, requires_grad=True)
     J = run(model, nsteps, e, h, n0=n0, segment=segment)
     J.backward()
-    return float(J.detach()), e.grad.numpy().copy(), float(h.grad)
+    # without a magnetic cell |H_bias| enters no operation (it acts only
+    # through H_eff in the LLG update of magnetic cells): its derivative is 0
+    gh = 0.0 if h.grad is None else float(h.grad)
+    return float(J.detach()), e.grad.numpy().copy(), gh
