@@ -59,19 +59,46 @@ def film_field(w: float, d1: float, d2: float, d3: float, eps_m: float, eps_c: f
     and B sin(k_c (d3 - z)) above it (PMC walls), film H = C e^{i k_m z} +
     D e^{-i k_m z} - M; H and (sigma - i eps w)^-1 dH/dz continuous at d1 and
     d2.  Returns (A, B, C, D, mean film H)."""
-    km, kc = wavenumber(w, eps_m, sigma_m), wavenumber(w, eps_c, sigma_c)
-    ym, yc = sigma_m - 1j * EPS0 * eps_m * w, sigma_c - 1j * EPS0 * eps_c * w
+    return layered_field(w, d1, d2, d3, eps_m, eps_c, sigma_m, sigma_c, M)[:5]
+
+
+def layered_field(w: float, d1: float, d2: float, L: float, eps_m: float, eps_c: float, sigma_m: float,
+                  sigma_c: float, M: float = 1.0, kt: float = 0.0, walls: str = "pmc"):
+    """Eqs. S7-S9 for a film [d1, d2] in a cavity [0, L], in the two forms a
+    closed cavity allows.  The fields are those of Eq. S7 times a fixed
+    transverse profile of wavenumber kt (a guided mode: for kt = 0 the
+    supplement's plane fields), so that in each layer
+        H'' + kappa^2 H = -kappa^2 M,   kappa^2 = k^2 - kt^2,
+    and the tangential E continuous at an interface is (iw mu0 / kappa^2) H'
+    (at kt = 0 the supplement's (sigma - i eps w)^-1 H').  walls = "pmc": H =
+    0 at 0 and L, the supplement's cavity; walls = "pec": tangential E = 0,
+    so H' = 0, and the cavity field is A cos(kappa z) below the film and
+    B cos(kappa (L - z)) above it.  Returns (A, B, C, D, mean film H,
+    determinant of the 4 x 4 system); the determinant vanishes at the
+    cavity's resonances with M = 0."""
+    if walls not in ("pmc", "pec"):
+        raise ValueError("walls: 'pmc' or 'pec'")
+    km = np.sqrt(wavenumber(w, eps_m, sigma_m) ** 2 - kt * kt)
+    kc = np.sqrt(wavenumber(w, eps_c, sigma_c) ** 2 - kt * kt)
+    # the interface weight kappa^2 / (i w mu0): H' / weight is continuous
+    ym, yc = km * km / (1j * w * MU0), kc * kc / (1j * w * MU0)
     e = np.exp
+    if walls == "pmc":
+        lo, dlo = np.sin(kc * d1), kc * np.cos(kc * d1)                    # A sin(kc z) and its slope at d1
+        hi, dhi = np.sin(kc * (L - d2)), -kc * np.cos(kc * (L - d2))      # B sin(kc (L - z)) at d2
+    else:
+        lo, dlo = np.cos(kc * d1), -kc * np.sin(kc * d1)
+        hi, dhi = np.cos(kc * (L - d2)), kc * np.sin(kc * (L - d2))
     A = np.array([
-        [np.sin(kc * d1), 0, -e(1j * km * d1), -e(-1j * km * d1)],
-        [0, np.sin(kc * (d3 - d2)), -e(1j * km * d2), -e(-1j * km * d2)],
-        [kc * np.cos(kc * d1) / yc, 0, -1j * km * e(1j * km * d1) / ym, 1j * km * e(-1j * km * d1) / ym],
-        [0, -kc * np.cos(kc * (d3 - d2)) / yc, -1j * km * e(1j * km * d2) / ym, 1j * km * e(-1j * km * d2) / ym],
+        [lo, 0, -e(1j * km * d1), -e(-1j * km * d1)],
+        [0, hi, -e(1j * km * d2), -e(-1j * km * d2)],
+        [dlo / yc, 0, -1j * km * e(1j * km * d1) / ym, 1j * km * e(-1j * km * d1) / ym],
+        [0, dhi / yc, -1j * km * e(1j * km * d2) / ym, 1j * km * e(-1j * km * d2) / ym],
     ], dtype=complex)
     rhs = np.array([-M, -M, 0, 0], dtype=complex)
     a, b, c, d = np.linalg.solve(A, rhs)
     mean = (c * (e(1j * km * d2) - e(1j * km * d1)) - d * (e(-1j * km * d2) - e(-1j * km * d1))) / (1j * km) / (d2 - d1) - M
-    return a, b, c, d, mean
+    return a, b, c, d, mean, np.linalg.det(A)
 
 
 def theta_zy(w: float, H: float, p=TABLE_S1, eps_m: float = 1.0, d1: float | None = None) -> complex:
@@ -83,19 +110,65 @@ def theta_zy(w: float, H: float, p=TABLE_S1, eps_m: float = 1.0, d1: float | Non
     return p["gamma"] * mean
 
 
-def chi(w: float, H: float, theta: complex, p=TABLE_S1) -> np.ndarray:
+def chi(w: float, H: float, theta: complex, p=TABLE_S1, demag: float = 1.0) -> np.ndarray:
     """Eq. S5b: gamma [[i w, 0, 0], [0, i w, A23], [0, A32 - theta_zy, i w]]^-1
     [[0, 0, 0], [0, 0, -1], [0, 1, 0]] with A23 = i alpha w - gamma H -
-    gamma Ms and A32 = -i alpha w + gamma H (Eq. S4a; theta_zx = theta_zz = 0)."""
+    gamma Ms and A32 = -i alpha w + gamma H (Eq. S4a; theta_zx = theta_zz = 0).
+    demag scales the film-normal Ms term of A23 (1 for the supplement's
+    continuous film)."""
     g, al, Ms = p["gamma"], p["alpha"], p["Ms"]
-    a23 = 1j * al * w - g * H - g * Ms
+    a23 = 1j * al * w - g * H - g * demag * Ms
     a32 = -1j * al * w + g * H
     L = np.array([[1j * w, 0, 0], [0, 1j * w, a23], [0, a32 - theta, 1j * w]], dtype=complex)
     R = np.array([[0, 0, 0], [0, 0, -1], [0, 1, 0]], dtype=complex)
     return g * np.linalg.solve(L, R)
 
 
-def p_abs(w: float, H: float, theta: complex, p=TABLE_S1) -> float:
+def p_abs(w: float, H: float, theta: complex, p=TABLE_S1, demag: float = 1.0) -> float:
     """Eq. S1 up to a constant: Im(h^T chi h) for the tabulated drive h."""
     h = np.asarray(p["h0"], dtype=complex)
-    return float(np.imag(h @ chi(w, H, theta, p) @ h))
+    return float(np.imag(h @ chi(w, H, theta, p, demag) @ h))
+
+
+def s3_determinant(w: complex, H: float, theta: complex, p=TABLE_S1, demag: float = 1.0) -> complex:
+    """The determinant of the y-z block of the S3 matrix of Eq. S5b, signed
+    so that it reads w^2 - (gamma (H + demag Ms) - i alpha w) (gamma H -
+    i alpha w - theta): its zeros in complex w are the poles of chi, the
+    resonances of the absorbed power (peak Re w, half-width -Im w)."""
+    g, al, Ms = p["gamma"], p["alpha"], p["Ms"]
+    a23 = 1j * al * w - g * H - g * demag * Ms
+    a32 = -1j * al * w + g * H
+    return -((1j * w) * (1j * w) - a23 * (a32 - theta))
+
+
+def _secant(f, z0: complex, z1: complex, tol: float, maxit: int) -> complex:
+    f0, f1 = f(z0), f(z1)
+    for _ in range(maxit):
+        z2 = z1 - f1 * (z1 - z0) / (f1 - f0)
+        if abs(z2 - z1) <= tol * abs(z2):
+            return z2
+        z0, f0, z1, f1 = z1, f1, z2, f(z2)
+    raise RuntimeError("secant iteration did not converge")
+
+
+def cavity_poles(H: float, d1: float, d2: float, L: float, guesses, p=TABLE_S1, eps_m: float = 1.0,
+                 kt: float = 0.0, walls: str = "pmc", demag: float = 1.0, tol: float = 1e-14):
+    """The poles of chi with the film's own cavity field as the coupling:
+    theta_zy(w) = gamma <H_y>(w) per unit m_y from layered_field (M = Ms),
+    inserted in Eq. S5b.  theta has poles at the bare cavity resonances, so
+    the zeros are sought of s3_determinant times the 4 x 4 determinant
+    (analytic in w), by secant steps from each guess (angular frequencies),
+    each later zero with the earlier ones divided out.  Time factor
+    exp(-i w t): a resonance decays as exp(Im w t).  Returned sorted by
+    Re w."""
+    def g(w):
+        *_, mean, det = layered_field(w, d1, d2, L, eps_m, p["eps_c"], p["sigma_m"], p["sigma_c"], M=p["Ms"],
+                                      kt=kt, walls=walls)
+        return s3_determinant(w, H, p["gamma"] * mean, p, demag) * det
+
+    roots = []
+    for w0 in guesses:
+        def f(w, r=tuple(roots)):
+            return g(w) / np.prod([w - x for x in r]) if r else g(w)
+        roots.append(_secant(f, complex(w0), complex(w0) * (1 + 1e-6), tol, 200))
+    return np.array(sorted(roots, key=lambda z: z.real))

@@ -77,3 +77,96 @@ def test_coupling_shifts_the_resonance_as_the_linearised_llg_says():
     w = np.linspace(0.97, 1.01, 8001) * W_M
     pa = np.array([abs(S.p_abs(x, H, theta, p0)) for x in w])
     assert w[np.argmax(pa)] == pytest.approx(w_c, rel=2e-5)
+
+
+def _fv_mean_field(w, d1, d2, L, eps_m, eps_c, sig_m, sig_c, kt, walls, n):
+    """Brute force for the pins below: the 1-D boundary-value problem
+    (H' / y)' + i w mu0 (H + M 1_film) = 0, y = kappa^2 / (i w mu0) per
+    layer (the in-plane Faraday and Ampere laws of a field with transverse
+    wavenumber kt), by finite volumes on n cells with the interfaces on cell
+    faces, H' / y continuous through them; the mean H over the film cells
+    for M = 1."""
+    from scipy.linalg import solve_banded
+
+    h = L / n
+    x = (np.arange(n) + 0.5) * h
+    film = (x > d1) & (x < d2)
+    k2 = np.where(film, S.EPS0 * eps_m * S.MU0 * w * w + 1j * sig_m * S.MU0 * w,
+                  S.EPS0 * eps_c * S.MU0 * w * w + 1j * sig_c * S.MU0 * w)
+    y = (k2 - kt * kt) / (1j * w * S.MU0)
+    a = 2.0 / (h * h * (y[:-1] + y[1:]))            # coupling through the face between cells i and i+1
+    diag = np.full(n, 1j * w * S.MU0, dtype=complex)
+    diag[:-1] -= a
+    diag[1:] -= a
+    if walls == "pmc":                               # H = 0 on the wall, half a cell from the first centre
+        diag[0] -= 2.0 / (h * h * y[0])
+        diag[-1] -= 2.0 / (h * h * y[-1])
+    ab = np.zeros((3, n), dtype=complex)
+    ab[0, 1:], ab[1], ab[2, :-1] = a, diag, a
+    H = solve_banded((1, 1), ab, -1j * w * S.MU0 * film.astype(complex))
+    return H[film].mean()
+
+
+@pytest.mark.parametrize("walls", ["pec", "pmc"])
+@pytest.mark.parametrize("kt", [0.0, 150.0])
+def test_layered_field_equals_a_finite_volume_solve(walls, kt):
+    """The cavity solve generalised to PEC walls and a guided mode (kt) equals
+    a finite-volume solve of the same 1-D problem: a 0.5 mm film of
+    eps_r 7.1 and sigma 0.05 S/m at 2-2.5 mm in a 1 cm cavity at 10 GHz, so
+    that the walls, the film's own wavenumber, the interface weights and kt
+    all change the answer at O(1); 40 000 cells (second order: ~1e-7)."""
+    w, L, d1, d2 = 2 * np.pi * 10e9, 1e-2, 2e-3, 2.5e-3
+    *_, mean, _ = S.layered_field(w, d1, d2, L, 7.1, 1.0, 0.05, 1e-3, M=1.0, kt=kt, walls=walls)
+    ref = _fv_mean_field(w, d1, d2, L, 7.1, 1.0, 0.05, 1e-3, kt, walls, 40000)
+    assert abs(mean - ref) < 1e-5 * abs(ref)
+    # the other wall type, or kt dropped, is far off
+    other = S.layered_field(w, d1, d2, L, 7.1, 1.0, 0.05, 1e-3, kt=kt, walls="pmc" if walls == "pec" else "pec")[4]
+    assert abs(other - ref) > 0.05 * abs(ref)
+    if kt:
+        assert abs(S.layered_field(w, d1, d2, L, 7.1, 1.0, 0.05, 1e-3, walls=walls)[4] - ref) > 0.05 * abs(ref)
+
+
+def test_cavity_poles_without_coupling_are_the_bare_resonances():
+    """With a vanishing film (Ms -> 1 A/m, so theta ~ 1e-6 of the scale) the
+    two poles found are the closed forms: the damped Kittel pole, the root
+    of (1 + alpha^2) w^2 + i alpha (A + B) w - A B = 0 with A = gamma (H +
+    N Ms), B = gamma H, and the lossy guided cavity mode, eps0 mu0 w^2 +
+    i sigma mu0 w = (pi / L)^2 + kt^2 (both decaying: Im w < 0)."""
+    p = dict(P, Ms=1.0)
+    H, L, kt, N = 2.0e5, 1.4112e-2, 9.8135, 0.5
+    t = 0.7e-6
+    A, B, al = p["gamma"] * (H + N * p["Ms"]), p["gamma"] * H, p["alpha"]
+    wm = (-1j * al * (A + B) + np.sqrt(-(al * (A + B)) ** 2 + 4 * (1 + al * al) * A * B)) / (2 * (1 + al * al))
+    q = (np.pi / L) ** 2 + kt * kt
+    s = p["sigma_c"] * S.MU0
+    wc = (-1j * s + np.sqrt(-s * s + 4 * S.EPS0 * S.MU0 * q)) / (2 * S.EPS0 * S.MU0)
+    r = S.cavity_poles(H, L / 8, L / 8 + t, L, [wm.real, wc.real], p, kt=kt, walls="pec", demag=N)
+    ref = np.array(sorted([wm, wc], key=lambda z: z.real))
+    assert np.all(np.abs(r - ref) < 1e-9 * np.abs(ref))
+    assert np.all(r.imag < 0)
+
+
+def test_cavity_poles_at_resonance_split_by_the_coupled_mode_estimate():
+    """Where the bare magnon and cavity frequencies meet, the two poles sit
+    about their mean, split by 2g with g^2 the product of the two
+    off-diagonal couplings of the 2 x 2 coupled-mode problem: the film's
+    field per unit m_y near the cavity pole, gamma <H_y> = R / (w - w_c),
+    and the magnon's shift by it, d w_m / d theta = -gamma (H + N Ms) /
+    (2 w_m), give (w - w_m)(w - w_c) = R d w_m / d theta = g^2, positive
+    (an anti-crossing); within 2 % (the estimate drops the damping and the
+    frequency dependence of R)."""
+    L, t, kt, N = 1.4112e-2, 0.7e-6, 9.8135, 0.5
+    d1 = L / 8
+    wc = S.C0 * np.sqrt((np.pi / L) ** 2 + kt * kt)
+    g, Ms = P["gamma"], P["Ms"]
+    H = (-N * Ms + np.sqrt((N * Ms) ** 2 + 4 * (wc / g) ** 2)) / 2     # gamma^2 H (H + N Ms) = wc^2
+    r = S.cavity_poles(H, d1, d1 + t, L, [wc * 0.99, wc * 1.01], kt=kt, walls="pec", demag=N)
+    # residue of the film's field at the cavity pole, from two points near it (lossless cavity)
+    th = lambda w: g * S.layered_field(w, d1, d1 + t, L, 1.0, 1.0, 0.0, 0.0, M=Ms, kt=kt, walls="pec")[4]
+    dw = 1e-4 * wc
+    R = 0.5 * (th(wc + dw) * dw - th(wc - dw) * dw)
+    g2 = (R * (-g * (H + N * Ms) / (2 * wc))).real
+    assert g2 > 0
+    split = r[1].real - r[0].real
+    assert split == pytest.approx(2 * np.sqrt(g2), rel=0.02)
+    assert 0.5 * (r[0].real + r[1].real) == pytest.approx(wc, rel=5e-4)
