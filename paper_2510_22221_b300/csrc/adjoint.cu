@@ -694,9 +694,9 @@ __global__ void __launch_bounds__(256) adj_curl_h_kernel(LaunchSet L, AdjSet A, 
     wn[o] = w[0];
     wn[fs + o] = w[1];
     wn[2 * fs + o] = w[2];
-    A.lamE[o] = Ca.x * ex;            // lambda_E = ca lambda_E'
-    A.lamE[fs + o] = Ca.y * ey;
-    A.lamE[2 * fs + o] = Ca.z * ez;
+    A.lamE[o] = __fmaf_rn(Ca.x, ex, ex);   // lambda_E = ca lambda_E' (the table holds ca - 1)
+    A.lamE[fs + o] = __fmaf_rn(Ca.y, ey, ey);
+    A.lamE[2 * fs + o] = __fmaf_rn(Ca.z, ez, ez);
     if (A.geps) {
         const int li = i - A.di0, lj = j - A.dj0, lk = k - A.dk0;
         if (li >= 0 && lj >= 0 && lk >= 0 && li <= A.dbx && lj <= A.dby && lk <= A.dbz) {
@@ -768,7 +768,7 @@ __global__ void __launch_bounds__(256) adj_face_fix_kernel(LaunchSet L, AdjSet A
     const float ca = comp == 0 ? Ca.x : (comp == 1 ? Ca.y : Ca.z), cb = comp == 0 ? Cb.x : (comp == 1 ? Cb.y : Cb.z);
     const float dw = cb * d;
     A.lamEn[par][comp * fs + o] += dw;
-    A.lamE[comp * fs + o] += ca * d;
+    A.lamE[comp * fs + o] += __fmaf_rn(ca, d, d);   // ca d from the table's ca - 1
     if (A.geps && dw != 0.f) {
         const long long plane = I->plane;
         const int px = I->px;

@@ -496,13 +496,19 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
         return table[mid[cid(i, j, k)]].eps_r;
     };
     const double dt = S->dt;
-    // per-cell class: (ca, cb, eps/2) of the three edges with index (i,j,k) + magnetic-face flags
+    // per-cell class: (ca - 1, cb, eps/2) of the three edges with index (i,j,k)
+    // + magnetic-face flags.  ca - 1 = -sigma / den is kept instead of ca: in
+    // FP32, ca = 1 - sigma dt / eps (~1 - 1e-7 for a weak conductor) would
+    // be rounded to a few units of the last place below 1, changing the
+    // conductive loss by up to ~10 %; ca - 1 holds it to full relative
+    // precision.  Edges held at zero (walls, PEC) have ca - 1 = -1, cb = 0.
     auto edge = [&](int comp, int i, int j, int k, float &ca, float &cb, float &he) {
         bool wall;
         if (comp == 0) wall = (j == 0 || k == 0);
         else if (comp == 1) wall = (i == 0 || k == 0);
         else wall = (i == 0 || j == 0);
-        ca = cb = he = 0.f;
+        ca = -1.f;
+        cb = he = 0.f;
         if (wall) return;
         double se = 0, ss = 0;
         bool pec = false;
@@ -520,7 +526,7 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
         if (pec) return;
         const double eps = kEps0 * se / 4, sig = ss / 4;
         const double den = eps / dt + sig / 2;
-        ca = (float)((eps / dt - sig / 2) / den);
+        ca = (float)(-sig / den);
         cb = (float)(1.0 / den);
         he = (float)(eps / 2);
     };
@@ -801,7 +807,7 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
             float flag;
             std::memcpy(&flag, &w[9], 4);
             tab[3 * c] = make_float4(v[0], v[1], v[2], flag);
-            for (int q = 0; q < 3; ++q) ca_nonpos = ca_nonpos || (v[3 + q] != 0.f && std::fabs(v[q]) < 1e-12f);
+            for (int q = 0; q < 3; ++q) ca_nonpos = ca_nonpos || (v[3 + q] != 0.f && v[q] == -1.f);   // ca = 0
             tab[3 * c + 1] = make_float4(v[3], v[4], v[5], 0.f);
             tab[3 * c + 2] = make_float4(v[6], v[7], v[8], 0.f);
         }

@@ -222,7 +222,7 @@ struct alignas(128) Inst {
     long long fstride;                    // F[b][c] = F[b][0] + c * fstride
     float *wHx, *wHy, *wHz;               // far-wall normal H: [nz][ny], [nz][nx], [ny][nx]
     const void *cls;                      // class id per cell: uint8 or uint16
-    const float4 *ctab;                   // 3 float4 per class: (ca, flags) (cb) (eps/2)
+    const float4 *ctab;                   // 3 float4 per class: (ca - 1, flags) (cb) (eps/2)
     int nclass;                           // entries of ctab
     double *probe_buf;                    // [cap][nprobe][9]
     double *energy_buf;                   // [cap]

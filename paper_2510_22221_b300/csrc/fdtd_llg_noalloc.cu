@@ -24,12 +24,14 @@ std::mutex g_noalloc_mu;
 double *g_noalloc_ptr[kNoAllocMaxDevices] = {};
 
 // One block per 32 x 8 x kKC tile: E = ca E + cb curl H on every stored edge
-// that is not in a wall, and the block's sum of E^2 of the new field.
+// that is not in a wall, written E + ((ca - 1) E + cb curl H) from cam1 =
+// ca - 1 (exact to FP32's relative precision where ca itself would be
+// rounded next to 1), and the block's sum of E^2 of the new field.
 __global__ void __launch_bounds__(kTX *kTY) noalloc_e_push_kernel(float *__restrict__ Ex, float *__restrict__ Ey,
                                                                   float *__restrict__ Ez, const float *__restrict__ Hx,
                                                                   const float *__restrict__ Hy, const float *__restrict__ Hz,
                                                                   int nx, int ny, int nz, float idx, float idy, float idz,
-                                                                  float ca, float cb, double *__restrict__ part)
+                                                                  float cam1, float cb, double *__restrict__ part)
 {
     __shared__ double sred[kTX * kTY / 32];
     const int ntx = (nx + kTX - 1) / kTX, nty = (ny + kTY - 1) / kTY;
@@ -53,9 +55,9 @@ __global__ void __launch_bounds__(kTX *kTY) noalloc_e_push_kernel(float *__restr
             const float cy = (hx - hx_km) * idz - (hz - hz_im) * idx;
             const float cz = (hy - hy_im) * idx - (hx - hx_jm) * idy;
             // edges lying in a wall stay at zero
-            const float ex = (j > 0 && k > 0) ? ca * Ex[o] + cb * cx : 0.f;
-            const float ey = (i > 0 && k > 0) ? ca * Ey[o] + cb * cy : 0.f;
-            const float ez = (i > 0 && j > 0) ? ca * Ez[o] + cb * cz : 0.f;
+            const float ex = (j > 0 && k > 0) ? Ex[o] + (cam1 * Ex[o] + cb * cx) : 0.f;
+            const float ey = (i > 0 && k > 0) ? Ey[o] + (cam1 * Ey[o] + cb * cy) : 0.f;
+            const float ez = (i > 0 && j > 0) ? Ez[o] + (cam1 * Ez[o] + cb * cz) : 0.f;
             Ex[o] = ex;
             Ey[o] = ey;
             Ez[o] = ez;
@@ -145,10 +147,10 @@ extern "C" int fdtd_llg_e_push_noalloc(float *Ex, float *Ey, float *Ez, const fl
     const double eps = kEps0 * eps_r;
     const double den = eps / dt + sigma / 2;
     const float cb = (float)(1.0 / den);
-    const float ca = (float)((eps / dt - sigma / 2) / den);
+    const float cam1 = (float)(-sigma / den);   // ca - 1
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     noalloc_e_push_kernel<<<(unsigned)nb, dim3(kTX, kTY), 0, s>>>(Ex, Ey, Ez, Hx, Hy, Hz, nx, ny, nz, (float)(1.0 / dx),
-                                                                 (float)(1.0 / dy), (float)(1.0 / dz), ca, cb, scratch);
+                                                                 (float)(1.0 / dy), (float)(1.0 / dz), cam1, cb, scratch);
     if (cudaGetLastError() != cudaSuccess) return noalloc_fail(FDTD_E_CUDA, "E push kernel launch failed");
     if (w_e) {
         noalloc_energy_kernel<<<1, 256, 0, s>>>(scratch, (int)nb, 0.5 * eps * dx * dy * dz, w_e);

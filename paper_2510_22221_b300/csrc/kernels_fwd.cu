@@ -211,10 +211,12 @@ __device__ __forceinline__ float curl2(float a1, float b1, float i1, float a2, f
 {
     return __fmaf_rn(__fsub_rn(a1, b1), i1, -__fmul_rn(__fsub_rn(a2, b2), i2));
 }
-// ca E^n + cb (curl H - J)
-__device__ __forceinline__ float e_next(float ca, float e, float cb, float c)
+// ca E^n + cb (curl H - J), as E^n + ((ca - 1) E^n + cb (curl H - J)) from
+// the class table's ca - 1 (cam1), which FP32 holds to full relative
+// precision where ca itself would be rounded next to 1
+__device__ __forceinline__ float e_next(float cam1, float e, float cb, float c)
 {
-    return __fmaf_rn(ca, e, __fmul_rn(cb, c));
+    return __fadd_rn(e, __fmaf_rn(cam1, e, __fmul_rn(cb, c)));
 }
 
 // ------------------------------------------------------------ magnet pass

@@ -82,9 +82,10 @@ __global__ void __launch_bounds__(kPT) pml_axis_kernel(const PmlLaunch P, int sr
         T[B * fs + off] = fmaf(-P.dtmu, corb, tb);
         T[CC * fs + off] = fmaf(-P.dtmu, corc, tc);
     } else {
+        // the class table holds ca - 1
         const float4 A = __ldg(P.ctab + 3 * cl), C = __ldg(P.ctab + 3 * cl + 1);
-        const float cab = B == 0 ? A.x : (B == 1 ? A.y : A.z), cbb = B == 0 ? C.x : (B == 1 ? C.y : C.z);
-        const float cac = CC == 0 ? A.x : (CC == 1 ? A.y : A.z), cbc = CC == 0 ? C.x : (CC == 1 ? C.y : C.z);
+        const float cab = 1.f + (B == 0 ? A.x : (B == 1 ? A.y : A.z)), cbb = B == 0 ? C.x : (B == 1 ? C.y : C.z);
+        const float cac = 1.f + (CC == 0 ? A.x : (CC == 1 ? A.y : A.z)), cbc = CC == 0 ? C.x : (CC == 1 ? C.y : C.z);
         if (cbb != 0.f) T[B * fs + off] = fmaf(cbb * __frcp_rn(cab), corb, tb);
         if (cbc != 0.f) T[CC * fs + off] = fmaf(cbc * __frcp_rn(cac), corc, tc);
     }

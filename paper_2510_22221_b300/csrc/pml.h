@@ -53,7 +53,7 @@ struct PmlLaunch {
     float id[3];                // 1/dx, 1/dy, 1/dz
     float dtmu;                 // dt / mu0
     const void *cls;            // class ids, [nz][ny][px]
-    const float4 *ctab;         // (ca, flags) (cb) (eps/2) per class
+    const float4 *ctab;         // (ca - 1, flags) (cb) (eps/2) per class
 };
 
 // Index of cell (i, j, k) in a psi array of axis a (side s, layer t).

@@ -175,6 +175,35 @@ def anticrossing_sweep(n_inst=5, b_lo=0.0375, b_hi=0.06, steps=16000, nx=24, ny=
     return out
 
 
+def quasi1d_film(h_oe=(1700.0, 1800.0, 1900.0), nx=20160, ny=32, thickness=0.7e-6, width=0.32,
+                 steps=680000) -> list:
+    """The supplement's film in a closed cavity that keeps its fields 1-D
+    (Supplementary Information, Table S1 materials; one instance per bias
+    field h_oe, in oersted).  A parallel-plate resonator: nx cells of the
+    film's thickness along x (1.41 cm, PEC ends), ny cells across y (width
+    0.32 m between PEC walls, so that the field's transverse sine varies
+    ~10^4 times more slowly than the film is thick), one cell along z;
+    its fundamental mode (E along z, H in the x-y plane) lies near
+    10.63 GHz.  A film one cell thick spans the cross-section at
+    i = nx // 8 (Ms 9.7e5 A/m, gamma' = mu0 gamma = 2.23e5, alpha 0.003,
+    eps_r 1, sigma 1e-3 S/m); the cavity is vacuum with sigma 1e-3 S/m.
+    Bias along z (in the film's plane); the film's uniform precession
+    crosses the cavity mode near 1800 Oe.  No source: the run starts from
+    a tilted film.  Probe at the film's centre cell."""
+    oe = 1e3 / (4 * np.pi)
+    dy = width / ny
+    i_f = nx // 8
+    out = []
+    for h in h_oe:
+        mats = [material(sigma=1e-3), material(eps_r=1.0, sigma=1e-3, Ms=9.7e5, alpha=0.003, gamma=2.23e5 / MU0)]
+        mid = np.zeros((1, ny, nx), dtype=np.uint8)
+        mid[0, :, i_f] = 1
+        out.append(Workload(f"quasi1d_{h:.0f}oe", nx, ny, 1, thickness, dy, dy, 0.95, steps, mats, mid,
+                            np.array([0.0, 0.0, h * oe]), [], [(i_f, ny // 2, 0)],
+                            note=f"quasi-1-D resonator {nx}x{ny}x1, film at i = {i_f}, bias {h:.0f} Oe along z"))
+    return out
+
+
 def adjoint_design(nx=128, ny=128, nz=64, steps=4000, seed=2, design=(32, 32, 4), block=(16, 16, 4)) -> Workload:
     """dx = 0.5 um PEC box, vacuum; design region design = (x, y, z) cells with
     eps_r ~ U[1, 12] (seed) between the source and the probe; a YIG block of
