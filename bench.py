@@ -786,7 +786,11 @@ def main():
     # then every step a step call whose probe rows and energy stream into
     # pinned host rings (written by the kernel that ends each call, no
     # per-step wait); the timed region ends when the last step's results are
-    # on the host
+    # on the host.  The timed run's handle is released first, as between two
+    # runs of a user's sweep, so that the new handle's device memory comes
+    # from torch's caching allocator as in such a sweep's later runs
+    tile_width = sim.get_tile_width()
+    sim.destroy()
     ke = K
     mat_pinned = torch.from_numpy(np.ascontiguousarray(w.mat_id).reshape(-1)).pin_memory()
     rows_h = torch.empty((ke, len(w.probes), 9), dtype=torch.float64).pin_memory()
@@ -796,7 +800,7 @@ def main():
     sim2 = pkg.FdtdLlg.create(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, courant_factor=w.courant, probe_capacity=ke + 8)
     sim2.set_materials(mat_pinned, [pkg.Material(**m) for m in w.materials], w.hbias)
     sim2.set_tiling(tiling["planes_per_task"])      # the tiling tuned above, reused as a user would
-    sim2.set_tile_width(sim.get_tile_width())
+    sim2.set_tile_width(tile_width)
     for s in w.sources:
         sim2.set_source(s["comp"], s["i"], s["j"], s["k"], s["J0"], s["f0"], s["Tp"], s["tpk"])
     for p in w.probes:
@@ -813,9 +817,10 @@ def main():
     line["e2e"] = {"value": round(world * w.cells * ke / te / 1e6, 1), "unit": UNIT,
                    "h2d_bytes_per_step": round((w.cells + 64 * len(w.materials)) / ke, 1),
                    "d2h_bytes_per_step": 8 * (9 * len(w.probes) + 1), "steps": ke,
-                   "includes": "create + set_materials (host preprocessing, H2D) + the headline run's tiling + per step: "
-                               "step call and D2H of the step's probe rows and energy into pinned host rings; one "
-                               "synchronisation at the end"}
+                   "includes": "create (device memory from torch's caching allocator, the timed run's handle "
+                               "released before) + set_materials (host preprocessing, H2D of the material ids) + the "
+                               "headline run's tiling + per step: step call and D2H of the step's probe rows and "
+                               "energy into pinned host rings; one synchronisation at the end"}
 
     if world > 1 and not args.no_extra:   # every rank takes part
         line["batch_sweep_sharded"] = sharded_sweep(torch, pkg, W, world, rank)
