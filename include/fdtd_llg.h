@@ -25,7 +25,11 @@
  * j = ny, k = nz) is stored in separate wall arrays (FDTD_F_HX_WALL ...).
  *
  * Edge material: eps_r and sigma of an edge are the mean over its four
- * cells; an edge touching a PEC cell, or lying in a wall, holds E = 0.  A
+ * cells; an edge touching a PEC cell, or lying in a wall, holds E = 0.  The
+ * E update ca E^n + cb (curl H - J) is applied in FP32 as E^n + ((ca - 1)
+ * E^n + cb (curl H - J)) with ca - 1 = -sigma / (eps/dt + sigma/2), which
+ * FP32 holds to full relative precision where ca next to 1 would lose a
+ * weak conductor's loss to rounding.  A
  * face adjacent to a magnetic cell subtracts half of that cell's change of
  * M; H_eff at a cell centre is the mean of the two faces of each component
  * plus H_bias.  Magnetisation is held as its deviation m = M - Ms h from the
@@ -484,8 +488,10 @@ int fdtd_llg_fit_coupling(const double *f_plus, const double *f_minus, int32_t n
  * point exists for callers that cannot allocate device memory (code running
  * inside another framework's memory pool, a real-time loop that forbids
  * allocation, a host that hands the library a fixed set of buffers).  It does
- * one Ampere update E = ca E + cb curl H of a uniform medium (eps_r, sigma)
- * with PEC walls on caller-owned device arrays in the compact layout
+ * one Ampere update E = ca E + cb curl H of a uniform medium (eps_r, sigma),
+ * in FP32 as E + ((ca - 1) E + cb curl H) like the solver's own update (ca - 1
+ * = -sigma / (eps/dt + sigma/2) keeps its full relative precision where ca
+ * next to 1 would not), with PEC walls on caller-owned device arrays in the compact layout
  * (nx*ny*nz floats each, pitch nx; wall edges stay zero) and, when w_e is not
  * NULL, writes the FP64 electric energy (eps0 eps_r / 2) sum E^2 dx dy dz of
  * the result to the device double *w_e.  Work is queued on `stream`
