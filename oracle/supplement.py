@@ -22,9 +22,13 @@ Readings (the supplement leaves them open):
     tabulated 7.1 (which gives 791 m^-1);
   * w_m is the Kittel frequency gamma' sqrt(H (H + Ms)) of the tabulated
     gamma' and Ms at 1800 Oe (14.1726 GHz, printed 14.17).
-Parity of <theta_zy> is unpinned: for the stated sizes the solve (and its
-thin-film closed form) gives ~1.36e7 Hz, far from the printed 4.966e9 Hz;
-the printed k^m and the Kittel frequency are reproduced.
+The printed k^m and the Kittel frequency are reproduced, and the printed
+<theta_zy> = 4.966e9 Hz is the film mean of Eq. S8's form evaluated on the
+printed Eq. S10 coefficients (real part to 7e-4).  Those coefficients are,
+though, a common 2.29 % above this solve's (same phases), and that excess
+is the whole printed coupling: the solve itself gives ~1.36e7 Hz, so the
+printed value stays unreproduced from the stated inputs (parity of the
+solve's <theta_zy> against the printed number unpinned).
 """
 from __future__ import annotations
 
@@ -97,8 +101,15 @@ def layered_field(w: float, d1: float, d2: float, L: float, eps_m: float, eps_c:
     ], dtype=complex)
     rhs = np.array([-M, -M, 0, 0], dtype=complex)
     a, b, c, d = np.linalg.solve(A, rhs)
-    mean = (c * (e(1j * km * d2) - e(1j * km * d1)) - d * (e(-1j * km * d2) - e(-1j * km * d1))) / (1j * km) / (d2 - d1) - M
-    return a, b, c, d, mean, np.linalg.det(A)
+    return a, b, c, d, film_mean(c, d, km, d1, d2, M), np.linalg.det(A)
+
+
+def film_mean(c: complex, d: complex, km: complex, d1: float, d2: float, M: float) -> complex:
+    """The film's mean field of Eq. S8's form C e^{i k z} + D e^{-i k z} - M
+    over [d1, d2] (the average that Eq. S13 takes, times gamma, as the
+    coupling)."""
+    e = np.exp
+    return (c * (e(1j * km * d2) - e(1j * km * d1)) - d * (e(-1j * km * d2) - e(-1j * km * d1))) / (1j * km) / (d2 - d1) - M
 
 
 def theta_zy(w: float, H: float, p=TABLE_S1, eps_m: float = 1.0, d1: float | None = None) -> complex:
