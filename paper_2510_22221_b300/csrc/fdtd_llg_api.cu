@@ -627,6 +627,7 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
         break;
     }
     if (nc && hc.top >= (unsigned)ntable) return fail(h, FDTD_E_INVAL, "mat_id references a material beyond ntable");
+    if (hc.mcount > K.mcap) return fail(h, FDTD_E_CUDA, "the device's list of magnetic cells overflowed");
     if (hc.overflow)
         return fail(h, FDTD_E_INVAL, "more than " + std::to_string(K.cap) + " distinct material neighbourhoods");
     std::vector<std::pair<uint64_t, uint64_t>> first_key(hc.kcount);   // (first cell, key)
@@ -689,18 +690,23 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
     const bool c16 = nclass > 256;
     // magnetic regions: face-connected components of cells with Ms > 0,
     // numbered in the order of their first cell
-    std::unordered_map<size_t, int> label;
-    label.reserve(2 * magcells.size());
+    // region label per magnetic cell, by its index in the sorted list of
+    // magnetic cells (every magnetic cell is in it)
+    std::vector<int> label(magcells.size(), -1);
+    auto mag_index = [&](size_t c) {
+        return (size_t)(std::lower_bound(magcells.begin(), magcells.end(), c) - magcells.begin());
+    };
     struct Box { int x0, y0, z0, x1, y1, z1; };
     std::vector<Box> boxes;
     std::vector<size_t> stack;
-    for (size_t c0 : magcells) {
-        if (label.count(c0)) continue;
+    for (size_t q0 = 0; q0 < magcells.size(); ++q0) {
+        if (label[q0] >= 0) continue;
+        const size_t c0 = magcells[q0];
         const int L = (int)boxes.size();
         Box b{nx, ny, nz, -1, -1, -1};
         stack.clear();
         stack.push_back(c0);
-        label.emplace(c0, L);
+        label[q0] = L;
         while (!stack.empty()) {
             const size_t c = stack.back();
             stack.pop_back();
@@ -711,7 +717,15 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
             for (auto &q : nb) {
                 if (q[0] < 0 || q[1] < 0 || q[2] < 0 || q[0] >= nx || q[1] >= ny || q[2] >= nz) continue;
                 const size_t cc = cid(q[0], q[1], q[2]);
-                if (magm[mid[cc]] && label.emplace(cc, L).second) stack.push_back(cc);
+                if (!magm[mid[cc]]) continue;
+                const size_t qi = mag_index(cc);
+                if (qi >= magcells.size() || magcells[qi] != cc)
+                    return fail(h, FDTD_E_CUDA, "the device's list of magnetic cells is incomplete");
+                int &lc = label[qi];
+                if (lc < 0) {
+                    lc = L;
+                    stack.push_back(cc);
+                }
             }
         }
         std::string why;
@@ -760,8 +774,7 @@ extern "C" int fdtd_llg_set_materials(fdtd_llg_t h, const uint8_t *mat_id, const
                 for (int li = 0; li < C.bx; ++li) {
                     const int v = (lk * C.by + lj) * C.bx + li;
                     const size_t c = cid(C.x0 + li, C.y0 + lj, C.z0 + lk);
-                    const auto it = label.find(c);
-                    hmat[off + v] = it != label.end() && it->second == (int)L ? (uint8_t)mm_index[mid[c]] : 0xFF;
+                    hmat[off + v] = magm[mid[c]] && label[mag_index(c)] == (int)L ? (uint8_t)mm_index[mid[c]] : 0xFF;
                 }
         C.m = I.mbuf + 3 * off;
         C.mat = I.magmat + off;
