@@ -12,7 +12,11 @@ solved by Eqs. S8 (forward and backward waves, minus M in the film), with
 E_i ~ (sigma - i eps0 eps_r w)^-1 (-dH_j/dz) from Eq. S9 continuous with H at
 z = d1, d2.  The film's mean field per unit m_y, times gamma, is the coupling
 <theta_zy> (Eq. S13); the susceptibility follows from Eq. S5b and the
-absorbed power from Eq. S1.
+absorbed power from Eq. S1.  layered_field solves the same equations for
+the cavity a PEC-walled solver can hold: walls of either kind and fields of
+Eq. S7 times a fixed transverse sine (a guided mode, k^2 -> k^2 - kt^2);
+cavity_poles gives the resonances of the absorbed power as the complex
+poles of chi with that solve's coupling.
 
 Readings (the supplement leaves them open):
   * the film is centred in the cavity (the phases of the printed Eq. S10
