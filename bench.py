@@ -326,6 +326,51 @@ def _peak(freqs, spec):
     return float(freqs[k])
 
 
+def quasi1d_run(torch, pkg, W):
+    """The supplement's film (Table S1) across a PEC parallel-plate resonator
+    at 1700/1800/1900 Oe, one batch of three 20160 x 32 x 1 grids from a
+    tilted film, 680 000 steps (1.5 ns): ESPRIT polaritons of the film's m_y
+    (library fit, block means of 1000 steps) against the stored analytic
+    poles of the supplement's model for the same resonator
+    (tests/golden/quasi1d_poles.json, written by the oracle's own script)."""
+    import numpy as np
+
+    ref = _golden("quasi1d_poles.json")
+    ws = W.quasi1d_film()
+    steps = ws[0].steps
+    batch = pkg.FdtdLlg.create_batch([(x.nx, x.ny, x.nz) for x in ws], [(x.dx, x.dy, x.dz) for x in ws],
+                                     courant_factor=ws[0].courant, probe_capacity=steps)
+    members = [batch.batch_member(q) for q in range(len(ws))]
+    tilt = 1e-3
+    for m, w in zip(members, ws):
+        pkg.configure(m, w)
+        ms = w.materials[1]["Ms"]
+        s = tilt * np.sin(np.pi * (np.arange(w.ny) + 0.5) / w.ny)[None, :, None] * (w.mat_id == 1)
+        m.set_field("dMy", ms * s)
+        m.set_field("dMz", ms * (np.sqrt(1.0 - s * s) - 1.0))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batch.step(steps)
+    batch.sync()
+    t = time.perf_counter() - t0
+    cells = sum(w.cells for w in ws)
+    runs = []
+    for q, (m, w) in enumerate(zip(members, ws)):
+        f, a, _, _ = pkg.fit_modes(m.probe(0)[:, 7], batch.dt, 12, pencil=200, fmin=9.5e9, fmax=12e9, max_modes=2,
+                                   decimate=1000)
+        r = {"name": w.name, "freq_hz": [float(v) for v in f], "decay_per_s": [float(v) for v in a]}
+        if ref is not None and len(f) == 2:
+            fa, aa = np.array(ref["runs"][q]["freq_hz"]), np.array(ref["runs"][q]["decay_per_s"])
+            r["freq_rel_err_max"] = float(np.max(np.abs(f - fa) / fa))
+            r["decay_rel_err_max"] = float(np.max(np.abs(a - aa) / aa))
+            r["splitting_rel_err"] = float(abs((f[1] - f[0]) / (fa[1] - fa[0]) - 1))
+        runs.append(r)
+    batch.destroy()
+    return {"workload": "quasi1d_film_3x20160x32x1", "steps": steps, "cells": cells,
+            "mcells_per_s": round(cells * steps / t / 1e6, 1), "ms_per_step": round(t / steps * 1e3, 5),
+            "reference": "analytic poles, tests/golden/quasi1d_poles.json" if ref else None, "runs": runs}
+
+
 def precision_vs_fp64(torch, pkg, W):
     """The FP32 strip-resonator run of 20000 steps against the stored FP64
     oracle run: largest relative L2 error of the probe spectra (|DFT| of E_x,
@@ -646,7 +691,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-extra", action="store_true", help="skip the adjoint, batched-sweep, 512x512x256 and absorbing-layer measurements")
-    ap.add_argument("--only", choices=["adjoint", "sweep", "large", "pml", "cpw", "cpw_fp", "surrogate", "cpu_table"],
+    ap.add_argument("--only", choices=["adjoint", "sweep", "large", "pml", "cpw", "cpw_fp", "surrogate", "cpu_table", "quasi1d"],
                     help="run just one of the extra measurements and print its JSON object")
     ap.add_argument("--adjoint-steps", type=int, default=4000, help="steps of the adjoint measurement")
     ap.add_argument("--cpw-steps", type=int, default=700_000, help="steps of the CPW resonance measurement (--only cpw_fp)")
@@ -678,6 +723,8 @@ def main():
             out = surrogate_run(torch)
         elif args.only == "cpu_table":
             out = cpu_table(torch, pkg, W)
+        elif args.only == "quasi1d":
+            out = quasi1d_run(torch, pkg, W)
         elif args.only == "cpw_fp":
             out = cpw_resonance(torch, pkg, W, steps=args.cpw_steps, film=args.cpw_film, h0_oe=args.cpw_h0,
                                 split=args.cpw_split)
