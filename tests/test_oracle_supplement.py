@@ -196,3 +196,21 @@ def test_printed_coupling_is_the_film_mean_of_the_printed_coefficients():
     _, _, c, d, _ = S.film_field(W_M, d1, d1 + t, d3, 1.0, 1.0, P["sigma_m"], P["sigma_c"], M=P["Ms"])
     assert abs(C) / abs(c) == pytest.approx(1.0229, abs=2e-4)
     assert abs(D) / abs(d) == pytest.approx(1.0229, abs=2e-4)
+
+
+def test_stored_quasi1d_poles_are_the_oracle_s():
+    """The stored poles the bench compares its quasi-1-D run with
+    (tests/golden/quasi1d_poles.json) are this oracle's, recomputed."""
+    import json
+    import os
+
+    from paper_2510_22221_b300 import workloads as W
+    from tests.golden.make_quasi1d_poles import poles
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "quasi1d_poles.json")) as f:
+        ref = json.load(f)
+    for w, r in zip(W.quasi1d_film(), ref["runs"]):
+        z = poles(w)
+        assert r["name"] == w.name
+        np.testing.assert_allclose(z.real / (2 * np.pi), r["freq_hz"], rtol=1e-12)
+        np.testing.assert_allclose(-z.imag, r["decay_per_s"], rtol=1e-9)
